@@ -1,0 +1,628 @@
+/*
+ * Oracle for the bit-adaptive particle position compressor of
+ * Ren, Di, Zhang, Zhao, Guo, "An Error-Bounded Lossy Compression Method with
+ * Bit-Adaptive Quantization for Particle Data" (arXiv 2404.02826).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded CPU
+ * restatement of the method, in double precision, written to check the CUDA
+ * library against.  Only tests/, __graft_entry__.smoke() and the CPU-baseline
+ * legs of bench.py load it; the product path never calls it.  It shares no
+ * code, header, table or helper with the CUDA library.
+ *
+ * Steps, in the paper's order (section / equation in brackets):
+ *   1. error bound eps and lattice step s   [Sec. 3, absolute / relative bound]
+ *   2. quantization onto the 2*eb lattice   [Sec. 3, linear-scale quantization, Eq. 1]
+ *   3. median k-d partition, leaves <= r    [Sec. 4.1, initial particle partitioning]
+ *   4. bit box per leaf: AABB, centre, m_d  [Sec. 4.1, bit box construction, Eq. 2]
+ *   5. codes and the sequence layout        [Fig. 2 caption; Sec. 4.2, Fig. 4]
+ *   6. decoding                             [Sec. 3, dequantization]
+ *   7. NRMSE / PSNR                         [Sec. 5.1]
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - the lattice origin is the per-axis minimum and the step is s = 2*eb',
+ *     eb' = eps - ulp_T(M2) - 4*ulp_f64(M2), M2 = 2*max(max|p|, eps), so that the
+ *     bound survives the rounding of the reconstruction to the input type;
+ *     when every particle is identical (Delta_max = 0) the step is 1;
+ *   - q = rint(((double)p - o) / s), round-half-even, one division, no
+ *     reciprocal; codes must stay below 2^30;
+ *   - the split axis is depth mod 3; a node is split on the total order
+ *     (code on the axis, original index); the first floor(n/2) go left, so the
+ *     median goes to the larger-coordinate side (Sec. 4.1);
+ *   - the bit-box centre is the leaf particle minimising the squared lattice
+ *     distance to the AABB centre, first in leaf order on ties;
+ *   - the centre is stored as its lattice code (not as a lossless float) and the
+ *     particle count replaces the end mark; see the stream layout below.
+ *
+ * Precision: compile with -ffp-contract=off so that no multiply-add is fused.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <float.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_NONFINITE 2
+#define OR_ERR_EB_TOO_SMALL 3
+#define OR_ERR_RANGE 4
+#define OR_ERR_CAPACITY 5
+#define OR_ERR_CORRUPT 6
+#define OR_ERR_NOMEM 9
+
+#define OR_F32 0
+#define OR_F64 1
+#define OR_ABS 0
+#define OR_REL 1
+
+#define OR_CODE_LIMIT (1LL << 30) /* codes must be < 2^30, so m_d <= 31 */
+#define OR_HEADER_BYTES 96u
+#define OR_LEAF_BYTES 32u
+
+/* ------------------------------------------------------------------------ */
+/* Step 1: error bound and lattice (Sec. 3).                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double lo[3], hi[3];  /* per-axis min / max of the input                    */
+    double delta_max;     /* Delta_max: largest per-axis range (Sec. 3)          */
+    double eps;           /* absolute bound: eb (abs) or eb * Delta_max (rel)    */
+    double eb_prime;      /* eps minus the rounding margin                        */
+    double s;             /* lattice step = 2 * eb'                               */
+    double o[3];          /* lattice origin = per-axis minimum                    */
+    int64_t qmax[3];      /* largest code per axis                                */
+} oracle_bound;
+
+static double coord(const void *pos, int dtype, uint64_t i, int d)
+{
+    if (dtype == OR_F32) return (double)((const float *)pos)[3 * i + d];
+    return ((const double *)pos)[3 * i + d];
+}
+
+/* Spacing of the floating-point grid with `prec` significand bits at the
+ * magnitude of x > 0 (subnormal spacing below 2^emin). */
+static double grid_spacing(double x, int prec, int emin)
+{
+    int e;
+    (void)frexp(x, &e); /* x = f * 2^e, f in [0.5, 1) */
+    int ex = e - 1;     /* floor(log2 x) */
+    if (ex < emin) ex = emin;
+    return ldexp(1.0, ex - (prec - 1));
+}
+
+/* Quantization code of one coordinate: index of the 2*eb' interval that holds
+ * it, counted from the origin (Sec. 3, Eq. 1 with the prediction at o). */
+static int64_t quantize_one(double p, double o, double s)
+{
+    double t = (p - o) / s;
+    return (int64_t)nearbyint(t);
+}
+
+int oracle_error_bound(const void *pos, uint64_t n, int dtype, int eb_mode, double eb,
+                       oracle_bound *b)
+{
+    if (dtype != OR_F32 && dtype != OR_F64) return OR_ERR_ARG;
+    if (eb_mode != OR_ABS && eb_mode != OR_REL) return OR_ERR_ARG;
+    if (!(eb > 0.0) || !isfinite(eb)) return OR_ERR_ARG;
+    if (n > 0 && pos == NULL) return OR_ERR_ARG;
+    memset(b, 0, sizeof(*b));
+    b->s = 1.0;
+    if (n == 0) {
+        b->eps = (eb_mode == OR_ABS) ? eb : 0.0;
+        b->eb_prime = b->eps;
+        return OR_OK;
+    }
+    for (int d = 0; d < 3; d++) {
+        b->lo[d] = INFINITY;
+        b->hi[d] = -INFINITY;
+    }
+    for (uint64_t i = 0; i < n; i++)
+        for (int d = 0; d < 3; d++) {
+            double v = coord(pos, dtype, i, d);
+            if (!isfinite(v)) return OR_ERR_NONFINITE;
+            if (v < b->lo[d]) b->lo[d] = v;
+            if (v > b->hi[d]) b->hi[d] = v;
+        }
+    /* Delta_max: the maximum range of coordinates across all dimensions. */
+    b->delta_max = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double r = b->hi[d] - b->lo[d];
+        if (r > b->delta_max) b->delta_max = r;
+    }
+    b->eps = (eb_mode == OR_ABS) ? eb : eb * b->delta_max;
+    for (int d = 0; d < 3; d++) b->o[d] = b->lo[d];
+    if (b->delta_max == 0.0) { /* every particle identical: all codes are 0 */
+        b->eb_prime = b->eps;
+        b->s = 1.0;
+        return OR_OK;
+    }
+    double m = 0.0;
+    for (int d = 0; d < 3; d++) {
+        if (fabs(b->lo[d]) > m) m = fabs(b->lo[d]);
+        if (fabs(b->hi[d]) > m) m = fabs(b->hi[d]);
+    }
+    double m2 = 2.0 * (m > b->eps ? m : b->eps);
+    double tmax = (dtype == OR_F32) ? (double)FLT_MAX : DBL_MAX;
+    if (!(m2 <= tmax)) return OR_ERR_RANGE;
+    double ulp_t = (dtype == OR_F32) ? grid_spacing(m2, 24, -126) : grid_spacing(m2, 53, -1022);
+    double ulp_d = grid_spacing(m2, 53, -1022);
+    b->eb_prime = b->eps - ulp_t - 4.0 * ulp_d;
+    if (!(b->eb_prime > 0.0)) return OR_ERR_EB_TOO_SMALL;
+    b->s = 2.0 * b->eb_prime;
+    for (int d = 0; d < 3; d++) {
+        b->qmax[d] = quantize_one(b->hi[d], b->o[d], b->s);
+        if (b->qmax[d] >= OR_CODE_LIMIT) return OR_ERR_RANGE;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 2: quantization (Sec. 3).                                            */
+/* ------------------------------------------------------------------------ */
+
+int oracle_quantize(const void *pos, uint64_t n, int dtype, const oracle_bound *b, int64_t *q)
+{
+    for (uint64_t i = 0; i < n; i++)
+        for (int d = 0; d < 3; d++) q[3 * i + d] = quantize_one(coord(pos, dtype, i, d), b->o[d], b->s);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 3: median k-d partition (Sec. 4.1).                                  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t key;
+    uint64_t idx;
+} keyed;
+
+static int by_key_then_index(const void *a, const void *b)
+{
+    const keyed *x = (const keyed *)a, *y = (const keyed *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+    return 0;
+}
+
+static int by_index(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+typedef struct {
+    uint64_t *leaf_off, *leaf_cnt;
+    uint64_t num_leaves, cap;
+} leaf_list;
+
+static int leaf_push(leaf_list *l, uint64_t off, uint64_t cnt)
+{
+    if (l->num_leaves == l->cap) {
+        uint64_t nc = l->cap ? 2 * l->cap : 64;
+        uint64_t *a = realloc(l->leaf_off, nc * sizeof(uint64_t));
+        if (!a) return OR_ERR_NOMEM;
+        l->leaf_off = a;
+        uint64_t *c = realloc(l->leaf_cnt, nc * sizeof(uint64_t));
+        if (!c) return OR_ERR_NOMEM;
+        l->leaf_cnt = c;
+        l->cap = nc;
+    }
+    l->leaf_off[l->num_leaves] = off;
+    l->leaf_cnt[l->num_leaves] = cnt;
+    l->num_leaves++;
+    return OR_OK;
+}
+
+/* ids[0..cnt) holds the node's particles in increasing original index.  A node
+ * with at most r particles is a subregion (leaf).  Otherwise the node is split
+ * by the median on axis depth mod 3: sorting the node by (code, index), the
+ * first floor(cnt/2) particles form the left child, so the median itself lies
+ * on the side with larger coordinates.  Both children keep index order. */
+static int split_node(const int64_t *q, uint64_t *ids, uint64_t base, uint64_t cnt, int depth, uint64_t r,
+                      leaf_list *leaves)
+{
+    if (cnt <= r) return leaf_push(leaves, base, cnt);
+    int axis = depth % 3;
+    keyed *tmp = malloc(cnt * sizeof(keyed));
+    if (!tmp) return OR_ERR_NOMEM;
+    for (uint64_t i = 0; i < cnt; i++) {
+        tmp[i].key = q[3 * ids[base + i] + axis];
+        tmp[i].idx = ids[base + i];
+    }
+    qsort(tmp, cnt, sizeof(keyed), by_key_then_index);
+    uint64_t k = cnt / 2;
+    for (uint64_t i = 0; i < cnt; i++) ids[base + i] = tmp[i].idx;
+    free(tmp);
+    qsort(ids + base, k, sizeof(uint64_t), by_index);
+    qsort(ids + base + k, cnt - k, sizeof(uint64_t), by_index);
+    int rc = split_node(q, ids, base, k, depth + 1, r, leaves);
+    if (rc) return rc;
+    return split_node(q, ids, base + k, cnt - k, depth + 1, r, leaves);
+}
+
+/* order[0..n): original indices, leaves concatenated left to right.
+ * leaf_off / leaf_cnt: allocated here (free with oracle_free). */
+int oracle_kdtree(const int64_t *q, uint64_t n, uint64_t r, uint64_t *order, uint64_t **leaf_off,
+                  uint64_t **leaf_cnt, uint64_t *num_leaves)
+{
+    if (r < 1) return OR_ERR_ARG;
+    leaf_list l = {0};
+    for (uint64_t i = 0; i < n; i++) order[i] = i;
+    int rc = OR_OK;
+    if (n > 0) rc = split_node(q, order, 0, n, 0, r, &l);
+    if (rc) {
+        free(l.leaf_off);
+        free(l.leaf_cnt);
+        return rc;
+    }
+    *leaf_off = l.leaf_off;
+    *leaf_cnt = l.leaf_cnt;
+    *num_leaves = l.num_leaves;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 4: bit box of one leaf (Sec. 4.1, Eq. 2).                            */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 2 on the lattice.  With positions on the lattice the distance from the
+ * centre is D = s*R and 2*eb' = s, so Eq. 2 reads m = ceil(log2(R + 0.5) + 1).
+ * For R = 0 that is 0.  For R >= 1 it is the least m with 2^(m-1) - 1 >= R,
+ * i.e. the bit length of R plus one. */
+uint32_t oracle_num_bits(uint64_t R)
+{
+    if (R == 0) return 0;
+    uint32_t m = 1;
+    while (((1ULL << (m - 1)) - 1ULL) < R) m++;
+    return m;
+}
+
+/* leafq[0..n) x 3 codes of one leaf in leaf order.  Outputs: centre position in
+ * the leaf, the AABB, the centre code and m_d. */
+int oracle_bitbox(const int64_t *leafq, uint64_t n, uint64_t *centre, int64_t lo[3], int64_t hi[3],
+                  int64_t qref[3], uint32_t m[3])
+{
+    if (n == 0) return OR_ERR_ARG;
+    for (int d = 0; d < 3; d++) lo[d] = hi[d] = leafq[d];
+    for (uint64_t i = 1; i < n; i++)
+        for (int d = 0; d < 3; d++) {
+            if (leafq[3 * i + d] < lo[d]) lo[d] = leafq[3 * i + d];
+            if (leafq[3 * i + d] > hi[d]) hi[d] = leafq[3 * i + d];
+        }
+    /* The centre is the particle closest to the AABB centre (lo+hi)/2; in
+     * doubled lattice units the squared distance is an exact integer. */
+    uint64_t best = 0, best_d2 = UINT64_MAX;
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t d2 = 0;
+        for (int d = 0; d < 3; d++) {
+            int64_t t = 2 * leafq[3 * i + d] - lo[d] - hi[d];
+            d2 += (uint64_t)(t * t);
+        }
+        if (d2 < best_d2) {
+            best_d2 = d2;
+            best = i;
+        }
+    }
+    *centre = best;
+    for (int d = 0; d < 3; d++) {
+        qref[d] = leafq[3 * best + d];
+        int64_t a = qref[d] - lo[d], c = hi[d] - qref[d];
+        uint64_t R = (uint64_t)(a > c ? a : c);
+        m[d] = oracle_num_bits(R);
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 5: stream layout (Sec. 4.2, Fig. 4; Fig. 2 caption for the codes).   */
+/*                                                                          */
+/* Header, 96 bytes, little-endian:                                          */
+/*   0 "PCB1"  4 u16 version=1  6 u8 dtype  7 u8 eb_mode  8 u64 n             */
+/*   16 f64 eb as given  24 f64 eps  32 f64 s  40 f64 o[3]                    */
+/*   64 u64 num_leaves  72 u64 payload_words  80 u32 leaf_size  84..95 zero   */
+/* Leaf table, 32 bytes per sequence (leaf), in leaf order:                  */
+/*   0 u64 first output particle  8 u64 first payload word                   */
+/*   16 i32 q_ref[3] (centre code)  28 u8 m[3]  31 u8 zero                    */
+/* Payload: u32 words.  Each leaf starts on a fresh word; its non-centre      */
+/* particles follow in leaf order, each as c_x (m_x bits), c_y, c_z, packed   */
+/* least-significant bit first.  c_d = (q_d - q_ref_d) + 2^(m_d-1) - 1.        */
+/* ------------------------------------------------------------------------ */
+
+static void put_u16(uint8_t *p, uint16_t v)
+{
+    p[0] = (uint8_t)v;
+    p[1] = (uint8_t)(v >> 8);
+}
+static void put_u32(uint8_t *p, uint32_t v)
+{
+    for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+static void put_u64(uint8_t *p, uint64_t v)
+{
+    for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+static void put_f64(uint8_t *p, double v)
+{
+    uint64_t u;
+    memcpy(&u, &v, 8);
+    put_u64(p, u);
+}
+static uint16_t get_u16(const uint8_t *p) { return (uint16_t)(p[0] | (p[1] << 8)); }
+static uint32_t get_u32(const uint8_t *p)
+{
+    uint32_t v = 0;
+    for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i);
+    return v;
+}
+static uint64_t get_u64(const uint8_t *p)
+{
+    uint64_t v = 0;
+    for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+static double get_f64(const uint8_t *p)
+{
+    uint64_t u = get_u64(p);
+    double v;
+    memcpy(&v, &u, 8);
+    return v;
+}
+
+/* Append `nbits` low bits of `v` to the word array, least significant first. */
+static void write_bits(uint32_t *words, uint64_t *bitpos, uint64_t v, uint32_t nbits)
+{
+    for (uint32_t b = 0; b < nbits; b++) {
+        uint64_t pos = *bitpos + b;
+        if ((v >> b) & 1ULL) words[pos >> 5] |= 1u << (pos & 31);
+    }
+    *bitpos += nbits;
+}
+
+static uint64_t read_bits(const uint32_t *words, uint64_t bitpos, uint32_t nbits)
+{
+    uint64_t v = 0;
+    for (uint32_t b = 0; b < nbits; b++) {
+        uint64_t pos = bitpos + b;
+        if ((words[pos >> 5] >> (pos & 31)) & 1u) v |= 1ULL << b;
+    }
+    return v;
+}
+
+/* Number of leaves the partition produces, for sizing. */
+static uint64_t leaves_for(uint64_t n, uint64_t r)
+{
+    if (n == 0) return 0;
+    if (n <= r) return 1;
+    return leaves_for(n / 2, r) + leaves_for(n - n / 2, r);
+}
+
+/* Full compression.  On success *out (malloc'd) holds the stream and *perm
+ * (malloc'd, may be NULL on request) maps each decoded particle to its
+ * original index. */
+int oracle_compress(const void *pos, uint64_t n, int dtype, int eb_mode, double eb, uint64_t leaf_size,
+                    uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out)
+{
+    *out = NULL;
+    *out_bytes = 0;
+    if (perm_out) *perm_out = NULL;
+    if (leaf_size < 1) return OR_ERR_ARG;
+    oracle_bound b;
+    int rc = oracle_error_bound(pos, n, dtype, eb_mode, eb, &b);
+    if (rc) return rc;
+
+    int64_t *q = NULL;
+    uint64_t *order = NULL, *loff = NULL, *lcnt = NULL, *perm = NULL, nl = 0;
+    uint64_t *centre = NULL, *wofs = NULL;
+    int64_t *qref = NULL;
+    uint32_t *mm = NULL, *words = NULL;
+    uint8_t *buf = NULL;
+    rc = OR_ERR_NOMEM;
+
+    q = malloc((n ? n : 1) * 3 * sizeof(int64_t));
+    order = malloc((n ? n : 1) * sizeof(uint64_t));
+    perm = malloc((n ? n : 1) * sizeof(uint64_t));
+    if (!q || !order || !perm) goto done;
+    oracle_quantize(pos, n, dtype, &b, q);
+    rc = oracle_kdtree(q, n, leaf_size, order, &loff, &lcnt, &nl);
+    if (rc) goto done;
+    rc = OR_ERR_NOMEM;
+
+    centre = malloc((nl ? nl : 1) * sizeof(uint64_t));
+    wofs = malloc((nl ? nl : 1) * sizeof(uint64_t));
+    qref = malloc((nl ? nl : 1) * 3 * sizeof(int64_t));
+    mm = malloc((nl ? nl : 1) * 3 * sizeof(uint32_t));
+    uint64_t maxleaf = leaf_size < n ? leaf_size : n;
+    int64_t *leafq = malloc((maxleaf ? maxleaf : 1) * 3 * sizeof(int64_t));
+    if (!centre || !wofs || !qref || !mm || !leafq) {
+        free(leafq);
+        goto done;
+    }
+    /* Bit boxes, and the size of each leaf's code block: storage-cost term (3)
+     * of Sec. 4.2, (m_x + m_y + m_z)(n_s - 1) bits, rounded up to words. */
+    uint64_t total_words = 0;
+    for (uint64_t L = 0; L < nl; L++) {
+        for (uint64_t i = 0; i < lcnt[L]; i++)
+            for (int d = 0; d < 3; d++) leafq[3 * i + d] = q[3 * order[loff[L] + i] + d];
+        int64_t lo[3], hi[3];
+        oracle_bitbox(leafq, lcnt[L], &centre[L], lo, hi, &qref[3 * L], &mm[3 * L]);
+        uint64_t bits = (uint64_t)(mm[3 * L] + mm[3 * L + 1] + mm[3 * L + 2]) * (lcnt[L] - 1);
+        wofs[L] = total_words;
+        total_words += (bits + 31) / 32;
+    }
+    free(leafq);
+
+    uint64_t bytes = OR_HEADER_BYTES + OR_LEAF_BYTES * nl + 4 * total_words;
+    buf = calloc(bytes, 1);
+    if (!buf) goto done;
+    memcpy(buf, "PCB1", 4);
+    put_u16(buf + 4, 1);
+    buf[6] = (uint8_t)dtype;
+    buf[7] = (uint8_t)eb_mode;
+    put_u64(buf + 8, n);
+    put_f64(buf + 16, eb);
+    put_f64(buf + 24, b.eps);
+    put_f64(buf + 32, b.s);
+    for (int d = 0; d < 3; d++) put_f64(buf + 40 + 8 * d, b.o[d]);
+    put_u64(buf + 64, nl);
+    put_u64(buf + 72, total_words);
+    put_u32(buf + 80, (uint32_t)leaf_size);
+    words = calloc(total_words ? total_words : 1, sizeof(uint32_t));
+    if (!words) goto done;
+
+    uint64_t outpos = 0;
+    for (uint64_t L = 0; L < nl; L++) {
+        uint8_t *rec = buf + OR_HEADER_BYTES + OR_LEAF_BYTES * L;
+        put_u64(rec + 0, loff[L]);
+        put_u64(rec + 8, wofs[L]);
+        for (int d = 0; d < 3; d++) put_u32(rec + 16 + 4 * d, (uint32_t)(int32_t)qref[3 * L + d]);
+        for (int d = 0; d < 3; d++) rec[28 + d] = (uint8_t)mm[3 * L + d];
+        /* Decoded order: the centre first, then the rest in leaf order. */
+        perm[outpos++] = order[loff[L] + centre[L]];
+        uint64_t bitpos = 32 * wofs[L];
+        for (uint64_t i = 0; i < lcnt[L]; i++) {
+            if (i == centre[L]) continue;
+            uint64_t id = order[loff[L] + i];
+            perm[outpos++] = id;
+            for (int d = 0; d < 3; d++) {
+                uint32_t md = mm[3 * L + d];
+                if (md == 0) continue;
+                /* Code of the interval holding the particle: the centre's own
+                 * interval is 2^(m-1) - 1 (Fig. 2 caption: one below is 2^(m-1) - 2). */
+                int64_t c = (q[3 * id + d] - qref[3 * L + d]) + ((1LL << (md - 1)) - 1);
+                write_bits(words, &bitpos, (uint64_t)c, md);
+            }
+        }
+    }
+    for (uint64_t w = 0; w < total_words; w++)
+        put_u32(buf + OR_HEADER_BYTES + OR_LEAF_BYTES * nl + 4 * w, words[w]);
+
+    *out = buf;
+    buf = NULL;
+    *out_bytes = bytes;
+    if (perm_out) {
+        *perm_out = perm;
+        perm = NULL;
+    }
+    rc = OR_OK;
+done:
+    free(q);
+    free(order);
+    free(loff);
+    free(lcnt);
+    free(perm);
+    free(centre);
+    free(wofs);
+    free(qref);
+    free(mm);
+    free(words);
+    free(buf);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 6: decoding (Sec. 3).  The reconstruction of code q on axis d is     */
+/* (T)(o_d + s*q): one double multiply, one double add, one rounding to T.   */
+/* ------------------------------------------------------------------------ */
+
+int oracle_stream_header(const uint8_t *st, uint64_t bytes, uint64_t *n, int *dtype, uint64_t *num_leaves,
+                         uint64_t *payload_words)
+{
+    if (bytes < OR_HEADER_BYTES) return OR_ERR_CORRUPT;
+    if (memcmp(st, "PCB1", 4) != 0 || get_u16(st + 4) != 1) return OR_ERR_CORRUPT;
+    if (st[6] > 1 || st[7] > 1) return OR_ERR_CORRUPT;
+    *n = get_u64(st + 8);
+    *dtype = st[6];
+    *num_leaves = get_u64(st + 64);
+    *payload_words = get_u64(st + 72);
+    if (*num_leaves > *n) return OR_ERR_CORRUPT;
+    if (*num_leaves > (bytes - OR_HEADER_BYTES) / OR_LEAF_BYTES) return OR_ERR_CORRUPT;
+    uint64_t rest = bytes - OR_HEADER_BYTES - OR_LEAF_BYTES * *num_leaves;
+    if (*payload_words > rest / 4) return OR_ERR_CORRUPT;
+    if ((*n > 0) != (*num_leaves > 0)) return OR_ERR_CORRUPT;
+    return OR_OK;
+}
+
+int oracle_decompress(const uint8_t *st, uint64_t bytes, void *out, uint64_t out_capacity_bytes)
+{
+    uint64_t n, nl, nw;
+    int dtype;
+    int rc = oracle_stream_header(st, bytes, &n, &dtype, &nl, &nw);
+    if (rc) return rc;
+    uint64_t esz = dtype == OR_F32 ? 4 : 8;
+    if (out_capacity_bytes < 3 * esz * n) return OR_ERR_CAPACITY;
+    double s = get_f64(st + 32), o[3];
+    for (int d = 0; d < 3; d++) o[d] = get_f64(st + 40 + 8 * d);
+    const uint8_t *tab = st + OR_HEADER_BYTES;
+    const uint8_t *pay = tab + OR_LEAF_BYTES * nl;
+    uint32_t *words = malloc((nw ? nw : 1) * sizeof(uint32_t));
+    if (!words) return OR_ERR_NOMEM;
+    for (uint64_t w = 0; w < nw; w++) words[w] = get_u32(pay + 4 * w);
+    uint64_t expect_word = 0;
+    rc = OR_OK;
+    for (uint64_t L = 0; L < nl && rc == OR_OK; L++) {
+        const uint8_t *rec = tab + OR_LEAF_BYTES * L;
+        uint64_t po = get_u64(rec), wo = get_u64(rec + 8);
+        uint64_t pend = (L + 1 < nl) ? get_u64(rec + OR_LEAF_BYTES) : n;
+        int64_t qref[3];
+        uint32_t m[3];
+        for (int d = 0; d < 3; d++) {
+            qref[d] = (int32_t)get_u32(rec + 16 + 4 * d);
+            m[d] = rec[28 + d];
+        }
+        if ((L == 0 && po != 0) || pend <= po || pend > n || wo != expect_word || m[0] > 31 || m[1] > 31 ||
+            m[2] > 31) {
+            rc = OR_ERR_CORRUPT;
+            break;
+        }
+        uint64_t cnt = pend - po;
+        uint64_t bits = (uint64_t)(m[0] + m[1] + m[2]) * (cnt - 1);
+        expect_word = wo + (bits + 31) / 32;
+        if (expect_word > nw) {
+            rc = OR_ERR_CORRUPT;
+            break;
+        }
+        uint64_t bitpos = 32 * wo;
+        for (uint64_t i = 0; i < cnt; i++) {
+            for (int d = 0; d < 3; d++) {
+                int64_t qd = qref[d];
+                if (i > 0 && m[d] > 0) {
+                    uint64_t c = read_bits(words, bitpos, m[d]);
+                    bitpos += m[d];
+                    qd = qref[d] + (int64_t)c - ((1LL << (m[d] - 1)) - 1);
+                }
+                double y = s * (double)qd;
+                double z = o[d] + y;
+                if (dtype == OR_F32)
+                    ((float *)out)[3 * (po + i) + d] = (float)z;
+                else
+                    ((double *)out)[3 * (po + i) + d] = z;
+            }
+        }
+    }
+    if (rc == OR_OK && expect_word != nw) rc = OR_ERR_CORRUPT;
+    free(words);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 7: NRMSE and PSNR (Sec. 5.1).  perm maps decoded -> original index.  */
+/* ------------------------------------------------------------------------ */
+
+double oracle_nrmse(const void *orig, const void *dec, const uint64_t *perm, uint64_t n, int dtype,
+                    double delta_max)
+{
+    if (n == 0 || !(delta_max > 0.0)) return 0.0;
+    double acc = 0.0;
+    for (uint64_t i = 0; i < n; i++)
+        for (int d = 0; d < 3; d++) {
+            double e = (coord(orig, dtype, perm[i], d) - coord(dec, dtype, i, d)) / delta_max;
+            acc += e * e;
+        }
+    return sqrt(acc / (3.0 * (double)n));
+}
+
+double oracle_psnr(double nrmse) { return -20.0 * log10(nrmse); }
+
+uint64_t oracle_num_leaves(uint64_t n, uint64_t r) { return r ? leaves_for(n, r) : 0; }
+
+void oracle_free(void *p) { free(p); }
