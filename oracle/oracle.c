@@ -30,6 +30,7 @@
  *     median goes to the larger-coordinate side (Sec. 4.1);
  *   - the bit-box centre is the leaf particle minimising the squared lattice
  *     distance to the AABB centre, first in leaf order on ties;
+ *   - a zero minimum or maximum is taken as +0 (signed zeros compare equal);
  *   - the centre is stored as its lattice code (not as a lossless float) and the
  *     particle count replaces the end mark; see the stream layout below.
  *
@@ -123,6 +124,12 @@ int oracle_error_bound(const void *pos, uint64_t n, int dtype, int eb_mode, doub
             if (v < b->lo[d]) b->lo[d] = v;
             if (v > b->hi[d]) b->hi[d] = v;
         }
+    /* A zero extremum is taken as +0, so that the result does not depend on
+     * whether -0 or +0 was met first. */
+    for (int d = 0; d < 3; d++) {
+        if (b->lo[d] == 0.0) b->lo[d] = 0.0;
+        if (b->hi[d] == 0.0) b->hi[d] = 0.0;
+    }
     /* Delta_max: the maximum range of coordinates across all dimensions. */
     b->delta_max = 0.0;
     for (int d = 0; d < 3; d++) {

@@ -359,3 +359,14 @@ def test_centre_brute_force(oracle_mod):
         dist = ((q - mid) ** 2).sum(1)
         assert c == int(np.flatnonzero(dist == dist.min())[0])
         assert lo.tolist() == q.min(0).tolist() and hi.tolist() == q.max(0).tolist()
+
+
+def test_signed_zero_extrema_do_not_depend_on_order(oracle_mod):
+    """Reading of Sec. 3 (origin at the minimum): -0 and +0 compare equal, so a zero
+    extremum is stored as +0 whichever sign was met first."""
+    a = np.array([[0.0, 1.0, 2.0], [-0.0, 3.0, 5.0], [1.0, 2.0, 3.0]], np.float32)
+    b = a[[1, 0, 2]]
+    sa, _ = oracle_mod.compress(a, oracle_mod.ABS, 0.01)
+    sb, _ = oracle_mod.compress(b, oracle_mod.ABS, 0.01)
+    assert streamfmt.parse(sa).o == streamfmt.parse(sb).o
+    assert np.signbit(streamfmt.parse(sa).o[0]) == False  # noqa: E712
