@@ -1,0 +1,159 @@
+/*
+ * pc.h - C ABI of the GB300 particle position compressor.
+ *
+ * The library implements the hot path of the error-bounded, bit-adaptive
+ * particle compressor of Ren, Di, Zhang, Zhao and Guo (arXiv 2404.02826):
+ *   - per-particle quantization of xyz onto a lattice of step 2*eb' (Sec. 3,
+ *     linear-scale quantization, Eq. 1), origin at the per-axis minimum;
+ *   - a median k-d partition into subregions of at most r particles (Sec. 4.1,
+ *     "initial particle partitioning"; axis = depth mod 3, the median on the
+ *     larger-coordinate side);
+ *   - one bit box per subregion: the particle closest to the AABB centre and
+ *     the bits per axis m_d of Eq. 2 (Sec. 4.1, "bit box construction");
+ *   - the codes of every particle packed at those widths into one stream
+ *     (Sec. 4.2, Fig. 4 data layout), and the inverse unpack and dequantize.
+ * Everything runs in hand-written CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions
+ *   - All data pointers are DEVICE pointers unless the name starts with host_.
+ *     The caller owns every buffer; no call allocates or frees device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Positions are array-of-structs T[n][3] (x, y, z), T = float or double,
+ *     naturally aligned (4 or 8 bytes); 16-byte alignment selects vector loads.
+ *   - Every call returns a pc_status.  After an error no output is valid.
+ *   - Calls are synchronous with respect to the host where stated: compress
+ *     and decompress each read a few bytes back (the value range, then the
+ *     final size or the error word) and so return with their work finished.
+ *
+ * Stream format (little-endian), version 1:
+ *   header, 96 bytes:
+ *      0 char[4] "PCB1"   4 u16 version   6 u8 dtype   7 u8 eb_mode
+ *      8 u64 n            16 f64 eb (as given)          24 f64 eps (absolute bound)
+ *     32 f64 s (lattice step)                           40 f64 o[3] (origin)
+ *     64 u64 num_leaves   72 u64 payload_words          80 u32 leaf_size
+ *     84..95 zero
+ *   leaf table, 32 bytes per leaf (one sequence of Fig. 4 each), in k-d order:
+ *      0 u64 index of the leaf's first decoded particle
+ *      8 u64 index of the leaf's first payload word
+ *     16 i32 q_ref[3] (lattice code of the bit-box centre)
+ *     28 u8 m[3] (bits per axis, 0..31)   31 u8 zero
+ *   payload: u32 words.  Each leaf starts on a word boundary; its non-centre
+ *     particles follow in leaf order as c_x (m_x bits), c_y, c_z, packed least
+ *     significant bit first, with c_d = (q_d - q_ref_d) + 2^(m_d-1) - 1.
+ *   Stream size = 96 + 32 * num_leaves + 4 * payload_words bytes.
+ *   Decoding emits, leaf by leaf, the centre and then the other particles;
+ *   particle order is not preserved (the paper keeps positions only, Sec. 2).
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PC_OK = 0,
+    PC_ERR_ARG = 1,          /* null pointer, bad dtype/mode, eb <= 0 or not finite, n >= 2^31, bad leaf size, misalignment */
+    PC_ERR_NONFINITE = 2,    /* NaN or Inf among the positions */
+    PC_ERR_EB_TOO_SMALL = 3, /* eb' = eps - ulp_T(M2) - 4 ulp_f64(M2) <= 0, M2 = 2 max(max|p|, eps) */
+    PC_ERR_RANGE = 4,        /* some code >= 2^30, or M2 above the largest finite T */
+    PC_ERR_CAPACITY = 5,     /* output or workspace too small */
+    PC_ERR_CORRUPT = 6,      /* stream fails validation (magic, version, sizes, widths, offsets) */
+    PC_ERR_TIMEOUT = 7,      /* a bounded device wait expired; the output is invalid */
+    PC_ERR_CUDA = 8          /* a CUDA runtime call failed */
+} pc_status;
+
+typedef enum { PC_F32 = 0, PC_F64 = 1 } pc_dtype;
+
+/* Error-bound modes of Sec. 3: absolute |p - p_hat| <= eb per coordinate, or
+ * value-range-relative eps = eb * Delta_max, Delta_max = max over axes of (max - min). */
+typedef enum { PC_EB_ABS = 0, PC_EB_REL = 1 } pc_eb_mode;
+
+/* Tuning knobs.  A NULL config means defaults. */
+typedef struct {
+    uint32_t leaf_size; /* r of Sec. 4.1: largest leaf; 0 = 4096; valid 1..PC_MAX_LEAF_SIZE */
+    uint32_t flags;     /* reserved, must be 0 */
+} pc_config;
+
+#define PC_DEFAULT_LEAF_SIZE 4096u
+#define PC_MAX_LEAF_SIZE 12000u
+#define PC_MAX_PARTICLES 2147483647ull /* n < 2^31 */
+#define PC_HEADER_BYTES 96u
+#define PC_LEAF_BYTES 32u
+
+/* Decoded header (host structure). */
+typedef struct {
+    uint64_t n;
+    uint32_t dtype;   /* pc_dtype */
+    uint32_t eb_mode; /* pc_eb_mode */
+    double eb;        /* bound as given to pc_compress */
+    double eps;       /* absolute bound every coordinate honours */
+    double s;         /* lattice step */
+    double o[3];      /* lattice origin */
+    uint64_t num_leaves;
+    uint64_t payload_words;
+    uint32_t leaf_size;
+    uint64_t total_bytes; /* 96 + 32 num_leaves + 4 payload_words */
+} pc_info;
+
+/* Worst-case stream size for n particles with this config, in bytes (host only). */
+int pc_compress_bound(uint64_t n, int dtype, const pc_config *cfg, uint64_t *out_bytes);
+
+/* Device scratch needed by pc_compress, in bytes (host only).  with_perm != 0
+ * sizes it for the optional permutation output. */
+int pc_compress_workspace_size(uint64_t n, int dtype, const pc_config *cfg, int with_perm, uint64_t *out_bytes);
+
+/* Compress n particles (Sec. 3, Sec. 4.1, Sec. 4.2).
+ *   positions  device, T[n][3]
+ *   out        device, at least pc_compress_bound bytes (16-byte aligned)
+ *   out_size   host, receives the stream size in bytes
+ *   workspace  device scratch of pc_compress_workspace_size bytes (256-byte aligned)
+ *   perm       optional device u32[n]: perm[i] = input index of decoded particle i
+ * Returns after the stream is complete on `stream`.  Every coordinate decodes
+ * within eps of its input: eps = eb (PC_EB_ABS) or eb * Delta_max (PC_EB_REL). */
+int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
+                uint32_t *perm, void *stream);
+
+/* Parse a stream header held in host memory (the first 96 bytes suffice). */
+int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info);
+
+/* Device scratch needed by pc_decompress, in bytes (host only). */
+int pc_decompress_workspace_size(uint64_t *out_bytes);
+
+/* Decompress a device stream into T[n][3] positions (Sec. 3 dequantization,
+ * p_hat = (T)(o + s q) with one double multiply and one double add).
+ *   stream_data     device, stream_bytes long (16-byte aligned)
+ *   out_positions   device, out_capacity_bytes >= 3 * sizeof(T) * n
+ *   workspace       device scratch of pc_decompress_workspace_size bytes
+ * Validates the header and the leaf table; returns PC_ERR_CORRUPT on any
+ * inconsistency without writing outside the given buffers. */
+int pc_decompress(const void *stream_data, uint64_t stream_bytes, void *out_positions, uint64_t out_capacity_bytes,
+                  void *workspace, uint64_t workspace_bytes, void *stream);
+
+/* Host-buffer variants: the same operations on HOST positions and streams
+ * (pinned memory gives the fastest copies).  The device workspace holds the
+ * staged input and output as well as the scratch; size it with the
+ * *_host_workspace_size calls.  Copies run on `stream` inside the call. */
+int pc_compress_host_workspace_size(uint64_t n, int dtype, const pc_config *cfg, uint64_t *out_bytes);
+int pc_compress_host(const void *host_positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                     void *host_out, uint64_t out_capacity, uint64_t *out_size, void *workspace,
+                     uint64_t workspace_bytes, void *stream);
+int pc_decompress_host_workspace_size(uint64_t n, int dtype, uint64_t stream_bytes, uint64_t *out_bytes);
+int pc_decompress_host(const void *host_stream, uint64_t stream_bytes, void *host_positions,
+                       uint64_t out_capacity_bytes, void *workspace, uint64_t workspace_bytes, void *stream);
+
+/* Static text for a status code. */
+const char *pc_error_string(int status);
+
+/* Stream format version this library writes and reads. */
+int pc_format_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PC_H */

@@ -1,0 +1,275 @@
+"""Python binding of the GB300 particle position compressor (C ABI in include/pc.h).
+
+The functions keep the C names and only marshal arguments: torch tensors supply
+device memory and streams, and every step of the compression and
+decompression runs in the CUDA kernels of ``libpcbox.so``.  There is no CPU
+path: if the library is missing, loading fails with an error.
+
+Method: arXiv 2404.02826 (Ren, Di, Zhang, Zhao, Guo), error-bounded lossy
+compression of particle positions with bit-adaptive quantization - lattice
+quantization (Sec. 3), median k-d partition and bit boxes (Sec. 4.1, Eq. 2),
+packed sequences (Sec. 4.2, Fig. 4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcbox.so")
+
+PC_OK = 0
+PC_ERR_ARG = 1
+PC_ERR_NONFINITE = 2
+PC_ERR_EB_TOO_SMALL = 3
+PC_ERR_RANGE = 4
+PC_ERR_CAPACITY = 5
+PC_ERR_CORRUPT = 6
+PC_ERR_TIMEOUT = 7
+PC_ERR_CUDA = 8
+PC_F32 = 0
+PC_F64 = 1
+PC_EB_ABS = 0
+PC_EB_REL = 1
+PC_DEFAULT_LEAF_SIZE = 4096
+PC_MAX_LEAF_SIZE = 12000
+PC_HEADER_BYTES = 96
+PC_LEAF_BYTES = 32
+
+# every entry point declared in include/pc.h
+EXPORTS = (
+    "pc_compress_bound", "pc_compress_workspace_size", "pc_compress", "pc_stream_info",
+    "pc_decompress_workspace_size", "pc_decompress", "pc_compress_host_workspace_size", "pc_compress_host",
+    "pc_decompress_host_workspace_size", "pc_decompress_host", "pc_error_string", "pc_format_version",
+)
+
+
+class PCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib().pc_error_string(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+class pc_config(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class pc_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("dtype", ctypes.c_uint32), ("eb_mode", ctypes.c_uint32),
+                ("eb", ctypes.c_double), ("eps", ctypes.c_double), ("s", ctypes.c_double),
+                ("o", ctypes.c_double * 3), ("num_leaves", ctypes.c_uint64), ("payload_words", ctypes.c_uint64),
+                ("leaf_size", ctypes.c_uint32), ("total_bytes", ctypes.c_uint64)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build() "
+                               "(the compressor has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        u64, i32, vp, dbl = ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+        pu64 = ctypes.POINTER(u64)
+        pcfg = ctypes.POINTER(pc_config)
+        L.pc_compress_bound.argtypes = [u64, i32, pcfg, pu64]
+        L.pc_compress_workspace_size.argtypes = [u64, i32, pcfg, i32, pu64]
+        L.pc_compress.argtypes = [vp, u64, i32, i32, dbl, pcfg, vp, u64, pu64, vp, u64, vp, vp]
+        L.pc_stream_info.argtypes = [vp, u64, ctypes.POINTER(pc_info)]
+        L.pc_decompress_workspace_size.argtypes = [pu64]
+        L.pc_decompress.argtypes = [vp, u64, vp, u64, vp, u64, vp]
+        L.pc_compress_host_workspace_size.argtypes = [u64, i32, pcfg, pu64]
+        L.pc_compress_host.argtypes = [vp, u64, i32, i32, dbl, pcfg, vp, u64, pu64, vp, u64, vp]
+        L.pc_decompress_host_workspace_size.argtypes = [u64, i32, u64, pu64]
+        L.pc_decompress_host.argtypes = [vp, u64, vp, u64, vp, u64, vp]
+        L.pc_error_string.argtypes = [i32]
+        L.pc_error_string.restype = ctypes.c_char_p
+        L.pc_format_version.argtypes = []
+        for name in EXPORTS:
+            f = getattr(L, name)
+            if f.restype is ctypes.c_int and name != "pc_error_string":
+                f.restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def load():
+    """Load the CUDA library (raises if it is not built)."""
+    return _lib()
+
+
+def _check(rc: int, where: str):
+    if rc != PC_OK:
+        raise PCError(rc, where)
+
+
+def _cfg(leaf_size: int) -> pc_config:
+    return pc_config(int(leaf_size), 0)
+
+
+def _dtype_of(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return PC_F32
+    if t.dtype == torch.float64:
+        return PC_F64
+    raise TypeError("positions must be float32 or float64")
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def pc_compress_bound(n: int, dtype: int, leaf_size: int = 0) -> int:
+    out = ctypes.c_uint64()
+    _check(_lib().pc_compress_bound(n, dtype, ctypes.byref(_cfg(leaf_size)), ctypes.byref(out)), "pc_compress_bound")
+    return out.value
+
+
+def pc_compress_workspace_size(n: int, dtype: int, leaf_size: int = 0, with_perm: bool = False) -> int:
+    out = ctypes.c_uint64()
+    _check(_lib().pc_compress_workspace_size(n, dtype, ctypes.byref(_cfg(leaf_size)), int(with_perm),
+                                             ctypes.byref(out)), "pc_compress_workspace_size")
+    return out.value
+
+
+def pc_compress(positions, eb_mode: int, eb: float, out, workspace, leaf_size: int = 0, perm=None,
+                stream=None) -> int:
+    """Compress device positions [n, 3] into the device byte tensor `out`; returns the stream size."""
+    n = positions.shape[0] if positions.dim() == 2 else positions.numel() // 3
+    size = ctypes.c_uint64()
+    rc = _lib().pc_compress(positions.data_ptr() if n else None, n, _dtype_of(positions), eb_mode, float(eb),
+                            ctypes.byref(_cfg(leaf_size)), out.data_ptr(), out.numel() * out.element_size(),
+                            ctypes.byref(size), workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                            perm.data_ptr() if perm is not None else None, _stream_handle(stream))
+    _check(rc, "pc_compress")
+    return size.value
+
+
+@dataclass
+class StreamInfo:
+    n: int
+    dtype: int
+    eb_mode: int
+    eb: float
+    eps: float
+    s: float
+    o: tuple
+    num_leaves: int
+    payload_words: int
+    leaf_size: int
+    total_bytes: int
+
+
+def pc_stream_info(header: bytes) -> StreamInfo:
+    info = pc_info()
+    buf = ctypes.create_string_buffer(bytes(header), len(header))
+    _check(_lib().pc_stream_info(buf, len(header), ctypes.byref(info)), "pc_stream_info")
+    return StreamInfo(info.n, info.dtype, info.eb_mode, info.eb, info.eps, info.s, tuple(info.o), info.num_leaves,
+                      info.payload_words, info.leaf_size, info.total_bytes)
+
+
+def pc_decompress_workspace_size() -> int:
+    out = ctypes.c_uint64()
+    _check(_lib().pc_decompress_workspace_size(ctypes.byref(out)), "pc_decompress_workspace_size")
+    return out.value
+
+
+def pc_decompress(stream_data, out_positions, workspace, nbytes: Optional[int] = None, stream=None) -> None:
+    """Decompress the device byte tensor `stream_data` into device positions `out_positions`."""
+    nb = nbytes if nbytes is not None else stream_data.numel()
+    rc = _lib().pc_decompress(stream_data.data_ptr(), nb, out_positions.data_ptr() if out_positions.numel() else None,
+                              out_positions.numel() * out_positions.element_size(), workspace.data_ptr(),
+                              workspace.numel() * workspace.element_size(), _stream_handle(stream))
+    _check(rc, "pc_decompress")
+
+
+def pc_compress_host_workspace_size(n: int, dtype: int, leaf_size: int = 0) -> int:
+    out = ctypes.c_uint64()
+    _check(_lib().pc_compress_host_workspace_size(n, dtype, ctypes.byref(_cfg(leaf_size)), ctypes.byref(out)),
+           "pc_compress_host_workspace_size")
+    return out.value
+
+
+def pc_compress_host(host_positions, eb_mode: int, eb: float, host_out, workspace, leaf_size: int = 0,
+                     stream=None) -> int:
+    """Host-buffer compression (CPU tensors, ideally pinned); returns the stream size."""
+    n = host_positions.shape[0]
+    size = ctypes.c_uint64()
+    rc = _lib().pc_compress_host(host_positions.data_ptr() if n else None, n, _dtype_of(host_positions), eb_mode,
+                                 float(eb), ctypes.byref(_cfg(leaf_size)), host_out.data_ptr(), host_out.numel(),
+                                 ctypes.byref(size), workspace.data_ptr(), workspace.numel(), _stream_handle(stream))
+    _check(rc, "pc_compress_host")
+    return size.value
+
+
+def pc_decompress_host_workspace_size(n: int, dtype: int, stream_bytes: int) -> int:
+    out = ctypes.c_uint64()
+    _check(_lib().pc_decompress_host_workspace_size(n, dtype, stream_bytes, ctypes.byref(out)),
+           "pc_decompress_host_workspace_size")
+    return out.value
+
+
+def pc_decompress_host(host_stream, nbytes: int, host_positions, workspace, stream=None) -> None:
+    rc = _lib().pc_decompress_host(host_stream.data_ptr(), nbytes, host_positions.data_ptr(),
+                                   host_positions.numel() * host_positions.element_size(), workspace.data_ptr(),
+                                   workspace.numel(), _stream_handle(stream))
+    _check(rc, "pc_decompress_host")
+
+
+def pc_error_string(status: int) -> str:
+    return _lib().pc_error_string(status).decode()
+
+
+def pc_format_version() -> int:
+    return int(_lib().pc_format_version())
+
+
+# ---------------------------------------------------------------------------
+# convenience wrappers that take buffers from torch's allocator
+# ---------------------------------------------------------------------------
+
+class Compressor:
+    """Holds device buffers sized for one problem size and reuses them."""
+
+    def __init__(self, n: int, dtype: int, leaf_size: int = 0, with_perm: bool = False, device="cuda"):
+        import torch
+        self.n, self.dtype, self.leaf_size, self.with_perm = n, dtype, leaf_size, with_perm
+        self.out = torch.empty(pc_compress_bound(n, dtype, leaf_size), dtype=torch.uint8, device=device)
+        self.ws = torch.empty(pc_compress_workspace_size(n, dtype, leaf_size, with_perm), dtype=torch.uint8,
+                              device=device)
+        self.perm = torch.empty(max(n, 1), dtype=torch.int32, device=device) if with_perm else None
+        self.dws = torch.empty(pc_decompress_workspace_size(), dtype=torch.uint8, device=device)
+
+    def compress(self, positions, eb_mode: int, eb: float, stream=None) -> int:
+        return pc_compress(positions, eb_mode, eb, self.out, self.ws, self.leaf_size, self.perm, stream)
+
+    def decompress(self, stream_data, out_positions, nbytes=None, stream=None) -> None:
+        pc_decompress(stream_data, out_positions, self.dws, nbytes, stream)
+
+
+def compress(positions, eb_mode: int, eb: float, leaf_size: int = 0, with_perm: bool = False):
+    """One-shot compression; returns (stream tensor on the device, perm or None)."""
+    n = positions.shape[0]
+    c = Compressor(n, _dtype_of(positions), leaf_size, with_perm, positions.device)
+    size = c.compress(positions, eb_mode, eb)
+    return c.out[:size].clone(), (c.perm[:n].clone() if with_perm else None)
+
+
+def decompress(stream_data):
+    """One-shot decompression of a device stream tensor; returns positions [n, 3] on the device."""
+    import torch
+    info = pc_stream_info(stream_data[:PC_HEADER_BYTES].cpu().numpy().tobytes())
+    dt = torch.float32 if info.dtype == PC_F32 else torch.float64
+    out = torch.empty((info.n, 3), dtype=dt, device=stream_data.device)
+    ws = torch.empty(pc_decompress_workspace_size(), dtype=torch.uint8, device=stream_data.device)
+    pc_decompress(stream_data, out, ws, info.total_bytes)
+    return out

@@ -1,0 +1,610 @@
+// C ABI (include/pc.h): argument checks, the error-bound arithmetic of Sec. 3
+// on the host, workspace layout, and the launch sequence of the hot path.
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/pc.h"
+#include "pc_internal.cuh"
+
+namespace pcx {
+
+uint32_t scatter_tile();
+
+int device_sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  static int cache[64] = {0};
+  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+  if (dev >= 0 && dev < 64) cache[dev] = v;
+  return v;
+}
+
+}  // namespace pcx
+
+namespace {
+
+using namespace pcx;
+
+constexpr uint64_t kAlign = 256;
+inline uint64_t align_up(uint64_t x, uint64_t a = kAlign) { return (x + a - 1) / a * a; }
+
+uint64_t leaves_for(uint64_t n, uint64_t r) {
+  // Node sizes at one depth take at most two values, floor and floor + 1, so
+  // count leaves per size class instead of walking the tree.
+  if (n == 0) return 0;
+  uint64_t total = 0;
+  uint64_t a = n, ca = 1, cb = 0;  // ca nodes of size a, cb nodes of size a + 1
+  for (;;) {
+    if (a + 1 <= r) return total + ca + cb;
+    if (a <= r) {  // size-a nodes are leaves, size-(a+1) nodes split once more into leaves
+      if (a == 0) return total + 2 * cb;
+      return total + ca + 2 * cb;
+    }
+    // every node splits
+    const uint64_t h = a >> 1;
+    uint64_t na = 0, nb = 0;  // counts of size h and h + 1 children
+    if (a & 1) {  // a = 2h + 1 -> h, h+1 ; a + 1 = 2h + 2 -> h+1, h+1
+      na += ca;
+      nb += ca + 2 * cb;
+    } else {  // a = 2h -> h, h ; a + 1 = 2h + 1 -> h, h+1
+      na += 2 * ca + cb;
+      nb += cb;
+    }
+    a = h;
+    ca = na;
+    cb = nb;
+  }
+}
+
+struct Plan {
+  uint64_t n = 0;
+  int dtype = 0;
+  uint32_t r = PC_DEFAULT_LEAF_SIZE;
+  bool idx = false;
+  uint64_t num_leaves = 0;
+  int max_levels = 0;  // global levels for the smallest subtree capacity
+  // workspace offsets
+  uint64_t off_partial = 0, off_range = 0, off_codes_a = 0, off_codes_b = 0, off_idx_a = 0, off_idx_b = 0;
+  uint64_t off_nodes = 0, off_leafinfo = 0;
+  uint64_t off_zero = 0, zero_bytes = 0;  // zeroed at every call:
+  uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_states = 0, off_err = 0, off_total = 0;
+  uint64_t total = 0;
+  int range_blocks = 0;
+};
+
+int global_levels(uint64_t n, uint32_t cap) {
+  int l = 0;
+  while (((n + (1ull << l) - 1) >> l) > cap) ++l;
+  return l;
+}
+
+uint32_t digit_bits_for(int level) {
+  int d = 22 - level;
+  if (d > 13) d = 13;
+  if (d < 8) d = 8;
+  return uint32_t(d);
+}
+
+uint64_t tiles_per_node(uint64_t n, int level) {
+  const uint64_t big = (n >> level) + 1;
+  const uint64_t t = (big + scatter_tile() - 1) / scatter_tile();
+  return t ? t : 1;
+}
+
+int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_count, Plan &p) {
+  if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_ARG;
+  if (n > PC_MAX_PARTICLES) return PC_ERR_ARG;
+  uint32_t r = PC_DEFAULT_LEAF_SIZE;
+  if (cfg) {
+    if (cfg->flags != 0) return PC_ERR_ARG;
+    if (cfg->leaf_size) r = cfg->leaf_size;
+  }
+  if (r < 1 || r > PC_MAX_LEAF_SIZE) return PC_ERR_ARG;
+  p.n = n;
+  p.dtype = dtype;
+  p.r = r;
+  p.idx = idx;
+  p.num_leaves = leaves_for(n, r);
+  const uint32_t cap_min = subtree_capacity(4, idx);
+  p.max_levels = global_levels(n, cap_min);
+  p.range_blocks = 4 * (sm_count > 0 ? sm_count : 148);
+  if (p.range_blocks > 1024) p.range_blocks = 1024;
+
+  uint64_t o = 0;
+  p.off_partial = o;
+  o = align_up(o + 8ull * sizeof(double) * p.range_blocks);
+  p.off_range = o;
+  o = align_up(o + sizeof(RangeResult));
+  p.off_codes_a = o;
+  o = align_up(o + 3 * align_up(4 * n));
+  p.off_codes_b = o;
+  o = align_up(o + 3 * align_up(4 * n));
+  if (idx) {
+    p.off_idx_a = o;
+    o = align_up(o + 4 * n);
+    p.off_idx_b = o;
+    o = align_up(o + 4 * n);
+  }
+  uint64_t node_count = 0;
+  for (int l = 0; l <= p.max_levels; ++l) node_count += 1ull << l;
+  p.off_nodes = o;
+  o = align_up(o + node_count * sizeof(LevelNode));
+  p.off_leafinfo = o;
+  o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafInfo));
+  // zeroed region
+  p.off_zero = o;
+  uint64_t hist_bins = 0, tiles = 0;
+  for (int l = 0; l < p.max_levels; ++l) {
+    const uint64_t b = (1ull << l) << digit_bits_for(l);
+    if (b > hist_bins) hist_bins = b;
+    tiles += (1ull << l) * tiles_per_node(n, l);
+  }
+  p.off_hist = o;
+  o = align_up(o + 4 * (hist_bins ? hist_bins : 1));
+  p.off_tiles = o;
+  o = align_up(o + 8 * (tiles ? tiles : 1));
+  p.off_tickets = o;
+  o = align_up(o + 4 * (p.max_levels + 2));
+  p.off_states = o;
+  o = align_up(o + 8 * (1ull << p.max_levels));
+  p.off_err = o;
+  o = align_up(o + 4);
+  p.off_total = o;
+  o = align_up(o + 8);
+  p.zero_bytes = o - p.off_zero;
+  p.total = o;
+  return PC_OK;
+}
+
+uint64_t stream_bound(uint64_t n, uint64_t leaves) {
+  // widths are at most 31 bits per axis: 93 bits per non-centre particle
+  return PC_HEADER_BYTES + 36ull * leaves + 4ull * ((93ull * n + 31) / 32);
+}
+
+// Spacing of the floating-point grid with `prec` significand bits at x > 0.
+double grid_spacing(double x, int prec, int emin) {
+  int e = 0;
+  std::frexp(x, &e);
+  int ex = e - 1;
+  if (ex < emin) ex = emin;
+  return std::ldexp(1.0, ex - (prec - 1));
+}
+
+struct Lattice {
+  double eps = 0, s = 1, o[3] = {0, 0, 0};
+  uint32_t qmax[3] = {0, 0, 0};
+};
+
+// Sec. 3: eps from the absolute or value-range-relative bound; the lattice
+// step s = 2 eb' keeps |p - (T)(o + s q)| <= eps after every rounding.
+int lattice_from_range(const RangeResult &rr, int dtype, int mode, double eb, Lattice &L) {
+  if (rr.nonfinite) return PC_ERR_NONFINITE;
+  double lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = rr.lo[d] == 0.0 ? 0.0 : rr.lo[d];
+    hi[d] = rr.hi[d] == 0.0 ? 0.0 : rr.hi[d];
+  }
+  double dmax = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double r = hi[d] - lo[d];
+    if (r > dmax) dmax = r;
+  }
+  L.eps = (mode == PC_EB_ABS) ? eb : eb * dmax;
+  for (int d = 0; d < 3; ++d) L.o[d] = lo[d];
+  if (dmax == 0.0) {
+    L.s = 1.0;
+    return PC_OK;
+  }
+  double m = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    if (std::fabs(lo[d]) > m) m = std::fabs(lo[d]);
+    if (std::fabs(hi[d]) > m) m = std::fabs(hi[d]);
+  }
+  const double m2 = 2.0 * (m > L.eps ? m : L.eps);
+  const double tmax = dtype == PC_F32 ? double(FLT_MAX) : DBL_MAX;
+  if (!(m2 <= tmax)) return PC_ERR_RANGE;
+  const double ulp_t = dtype == PC_F32 ? grid_spacing(m2, 24, -126) : grid_spacing(m2, 53, -1022);
+  const double ulp_d = grid_spacing(m2, 53, -1022);
+  const double ebp = L.eps - ulp_t - 4.0 * ulp_d;
+  if (!(ebp > 0.0)) return PC_ERR_EB_TOO_SMALL;
+  L.s = 2.0 * ebp;
+  for (int d = 0; d < 3; ++d) {
+    const double q = std::nearbyint((hi[d] - lo[d]) / L.s);
+    if (!(q < double(kCodeLimit))) return PC_ERR_RANGE;
+    L.qmax[d] = uint32_t(q);
+  }
+  return PC_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PC_OK : PC_ERR_CUDA; }
+
+#define PC_TRY(x)                        \
+  do {                                   \
+    cudaError_t e_ = (x);                \
+    if (e_ != cudaSuccess) return PC_ERR_CUDA; \
+  } while (0)
+
+int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                  void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
+                  uint32_t *perm, cudaStream_t st) {
+  if (!out || !out_size || (n > 0 && !positions)) return PC_ERR_ARG;
+  if (eb_mode != PC_EB_ABS && eb_mode != PC_EB_REL) return PC_ERR_ARG;
+  if (!(eb > 0.0) || !std::isfinite(eb)) return PC_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(out) % 16) return PC_ERR_ARG;
+  const size_t esz = dtype == PC_F32 ? 4 : 8;
+  if (n > 0 && reinterpret_cast<uintptr_t>(positions) % esz) return PC_ERR_ARG;
+  Plan p;
+  int rc = make_plan(n, dtype, cfg, perm != nullptr, device_sm_count(), p);
+  if (rc) return rc;
+  if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign) return PC_ERR_ARG;
+  if (workspace_bytes < p.total) return PC_ERR_CAPACITY;
+  if (out_capacity < stream_bound(n, p.num_leaves)) return PC_ERR_CAPACITY;
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  uint32_t *err = reinterpret_cast<uint32_t *>(ws + p.off_err);
+  uint64_t *total_dev = reinterpret_cast<uint64_t *>(ws + p.off_total);
+  PC_TRY(cudaMemsetAsync(ws + p.off_zero, 0, p.zero_bytes, st));
+
+  HeaderLaunch hl = {};
+  hl.out = static_cast<uint8_t *>(out);
+  hl.n = n;
+  hl.dtype = dtype;
+  hl.eb_mode = eb_mode;
+  hl.eb = eb;
+  hl.num_leaves = p.num_leaves;
+  hl.leaf_size = p.r;
+  hl.total_bytes = total_dev;
+  hl.err = err;
+
+  Lattice L;
+  if (n == 0) {
+    L.eps = eb_mode == PC_EB_ABS ? eb : 0.0;
+  } else {
+    // a1: value range (the one read-back before the launches that follow)
+    RangeLaunch ra = {};
+    ra.pos = positions;
+    ra.n = n;
+    ra.dtype = dtype;
+    ra.vec = reinterpret_cast<uintptr_t>(positions) % 16 == 0;
+    ra.partial = reinterpret_cast<double *>(ws + p.off_partial);
+    ra.result = reinterpret_cast<RangeResult *>(ws + p.off_range);
+    ra.blocks = p.range_blocks;
+    PC_TRY(launch_range(ra, st));
+    RangeResult rr;
+    PC_TRY(cudaMemcpyAsync(&rr, ra.result, sizeof(rr), cudaMemcpyDeviceToHost, st));
+    PC_TRY(cudaStreamSynchronize(st));
+    rc = lattice_from_range(rr, dtype, eb_mode, eb, L);
+    if (rc) return rc;
+
+    const uint32_t qmax = L.qmax[0] > L.qmax[1] ? (L.qmax[0] > L.qmax[2] ? L.qmax[0] : L.qmax[2])
+                                                 : (L.qmax[1] > L.qmax[2] ? L.qmax[1] : L.qmax[2]);
+    const int cb = qmax < 65536u ? 2 : 4;
+    void *codes_a[3], *codes_b[3];
+    for (int d = 0; d < 3; ++d) {
+      codes_a[d] = ws + p.off_codes_a + uint64_t(d) * align_up(4 * n);
+      codes_b[d] = ws + p.off_codes_b + uint64_t(d) * align_up(4 * n);
+    }
+    uint32_t *idx_a = p.idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_a) : nullptr;
+    uint32_t *idx_b = p.idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_b) : nullptr;
+
+    // a2: quantize
+    QuantLaunch qa = {};
+    qa.pos = positions;
+    qa.n = n;
+    qa.dtype = dtype;
+    qa.code_bytes = cb;
+    qa.vec = ra.vec;
+    for (int d = 0; d < 3; ++d) {
+      qa.qp.o[d] = L.o[d];
+      qa.qp.of[d] = float(L.o[d]);
+      qa.q[d] = codes_a[d];
+    }
+    qa.qp.s = L.s;
+    const double inv = 1.0 / L.s;
+    qa.qp.rh = float(inv);
+    qa.qp.rl = float(inv - double(qa.qp.rh));
+    qa.fast = dtype == PC_F32 && qmax < (1u << 22) && inv > 0x1p-100 && inv < 0x1p100;
+    qa.idx = idx_a;
+    qa.blocks = 8 * device_sm_count();
+    PC_TRY(launch_quantize(qa, st));
+
+    // a3: global k-d levels
+    const uint32_t cap = subtree_capacity(cb, p.idx);
+    const int levels = global_levels(n, cap);
+    LevelNode *nodes = reinterpret_cast<LevelNode *>(ws + p.off_nodes);
+    uint64_t node_base = 0, tile_base = 0;
+    void **src = codes_a, **dst = codes_b;
+    uint32_t *isrc = idx_a, *idst = idx_b;
+    for (int l = 0; l < levels; ++l) {
+      LevelLaunch la = {};
+      la.n = n;
+      la.level = l;
+      la.code_bytes = cb;
+      la.with_idx = p.idx;
+      la.digit_bits = digit_bits_for(l);
+      const uint32_t bits = bit_length(L.qmax[l % 3]);
+      la.passes = (bits + la.digit_bits - 1) / la.digit_bits;
+      la.tiles_per_node = uint32_t(tiles_per_node(n, l));
+      la.root_hi = L.qmax[0];
+      for (int d = 0; d < 3; ++d) {
+        la.src[d] = src[d];
+        la.dst[d] = dst[d];
+      }
+      la.src_idx = isrc;
+      la.dst_idx = idst;
+      la.nodes = nodes + node_base;
+      la.children = (l + 1 < levels) ? nodes + node_base + (1ull << l) : nullptr;
+      la.hist = reinterpret_cast<uint32_t *>(ws + p.off_hist);
+      la.tile_state = reinterpret_cast<unsigned long long *>(ws + p.off_tiles) + tile_base;
+      la.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + l;
+      la.err = err;
+      la.hist_blocks = 2 * device_sm_count();
+      PC_TRY(launch_level(la, st));
+      node_base += 1ull << l;
+      tile_base += (1ull << l) * la.tiles_per_node;
+      void **t = src;
+      src = dst;
+      dst = t;
+      uint32_t *ti = isrc;
+      isrc = idst;
+      idst = ti;
+    }
+
+    // a3-a5: subtrees in shared memory, bit boxes, payload
+    const uint64_t small = n >> levels;
+    SubtreeLaunch sa = {};
+    sa.n = n;
+    sa.root_level = levels;
+    sa.code_bytes = cb;
+    sa.with_idx = p.idx;
+    sa.leaf_size = p.r;
+    sa.leaves_small = leaves_for(small, p.r);
+    sa.leaves_big = leaves_for(small + 1, p.r);
+    for (int d = 0; d < 3; ++d) sa.src[d] = src[d];
+    sa.src_idx = isrc;
+    sa.out = static_cast<uint8_t *>(out);
+    sa.num_leaves = p.num_leaves;
+    sa.perm = perm;
+    sa.leaf_info = reinterpret_cast<LeafInfo *>(ws + p.off_leafinfo);
+    sa.state = reinterpret_cast<unsigned long long *>(ws + p.off_states);
+    sa.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + p.max_levels + 1;
+    sa.err = err;
+    PC_TRY(launch_subtree(sa, st));
+    hl.last_state = sa.state + ((1ull << levels) - 1);
+  }
+  hl.eps = L.eps;
+  hl.s = L.s;
+  for (int d = 0; d < 3; ++d) hl.o[d] = L.o[d];
+  PC_TRY(launch_header(hl, st));
+  struct {
+    uint64_t total;
+    uint32_t err;
+  } back = {0, 0};
+  PC_TRY(cudaMemcpyAsync(&back.total, total_dev, 8, cudaMemcpyDeviceToHost, st));
+  PC_TRY(cudaMemcpyAsync(&back.err, err, 4, cudaMemcpyDeviceToHost, st));
+  PC_TRY(cudaStreamSynchronize(st));
+  if (back.err & kErrTimeout) return PC_ERR_TIMEOUT;
+  if (back.err) return PC_ERR_CUDA;
+  *out_size = back.total;
+  return PC_OK;
+}
+
+int parse_header(const uint8_t *h, uint64_t avail, pc_info *info) {
+  if (avail < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
+  if (std::memcmp(h, "PCB1", 4) != 0) return PC_ERR_CORRUPT;
+  uint16_t ver;
+  std::memcpy(&ver, h + 4, 2);
+  if (ver != 1) return PC_ERR_CORRUPT;
+  if (h[6] > 1 || h[7] > 1) return PC_ERR_CORRUPT;
+  pc_info I = {};
+  I.dtype = h[6];
+  I.eb_mode = h[7];
+  std::memcpy(&I.n, h + 8, 8);
+  std::memcpy(&I.eb, h + 16, 8);
+  std::memcpy(&I.eps, h + 24, 8);
+  std::memcpy(&I.s, h + 32, 8);
+  std::memcpy(I.o, h + 40, 24);
+  std::memcpy(&I.num_leaves, h + 64, 8);
+  std::memcpy(&I.payload_words, h + 72, 8);
+  std::memcpy(&I.leaf_size, h + 80, 4);
+  for (int i = 84; i < 96; ++i)
+    if (h[i]) return PC_ERR_CORRUPT;
+  if (I.n > PC_MAX_PARTICLES || I.num_leaves > I.n || ((I.n > 0) != (I.num_leaves > 0))) return PC_ERR_CORRUPT;
+  if (I.payload_words > (1ull << 40)) return PC_ERR_CORRUPT;
+  if (!std::isfinite(I.s) || !(I.s > 0.0)) return PC_ERR_CORRUPT;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(I.o[d])) return PC_ERR_CORRUPT;
+  I.total_bytes = PC_HEADER_BYTES + PC_LEAF_BYTES * I.num_leaves + 4 * I.payload_words;
+  *info = I;
+  return PC_OK;
+}
+
+int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_positions, uint64_t out_capacity_bytes,
+                    void *workspace, uint64_t workspace_bytes, cudaStream_t st) {
+  if (!stream_data || !workspace) return PC_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(stream_data) % 16 || reinterpret_cast<uintptr_t>(workspace) % kAlign)
+    return PC_ERR_ARG;
+  if (workspace_bytes < kAlign) return PC_ERR_CAPACITY;
+  if (stream_bytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
+  uint8_t h[PC_HEADER_BYTES];
+  PC_TRY(cudaMemcpyAsync(h, stream_data, PC_HEADER_BYTES, cudaMemcpyDeviceToHost, st));
+  PC_TRY(cudaStreamSynchronize(st));
+  pc_info I;
+  int rc = parse_header(h, PC_HEADER_BYTES, &I);
+  if (rc) return rc;
+  if (I.total_bytes > stream_bytes) return PC_ERR_CORRUPT;
+  const uint64_t esz = I.dtype == PC_F32 ? 4 : 8;
+  if (out_capacity_bytes < 3 * esz * I.n) return PC_ERR_CAPACITY;
+  if (I.n == 0) return PC_OK;
+  if (!out_positions || reinterpret_cast<uintptr_t>(out_positions) % esz) return PC_ERR_ARG;
+  uint32_t *err = static_cast<uint32_t *>(workspace);
+  PC_TRY(cudaMemsetAsync(err, 0, 4, st));
+  DecodeLaunch da = {};
+  da.stream = static_cast<const uint8_t *>(stream_data);
+  da.n = I.n;
+  da.dtype = int(I.dtype);
+  da.num_leaves = I.num_leaves;
+  da.payload_words = I.payload_words;
+  da.s = I.s;
+  bool exact_o = true;
+  for (int d = 0; d < 3; ++d) {
+    da.o[d] = I.o[d];
+    da.of[d] = float(I.o[d]);
+    exact_o = exact_o && double(da.of[d]) == I.o[d];
+  }
+  da.sh = float(I.s);
+  da.sl = float(I.s - double(da.sh));
+  da.fast = I.dtype == PC_F32 && exact_o && I.s > 0x1p-100 && I.s < 0x1p100;
+  da.out = out_positions;
+  da.vec = reinterpret_cast<uintptr_t>(out_positions) % 16 == 0;
+  da.err = err;
+  PC_TRY(launch_decode(da, st));
+  uint32_t e = 0;
+  PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+  PC_TRY(cudaStreamSynchronize(st));
+  if (e & kErrCorrupt) return PC_ERR_CORRUPT;
+  if (e) return PC_ERR_CUDA;
+  return PC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pc_compress_bound(uint64_t n, int dtype, const pc_config *cfg, uint64_t *out_bytes) {
+  if (!out_bytes) return PC_ERR_ARG;
+  Plan p;
+  int rc = make_plan(n, dtype, cfg, false, 148, p);
+  if (rc) return rc;
+  *out_bytes = stream_bound(n, p.num_leaves);
+  return PC_OK;
+}
+
+int pc_compress_workspace_size(uint64_t n, int dtype, const pc_config *cfg, int with_perm, uint64_t *out_bytes) {
+  if (!out_bytes) return PC_ERR_ARG;
+  Plan p;
+  // size for the largest block count the device may use
+  int rc = make_plan(n, dtype, cfg, with_perm != 0, 256, p);
+  if (rc) return rc;
+  *out_bytes = p.total;
+  return PC_OK;
+}
+
+int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg, void *out,
+                uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes, uint32_t *perm,
+                void *stream) {
+  return compress_impl(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, workspace,
+                       workspace_bytes, perm, static_cast<cudaStream_t>(stream));
+}
+
+int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info) {
+  if (!host_header || !info) return PC_ERR_ARG;
+  return parse_header(static_cast<const uint8_t *>(host_header), header_bytes, info);
+}
+
+int pc_decompress_workspace_size(uint64_t *out_bytes) {
+  if (!out_bytes) return PC_ERR_ARG;
+  *out_bytes = kAlign;
+  return PC_OK;
+}
+
+int pc_decompress(const void *stream_data, uint64_t stream_bytes, void *out_positions, uint64_t out_capacity_bytes,
+                  void *workspace, uint64_t workspace_bytes, void *stream) {
+  return decompress_impl(stream_data, stream_bytes, out_positions, out_capacity_bytes, workspace, workspace_bytes,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int pc_compress_host_workspace_size(uint64_t n, int dtype, const pc_config *cfg, uint64_t *out_bytes) {
+  if (!out_bytes) return PC_ERR_ARG;
+  uint64_t ws = 0, bound = 0;
+  int rc = pc_compress_workspace_size(n, dtype, cfg, 0, &ws);
+  if (rc) return rc;
+  rc = pc_compress_bound(n, dtype, cfg, &bound);
+  if (rc) return rc;
+  const uint64_t esz = dtype == PC_F32 ? 4 : 8;
+  *out_bytes = align_up(3 * esz * n) + align_up(bound) + ws;
+  return PC_OK;
+}
+
+int pc_compress_host(const void *host_positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                     void *host_out, uint64_t out_capacity, uint64_t *out_size, void *workspace,
+                     uint64_t workspace_bytes, void *stream) {
+  if (!host_out || !out_size || !workspace || (n > 0 && !host_positions)) return PC_ERR_ARG;
+  if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_ARG;
+  uint64_t need = 0, bound = 0;
+  int rc = pc_compress_host_workspace_size(n, dtype, cfg, &need);
+  if (rc) return rc;
+  if (workspace_bytes < need) return PC_ERR_CAPACITY;
+  pc_compress_bound(n, dtype, cfg, &bound);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t esz = dtype == PC_F32 ? 4 : 8;
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  uint8_t *dpos = ws;
+  uint8_t *dout = ws + align_up(3 * esz * n);
+  uint8_t *rest = dout + align_up(bound);
+  if (n) PC_TRY(cudaMemcpyAsync(dpos, host_positions, 3 * esz * n, cudaMemcpyHostToDevice, st));
+  uint64_t size = 0;
+  rc = compress_impl(dpos, n, dtype, eb_mode, eb, cfg, dout, bound, &size, rest, workspace_bytes - (rest - ws),
+                     nullptr, st);
+  if (rc) return rc;
+  if (size > out_capacity) return PC_ERR_CAPACITY;
+  PC_TRY(cudaMemcpyAsync(host_out, dout, size, cudaMemcpyDeviceToHost, st));
+  PC_TRY(cudaStreamSynchronize(st));
+  *out_size = size;
+  return PC_OK;
+}
+
+int pc_decompress_host_workspace_size(uint64_t n, int dtype, uint64_t stream_bytes, uint64_t *out_bytes) {
+  if (!out_bytes || (dtype != PC_F32 && dtype != PC_F64)) return PC_ERR_ARG;
+  const uint64_t esz = dtype == PC_F32 ? 4 : 8;
+  *out_bytes = align_up(stream_bytes) + align_up(3 * esz * n) + kAlign;
+  return PC_OK;
+}
+
+int pc_decompress_host(const void *host_stream, uint64_t stream_bytes, void *host_positions,
+                       uint64_t out_capacity_bytes, void *workspace, uint64_t workspace_bytes, void *stream) {
+  if (!host_stream || !workspace) return PC_ERR_ARG;
+  pc_info I;
+  int rc = pc_stream_info(host_stream, stream_bytes, &I);
+  if (rc) return rc;
+  if (I.total_bytes > stream_bytes) return PC_ERR_CORRUPT;
+  const uint64_t esz = I.dtype == PC_F32 ? 4 : 8;
+  if (out_capacity_bytes < 3 * esz * I.n) return PC_ERR_CAPACITY;
+  if (I.n > 0 && !host_positions) return PC_ERR_ARG;
+  uint64_t need = 0;
+  pc_decompress_host_workspace_size(I.n, int(I.dtype), I.total_bytes, &need);
+  if (workspace_bytes < need) return PC_ERR_CAPACITY;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  uint8_t *dst_stream = ws;
+  uint8_t *dpos = ws + align_up(I.total_bytes);
+  uint8_t *rest = dpos + align_up(3 * esz * I.n);
+  PC_TRY(cudaMemcpyAsync(dst_stream, host_stream, I.total_bytes, cudaMemcpyHostToDevice, st));
+  rc = decompress_impl(dst_stream, I.total_bytes, dpos, 3 * esz * I.n, rest, kAlign, st);
+  if (rc) return rc;
+  if (I.n) PC_TRY(cudaMemcpyAsync(host_positions, dpos, 3 * esz * I.n, cudaMemcpyDeviceToHost, st));
+  PC_TRY(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+const char *pc_error_string(int status) {
+  switch (status) {
+    case PC_OK: return "ok";
+    case PC_ERR_ARG: return "invalid argument";
+    case PC_ERR_NONFINITE: return "non-finite coordinate in the input";
+    case PC_ERR_EB_TOO_SMALL: return "error bound below the rounding margin of the input type";
+    case PC_ERR_RANGE: return "quantization codes or magnitudes out of range";
+    case PC_ERR_CAPACITY: return "output or workspace buffer too small";
+    case PC_ERR_CORRUPT: return "corrupt or inconsistent stream";
+    case PC_ERR_TIMEOUT: return "a bounded device wait expired";
+    case PC_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int pc_format_version(void) { return 1; }
+
+}  // extern "C"

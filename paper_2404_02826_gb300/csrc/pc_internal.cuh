@@ -1,0 +1,192 @@
+// Internal declarations shared by the translation units of the CUDA library.
+// Nothing here is part of the public C ABI (include/pc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace pcx {
+
+constexpr uint32_t kHeaderBytes = 96;
+constexpr uint32_t kLeafBytes = 32;
+constexpr int64_t kCodeLimit = int64_t(1) << 30;  // codes < 2^30, so m_d <= 31
+
+// Bits of the device error word.
+enum : uint32_t { kErrTimeout = 1u, kErrCorrupt = 2u, kErrInternal = 4u };
+
+// Spin limit of every device-side wait (look-back on a predecessor's state).
+// With a 64 ns back-off this is about one second before the wait gives up.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Result of the range reduction (Sec. 3: per-axis min / max, Delta_max).
+struct RangeResult {
+  double lo[3];
+  double hi[3];
+  uint32_t nonfinite;
+  uint32_t pad;
+};
+
+// Lattice parameters handed to the quantize kernel.
+struct QuantParams {
+  double o[3];   // origin (per-axis minimum)
+  double s;      // step 2 eb'
+  float of[3];   // origin as float (exact for float input)
+  float rh, rl;  // 1/s as an unevaluated float sum rh + rl
+};
+
+// Per-node state of one global k-d level (Sec. 4.1 median split by radix select).
+struct LevelNode {
+  uint32_t lo, hi;   // code bounds of the node on its split axis
+  uint32_t prefix;   // selected high digits of (code - lo)
+  int32_t shift;     // low bit of the current digit
+  uint32_t width;    // bits of the current digit; 0 once the split is known
+  uint32_t below;    // particles in lower buckets of earlier digits
+  uint32_t v;        // split code
+  uint32_t less;     // particles with code < v
+  uint32_t tleft;    // particles with code == v that go left (first in index order)
+  uint32_t pad[3];
+};
+
+// Per-leaf facts kept between the bit-box pass and the packing pass.
+struct LeafInfo {
+  uint32_t off;      // first particle, relative to the subtree root
+  uint32_t cnt;      // particles
+  uint32_t centre;   // position of the centre inside the leaf
+  uint32_t words;    // payload words of the leaf
+  uint32_t lword;    // first payload word, relative to the subtree
+  int32_t qref[3];
+  uint32_t m;        // m_x | m_y << 8 | m_z << 16
+  uint32_t pad;
+};
+
+// Offset and size of node j at depth `level` of the median tree over n
+// particles: the left child takes floor(c/2), the right ceil(c/2) (Sec. 4.1).
+__host__ __device__ inline void node_range(uint64_t n, int level, uint64_t j, uint64_t &off, uint64_t &cnt) {
+  off = 0;
+  cnt = n;
+  for (int b = level - 1; b >= 0; --b) {
+    uint64_t half = cnt >> 1;
+    if ((j >> b) & 1ull) {
+      off += half;
+      cnt -= half;
+    } else {
+      cnt = half;
+    }
+  }
+}
+
+__host__ __device__ inline uint32_t bit_length(uint64_t x) {
+  uint32_t b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+// Eq. 2 on the lattice: m = 0 for R = 0, else bit_length(R) + 1.
+__host__ __device__ inline uint32_t bits_for_range(uint32_t R) { return R ? bit_length(R) + 1 : 0; }
+
+// ---- launchers (defined in the kernel translation units) -------------------
+
+struct RangeLaunch {
+  const void *pos;
+  uint64_t n;
+  int dtype;
+  bool vec;
+  double *partial;  // [blocks][7]
+  RangeResult *result;
+  int blocks;
+};
+cudaError_t launch_range(const RangeLaunch &a, cudaStream_t st);
+
+struct QuantLaunch {
+  const void *pos;
+  uint64_t n;
+  int dtype;
+  int code_bytes;  // 2 or 4
+  bool vec;
+  bool fast;
+  QuantParams qp;
+  void *q[3];
+  uint32_t *idx;  // optional identity permutation
+  int blocks;
+};
+cudaError_t launch_quantize(const QuantLaunch &a, cudaStream_t st);
+
+struct LevelLaunch {
+  uint64_t n;
+  int level;
+  int code_bytes;
+  bool with_idx;
+  uint32_t digit_bits;
+  uint32_t passes;
+  uint32_t tiles_per_node;
+  uint32_t root_hi;       // level 0 only: bounds of the x codes are [0, root_hi]
+  const void *src[3];
+  void *dst[3];
+  const uint32_t *src_idx;
+  uint32_t *dst_idx;
+  LevelNode *nodes;       // this level [2^level]
+  LevelNode *children;    // next level [2^(level+1)]
+  uint32_t *hist;         // [2^level][2^digit_bits], zero on entry, zero on exit
+  unsigned long long *tile_state;
+  uint32_t *ticket;
+  uint32_t *err;
+  int hist_blocks;
+};
+cudaError_t launch_level(const LevelLaunch &a, cudaStream_t st);
+
+struct SubtreeLaunch {
+  uint64_t n;
+  int root_level;           // depth of the subtree roots
+  int code_bytes;
+  bool with_idx;
+  uint32_t leaf_size;
+  uint64_t leaves_small;    // leaves under a root of floor(n / 2^root_level) particles
+  uint64_t leaves_big;      // leaves under a root of one more particle
+  const void *src[3];
+  const uint32_t *src_idx;
+  uint8_t *out;             // stream base
+  uint64_t num_leaves;
+  uint32_t *perm;           // optional
+  LeafInfo *leaf_info;      // [num_leaves]
+  unsigned long long *state;  // [2^root_level]
+  uint32_t *ticket;
+  uint32_t *err;
+};
+cudaError_t launch_subtree(const SubtreeLaunch &a, cudaStream_t st);
+uint32_t subtree_capacity(int code_bytes, bool with_idx);
+
+struct HeaderLaunch {
+  uint8_t *out;
+  uint64_t n;
+  int dtype, eb_mode;
+  double eb, eps, s, o[3];
+  uint64_t num_leaves;
+  uint32_t leaf_size;
+  const unsigned long long *last_state;  // null when there are no leaves
+  uint64_t *total_bytes;                 // device slot read back by the host
+  uint32_t *err;
+};
+cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st);
+
+struct DecodeLaunch {
+  const uint8_t *stream;
+  uint64_t n;
+  int dtype;
+  uint64_t num_leaves;
+  uint64_t payload_words;
+  double s, o[3];
+  bool fast;       // float output with the float-pair fast path
+  float of[3];     // origin as float
+  float sh, sl;    // s as an unevaluated float sum
+  void *out;
+  bool vec;
+  uint32_t *err;
+};
+cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace pcx

@@ -1,0 +1,89 @@
+"""CPU-only checks of the C-ABI library: it builds, loads without a GPU, exports
+every entry point that include/pc.h declares, and its host-only calls (sizes,
+header parsing, status strings) agree with the oracle's streams."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def pc():
+    from paper_2404_02826_gb300 import build as b
+
+    b.build()
+    import paper_2404_02826_gb300 as pc
+
+    pc.load()
+    return pc
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(pc_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(pc):
+    lib = pc.load()
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(pc.EXPORTS)
+
+
+def test_status_strings(pc):
+    for code in range(0, 9):
+        s = pc.pc_error_string(code)
+        assert isinstance(s, str) and s
+    assert pc.pc_format_version() == 1
+
+
+@pytest.mark.parametrize("gen,n,r", [("uniform", 5000, 300), ("cosmology", 20000, 4096), ("fluid", 9000, 64),
+                                     ("uniform", 1, 4096), ("uniform", 0, 4096)])
+def test_stream_info_and_bound_match_oracle_streams(pc, oracle_mod, gen, n, r):
+    pos = synth.by_name(gen, n, seed=2) if n else np.zeros((0, 3), np.float32)
+    stream, _ = oracle_mod.compress(pos, oracle_mod.REL, 1e-3, leaf_size=r)
+    info = pc.pc_stream_info(stream[:96])
+    n0, dt, nl, nw = oracle_mod.stream_header(stream)
+    assert (info.n, info.dtype, info.num_leaves, info.payload_words) == (n0, dt, nl, nw)
+    assert info.total_bytes == len(stream)
+    assert info.leaf_size == r
+    dtype = pc.PC_F32 if pos.dtype == np.float32 else pc.PC_F64
+    assert pc.pc_compress_bound(n, dtype, r) >= len(stream)
+    assert nl == oracle_mod.num_leaves(n, r)
+
+
+def test_leaf_count_rule_matches_oracle(pc, oracle_mod):
+    # the library sizes its leaf table from (n, r) alone; the bound exposes it
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        n = int(rng.integers(0, 1 << 22))
+        r = int(rng.integers(1, 12001))
+        L = oracle_mod.num_leaves(n, r)
+        b = pc.pc_compress_bound(n, pc.PC_F32, r)
+        assert b == 96 + 36 * L + 4 * ((93 * n + 31) // 32)
+
+
+def test_argument_errors_without_gpu(pc):
+    with pytest.raises(pc.PCError) as e:
+        pc.pc_compress_bound(10, 7)
+    assert e.value.status == pc.PC_ERR_ARG
+    with pytest.raises(pc.PCError):
+        pc.pc_compress_workspace_size(10, pc.PC_F32, leaf_size=pc.PC_MAX_LEAF_SIZE + 1)
+    with pytest.raises(pc.PCError) as e:
+        pc.pc_stream_info(b"XXXX" + bytes(92))
+    assert e.value.status == pc.PC_ERR_CORRUPT
+    with pytest.raises(pc.PCError):
+        pc.pc_compress_bound(1 << 31, pc.PC_F32)
