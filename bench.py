@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 particle position compressor (arXiv 2404.02826 hot path).
+
+One step = compress + decompress of one synthetic snapshot through the C ABI
+(value range, quantization, k-d partition, bit boxes, packing, then unpack and
+dequantize).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+value      uncompressed bytes (n * 3 * sizeof(T)) through one round trip per
+           second, inputs already resident in HBM; whole job over all ranks
+e2e        the same metric through the host-buffer entry points: positions
+           copied in from pinned memory, the stream copied out, copied back in
+           and the positions copied out, every step
+roofline   the kernel with the largest traced time: algorithmic bytes per
+           launch / mean launch time (CUDA events on the launching stream),
+           against the measured HBM copy bandwidth
+cpu_baseline  the oracle (single thread) on a bounded sample of the workload
+
+With N > 1 (torchrun), every rank compresses its own snapshot (replicas, no
+collective on the data path); time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: generator, n, dtype, eb mode, eb
+    "cosmology-2^27-f32-rel1e-4": ("cosmology", 1 << 27, "f32", "rel", 1e-4),
+    "cosmology-2^27-f32-rel1e-3": ("cosmology", 1 << 27, "f32", "rel", 1e-3),
+    "uniform-2^20-f32-rel1e-3": ("uniform", 1 << 20, "f32", "rel", 1e-3),
+    "fluid-2^24-f64-abs1e-4": ("fluid", 1 << 24, "f64", "abs", 1e-4),
+    "cosmology-2^24-f32-rel1e-4": ("cosmology", 1 << 24, "f32", "rel", 1e-4),
+}
+DEFAULT_WORKLOAD = "cosmology-2^27-f32-rel1e-4"
+CPU_SAMPLE = 1 << 22        # particles of the oracle's timed sample (cpu_baseline)
+REF_SAMPLE = 1 << 20        # particles per step of the reference arm
+METRIC = "compress+decompress round-trip throughput (uncompressed bytes)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--leaf-size", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def generate(gen, n, dtype, seed):
+    import numpy as np
+
+    import synth
+
+    dt = np.float32 if dtype == "f32" else np.float64
+    return synth.by_name(gen, n, seed=seed, dtype=dt)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while it runs."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20"]
+        if gpu_id:
+            cmd.insert(1, f"--id={gpu_id}")
+        self.rows = []
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [r for t, r in self.rows if t0 <= t <= t1 + 0.05 and len(r) >= 9]
+        window = "timed"
+        if not rows:  # region shorter than the sampling period: take the samples around it
+            rows = [r for t, r in self.rows if t0 - 1.0 <= t <= t1 + 1.0 and len(r) >= 9]
+            window = "around-timed"
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no-samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "window": window,
+                "power_w_max": max(pw) if pw else None}
+
+
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str, n: int):
+    """DRAM bytes per launch of `kernel` from a committed ncu capture, scaled to
+    n particles; None when the capture is missing or the kernel source changed."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        if rec["source_hash"] != source_hash(rec["sources"]):
+            return None
+        return rec["dram_bytes_per_particle"] * n
+    except Exception:
+        return None
+
+
+def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False):
+    """Bytes a launch must move at minimum (per-kernel figures, stated in the design notes)."""
+    idx = 4 if with_idx else 0
+    return {
+        "k_range": 3 * esz * n,
+        "k_quantize": 3 * esz * n + 3 * cb * n + idx * n,
+        "k_hist": cb * n,
+        "k_scatter": 2 * (3 * cb + idx) * n,
+        "k_subtree": (3 * cb + idx) * n + stream_bytes,
+        "k_decode": stream_bytes + 3 * esz * n,
+    }.get(kernel)
+
+
+def oracle_round_trip(pos, mode, eb, leaf_size):
+    import oracle
+
+    m = oracle.REL if mode == "rel" else oracle.ABS
+    stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False)
+    oracle.decompress(stream)
+    return len(stream)
+
+
+def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE):
+    gen, n, dtype, mode, eb = spec
+    pos = generate(gen, n_sample, dtype, seed=0)
+    t0 = time.perf_counter()
+    oracle_round_trip(pos, mode, eb, leaf_size)
+    dt = time.perf_counter() - t0
+    return {"value": round(pos.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_sample} particles of the {gen} generator ({dtype}, {mode} eb {eb}), one compress + "
+                      f"decompress in {dt:.2f} s"}
+
+
+def run_reference(args, spec):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    gen, n, dtype, mode, eb = spec
+    import oracle
+
+    oracle.build()
+    samples = [generate(gen, REF_SAMPLE, dtype, seed=s) for s in range(2)]
+    for i in range(args.warmup):
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    units = samples[0].nbytes * args.steps
+    value = units / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "sample_particles_per_step": REF_SAMPLE, "leaf_size": args.leaf_size,
+                   "note": "the oracle (plain single-threaded C, double precision) on host cores"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{REF_SAMPLE} particles of the {gen} generator per step"},
+        "e2e": {"value": round(value, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, spec):
+    import numpy as np
+    import torch
+
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as pcbuild
+
+    gen, n, dtype, mode, eb = spec
+    world, rank, local = dist_setup(args)
+    if rank == 0:
+        pcbuild.build()
+    barrier(world)
+    pc.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream()
+    pos_h = generate(gen, n, dtype, seed=rank)
+    pdt = pc.PC_F32 if dtype == "f32" else pc.PC_F64
+    emode = pc.PC_EB_REL if mode == "rel" else pc.PC_EB_ABS
+    esz = 4 if dtype == "f32" else 8
+    pos = torch.from_numpy(pos_h).to(dev)
+    comp = pc.Compressor(n, pdt, leaf_size=args.leaf_size, device=dev)
+    dec = torch.empty_like(pos)
+
+    def step():
+        size = comp.compress(pos, emode, eb)
+        comp.decompress(comp.out, dec, size)
+        return size
+
+    size = 0
+    for _ in range(max(args.warmup, 3)):
+        size = step()
+    torch.cuda.synchronize()
+    info = pc.pc_stream_info(comp.out[:96].cpu().numpy().tobytes())
+    lo = pos.amin(0).double().cpu().numpy()
+    hi = pos.amax(0).double().cpu().numpy()
+    qmax = int(np.rint((hi - lo) / info.s).max())
+    cb = 2 if qmax < 65536 else 4
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    pc.pc_trace_reset()
+    pc.pc_trace_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for i in range(args.steps):
+        ev[i][0].record(st)
+        size = comp.compress(pos, emode, eb)
+        ev[i][1].record(st)
+        comp.decompress(comp.out, dec, size)
+        ev[i][2].record(st)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall1 = time.time()
+    pc.pc_trace_enable(False)
+    time.sleep(0.1)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    comp_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    dec_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
+    total_ms = max_over_ranks(total_ms, world)
+    nbytes = 3 * esz * n
+    value = world * nbytes * args.steps / (total_ms / 1e3) / 1e9
+
+    table = pc.trace_table()
+    launches = int(sum(v[0] for v in table.values()))
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(table.items(), key=lambda kv: -kv[1][1])}
+    top = max(table, key=lambda k: table[k][1])
+    per_launch_ms = table[top][1] / table[top][0]
+    alg = algorithmic_bytes(top, n, esz, cb, size)
+    peak, peak_kind = peaks()
+    roofline = None
+    if alg is not None:
+        achieved = alg / (per_launch_ms / 1e3) / 1e9
+        roofline = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                    "traffic": measured_traffic(top, args.workload, n),
+                    "algorithmic_bytes_per_launch": alg, "mean_launch_ms": round(per_launch_ms, 4)}
+    # whole-step algorithmic bytes (input read + stream written + stream read + output written)
+    step_alg = 2 * (nbytes + size)
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        e2e = measure_e2e(pc, pos_h, pdt, emode, eb, args, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, args.leaf_size)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": args.workload, "generator": gen, "particles": n, "eb_mode": mode, "eb": eb,
+                       "leaf_size": args.leaf_size, "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (no flush)", "code_bytes": cb},
+            "compress_gbs": round(world * nbytes * args.steps / (comp_ms / 1e3) / 1e9, 3),
+            "decompress_gbs": round(world * nbytes * args.steps / (dec_ms / 1e3) / 1e9, 3),
+            "compression_ratio": round(nbytes / size, 4), "bits_per_particle": round(8 * size / n, 4),
+            "step_hbm_frac_algorithmic": round(step_alg / (total_ms / args.steps / 1e3) / 1e9 / peak, 4),
+            "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def measure_e2e(pc, pos_h, pdt, emode, eb, args, world):
+    """Round trips through the host-buffer entry points, copies inside the timing."""
+    import torch
+
+    n = pos_h.shape[0]
+    dev = torch.cuda.current_device()
+    hp = torch.from_numpy(pos_h).pin_memory()
+    bound = pc.pc_compress_bound(n, pdt, args.leaf_size)
+    hstream = torch.empty(bound, dtype=torch.uint8).pin_memory()
+    hdec = torch.empty_like(hp).pin_memory()
+    ws_c = torch.empty(pc.pc_compress_host_workspace_size(n, pdt, args.leaf_size), dtype=torch.uint8, device=dev)
+    ws_d = torch.empty(pc.pc_decompress_host_workspace_size(n, pdt, bound), dtype=torch.uint8, device=dev)
+    size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, args.leaf_size)  # warm-up
+    pc.pc_decompress_host(hstream, size, hdec, ws_d)
+    times = []
+    for _ in range(args.e2e_steps):
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, args.leaf_size)
+        pc.pc_decompress_host(hstream, size, hdec, ws_d)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = max_over_ranks(sum(times), world)
+    value = world * hp.numel() * hp.element_size() * args.e2e_steps / t / 1e9
+    del ws_c, ws_d
+    return {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": int(hp.nbytes + size),
+            "d2h_bytes_per_step": int(size + hp.nbytes), "steps": args.e2e_steps,
+            "api": "pc_compress_host + pc_decompress_host (pinned host buffers)"}
+
+
+def main():
+    args = parse()
+    spec = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, spec)
+    else:
+        run_ours(args, spec)
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,17 @@ int pc_decompress_host_workspace_size(uint64_t n, int dtype, uint64_t stream_byt
 int pc_decompress_host(const void *host_stream, uint64_t stream_bytes, void *host_positions,
                        uint64_t out_capacity_bytes, void *workspace, uint64_t workspace_bytes, void *stream);
 
+/* Kernel tracing.  While enabled, every kernel launch of the library is
+ * bracketed by CUDA events recorded on the launching stream; elapsed times are
+ * accumulated per kernel name when a call synchronises (compress and
+ * decompress do so before returning).  Tracing is off by default and costs two
+ * event records per launch when on.  pc_trace_get reports entry i in
+ * [0, pc_trace_count()): its static name, launches and total milliseconds. */
+int pc_trace_enable(int on);
+int pc_trace_reset(void);
+int pc_trace_count(void);
+int pc_trace_get(int i, const char **name, uint64_t *launches, double *total_ms);
+
 /* Static text for a status code. */
 const char *pc_error_string(int status);
 

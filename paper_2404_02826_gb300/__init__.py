@@ -43,6 +43,7 @@ EXPORTS = (
     "pc_compress_bound", "pc_compress_workspace_size", "pc_compress", "pc_stream_info",
     "pc_decompress_workspace_size", "pc_decompress", "pc_compress_host_workspace_size", "pc_compress_host",
     "pc_decompress_host_workspace_size", "pc_decompress_host", "pc_error_string", "pc_format_version",
+    "pc_trace_enable", "pc_trace_reset", "pc_trace_count", "pc_trace_get",
 )
 
 
@@ -90,10 +91,10 @@ def _lib():
         L.pc_error_string.argtypes = [i32]
         L.pc_error_string.restype = ctypes.c_char_p
         L.pc_format_version.argtypes = []
-        for name in EXPORTS:
-            f = getattr(L, name)
-            if f.restype is ctypes.c_int and name != "pc_error_string":
-                f.restype = ctypes.c_int
+        L.pc_trace_enable.argtypes = [i32]
+        L.pc_trace_reset.argtypes = []
+        L.pc_trace_count.argtypes = []
+        L.pc_trace_get.argtypes = [i32, ctypes.POINTER(ctypes.c_char_p), pu64, ctypes.POINTER(dbl)]
         _LIB = L
     return _LIB
 
@@ -231,6 +232,31 @@ def pc_error_string(status: int) -> str:
 
 def pc_format_version() -> int:
     return int(_lib().pc_format_version())
+
+
+def pc_trace_enable(on: bool = True) -> None:
+    _check(_lib().pc_trace_enable(int(on)), "pc_trace_enable")
+
+
+def pc_trace_reset() -> None:
+    _check(_lib().pc_trace_reset(), "pc_trace_reset")
+
+
+def pc_trace_count() -> int:
+    return int(_lib().pc_trace_count())
+
+
+def pc_trace_get(i: int):
+    name = ctypes.c_char_p()
+    launches = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(_lib().pc_trace_get(i, ctypes.byref(name), ctypes.byref(launches), ctypes.byref(ms)), "pc_trace_get")
+    return name.value.decode(), launches.value, ms.value
+
+
+def trace_table() -> dict:
+    """{kernel name: (launches, total ms)} accumulated while tracing was enabled."""
+    return {n: (l, t) for n, l, t in (pc_trace_get(i) for i in range(pc_trace_count()))}
 
 
 # ---------------------------------------------------------------------------

@@ -214,6 +214,7 @@ __global__ void k_header(HeaderLaunch a) {
 template <typename T, bool FAST>
 void decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
   const unsigned blocks = unsigned((a.n + kChunk - 1) / kChunk);
+  TraceScope ts("k_decode", st);
   if (a.vec) k_decode<T, FAST, true><<<blocks, kDecThreads, 0, st>>>(a);
   else k_decode<T, FAST, false><<<blocks, kDecThreads, 0, st>>>(a);
 }
@@ -221,14 +222,18 @@ void decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st) {
+  TraceScope ts("k_header", st);
   k_header<<<1, 1, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_validate<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
-                                                                      a.err);
+  {
+    TraceScope ts("k_validate", st);
+    k_validate<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
+                                                                        a.err);
+  }
   if (a.dtype == 0) {
     if (a.fast) decode_dispatch<float, true>(a, st);
     else decode_dispatch<float, false>(a, st);

@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(kThreads) k_quant_f64(const double *__restrict
 template <typename C>
 cudaError_t quant_dispatch(const QuantLaunch &a, cudaStream_t st) {
   C *qx = static_cast<C *>(a.q[0]), *qy = static_cast<C *>(a.q[1]), *qz = static_cast<C *>(a.q[2]);
+  TraceScope ts("k_quantize", st);
   if (a.dtype == 0) {
     const float *p = static_cast<const float *>(a.pos);
     if (a.vec && a.fast) k_quant_f32<C, true, true><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
@@ -364,6 +365,7 @@ cudaError_t quant_dispatch(const QuantLaunch &a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_range(const RangeLaunch &a, cudaStream_t st) {
+  TraceScope ts("k_range", st);
   if (a.dtype == 0) {
     const float *p = static_cast<const float *>(a.pos);
     if (a.vec) k_range_f32<true><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.partial);

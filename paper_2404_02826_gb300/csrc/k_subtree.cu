@@ -553,6 +553,7 @@ cudaError_t subtree_dispatch(const SubtreeLaunch &a, cudaStream_t st) {
                                        int(smem));
   if (e != cudaSuccess) return e;
   const uint64_t roots = 1ull << a.root_level;
+  TraceScope ts("k_subtree", st);
   k_subtree<C, IDX, EMAX><<<unsigned(roots), kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }

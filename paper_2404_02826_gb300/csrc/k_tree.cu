@@ -416,18 +416,27 @@ __global__ void __launch_bounds__(kScatThreads) k_scatter(LevelLaunch a) {
 template <typename C, bool IDX>
 cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   const uint64_t count = 1ull << a.level;
-  k_prep<<<unsigned((count + 255) / 256), 256, 0, st>>>(a.nodes, a.children, a.n, a.level, a.digit_bits, a.root_hi);
+  {
+    TraceScope ts("k_prep", st);
+    k_prep<<<unsigned((count + 255) / 256), 256, 0, st>>>(a.nodes, a.children, a.n, a.level, a.digit_bits,
+                                                          a.root_hi);
+  }
   const int axis = a.level % 3;
   const C *codes = static_cast<const C *>(a.src[axis]);
   const size_t hsm = sizeof(uint32_t) << a.digit_bits;
   for (uint32_t p = 0; p < a.passes; ++p) {
-    k_hist<C><<<a.hist_blocks, kHistThreads, hsm, st>>>(codes, a.nodes, a.hist, a.n, a.level, a.digit_bits);
+    {
+      TraceScope ts("k_hist", st);
+      k_hist<C><<<a.hist_blocks, kHistThreads, hsm, st>>>(codes, a.nodes, a.hist, a.n, a.level, a.digit_bits);
+    }
+    TraceScope ts("k_select", st);
     k_select<<<unsigned(count), kSelThreads, 0, st>>>(a.nodes, a.hist, a.n, a.level, a.digit_bits);
   }
   const size_t ssm = sizeof(ScatShared<C, IDX>);
   cudaError_t e = cudaFuncSetAttribute(k_scatter<C, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ssm));
   if (e != cudaSuccess) return e;
   const uint64_t tiles = count * a.tiles_per_node;
+  TraceScope ts("k_scatter", st);
   k_scatter<C, IDX><<<unsigned(tiles), kScatThreads, ssm, st>>>(a);
   return cudaGetLastError();
 }

@@ -386,6 +386,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
   PC_TRY(cudaMemcpyAsync(&back.total, total_dev, 8, cudaMemcpyDeviceToHost, st));
   PC_TRY(cudaMemcpyAsync(&back.err, err, 4, cudaMemcpyDeviceToHost, st));
   PC_TRY(cudaStreamSynchronize(st));
+  trace_flush();
   if (back.err & kErrTimeout) return PC_ERR_TIMEOUT;
   if (back.err) return PC_ERR_CUDA;
   *out_size = back.total;
@@ -465,6 +466,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   uint32_t e = 0;
   PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
   PC_TRY(cudaStreamSynchronize(st));
+  trace_flush();
   if (e & kErrCorrupt) return PC_ERR_CORRUPT;
   if (e) return PC_ERR_CUDA;
   return PC_OK;

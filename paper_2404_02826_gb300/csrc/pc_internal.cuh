@@ -87,6 +87,22 @@ __host__ __device__ inline uint32_t bit_length(uint64_t x) {
 // Eq. 2 on the lattice: m = 0 for R = 0, else bit_length(R) + 1.
 __host__ __device__ inline uint32_t bits_for_range(uint32_t R) { return R ? bit_length(R) + 1 : 0; }
 
+// Brackets the launches issued during its lifetime with CUDA events when
+// tracing is on (pc_trace_enable); results are collected by trace_flush().
+class TraceScope {
+ public:
+  TraceScope(const char *name, cudaStream_t st);
+  ~TraceScope();
+  TraceScope(const TraceScope &) = delete;
+  TraceScope &operator=(const TraceScope &) = delete;
+
+ private:
+  const char *name_;
+  cudaStream_t st_;
+  void *a_, *b_;
+};
+void trace_flush();
+
 // ---- launchers (defined in the kernel translation units) -------------------
 
 struct RangeLaunch {
