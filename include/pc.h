@@ -118,6 +118,26 @@ int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, doubl
                 void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
                 uint32_t *perm, void *stream);
 
+/* Compression for callers that may not allocate device memory (the paper has
+ * no counterpart; this is a deployment convenience).  Examples are code running
+ * inside another framework's memory pool that is only handed its input and
+ * output buffers, and latency-critical paths where cudaMalloc / cudaFree could
+ * synchronise the device.  It behaves like pc_compress without `perm`, but its
+ * scratch is a library-owned static device array of PC_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that each GPU using it keeps until the process exits:
+ *   - problems whose scratch exceeds the array (above about 2^20 particles at
+ *     the default leaf size; pc_compress_workspace_size tells) return
+ *     PC_ERR_CAPACITY before any work;
+ *   - the first call on a device looks up the array's device address and
+ *     caches it: make that first call before any stream capture;
+ *   - all calls on a device share the array; what must start at zero is
+ *     cleared by every call, but calls that overlap on the GPU race on it and
+ *     must be serialised by the caller;
+ *   - no allocation happens while kernel tracing (pc_trace_enable) is off. */
+#define PC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int pc_compress_noalloc(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                        void *out, uint64_t out_capacity, uint64_t *out_size, void *stream);
+
 /* Parse a stream header held in host memory (the first 96 bytes suffice). */
 int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info);
 

@@ -43,8 +43,9 @@ EXPORTS = (
     "pc_compress_bound", "pc_compress_workspace_size", "pc_compress", "pc_stream_info",
     "pc_decompress_workspace_size", "pc_decompress", "pc_compress_host_workspace_size", "pc_compress_host",
     "pc_decompress_host_workspace_size", "pc_decompress_host", "pc_error_string", "pc_format_version",
-    "pc_trace_enable", "pc_trace_reset", "pc_trace_count", "pc_trace_get",
+    "pc_trace_enable", "pc_trace_reset", "pc_trace_count", "pc_trace_get", "pc_compress_noalloc",
 )
+PC_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class PCError(RuntimeError):
@@ -91,6 +92,7 @@ def _lib():
         L.pc_error_string.argtypes = [i32]
         L.pc_error_string.restype = ctypes.c_char_p
         L.pc_format_version.argtypes = []
+        L.pc_compress_noalloc.argtypes = [vp, u64, i32, i32, dbl, pcfg, vp, u64, pu64, vp]
         L.pc_trace_enable.argtypes = [i32]
         L.pc_trace_reset.argtypes = []
         L.pc_trace_count.argtypes = []
@@ -152,6 +154,21 @@ def pc_compress(positions, eb_mode: int, eb: float, out, workspace, leaf_size: i
                             ctypes.byref(size), workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                             perm.data_ptr() if perm is not None else None, _stream_handle(stream))
     _check(rc, "pc_compress")
+    return size.value
+
+
+def pc_compress_noalloc(positions, eb_mode: int, eb: float, out, leaf_size: int = 0, stream=None) -> int:
+    """Compress with the library's static scratch (no device allocation by the library).
+
+    For callers that may not allocate device memory; the scratch is a 32 MiB
+    array per GPU shared by all calls, so calls must not overlap on the GPU.
+    Problems that do not fit raise PCError with PC_ERR_CAPACITY."""
+    n = positions.shape[0] if positions.dim() == 2 else positions.numel() // 3
+    size = ctypes.c_uint64()
+    rc = _lib().pc_compress_noalloc(positions.data_ptr() if n else None, n, _dtype_of(positions), eb_mode,
+                                    float(eb), ctypes.byref(_cfg(leaf_size)), out.data_ptr(),
+                                    out.numel() * out.element_size(), ctypes.byref(size), _stream_handle(stream))
+    _check(rc, "pc_compress_noalloc")
     return size.value
 
 

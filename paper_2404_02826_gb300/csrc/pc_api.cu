@@ -474,6 +474,17 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
 
 }  // namespace
 
+namespace pcx {
+
+int compress_device(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                    void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
+                    cudaStream_t st) {
+  return compress_impl(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, workspace,
+                       workspace_bytes, nullptr, st);
+}
+
+}  // namespace pcx
+
 extern "C" {
 
 int pc_compress_bound(uint64_t n, int dtype, const pc_config *cfg, uint64_t *out_bytes) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "../../include/pc.h"
+
 namespace pcx {
 
 constexpr uint32_t kHeaderBytes = 96;
@@ -204,5 +206,10 @@ struct DecodeLaunch {
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
 
 int device_sm_count();
+
+// pc_compress without the optional permutation, on a caller-provided workspace.
+int compress_device(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                    void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
+                    cudaStream_t st);
 
 }  // namespace pcx
