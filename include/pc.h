@@ -141,8 +141,9 @@ int pc_compress_noalloc(const void *positions, uint64_t n, int dtype, int eb_mod
 /* Parse a stream header held in host memory (the first 96 bytes suffice). */
 int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info);
 
-/* Device scratch needed by pc_decompress, in bytes (host only). */
-int pc_decompress_workspace_size(uint64_t *out_bytes);
+/* Device scratch needed by pc_decompress for a stream of n particles
+ * (pc_info.n), in bytes (host only). */
+int pc_decompress_workspace_size(uint64_t n, uint64_t *out_bytes);
 
 /* Decompress a device stream into T[n][3] positions (Sec. 3 dequantization,
  * p_hat = (T)(o + s q) with one double multiply and one double add).

@@ -83,7 +83,7 @@ def _lib():
         L.pc_compress_workspace_size.argtypes = [u64, i32, pcfg, i32, pu64]
         L.pc_compress.argtypes = [vp, u64, i32, i32, dbl, pcfg, vp, u64, pu64, vp, u64, vp, vp]
         L.pc_stream_info.argtypes = [vp, u64, ctypes.POINTER(pc_info)]
-        L.pc_decompress_workspace_size.argtypes = [pu64]
+        L.pc_decompress_workspace_size.argtypes = [u64, pu64]
         L.pc_decompress.argtypes = [vp, u64, vp, u64, vp, u64, vp]
         L.pc_compress_host_workspace_size.argtypes = [u64, i32, pcfg, pu64]
         L.pc_compress_host.argtypes = [vp, u64, i32, i32, dbl, pcfg, vp, u64, pu64, vp, u64, vp]
@@ -195,9 +195,9 @@ def pc_stream_info(header: bytes) -> StreamInfo:
                       info.payload_words, info.leaf_size, info.total_bytes)
 
 
-def pc_decompress_workspace_size() -> int:
+def pc_decompress_workspace_size(n: int) -> int:
     out = ctypes.c_uint64()
-    _check(_lib().pc_decompress_workspace_size(ctypes.byref(out)), "pc_decompress_workspace_size")
+    _check(_lib().pc_decompress_workspace_size(n, ctypes.byref(out)), "pc_decompress_workspace_size")
     return out.value
 
 
@@ -290,7 +290,7 @@ class Compressor:
         self.ws = torch.empty(pc_compress_workspace_size(n, dtype, leaf_size, with_perm), dtype=torch.uint8,
                               device=device)
         self.perm = torch.empty(max(n, 1), dtype=torch.int32, device=device) if with_perm else None
-        self.dws = torch.empty(pc_decompress_workspace_size(), dtype=torch.uint8, device=device)
+        self.dws = torch.empty(pc_decompress_workspace_size(n), dtype=torch.uint8, device=device)
 
     def compress(self, positions, eb_mode: int, eb: float, stream=None) -> int:
         return pc_compress(positions, eb_mode, eb, self.out, self.ws, self.leaf_size, self.perm, stream)
@@ -313,6 +313,6 @@ def decompress(stream_data):
     info = pc_stream_info(stream_data[:PC_HEADER_BYTES].cpu().numpy().tobytes())
     dt = torch.float32 if info.dtype == PC_F32 else torch.float64
     out = torch.empty((info.n, 3), dtype=dt, device=stream_data.device)
-    ws = torch.empty(pc_decompress_workspace_size(), dtype=torch.uint8, device=stream_data.device)
+    ws = torch.empty(pc_decompress_workspace_size(info.n), dtype=torch.uint8, device=stream_data.device)
     pc_decompress(stream_data, out, ws, info.total_bytes)
     return out

@@ -4,12 +4,14 @@
 // Decoding reconstructs p_hat = (T)(o + s q) with one double multiply and one
 // double add, q = q_ref + c - (2^(m-1) - 1) and q = q_ref for the centre.  For
 // float output the kernel evaluates that expression on the FP32 pipe: s q and
-// o + s q are formed as unevaluated float sums with error-free products and
-// sums (relative error below 2^-45 of max(|o|, |s q|)), rounded once to float,
-// and the literal double expression is used whenever that sum lies within
-// 2^-40 of a rounding midpoint, sits on a power of two, or is tiny.  Elsewhere
-// the two agree, because the double-precision value is within 2^-51 of the
-// exact one.  Double output uses the double expression directly.
+// o + s q are formed as an unevaluated float sum zh + zl with error-free
+// products and sums (error below 2^-45 of max(|o|, |s q|)).  It then rounds
+// zh + zl - tol and zh + zl + tol to float, tol = 2^-40 max(|o|, |s q|): when
+// both give the same float, every real number in between - the exact value and
+// the double-precision value, which is within 2^-51 of it - rounds to that
+// float too (rounding to nearest is monotone).  Otherwise, and for tiny or
+// huge magnitudes, the literal double expression decides.  Double output uses
+// the double expression directly.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -20,6 +22,7 @@ namespace {
 constexpr int kDecThreads = 256;
 constexpr int kDecPer = 4;                          // particles per thread
 constexpr int kChunk = kDecThreads * kDecPer;       // particles per block
+constexpr int kChunkLeaves = 32;                    // leaves of one chunk held in shared memory
 
 struct Rec {
   uint64_t po, wo;
@@ -48,9 +51,10 @@ __device__ __forceinline__ uint64_t leaf_words(const Rec &r, uint64_t cnt) {
   return ((uint64_t)(r.m[0] + r.m[1] + r.m[2]) * (cnt - 1) + 31) >> 5;
 }
 
-// One thread per leaf: every field and every neighbour relation is checked.
+// One thread per leaf: every field and every neighbour relation is checked,
+// and each decode chunk whose first particle lies in this leaf records it.
 __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves, uint64_t words,
-                           uint32_t *err) {
+                           uint32_t *chunk_leaf, uint32_t *err) {
   const uint64_t L = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (L >= num_leaves) return;
   const uint8_t *table = stream + kHeaderBytes;
@@ -63,101 +67,143 @@ __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint6
     const uint64_t wnext = (L + 1 < num_leaves) ? load_rec(table, L + 1).wo : words;
     ok = r.wo <= words && wend == wnext;
   }
-  if (!ok) atomicOr(err, kErrCorrupt);
+  if (!ok) {
+    atomicOr(err, kErrCorrupt);
+    return;
+  }
+  for (uint64_t c = (r.po + kChunk - 1) / kChunk; c * kChunk < pend; ++c) chunk_leaf[c] = uint32_t(L);
 }
 
-__device__ __forceinline__ uint32_t get_bits(const uint32_t *__restrict__ w, uint64_t nwords, uint64_t bit,
-                                             uint32_t m) {
-  const uint64_t i = bit >> 5;
-  const uint32_t lo = i < nwords ? __ldg(w + i) : 0u;
-  const uint32_t hi = (i + 1) < nwords ? __ldg(w + i + 1) : 0u;
-  const unsigned long long v = ((unsigned long long)hi << 32 | lo) >> (bit & 31);
-  return uint32_t(v) & ((1u << m) - 1u);
+__device__ __forceinline__ uint32_t word_at(const uint32_t *__restrict__ w, uint64_t nwords, uint64_t i) {
+  return i < nwords ? __ldg(w + i) : 0u;
 }
 
-// float-pair evaluation of (float)(o + s*q) with a double fallback
+__device__ __forceinline__ float dequant_exact(int32_t q, double od, double s) {
+  return __double2float_rn(__dadd_rn(od, __dmul_rn(s, (double)q)));
+}
+// The same, kept out of line so that the rare fallback below is a real branch:
+// inlined, the compiler evaluates it speculatively on GB300's narrow FP64 pipe.
+__device__ __noinline__ float dequant_exact_call(int32_t q, double od, double s) { return dequant_exact(q, od, s); }
+
+// float-pair evaluation of (float)(o + s*q), exact by the monotonicity check
 __device__ __forceinline__ float dequant_fast(int32_t q, float of, double od, double s, float sh, float sl) {
-  if (q < 0 || q >= (1 << 24)) return __double2float_rn(__dadd_rn(od, __dmul_rn(s, (double)q)));
-  const float qf = (float)q;  // exact
+  const float qf = (float)q;  // exact while |q| < 2^24
   const float yh = __fmul_rn(sh, qf);
   const float ye = __fmaf_rn(sh, qf, -yh);
   const float yl = __fmaf_rn(sl, qf, ye);
-  // TwoSum(of, yh)
+  // TwoSum(of, yh): zh + ze == of + yh exactly
   const float zh = __fadd_rn(of, yh);
   const float bb = __fsub_rn(zh, of);
   const float ze = __fadd_rn(__fsub_rn(of, __fsub_rn(zh, bb)), __fsub_rn(yh, bb));
   const float zl = __fadd_rn(ze, yl);
-  const float out = __fadd_rn(zh, zl);
-  // exact residual of the final rounding
-  const float b2 = __fsub_rn(out, zh);
-  const float err = __fadd_rn(__fsub_rn(zh, __fsub_rn(out, b2)), __fsub_rn(zl, b2));
-  const uint32_t ob = __float_as_uint(out) & 0x7fffffffu;
-  const uint32_t ex = ob >> 23;
   const float mag = fmaxf(fabsf(of), fabsf(yh));
-  const uint32_t mb = __float_as_uint(mag) >> 23;
-  if (ex >= 64 && ex < 255 && (ob & 0x7fffffu) != 0 && mb >= 64 && mb < 255) {
-    const float half = __uint_as_float((ex - 24) << 23);  // half a unit in the last place of out
-    const float tol = __uint_as_float((mb - 40) << 23);   // 2^-40 of max(|o|, |s q|), rounded down
-    if (__fsub_rn(half, fabsf(err)) > tol) return out;
-  }
-  return __double2float_rn(__dadd_rn(od, __dmul_rn(s, (double)q)));
+  const float tol = __fmul_rn(mag, 0x1p-40f);
+  const float r1 = __fadd_rn(zh, __fsub_rn(zl, tol));
+  const float r2 = __fadd_rn(zh, __fadd_rn(zl, tol));
+  if (__builtin_expect(r1 == r2 && mag > 0x1p-80f && mag < 0x1p100f && (unsigned)q < (1u << 24), 1)) return r1;
+  return dequant_exact_call(q, od, s);
+}
+
+// Code of m bits at bit offset r (0 <= r < 96) of the window w0..w3.
+__device__ __forceinline__ uint32_t window_bits(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t r,
+                                                uint32_t m) {
+  const uint32_t k = r >> 5;
+  const uint32_t lo = k == 0 ? w0 : (k == 1 ? w1 : w2);
+  const uint32_t hi = k == 0 ? w1 : (k == 1 ? w2 : w3);
+  return __funnelshift_r(lo, hi, r & 31) & ((1u << m) - 1u);
 }
 
 template <typename T, bool FAST, bool VEC>
 __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
   __shared__ __align__(16) T stage[3 * kChunk];
-  __shared__ uint64_t first_leaf;
+  __shared__ uint64_t s_po[kChunkLeaves + 1], s_wo[kChunkLeaves];
+  __shared__ int32_t s_q[kChunkLeaves][3];
+  __shared__ uint32_t s_m[kChunkLeaves];
+  __shared__ int s_count;
   if (*a.err) return;  // validation failed: write nothing
   const uint64_t c0 = uint64_t(blockIdx.x) * kChunk;
   if (c0 >= a.n) return;
   const uint64_t c1 = (c0 + kChunk) < a.n ? (c0 + kChunk) : a.n;
   const uint8_t *table = a.stream + kHeaderBytes;
   const uint32_t *words = reinterpret_cast<const uint32_t *>(table + uint64_t(kLeafBytes) * a.num_leaves);
-  if (threadIdx.x == 0) {
-    uint64_t lo = 0, hi = a.num_leaves - 1;  // last leaf with po <= c0
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi + 1) >> 1;
-      if (load_rec(table, mid).po <= c0) lo = mid;
-      else hi = mid - 1;
+  const uint64_t first = a.chunk_leaf[blockIdx.x];
+  // the chunk's leaves (usually one or two) into shared memory
+  if (threadIdx.x < kChunkLeaves + 1) {
+    const uint64_t L = first + threadIdx.x;
+    if (L < a.num_leaves) {
+      const Rec r = load_rec(table, L);
+      s_po[threadIdx.x] = r.po;
+      if (threadIdx.x < kChunkLeaves) {
+        s_wo[threadIdx.x] = r.wo;
+        s_q[threadIdx.x][0] = r.q[0];
+        s_q[threadIdx.x][1] = r.q[1];
+        s_q[threadIdx.x][2] = r.q[2];
+        s_m[threadIdx.x] = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
+      }
+    } else {
+      s_po[threadIdx.x] = a.n;
     }
-    first_leaf = lo;
   }
   __syncthreads();
-  const uint64_t Lf = first_leaf;
+  if (threadIdx.x == 0) {
+    int c = 1;
+    while (c < kChunkLeaves && s_po[c] < c1) ++c;
+    s_count = c;
+  }
+  __syncthreads();
+  const int count = s_count;
+  const bool in_smem = count < kChunkLeaves || s_po[kChunkLeaves] >= c1;
+#pragma unroll
   for (int k = 0; k < kDecPer; ++k) {
     const uint64_t g = c0 + uint64_t(k) * kDecThreads + threadIdx.x;
-    if (g >= c1) break;
-    // leaf of g: the last L >= Lf with po(L) <= g
-    uint64_t lo = Lf, hi = a.num_leaves - 1;
-    uint64_t span = 1;
-    while (lo + span <= hi && load_rec(table, lo + span).po <= g) span <<= 1;  // gallop
-    hi = (lo + span) < hi ? (lo + span) : hi;
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi + 1) >> 1;
-      if (load_rec(table, mid).po <= g) lo = mid;
-      else hi = mid - 1;
-    }
-    const Rec r = load_rec(table, lo);
-    const uint64_t i = g - r.po;
-    int32_t q[3] = {r.q[0], r.q[1], r.q[2]};
-    if (i > 0) {
-      const uint32_t w = r.m[0] + r.m[1] + r.m[2];
-      uint64_t bit = 32ull * r.wo + (i - 1) * (uint64_t)w;
-      for (int d = 0; d < 3; ++d) {
-        const uint32_t m = r.m[d];
-        if (m) {
-          const uint32_t c = get_bits(words, a.payload_words, bit, m);
-          q[d] = r.q[d] + int32_t(c) - int32_t((1u << (m - 1)) - 1u);
-          bit += m;
-        }
+    if (g >= c1) continue;
+    uint64_t po, wo;
+    int32_t q0, q1, q2;
+    uint32_t mm;
+    if (in_smem) {
+      int L = 0;
+      while (L + 1 < count && s_po[L + 1] <= g) ++L;
+      po = s_po[L];
+      wo = s_wo[L];
+      q0 = s_q[L][0];
+      q1 = s_q[L][1];
+      q2 = s_q[L][2];
+      mm = s_m[L];
+    } else {  // many small leaves in this chunk: search the table
+      uint64_t lo = first, hi = a.num_leaves - 1;
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (load_rec(table, mid).po <= g) lo = mid;
+        else hi = mid - 1;
       }
+      const Rec r = load_rec(table, lo);
+      po = r.po;
+      wo = r.wo;
+      q0 = r.q[0];
+      q1 = r.q[1];
+      q2 = r.q[2];
+      mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
+    }
+    const uint64_t i = g - po;
+    if (i > 0) {
+      const uint32_t m0 = mm & 0xffu, m1 = (mm >> 8) & 0xffu, m2 = (mm >> 16) & 0xffu;
+      const uint64_t bit = 32ull * wo + (i - 1) * (uint64_t)(m0 + m1 + m2);
+      const uint64_t wi = bit >> 5;
+      const uint32_t w0 = word_at(words, a.payload_words, wi), w1 = word_at(words, a.payload_words, wi + 1);
+      const uint32_t w2 = word_at(words, a.payload_words, wi + 2), w3 = word_at(words, a.payload_words, wi + 3);
+      const uint32_t r0 = uint32_t(bit & 31);
+      if (m0) q0 += int32_t(window_bits(w0, w1, w2, w3, r0, m0)) - int32_t((1u << (m0 - 1)) - 1u);
+      if (m1) q1 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0, m1)) - int32_t((1u << (m1 - 1)) - 1u);
+      if (m2) q2 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0 + m1, m2)) - int32_t((1u << (m2 - 1)) - 1u);
     }
     const uint32_t sl = uint32_t(g - c0);
+    const int32_t q[3] = {q0, q1, q2};
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
       T v;
       if (sizeof(T) == 4) {
         if (FAST) v = (T)dequant_fast(q[d], a.of[d], a.o[d], a.s, a.sh, a.sl);
-        else v = (T)__double2float_rn(__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q[d])));
+        else v = (T)dequant_exact(q[d], a.o[d], a.s);
       } else {
         v = (T)__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q[d]));
       }
@@ -178,12 +224,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
 }
 
 __global__ void k_header(HeaderLaunch a) {
-  uint64_t words = 0;
-  if (a.last_state) {
-    const unsigned long long s = *a.last_state;
-    if ((s >> 62) != 2) atomicOr(a.err, kErrInternal);
-    words = s & ((1ull << 62) - 1);
-  }
+  const uint64_t words = a.total_words ? *a.total_words : 0;
   __align__(16) uint8_t h[kHeaderBytes];
   for (int i = 0; i < int(kHeaderBytes); ++i) h[i] = 0;
   h[0] = 'P';
@@ -213,13 +254,15 @@ __global__ void k_header(HeaderLaunch a) {
 
 template <typename T, bool FAST>
 void decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
-  const unsigned blocks = unsigned((a.n + kChunk - 1) / kChunk);
+  const unsigned blocks = unsigned(decode_chunks(a.n));
   TraceScope ts("k_decode", st);
   if (a.vec) k_decode<T, FAST, true><<<blocks, kDecThreads, 0, st>>>(a);
   else k_decode<T, FAST, false><<<blocks, kDecThreads, 0, st>>>(a);
 }
 
 }  // namespace
+
+uint64_t decode_chunks(uint64_t n) { return (n + kChunk - 1) / kChunk; }
 
 cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st) {
   TraceScope ts("k_header", st);
@@ -232,7 +275,7 @@ cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st) {
   {
     TraceScope ts("k_validate", st);
     k_validate<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
-                                                                        a.err);
+                                                                        a.chunk_leaf, a.err);
   }
   if (a.dtype == 0) {
     if (a.fast) decode_dispatch<float, true>(a, st);

@@ -1,0 +1,317 @@
+// Leaves of the k-d partition: bit boxes (Sec. 4.1, Eq. 2) and the packed
+// sequences (Sec. 4.2, Fig. 4) of arXiv 2404.02826.
+//
+// After the last level the codes are stored leaf after leaf, each leaf in
+// original-index order.  Four kernels:
+//   k_leaftable  the leaf ranges, from the deterministic node sizes;
+//   k_leafbox    one CTA per leaf: AABB, the particle closest to the AABB
+//                centre (squared distance in doubled lattice units, first in
+//                leaf order on ties), R_d and m_d = bit_length(R_d) + 1 (0 for
+//                R_d = 0), and the leaf's payload size (sum m)(n - 1) bits;
+//   k_leafscan   exclusive scan of the payload words: each leaf's first word;
+//   k_leafpack   one CTA per leaf: its 32-byte record, its payload and the
+//                optional permutation.  A warp packs 32 consecutive particles
+//                at a time; 32 particles of w bits fill exactly w words, so each
+//                lane assembles whole words from the staged w-bit values.
+#include <cstdint>
+
+#include "pc_internal.cuh"
+
+namespace pcx {
+namespace {
+
+constexpr int kBoxThreads = 256;
+constexpr int kPackThreads = 256;
+constexpr int kPackWarps = kPackThreads / 32;
+
+__global__ void k_leaftable(uint64_t n, int level, uint32_t r, LeafRec *recs, uint64_t num_leaves) {
+  const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (level < 0) {  // no split at all: one leaf
+    if (j == 0 && num_leaves == 1) {
+      LeafRec z = {};
+      z.off = 0;
+      z.cnt = uint32_t(n);
+      recs[0] = z;
+    }
+    return;
+  }
+  if (j >= (1ull << level)) return;
+  uint64_t off, cnt;
+  node_range(n, level, j, off, cnt);
+  const uint64_t a = n >> level;
+  // leaves before this node: 2 per earlier node if every node splits, else
+  // one per earlier node plus one per earlier node of the larger size
+  const uint64_t base = a > r ? 2 * j : j + (off - j * a);
+  LeafRec x = {};
+  if (cnt <= r) {
+    x.off = uint32_t(off);
+    x.cnt = uint32_t(cnt);
+    if (base < num_leaves) recs[base] = x;
+  } else {
+    const uint64_t h = cnt >> 1;
+    x.off = uint32_t(off);
+    x.cnt = uint32_t(h);
+    if (base < num_leaves) recs[base] = x;
+    x.off = uint32_t(off + h);
+    x.cnt = uint32_t(cnt - h);
+    if (base + 1 < num_leaves) recs[base + 1] = x;
+  }
+}
+
+template <typename C>
+struct Vec16;  // codes per 16-byte vector
+template <>
+struct Vec16<uint16_t> {
+  static constexpr int N = 8;
+  static __device__ __forceinline__ uint32_t at(const uint4 &w, int i) {
+    const uint32_t x = i < 2 ? w.x : (i < 4 ? w.y : (i < 6 ? w.z : w.w));
+    return (i & 1) ? (x >> 16) : (x & 0xffffu);
+  }
+};
+template <>
+struct Vec16<uint32_t> {
+  static constexpr int N = 4;
+  static __device__ __forceinline__ uint32_t at(const uint4 &w, int i) {
+    return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
+  }
+};
+
+// Calls f(position in leaf, x, y, z) for every particle of [off, off + cnt),
+// with 16-byte loads on the aligned body.
+template <typename C, typename F>
+__device__ __forceinline__ void for_leaf(const C *q0, const C *q1, const C *q2, uint32_t off, uint32_t cnt, F f) {
+  constexpr uint32_t kV = Vec16<C>::N;
+  const uint32_t a0 = min((off + kV - 1) / kV * kV, off + cnt);
+  const uint32_t a1 = max(a0, (off + cnt) / kV * kV);
+  for (uint32_t e = off + threadIdx.x; e < a0; e += blockDim.x) f(e - off, uint32_t(q0[e]), uint32_t(q1[e]), uint32_t(q2[e]));
+  for (uint32_t e = a1 + threadIdx.x; e < off + cnt; e += blockDim.x)
+    f(e - off, uint32_t(q0[e]), uint32_t(q1[e]), uint32_t(q2[e]));
+  const uint32_t nv = (a1 - a0) / kV;
+  const uint4 *v0 = reinterpret_cast<const uint4 *>(q0 + a0), *v1 = reinterpret_cast<const uint4 *>(q1 + a0),
+              *v2 = reinterpret_cast<const uint4 *>(q2 + a0);
+  for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
+    const uint4 x = __ldcg(v0 + i), y = __ldcg(v1 + i), z = __ldcg(v2 + i);
+#pragma unroll
+    for (int c = 0; c < int(kV); ++c)
+      f(a0 - off + i * kV + c, Vec16<C>::at(x, c), Vec16<C>::at(y, c), Vec16<C>::at(z, c));
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q0, const C *__restrict__ q1,
+                                                         const C *__restrict__ q2, LeafRec *recs) {
+  __shared__ uint32_t red[6][kBoxThreads / 32];
+  __shared__ unsigned long long rd[kBoxThreads / 32];
+  __shared__ uint32_t rp[kBoxThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  LeafRec rec = recs[blockIdx.x];
+  const uint32_t off = rec.off, cnt = rec.cnt;
+  uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0, 0, 0};
+  for_leaf(q0, q1, q2, off, cnt, [&](uint32_t, uint32_t x, uint32_t y, uint32_t z) {
+    mn[0] = min(mn[0], x);
+    mx[0] = max(mx[0], x);
+    mn[1] = min(mn[1], y);
+    mx[1] = max(mx[1], y);
+    mn[2] = min(mn[2], z);
+    mx[2] = max(mx[2], z);
+  });
+  for (int d = 0; d < 3; ++d) {
+    mn[d] = __reduce_min_sync(0xffffffffu, mn[d]);
+    mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
+    if (lane == 0) {
+      red[2 * d][warp] = mn[d];
+      red[2 * d + 1][warp] = mx[d];
+    }
+  }
+  __syncthreads();
+  uint32_t lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = red[2 * d][0];
+    hi[d] = red[2 * d + 1][0];
+    for (int w = 1; w < kBoxThreads / 32; ++w) {
+      lo[d] = min(lo[d], red[2 * d][w]);
+      hi[d] = max(hi[d], red[2 * d + 1][w]);
+    }
+  }
+  // centre: least squared distance to the AABB centre, lowest position on ties
+  unsigned long long bd = ~0ull;
+  uint32_t bp = 0xffffffffu;
+  const long long s0 = (long long)lo[0] + hi[0], s1 = (long long)lo[1] + hi[1], s2 = (long long)lo[2] + hi[2];
+  for_leaf(q0, q1, q2, off, cnt, [&](uint32_t p, uint32_t x, uint32_t y, uint32_t z) {
+    const long long a = 2ll * x - s0, b = 2ll * y - s1, c = 2ll * z - s2;
+    const unsigned long long d2 = (unsigned long long)(a * a) + (unsigned long long)(b * b) + (unsigned long long)(c * c);
+    if (d2 < bd || (d2 == bd && p < bp)) {
+      bd = d2;
+      bp = p;
+    }
+  });
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+    const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+    if (od < bd || (od == bd && op < bp)) {
+      bd = od;
+      bp = op;
+    }
+  }
+  if (lane == 0) {
+    rd[warp] = bd;
+    rp[warp] = bp;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kBoxThreads / 32; ++w)
+      if (rd[w] < bd || (rd[w] == bd && rp[w] < bp)) {
+        bd = rd[w];
+        bp = rp[w];
+      }
+    const uint32_t c = bp;
+    const uint32_t qc[3] = {uint32_t(q0[off + c]), uint32_t(q1[off + c]), uint32_t(q2[off + c])};
+    uint32_t m[3];
+    for (int d = 0; d < 3; ++d) {
+      const uint32_t R = max(qc[d] - lo[d], hi[d] - qc[d]);
+      m[d] = bits_for_range(R);
+      rec.qref[d] = int32_t(qc[d]);
+    }
+    rec.centre = c;
+    rec.m = m[0] | (m[1] << 8) | (m[2] << 16);
+    const uint64_t bits = uint64_t(m[0] + m[1] + m[2]) * (cnt - 1);
+    rec.words = uint32_t((bits + 31) >> 5);
+    recs[blockIdx.x] = rec;
+  }
+}
+
+// Exclusive scan of the leaves' payload words (one block).
+__global__ void __launch_bounds__(1024) k_leafscan(LeafRec *recs, uint64_t num_leaves, uint64_t *total_words) {
+  __shared__ unsigned long long wt[33];
+  const uint64_t per = (num_leaves + blockDim.x - 1) / blockDim.x;
+  const uint64_t l0 = threadIdx.x * per, l1 = (l0 + per) < num_leaves ? (l0 + per) : num_leaves;
+  unsigned long long sum = 0;
+  for (uint64_t l = l0; l < l1; ++l) sum += recs[l].words;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wt[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long x = wt[lane];
+    unsigned long long xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    wt[lane] = xi - x;
+    if (lane == 31) wt[32] = xi;
+  }
+  __syncthreads();
+  unsigned long long run = wt[warp] + incl - sum;
+  for (uint64_t l = l0; l < l1; ++l) {
+    recs[l].word_off = run;
+    run += recs[l].words;
+  }
+  if (threadIdx.x == 0) *total_words = wt[32];
+}
+
+template <typename C, bool IDX>
+__global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__ q0, const C *__restrict__ q1,
+                                                           const C *__restrict__ q2, const uint32_t *__restrict__ idx,
+                                                           const LeafRec *__restrict__ recs, uint8_t *out,
+                                                           uint64_t num_leaves, uint32_t *perm) {
+  __shared__ uint32_t sv[kPackWarps][32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const LeafRec rec = recs[blockIdx.x];
+  const uint32_t off = rec.off, cnt = rec.cnt, centre = rec.centre;
+  const uint32_t m0 = rec.m & 0xffu, m1 = (rec.m >> 8) & 0xffu, m2 = (rec.m >> 16) & 0xffu;
+  const uint32_t w = m0 + m1 + m2;
+  if (threadIdx.x == 0) {
+    uint4 *r = reinterpret_cast<uint4 *>(out + kHeaderBytes + uint64_t(kLeafBytes) * blockIdx.x);
+    const uint64_t po = off, wo = rec.word_off;
+    r[0] = make_uint4(uint32_t(po), uint32_t(po >> 32), uint32_t(wo), uint32_t(wo >> 32));
+    r[1] = make_uint4(uint32_t(rec.qref[0]), uint32_t(rec.qref[1]), uint32_t(rec.qref[2]), rec.m);
+  }
+  if (IDX && perm) {
+    for (uint32_t i = threadIdx.x; i < cnt; i += kPackThreads) {
+      const uint32_t src = i == 0 ? centre : (i - 1 < centre ? i - 1 : i);
+      perm[off + i] = idx[off + src];
+    }
+  }
+  if (w == 0 || cnt < 2) return;
+  uint32_t *payload = reinterpret_cast<uint32_t *>(out + kHeaderBytes + uint64_t(kLeafBytes) * num_leaves) + rec.word_off;
+  const uint32_t h0 = m0 ? (1u << (m0 - 1)) - 1u : 0u;
+  const uint32_t h1 = m1 ? (1u << (m1 - 1)) - 1u : 0u;
+  const uint32_t h2 = m2 ? (1u << (m2 - 1)) - 1u : 0u;
+  const uint32_t r0 = uint32_t(rec.qref[0]), r1 = uint32_t(rec.qref[1]), r2 = uint32_t(rec.qref[2]);
+  const uint32_t slots = cnt - 1;
+  const uint32_t words = rec.words;
+  const uint32_t chunks = (slots + 31) / 32;
+  for (uint32_t ch = warp; ch < chunks; ch += kPackWarps) {
+    // this lane's particle as one w-bit value: c_x | c_y << m_x | c_z << (m_x + m_y)
+    const uint32_t s = ch * 32 + lane;
+    unsigned __int128 V = 0;
+    if (s < slots) {
+      const uint32_t p = off + (s < centre ? s : s + 1);
+      const uint32_t cx = m0 ? uint32_t(q0[p]) - r0 + h0 : 0u;
+      const uint32_t cy = m1 ? uint32_t(q1[p]) - r1 + h1 : 0u;
+      const uint32_t cz = m2 ? uint32_t(q2[p]) - r2 + h2 : 0u;
+      V = (unsigned __int128)cx | ((unsigned __int128)cy << m0) | ((unsigned __int128)cz << (m0 + m1));
+    }
+    sv[warp][lane][0] = uint32_t(V);
+    sv[warp][lane][1] = uint32_t(V >> 32);
+    sv[warp][lane][2] = uint32_t(V >> 64);
+    __syncwarp();
+    // the 32 values occupy exactly w words of this chunk
+    for (uint32_t t = lane; t < w; t += 32) {
+      const uint32_t gw = ch * w + t;
+      if (gw >= words) break;
+      const uint32_t b0 = 32 * t;
+      const uint32_t i0 = b0 / w, i1 = min((b0 + 31) / w, 31u);
+      uint32_t word = 0;
+      for (uint32_t i = i0; i <= i1; ++i) {
+        const unsigned __int128 Vi = (unsigned __int128)sv[warp][i][0] | ((unsigned __int128)sv[warp][i][1] << 32) |
+                                     ((unsigned __int128)sv[warp][i][2] << 64);
+        const uint32_t start = i * w;  // bit of this value within the chunk
+        if (start >= b0) word |= uint32_t(Vi << (start - b0));
+        else word |= uint32_t(Vi >> (b0 - start));
+      }
+      __stcs(payload + gw, word);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename C, bool IDX>
+cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
+  const C *q0 = static_cast<const C *>(a.codes[0]), *q1 = static_cast<const C *>(a.codes[1]),
+          *q2 = static_cast<const C *>(a.codes[2]);
+  {
+    TraceScope ts("k_leaftable", st);
+    const uint64_t nodes = a.split_level < 0 ? 1 : (1ull << a.split_level);
+    k_leaftable<<<unsigned((nodes + 255) / 256), 256, 0, st>>>(a.n, a.split_level, a.leaf_size, a.recs,
+                                                               a.num_leaves);
+  }
+  {
+    TraceScope ts("k_leafbox", st);
+    k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs);
+  }
+  {
+    TraceScope ts("k_leafscan", st);
+    k_leafscan<<<1, 1024, 0, st>>>(a.recs, a.num_leaves, a.total_words);
+  }
+  TraceScope ts("k_leafpack", st);
+  k_leafpack<C, IDX><<<unsigned(a.num_leaves), kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out, a.num_leaves,
+                                                                      a.perm);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st) {
+  if (a.n == 0 || a.num_leaves == 0) return cudaSuccess;
+  if (a.code_bytes == 2)
+    return a.idx ? leaves_dispatch<uint16_t, true>(a, st) : leaves_dispatch<uint16_t, false>(a, st);
+  return a.idx ? leaves_dispatch<uint32_t, true>(a, st) : leaves_dispatch<uint32_t, false>(a, st);
+}
+
+}  // namespace pcx

@@ -242,6 +242,10 @@ __device__ __forceinline__ uint32_t quant_exact(double p, double o, double s) {
   return (uint32_t)rint(__ddiv_rn(__dsub_rn(p, o), s));
 }
 
+// Out of line, so that the rare fallback stays a branch and is not evaluated
+// speculatively on the narrow FP64 pipe.
+__device__ __noinline__ uint32_t quant_exact_call(float p, double o, double s) { return quant_exact((double)p, o, s); }
+
 // Same result for float input, evaluated on the FP32 pipe (see file comment).
 __device__ __forceinline__ uint32_t quant_fast(float p, float o, double od, double s, float rh, float rl) {
   // TwoSum(p, -o): dh + dl == p - o exactly.
@@ -254,8 +258,8 @@ __device__ __forceinline__ uint32_t quant_fast(float p, float o, double od, doub
   float tl = __fmaf_rn(dh, rl, __fmaf_rn(dl, rh, pe));
   float q0 = rintf(th);
   float r = __fadd_rn(__fsub_rn(th, q0), tl);
-  if (fabsf(r) < 0.5f - 0x1p-20f) return (uint32_t)q0;
-  return quant_exact((double)p, od, s);
+  if (__builtin_expect(fabsf(r) < 0.5f - 0x1p-20f, 1)) return (uint32_t)q0;
+  return quant_exact_call(p, od, s);
 }
 
 template <typename C>

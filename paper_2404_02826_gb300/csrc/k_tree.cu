@@ -3,8 +3,8 @@
 // A node at depth l splits on axis l mod 3.  Sorting its particles by
 // (code, original index), the first floor(c/2) go left, so the median lies on
 // the larger-coordinate side.  Particles of a node are stored contiguously and
-// in original-index order (every partition below is stable), so "original
-// index" is simply "position in the node".
+// in original-index order (every partition is stable), so "original index" is
+// simply "position in the node".
 //
 // One level is four kernels:
 //   prep     per node: code bounds -> first radix digit (or "all equal")
@@ -12,11 +12,8 @@
 //   select   per node: the bucket that holds rank floor(c/2); after the last
 //            digit this gives the split code v, the count below it and how
 //            many particles equal to v go left
-//   scatter  stable two-way partition of every node into its children, with
-//            the node-local prefix counts obtained by a decoupled look-back
-//            over the node's tiles; it also records each child's code bounds
-//            on the next axis
-#include <cuda/atomic>
+//   scatter  stable two-way partition of every node into its children
+//            (k_scatter.cu)
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -26,70 +23,12 @@ namespace {
 
 constexpr int kHistThreads = 512;
 constexpr int kSelThreads = 256;
-constexpr int kScatThreads = 256;
-constexpr int kScatWarps = kScatThreads / 32;
-constexpr int kScatItems = 16;                         // per lane
-constexpr int kTile = kScatThreads * kScatItems;       // 4096 particles
-
-constexpr unsigned long long kFlagA = 1ull << 62;      // tile aggregate published
-constexpr unsigned long long kFlagP = 2ull << 62;      // inclusive prefix published
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
-
-__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v) {
-  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
-  r.store(v, cuda::memory_order_release);
-}
-__device__ __forceinline__ unsigned long long ld_acquire(unsigned long long *p) {
-  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
-  return r.load(cuda::memory_order_acquire);
-}
-__device__ __forceinline__ uint32_t ld_relaxed(uint32_t *p) {
-  cuda::atomic_ref<uint32_t, cuda::thread_scope_device> r(*p);
-  return r.load(cuda::memory_order_relaxed);
-}
-
-// Decoupled look-back: tile t publishes its aggregate, sums its predecessors
-// back to the first inclusive prefix (or the node's first tile), publishes its
-// own inclusive prefix and returns the exclusive one.  Every wait is bounded;
-// on expiry the error word is set and the tile unblocks its successors.
-__device__ unsigned long long lookback(unsigned long long *state, uint64_t t, uint64_t first,
-                                       unsigned long long agg, uint32_t *err) {
-  if (t == first) {
-    st_release(&state[t], kFlagP | agg);
-    return 0;
-  }
-  st_release(&state[t], kFlagA | agg);
-  unsigned long long excl = 0;
-  uint64_t pred = t - 1;
-  for (;;) {
-    unsigned long long s;
-    uint32_t spins = 0;
-    while (((s = ld_acquire(&state[pred])) >> 62) == 0) {
-      if (++spins > kSpinLimit || (ld_relaxed(err) & kErrTimeout)) {
-        atomicOr(err, kErrTimeout);
-        st_release(&state[t], kFlagP | ((excl + agg) & kValMask));
-        return excl;
-      }
-      __nanosleep(64);
-    }
-    excl += s & kValMask;
-    if ((s & ~kValMask) == kFlagP || pred == first) break;
-    --pred;
-  }
-  st_release(&state[t], kFlagP | ((excl + agg) & kValMask));
-  return excl;
-}
-
-template <typename C>
-__device__ __forceinline__ uint32_t ldc(const C *p) {
-  return (uint32_t)__ldcg(p);
-}
 
 // --------------------------------------------------------------------------
 // prep: first digit of every node; children bounds reset for the scatter
 // --------------------------------------------------------------------------
 __global__ void k_prep(LevelNode *nodes, LevelNode *children, uint64_t n, int level, uint32_t digit_bits,
-                       uint32_t root_hi) {
+                       uint32_t root_hi, uint32_t leaf_size) {
   const uint64_t count = 1ull << level;
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= count) return;
@@ -105,7 +44,12 @@ __global__ void k_prep(LevelNode *nodes, LevelNode *children, uint64_t n, int le
   node_range(n, level, j, off, cnt);
   const uint32_t k = uint32_t(cnt >> 1);
   const uint32_t B = bit_length(nd.hi - nd.lo);
-  if (B == 0) {
+  if (cnt <= leaf_size) {  // already a leaf: every code is below v, the node is copied as is
+    nd.width = 0;
+    nd.v = 0xffffffffu;
+    nd.less = uint32_t(cnt);
+    nd.tleft = 0;
+  } else if (B == 0) {
     nd.width = 0;
     nd.v = nd.lo;
     nd.less = 0;
@@ -127,25 +71,27 @@ __global__ void k_prep(LevelNode *nodes, LevelNode *children, uint64_t n, int le
 }
 
 // --------------------------------------------------------------------------
-// hist: each block walks a contiguous range of particles node by node
+// hist: each block walks a contiguous, 16-aligned range node by node
 // --------------------------------------------------------------------------
 template <typename C>
 __global__ void __launch_bounds__(kHistThreads) k_hist(const C *__restrict__ codes, const LevelNode *__restrict__ nodes,
                                                        uint32_t *__restrict__ hist, uint64_t n, int level,
                                                        uint32_t digit_bits) {
   extern __shared__ uint32_t sh[];
-  uint64_t start = n * blockIdx.x / gridDim.x;
-  const uint64_t end = n * (blockIdx.x + 1) / gridDim.x;
+  uint64_t start = ((n * blockIdx.x / gridDim.x) + 15) & ~15ull;
+  uint64_t end = blockIdx.x + 1 == gridDim.x ? n : (((n * (blockIdx.x + 1) / gridDim.x) + 15) & ~15ull);
+  if (end > n) end = n;
   if (start >= end) return;
-  // node holding `start`: the last j with off(j) <= start
-  uint64_t lo = 0, hi = (1ull << level) - 1;
+  uint64_t lo = 0, hi = (1ull << level) - 1;  // node holding `start`
   while (lo < hi) {
-    uint64_t mid = (lo + hi + 1) >> 1, off, cnt;
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    uint64_t off, cnt;
     node_range(n, level, mid, off, cnt);
     if (off <= start) lo = mid;
     else hi = mid - 1;
   }
   uint64_t j = lo;
+  constexpr uint32_t kVec = 16 / sizeof(C);  // codes per 16-byte load
   while (start < end) {
     uint64_t off, cnt;
     node_range(n, level, j, off, cnt);
@@ -153,12 +99,44 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const C *__restrict__ cod
     const LevelNode nd = nodes[j];
     if (nd.width) {
       const uint32_t nb = 1u << nd.width, mask = nb - 1;
+      const uint32_t lo_c = nd.lo, prefix = nd.prefix, width = nd.width;
+      const int shift = nd.shift;
       for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0;
       __syncthreads();
-      for (uint64_t e = start + threadIdx.x; e < seg_end; e += blockDim.x) {
-        const uint32_t rel = ldc(codes + e) - nd.lo;
-        const uint32_t hi_bits = rel >> nd.shift;
-        if ((hi_bits >> nd.width) == nd.prefix) atomicAdd(&sh[hi_bits & mask], 1u);
+      auto add = [&](uint32_t q) {
+        const uint32_t hb = (q - lo_c) >> shift;
+        if ((hb >> width) == prefix) atomicAdd(&sh[hb & mask], 1u);
+      };
+      auto add4 = [&](const uint4 &w) {
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (sizeof(C) == 2) {
+            add(x[c] & 0xffffu);
+            add(x[c] >> 16);
+          } else {
+            add(x[c]);
+          }
+        }
+      };
+      const uint64_t a0 = (start + kVec - 1) / kVec * kVec;  // first aligned index
+      const uint64_t a1 = seg_end / kVec * kVec;              // end of the aligned body
+      if (a0 >= a1) {
+        for (uint64_t e = start + threadIdx.x; e < seg_end; e += blockDim.x) add(__ldcg(codes + e));
+      } else {
+        for (uint64_t e = start + threadIdx.x; e < a0; e += blockDim.x) add(__ldcg(codes + e));
+        for (uint64_t e = a1 + threadIdx.x; e < seg_end; e += blockDim.x) add(__ldcg(codes + e));
+        const uint4 *v = reinterpret_cast<const uint4 *>(codes + a0);
+        const uint64_t nv = (a1 - a0) / kVec;
+        uint64_t i = threadIdx.x;
+        for (; i + 3 * blockDim.x < nv; i += 4 * blockDim.x) {
+          uint4 w[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w[u] = __ldcg(v + i + u * blockDim.x);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) add4(w[u]);
+        }
+        for (; i < nv; i += blockDim.x) add4(__ldcg(v + i));
       }
       __syncthreads();
       uint32_t *g = hist + (j << digit_bits);
@@ -262,164 +240,13 @@ __global__ void __launch_bounds__(kSelThreads) k_select(LevelNode *nodes, uint32
   }
 }
 
-// --------------------------------------------------------------------------
-// scatter: stable partition of each node into its two children
-// --------------------------------------------------------------------------
-template <typename C, bool IDX>
-struct ScatShared {
-  C q[3][kTile];
-  uint32_t idx[IDX ? kTile : 1];
-  uint32_t wless[kScatWarps], wtie[kScatWarps];
-  uint32_t wless_ex[kScatWarps], wtie_ex[kScatWarps];
-  uint64_t tile;
-  uint32_t left_before, right_before, left_tile, less_before, tie_before;
-};
-
-template <typename C, bool IDX>
-__global__ void __launch_bounds__(kScatThreads) k_scatter(LevelLaunch a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  ScatShared<C, IDX> &S = *reinterpret_cast<ScatShared<C, IDX> *>(smraw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int axis = a.level % 3, nxt = (a.level + 1) % 3;
-  if (threadIdx.x == 0) S.tile = atomicAdd(a.ticket, 1u);
-  __syncthreads();
-  const uint64_t t = S.tile;
-  const uint64_t T = a.tiles_per_node;
-  const uint64_t j = t / T, i = t % T;
-  uint64_t off, cnt;
-  node_range(a.n, a.level, j, off, cnt);
-  const uint64_t k = cnt >> 1;
-  const uint64_t tb = off + (cnt * i) / T;
-  const uint64_t te = off + (cnt * (i + 1)) / T;
-  const uint32_t sz = uint32_t(te - tb);
-  const LevelNode nd = a.nodes[j];
-  const uint32_t v = nd.v, tl = nd.tleft;
-  const C *src0 = static_cast<const C *>(a.src[0]);
-  const C *src1 = static_cast<const C *>(a.src[1]);
-  const C *src2 = static_cast<const C *>(a.src[2]);
-
-  uint32_t q0[kScatItems], q1[kScatItems], q2[kScatItems], id[IDX ? kScatItems : 1];
-  uint32_t wl = 0, wt = 0;
-#pragma unroll
-  for (int e = 0; e < kScatItems; ++e) {
-    const uint32_t p = uint32_t(warp) * (32 * kScatItems) + uint32_t(e) * 32 + lane;
-    const bool valid = p < sz;
-    q0[e] = valid ? ldc(src0 + tb + p) : 0;
-    q1[e] = valid ? ldc(src1 + tb + p) : 0;
-    q2[e] = valid ? ldc(src2 + tb + p) : 0;
-    if (IDX) id[e] = valid ? __ldcg(a.src_idx + tb + p) : 0;
-    const uint32_t qa = axis == 0 ? q0[e] : (axis == 1 ? q1[e] : q2[e]);
-    wl += __popc(__ballot_sync(0xffffffffu, valid && qa < v));
-    wt += __popc(__ballot_sync(0xffffffffu, valid && qa == v));
-  }
-  if (lane == 0) {
-    S.wless[warp] = wl;
-    S.wtie[warp] = wt;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t sl = 0, st = 0;
-    for (int w = 0; w < kScatWarps; ++w) {
-      S.wless_ex[w] = sl;
-      S.wtie_ex[w] = st;
-      sl += S.wless[w];
-      st += S.wtie[w];
-    }
-    const unsigned long long agg = ((unsigned long long)sl << 31) | st;
-    const unsigned long long ex = lookback(a.tile_state, t, j * T, agg, a.err);
-    const uint32_t less_before = uint32_t(ex >> 31), tie_before = uint32_t(ex & 0x7fffffffu);
-    const uint32_t lb = less_before + min(tie_before, tl);
-    const uint32_t lincl = less_before + sl + min(tie_before + st, tl);
-    S.less_before = less_before;
-    S.tie_before = tie_before;
-    S.left_before = lb;
-    S.left_tile = lincl - lb;
-    S.right_before = uint32_t(tb - off) - lb;
-  }
-  __syncthreads();
-  const uint32_t less_before = S.less_before, tie_before = S.tie_before;
-  const uint32_t left_before = S.left_before, left_tile = S.left_tile, right_before = S.right_before;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t run_l = S.wless_ex[warp], run_t = S.wtie_ex[warp];
-  uint32_t cmin0 = 0xffffffffu, cmax0 = 0, cmin1 = 0xffffffffu, cmax1 = 0;
-#pragma unroll
-  for (int e = 0; e < kScatItems; ++e) {
-    const uint32_t p = uint32_t(warp) * (32 * kScatItems) + uint32_t(e) * 32 + lane;
-    const bool valid = p < sz;
-    const uint32_t qa = axis == 0 ? q0[e] : (axis == 1 ? q1[e] : q2[e]);
-    const bool isless = valid && qa < v, istie = valid && qa == v;
-    const uint32_t bl = __ballot_sync(0xffffffffu, isless), bt = __ballot_sync(0xffffffffu, istie);
-    const uint32_t less_ex = run_l + __popc(bl & lt_mask);
-    const uint32_t tie_ex = run_t + __popc(bt & lt_mask);
-    run_l += __popc(bl);
-    run_t += __popc(bt);
-    if (valid) {
-      const uint32_t trank = tie_before + tie_ex;
-      const bool left = isless || (istie && trank < tl);
-      const uint32_t glrank = less_before + less_ex + min(trank, tl);
-      uint32_t local;
-      if (left) {
-        local = glrank - left_before;
-      } else {
-        const uint32_t grrank = uint32_t(tb + p - off) - glrank;
-        local = left_tile + (grrank - right_before);
-      }
-      if (local < sz) {
-        S.q[0][local] = (C)q0[e];
-        S.q[1][local] = (C)q1[e];
-        S.q[2][local] = (C)q2[e];
-        if (IDX) S.idx[local] = id[e];
-      } else {
-        atomicOr(a.err, kErrInternal);
-      }
-      const uint32_t qn = nxt == 0 ? q0[e] : (nxt == 1 ? q1[e] : q2[e]);
-      if (left) {
-        cmin0 = min(cmin0, qn);
-        cmax0 = max(cmax0, qn);
-      } else {
-        cmin1 = min(cmin1, qn);
-        cmax1 = max(cmax1, qn);
-      }
-    }
-  }
-  cmin0 = __reduce_min_sync(0xffffffffu, cmin0);
-  cmax0 = __reduce_max_sync(0xffffffffu, cmax0);
-  cmin1 = __reduce_min_sync(0xffffffffu, cmin1);
-  cmax1 = __reduce_max_sync(0xffffffffu, cmax1);
-  if (lane == 0 && a.children) {
-    if (cmin0 <= cmax0) {
-      atomicMin(&a.children[2 * j].lo, cmin0);
-      atomicMax(&a.children[2 * j].hi, cmax0);
-    }
-    if (cmin1 <= cmax1) {
-      atomicMin(&a.children[2 * j + 1].lo, cmin1);
-      atomicMax(&a.children[2 * j + 1].hi, cmax1);
-    }
-  }
-  __syncthreads();
-  C *d0 = static_cast<C *>(a.dst[0]);
-  C *d1 = static_cast<C *>(a.dst[1]);
-  C *d2 = static_cast<C *>(a.dst[2]);
-  for (uint32_t p = threadIdx.x; p < sz; p += kScatThreads) {
-    const uint64_t dst = p < left_tile ? off + left_before + p : off + k + right_before + (p - left_tile);
-    if (dst >= off + cnt) {
-      atomicOr(a.err, kErrInternal);
-      continue;
-    }
-    __stcg(d0 + dst, S.q[0][p]);
-    __stcg(d1 + dst, S.q[1][p]);
-    __stcg(d2 + dst, S.q[2][p]);
-    if (IDX) __stcg(a.dst_idx + dst, S.idx[p]);
-  }
-}
-
-template <typename C, bool IDX>
+template <typename C>
 cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   const uint64_t count = 1ull << a.level;
   {
     TraceScope ts("k_prep", st);
     k_prep<<<unsigned((count + 255) / 256), 256, 0, st>>>(a.nodes, a.children, a.n, a.level, a.digit_bits,
-                                                          a.root_hi);
+                                                          a.root_hi, a.leaf_size);
   }
   const int axis = a.level % 3;
   const C *codes = static_cast<const C *>(a.src[axis]);
@@ -432,23 +259,13 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
     TraceScope ts("k_select", st);
     k_select<<<unsigned(count), kSelThreads, 0, st>>>(a.nodes, a.hist, a.n, a.level, a.digit_bits);
   }
-  const size_t ssm = sizeof(ScatShared<C, IDX>);
-  cudaError_t e = cudaFuncSetAttribute(k_scatter<C, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ssm));
-  if (e != cudaSuccess) return e;
-  const uint64_t tiles = count * a.tiles_per_node;
-  TraceScope ts("k_scatter", st);
-  k_scatter<C, IDX><<<unsigned(tiles), kScatThreads, ssm, st>>>(a);
-  return cudaGetLastError();
+  return launch_scatter(a, st);
 }
 
 }  // namespace
 
-uint32_t scatter_tile() { return kTile; }
-
 cudaError_t launch_level(const LevelLaunch &a, cudaStream_t st) {
-  if (a.code_bytes == 2)
-    return a.with_idx ? level_dispatch<uint16_t, true>(a, st) : level_dispatch<uint16_t, false>(a, st);
-  return a.with_idx ? level_dispatch<uint32_t, true>(a, st) : level_dispatch<uint32_t, false>(a, st);
+  return a.code_bytes == 2 ? level_dispatch<uint16_t>(a, st) : level_dispatch<uint32_t>(a, st);
 }
 
 }  // namespace pcx

@@ -10,8 +10,6 @@
 
 namespace pcx {
 
-uint32_t scatter_tile();
-
 int device_sm_count() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -66,33 +64,44 @@ struct Plan {
   uint32_t r = PC_DEFAULT_LEAF_SIZE;
   bool idx = false;
   uint64_t num_leaves = 0;
-  int max_levels = 0;  // global levels for the smallest subtree capacity
+  int levels = 0;  // levels that split nodes: while the largest node exceeds r
   // workspace offsets
   uint64_t off_partial = 0, off_range = 0, off_codes_a = 0, off_codes_b = 0, off_idx_a = 0, off_idx_b = 0;
-  uint64_t off_nodes = 0, off_leafinfo = 0;
+  uint64_t off_nodes = 0, off_leafrec = 0, off_words = 0;
   uint64_t off_zero = 0, zero_bytes = 0;  // zeroed at every call:
-  uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_states = 0, off_err = 0, off_total = 0;
+  uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_err = 0, off_total = 0;
   uint64_t total = 0;
   int range_blocks = 0;
 };
 
-int global_levels(uint64_t n, uint32_t cap) {
+// Levels of the median tree that split nodes: node sizes at depth l are
+// floor(n / 2^l) or ceil(n / 2^l), and a node of at most r particles is a leaf.
+int split_levels(uint64_t n, uint32_t r) {
   int l = 0;
-  while (((n + (1ull << l) - 1) >> l) > cap) ++l;
+  while (((n + (1ull << l) - 1) >> l) > r) ++l;
   return l;
 }
 
+// Radix digit of the per-node histograms at one level (2^level nodes): wide
+// at the top, narrower below so that a level's bins stay within 2^22.
 uint32_t digit_bits_for(int level) {
   int d = 22 - level;
   if (d > 13) d = 13;
-  if (d < 8) d = 8;
+  if (d < 6) d = 6;
   return uint32_t(d);
 }
 
-uint64_t tiles_per_node(uint64_t n, int level) {
+// Tiles per node at one level: node sizes are floor(n / 2^level) or one more.
+uint64_t tiles_per_node(uint64_t n, int level, uint32_t tile) {
   const uint64_t big = (n >> level) + 1;
-  const uint64_t t = (big + scatter_tile() - 1) / scatter_tile();
+  const uint64_t t = (big + tile - 1) / tile;
   return t ? t : 1;
+}
+
+// smallest scatter tile over code widths: sizes the look-back state for any data
+uint32_t min_scatter_tile(bool idx) {
+  const uint32_t a = scatter_tile(2, idx), b = scatter_tile(4, idx);
+  return a < b ? a : b;
 }
 
 int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_count, Plan &p) {
@@ -109,8 +118,7 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   p.r = r;
   p.idx = idx;
   p.num_leaves = leaves_for(n, r);
-  const uint32_t cap_min = subtree_capacity(4, idx);
-  p.max_levels = global_levels(n, cap_min);
+  p.levels = split_levels(n, r);
   p.range_blocks = 4 * (sm_count > 0 ? sm_count : 148);
   if (p.range_blocks > 1024) p.range_blocks = 1024;
 
@@ -130,27 +138,27 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
     o = align_up(o + 4 * n);
   }
   uint64_t node_count = 0;
-  for (int l = 0; l <= p.max_levels; ++l) node_count += 1ull << l;
+  for (int l = 0; l <= p.levels; ++l) node_count += 1ull << l;
   p.off_nodes = o;
   o = align_up(o + node_count * sizeof(LevelNode));
-  p.off_leafinfo = o;
-  o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafInfo));
+  p.off_leafrec = o;
+  o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafRec));
+  p.off_words = o;
+  o = align_up(o + 8);
   // zeroed region
   p.off_zero = o;
   uint64_t hist_bins = 0, tiles = 0;
-  for (int l = 0; l < p.max_levels; ++l) {
+  for (int l = 0; l < p.levels; ++l) {
     const uint64_t b = (1ull << l) << digit_bits_for(l);
     if (b > hist_bins) hist_bins = b;
-    tiles += (1ull << l) * tiles_per_node(n, l);
+    tiles += (1ull << l) * tiles_per_node(n, l, min_scatter_tile(idx));
   }
   p.off_hist = o;
   o = align_up(o + 4 * (hist_bins ? hist_bins : 1));
   p.off_tiles = o;
   o = align_up(o + 8 * (tiles ? tiles : 1));
   p.off_tickets = o;
-  o = align_up(o + 4 * (p.max_levels + 2));
-  p.off_states = o;
-  o = align_up(o + 8 * (1ull << p.max_levels));
+  o = align_up(o + 4 * (p.levels + 1));
   p.off_err = o;
   o = align_up(o + 4);
   p.off_total = o;
@@ -219,8 +227,6 @@ int lattice_from_range(const RangeResult &rr, int dtype, int mode, double eb, La
   }
   return PC_OK;
 }
-
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? PC_OK : PC_ERR_CUDA; }
 
 #define PC_TRY(x)                        \
   do {                                   \
@@ -311,9 +317,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     qa.blocks = 8 * device_sm_count();
     PC_TRY(launch_quantize(qa, st));
 
-    // a3: global k-d levels
-    const uint32_t cap = subtree_capacity(cb, p.idx);
-    const int levels = global_levels(n, cap);
+    // a3: the k-d levels, down to the leaves
+    const int levels = p.levels;
     LevelNode *nodes = reinterpret_cast<LevelNode *>(ws + p.off_nodes);
     uint64_t node_base = 0, tile_base = 0;
     void **src = codes_a, **dst = codes_b;
@@ -324,10 +329,11 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.level = l;
       la.code_bytes = cb;
       la.with_idx = p.idx;
+      la.leaf_size = p.r;
       la.digit_bits = digit_bits_for(l);
       const uint32_t bits = bit_length(L.qmax[l % 3]);
       la.passes = (bits + la.digit_bits - 1) / la.digit_bits;
-      la.tiles_per_node = uint32_t(tiles_per_node(n, l));
+      la.tiles_per_node = uint32_t(tiles_per_node(n, l, scatter_tile(cb, p.idx)));
       la.root_hi = L.qmax[0];
       for (int d = 0; d < 3; ++d) {
         la.src[d] = src[d];
@@ -353,27 +359,21 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       idst = ti;
     }
 
-    // a3-a5: subtrees in shared memory, bit boxes, payload
-    const uint64_t small = n >> levels;
-    SubtreeLaunch sa = {};
-    sa.n = n;
-    sa.root_level = levels;
-    sa.code_bytes = cb;
-    sa.with_idx = p.idx;
-    sa.leaf_size = p.r;
-    sa.leaves_small = leaves_for(small, p.r);
-    sa.leaves_big = leaves_for(small + 1, p.r);
-    for (int d = 0; d < 3; ++d) sa.src[d] = src[d];
-    sa.src_idx = isrc;
-    sa.out = static_cast<uint8_t *>(out);
-    sa.num_leaves = p.num_leaves;
-    sa.perm = perm;
-    sa.leaf_info = reinterpret_cast<LeafInfo *>(ws + p.off_leafinfo);
-    sa.state = reinterpret_cast<unsigned long long *>(ws + p.off_states);
-    sa.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + p.max_levels + 1;
-    sa.err = err;
-    PC_TRY(launch_subtree(sa, st));
-    hl.last_state = sa.state + ((1ull << levels) - 1);
+    // a4-a5: bit boxes, payload offsets, packing
+    LeafLaunch lf = {};
+    lf.n = n;
+    lf.split_level = levels - 1;
+    lf.code_bytes = cb;
+    lf.leaf_size = p.r;
+    lf.num_leaves = p.num_leaves;
+    for (int d = 0; d < 3; ++d) lf.codes[d] = src[d];
+    lf.idx = isrc;
+    lf.out = static_cast<uint8_t *>(out);
+    lf.perm = perm;
+    lf.recs = reinterpret_cast<LeafRec *>(ws + p.off_leafrec);
+    lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
+    PC_TRY(launch_leaves(lf, st));
+    hl.total_words = lf.total_words;
   }
   hl.eps = L.eps;
   hl.s = L.s;
@@ -392,6 +392,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
   *out_size = back.total;
   return PC_OK;
 }
+
+// error word, then one u32 per decode chunk (its first particle's leaf)
+uint64_t decompress_ws_bytes(uint64_t n) { return kAlign + align_up(4 * decode_chunks(n)); }
 
 int parse_header(const uint8_t *h, uint64_t avail, pc_info *info) {
   if (avail < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
@@ -428,7 +431,6 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   if (!stream_data || !workspace) return PC_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(stream_data) % 16 || reinterpret_cast<uintptr_t>(workspace) % kAlign)
     return PC_ERR_ARG;
-  if (workspace_bytes < kAlign) return PC_ERR_CAPACITY;
   if (stream_bytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
   uint8_t h[PC_HEADER_BYTES];
   PC_TRY(cudaMemcpyAsync(h, stream_data, PC_HEADER_BYTES, cudaMemcpyDeviceToHost, st));
@@ -441,6 +443,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   if (out_capacity_bytes < 3 * esz * I.n) return PC_ERR_CAPACITY;
   if (I.n == 0) return PC_OK;
   if (!out_positions || reinterpret_cast<uintptr_t>(out_positions) % esz) return PC_ERR_ARG;
+  if (workspace_bytes < decompress_ws_bytes(I.n)) return PC_ERR_CAPACITY;
   uint32_t *err = static_cast<uint32_t *>(workspace);
   PC_TRY(cudaMemsetAsync(err, 0, 4, st));
   DecodeLaunch da = {};
@@ -462,6 +465,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   da.out = out_positions;
   da.vec = reinterpret_cast<uintptr_t>(out_positions) % 16 == 0;
   da.err = err;
+  da.chunk_leaf = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(workspace) + kAlign);
   PC_TRY(launch_decode(da, st));
   uint32_t e = 0;
   PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
@@ -518,9 +522,9 @@ int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info
   return parse_header(static_cast<const uint8_t *>(host_header), header_bytes, info);
 }
 
-int pc_decompress_workspace_size(uint64_t *out_bytes) {
+int pc_decompress_workspace_size(uint64_t n, uint64_t *out_bytes) {
   if (!out_bytes) return PC_ERR_ARG;
-  *out_bytes = kAlign;
+  *out_bytes = decompress_ws_bytes(n);
   return PC_OK;
 }
 
@@ -573,7 +577,7 @@ int pc_compress_host(const void *host_positions, uint64_t n, int dtype, int eb_m
 int pc_decompress_host_workspace_size(uint64_t n, int dtype, uint64_t stream_bytes, uint64_t *out_bytes) {
   if (!out_bytes || (dtype != PC_F32 && dtype != PC_F64)) return PC_ERR_ARG;
   const uint64_t esz = dtype == PC_F32 ? 4 : 8;
-  *out_bytes = align_up(stream_bytes) + align_up(3 * esz * n) + kAlign;
+  *out_bytes = align_up(stream_bytes) + align_up(3 * esz * n) + decompress_ws_bytes(n);
   return PC_OK;
 }
 
@@ -596,7 +600,7 @@ int pc_decompress_host(const void *host_stream, uint64_t stream_bytes, void *hos
   uint8_t *dpos = ws + align_up(I.total_bytes);
   uint8_t *rest = dpos + align_up(3 * esz * I.n);
   PC_TRY(cudaMemcpyAsync(dst_stream, host_stream, I.total_bytes, cudaMemcpyHostToDevice, st));
-  rc = decompress_impl(dst_stream, I.total_bytes, dpos, 3 * esz * I.n, rest, kAlign, st);
+  rc = decompress_impl(dst_stream, I.total_bytes, dpos, 3 * esz * I.n, rest, decompress_ws_bytes(I.n), st);
   if (rc) return rc;
   if (I.n) PC_TRY(cudaMemcpyAsync(host_positions, dpos, 3 * esz * I.n, cudaMemcpyDeviceToHost, st));
   PC_TRY(cudaStreamSynchronize(st));

@@ -50,16 +50,87 @@ struct LevelNode {
 };
 
 // Per-leaf facts kept between the bit-box pass and the packing pass.
-struct LeafInfo {
-  uint32_t off;      // first particle, relative to the subtree root
-  uint32_t cnt;      // particles
-  uint32_t centre;   // position of the centre inside the leaf
-  uint32_t words;    // payload words of the leaf
-  uint32_t lword;    // first payload word, relative to the subtree
-  int32_t qref[3];
-  uint32_t m;        // m_x | m_y << 8 | m_z << 16
-  uint32_t pad;
+struct LeafRec {
+  uint32_t off;       // first particle of the leaf (leaf-ordered arrays, = first decoded particle)
+  uint32_t cnt;       // particles
+  uint32_t centre;    // position of the bit-box centre inside the leaf
+  uint32_t m;         // m_x | m_y << 8 | m_z << 16
+  int32_t qref[3];    // centre code
+  uint32_t words;     // payload words of the leaf
+  uint64_t word_off;  // first payload word
+  uint64_t pad;
 };
+
+// Look-back state words: flag in the top two bits, value below.
+constexpr unsigned long long kFlagA = 1ull << 62;  // aggregate published
+constexpr unsigned long long kFlagP = 2ull << 62;  // inclusive prefix published
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Warp-wide decoupled look-back, called by all 32 lanes of one warp.  Item t
+// publishes its aggregate, sums its predecessors 32 at a time back to the
+// nearest published inclusive prefix (items before `first` count as an empty
+// prefix), publishes its own inclusive prefix and returns the exclusive one.
+// Every wait is bounded: on expiry the error word gets kErrTimeout and the item
+// publishes what it has so that its successors do not wait.
+__device__ __forceinline__ unsigned long long warp_lookback(unsigned long long *state, int64_t t, int64_t first,
+                                                            unsigned long long agg, uint32_t *err) {
+  const int lane = threadIdx.x & 31;
+  if (t == first) {
+    if (lane == 0) st_release(&state[t], kFlagP | agg);
+    return 0;
+  }
+  if (lane == 0) st_release(&state[t], kFlagA | agg);
+  unsigned long long excl = 0;
+  int64_t end = t - 1;
+  for (;;) {
+    const int64_t pred = end - lane;
+    const bool inside = pred >= first;
+    unsigned long long s = kFlagP;
+    uint32_t spins = 0;
+    bool timed_out = false;
+    for (;;) {
+      if (inside) s = ld_acquire(&state[pred]);
+      if (__all_sync(0xffffffffu, (s >> 62) != 0)) break;
+      if (++spins > kSpinLimit || (ld_relaxed(err) & kErrTimeout)) {
+        timed_out = true;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (__any_sync(0xffffffffu, timed_out)) {
+      if (lane == 0) {
+        atomicOr(err, kErrTimeout);
+        st_release(&state[t], kFlagP | ((excl + agg) & kValMask));
+      }
+      return excl;
+    }
+    const uint32_t pmask = __ballot_sync(0xffffffffu, (s & ~kValMask) == kFlagP);
+    const int cut = pmask ? (__ffs(pmask) - 1) : 31;
+    unsigned long long v = lane <= cut ? (s & kValMask) : 0ull;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (pmask) break;
+    end -= 32;
+  }
+  if (lane == 0) st_release(&state[t], kFlagP | ((excl + agg) & kValMask));
+  return excl;
+}
+#endif
 
 // Offset and size of node j at depth `level` of the median tree over n
 // particles: the left child takes floor(c/2), the right ceil(c/2) (Sec. 4.1).
@@ -137,6 +208,7 @@ struct LevelLaunch {
   int level;
   int code_bytes;
   bool with_idx;
+  uint32_t leaf_size;     // nodes of at most this many particles are leaves (copied unchanged)
   uint32_t digit_bits;
   uint32_t passes;
   uint32_t tiles_per_node;
@@ -154,27 +226,23 @@ struct LevelLaunch {
   int hist_blocks;
 };
 cudaError_t launch_level(const LevelLaunch &a, cudaStream_t st);
+cudaError_t launch_scatter(const LevelLaunch &a, cudaStream_t st);
+uint32_t scatter_tile(int code_bytes, bool with_idx);  // largest tile of one scatter CTA
 
-struct SubtreeLaunch {
+struct LeafLaunch {
   uint64_t n;
-  int root_level;           // depth of the subtree roots
+  int split_level;          // last level that split nodes (-1: the root is the only leaf)
   int code_bytes;
-  bool with_idx;
   uint32_t leaf_size;
-  uint64_t leaves_small;    // leaves under a root of floor(n / 2^root_level) particles
-  uint64_t leaves_big;      // leaves under a root of one more particle
-  const void *src[3];
-  const uint32_t *src_idx;
-  uint8_t *out;             // stream base
   uint64_t num_leaves;
+  const void *codes[3];     // leaf-ordered codes
+  const uint32_t *idx;      // leaf-ordered input indices (optional)
+  uint8_t *out;             // stream base
   uint32_t *perm;           // optional
-  LeafInfo *leaf_info;      // [num_leaves]
-  unsigned long long *state;  // [2^root_level]
-  uint32_t *ticket;
-  uint32_t *err;
+  LeafRec *recs;            // [num_leaves]
+  uint64_t *total_words;    // device slot: payload words of the stream
 };
-cudaError_t launch_subtree(const SubtreeLaunch &a, cudaStream_t st);
-uint32_t subtree_capacity(int code_bytes, bool with_idx);
+cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st);
 
 struct HeaderLaunch {
   uint8_t *out;
@@ -183,8 +251,8 @@ struct HeaderLaunch {
   double eb, eps, s, o[3];
   uint64_t num_leaves;
   uint32_t leaf_size;
-  const unsigned long long *last_state;  // null when there are no leaves
-  uint64_t *total_bytes;                 // device slot read back by the host
+  const uint64_t *total_words;  // null when there are no leaves
+  uint64_t *total_bytes;        // device slot read back by the host
   uint32_t *err;
 };
 cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st);
@@ -202,8 +270,10 @@ struct DecodeLaunch {
   void *out;
   bool vec;
   uint32_t *err;
+  uint32_t *chunk_leaf;  // [decode_chunks(n)]: leaf holding each chunk's first particle
 };
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
+uint64_t decode_chunks(uint64_t n);
 
 int device_sm_count();
 

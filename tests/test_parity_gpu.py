@@ -184,7 +184,7 @@ def test_corrupt_streams_are_rejected(pc, oracle_mod):
     pos = synth.cosmology(50_000, seed=21)
     stream, _ = oracle_mod.compress(pos, oracle_mod.REL, 1e-3, leaf_size=1000)
     dev = torch.device("cuda:0")
-    ws = torch.empty(pc.pc_decompress_workspace_size(), dtype=torch.uint8, device=dev)
+    ws = torch.empty(pc.pc_decompress_workspace_size(50_000), dtype=torch.uint8, device=dev)
     out = torch.empty((50_000, 3), dtype=torch.float32, device=dev)
 
     def attempt(buf, nbytes=None):
