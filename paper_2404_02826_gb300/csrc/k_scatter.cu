@@ -11,13 +11,14 @@
 //               Memory Accelerator copies the next tile's codes into the other
 //               half of a shared-memory double buffer (cp.async.bulk completing
 //               on an mbarrier).  Per tile: one thread per 16 consecutive
-//               particles forms bit masks of "code < v" and "code == v" and a
-//               block scan gives per-group prefixes; then consecutive threads
-//               take consecutive particles, compute their rank from the masks
-//               and write them to the left or right run, so stores to each run
-//               are contiguous across a warp.  The children's code bounds on
-//               the next axis are reduced per CTA and folded in with an atomic
-//               only when they improve the stored bound.
+//               particles forms bit masks of "code < v" and "code == v"; after
+//               a block scan of their counts the same thread walks its group
+//               and records each particle's place in the tile's left or right
+//               run as a 16-bit index; then consecutive threads take
+//               consecutive particles and store them, so stores to each run are
+//               contiguous across a warp.  The children's code bounds on the
+//               next axis are reduced per CTA and folded in with an atomic only
+//               when they improve the stored bound.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -34,7 +35,14 @@ struct Cfg {
   static constexpr int kBytesPer = 3 * int(sizeof(C)) + (IDX ? 4 : 0);
   static constexpr int kWin = kBytesPer <= 6 ? 8192 : 4096;  // window of particles held per buffer
   static constexpr int kTile = kWin - 16;                      // largest tile: an aligned window covers it
-  static constexpr int kGroups = kWin / 16;
+};
+
+// Tile i of node j covers positions [i*ts, (i+1)*ts) of the node, clipped to
+// its size, with ts = ceil(cnt / T).  Everything fits 32 bits (n < 2^31), and
+// the host picks T so that ts never exceeds the largest tile.  Computed once
+// per tile by one thread: 64-bit division would run on the FP64 pipe.
+struct TileGeom {
+  uint32_t j, off, cnt, tb, te;
 };
 
 template <typename C, bool IDX>
@@ -42,14 +50,14 @@ struct Smem {
   using F = Cfg<C, IDX>;
   C in[2][3][F::kWin];
   uint32_t idx[IDX ? 2 : 1][IDX ? F::kWin : 4];
-  uint32_t gmask[F::kGroups];  // less mask | tie mask << 16 of each 16-particle group
-  uint32_t gpre[F::kGroups];   // exclusive (less << 16 | tie) counts of the groups before it
+  uint16_t dst[F::kWin];       // tile-local destination of each window slot (0xffff: none)
   uint32_t scan[33];
   uint32_t red[4][kWarps];
   unsigned long long bar[2];
   unsigned long long pre[2];  // (less << 31 | tie) of the node's tiles before this one
   uint32_t tile[2];
   uint32_t v[2], tleft[2];
+  TileGeom geo[2];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -121,32 +129,62 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *warp_t
   return r;
 }
 
-struct TileGeom {
-  uint64_t j, off, cnt, tb, te, w0;
+// 16 consecutive codes starting at a 16-aligned slot, read with 16-byte loads.
+template <typename C>
+struct Group16;
+template <>
+struct Group16<uint16_t> {
+  uint32_t w[8];  // two codes per word, element 2i in the low half
+  __device__ __forceinline__ void load(const uint16_t *p) {
+    const uint4 a = reinterpret_cast<const uint4 *>(p)[0], b = reinterpret_cast<const uint4 *>(p)[1];
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+  }
+  __device__ __forceinline__ uint32_t get(int j) const { return (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu); }
 };
-__device__ __forceinline__ TileGeom tile_geom(const LevelLaunch &a, uint64_t t) {
+template <>
+struct Group16<uint32_t> {
+  uint32_t w[16];
+  __device__ __forceinline__ void load(const uint32_t *p) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint4 a = reinterpret_cast<const uint4 *>(p)[i];
+      w[4 * i] = a.x; w[4 * i + 1] = a.y; w[4 * i + 2] = a.z; w[4 * i + 3] = a.w;
+    }
+  }
+  __device__ __forceinline__ uint32_t get(int j) const { return w[j]; }
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const LevelLaunch &a, uint32_t t) {
   TileGeom g;
-  const uint64_t T = a.tiles_per_node;
+  const uint32_t T = a.tiles_per_node;
   g.j = t / T;
-  const uint64_t i = t % T;
-  node_range(a.n, a.level, g.j, g.off, g.cnt);
-  g.tb = g.off + (g.cnt * i) / T;
-  g.te = g.off + (g.cnt * (i + 1)) / T;
-  g.w0 = g.tb & ~uint64_t(15);
+  const uint32_t i = t - g.j * T;
+  uint64_t off, cnt;
+  node_range(a.n, a.level, g.j, off, cnt);
+  g.off = uint32_t(off);
+  g.cnt = uint32_t(cnt);
+  const uint32_t ts = (g.cnt + T - 1) / T;
+  g.tb = g.off + min(i * ts, g.cnt);
+  g.te = g.off + min(i * ts + ts, g.cnt);
   return g;
 }
 
 // Thread 0: copies the window of tile t into buffer b and reads its node and
 // its prefix counts (the loads complete while the current tile is processed).
 template <typename C, bool IDX>
-__device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S, uint64_t t, int b, uint32_t &v,
+__device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S, uint32_t t, int b, uint32_t &v,
                                            uint32_t &tl, unsigned long long &pre) {
   const TileGeom g = tile_geom(a, t);
-  const uint32_t nwin = uint32_t((g.te - g.w0 + 15) & ~uint64_t(15));
+  S.geo[b] = g;
+  const uint32_t w0 = g.tb & ~15u;
+  const uint32_t nwin = (g.te - w0 + 15) & ~15u;
   const uint32_t bytes = nwin * uint32_t(sizeof(C));
   mbar_expect_tx(&S.bar[b], 3 * bytes + (IDX ? 4 * nwin : 0));
-  for (int d = 0; d < 3; ++d) bulk_g2s(S.in[b][d], static_cast<const C *>(a.src[d]) + g.w0, bytes, &S.bar[b]);
-  if (IDX) bulk_g2s(S.idx[b], a.src_idx + g.w0, 4 * nwin, &S.bar[b]);
+  if (nwin) {
+    for (int d = 0; d < 3; ++d) bulk_g2s(S.in[b][d], static_cast<const C *>(a.src[d]) + w0, bytes, &S.bar[b]);
+    if (IDX) bulk_g2s(S.idx[b], a.src_idx + w0, 4 * nwin, &S.bar[b]);
+  }
   v = a.nodes[g.j].v;
   tl = a.nodes[g.j].tleft;
   pre = a.tile_state[t];
@@ -196,74 +234,95 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t ti
     if (b) phase1 ^= 1u;
     else phase0 ^= 1u;
 
-    const TileGeom g = tile_geom(a, t);
-    const uint32_t k = uint32_t(g.cnt >> 1);
-    const uint32_t sz = uint32_t(g.te - g.tb);
-    const uint32_t lead = uint32_t(g.tb - g.w0);
+    const TileGeom g = S.geo[b];
+    const uint32_t k = g.cnt >> 1;
+    const uint32_t sz = g.te - g.tb;
+    const uint32_t lead = g.tb & 15u;
     const uint32_t ngroups = (lead + sz + 15) >> 4;
     const uint32_t v = S.v[b], tl = S.tleft[b];
     const unsigned long long pre = S.pre[b];
     const uint32_t less_before = uint32_t(pre >> 31), tie_before = uint32_t(pre & 0x7fffffffu);
-    const C *qa = S.in[b][axis];
+    const uint32_t node_pos0 = g.tb - g.off;  // position of the tile's first particle in the node
+    C *n0 = d0 + g.off, *n1 = d1 + g.off, *n2 = d2 + g.off;
+    uint32_t *ni = IDX ? a.dst_idx + g.off : nullptr;
 
-    // 1. classify: masks of each 16-particle group and their prefixes
-    uint32_t lm = 0, tm = 0;
-    if (threadIdx.x < ngroups) {
-      const uint32_t base = threadIdx.x * 16;
+    // 1. each thread classifies its 16-particle group (registers only)
+    const bool mine = threadIdx.x < ngroups;
+    const uint32_t base = threadIdx.x * 16;
+    const C *qa = S.in[b][axis];
+    const C *qn = S.in[b][nxt];
+    uint32_t lm = 0, tm = 0, vm = 0;
+    if (mine) {
+      Group16<C> ga;  // 16-byte loads: scalar loads 16 particles apart would hit the same bank
+      ga.load(qa + base);
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) {
         const uint32_t wp = base + jj;
-        const uint32_t q = qa[wp];
+        const uint32_t q = ga.get(jj);
         const bool valid = wp >= lead && wp < lead + sz;
+        vm |= uint32_t(valid) << jj;
         lm |= uint32_t(valid && q < v) << jj;
         tm |= uint32_t(valid && q == v) << jj;
       }
     }
     uint32_t total;
     const uint32_t ex = block_excl_scan((uint32_t(__popc(lm)) << 16) | uint32_t(__popc(tm)), S.scan, total);
-    (void)total;
-    if (threadIdx.x < ngroups) {
-      S.gmask[threadIdx.x] = lm | (tm << 16);
-      S.gpre[threadIdx.x] = ex;
-    }
-    __syncthreads();  // group masks and prefixes visible to every thread
-    // 2. scatter, consecutive threads on consecutive particles
+    // the tile's particles split into a left run [0, left_tile) and a right run [left_tile, sz)
+    const uint32_t left_before = less_before + min(tie_before, tl);
+    const uint32_t left_tile = less_before + (total >> 16) + min(tie_before + (total & 0xffffu), tl) - left_before;
+    const uint32_t right_before = node_pos0 - left_before;
+    // 2. tile-local destination of every particle of the group, and the children bounds
     uint32_t cmin0 = 0xffffffffu, cmax0 = 0, cmin1 = 0xffffffffu, cmax1 = 0;
-    const uint32_t node_pos0 = uint32_t(g.tb - g.off);  // position of the tile's first particle in the node
-    C *n0 = d0 + g.off, *n1 = d1 + g.off, *n2 = d2 + g.off;
-    uint32_t *ni = IDX ? a.dst_idx + g.off : nullptr;
-    const uint32_t cnt = uint32_t(g.cnt);
+    if (mine) {
+      uint32_t run_l = less_before + (ex >> 16), run_t = tie_before + (ex & 0xffffu);
+      uint32_t pk[8];
+      Group16<C> gn;
+      gn.load(qn + base);
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const bool valid = (vm >> jj) & 1u, isless = (lm >> jj) & 1u, istie = (tm >> jj) & 1u;
+        const bool left = isless || (istie && run_t < tl);
+        const uint32_t glrank = run_l + min(run_t, tl);
+        const uint32_t pos = node_pos0 + (base + jj - lead);  // position in the node
+        uint32_t d = left ? glrank - left_before : left_tile + (pos - glrank - right_before);
+        d = valid ? d : 0xffffu;
+        if (jj & 1) pk[jj >> 1] |= d << 16;
+        else pk[jj >> 1] = d & 0xffffu;
+        run_l += isless;
+        run_t += istie;
+        if (valid) {
+          const uint32_t xn = gn.get(jj);
+          if (left) {
+            cmin0 = min(cmin0, xn);
+            cmax0 = max(cmax0, xn);
+          } else {
+            cmin1 = min(cmin1, xn);
+            cmax1 = max(cmax1, xn);
+          }
+        }
+      }
+      uint4 *dv = reinterpret_cast<uint4 *>(S.dst + base);
+      dv[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      dv[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+    __syncthreads();  // destinations visible to every thread
+    // 3. stores, consecutive threads on consecutive particles
+    const uint32_t cnt = g.cnt;
+    const uint32_t baseR = k + right_before - left_tile;  // node position = local + baseR in the right run
     for (uint32_t p = threadIdx.x; p < sz; p += kThreads) {
       const uint32_t wp = lead + p;
-      const uint32_t gi = wp >> 4, jj = wp & 15;
-      const uint32_t gm = S.gmask[gi], gp = S.gpre[gi];
-      const uint32_t below = (1u << jj) - 1u;
-      const uint32_t lmask = gm & 0xffffu, tmask = gm >> 16;
-      const uint32_t run_l = less_before + (gp >> 16) + __popc(lmask & below);
-      const uint32_t run_t = tie_before + (gp & 0xffffu) + __popc(tmask & below);
-      const bool isless = (lmask >> jj) & 1u, istie = (tmask >> jj) & 1u;
-      const bool left = isless || (istie && run_t < tl);
-      const uint32_t glrank = run_l + min(run_t, tl);
-      const uint32_t dst = left ? glrank : k + (node_pos0 + p - glrank);
-      const C x0 = S.in[b][0][wp], x1 = S.in[b][1][wp], x2 = S.in[b][2][wp];
-      if (dst < cnt) {
-        __stcg(n0 + dst, x0);
-        __stcg(n1 + dst, x1);
-        __stcg(n2 + dst, x2);
+      const uint32_t dl = S.dst[wp];
+      const uint32_t dst = dl + (dl < left_tile ? left_before : baseR);
+      if (dl < sz && dst < cnt) {
+        __stcg(n0 + dst, S.in[b][0][wp]);
+        __stcg(n1 + dst, S.in[b][1][wp]);
+        __stcg(n2 + dst, S.in[b][2][wp]);
         if (IDX) __stcg(ni + dst, S.idx[b][wp]);
       } else {
         atomicOr(a.err, kErrInternal);
       }
-      const uint32_t xn = nxt == 0 ? uint32_t(x0) : (nxt == 1 ? uint32_t(x1) : uint32_t(x2));
-      if (left) {
-        cmin0 = min(cmin0, xn);
-        cmax0 = max(cmax0, xn);
-      } else {
-        cmin1 = min(cmin1, xn);
-        cmax1 = max(cmax1, xn);
-      }
     }
-    // 3. children bounds on the next axis
+    // 4. children bounds on the next axis
     if (a.children) {
       cmin0 = __reduce_min_sync(0xffffffffu, cmin0);
       cmax0 = __reduce_max_sync(0xffffffffu, cmax0);
@@ -311,8 +370,15 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t ti
 template <typename C>
 __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
   __shared__ uint32_t red[2][8];
-  const TileGeom g = tile_geom(a, blockIdx.x);
-  const uint32_t v = a.nodes[g.j].v;
+  __shared__ TileGeom sg;
+  __shared__ uint32_t sv;
+  if (threadIdx.x == 0) {
+    sg = tile_geom(a, blockIdx.x);
+    sv = a.nodes[sg.j].v;
+  }
+  __syncthreads();
+  const TileGeom g = sg;
+  const uint32_t v = sv;
   const C *q = static_cast<const C *>(a.src[a.level % 3]);
   constexpr uint32_t kVec = 16 / sizeof(C);
   uint32_t less = 0, tie = 0;
@@ -320,15 +386,15 @@ __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
     less += x < v;
     tie += x == v;
   };
-  const uint64_t a0 = (g.tb + kVec - 1) / kVec * kVec, a1 = g.te / kVec * kVec;
+  const uint32_t a0 = (g.tb + kVec - 1) & ~(kVec - 1), a1 = g.te & ~(kVec - 1);
   if (a0 >= a1) {
-    for (uint64_t e = g.tb + threadIdx.x; e < g.te; e += blockDim.x) one(__ldcg(q + e));
+    for (uint32_t e = g.tb + threadIdx.x; e < g.te; e += blockDim.x) one(__ldcg(q + e));
   } else {
-    for (uint64_t e = g.tb + threadIdx.x; e < a0; e += blockDim.x) one(__ldcg(q + e));
-    for (uint64_t e = a1 + threadIdx.x; e < g.te; e += blockDim.x) one(__ldcg(q + e));
+    for (uint32_t e = g.tb + threadIdx.x; e < a0; e += blockDim.x) one(__ldcg(q + e));
+    for (uint32_t e = a1 + threadIdx.x; e < g.te; e += blockDim.x) one(__ldcg(q + e));
     const uint4 *vp = reinterpret_cast<const uint4 *>(q + a0);
-    const uint64_t nv = (a1 - a0) / kVec;
-    for (uint64_t i = threadIdx.x; i < nv; i += blockDim.x) {
+    const uint32_t nv = (a1 - a0) / kVec;
+    for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
       const uint4 w = __ldcg(vp + i);
       const uint32_t x[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
