@@ -23,6 +23,10 @@ constexpr int kDecThreads = 256;
 constexpr int kDecPer = 4;                          // particles per thread
 constexpr int kChunk = kDecThreads * kDecPer;       // particles per block
 constexpr int kChunkLeaves = 32;                    // leaves of one chunk held in shared memory
+// Payload words staged per chunk: kChunk particles of at most 93 bits, up to
+// kChunkLeaves word-aligned leaf starts, the alignment of the first staged
+// word and a 4-word read window past the last particle fit in 3 * kChunk + 64.
+constexpr int kWordCap = 3 * kChunk + 64;
 
 struct Rec {
   uint64_t po, wo;
@@ -113,13 +117,50 @@ __device__ __forceinline__ uint32_t window_bits(uint32_t w0, uint32_t w1, uint32
   return __funnelshift_r(lo, hi, r & 31) & ((1u << m) - 1u);
 }
 
+// Dequantizes one particle's three codes into the chunk's staging area.
+template <typename T, bool FAST>
+__device__ __forceinline__ void put_particle(const DecodeLaunch &a, T *stage, uint32_t sl, int32_t q0, int32_t q1,
+                                             int32_t q2) {
+  const int32_t q[3] = {q0, q1, q2};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T v;
+    if (sizeof(T) == 4) {
+      if (FAST) v = (T)dequant_fast(q[d], a.of[d], a.o[d], a.s, a.sh, a.sl);
+      else v = (T)dequant_exact(q[d], a.o[d], a.s);
+    } else {
+      v = (T)__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q[d]));
+    }
+    stage[3 * sl + d] = v;
+  }
+}
+
+// c = code - (2^(m-1) - 1) for the three fields of one particle starting at
+// bit r0 of the 4-word window.
+__device__ __forceinline__ void add_fields(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t r0,
+                                           uint32_t mm, int32_t &q0, int32_t &q1, int32_t &q2) {
+  const uint32_t m0 = mm & 0xffu, m1 = (mm >> 8) & 0xffu, m2 = (mm >> 16) & 0xffu;
+  if (m0) q0 += int32_t(window_bits(w0, w1, w2, w3, r0, m0)) - int32_t((1u << (m0 - 1)) - 1u);
+  if (m1) q1 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0, m1)) - int32_t((1u << (m1 - 1)) - 1u);
+  if (m2) q2 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0 + m1, m2)) - int32_t((1u << (m2 - 1)) - 1u);
+}
+
+// One block decodes a chunk of kChunk consecutive particles.  When the chunk
+// holds at most kChunkLeaves leaves (always, unless leaves are tiny), their
+// records and the payload words the chunk spans are staged in shared memory
+// with coalesced loads, and every particle is located with 32-bit arithmetic
+// relative to the staged words.  Otherwise each particle searches the leaf
+// table and reads its words from global memory.
 template <typename T, bool FAST, bool VEC>
 __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
   __shared__ __align__(16) T stage[3 * kChunk];
-  __shared__ uint64_t s_po[kChunkLeaves + 1], s_wo[kChunkLeaves];
+  __shared__ __align__(16) uint32_t sw[kWordCap];
+  __shared__ uint64_t s_po[kChunkLeaves + 1], s_wo[kChunkLeaves + 1];
+  __shared__ int64_t s_base[kChunkLeaves];  // staged-relative bit of "particle 0" of the leaf, minus one field width
   __shared__ int32_t s_q[kChunkLeaves][3];
-  __shared__ uint32_t s_m[kChunkLeaves];
-  __shared__ int s_count;
+  __shared__ uint32_t s_m[kChunkLeaves + 1];
+  __shared__ int s_count, s_staged;
+  __shared__ uint64_t s_lo, s_hi, s_end;
   if (*a.err) return;  // validation failed: write nothing
   const uint64_t c0 = uint64_t(blockIdx.x) * kChunk;
   if (c0 >= a.n) return;
@@ -127,21 +168,22 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
   const uint8_t *table = a.stream + kHeaderBytes;
   const uint32_t *words = reinterpret_cast<const uint32_t *>(table + uint64_t(kLeafBytes) * a.num_leaves);
   const uint64_t first = a.chunk_leaf[blockIdx.x];
-  // the chunk's leaves (usually one or two) into shared memory
   if (threadIdx.x < kChunkLeaves + 1) {
     const uint64_t L = first + threadIdx.x;
     if (L < a.num_leaves) {
       const Rec r = load_rec(table, L);
       s_po[threadIdx.x] = r.po;
+      s_wo[threadIdx.x] = r.wo;
+      s_m[threadIdx.x] = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
       if (threadIdx.x < kChunkLeaves) {
-        s_wo[threadIdx.x] = r.wo;
         s_q[threadIdx.x][0] = r.q[0];
         s_q[threadIdx.x][1] = r.q[1];
         s_q[threadIdx.x][2] = r.q[2];
-        s_m[threadIdx.x] = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
       }
     } else {
       s_po[threadIdx.x] = a.n;
+      s_wo[threadIdx.x] = a.payload_words;
+      s_m[threadIdx.x] = 0;
     }
   }
   __syncthreads();
@@ -149,65 +191,107 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
     int c = 1;
     while (c < kChunkLeaves && s_po[c] < c1) ++c;
     s_count = c;
+    const bool in_smem = c < kChunkLeaves || s_po[kChunkLeaves] >= c1;
+    int staged = 0;
+    if (in_smem) {
+      // first bit of particle c0 and end bit of particle c1 - 1
+      auto width = [](uint32_t mm) { return uint64_t((mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu)); };
+      const uint64_t i0 = c0 - s_po[0];
+      const uint64_t b0 = 32 * s_wo[0] + (i0 ? (i0 - 1) * width(s_m[0]) : 0);
+      const uint64_t il = (c1 - 1) - s_po[c - 1];
+      const uint64_t b1 = 32 * s_wo[c - 1] + il * width(s_m[c - 1]);
+      const uint64_t lo = (b0 >> 5) & ~3ull;  // 16-byte aligned start of the staged words
+      const uint64_t end = ((b1 + 31) >> 5) + 4;  // words a particle's 4-word window may touch
+      if (end - lo <= kWordCap) {
+        staged = 1;
+        s_lo = lo;
+        s_end = end;
+        s_hi = end < a.payload_words ? end : a.payload_words;
+        for (int L = 0; L < c; ++L)
+          s_base[L] = int64_t(32 * s_wo[L]) - int64_t(32 * lo) - int64_t(width(s_m[L]));
+      }
+    }
+    s_staged = staged;
   }
   __syncthreads();
   const int count = s_count;
-  const bool in_smem = count < kChunkLeaves || s_po[kChunkLeaves] >= c1;
+  T *stage_t = stage;
+  if (s_staged) {
+    const uint64_t lo = s_lo, hi = s_hi;
+    const uint32_t nst = uint32_t(s_end - lo);
+    const uint32_t nreal = hi > lo ? uint32_t(hi - lo) : 0u;
+    if ((reinterpret_cast<uintptr_t>(words) & 15) == 0) {
+      const uint32_t nvec = nreal >> 2;
+      const uint4 *src = reinterpret_cast<const uint4 *>(words + lo);
+      uint4 *dst = reinterpret_cast<uint4 *>(sw);
+      for (uint32_t v = threadIdx.x; v < nvec; v += kDecThreads) dst[v] = __ldg(src + v);
+      for (uint32_t w = 4 * nvec + threadIdx.x; w < nst; w += kDecThreads) sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
+    } else {
+      for (uint32_t w = threadIdx.x; w < nst; w += kDecThreads) sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
+    }
+    __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kDecPer; ++k) {
-    const uint64_t g = c0 + uint64_t(k) * kDecThreads + threadIdx.x;
-    if (g >= c1) continue;
-    uint64_t po, wo;
-    int32_t q0, q1, q2;
-    uint32_t mm;
-    if (in_smem) {
+    for (int k = 0; k < kDecPer; ++k) {
+      const uint32_t sl = uint32_t(k) * kDecThreads + threadIdx.x;
+      const uint64_t g = c0 + sl;
+      if (g >= c1) continue;
       int L = 0;
       while (L + 1 < count && s_po[L + 1] <= g) ++L;
-      po = s_po[L];
-      wo = s_wo[L];
-      q0 = s_q[L][0];
-      q1 = s_q[L][1];
-      q2 = s_q[L][2];
-      mm = s_m[L];
-    } else {  // many small leaves in this chunk: search the table
-      uint64_t lo = first, hi = a.num_leaves - 1;
-      while (lo < hi) {
-        const uint64_t mid = (lo + hi + 1) >> 1;
-        if (load_rec(table, mid).po <= g) lo = mid;
-        else hi = mid - 1;
+      int32_t q0 = s_q[L][0], q1 = s_q[L][1], q2 = s_q[L][2];
+      const uint32_t i = uint32_t(g - s_po[L]);
+      if (i > 0) {
+        const uint32_t mm = s_m[L];
+        const uint32_t w = (mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu);
+        const uint32_t bit = uint32_t(s_base[L] + int64_t(uint64_t(i) * w));
+        const uint32_t wi = bit >> 5;
+        add_fields(sw[wi], sw[wi + 1], sw[wi + 2], sw[wi + 3], bit & 31u, mm, q0, q1, q2);
       }
-      const Rec r = load_rec(table, lo);
-      po = r.po;
-      wo = r.wo;
-      q0 = r.q[0];
-      q1 = r.q[1];
-      q2 = r.q[2];
-      mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
+      put_particle<T, FAST>(a, stage_t, sl, q0, q1, q2);
     }
-    const uint64_t i = g - po;
-    if (i > 0) {
-      const uint32_t m0 = mm & 0xffu, m1 = (mm >> 8) & 0xffu, m2 = (mm >> 16) & 0xffu;
-      const uint64_t bit = 32ull * wo + (i - 1) * (uint64_t)(m0 + m1 + m2);
-      const uint64_t wi = bit >> 5;
-      const uint32_t w0 = word_at(words, a.payload_words, wi), w1 = word_at(words, a.payload_words, wi + 1);
-      const uint32_t w2 = word_at(words, a.payload_words, wi + 2), w3 = word_at(words, a.payload_words, wi + 3);
-      const uint32_t r0 = uint32_t(bit & 31);
-      if (m0) q0 += int32_t(window_bits(w0, w1, w2, w3, r0, m0)) - int32_t((1u << (m0 - 1)) - 1u);
-      if (m1) q1 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0, m1)) - int32_t((1u << (m1 - 1)) - 1u);
-      if (m2) q2 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0 + m1, m2)) - int32_t((1u << (m2 - 1)) - 1u);
-    }
-    const uint32_t sl = uint32_t(g - c0);
-    const int32_t q[3] = {q0, q1, q2};
+  } else {
+    const bool in_smem = count < kChunkLeaves || s_po[kChunkLeaves] >= c1;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T v;
-      if (sizeof(T) == 4) {
-        if (FAST) v = (T)dequant_fast(q[d], a.of[d], a.o[d], a.s, a.sh, a.sl);
-        else v = (T)dequant_exact(q[d], a.o[d], a.s);
-      } else {
-        v = (T)__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q[d]));
+    for (int k = 0; k < kDecPer; ++k) {
+      const uint32_t sl = uint32_t(k) * kDecThreads + threadIdx.x;
+      const uint64_t g = c0 + sl;
+      if (g >= c1) continue;
+      uint64_t po, wo;
+      int32_t q0, q1, q2;
+      uint32_t mm;
+      if (in_smem) {
+        int L = 0;
+        while (L + 1 < count && s_po[L + 1] <= g) ++L;
+        po = s_po[L];
+        wo = s_wo[L];
+        q0 = s_q[L][0];
+        q1 = s_q[L][1];
+        q2 = s_q[L][2];
+        mm = s_m[L];
+      } else {  // many small leaves in this chunk: search the table
+        uint64_t lo = first, hi = a.num_leaves - 1;
+        while (lo < hi) {
+          const uint64_t mid = (lo + hi + 1) >> 1;
+          if (load_rec(table, mid).po <= g) lo = mid;
+          else hi = mid - 1;
+        }
+        const Rec r = load_rec(table, lo);
+        po = r.po;
+        wo = r.wo;
+        q0 = r.q[0];
+        q1 = r.q[1];
+        q2 = r.q[2];
+        mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
       }
-      stage[3 * sl + d] = v;
+      const uint64_t i = g - po;
+      if (i > 0) {
+        const uint32_t w = (mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu);
+        const uint64_t bit = 32ull * wo + (i - 1) * uint64_t(w);
+        const uint64_t wi = bit >> 5;
+        add_fields(word_at(words, a.payload_words, wi), word_at(words, a.payload_words, wi + 1),
+                   word_at(words, a.payload_words, wi + 2), word_at(words, a.payload_words, wi + 3),
+                   uint32_t(bit & 31), mm, q0, q1, q2);
+      }
+      put_particle<T, FAST>(a, stage_t, sl, q0, q1, q2);
     }
   }
   __syncthreads();

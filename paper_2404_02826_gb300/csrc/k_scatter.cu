@@ -10,15 +10,15 @@
 //   k_scatter   persistent CTAs; while one tile is partitioned, the Tensor
 //               Memory Accelerator copies the next tile's codes into the other
 //               half of a shared-memory double buffer (cp.async.bulk completing
-//               on an mbarrier).  Per tile: one thread per 16 consecutive
-//               particles forms bit masks of "code < v" and "code == v"; after
-//               a block scan of their counts the same thread walks its group
-//               and records each particle's place in the tile's left or right
-//               run as a 16-bit index; then consecutive threads take
-//               consecutive particles and store them, so stores to each run are
-//               contiguous across a warp.  The children's code bounds on the
-//               next axis are reduced per CTA and folded in with an atomic only
-//               when they improve the stored bound.
+//               on an mbarrier).  Per tile: consecutive lanes take consecutive
+//               particles; two warp ballots give the masks of "code < v" and
+//               "code == v" of 32 particles, one block scan turns the counts of
+//               every (round, warp) into prefixes, and each particle's place in
+//               its child follows from its prefix and the popcount of the
+//               masks below its lane.  Stores to each child are contiguous
+//               across a warp.  The children's code bounds on the next axis are
+//               reduced per CTA and folded in with an atomic only when they
+//               improve the stored bound.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -35,6 +35,7 @@ struct Cfg {
   static constexpr int kBytesPer = 3 * int(sizeof(C)) + (IDX ? 4 : 0);
   static constexpr int kWin = kBytesPer <= 6 ? 8192 : 4096;  // window of particles held per buffer
   static constexpr int kTile = kWin - 16;                      // largest tile: an aligned window covers it
+  static constexpr int kRounds = kWin / kThreads;              // window slots per thread
 };
 
 // Tile i of node j covers positions [i*ts, (i+1)*ts) of the node, clipped to
@@ -50,13 +51,15 @@ struct Smem {
   using F = Cfg<C, IDX>;
   C in[2][3][F::kWin];
   uint32_t idx[IDX ? 2 : 1][IDX ? F::kWin : 4];
-  uint16_t dst[F::kWin];       // tile-local destination of each window slot (0xffff: none)
-  uint32_t scan[33];
+  alignas(16) uint32_t wc[F::kRounds * kWarps];  // (less << 16 | tie) per round and warp
+  uint2 msk[F::kRounds * kWarps];                // ("code < v", "code == v") ballots per round and warp
+  uint2 pref[F::kRounds * kWarps];               // (left-going, ties) in the node before each round and warp
   uint32_t red[4][kWarps];
   unsigned long long bar[2];
   unsigned long long pre[2];  // (less << 31 | tie) of the node's tiles before this one
   uint32_t tile[2];
   uint32_t v[2], tleft[2];
+  uint2 cb[2][2];  // children's (lo, hi) as read when the tile was issued
   TileGeom geo[2];
 };
 
@@ -103,58 +106,6 @@ __device__ __forceinline__ void wait_buffer(unsigned long long *bar, uint32_t pa
   }
 }
 
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *warp_tot, uint32_t &total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = x;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) warp_tot[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t t = lane < kWarps ? warp_tot[lane] : 0;
-    uint32_t ti = t;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
-      if (lane >= o) ti += y;
-    }
-    if (lane < kWarps) warp_tot[lane] = ti - t;
-    if (lane == 31) warp_tot[32] = ti;
-  }
-  __syncthreads();
-  total = warp_tot[32];
-  const uint32_t r = warp_tot[warp] + incl - x;
-  __syncthreads();
-  return r;
-}
-
-// 16 consecutive codes starting at a 16-aligned slot, read with 16-byte loads.
-template <typename C>
-struct Group16;
-template <>
-struct Group16<uint16_t> {
-  uint32_t w[8];  // two codes per word, element 2i in the low half
-  __device__ __forceinline__ void load(const uint16_t *p) {
-    const uint4 a = reinterpret_cast<const uint4 *>(p)[0], b = reinterpret_cast<const uint4 *>(p)[1];
-    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-  }
-  __device__ __forceinline__ uint32_t get(int j) const { return (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu); }
-};
-template <>
-struct Group16<uint32_t> {
-  uint32_t w[16];
-  __device__ __forceinline__ void load(const uint32_t *p) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint4 a = reinterpret_cast<const uint4 *>(p)[i];
-      w[4 * i] = a.x; w[4 * i + 1] = a.y; w[4 * i + 2] = a.z; w[4 * i + 3] = a.w;
-    }
-  }
-  __device__ __forceinline__ uint32_t get(int j) const { return w[j]; }
-};
-
 __device__ __forceinline__ TileGeom tile_geom(const LevelLaunch &a, uint32_t t) {
   TileGeom g;
   const uint32_t T = a.tiles_per_node;
@@ -170,11 +121,18 @@ __device__ __forceinline__ TileGeom tile_geom(const LevelLaunch &a, uint32_t t) 
   return g;
 }
 
-// Thread 0: copies the window of tile t into buffer b and reads its node and
-// its prefix counts (the loads complete while the current tile is processed).
+// What thread 0 reads for a tile it has just issued; the loads complete while
+// the current tile is processed and are used at its end.
+struct Pending {
+  uint32_t v, tl;
+  unsigned long long pre;
+  uint2 c0, c1;  // children's stored (lo, hi); bounds only tighten, so an old value is a safe filter
+};
+
+// Thread 0: copies the window of tile t into buffer b and starts the loads of
+// its node, its prefix counts and its children's bounds.
 template <typename C, bool IDX>
-__device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S, uint32_t t, int b, uint32_t &v,
-                                           uint32_t &tl, unsigned long long &pre) {
+__device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S, uint32_t t, int b, Pending &p) {
   const TileGeom g = tile_geom(a, t);
   S.geo[b] = g;
   const uint32_t w0 = g.tb & ~15u;
@@ -185,19 +143,38 @@ __device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S
     for (int d = 0; d < 3; ++d) bulk_g2s(S.in[b][d], static_cast<const C *>(a.src[d]) + w0, bytes, &S.bar[b]);
     if (IDX) bulk_g2s(S.idx[b], a.src_idx + w0, 4 * nwin, &S.bar[b]);
   }
-  v = a.nodes[g.j].v;
-  tl = a.nodes[g.j].tleft;
-  pre = a.tile_state[t];
+  p.v = a.nodes[g.j].v;
+  p.tl = a.nodes[g.j].tleft;
+  p.pre = a.tile_state[t];
+  if (a.children) {
+    p.c0 = __ldcg(reinterpret_cast<const uint2 *>(&a.children[2 * g.j].lo));
+    p.c1 = __ldcg(reinterpret_cast<const uint2 *>(&a.children[2 * g.j + 1].lo));
+  }
 }
 
 template <typename C, bool IDX>
-__global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t tiles) {
+__device__ __forceinline__ void publish(Smem<C, IDX> &S, int b, const Pending &p) {
+  S.v[b] = p.v;
+  S.tleft[b] = p.tl;
+  S.pre[b] = p.pre;
+  S.cb[b][0] = p.c0;
+  S.cb[b][1] = p.c1;
+}
+
+// Persistent CTA.  Thread 0 keeps one ticket and one tile copy ahead of the
+// tile being partitioned, so neither the ticket atomic nor the copy is waited
+// for; three block barriers per tile.  AXIS is the split axis of the level.
+template <typename C, bool IDX, int AXIS>
+__global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t tiles) {
+  using F = Cfg<C, IDX>;
+  constexpr int kPer = F::kRounds * kWarps / 32;  // scan entries per lane of warp 0
+  static_assert(kPer == 4 || kPer == 8, "scan entries per lane");
+  constexpr int NXT = (AXIS + 1) % 3;
   extern __shared__ __align__(128) unsigned char smraw[];
   Smem<C, IDX> &S = *reinterpret_cast<Smem<C, IDX> *>(smraw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int axis = a.level % 3, nxt = (a.level + 1) % 3;
-  uint32_t pend_v = 0, pend_tl = 0;
-  unsigned long long pend_pre = 0;
+  Pending pend = {};
+  uint32_t next_t = tiles;  // thread 0: the tile after the one in flight
   if (threadIdx.x == 0) {
     mbar_init(&S.bar[0], 1);
     mbar_init(&S.bar[1], 1);
@@ -205,10 +182,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t ti
     const uint32_t t0 = atomicAdd(a.ticket, 1u);
     S.tile[0] = t0;
     if (t0 < tiles) {
-      issue_tile(a, S, t0, 0, pend_v, pend_tl, pend_pre);
-      S.v[0] = pend_v;
-      S.tleft[0] = pend_tl;
-      S.pre[0] = pend_pre;
+      issue_tile(a, S, t0, 0, pend);
+      publish(S, 0, pend);
+      next_t = atomicAdd(a.ticket, 1u);
     }
   }
   __syncthreads();
@@ -217,17 +193,20 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t ti
   C *d0 = static_cast<C *>(a.dst[0]);
   C *d1 = static_cast<C *>(a.dst[1]);
   C *d2 = static_cast<C *>(a.dst[2]);
+  const uint32_t lt_mask = (1u << lane) - 1u, lane_bit = 1u << lane;
+  const bool bounds = a.children != nullptr;
   for (;;) {
     const uint32_t t = S.tile[b];
     if (t >= tiles) break;
     bool prefetched = false;
+    uint32_t after = tiles;
     if (threadIdx.x == 0) {
-      const uint32_t tn = atomicAdd(a.ticket, 1u);
-      S.tile[b ^ 1] = tn;
-      if (tn < tiles) {
+      S.tile[b ^ 1] = next_t;
+      if (next_t < tiles) {
         fence_proxy_async();  // earlier generic reads of that buffer precede the async writes
-        issue_tile(a, S, tn, b ^ 1, pend_v, pend_tl, pend_pre);
+        issue_tile(a, S, next_t, b ^ 1, pend);
         prefetched = true;
+        after = atomicAdd(a.ticket, 1u);
       }
     }
     wait_buffer(&S.bar[b], b ? phase1 : phase0, a.err);
@@ -236,62 +215,103 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t ti
 
     const TileGeom g = S.geo[b];
     const uint32_t k = g.cnt >> 1;
-    const uint32_t sz = g.te - g.tb;
     const uint32_t lead = g.tb & 15u;
-    const uint32_t ngroups = (lead + sz + 15) >> 4;
+    const uint32_t nslots = lead + (g.te - g.tb);
     const uint32_t v = S.v[b], tl = S.tleft[b];
-    const unsigned long long pre = S.pre[b];
-    const uint32_t less_before = uint32_t(pre >> 31), tie_before = uint32_t(pre & 0x7fffffffu);
-    const uint32_t node_pos0 = g.tb - g.off;  // position of the tile's first particle in the node
     C *n0 = d0 + g.off, *n1 = d1 + g.off, *n2 = d2 + g.off;
     uint32_t *ni = IDX ? a.dst_idx + g.off : nullptr;
+    const C *x0s = S.in[b][0], *x1s = S.in[b][1], *x2s = S.in[b][2];
+    const C *qa = AXIS == 0 ? x0s : (AXIS == 1 ? x1s : x2s);
 
-    // 1. each thread classifies its 16-particle group (registers only)
-    const bool mine = threadIdx.x < ngroups;
-    const uint32_t base = threadIdx.x * 16;
-    const C *qa = S.in[b][axis];
-    const C *qn = S.in[b][nxt];
-    uint32_t lm = 0, tm = 0, vm = 0;
-    if (mine) {
-      Group16<C> ga;  // 16-byte loads: scalar loads 16 particles apart would hit the same bank
-      ga.load(qa + base);
-#pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const uint32_t wp = base + jj;
-        const uint32_t q = ga.get(jj);
-        const bool valid = wp >= lead && wp < lead + sz;
-        vm |= uint32_t(valid) << jj;
-        lm |= uint32_t(valid && q < v) << jj;
-        tm |= uint32_t(valid && q == v) << jj;
+    // Window slot wp = r * kThreads + threadIdx.x in round r: a warp covers 32
+    // consecutive slots, so two ballots give the "code < v" and "code == v"
+    // masks of those 32 particles.  Slots outside [lead, nslots) are not
+    // particles of the tile; only the first and the last round have any.
+    const uint32_t rounds = (nslots + kThreads - 1) / kThreads;
+    // 1. masks and counts per round and warp
+    for (uint32_t r = 0; r < rounds; ++r) {
+      const uint32_t wp = r * kThreads + threadIdx.x;
+      const uint32_t q = qa[wp];
+      const bool valid = wp >= lead && wp < nslots;
+      const uint32_t lm = __ballot_sync(0xffffffffu, valid && q < v);
+      const uint32_t tm = __ballot_sync(0xffffffffu, valid && q == v);
+      if (lane == 0) {
+        S.wc[r * kWarps + warp] = (uint32_t(__popc(lm)) << 16) | uint32_t(__popc(tm));
+        S.msk[r * kWarps + warp] = make_uint2(lm, tm);
       }
     }
-    uint32_t total;
-    const uint32_t ex = block_excl_scan((uint32_t(__popc(lm)) << 16) | uint32_t(__popc(tm)), S.scan, total);
-    // the tile's particles split into a left run [0, left_tile) and a right run [left_tile, sz)
-    const uint32_t left_before = less_before + min(tie_before, tl);
-    const uint32_t left_tile = less_before + (total >> 16) + min(tie_before + (total & 0xffffu), tl) - left_before;
-    const uint32_t right_before = node_pos0 - left_before;
-    // 2. tile-local destination of every particle of the group, and the children bounds
-    uint32_t cmin0 = 0xffffffffu, cmax0 = 0, cmin1 = 0xffffffffu, cmax1 = 0;
-    if (mine) {
-      uint32_t run_l = less_before + (ex >> 16), run_t = tie_before + (ex & 0xffffu);
-      uint32_t pk[8];
-      Group16<C> gn;
-      gn.load(qn + base);
+    __syncthreads();
+    // 2. warp 0: exclusive scan of the counts, kPer entries per lane, turned
+    //    into (left-going particles, ties) of the node before each entry
+    if (warp == 0) {
+      const unsigned long long pre = S.pre[b];
+      const uint32_t less_before = uint32_t(pre >> 31), tie_before = uint32_t(pre & 0x7fffffffu);
+      const uint32_t ne = rounds * kWarps;
+      uint32_t e[kPer];
+      const uint4 *w4 = reinterpret_cast<const uint4 *>(S.wc + kPer * lane);
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const bool valid = (vm >> jj) & 1u, isless = (lm >> jj) & 1u, istie = (tm >> jj) & 1u;
-        const bool left = isless || (istie && run_t < tl);
-        const uint32_t glrank = run_l + min(run_t, tl);
-        const uint32_t pos = node_pos0 + (base + jj - lead);  // position in the node
-        uint32_t d = left ? glrank - left_before : left_tile + (pos - glrank - right_before);
-        d = valid ? d : 0xffffu;
-        if (jj & 1) pk[jj >> 1] |= d << 16;
-        else pk[jj >> 1] = d & 0xffffu;
-        run_l += isless;
-        run_t += istie;
-        if (valid) {
-          const uint32_t xn = gn.get(jj);
+      for (int h = 0; h < kPer / 4; ++h) {
+        const uint4 x = w4[h];
+        e[4 * h] = x.x;
+        e[4 * h + 1] = x.y;
+        e[4 * h + 2] = x.z;
+        e[4 * h + 3] = x.w;
+      }
+      uint32_t sum = 0;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const uint32_t x = (kPer * uint32_t(lane) + i) < ne ? e[i] : 0u;
+        e[i] = sum;
+        sum += x;
+      }
+      uint32_t incl = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t base = incl - sum;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const uint32_t ex = base + e[i];
+        const uint32_t lb = less_before + (ex >> 16), tb = tie_before + (ex & 0xffffu);
+        S.pref[kPer * lane + i] = make_uint2(lb + min(tb, tl), tb);
+      }
+    }
+    __syncthreads();
+    // 3. every particle's place in the node; stores with consecutive lanes on
+    //    consecutive particles, so each child's run is contiguous across a warp
+    const uint32_t cnt = g.cnt;
+    const uint32_t kpos = k + (g.tb - g.off) - lead;  // k + node position of window slot 0
+    uint32_t cmin0 = 0xffffffffu, cmax0 = 0, cmin1 = 0xffffffffu, cmax1 = 0;
+    for (uint32_t r = 0; r < rounds; ++r) {
+      const uint32_t wp = r * kThreads + threadIdx.x;
+      const uint2 mk = S.msk[r * kWarps + warp];
+      const uint2 pf = S.pref[r * kWarps + warp];
+      bool left;
+      uint32_t glrank;  // left-going particles of the node before this one
+      if (mk.y == 0) {  // no particle of this warp's 32 has code v
+        left = (mk.x & lane_bit) != 0;
+        glrank = pf.x + __popc(mk.x & lt_mask);
+      } else {
+        const uint32_t run_t = pf.y + __popc(mk.y & lt_mask);
+        const uint32_t run_l = pf.x - min(pf.y, tl) + __popc(mk.x & lt_mask);
+        left = (mk.x & lane_bit) || ((mk.y & lane_bit) && run_t < tl);
+        glrank = run_l + min(run_t, tl);
+      }
+      const bool valid = (r > 0 && r + 1 < rounds) || (wp >= lead && wp < nslots);
+      if (valid) {
+        const uint32_t dst = left ? glrank : kpos + wp - glrank;
+        const C x0 = x0s[wp], x1 = x1s[wp], x2 = x2s[wp];
+        if (dst < cnt) {
+          __stcg(n0 + dst, x0);
+          __stcg(n1 + dst, x1);
+          __stcg(n2 + dst, x2);
+          if (IDX) __stcg(ni + dst, S.idx[b][wp]);
+        } else {
+          atomicOr(a.err, kErrInternal);
+        }
+        if (bounds) {
+          const uint32_t xn = NXT == 0 ? x0 : (NXT == 1 ? x1 : x2);
           if (left) {
             cmin0 = min(cmin0, xn);
             cmax0 = max(cmax0, xn);
@@ -301,29 +321,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t ti
           }
         }
       }
-      uint4 *dv = reinterpret_cast<uint4 *>(S.dst + base);
-      dv[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      dv[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
-    __syncthreads();  // destinations visible to every thread
-    // 3. stores, consecutive threads on consecutive particles
-    const uint32_t cnt = g.cnt;
-    const uint32_t baseR = k + right_before - left_tile;  // node position = local + baseR in the right run
-    for (uint32_t p = threadIdx.x; p < sz; p += kThreads) {
-      const uint32_t wp = lead + p;
-      const uint32_t dl = S.dst[wp];
-      const uint32_t dst = dl + (dl < left_tile ? left_before : baseR);
-      if (dl < sz && dst < cnt) {
-        __stcg(n0 + dst, S.in[b][0][wp]);
-        __stcg(n1 + dst, S.in[b][1][wp]);
-        __stcg(n2 + dst, S.in[b][2][wp]);
-        if (IDX) __stcg(ni + dst, S.idx[b][wp]);
-      } else {
-        atomicOr(a.err, kErrInternal);
-      }
-    }
-    // 4. children bounds on the next axis
-    if (a.children) {
+    // 4. children bounds on the next axis: per warp, then warp 0 folds them in
+    if (bounds) {
       cmin0 = __reduce_min_sync(0xffffffffu, cmin0);
       cmax0 = __reduce_max_sync(0xffffffffu, cmax0);
       cmin1 = __reduce_min_sync(0xffffffffu, cmin1);
@@ -335,33 +335,30 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LevelLaunch a, uint32_t ti
         S.red[3][warp] = cmax1;
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (a.children) {
-        uint32_t m0 = S.red[0][0], x0 = S.red[1][0], m1 = S.red[2][0], x1 = S.red[3][0];
-        for (int w = 1; w < kWarps; ++w) {
-          m0 = min(m0, S.red[0][w]);
-          x0 = max(x0, S.red[1][w]);
-          m1 = min(m1, S.red[2][w]);
-          x1 = max(x1, S.red[3][w]);
-        }
-        LevelNode *c0 = a.children + 2 * g.j, *c1 = c0 + 1;
-        if (m0 <= x0) {
-          if (m0 < ld_relaxed(&c0->lo)) atomicMin(&c0->lo, m0);
-          if (x0 > ld_relaxed(&c0->hi)) atomicMax(&c0->hi, x0);
-        }
-        if (m1 <= x1) {
-          if (m1 < ld_relaxed(&c1->lo)) atomicMin(&c1->lo, m1);
-          if (x1 > ld_relaxed(&c1->hi)) atomicMax(&c1->hi, x1);
+    if (threadIdx.x == 0 && prefetched) publish(S, b ^ 1, pend);
+    __syncthreads();  // the next tile's state is published; S.red is complete
+    if (warp == 0) {
+      if (bounds) {
+        const bool in = lane < kWarps;
+        const uint32_t m0 = __reduce_min_sync(0xffffffffu, in ? S.red[0][lane] : 0xffffffffu);
+        const uint32_t x0 = __reduce_max_sync(0xffffffffu, in ? S.red[1][lane] : 0u);
+        const uint32_t m1 = __reduce_min_sync(0xffffffffu, in ? S.red[2][lane] : 0xffffffffu);
+        const uint32_t x1 = __reduce_max_sync(0xffffffffu, in ? S.red[3][lane] : 0u);
+        if (lane == 0) {
+          const uint2 s0 = S.cb[b][0], s1 = S.cb[b][1];
+          LevelNode *c0 = a.children + 2 * g.j, *c1 = c0 + 1;
+          if (m0 <= x0) {
+            if (m0 < s0.x) atomicMin(&c0->lo, m0);
+            if (x0 > s0.y) atomicMax(&c0->hi, x0);
+          }
+          if (m1 <= x1) {
+            if (m1 < s1.x) atomicMin(&c1->lo, m1);
+            if (x1 > s1.y) atomicMax(&c1->hi, x1);
+          }
         }
       }
-      if (prefetched) {
-        S.v[b ^ 1] = pend_v;
-        S.tleft[b ^ 1] = pend_tl;
-        S.pre[b ^ 1] = pend_pre;
-      }
+      if (lane == 0) next_t = after;
     }
-    __syncthreads();
     b ^= 1;
   }
 }
@@ -460,6 +457,23 @@ __global__ void __launch_bounds__(1024) k_tilescan(LevelLaunch a) {
   }
 }
 
+template <typename C, bool IDX, int AXIS>
+cudaError_t scatter_launch(const LevelLaunch &a, uint32_t tiles, cudaStream_t st) {
+  const size_t smem = sizeof(Smem<C, IDX>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_scatter<C, IDX, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<C, IDX, AXIS>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = uint64_t(per_sm) * uint64_t(device_sm_count());
+  if (grid > tiles) grid = tiles;
+  TraceScope ts("k_scatter", st);
+  k_scatter<C, IDX, AXIS><<<unsigned(grid), kThreads, smem, st>>>(a, tiles);
+  return cudaGetLastError();
+}
+
 template <typename C, bool IDX>
 cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
   const uint64_t tiles = (1ull << a.level) * a.tiles_per_node;
@@ -471,18 +485,11 @@ cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
     TraceScope ts("k_tilescan", st);
     k_tilescan<<<unsigned(1ull << a.level), 1024, 0, st>>>(a);
   }
-  const size_t smem = sizeof(Smem<C, IDX>);
-  cudaError_t e = cudaFuncSetAttribute(k_scatter<C, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<C, IDX>, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  uint64_t grid = uint64_t(per_sm) * uint64_t(device_sm_count());
-  if (grid > tiles) grid = tiles;
-  TraceScope ts("k_scatter", st);
-  k_scatter<C, IDX><<<unsigned(grid), kThreads, smem, st>>>(a, uint32_t(tiles));
-  return cudaGetLastError();
+  switch (a.level % 3) {
+    case 0: return scatter_launch<C, IDX, 0>(a, uint32_t(tiles), st);
+    case 1: return scatter_launch<C, IDX, 1>(a, uint32_t(tiles), st);
+    default: return scatter_launch<C, IDX, 2>(a, uint32_t(tiles), st);
+  }
 }
 
 }  // namespace
