@@ -57,25 +57,49 @@ __device__ __forceinline__ uint64_t leaf_words(const Rec &r, uint64_t cnt) {
 
 // One thread per leaf: every field and every neighbour relation is checked,
 // and each decode chunk whose first particle lies in this leaf records it.
+// The range of codes a leaf can produce, [q_ref - 2^(m-1) + 1, q_ref + 2^(m-1)]
+// per axis (any m-bit field, the unused all-ones one included), is reduced
+// per warp into qb: qb[d] = max(0, -lowest code), qb[3 + d] = highest code.
 __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves, uint64_t words,
-                           uint32_t *chunk_leaf, uint32_t *err) {
+                           uint32_t *chunk_leaf, uint32_t *err, int32_t *qb) {
   const uint64_t L = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (L >= num_leaves) return;
+  const bool mine = L < num_leaves;
   const uint8_t *table = stream + kHeaderBytes;
-  const Rec r = load_rec(table, L);
-  const uint64_t pend = (L + 1 < num_leaves) ? load_rec(table, L + 1).po : n;
-  bool ok = r.zero == 0 && r.m[0] <= 31 && r.m[1] <= 31 && r.m[2] <= 31 && pend > r.po && pend <= n;
-  if (L == 0) ok = ok && r.po == 0 && r.wo == 0;
-  if (ok) {
-    const uint64_t wend = r.wo + leaf_words(r, pend - r.po);
-    const uint64_t wnext = (L + 1 < num_leaves) ? load_rec(table, L + 1).wo : words;
-    ok = r.wo <= words && wend == wnext;
+  int32_t neg[3] = {0, 0, 0}, top[3] = {0, 0, 0};
+  if (mine) {
+    const Rec r = load_rec(table, L);
+    const uint64_t pend = (L + 1 < num_leaves) ? load_rec(table, L + 1).po : n;
+    bool ok = r.zero == 0 && r.m[0] <= 31 && r.m[1] <= 31 && r.m[2] <= 31 && pend > r.po && pend <= n;
+    if (L == 0) ok = ok && r.po == 0 && r.wo == 0;
+    if (ok) {
+      const uint64_t wend = r.wo + leaf_words(r, pend - r.po);
+      const uint64_t wnext = (L + 1 < num_leaves) ? load_rec(table, L + 1).wo : words;
+      ok = r.wo <= words && wend == wnext;
+    }
+    if (!ok) {
+      atomicOr(err, kErrCorrupt);
+    } else {
+      for (uint64_t c = (r.po + kChunk - 1) / kChunk; c * kChunk < pend; ++c) chunk_leaf[c] = uint32_t(L);
+      for (int d = 0; d < 3; ++d) {
+        const int64_t half = r.m[d] ? (int64_t(1) << (r.m[d] - 1)) : 0;
+        const int64_t lo = int64_t(r.q[d]) - (half ? half - 1 : 0), hi = int64_t(r.q[d]) + half;
+        neg[d] = int32_t(lo >= 0 ? 0 : (-lo > 0x7fffffff ? 0x7fffffff : -lo));
+        top[d] = int32_t(hi <= 0 ? 0 : (hi > 0x7fffffff ? 0x7fffffff : hi));
+      }
+    }
   }
-  if (!ok) {
-    atomicOr(err, kErrCorrupt);
-    return;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    neg[d] = __reduce_max_sync(0xffffffffu, neg[d]);
+    top[d] = __reduce_max_sync(0xffffffffu, top[d]);
   }
-  for (uint64_t c = (r.po + kChunk - 1) / kChunk; c * kChunk < pend; ++c) chunk_leaf[c] = uint32_t(L);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (neg[d]) atomicMax(qb + d, neg[d]);
+      if (top[d]) atomicMax(qb + 3 + d, top[d]);
+    }
+  }
 }
 
 __device__ __forceinline__ uint32_t word_at(const uint32_t *__restrict__ w, uint64_t nwords, uint64_t i) {
@@ -117,22 +141,53 @@ __device__ __forceinline__ uint32_t window_bits(uint32_t w0, uint32_t w1, uint32
   return __funnelshift_r(lo, hi, r & 31) & ((1u << m) - 1u);
 }
 
-// Dequantizes one particle's three codes into the chunk's staging area.
+// Entries of the dequantization table (global memory, read through L1).
+constexpr uint32_t kTabEntries = 24576;
+
+// Constants of one leaf of the chunk being decoded.
+struct LeafC {
+  int32_t rel;       // first particle of the leaf minus the chunk's first particle
+  int32_t base;      // bit of particle i is base + i * w, relative to the first staged word
+  uint32_t w;        // m_x + m_y + m_z
+  uint32_t m0;       // m_x
+  uint32_t s2;       // m_x + m_y: first bit of the z field
+  uint32_t mask[3];  // 2^m_d - 1
+  int32_t off[3];    // q_ref_d - (2^(m_d - 1) - 1): the code of field value 0
+  int32_t qref[3];
+  uint32_t pad[2];
+};
+
+template <typename T>
+struct DecSmem {
+  T stage[3 * kChunk];
+  uint32_t sw[kWordCap];
+  LeafC lc[kChunkLeaves];
+  uint64_t po[kChunkLeaves + 1], wo[kChunkLeaves + 1];
+  uint32_t mm[kChunkLeaves + 1];
+  int32_t q[kChunkLeaves][3];
+  uint64_t lo, hi, end;
+  int count, staged;
+};
+
+// Whether every code lies in [0, qmax_d] with sum_d (qmax_d + 1) <= kTabEntries;
+// then tb1, tb2 are where the y and z tables start.
+__device__ __forceinline__ bool table_fits(const int32_t *qb, uint32_t &tb1, uint32_t &tb2, uint32_t &te) {
+  if (qb[0] | qb[1] | qb[2]) return false;
+  const uint64_t e0 = uint64_t(qb[3]) + 1, e1 = uint64_t(qb[4]) + 1, e2 = uint64_t(qb[5]) + 1;
+  tb1 = uint32_t(e0);
+  tb2 = uint32_t(e0 + e1);
+  te = uint32_t(e0 + e1 + e2);
+  return e0 + e1 + e2 <= kTabEntries;
+}
+
+// (T)(o_d + s q) by the double expression; float output on the FP32 pipe when exact.
 template <typename T, bool FAST>
-__device__ __forceinline__ void put_particle(const DecodeLaunch &a, T *stage, uint32_t sl, int32_t q0, int32_t q1,
-                                             int32_t q2) {
-  const int32_t q[3] = {q0, q1, q2};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    T v;
-    if (sizeof(T) == 4) {
-      if (FAST) v = (T)dequant_fast(q[d], a.of[d], a.o[d], a.s, a.sh, a.sl);
-      else v = (T)dequant_exact(q[d], a.o[d], a.s);
-    } else {
-      v = (T)__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q[d]));
-    }
-    stage[3 * sl + d] = v;
+__device__ __forceinline__ T dequant(const DecodeLaunch &a, int d, int32_t q) {
+  if (sizeof(T) == 4) {
+    if (FAST) return (T)dequant_fast(q, a.of[d], a.o[d], a.s, a.sh, a.sl);
+    return (T)dequant_exact(q, a.o[d], a.s);
   }
+  return (T)__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q));
 }
 
 // c = code - (2^(m-1) - 1) for the three fields of one particle starting at
@@ -145,165 +200,234 @@ __device__ __forceinline__ void add_fields(uint32_t w0, uint32_t w1, uint32_t w2
   if (m2) q2 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0 + m1, m2)) - int32_t((1u << (m2 - 1)) - 1u);
 }
 
-// One block decodes a chunk of kChunk consecutive particles.  When the chunk
-// holds at most kChunkLeaves leaves (always, unless leaves are tiny), their
-// records and the payload words the chunk spans are staged in shared memory
-// with coalesced loads, and every particle is located with 32-bit arithmetic
-// relative to the staged words.  Otherwise each particle searches the leaf
-// table and reads its words from global memory.
+// (T)(o_d + s q) for every code q in [0, qmax_d] of the three axes, one
+// table after another: the dequantization of a particle becomes three
+// lookups, and the double expression is evaluated once per code.
+template <typename T, bool FAST>
+__global__ void k_dtable(DecodeLaunch a) {
+  if (*a.err) return;
+  uint32_t tb1, tb2, te;
+  if (!table_fits(a.qb, tb1, tb2, te)) return;
+  T *tab = static_cast<T *>(a.tab);
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < te; e += gridDim.x * blockDim.x) {
+    const int d = e < tb1 ? 0 : (e < tb2 ? 1 : 2);
+    const int32_t q = int32_t(e - (d == 0 ? 0u : (d == 1 ? tb1 : tb2)));
+    tab[e] = dequant<T, FAST>(a, d, q);
+  }
+}
+
+// One block per chunk of kChunk consecutive particles.
+//  * Dequantization reads the code tables (k_dtable) when they exist; the
+//    particles of a leaf have nearby codes, so a warp's lookups touch few
+//    cache lines.
+//  * When the chunk holds at most kChunkLeaves leaves (always, unless leaves
+//    are tiny), the payload words it spans are staged in shared memory with
+//    coalesced loads and each particle's fields are cut from a 96-bit window
+//    with funnel shifts and per-leaf masks.  Otherwise each particle searches
+//    the leaf table and reads its words from global memory.
 template <typename T, bool FAST, bool VEC>
 __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
-  __shared__ __align__(16) T stage[3 * kChunk];
-  __shared__ __align__(16) uint32_t sw[kWordCap];
-  __shared__ uint64_t s_po[kChunkLeaves + 1], s_wo[kChunkLeaves + 1];
-  __shared__ int64_t s_base[kChunkLeaves];  // staged-relative bit of "particle 0" of the leaf, minus one field width
-  __shared__ int32_t s_q[kChunkLeaves][3];
-  __shared__ uint32_t s_m[kChunkLeaves + 1];
-  __shared__ int s_count, s_staged;
-  __shared__ uint64_t s_lo, s_hi, s_end;
+  __shared__ __align__(16) DecSmem<T> S;
   if (*a.err) return;  // validation failed: write nothing
-  const uint64_t c0 = uint64_t(blockIdx.x) * kChunk;
-  if (c0 >= a.n) return;
-  const uint64_t c1 = (c0 + kChunk) < a.n ? (c0 + kChunk) : a.n;
   const uint8_t *table = a.stream + kHeaderBytes;
   const uint32_t *words = reinterpret_cast<const uint32_t *>(table + uint64_t(kLeafBytes) * a.num_leaves);
-  const uint64_t first = a.chunk_leaf[blockIdx.x];
-  if (threadIdx.x < kChunkLeaves + 1) {
-    const uint64_t L = first + threadIdx.x;
-    if (L < a.num_leaves) {
-      const Rec r = load_rec(table, L);
-      s_po[threadIdx.x] = r.po;
-      s_wo[threadIdx.x] = r.wo;
-      s_m[threadIdx.x] = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
-      if (threadIdx.x < kChunkLeaves) {
-        s_q[threadIdx.x][0] = r.q[0];
-        s_q[threadIdx.x][1] = r.q[1];
-        s_q[threadIdx.x][2] = r.q[2];
+  uint32_t tb1 = 0, tb2 = 0, te = 0;
+  const bool use_table = table_fits(a.qb, tb1, tb2, te);
+  const T *tab0 = static_cast<const T *>(a.tab), *tab1 = tab0 + tb1, *tab2 = tab0 + tb2;
+  {
+    const uint64_t chunk = blockIdx.x;
+    const uint64_t c0 = chunk * kChunk;
+    const uint64_t c1 = (c0 + kChunk) < a.n ? (c0 + kChunk) : a.n;
+    const uint64_t first = a.chunk_leaf[chunk];
+    if (threadIdx.x < kChunkLeaves + 1) {
+      const uint64_t L = first + threadIdx.x;
+      if (L < a.num_leaves) {
+        const Rec r = load_rec(table, L);
+        S.po[threadIdx.x] = r.po;
+        S.wo[threadIdx.x] = r.wo;
+        S.mm[threadIdx.x] = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
+        if (threadIdx.x < kChunkLeaves) {
+          S.q[threadIdx.x][0] = r.q[0];
+          S.q[threadIdx.x][1] = r.q[1];
+          S.q[threadIdx.x][2] = r.q[2];
+        }
+      } else {
+        S.po[threadIdx.x] = a.n;
+        S.wo[threadIdx.x] = a.payload_words;
+        S.mm[threadIdx.x] = 0;
       }
-    } else {
-      s_po[threadIdx.x] = a.n;
-      s_wo[threadIdx.x] = a.payload_words;
-      s_m[threadIdx.x] = 0;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int c = 1;
-    while (c < kChunkLeaves && s_po[c] < c1) ++c;
-    s_count = c;
-    const bool in_smem = c < kChunkLeaves || s_po[kChunkLeaves] >= c1;
-    int staged = 0;
-    if (in_smem) {
-      // first bit of particle c0 and end bit of particle c1 - 1
-      auto width = [](uint32_t mm) { return uint64_t((mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu)); };
-      const uint64_t i0 = c0 - s_po[0];
-      const uint64_t b0 = 32 * s_wo[0] + (i0 ? (i0 - 1) * width(s_m[0]) : 0);
-      const uint64_t il = (c1 - 1) - s_po[c - 1];
-      const uint64_t b1 = 32 * s_wo[c - 1] + il * width(s_m[c - 1]);
-      const uint64_t lo = (b0 >> 5) & ~3ull;  // 16-byte aligned start of the staged words
-      const uint64_t end = ((b1 + 31) >> 5) + 4;  // words a particle's 4-word window may touch
-      if (end - lo <= kWordCap) {
-        staged = 1;
-        s_lo = lo;
-        s_end = end;
-        s_hi = end < a.payload_words ? end : a.payload_words;
-        for (int L = 0; L < c; ++L)
-          s_base[L] = int64_t(32 * s_wo[L]) - int64_t(32 * lo) - int64_t(width(s_m[L]));
-      }
-    }
-    s_staged = staged;
-  }
-  __syncthreads();
-  const int count = s_count;
-  T *stage_t = stage;
-  if (s_staged) {
-    const uint64_t lo = s_lo, hi = s_hi;
-    const uint32_t nst = uint32_t(s_end - lo);
-    const uint32_t nreal = hi > lo ? uint32_t(hi - lo) : 0u;
-    if ((reinterpret_cast<uintptr_t>(words) & 15) == 0) {
-      const uint32_t nvec = nreal >> 2;
-      const uint4 *src = reinterpret_cast<const uint4 *>(words + lo);
-      uint4 *dst = reinterpret_cast<uint4 *>(sw);
-      for (uint32_t v = threadIdx.x; v < nvec; v += kDecThreads) dst[v] = __ldg(src + v);
-      for (uint32_t w = 4 * nvec + threadIdx.x; w < nst; w += kDecThreads) sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
-    } else {
-      for (uint32_t w = threadIdx.x; w < nst; w += kDecThreads) sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kDecPer; ++k) {
-      const uint32_t sl = uint32_t(k) * kDecThreads + threadIdx.x;
-      const uint64_t g = c0 + sl;
-      if (g >= c1) continue;
-      int L = 0;
-      while (L + 1 < count && s_po[L + 1] <= g) ++L;
-      int32_t q0 = s_q[L][0], q1 = s_q[L][1], q2 = s_q[L][2];
-      const uint32_t i = uint32_t(g - s_po[L]);
-      if (i > 0) {
-        const uint32_t mm = s_m[L];
-        const uint32_t w = (mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu);
-        const uint32_t bit = uint32_t(s_base[L] + int64_t(uint64_t(i) * w));
-        const uint32_t wi = bit >> 5;
-        add_fields(sw[wi], sw[wi + 1], sw[wi + 2], sw[wi + 3], bit & 31u, mm, q0, q1, q2);
-      }
-      put_particle<T, FAST>(a, stage_t, sl, q0, q1, q2);
-    }
-  } else {
-    const bool in_smem = count < kChunkLeaves || s_po[kChunkLeaves] >= c1;
-#pragma unroll
-    for (int k = 0; k < kDecPer; ++k) {
-      const uint32_t sl = uint32_t(k) * kDecThreads + threadIdx.x;
-      const uint64_t g = c0 + sl;
-      if (g >= c1) continue;
-      uint64_t po, wo;
-      int32_t q0, q1, q2;
-      uint32_t mm;
+    if (threadIdx.x == 0) {
+      int c = 1;
+      while (c < kChunkLeaves && S.po[c] < c1) ++c;
+      S.count = c;
+      const bool in_smem = c < kChunkLeaves || S.po[kChunkLeaves] >= c1;
+      int staged = 0;
       if (in_smem) {
-        int L = 0;
-        while (L + 1 < count && s_po[L + 1] <= g) ++L;
-        po = s_po[L];
-        wo = s_wo[L];
-        q0 = s_q[L][0];
-        q1 = s_q[L][1];
-        q2 = s_q[L][2];
-        mm = s_m[L];
-      } else {  // many small leaves in this chunk: search the table
-        uint64_t lo = first, hi = a.num_leaves - 1;
-        while (lo < hi) {
-          const uint64_t mid = (lo + hi + 1) >> 1;
-          if (load_rec(table, mid).po <= g) lo = mid;
-          else hi = mid - 1;
+        // first bit of particle c0 and end bit of particle c1 - 1
+        auto width = [](uint32_t mm) { return uint64_t((mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu)); };
+        const uint64_t i0 = c0 - S.po[0];
+        const uint64_t b0 = 32 * S.wo[0] + (i0 ? (i0 - 1) * width(S.mm[0]) : 0);
+        const uint64_t il = (c1 - 1) - S.po[c - 1];
+        const uint64_t b1 = 32 * S.wo[c - 1] + il * width(S.mm[c - 1]);
+        const uint64_t lo = (b0 >> 5) & ~3ull;      // 16-byte aligned start of the staged words
+        const uint64_t end = ((b1 + 31) >> 5) + 4;  // words a particle's 4-word window may touch
+        if (end - lo <= kWordCap) {
+          staged = 1;
+          S.lo = lo;
+          S.end = end;
+          S.hi = end < a.payload_words ? end : a.payload_words;
         }
-        const Rec r = load_rec(table, lo);
-        po = r.po;
-        wo = r.wo;
-        q0 = r.q[0];
-        q1 = r.q[1];
-        q2 = r.q[2];
-        mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
       }
-      const uint64_t i = g - po;
-      if (i > 0) {
-        const uint32_t w = (mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu);
-        const uint64_t bit = 32ull * wo + (i - 1) * uint64_t(w);
-        const uint64_t wi = bit >> 5;
-        add_fields(word_at(words, a.payload_words, wi), word_at(words, a.payload_words, wi + 1),
-                   word_at(words, a.payload_words, wi + 2), word_at(words, a.payload_words, wi + 3),
-                   uint32_t(bit & 31), mm, q0, q1, q2);
-      }
-      put_particle<T, FAST>(a, stage_t, sl, q0, q1, q2);
+      S.staged = staged;
     }
-  }
-  __syncthreads();
-  T *out = static_cast<T *>(a.out) + 3 * c0;
-  const uint32_t total = uint32_t(3 * (c1 - c0));
-  if (VEC && (total % (16 / sizeof(T))) == 0) {
-    const uint32_t nv = total / (16 / sizeof(T));
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(stage);
-    uint4 *o4 = reinterpret_cast<uint4 *>(out);
-    for (uint32_t v = threadIdx.x; v < nv; v += kDecThreads) __stcs(o4 + v, s4[v]);
-  } else {
-    for (uint32_t v = threadIdx.x; v < total; v += kDecThreads) out[v] = stage[v];
+    __syncthreads();
+    const int count = S.count;
+    if (S.staged) {
+      const uint64_t lo = S.lo, hi = S.hi;
+      if (threadIdx.x < count) {
+        const int L = threadIdx.x;
+        const uint32_t mm = S.mm[L];
+        const uint32_t m0 = mm & 0xffu, m1 = (mm >> 8) & 0xffu, m2 = (mm >> 16) & 0xffu;
+        LeafC lc;
+        lc.rel = int32_t(int64_t(S.po[L]) - int64_t(c0));
+        lc.w = m0 + m1 + m2;
+        lc.base = int32_t(int64_t(32 * S.wo[L]) - int64_t(32 * lo) - int64_t(lc.w));
+        lc.m0 = m0;
+        lc.s2 = m0 + m1;
+        const uint32_t m[3] = {m0, m1, m2};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          lc.mask[d] = (1u << m[d]) - 1u;
+          lc.qref[d] = S.q[L][d];
+          lc.off[d] = S.q[L][d] - int32_t(m[d] ? (1u << (m[d] - 1)) - 1u : 0u);
+        }
+        lc.pad[0] = lc.pad[1] = 0;
+        S.lc[L] = lc;
+      }
+      const uint32_t nst = uint32_t(S.end - lo);
+      const uint32_t nreal = hi > lo ? uint32_t(hi - lo) : 0u;
+      if ((reinterpret_cast<uintptr_t>(words) & 15) == 0) {
+        const uint32_t nvec = nreal >> 2;
+        const uint4 *src = reinterpret_cast<const uint4 *>(words + lo);
+        uint4 *dst = reinterpret_cast<uint4 *>(S.sw);
+        for (uint32_t v = threadIdx.x; v < nvec; v += kDecThreads) dst[v] = __ldg(src + v);
+        for (uint32_t w = 4 * nvec + threadIdx.x; w < nst; w += kDecThreads)
+          S.sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
+      } else {
+        for (uint32_t w = threadIdx.x; w < nst; w += kDecThreads) S.sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
+      }
+      __syncthreads();
+      const int32_t nloc = int32_t(c1 - c0);
+#pragma unroll
+      for (int k = 0; k < kDecPer; ++k) {
+        const int32_t sl = k * kDecThreads + int32_t(threadIdx.x);
+        if (sl >= nloc) continue;
+        int L = 0;
+        while (L + 1 < count && S.lc[L + 1].rel <= sl) ++L;
+        const LeafC &lc = S.lc[L];
+        const uint32_t i = uint32_t(sl) - uint32_t(lc.rel);
+        int32_t q0, q1, q2;
+        if (i == 0) {
+          q0 = lc.qref[0];
+          q1 = lc.qref[1];
+          q2 = lc.qref[2];
+        } else {
+          const uint32_t bit = uint32_t(lc.base) + i * lc.w;  // modulo 2^32; the result is below 2^17
+          const uint32_t wi = bit >> 5, r0 = bit & 31u;
+          const uint32_t a0 = S.sw[wi], a1 = S.sw[wi + 1], a2 = S.sw[wi + 2], a3 = S.sw[wi + 3];
+          const uint32_t v0 = __funnelshift_r(a0, a1, r0);  // bits [bit, bit + 96) of the payload
+          const uint32_t v1 = __funnelshift_r(a1, a2, r0);
+          const uint32_t v2 = __funnelshift_r(a2, a3, r0);
+          const bool hi2 = lc.s2 >= 32;
+          q0 = lc.off[0] + int32_t(v0 & lc.mask[0]);
+          q1 = lc.off[1] + int32_t(__funnelshift_r(v0, v1, lc.m0) & lc.mask[1]);
+          q2 = lc.off[2] + int32_t(__funnelshift_r(hi2 ? v1 : v0, hi2 ? v2 : v1, lc.s2) & lc.mask[2]);
+        }
+        T x0, x1, x2;
+        if (use_table) {
+          x0 = __ldg(tab0 + q0);
+          x1 = __ldg(tab1 + q1);
+          x2 = __ldg(tab2 + q2);
+        } else {
+          x0 = dequant<T, FAST>(a, 0, q0);
+          x1 = dequant<T, FAST>(a, 1, q1);
+          x2 = dequant<T, FAST>(a, 2, q2);
+        }
+        S.stage[3 * sl] = x0;
+        S.stage[3 * sl + 1] = x1;
+        S.stage[3 * sl + 2] = x2;
+      }
+    } else {
+      const bool in_smem = count < kChunkLeaves || S.po[kChunkLeaves] >= c1;
+#pragma unroll
+      for (int k = 0; k < kDecPer; ++k) {
+        const uint32_t sl = uint32_t(k) * kDecThreads + threadIdx.x;
+        const uint64_t g = c0 + sl;
+        if (g >= c1) continue;
+        uint64_t po, wo;
+        int32_t q0, q1, q2;
+        uint32_t mm;
+        if (in_smem) {
+          int L = 0;
+          while (L + 1 < count && S.po[L + 1] <= g) ++L;
+          po = S.po[L];
+          wo = S.wo[L];
+          q0 = S.q[L][0];
+          q1 = S.q[L][1];
+          q2 = S.q[L][2];
+          mm = S.mm[L];
+        } else {  // many small leaves in this chunk: search the table
+          uint64_t lo = first, hi = a.num_leaves - 1;
+          while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (load_rec(table, mid).po <= g) lo = mid;
+            else hi = mid - 1;
+          }
+          const Rec r = load_rec(table, lo);
+          po = r.po;
+          wo = r.wo;
+          q0 = r.q[0];
+          q1 = r.q[1];
+          q2 = r.q[2];
+          mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
+        }
+        const uint64_t i = g - po;
+        if (i > 0) {
+          const uint32_t w = (mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu);
+          const uint64_t bit = 32ull * wo + (i - 1) * uint64_t(w);
+          const uint64_t wi = bit >> 5;
+          add_fields(word_at(words, a.payload_words, wi), word_at(words, a.payload_words, wi + 1),
+                     word_at(words, a.payload_words, wi + 2), word_at(words, a.payload_words, wi + 3),
+                     uint32_t(bit & 31), mm, q0, q1, q2);
+        }
+        T x0, x1, x2;
+        if (use_table) {
+          x0 = __ldg(tab0 + q0);
+          x1 = __ldg(tab1 + q1);
+          x2 = __ldg(tab2 + q2);
+        } else {
+          x0 = dequant<T, FAST>(a, 0, q0);
+          x1 = dequant<T, FAST>(a, 1, q1);
+          x2 = dequant<T, FAST>(a, 2, q2);
+        }
+        S.stage[3 * sl] = x0;
+        S.stage[3 * sl + 1] = x1;
+        S.stage[3 * sl + 2] = x2;
+      }
+    }
+    __syncthreads();
+    T *out = static_cast<T *>(a.out) + 3 * c0;
+    const uint32_t total = uint32_t(3 * (c1 - c0));
+    if (VEC && (total % (16 / sizeof(T))) == 0) {
+      const uint32_t nv = total / (16 / sizeof(T));
+      const uint4 *s4 = reinterpret_cast<const uint4 *>(S.stage);
+      uint4 *o4 = reinterpret_cast<uint4 *>(out);
+      for (uint32_t v = threadIdx.x; v < nv; v += kDecThreads) __stcs(o4 + v, s4[v]);
+    } else {
+      for (uint32_t v = threadIdx.x; v < total; v += kDecThreads) out[v] = S.stage[v];
+    }
   }
 }
 
@@ -336,17 +460,26 @@ __global__ void k_header(HeaderLaunch a) {
   *a.total_bytes = uint64_t(kHeaderBytes) + uint64_t(kLeafBytes) * a.num_leaves + 4ull * words;
 }
 
-template <typename T, bool FAST>
-void decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
-  const unsigned blocks = unsigned(decode_chunks(a.n));
+template <typename T, bool FAST, bool VEC>
+cudaError_t decode_launch(const DecodeLaunch &a, cudaStream_t st) {
+  {
+    TraceScope ts("k_dtable", st);
+    k_dtable<T, FAST><<<unsigned((kTabEntries + 255) / 256), 256, 0, st>>>(a);
+  }
   TraceScope ts("k_decode", st);
-  if (a.vec) k_decode<T, FAST, true><<<blocks, kDecThreads, 0, st>>>(a);
-  else k_decode<T, FAST, false><<<blocks, kDecThreads, 0, st>>>(a);
+  k_decode<T, FAST, VEC><<<unsigned(decode_chunks(a.n)), kDecThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, bool FAST>
+cudaError_t decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
+  return a.vec ? decode_launch<T, FAST, true>(a, st) : decode_launch<T, FAST, false>(a, st);
 }
 
 }  // namespace
 
 uint64_t decode_chunks(uint64_t n) { return (n + kChunk - 1) / kChunk; }
+uint64_t decode_table_bytes() { return uint64_t(kTabEntries) * sizeof(double); }
 
 cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st) {
   TraceScope ts("k_header", st);
@@ -359,15 +492,10 @@ cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st) {
   {
     TraceScope ts("k_validate", st);
     k_validate<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
-                                                                        a.chunk_leaf, a.err);
+                                                                        a.chunk_leaf, a.err, a.qb);
   }
-  if (a.dtype == 0) {
-    if (a.fast) decode_dispatch<float, true>(a, st);
-    else decode_dispatch<float, false>(a, st);
-  } else {
-    decode_dispatch<double, false>(a, st);
-  }
-  return cudaGetLastError();
+  if (a.dtype == 0) return a.fast ? decode_dispatch<float, true>(a, st) : decode_dispatch<float, false>(a, st);
+  return decode_dispatch<double, false>(a, st);
 }
 
 }  // namespace pcx

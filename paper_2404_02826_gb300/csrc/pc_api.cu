@@ -394,7 +394,10 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
 }
 
 // error word, then one u32 per decode chunk (its first particle's leaf)
-uint64_t decompress_ws_bytes(uint64_t n) { return kAlign + align_up(4 * decode_chunks(n)); }
+// error word and code bounds, the dequantization table, the chunk-to-leaf map
+uint64_t decompress_ws_bytes(uint64_t n) {
+  return kAlign + align_up(decode_table_bytes()) + align_up(4 * decode_chunks(n));
+}
 
 int parse_header(const uint8_t *h, uint64_t avail, pc_info *info) {
   if (avail < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
@@ -445,7 +448,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   if (!out_positions || reinterpret_cast<uintptr_t>(out_positions) % esz) return PC_ERR_ARG;
   if (workspace_bytes < decompress_ws_bytes(I.n)) return PC_ERR_CAPACITY;
   uint32_t *err = static_cast<uint32_t *>(workspace);
-  PC_TRY(cudaMemsetAsync(err, 0, 4, st));
+  PC_TRY(cudaMemsetAsync(err, 0, 64, st));  // error word and code bounds
   DecodeLaunch da = {};
   da.stream = static_cast<const uint8_t *>(stream_data);
   da.n = I.n;
@@ -465,7 +468,10 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   da.out = out_positions;
   da.vec = reinterpret_cast<uintptr_t>(out_positions) % 16 == 0;
   da.err = err;
-  da.chunk_leaf = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(workspace) + kAlign);
+  da.qb = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(workspace) + 32);
+  da.tab = static_cast<uint8_t *>(workspace) + kAlign;
+  da.chunk_leaf = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(workspace) + kAlign +
+                                               align_up(decode_table_bytes()));
   PC_TRY(launch_decode(da, st));
   uint32_t e = 0;
   PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));

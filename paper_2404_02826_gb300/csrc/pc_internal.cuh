@@ -270,10 +270,13 @@ struct DecodeLaunch {
   void *out;
   bool vec;
   uint32_t *err;
+  int32_t *qb;           // [6], zero on entry: per axis max(0, -lowest code), then highest code
+  void *tab;             // [decode_table_bytes()]: dequantized value of every code, when they fit
   uint32_t *chunk_leaf;  // [decode_chunks(n)]: leaf holding each chunk's first particle
 };
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
 uint64_t decode_chunks(uint64_t n);
+uint64_t decode_table_bytes();
 
 int device_sm_count();
 
