@@ -159,7 +159,6 @@ struct LeafC {
 
 template <typename T>
 struct DecSmem {
-  T stage[3 * kChunk];
   uint32_t sw[kWordCap];
   LeafC lc[kChunkLeaves];
   uint64_t po[kChunkLeaves + 1], wo[kChunkLeaves + 1];
@@ -198,6 +197,22 @@ __device__ __forceinline__ void add_fields(uint32_t w0, uint32_t w1, uint32_t w2
   if (m0) q0 += int32_t(window_bits(w0, w1, w2, w3, r0, m0)) - int32_t((1u << (m0 - 1)) - 1u);
   if (m1) q1 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0, m1)) - int32_t((1u << (m1 - 1)) - 1u);
   if (m2) q2 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0 + m1, m2)) - int32_t((1u << (m2 - 1)) - 1u);
+}
+
+// Dequantizes one particle's codes into v[0..2]: table lookups when the
+// tables exist, else the double expression.
+template <typename T, bool FAST>
+__device__ __forceinline__ void put3(const DecodeLaunch &a, bool use_table, const T *t0, const T *t1, const T *t2,
+                                     T &v0, T &v1, T &v2, int32_t q0, int32_t q1, int32_t q2) {
+  if (use_table) {
+    v0 = __ldg(t0 + q0);
+    v1 = __ldg(t1 + q1);
+    v2 = __ldg(t2 + q2);
+  } else {
+    v0 = dequant<T, FAST>(a, 0, q0);
+    v1 = dequant<T, FAST>(a, 1, q1);
+    v2 = dequant<T, FAST>(a, 2, q2);
+  }
 }
 
 // (T)(o_d + s q) for every code q in [0, qmax_d] of the three axes, one
@@ -284,6 +299,8 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
     }
     __syncthreads();
     const int count = S.count;
+    const int32_t nloc = int32_t(c1 - c0);
+    __align__(16) T vals[3 * kDecPer];
     if (S.staged) {
       const uint64_t lo = S.lo, hi = S.hi;
       if (threadIdx.x < count) {
@@ -319,53 +336,51 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
         for (uint32_t w = threadIdx.x; w < nst; w += kDecThreads) S.sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
       }
       __syncthreads();
-      const int32_t nloc = int32_t(c1 - c0);
-#pragma unroll
-      for (int k = 0; k < kDecPer; ++k) {
-        const int32_t sl = k * kDecThreads + int32_t(threadIdx.x);
-        if (sl >= nloc) continue;
+      // kDecPer consecutive particles per thread: one leaf lookup for the run
+      const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
+      if (sl0 < nloc) {
         int L = 0;
-        while (L + 1 < count && S.lc[L + 1].rel <= sl) ++L;
-        const LeafC &lc = S.lc[L];
-        const uint32_t i = uint32_t(sl) - uint32_t(lc.rel);
-        int32_t q0, q1, q2;
-        if (i == 0) {
-          q0 = lc.qref[0];
-          q1 = lc.qref[1];
-          q2 = lc.qref[2];
-        } else {
-          const uint32_t bit = uint32_t(lc.base) + i * lc.w;  // modulo 2^32; the result is below 2^17
-          const uint32_t wi = bit >> 5, r0 = bit & 31u;
-          const uint32_t a0 = S.sw[wi], a1 = S.sw[wi + 1], a2 = S.sw[wi + 2], a3 = S.sw[wi + 3];
-          const uint32_t v0 = __funnelshift_r(a0, a1, r0);  // bits [bit, bit + 96) of the payload
-          const uint32_t v1 = __funnelshift_r(a1, a2, r0);
-          const uint32_t v2 = __funnelshift_r(a2, a3, r0);
-          const bool hi2 = lc.s2 >= 32;
-          q0 = lc.off[0] + int32_t(v0 & lc.mask[0]);
-          q1 = lc.off[1] + int32_t(__funnelshift_r(v0, v1, lc.m0) & lc.mask[1]);
-          q2 = lc.off[2] + int32_t(__funnelshift_r(hi2 ? v1 : v0, hi2 ? v2 : v1, lc.s2) & lc.mask[2]);
+        while (L + 1 < count && S.lc[L + 1].rel <= sl0) ++L;
+        LeafC lc = S.lc[L];
+        int32_t next = L + 1 < count ? S.lc[L + 1].rel : 0x7fffffff;
+#pragma unroll
+        for (int k = 0; k < kDecPer; ++k) {
+          const int32_t sl = sl0 + k;
+          if (sl >= nloc) continue;
+          if (sl >= next) {  // the run crosses into the next leaf
+            ++L;
+            lc = S.lc[L];
+            next = L + 1 < count ? S.lc[L + 1].rel : 0x7fffffff;
+          }
+          const uint32_t i = uint32_t(sl) - uint32_t(lc.rel);
+          int32_t q0, q1, q2;
+          if (i == 0) {
+            q0 = lc.qref[0];
+            q1 = lc.qref[1];
+            q2 = lc.qref[2];
+          } else {
+            const uint32_t bit = uint32_t(lc.base) + i * lc.w;  // modulo 2^32; the result is below 2^17
+            const uint32_t wi = bit >> 5, r0 = bit & 31u;
+            const uint32_t a0 = S.sw[wi], a1 = S.sw[wi + 1], a2 = S.sw[wi + 2], a3 = S.sw[wi + 3];
+            const uint32_t v0 = __funnelshift_r(a0, a1, r0);  // bits [bit, bit + 96) of the payload
+            const uint32_t v1 = __funnelshift_r(a1, a2, r0);
+            const uint32_t v2 = __funnelshift_r(a2, a3, r0);
+            const bool hi2 = lc.s2 >= 32;
+            q0 = lc.off[0] + int32_t(v0 & lc.mask[0]);
+            q1 = lc.off[1] + int32_t(__funnelshift_r(v0, v1, lc.m0) & lc.mask[1]);
+            q2 = lc.off[2] + int32_t(__funnelshift_r(hi2 ? v1 : v0, hi2 ? v2 : v1, lc.s2) & lc.mask[2]);
+          }
+          put3<T, FAST>(a, use_table, tab0, tab1, tab2, vals[3 * k], vals[3 * k + 1], vals[3 * k + 2], q0, q1, q2);
         }
-        T x0, x1, x2;
-        if (use_table) {
-          x0 = __ldg(tab0 + q0);
-          x1 = __ldg(tab1 + q1);
-          x2 = __ldg(tab2 + q2);
-        } else {
-          x0 = dequant<T, FAST>(a, 0, q0);
-          x1 = dequant<T, FAST>(a, 1, q1);
-          x2 = dequant<T, FAST>(a, 2, q2);
-        }
-        S.stage[3 * sl] = x0;
-        S.stage[3 * sl + 1] = x1;
-        S.stage[3 * sl + 2] = x2;
       }
     } else {
       const bool in_smem = count < kChunkLeaves || S.po[kChunkLeaves] >= c1;
+      const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
 #pragma unroll
       for (int k = 0; k < kDecPer; ++k) {
-        const uint32_t sl = uint32_t(k) * kDecThreads + threadIdx.x;
-        const uint64_t g = c0 + sl;
-        if (g >= c1) continue;
+        const int32_t sl = sl0 + k;
+        if (sl >= nloc) continue;
+        const uint64_t g = c0 + uint64_t(sl);
         uint64_t po, wo;
         int32_t q0, q1, q2;
         uint32_t mm;
@@ -402,31 +417,25 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
                      word_at(words, a.payload_words, wi + 2), word_at(words, a.payload_words, wi + 3),
                      uint32_t(bit & 31), mm, q0, q1, q2);
         }
-        T x0, x1, x2;
-        if (use_table) {
-          x0 = __ldg(tab0 + q0);
-          x1 = __ldg(tab1 + q1);
-          x2 = __ldg(tab2 + q2);
-        } else {
-          x0 = dequant<T, FAST>(a, 0, q0);
-          x1 = dequant<T, FAST>(a, 1, q1);
-          x2 = dequant<T, FAST>(a, 2, q2);
-        }
-        S.stage[3 * sl] = x0;
-        S.stage[3 * sl + 1] = x1;
-        S.stage[3 * sl + 2] = x2;
+        put3<T, FAST>(a, use_table, tab0, tab1, tab2, vals[3 * k], vals[3 * k + 1], vals[3 * k + 2], q0, q1, q2);
       }
     }
-    __syncthreads();
-    T *out = static_cast<T *>(a.out) + 3 * c0;
-    const uint32_t total = uint32_t(3 * (c1 - c0));
-    if (VEC && (total % (16 / sizeof(T))) == 0) {
-      const uint32_t nv = total / (16 / sizeof(T));
-      const uint4 *s4 = reinterpret_cast<const uint4 *>(S.stage);
-      uint4 *o4 = reinterpret_cast<uint4 *>(out);
-      for (uint32_t v = threadIdx.x; v < nv; v += kDecThreads) __stcs(o4 + v, s4[v]);
-    } else {
-      for (uint32_t v = threadIdx.x; v < total; v += kDecThreads) out[v] = S.stage[v];
+    // the run's 3 * kDecPer values are consecutive in the output
+    const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
+    if (sl0 < nloc) {
+      T *out = static_cast<T *>(a.out) + 3 * (c0 + uint64_t(sl0));
+      if (VEC && sl0 + kDecPer <= nloc) {
+        constexpr int kVec = 3 * kDecPer * int(sizeof(T)) / 16;
+        uint4 *o4 = reinterpret_cast<uint4 *>(out);
+        const uint4 *v4 = reinterpret_cast<const uint4 *>(vals);
+#pragma unroll
+        for (int v = 0; v < kVec; ++v) __stcs(o4 + v, v4[v]);
+      } else {
+        const int m = 3 * min(kDecPer, nloc - sl0);
+#pragma unroll
+        for (int v = 0; v < 3 * kDecPer; ++v)
+          if (v < m) out[v] = vals[v];
+      }
     }
   }
 }
