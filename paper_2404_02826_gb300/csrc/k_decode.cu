@@ -55,13 +55,23 @@ __device__ __forceinline__ uint64_t leaf_words(const Rec &r, uint64_t cnt) {
   return ((uint64_t)(r.m[0] + r.m[1] + r.m[2]) * (cnt - 1) + 31) >> 5;
 }
 
+// What a decode chunk needs before it can start: its leaves and the payload
+// words its particles span (from a 16-byte aligned word, plus the 4-word read
+// window of its last particle).
+struct ChunkInfo {
+  uint64_t lo, end;     // staged words [lo, end) of the payload
+  uint32_t first, last;  // leaves of the chunk's first and last particle
+  uint32_t pad[2];
+};
+
 // One thread per leaf: every field and every neighbour relation is checked,
-// and each decode chunk whose first particle lies in this leaf records it.
+// and each decode chunk whose first particle lies in this leaf gets its first
+// leaf and first word, the chunk before it its last leaf and end word.
 // The range of codes a leaf can produce, [q_ref - 2^(m-1) + 1, q_ref + 2^(m-1)]
 // per axis (any m-bit field, the unused all-ones one included), is reduced
 // per warp into qb: qb[d] = max(0, -lowest code), qb[3 + d] = highest code.
 __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves, uint64_t words,
-                           uint32_t *chunk_leaf, uint32_t *err, int32_t *qb) {
+                           ChunkInfo *info, uint32_t *err, int32_t *qb) {
   const uint64_t L = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool mine = L < num_leaves;
   const uint8_t *table = stream + kHeaderBytes;
@@ -79,7 +89,22 @@ __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint6
     if (!ok) {
       atomicOr(err, kErrCorrupt);
     } else {
-      for (uint64_t c = (r.po + kChunk - 1) / kChunk; c * kChunk < pend; ++c) chunk_leaf[c] = uint32_t(L);
+      const uint64_t w = r.m[0] + r.m[1] + r.m[2];
+      for (uint64_t c = (r.po + kChunk - 1) / kChunk; c * kChunk < pend; ++c) {
+        const uint64_t c0 = c * kChunk;
+        const uint64_t bit = 32 * r.wo + (c0 > r.po ? (c0 - r.po - 1) * w : 0);  // first bit of particle c0
+        info[c].lo = (bit >> 5) & ~3ull;
+        info[c].first = uint32_t(L);
+        if (c > 0) {
+          info[c - 1].end = ((bit + 31) >> 5) + 4;
+          info[c - 1].last = c0 == r.po ? uint32_t(L - 1) : uint32_t(L);
+        }
+      }
+      if (L + 1 == num_leaves) {
+        const uint64_t c = (n - 1) / kChunk;
+        info[c].end = words + 4;
+        info[c].last = uint32_t(L);
+      }
       for (int d = 0; d < 3; ++d) {
         const int64_t half = r.m[d] ? (int64_t(1) << (r.m[d] - 1)) : 0;
         const int64_t lo = int64_t(r.q[d]) - (half ? half - 1 : 0), hi = int64_t(r.q[d]) + half;
@@ -161,11 +186,6 @@ template <typename T>
 struct DecSmem {
   uint32_t sw[kWordCap];
   LeafC lc[kChunkLeaves];
-  uint64_t po[kChunkLeaves + 1], wo[kChunkLeaves + 1];
-  uint32_t mm[kChunkLeaves + 1];
-  int32_t q[kChunkLeaves][3];
-  uint64_t lo, hi, end;
-  int count, staged;
 };
 
 // Whether every code lies in [0, qmax_d] with sum_d (qmax_d + 1) <= kTabEntries;
@@ -253,77 +273,32 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
     const uint64_t chunk = blockIdx.x;
     const uint64_t c0 = chunk * kChunk;
     const uint64_t c1 = (c0 + kChunk) < a.n ? (c0 + kChunk) : a.n;
-    const uint64_t first = a.chunk_leaf[chunk];
-    if (threadIdx.x < kChunkLeaves + 1) {
-      const uint64_t L = first + threadIdx.x;
-      if (L < a.num_leaves) {
-        const Rec r = load_rec(table, L);
-        S.po[threadIdx.x] = r.po;
-        S.wo[threadIdx.x] = r.wo;
-        S.mm[threadIdx.x] = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
-        if (threadIdx.x < kChunkLeaves) {
-          S.q[threadIdx.x][0] = r.q[0];
-          S.q[threadIdx.x][1] = r.q[1];
-          S.q[threadIdx.x][2] = r.q[2];
-        }
-      } else {
-        S.po[threadIdx.x] = a.n;
-        S.wo[threadIdx.x] = a.payload_words;
-        S.mm[threadIdx.x] = 0;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int c = 1;
-      while (c < kChunkLeaves && S.po[c] < c1) ++c;
-      S.count = c;
-      const bool in_smem = c < kChunkLeaves || S.po[kChunkLeaves] >= c1;
-      int staged = 0;
-      if (in_smem) {
-        // first bit of particle c0 and end bit of particle c1 - 1
-        auto width = [](uint32_t mm) { return uint64_t((mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu)); };
-        const uint64_t i0 = c0 - S.po[0];
-        const uint64_t b0 = 32 * S.wo[0] + (i0 ? (i0 - 1) * width(S.mm[0]) : 0);
-        const uint64_t il = (c1 - 1) - S.po[c - 1];
-        const uint64_t b1 = 32 * S.wo[c - 1] + il * width(S.mm[c - 1]);
-        const uint64_t lo = (b0 >> 5) & ~3ull;      // 16-byte aligned start of the staged words
-        const uint64_t end = ((b1 + 31) >> 5) + 4;  // words a particle's 4-word window may touch
-        if (end - lo <= kWordCap) {
-          staged = 1;
-          S.lo = lo;
-          S.end = end;
-          S.hi = end < a.payload_words ? end : a.payload_words;
-        }
-      }
-      S.staged = staged;
-    }
-    __syncthreads();
-    const int count = S.count;
+    const ChunkInfo ci = static_cast<const ChunkInfo *>(a.chunks)[chunk];
+    const uint32_t count = ci.last - ci.first + 1;
+    const bool staged = count <= uint32_t(kChunkLeaves) && ci.end - ci.lo <= uint64_t(kWordCap);
     const int32_t nloc = int32_t(c1 - c0);
     __align__(16) T vals[3 * kDecPer];
-    if (S.staged) {
-      const uint64_t lo = S.lo, hi = S.hi;
+    if (staged) {
+      const uint64_t lo = ci.lo, hi = ci.end < a.payload_words ? ci.end : a.payload_words;
       if (threadIdx.x < count) {
         const int L = threadIdx.x;
-        const uint32_t mm = S.mm[L];
-        const uint32_t m0 = mm & 0xffu, m1 = (mm >> 8) & 0xffu, m2 = (mm >> 16) & 0xffu;
+        const Rec r = load_rec(table, ci.first + L);
         LeafC lc;
-        lc.rel = int32_t(int64_t(S.po[L]) - int64_t(c0));
-        lc.w = m0 + m1 + m2;
-        lc.base = int32_t(int64_t(32 * S.wo[L]) - int64_t(32 * lo) - int64_t(lc.w));
-        lc.m0 = m0;
-        lc.s2 = m0 + m1;
-        const uint32_t m[3] = {m0, m1, m2};
+        lc.rel = int32_t(int64_t(r.po) - int64_t(c0));
+        lc.w = r.m[0] + r.m[1] + r.m[2];
+        lc.base = int32_t(int64_t(32 * r.wo) - int64_t(32 * lo) - int64_t(lc.w));
+        lc.m0 = r.m[0];
+        lc.s2 = r.m[0] + r.m[1];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          lc.mask[d] = (1u << m[d]) - 1u;
-          lc.qref[d] = S.q[L][d];
-          lc.off[d] = S.q[L][d] - int32_t(m[d] ? (1u << (m[d] - 1)) - 1u : 0u);
+          lc.mask[d] = (1u << r.m[d]) - 1u;
+          lc.qref[d] = r.q[d];
+          lc.off[d] = r.q[d] - int32_t(r.m[d] ? (1u << (r.m[d] - 1)) - 1u : 0u);
         }
         lc.pad[0] = lc.pad[1] = 0;
         S.lc[L] = lc;
       }
-      const uint32_t nst = uint32_t(S.end - lo);
+      const uint32_t nst = uint32_t(ci.end - lo);
       const uint32_t nreal = hi > lo ? uint32_t(hi - lo) : 0u;
       if ((reinterpret_cast<uintptr_t>(words) & 15) == 0) {
         const uint32_t nvec = nreal >> 2;
@@ -340,9 +315,9 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
       const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
       if (sl0 < nloc) {
         int L = 0;
-        while (L + 1 < count && S.lc[L + 1].rel <= sl0) ++L;
+        while (L + 1 < int(count) && S.lc[L + 1].rel <= sl0) ++L;
         LeafC lc = S.lc[L];
-        int32_t next = L + 1 < count ? S.lc[L + 1].rel : 0x7fffffff;
+        int32_t next = L + 1 < int(count) ? S.lc[L + 1].rel : 0x7fffffff;
 #pragma unroll
         for (int k = 0; k < kDecPer; ++k) {
           const int32_t sl = sl0 + k;
@@ -350,7 +325,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
           if (sl >= next) {  // the run crosses into the next leaf
             ++L;
             lc = S.lc[L];
-            next = L + 1 < count ? S.lc[L + 1].rel : 0x7fffffff;
+            next = L + 1 < int(count) ? S.lc[L + 1].rel : 0x7fffffff;
           }
           const uint32_t i = uint32_t(sl) - uint32_t(lc.rel);
           int32_t q0, q1, q2;
@@ -374,40 +349,23 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
         }
       }
     } else {
-      const bool in_smem = count < kChunkLeaves || S.po[kChunkLeaves] >= c1;
       const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
 #pragma unroll
       for (int k = 0; k < kDecPer; ++k) {
         const int32_t sl = sl0 + k;
         if (sl >= nloc) continue;
         const uint64_t g = c0 + uint64_t(sl);
-        uint64_t po, wo;
-        int32_t q0, q1, q2;
-        uint32_t mm;
-        if (in_smem) {
-          int L = 0;
-          while (L + 1 < count && S.po[L + 1] <= g) ++L;
-          po = S.po[L];
-          wo = S.wo[L];
-          q0 = S.q[L][0];
-          q1 = S.q[L][1];
-          q2 = S.q[L][2];
-          mm = S.mm[L];
-        } else {  // many small leaves in this chunk: search the table
-          uint64_t lo = first, hi = a.num_leaves - 1;
-          while (lo < hi) {
-            const uint64_t mid = (lo + hi + 1) >> 1;
-            if (load_rec(table, mid).po <= g) lo = mid;
-            else hi = mid - 1;
-          }
-          const Rec r = load_rec(table, lo);
-          po = r.po;
-          wo = r.wo;
-          q0 = r.q[0];
-          q1 = r.q[1];
-          q2 = r.q[2];
-          mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
+        // many leaves, or a span beyond the staging area: search the leaf table
+        uint64_t lo = ci.first, hi = ci.last;
+        while (lo < hi) {
+          const uint64_t mid = (lo + hi + 1) >> 1;
+          if (load_rec(table, mid).po <= g) lo = mid;
+          else hi = mid - 1;
         }
+        const Rec r = load_rec(table, lo);
+        const uint64_t po = r.po, wo = r.wo;
+        int32_t q0 = r.q[0], q1 = r.q[1], q2 = r.q[2];
+        const uint32_t mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
         const uint64_t i = g - po;
         if (i > 0) {
           const uint32_t w = (mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu);
@@ -489,6 +447,7 @@ cudaError_t decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
 
 uint64_t decode_chunks(uint64_t n) { return (n + kChunk - 1) / kChunk; }
 uint64_t decode_table_bytes() { return uint64_t(kTabEntries) * sizeof(double); }
+uint64_t decode_chunk_bytes(uint64_t n) { return decode_chunks(n) * sizeof(ChunkInfo); }
 
 cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st) {
   TraceScope ts("k_header", st);
@@ -501,7 +460,7 @@ cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st) {
   {
     TraceScope ts("k_validate", st);
     k_validate<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
-                                                                        a.chunk_leaf, a.err, a.qb);
+                                                                        static_cast<ChunkInfo *>(a.chunks), a.err, a.qb);
   }
   if (a.dtype == 0) return a.fast ? decode_dispatch<float, true>(a, st) : decode_dispatch<float, false>(a, st);
   return decode_dispatch<double, false>(a, st);

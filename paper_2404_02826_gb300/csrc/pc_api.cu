@@ -394,9 +394,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
 }
 
 // error word, then one u32 per decode chunk (its first particle's leaf)
-// error word and code bounds, the dequantization table, the chunk-to-leaf map
+// error word and code bounds, the dequantization table, the per-chunk facts
 uint64_t decompress_ws_bytes(uint64_t n) {
-  return kAlign + align_up(decode_table_bytes()) + align_up(4 * decode_chunks(n));
+  return kAlign + align_up(decode_table_bytes()) + align_up(decode_chunk_bytes(n));
 }
 
 int parse_header(const uint8_t *h, uint64_t avail, pc_info *info) {
@@ -470,8 +470,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   da.err = err;
   da.qb = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(workspace) + 32);
   da.tab = static_cast<uint8_t *>(workspace) + kAlign;
-  da.chunk_leaf = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(workspace) + kAlign +
-                                               align_up(decode_table_bytes()));
+  da.chunks = static_cast<uint8_t *>(workspace) + kAlign + align_up(decode_table_bytes());
   PC_TRY(launch_decode(da, st));
   uint32_t e = 0;
   PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));

@@ -272,11 +272,12 @@ struct DecodeLaunch {
   uint32_t *err;
   int32_t *qb;           // [6], zero on entry: per axis max(0, -lowest code), then highest code
   void *tab;             // [decode_table_bytes()]: dequantized value of every code, when they fit
-  uint32_t *chunk_leaf;  // [decode_chunks(n)]: leaf holding each chunk's first particle
+  void *chunks;          // [decode_chunk_bytes(n)]: per decode chunk, its leaves and payload words
 };
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
 uint64_t decode_chunks(uint64_t n);
 uint64_t decode_table_bytes();
+uint64_t decode_chunk_bytes(uint64_t n);
 
 int device_sm_count();
 
