@@ -11,7 +11,11 @@
 // within 2^-20 of one half, the literal double-precision expression decides.
 // Outside that window the float-pair value is within 2^-21 of the exact
 // quotient (codes < 2^22), so it and the double-precision quotient round to
-// the same integer.  Codes are written as structure-of-arrays (u16 or u32).
+// the same integer.  For double input the subtraction stays in double, the
+// quotient is formed as (p - o) * fl(1/s) and rounded with integer operations
+// on its bits; within 2^-20 of one half (products are within 2^-51 relative,
+// so under 2^-20 absolute, of the double quotient) the division decides.
+// Codes are written as structure-of-arrays (u16 or u32).
 #include <cfloat>
 #include <cstdint>
 
@@ -262,6 +266,34 @@ __device__ __forceinline__ uint32_t quant_fast(float p, float o, double od, doub
   return quant_exact_call(p, od, s);
 }
 
+__device__ __noinline__ uint32_t quant_exact_call64(double p, double o, double s) { return quant_exact(p, o, s); }
+
+// Same result for double input with two double operations: t = (p - o) * inv
+// and the round-to-nearest-even of t taken from its bits (t >= 0, as o is the
+// minimum), unless t lies within 2^-20 of a half-integer or at 2^31 or above.
+__device__ __forceinline__ uint32_t quant_fast64(double p, double o, double s, double inv) {
+  const double t = __dmul_rn(__dsub_rn(p, o), inv);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  const int e = int((b >> 52) & 0x7ff) - 1023;  // t in [2^e, 2^(e+1))
+  const unsigned long long mant = (b & 0xfffffffffffffull) | (1ull << 52);
+  uint32_t q = 0;
+  bool ok;
+  if (e <= -3) {
+    ok = true;  // t < 1/4
+  } else if (e == -2) {
+    ok = (b & 0xfffffffffffffull) < (1ull << 52) - (1ull << 34);  // t < 1/2 - 2^-20
+  } else if (e <= 30) {
+    const int F = 52 - e;  // fraction bits of t, 22 .. 53
+    const unsigned long long fr = mant & ((1ull << F) - 1), half = 1ull << (F - 1), mg = 1ull << (F - 20);
+    ok = fr + mg < half || fr > half + mg;
+    q = uint32_t(mant >> F) + (fr > half ? 1u : 0u);
+  } else {
+    ok = false;
+  }
+  if (__builtin_expect(ok, 1)) return q;
+  return quant_exact_call64(p, o, s);
+}
+
 template <typename C>
 struct CodeVec;
 template <>
@@ -321,12 +353,16 @@ __global__ void __launch_bounds__(kThreads) k_quant_f32(const float *__restrict_
   }
 }
 
-template <typename C, bool VEC>
+template <typename C, bool VEC, bool FAST>
 __global__ void __launch_bounds__(kThreads) k_quant_f64(const double *__restrict__ pos, uint64_t n, QuantParams qp,
                                                         C *__restrict__ qx, C *__restrict__ qy, C *__restrict__ qz,
                                                         uint32_t *__restrict__ idx) {
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  auto quant_exact = [&](double p, double o, double s) -> uint32_t {
+    if (FAST) return quant_fast64(p, o, s, qp.inv);
+    return pcx::quant_exact(p, o, s);
+  };
   uint64_t done = 0;
   if (VEC) {
     const double2 *p2 = reinterpret_cast<const double2 *>(pos);
@@ -360,8 +396,13 @@ cudaError_t quant_dispatch(const QuantLaunch &a, cudaStream_t st) {
     else k_quant_f32<C, false, false><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
   } else {
     const double *p = static_cast<const double *>(a.pos);
-    if (a.vec) k_quant_f64<C, true><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
-    else k_quant_f64<C, false><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
+    if (a.fast) {
+      if (a.vec) k_quant_f64<C, true, true><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
+      else k_quant_f64<C, false, true><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
+    } else {
+      if (a.vec) k_quant_f64<C, true, false><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
+      else k_quant_f64<C, false, false><<<a.blocks, kThreads, 0, st>>>(p, a.n, a.qp, qx, qy, qz, a.idx);
+    }
   }
   return cudaGetLastError();
 }

@@ -312,7 +312,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     const double inv = 1.0 / L.s;
     qa.qp.rh = float(inv);
     qa.qp.rl = float(inv - double(qa.qp.rh));
-    qa.fast = dtype == PC_F32 && qmax < (1u << 22) && inv > 0x1p-100 && inv < 0x1p100;
+    qa.qp.inv = inv;
+    qa.fast = dtype == PC_F32 ? (qmax < (1u << 22) && inv > 0x1p-100 && inv < 0x1p100)
+                              : (inv > 0x1p-1000 && inv < 0x1p1000);
     qa.idx = idx_a;
     qa.blocks = 8 * device_sm_count();
     PC_TRY(launch_quantize(qa, st));

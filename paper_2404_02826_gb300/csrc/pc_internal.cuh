@@ -34,6 +34,7 @@ struct QuantParams {
   double s;      // step 2 eb'
   float of[3];   // origin as float (exact for float input)
   float rh, rl;  // 1/s as an unevaluated float sum rh + rl
+  double inv;    // fl(1/s)
 };
 
 // Per-node state of one global k-d level (Sec. 4.1 median split by radix select).

@@ -136,6 +136,13 @@ def test_parity_float32_exact_division_path(pc, oracle_mod):
     check_against_oracle(pc, oracle_mod, pos, pc.PC_EB_ABS, eps, 4096)
 
 
+def test_parity_float64_wide_codes(pc, oracle_mod):
+    """float64 input with codes near 2^29: the quantizer's rounding from the
+    bits of (p - o) * (1/s) at its widest, and its division fallback."""
+    pos = synth.uniform(50_000, seed=6, box=1.0, dtype=np.float64)
+    check_against_oracle(pc, oracle_mod, pos, pc.PC_EB_ABS, 1e-9, 4096)
+
+
 def test_parity_without_perm(pc, oracle_mod):
     pos = synth.cosmology(120_000, seed=8)
     check_against_oracle(pc, oracle_mod, pos, pc.PC_EB_REL, 1e-4, 4096, with_perm=False)
