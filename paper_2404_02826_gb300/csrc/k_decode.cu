@@ -69,13 +69,13 @@ struct ChunkInfo {
 // leaf and first word, the chunk before it its last leaf and end word.
 // The range of codes a leaf can produce, [q_ref - 2^(m-1) + 1, q_ref + 2^(m-1)]
 // per axis (any m-bit field, the unused all-ones one included), is reduced
-// per warp into qb: qb[d] = max(0, -lowest code), qb[3 + d] = highest code.
+// per warp into qb: qb[d] = min(0, lowest code), qb[3 + d] = max(0, highest).
 __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves, uint64_t words,
                            ChunkInfo *info, uint32_t *err, int32_t *qb) {
   const uint64_t L = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool mine = L < num_leaves;
   const uint8_t *table = stream + kHeaderBytes;
-  int32_t neg[3] = {0, 0, 0}, top[3] = {0, 0, 0};
+  int32_t low[3] = {0, 0, 0}, top[3] = {0, 0, 0};
   if (mine) {
     const Rec r = load_rec(table, L);
     const uint64_t pend = (L + 1 < num_leaves) ? load_rec(table, L + 1).po : n;
@@ -108,20 +108,20 @@ __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint6
       for (int d = 0; d < 3; ++d) {
         const int64_t half = r.m[d] ? (int64_t(1) << (r.m[d] - 1)) : 0;
         const int64_t lo = int64_t(r.q[d]) - (half ? half - 1 : 0), hi = int64_t(r.q[d]) + half;
-        neg[d] = int32_t(lo >= 0 ? 0 : (-lo > 0x7fffffff ? 0x7fffffff : -lo));
-        top[d] = int32_t(hi <= 0 ? 0 : (hi > 0x7fffffff ? 0x7fffffff : hi));
+        low[d] = int32_t(lo >= 0 ? 0 : (lo < -0x7fffffffll ? -0x7fffffffll : lo));
+        top[d] = int32_t(hi <= 0 ? 0 : (hi > 0x7fffffffll ? 0x7fffffffll : hi));
       }
     }
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    neg[d] = __reduce_max_sync(0xffffffffu, neg[d]);
+    low[d] = __reduce_min_sync(0xffffffffu, low[d]);
     top[d] = __reduce_max_sync(0xffffffffu, top[d]);
   }
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      if (neg[d]) atomicMax(qb + d, neg[d]);
+      if (low[d]) atomicMin(qb + d, low[d]);
       if (top[d]) atomicMax(qb + 3 + d, top[d]);
     }
   }
@@ -188,15 +188,16 @@ struct DecSmem {
   LeafC lc[kChunkLeaves];
 };
 
-// Whether every code lies in [0, qmax_d] with sum_d (qmax_d + 1) <= kTabEntries;
-// then tb1, tb2 are where the y and z tables start.
-__device__ __forceinline__ bool table_fits(const int32_t *qb, uint32_t &tb1, uint32_t &tb2, uint32_t &te) {
-  if (qb[0] | qb[1] | qb[2]) return false;
-  const uint64_t e0 = uint64_t(qb[3]) + 1, e1 = uint64_t(qb[4]) + 1, e2 = uint64_t(qb[5]) + 1;
-  tb1 = uint32_t(e0);
-  tb2 = uint32_t(e0 + e1);
-  te = uint32_t(e0 + e1 + e2);
-  return e0 + e1 + e2 <= kTabEntries;
+// Whether the code ranges [lo_d, hi_d] of the three axes fit kTabEntries
+// entries together; tb[d] is where axis d's table starts.
+__device__ __forceinline__ bool table_fits(const int32_t *qb, uint32_t tb[3], uint32_t &te) {
+  uint64_t e = 0;
+  for (int d = 0; d < 3; ++d) {
+    tb[d] = uint32_t(e);
+    e += uint64_t(int64_t(qb[3 + d]) - int64_t(qb[d]) + 1);
+  }
+  te = uint32_t(e < kTabEntries ? e : kTabEntries);
+  return e <= kTabEntries;
 }
 
 // (T)(o_d + s q) by the double expression; float output on the FP32 pipe when exact.
@@ -235,18 +236,18 @@ __device__ __forceinline__ void put3(const DecodeLaunch &a, bool use_table, cons
   }
 }
 
-// (T)(o_d + s q) for every code q in [0, qmax_d] of the three axes, one
+// (T)(o_d + s q) for every code q in [lo_d, hi_d] of the three axes, one
 // table after another: the dequantization of a particle becomes three
 // lookups, and the double expression is evaluated once per code.
 template <typename T, bool FAST>
 __global__ void k_dtable(DecodeLaunch a) {
   if (*a.err) return;
-  uint32_t tb1, tb2, te;
-  if (!table_fits(a.qb, tb1, tb2, te)) return;
+  uint32_t tb[3], te;
+  if (!table_fits(a.qb, tb, te)) return;
   T *tab = static_cast<T *>(a.tab);
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < te; e += gridDim.x * blockDim.x) {
-    const int d = e < tb1 ? 0 : (e < tb2 ? 1 : 2);
-    const int32_t q = int32_t(e - (d == 0 ? 0u : (d == 1 ? tb1 : tb2)));
+    const int d = e < tb[1] ? 0 : (e < tb[2] ? 1 : 2);
+    const int32_t q = a.qb[d] + int32_t(e - tb[d]);
     tab[e] = dequant<T, FAST>(a, d, q);
   }
 }
@@ -266,9 +267,12 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
   if (*a.err) return;  // validation failed: write nothing
   const uint8_t *table = a.stream + kHeaderBytes;
   const uint32_t *words = reinterpret_cast<const uint32_t *>(table + uint64_t(kLeafBytes) * a.num_leaves);
-  uint32_t tb1 = 0, tb2 = 0, te = 0;
-  const bool use_table = table_fits(a.qb, tb1, tb2, te);
-  const T *tab0 = static_cast<const T *>(a.tab), *tab1 = tab0 + tb1, *tab2 = tab0 + tb2;
+  uint32_t tb[3], te = 0;
+  const bool use_table = table_fits(a.qb, tb, te);
+  // table of axis d indexed by the code itself: its start minus the lowest code
+  const T *tabs = static_cast<const T *>(a.tab);
+  const T *tab0 = tabs + (int64_t(tb[0]) - a.qb[0]), *tab1 = tabs + (int64_t(tb[1]) - a.qb[1]),
+          *tab2 = tabs + (int64_t(tb[2]) - a.qb[2]);
   {
     const uint64_t chunk = blockIdx.x;
     const uint64_t c0 = chunk * kChunk;

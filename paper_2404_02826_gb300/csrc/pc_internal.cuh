@@ -271,7 +271,7 @@ struct DecodeLaunch {
   void *out;
   bool vec;
   uint32_t *err;
-  int32_t *qb;           // [6], zero on entry: per axis max(0, -lowest code), then highest code
+  int32_t *qb;           // [6], zero on entry: per axis min(0, lowest code), then max(0, highest code)
   void *tab;             // [decode_table_bytes()]: dequantized value of every code, when they fit
   void *chunks;          // [decode_chunk_bytes(n)]: per decode chunk, its leaves and payload words
 };
