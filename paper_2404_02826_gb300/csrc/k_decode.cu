@@ -210,6 +210,21 @@ __device__ __forceinline__ T dequant(const DecodeLaunch &a, int d, int32_t q) {
   return (T)__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q));
 }
 
+// The same for the per-particle path when there are no tables.  Float output
+// with the float-pair check stays inline (FP32 pipe); the double expression
+// is kept out of line, so that it is not evaluated speculatively on GB300's
+// narrow FP64 pipe beside the table lookups.
+template <typename T>
+__device__ __noinline__ T dequant_double_call(const DecodeLaunch &a, int d, int32_t q) {
+  if (sizeof(T) == 4) return (T)dequant_exact(q, a.o[d], a.s);
+  return (T)__dadd_rn(a.o[d], __dmul_rn(a.s, (double)q));
+}
+template <typename T, bool FAST>
+__device__ __forceinline__ T dequant_particle(const DecodeLaunch &a, int d, int32_t q) {
+  if (sizeof(T) == 4 && FAST) return (T)dequant_fast(q, a.of[d], a.o[d], a.s, a.sh, a.sl);
+  return dequant_double_call<T>(a, d, q);
+}
+
 // c = code - (2^(m-1) - 1) for the three fields of one particle starting at
 // bit r0 of the 4-word window.
 __device__ __forceinline__ void add_fields(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t r0,
@@ -218,22 +233,6 @@ __device__ __forceinline__ void add_fields(uint32_t w0, uint32_t w1, uint32_t w2
   if (m0) q0 += int32_t(window_bits(w0, w1, w2, w3, r0, m0)) - int32_t((1u << (m0 - 1)) - 1u);
   if (m1) q1 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0, m1)) - int32_t((1u << (m1 - 1)) - 1u);
   if (m2) q2 += int32_t(window_bits(w0, w1, w2, w3, r0 + m0 + m1, m2)) - int32_t((1u << (m2 - 1)) - 1u);
-}
-
-// Dequantizes one particle's codes into v[0..2]: table lookups when the
-// tables exist, else the double expression.
-template <typename T, bool FAST>
-__device__ __forceinline__ void put3(const DecodeLaunch &a, bool use_table, const T *t0, const T *t1, const T *t2,
-                                     T &v0, T &v1, T &v2, int32_t q0, int32_t q1, int32_t q2) {
-  if (use_table) {
-    v0 = __ldg(t0 + q0);
-    v1 = __ldg(t1 + q1);
-    v2 = __ldg(t2 + q2);
-  } else {
-    v0 = dequant<T, FAST>(a, 0, q0);
-    v1 = dequant<T, FAST>(a, 1, q1);
-    v2 = dequant<T, FAST>(a, 2, q2);
-  }
 }
 
 // (T)(o_d + s q) for every code q in [lo_d, hi_d] of the three axes, one
@@ -282,6 +281,9 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
     const bool staged = count <= uint32_t(kChunkLeaves) && ci.end - ci.lo <= uint64_t(kWordCap);
     const int32_t nloc = int32_t(c1 - c0);
     __align__(16) T vals[3 * kDecPer];
+    int32_t qs[3 * kDecPer];  // codes of the run; unused slots hold the lowest code, a valid table index
+#pragma unroll
+    for (int v = 0; v < 3 * kDecPer; ++v) qs[v] = a.qb[v % 3];
     if (staged) {
       const uint64_t lo = ci.lo, hi = ci.end < a.payload_words ? ci.end : a.payload_words;
       if (threadIdx.x < count) {
@@ -349,7 +351,9 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
             q1 = lc.off[1] + int32_t(__funnelshift_r(v0, v1, lc.m0) & lc.mask[1]);
             q2 = lc.off[2] + int32_t(__funnelshift_r(hi2 ? v1 : v0, hi2 ? v2 : v1, lc.s2) & lc.mask[2]);
           }
-          put3<T, FAST>(a, use_table, tab0, tab1, tab2, vals[3 * k], vals[3 * k + 1], vals[3 * k + 2], q0, q1, q2);
+          qs[3 * k] = q0;
+          qs[3 * k + 1] = q1;
+          qs[3 * k + 2] = q2;
         }
       }
     } else {
@@ -379,8 +383,18 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
                      word_at(words, a.payload_words, wi + 2), word_at(words, a.payload_words, wi + 3),
                      uint32_t(bit & 31), mm, q0, q1, q2);
         }
-        put3<T, FAST>(a, use_table, tab0, tab1, tab2, vals[3 * k], vals[3 * k + 1], vals[3 * k + 2], q0, q1, q2);
+        qs[3 * k] = q0;
+        qs[3 * k + 1] = q1;
+        qs[3 * k + 2] = q2;
       }
+    }
+    // dequantize the run: all lookups issued together
+    if (use_table) {
+#pragma unroll
+      for (int v = 0; v < 3 * kDecPer; ++v) vals[v] = __ldg((v % 3 == 0 ? tab0 : (v % 3 == 1 ? tab1 : tab2)) + qs[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 3 * kDecPer; ++v) vals[v] = dequant_particle<T, FAST>(a, v % 3, qs[v]);
     }
     // the run's 3 * kDecPer values are consecutive in the output
     const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
