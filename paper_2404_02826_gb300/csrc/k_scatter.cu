@@ -16,9 +16,7 @@
 //               every (round, warp) into prefixes, and each particle's place in
 //               its child follows from its prefix and the popcount of the
 //               masks below its lane.  Stores to each child are contiguous
-//               across a warp.  The children's code bounds on the next axis are
-//               reduced per CTA and folded in with an atomic only when they
-//               improve the stored bound.
+//               across a warp.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -54,12 +52,10 @@ struct Smem {
   alignas(16) uint32_t wc[F::kRounds * kWarps];  // (less << 16 | tie) per round and warp
   uint2 msk[F::kRounds * kWarps];                // ("code < v", "code == v") ballots per round and warp
   uint2 pref[F::kRounds * kWarps];               // (left-going, ties) in the node before each round and warp
-  uint32_t red[4][kWarps];
   unsigned long long bar[2];
   unsigned long long pre[2];  // (less << 31 | tie) of the node's tiles before this one
   uint32_t tile[2];
   uint32_t v[2], tleft[2];
-  uint2 cb[2][2];  // children's (lo, hi) as read when the tile was issued
   TileGeom geo[2];
 };
 
@@ -126,11 +122,10 @@ __device__ __forceinline__ TileGeom tile_geom(const LevelLaunch &a, uint32_t t) 
 struct Pending {
   uint32_t v, tl;
   unsigned long long pre;
-  uint2 c0, c1;  // children's stored (lo, hi); bounds only tighten, so an old value is a safe filter
 };
 
 // Thread 0: copies the window of tile t into buffer b and starts the loads of
-// its node, its prefix counts and its children's bounds.
+// its node and its prefix counts.
 template <typename C, bool IDX>
 __device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S, uint32_t t, int b, Pending &p) {
   const TileGeom g = tile_geom(a, t);
@@ -146,10 +141,6 @@ __device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S
   p.v = a.nodes[g.j].v;
   p.tl = a.nodes[g.j].tleft;
   p.pre = a.tile_state[t];
-  if (a.children) {
-    p.c0 = __ldcg(reinterpret_cast<const uint2 *>(&a.children[2 * g.j].lo));
-    p.c1 = __ldcg(reinterpret_cast<const uint2 *>(&a.children[2 * g.j + 1].lo));
-  }
 }
 
 template <typename C, bool IDX>
@@ -157,8 +148,6 @@ __device__ __forceinline__ void publish(Smem<C, IDX> &S, int b, const Pending &p
   S.v[b] = p.v;
   S.tleft[b] = p.tl;
   S.pre[b] = p.pre;
-  S.cb[b][0] = p.c0;
-  S.cb[b][1] = p.c1;
 }
 
 // Persistent CTA.  Thread 0 keeps one ticket and one tile copy ahead of the
@@ -169,7 +158,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
   using F = Cfg<C, IDX>;
   constexpr int kPer = F::kRounds * kWarps / 32;  // scan entries per lane of warp 0
   static_assert(kPer == 4 || kPer == 8, "scan entries per lane");
-  constexpr int NXT = (AXIS + 1) % 3;
   extern __shared__ __align__(128) unsigned char smraw[];
   Smem<C, IDX> &S = *reinterpret_cast<Smem<C, IDX> *>(smraw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -194,7 +182,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
   C *d1 = static_cast<C *>(a.dst[1]);
   C *d2 = static_cast<C *>(a.dst[2]);
   const uint32_t lt_mask = (1u << lane) - 1u, lane_bit = 1u << lane;
-  const bool bounds = a.children != nullptr;
   for (;;) {
     const uint32_t t = S.tile[b];
     if (t >= tiles) break;
@@ -282,7 +269,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
     //    consecutive particles, so each child's run is contiguous across a warp
     const uint32_t cnt = g.cnt;
     const uint32_t kpos = k + (g.tb - g.off) - lead;  // k + node position of window slot 0
-    uint32_t cmin0 = 0xffffffffu, cmax0 = 0, cmin1 = 0xffffffffu, cmax1 = 0;
     for (uint32_t r = 0; r < rounds; ++r) {
       const uint32_t wp = r * kThreads + threadIdx.x;
       const uint2 mk = S.msk[r * kWarps + warp];
@@ -310,55 +296,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
         } else {
           atomicOr(a.err, kErrInternal);
         }
-        if (bounds) {
-          const uint32_t xn = NXT == 0 ? x0 : (NXT == 1 ? x1 : x2);
-          if (left) {
-            cmin0 = min(cmin0, xn);
-            cmax0 = max(cmax0, xn);
-          } else {
-            cmin1 = min(cmin1, xn);
-            cmax1 = max(cmax1, xn);
-          }
-        }
       }
     }
-    // 4. children bounds on the next axis: per warp, then warp 0 folds them in
-    if (bounds) {
-      cmin0 = __reduce_min_sync(0xffffffffu, cmin0);
-      cmax0 = __reduce_max_sync(0xffffffffu, cmax0);
-      cmin1 = __reduce_min_sync(0xffffffffu, cmin1);
-      cmax1 = __reduce_max_sync(0xffffffffu, cmax1);
-      if (lane == 0) {
-        S.red[0][warp] = cmin0;
-        S.red[1][warp] = cmax0;
-        S.red[2][warp] = cmin1;
-        S.red[3][warp] = cmax1;
-      }
+    if (threadIdx.x == 0) {
+      if (prefetched) publish(S, b ^ 1, pend);
+      next_t = after;
     }
-    if (threadIdx.x == 0 && prefetched) publish(S, b ^ 1, pend);
-    __syncthreads();  // the next tile's state is published; S.red is complete
-    if (warp == 0) {
-      if (bounds) {
-        const bool in = lane < kWarps;
-        const uint32_t m0 = __reduce_min_sync(0xffffffffu, in ? S.red[0][lane] : 0xffffffffu);
-        const uint32_t x0 = __reduce_max_sync(0xffffffffu, in ? S.red[1][lane] : 0u);
-        const uint32_t m1 = __reduce_min_sync(0xffffffffu, in ? S.red[2][lane] : 0xffffffffu);
-        const uint32_t x1 = __reduce_max_sync(0xffffffffu, in ? S.red[3][lane] : 0u);
-        if (lane == 0) {
-          const uint2 s0 = S.cb[b][0], s1 = S.cb[b][1];
-          LevelNode *c0 = a.children + 2 * g.j, *c1 = c0 + 1;
-          if (m0 <= x0) {
-            if (m0 < s0.x) atomicMin(&c0->lo, m0);
-            if (x0 > s0.y) atomicMax(&c0->hi, x0);
-          }
-          if (m1 <= x1) {
-            if (m1 < s1.x) atomicMin(&c1->lo, m1);
-            if (x1 > s1.y) atomicMax(&c1->hi, x1);
-          }
-        }
-      }
-      if (lane == 0) next_t = after;
-    }
+    __syncthreads();  // the next tile's state is published; this tile's buffer may be refilled
     b ^= 1;
   }
 }

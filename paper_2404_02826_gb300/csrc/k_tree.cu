@@ -25,21 +25,34 @@ constexpr int kHistThreads = 512;
 constexpr int kSelThreads = 256;
 
 // --------------------------------------------------------------------------
-// prep: first digit of every node; children bounds reset for the scatter
+// prep: bounds of every node from its parent's split, then its first digit
 // --------------------------------------------------------------------------
-__global__ void k_prep(LevelNode *nodes, LevelNode *children, uint64_t n, int level, uint32_t digit_bits,
-                       uint32_t root_hi, uint32_t leaf_size) {
+__global__ void k_prep(LevelNode *nodes, const LevelNode *parents, uint64_t n, int level, uint32_t digit_bits,
+                       LevelLaunch::RootHi root_hi, uint32_t leaf_size) {
   const uint64_t count = 1ull << level;
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= count) return;
   LevelNode nd = {};
   if (level == 0) {
-    nd.lo = 0;
-    nd.hi = root_hi;
+    for (int d = 0; d < 3; ++d) {
+      nd.blo[d] = 0;
+      nd.bhi[d] = root_hi.v[d];
+    }
   } else {
-    nd.lo = nodes[j].lo;
-    nd.hi = nodes[j].hi;
+    const LevelNode &p = parents[j >> 1];
+    for (int d = 0; d < 3; ++d) {
+      nd.blo[d] = p.blo[d];
+      nd.bhi[d] = p.bhi[d];
+    }
+    if (p.v != 0xffffffffu) {  // the parent was split at p.v on its axis
+      const int pa = (level - 1) % 3;
+      if (j & 1) nd.blo[pa] = p.v;
+      else nd.bhi[pa] = p.v;
+    }
   }
+  const int axis = level % 3;
+  nd.lo = nd.blo[axis];
+  nd.hi = nd.bhi[axis];
   uint64_t off, cnt;
   node_range(n, level, j, off, cnt);
   const uint32_t k = uint32_t(cnt >> 1);
@@ -61,13 +74,6 @@ __global__ void k_prep(LevelNode *nodes, LevelNode *children, uint64_t n, int le
     nd.below = 0;
   }
   nodes[j] = nd;
-  if (children) {
-    LevelNode c = {};
-    c.lo = 0xffffffffu;
-    c.hi = 0;
-    children[2 * j] = c;
-    children[2 * j + 1] = c;
-  }
 }
 
 // --------------------------------------------------------------------------
@@ -245,8 +251,10 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   const uint64_t count = 1ull << a.level;
   {
     TraceScope ts("k_prep", st);
-    k_prep<<<unsigned((count + 255) / 256), 256, 0, st>>>(a.nodes, a.children, a.n, a.level, a.digit_bits,
-                                                          a.root_hi, a.leaf_size);
+    LevelLaunch::RootHi rh;
+    for (int d = 0; d < 3; ++d) rh.v[d] = a.root_hi[d];
+    k_prep<<<unsigned((count + 255) / 256), 256, 0, st>>>(a.nodes, a.parents, a.n, a.level, a.digit_bits, rh,
+                                                          a.leaf_size);
   }
   const int axis = a.level % 3;
   const C *codes = static_cast<const C *>(a.src[axis]);

@@ -336,7 +336,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       const uint32_t bits = bit_length(L.qmax[l % 3]);
       la.passes = (bits + la.digit_bits - 1) / la.digit_bits;
       la.tiles_per_node = uint32_t(tiles_per_node(n, l, scatter_tile(cb, p.idx)));
-      la.root_hi = L.qmax[0];
+      for (int d = 0; d < 3; ++d) la.root_hi[d] = L.qmax[d];
       for (int d = 0; d < 3; ++d) {
         la.src[d] = src[d];
         la.dst[d] = dst[d];
@@ -344,7 +344,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.src_idx = isrc;
       la.dst_idx = idst;
       la.nodes = nodes + node_base;
-      la.children = (l + 1 < levels) ? nodes + node_base + (1ull << l) : nullptr;
+      la.parents = l > 0 ? nodes + node_base - (1ull << (l - 1)) : nullptr;
       la.hist = reinterpret_cast<uint32_t *>(ws + p.off_hist);
       la.tile_state = reinterpret_cast<unsigned long long *>(ws + p.off_tiles) + tile_base;
       la.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + l;

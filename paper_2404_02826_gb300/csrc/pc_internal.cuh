@@ -47,7 +47,9 @@ struct LevelNode {
   uint32_t v;        // split code
   uint32_t less;     // particles with code < v
   uint32_t tleft;    // particles with code == v that go left (first in index order)
-  uint32_t pad[3];
+  uint32_t blo[3];   // code bounds on every axis, inherited from the ancestors' splits:
+  uint32_t bhi[3];   //   the left child of a split at v has codes <= v, the right child >= v
+  uint32_t pad;
 };
 
 // Per-leaf facts kept between the bit-box pass and the packing pass.
@@ -205,6 +207,9 @@ struct QuantLaunch {
 cudaError_t launch_quantize(const QuantLaunch &a, cudaStream_t st);
 
 struct LevelLaunch {
+  struct RootHi {
+    uint32_t v[3];
+  };
   uint64_t n;
   int level;
   int code_bytes;
@@ -213,13 +218,13 @@ struct LevelLaunch {
   uint32_t digit_bits;
   uint32_t passes;
   uint32_t tiles_per_node;
-  uint32_t root_hi;       // level 0 only: bounds of the x codes are [0, root_hi]
+  uint32_t root_hi[3];    // level 0: the codes of axis d lie in [0, root_hi[d]]
   const void *src[3];
   void *dst[3];
   const uint32_t *src_idx;
   uint32_t *dst_idx;
   LevelNode *nodes;       // this level [2^level]
-  LevelNode *children;    // next level [2^(level+1)]
+  const LevelNode *parents;  // previous level [2^(level-1)], null at level 0
   uint32_t *hist;         // [2^level][2^digit_bits], zero on entry, zero on exit
   unsigned long long *tile_state;
   uint32_t *ticket;
