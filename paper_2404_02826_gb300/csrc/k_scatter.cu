@@ -5,18 +5,18 @@
 // has v above every code and is copied unchanged.
 //
 // Three kernels per level:
-//   k_count     per tile: how many particles have code < v and code == v;
-//   k_tilescan  per node: exclusive scan of its tiles' counts;
+//   k_count     per tile, in groups of 32 consecutive window slots: the bit
+//               masks of "code < v" and "code == v" of every group, their
+//               prefix counts within the tile, and the tile's totals;
+//   k_tilescan  per node: exclusive scan of its tiles' totals;
 //   k_scatter   persistent CTAs; while one tile is partitioned, the Tensor
 //               Memory Accelerator copies the next tile's codes into the other
 //               half of a shared-memory double buffer (cp.async.bulk completing
-//               on an mbarrier).  Per tile: consecutive lanes take consecutive
-//               particles; two warp ballots give the masks of "code < v" and
-//               "code == v" of 32 particles, one block scan turns the counts of
-//               every (round, warp) into prefixes, and each particle's place in
-//               its child follows from its prefix and the popcount of the
-//               masks below its lane.  Stores to each child are contiguous
-//               across a warp.
+//               on an mbarrier), with the tile's group records.  Consecutive
+//               lanes take consecutive particles, a warp one group; each
+//               particle's place in its child follows from the group's prefix
+//               and the popcount of the group's masks below its lane.  Stores
+//               to each child are contiguous across a warp.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -34,7 +34,12 @@ struct Cfg {
   static constexpr int kWin = kBytesPer <= 6 ? 8192 : 4096;  // window of particles held per buffer
   static constexpr int kTile = kWin - 16;                      // largest tile: an aligned window covers it
   static constexpr int kRounds = kWin / kThreads;              // window slots per thread
+  static constexpr int kGroups = kWin / 32;                    // 32-slot groups of a window
 };
+
+// Group record: masks of "code < v" and "code == v" over 32 window slots, and
+// (less << 16 | tie) of the tile's groups before it.
+using GroupRec = uint4;
 
 // Tile i of node j covers positions [i*ts, (i+1)*ts) of the node, clipped to
 // its size, with ts = ceil(cnt / T).  Everything fits 32 bits (n < 2^31), and
@@ -49,13 +54,11 @@ struct Smem {
   using F = Cfg<C, IDX>;
   C in[2][3][F::kWin];
   uint32_t idx[IDX ? 2 : 1][IDX ? F::kWin : 4];
-  alignas(16) uint32_t wc[F::kRounds * kWarps];  // (less << 16 | tie) per round and warp
-  uint2 msk[F::kRounds * kWarps];                // ("code < v", "code == v") ballots per round and warp
-  uint2 pref[F::kRounds * kWarps];               // (left-going, ties) in the node before each round and warp
+  GroupRec grp[2][F::kGroups];
   unsigned long long bar[2];
   unsigned long long pre[2];  // (less << 31 | tie) of the node's tiles before this one
   uint32_t tile[2];
-  uint32_t v[2], tleft[2];
+  uint32_t tleft[2];
   TileGeom geo[2];
 };
 
@@ -120,7 +123,7 @@ __device__ __forceinline__ TileGeom tile_geom(const LevelLaunch &a, uint32_t t) 
 // What thread 0 reads for a tile it has just issued; the loads complete while
 // the current tile is processed and are used at its end.
 struct Pending {
-  uint32_t v, tl;
+  uint32_t tl;
   unsigned long long pre;
 };
 
@@ -133,19 +136,20 @@ __device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S
   const uint32_t w0 = g.tb & ~15u;
   const uint32_t nwin = (g.te - w0 + 15) & ~15u;
   const uint32_t bytes = nwin * uint32_t(sizeof(C));
-  mbar_expect_tx(&S.bar[b], 3 * bytes + (IDX ? 4 * nwin : 0));
+  const uint32_t ngrp = (g.te - w0 + 31) >> 5;
+  mbar_expect_tx(&S.bar[b], 3 * bytes + (IDX ? 4 * nwin : 0) + ngrp * uint32_t(sizeof(GroupRec)));
   if (nwin) {
     for (int d = 0; d < 3; ++d) bulk_g2s(S.in[b][d], static_cast<const C *>(a.src[d]) + w0, bytes, &S.bar[b]);
     if (IDX) bulk_g2s(S.idx[b], a.src_idx + w0, 4 * nwin, &S.bar[b]);
+    bulk_g2s(S.grp[b], static_cast<const GroupRec *>(a.groups) + uint64_t(t) * Cfg<C, IDX>::kGroups,
+             ngrp * uint32_t(sizeof(GroupRec)), &S.bar[b]);
   }
-  p.v = a.nodes[g.j].v;
   p.tl = a.nodes[g.j].tleft;
   p.pre = a.tile_state[t];
 }
 
 template <typename C, bool IDX>
 __device__ __forceinline__ void publish(Smem<C, IDX> &S, int b, const Pending &p) {
-  S.v[b] = p.v;
   S.tleft[b] = p.tl;
   S.pre[b] = p.pre;
 }
@@ -155,9 +159,6 @@ __device__ __forceinline__ void publish(Smem<C, IDX> &S, int b, const Pending &p
 // for; three block barriers per tile.  AXIS is the split axis of the level.
 template <typename C, bool IDX, int AXIS>
 __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t tiles) {
-  using F = Cfg<C, IDX>;
-  constexpr int kPer = F::kRounds * kWarps / 32;  // scan entries per lane of warp 0
-  static_assert(kPer == 4 || kPer == 8, "scan entries per lane");
   extern __shared__ __align__(128) unsigned char smraw[];
   Smem<C, IDX> &S = *reinterpret_cast<Smem<C, IDX> *>(smraw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -204,85 +205,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
     const uint32_t k = g.cnt >> 1;
     const uint32_t lead = g.tb & 15u;
     const uint32_t nslots = lead + (g.te - g.tb);
-    const uint32_t v = S.v[b], tl = S.tleft[b];
+    const uint32_t tl = S.tleft[b];
     C *n0 = d0 + g.off, *n1 = d1 + g.off, *n2 = d2 + g.off;
     uint32_t *ni = IDX ? a.dst_idx + g.off : nullptr;
     const C *x0s = S.in[b][0], *x1s = S.in[b][1], *x2s = S.in[b][2];
-    const C *qa = AXIS == 0 ? x0s : (AXIS == 1 ? x1s : x2s);
 
-    // Window slot wp = r * kThreads + threadIdx.x in round r: a warp covers 32
-    // consecutive slots, so two ballots give the "code < v" and "code == v"
-    // masks of those 32 particles.  Slots outside [lead, nslots) are not
-    // particles of the tile; only the first and the last round have any.
+    // Window slot wp = r * kThreads + threadIdx.x in round r: warp w covers
+    // group r * kWarps + w.  Slots outside [lead, nslots) are not particles of
+    // the tile; only the first and the last round have any.
     const uint32_t rounds = (nslots + kThreads - 1) / kThreads;
-    // 1. masks and counts per round and warp
-    for (uint32_t r = 0; r < rounds; ++r) {
-      const uint32_t wp = r * kThreads + threadIdx.x;
-      const uint32_t q = qa[wp];
-      const bool valid = wp >= lead && wp < nslots;
-      const uint32_t lm = __ballot_sync(0xffffffffu, valid && q < v);
-      const uint32_t tm = __ballot_sync(0xffffffffu, valid && q == v);
-      if (lane == 0) {
-        S.wc[r * kWarps + warp] = (uint32_t(__popc(lm)) << 16) | uint32_t(__popc(tm));
-        S.msk[r * kWarps + warp] = make_uint2(lm, tm);
-      }
-    }
-    __syncthreads();
-    // 2. warp 0: exclusive scan of the counts, kPer entries per lane, turned
-    //    into (left-going particles, ties) of the node before each entry
-    if (warp == 0) {
-      const unsigned long long pre = S.pre[b];
-      const uint32_t less_before = uint32_t(pre >> 31), tie_before = uint32_t(pre & 0x7fffffffu);
-      const uint32_t ne = rounds * kWarps;
-      uint32_t e[kPer];
-      const uint4 *w4 = reinterpret_cast<const uint4 *>(S.wc + kPer * lane);
-#pragma unroll
-      for (int h = 0; h < kPer / 4; ++h) {
-        const uint4 x = w4[h];
-        e[4 * h] = x.x;
-        e[4 * h + 1] = x.y;
-        e[4 * h + 2] = x.z;
-        e[4 * h + 3] = x.w;
-      }
-      uint32_t sum = 0;
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        const uint32_t x = (kPer * uint32_t(lane) + i) < ne ? e[i] : 0u;
-        e[i] = sum;
-        sum += x;
-      }
-      uint32_t incl = sum;
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const uint32_t base = incl - sum;
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        const uint32_t ex = base + e[i];
-        const uint32_t lb = less_before + (ex >> 16), tb = tie_before + (ex & 0xffffu);
-        S.pref[kPer * lane + i] = make_uint2(lb + min(tb, tl), tb);
-      }
-    }
-    __syncthreads();
-    // 3. every particle's place in the node; stores with consecutive lanes on
-    //    consecutive particles, so each child's run is contiguous across a warp
+    const unsigned long long pre = S.pre[b];
+    const uint32_t less_before = uint32_t(pre >> 31), tie_before = uint32_t(pre & 0x7fffffffu);
     const uint32_t cnt = g.cnt;
     const uint32_t kpos = k + (g.tb - g.off) - lead;  // k + node position of window slot 0
     for (uint32_t r = 0; r < rounds; ++r) {
       const uint32_t wp = r * kThreads + threadIdx.x;
-      const uint2 mk = S.msk[r * kWarps + warp];
-      const uint2 pf = S.pref[r * kWarps + warp];
+      const GroupRec gr = S.grp[b][r * kWarps + warp];
+      const uint32_t lb = less_before + (gr.z >> 16), tb = tie_before + (gr.z & 0xffffu);
       bool left;
       uint32_t glrank;  // left-going particles of the node before this one
-      if (mk.y == 0) {  // no particle of this warp's 32 has code v
-        left = (mk.x & lane_bit) != 0;
-        glrank = pf.x + __popc(mk.x & lt_mask);
+      if (gr.y == 0) {  // no particle of the group has code v
+        left = (gr.x & lane_bit) != 0;
+        glrank = lb + min(tb, tl) + __popc(gr.x & lt_mask);
       } else {
-        const uint32_t run_t = pf.y + __popc(mk.y & lt_mask);
-        const uint32_t run_l = pf.x - min(pf.y, tl) + __popc(mk.x & lt_mask);
-        left = (mk.x & lane_bit) || ((mk.y & lane_bit) && run_t < tl);
-        glrank = run_l + min(run_t, tl);
+        const uint32_t run_t = tb + __popc(gr.y & lt_mask);
+        left = (gr.x & lane_bit) || ((gr.y & lane_bit) && run_t < tl);
+        glrank = lb + __popc(gr.x & lt_mask) + min(run_t, tl);
       }
       const bool valid = (r > 0 && r + 1 < rounds) || (wp >= lead && wp < nslots);
       if (valid) {
@@ -307,10 +255,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
   }
 }
 
-// Per tile: how many particles have code < v and code == v (one block per tile).
-template <typename C>
+// Per tile (one block of 8 warps): for every 32-slot group of the tile's
+// window, the masks of "code < v" and "code == v" and the counts of the
+// groups before it; the tile's totals go to tile_state for the node scan.
+// Warp w takes a contiguous run of kGroups / 8 groups.  A lane loads 16 bytes
+// (kPerLane codes) at a time and classifies them; the lanes sharing a group
+// OR their bits together with xor-shuffles.
+template <typename C, bool IDX>
 __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
-  __shared__ uint32_t red[2][8];
+  constexpr int kG = Cfg<C, IDX>::kGroups;
+  constexpr int kPerWarp = kG / 8;                    // groups of one warp
+  constexpr int kPerLane = 16 / int(sizeof(C));       // codes of one 16-byte load
+  constexpr int kLanesPerGroup = 32 / kPerLane;       // 4 (u16) or 8 (u32)
+  constexpr int kGroupsPerLoad = 32 / kLanesPerGroup;  // groups one warp-wide load covers
+  constexpr int kLoads = kPerWarp / kGroupsPerLoad;
+  static_assert(kPerWarp <= 32 && kLoads * kGroupsPerLoad == kPerWarp, "group layout");
+  __shared__ uint32_t wtot[8];
   __shared__ TileGeom sg;
   __shared__ uint32_t sv;
   if (threadIdx.x == 0) {
@@ -320,50 +280,70 @@ __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
   __syncthreads();
   const TileGeom g = sg;
   const uint32_t v = sv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const C *q = static_cast<const C *>(a.src[a.level % 3]);
-  constexpr uint32_t kVec = 16 / sizeof(C);
-  uint32_t less = 0, tie = 0;
-  auto one = [&](uint32_t x) {
-    less += x < v;
-    tie += x == v;
-  };
-  const uint32_t a0 = (g.tb + kVec - 1) & ~(kVec - 1), a1 = g.te & ~(kVec - 1);
-  if (a0 >= a1) {
-    for (uint32_t e = g.tb + threadIdx.x; e < g.te; e += blockDim.x) one(__ldcg(q + e));
-  } else {
-    for (uint32_t e = g.tb + threadIdx.x; e < a0; e += blockDim.x) one(__ldcg(q + e));
-    for (uint32_t e = a1 + threadIdx.x; e < g.te; e += blockDim.x) one(__ldcg(q + e));
-    const uint4 *vp = reinterpret_cast<const uint4 *>(q + a0);
-    const uint32_t nv = (a1 - a0) / kVec;
-    for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
-      const uint4 w = __ldcg(vp + i);
-      const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+  const uint32_t w0 = g.tb & ~15u;
+  const uint32_t ngrp = (g.te - w0 + 31) >> 5;
+  const uint32_t run0 = w0 + uint32_t(warp) * (32u * kPerWarp);  // first slot of this warp's run
+  // all of the lane's loads first
+  uint4 raw[kLoads];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (sizeof(C) == 2) {
-          one(x[c] & 0xffffu);
-          one(x[c] >> 16);
-        } else {
-          one(x[c]);
-        }
-      }
-    }
+  for (int i = 0; i < kLoads; ++i) {
+    const uint32_t s0 = run0 + uint32_t(i) * (32u * kGroupsPerLoad) + uint32_t(lane) * kPerLane;
+    raw[i] = s0 < g.te ? __ldcs(reinterpret_cast<const uint4 *>(q + s0)) : make_uint4(0u, 0u, 0u, 0u);
   }
-  less = __reduce_add_sync(0xffffffffu, less);
-  tie = __reduce_add_sync(0xffffffffu, tie);
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = less;
-    red[1][threadIdx.x >> 5] = tie;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  uint32_t mylm = 0, mytm = 0, mycnt = 0;  // lane i: group warp * kPerWarp + i
+#pragma unroll
+  for (int i = 0; i < kLoads; ++i) {
+    const uint32_t s0 = run0 + uint32_t(i) * (32u * kGroupsPerLoad) + uint32_t(lane) * kPerLane;
+    // valid slots of this lane's codes: [tb, te) relative to s0
+    const int vlo = min(max(int(g.tb) - int(s0), 0), kPerLane), vhi = min(max(int(g.te) - int(s0), 0), kPerLane);
+    const uint32_t vm = ((1u << vhi) - 1u) & ~((1u << vlo) - 1u);
+    const uint32_t w[4] = {raw[i].x, raw[i].y, raw[i].z, raw[i].w};
     uint32_t l = 0, t = 0;
-    for (int w = 0; w < 8; ++w) {
-      l += red[0][w];
-      t += red[1][w];
+#pragma unroll
+    for (int c = 0; c < kPerLane; ++c) {
+      const uint32_t x = sizeof(C) == 2 ? ((w[c >> 1] >> (16 * (c & 1))) & 0xffffu) : w[c];
+      l |= uint32_t(x < v) << c;
+      t |= uint32_t(x == v) << c;
     }
-    a.tile_state[blockIdx.x] = ((unsigned long long)l << 31) | t;
+    const int sh = kPerLane * (lane % kLanesPerGroup);
+    l = (l & vm) << sh;
+    t = (t & vm) << sh;
+#pragma unroll
+    for (int o = 1; o < kLanesPerGroup; o <<= 1) {
+      l |= __shfl_xor_sync(0xffffffffu, l, o);
+      t |= __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    // group i * kGroupsPerLoad + j sits in lanes j * kLanesPerGroup ...; hand it to lane i * kGroupsPerLoad + j
+    const int src = (lane % kGroupsPerLoad) * kLanesPerGroup;
+    const uint32_t gl = __shfl_sync(0xffffffffu, l, src), gt = __shfl_sync(0xffffffffu, t, src);
+    if (lane / kGroupsPerLoad == i) {
+      mylm = gl;
+      mytm = gt;
+      mycnt = (uint32_t(__popc(gl)) << 16) | uint32_t(__popc(gt));
+    }
   }
+  // prefix of the groups: within the warp, then across warps
+  uint32_t incl = mycnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint32_t wbase = 0, total = 0;
+  for (int w = 0; w < 8; ++w) {
+    const uint32_t x = wtot[w];
+    wbase += w < warp ? x : 0u;
+    total += x;
+  }
+  const uint32_t m = uint32_t(warp * kPerWarp + lane);
+  if (lane < kPerWarp && m < ngrp) {
+    GroupRec *out = static_cast<GroupRec *>(a.groups) + uint64_t(blockIdx.x) * kG;
+    out[m] = make_uint4(mylm, mytm, wbase + incl - mycnt, 0u);
+  }
+  if (threadIdx.x == 0) a.tile_state[blockIdx.x] = ((unsigned long long)(total >> 16) << 31) | (total & 0xffffu);
 }
 
 // Per node: exclusive scan of its tiles' (less << 31 | tie) counts, in place.
@@ -423,7 +403,7 @@ cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
   const uint64_t tiles = (1ull << a.level) * a.tiles_per_node;
   {
     TraceScope ts("k_count", st);
-    k_count<C><<<unsigned(tiles), 256, 0, st>>>(a);
+    k_count<C, IDX><<<unsigned(tiles), 256, 0, st>>>(a);
   }
   {
     TraceScope ts("k_tilescan", st);
@@ -437,6 +417,11 @@ cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+uint32_t scatter_groups(int code_bytes, bool with_idx) {
+  if (code_bytes == 2) return with_idx ? Cfg<uint16_t, true>::kGroups : Cfg<uint16_t, false>::kGroups;
+  return with_idx ? Cfg<uint32_t, true>::kGroups : Cfg<uint32_t, false>::kGroups;
+}
 
 uint32_t scatter_tile(int code_bytes, bool with_idx) {
   if (code_bytes == 2) return with_idx ? Cfg<uint16_t, true>::kTile : Cfg<uint16_t, false>::kTile;

@@ -70,6 +70,7 @@ struct Plan {
   uint64_t off_nodes = 0, off_leafrec = 0, off_words = 0;
   uint64_t off_zero = 0, zero_bytes = 0;  // zeroed at every call:
   uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_err = 0, off_total = 0;
+  uint64_t off_groups = 0;
   uint64_t total = 0;
   int range_blocks = 0;
 };
@@ -90,6 +91,10 @@ uint32_t digit_bits_for(int level) {
   if (d < 6) d = 6;
   return uint32_t(d);
 }
+
+// Bytes of one axis's code array: room for u32 codes and for the 16-byte
+// loads of a tile's last group, which may reach up to 64 bytes past n.
+inline uint64_t code_stride(uint64_t n) { return align_up(4 * n + 64); }
 
 // Tiles per node at one level: node sizes are floor(n / 2^level) or one more.
 uint64_t tiles_per_node(uint64_t n, int level, uint32_t tile) {
@@ -128,9 +133,9 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   p.off_range = o;
   o = align_up(o + sizeof(RangeResult));
   p.off_codes_a = o;
-  o = align_up(o + 3 * align_up(4 * n));
+  o = align_up(o + 3 * code_stride(n));
   p.off_codes_b = o;
-  o = align_up(o + 3 * align_up(4 * n));
+  o = align_up(o + 3 * code_stride(n));
   if (idx) {
     p.off_idx_a = o;
     o = align_up(o + 4 * n);
@@ -145,6 +150,15 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafRec));
   p.off_words = o;
   o = align_up(o + 8);
+  // group records of the scatter's classification, one level at a time
+  uint64_t group_bytes = 16;
+  for (int l = 0; l < p.levels; ++l)
+    for (int cb = 2; cb <= 4; cb += 2) {
+      const uint64_t g = (1ull << l) * tiles_per_node(n, l, scatter_tile(cb, idx)) * scatter_groups(cb, idx) * 16;
+      if (g > group_bytes) group_bytes = g;
+    }
+  p.off_groups = o;
+  o = align_up(o + group_bytes);
   // zeroed region
   p.off_zero = o;
   uint64_t hist_bins = 0, tiles = 0;
@@ -290,8 +304,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     const int cb = qmax < 65536u ? 2 : 4;
     void *codes_a[3], *codes_b[3];
     for (int d = 0; d < 3; ++d) {
-      codes_a[d] = ws + p.off_codes_a + uint64_t(d) * align_up(4 * n);
-      codes_b[d] = ws + p.off_codes_b + uint64_t(d) * align_up(4 * n);
+      codes_a[d] = ws + p.off_codes_a + uint64_t(d) * code_stride(n);
+      codes_b[d] = ws + p.off_codes_b + uint64_t(d) * code_stride(n);
     }
     uint32_t *idx_a = p.idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_a) : nullptr;
     uint32_t *idx_b = p.idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_b) : nullptr;
@@ -347,6 +361,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.parents = l > 0 ? nodes + node_base - (1ull << (l - 1)) : nullptr;
       la.hist = reinterpret_cast<uint32_t *>(ws + p.off_hist);
       la.tile_state = reinterpret_cast<unsigned long long *>(ws + p.off_tiles) + tile_base;
+      la.groups = ws + p.off_groups;
       la.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + l;
       la.err = err;
       la.hist_blocks = 2 * device_sm_count();

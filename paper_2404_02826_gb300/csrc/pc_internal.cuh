@@ -227,13 +227,15 @@ struct LevelLaunch {
   const LevelNode *parents;  // previous level [2^(level-1)], null at level 0
   uint32_t *hist;         // [2^level][2^digit_bits], zero on entry, zero on exit
   unsigned long long *tile_state;
+  void *groups;           // [tiles][scatter_groups()] group records of this level
   uint32_t *ticket;
   uint32_t *err;
   int hist_blocks;
 };
 cudaError_t launch_level(const LevelLaunch &a, cudaStream_t st);
 cudaError_t launch_scatter(const LevelLaunch &a, cudaStream_t st);
-uint32_t scatter_tile(int code_bytes, bool with_idx);  // largest tile of one scatter CTA
+uint32_t scatter_tile(int code_bytes, bool with_idx);    // largest tile of one scatter CTA
+uint32_t scatter_groups(int code_bytes, bool with_idx);  // 16-byte group records per tile
 
 struct LeafLaunch {
   uint64_t n;
