@@ -14,6 +14,9 @@
 //            many particles equal to v go left
 //   scatter  stable two-way partition of every node into its children
 //            (k_scatter.cu)
+// Levels of many small nodes replace hist and select by k_median: one warp per
+// node with a private shared-memory histogram runs every digit of the radix
+// select for its node, with no block barrier and no global histogram.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -23,6 +26,8 @@ namespace {
 
 constexpr int kHistThreads = 512;
 constexpr int kSelThreads = 256;
+constexpr int kMedWarps = 16;                 // warps (nodes in flight) per k_median block
+constexpr uint32_t kMedBins = 1u << kMedD;    // private histogram of one warp
 
 // --------------------------------------------------------------------------
 // prep: bounds of every node from its parent's split, then its first digit
@@ -246,6 +251,108 @@ __global__ void __launch_bounds__(kSelThreads) k_select(LevelNode *nodes, uint32
   }
 }
 
+// --------------------------------------------------------------------------
+// median: one warp per node, all digits (levels of many small nodes)
+// --------------------------------------------------------------------------
+template <typename C>
+__global__ void __launch_bounds__(kMedWarps * 32) k_median(const C *__restrict__ codes, LevelNode *nodes, uint64_t n,
+                                                            int level) {
+  extern __shared__ uint32_t med_hist[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *h = med_hist + warp * kMedBins;
+  const uint64_t count = 1ull << level;
+  constexpr uint32_t kVec = 16 / sizeof(C);
+  for (uint64_t j = uint64_t(blockIdx.x) * kMedWarps + warp; j < count; j += uint64_t(gridDim.x) * kMedWarps) {
+    LevelNode nd = nodes[j];
+    if (nd.width == 0) continue;  // a leaf, or all codes equal: prep has decided
+    uint64_t off64, cnt64;
+    node_range(n, level, j, off64, cnt64);
+    const uint32_t off = uint32_t(off64), cnt = uint32_t(cnt64), k = cnt >> 1;
+    for (;;) {
+      const uint32_t lo_c = nd.lo, prefix = nd.prefix, width = nd.width, mask = (1u << width) - 1u;
+      const int shift = nd.shift;
+      for (uint32_t b = lane; b < kMedBins; b += 32) h[b] = 0;
+      __syncwarp();
+      auto add = [&](uint32_t q) {
+        const uint32_t hb = (q - lo_c) >> shift;
+        if ((hb >> width) == prefix) atomicAdd(&h[hb & mask], 1u);
+      };
+      const uint32_t a0 = min((off + kVec - 1) & ~(kVec - 1), off + cnt), a1 = max(a0, (off + cnt) & ~(kVec - 1));
+      for (uint32_t e = off + lane; e < a0; e += 32) add(__ldcg(codes + e));
+      for (uint32_t e = a1 + lane; e < off + cnt; e += 32) add(__ldcg(codes + e));
+      const uint4 *v4 = reinterpret_cast<const uint4 *>(codes + a0);
+      const uint32_t nv = (a1 - a0) / kVec;
+      uint32_t i = lane;
+      for (; i + 96 < nv; i += 128) {
+        uint4 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = __ldcg(v4 + i + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t x[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (sizeof(C) == 2) {
+              add(x[c] & 0xffffu);
+              add(x[c] >> 16);
+            } else {
+              add(x[c]);
+            }
+          }
+        }
+      }
+      for (; i < nv; i += 32) {
+        const uint4 w = __ldcg(v4 + i);
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (sizeof(C) == 2) {
+            add(x[c] & 0xffffu);
+            add(x[c] >> 16);
+          } else {
+            add(x[c]);
+          }
+        }
+      }
+      __syncwarp();
+      // the bucket holding rank k - below: 32 bins at a time, one per lane
+      const uint32_t target = k - nd.below;
+      uint32_t run = 0, found_b = 0, found_before = 0;
+      const uint32_t nb = 1u << width;
+      for (uint32_t c0 = 0; c0 < nb; c0 += 32) {
+        const uint32_t x = c0 + lane < nb ? h[c0 + lane] : 0u;
+        uint32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint32_t hit = __ballot_sync(0xffffffffu, x && run + incl - x <= target && target < run + incl);
+        if (hit) {
+          const int src = __ffs(hit) - 1;
+          found_b = c0 + src;
+          found_before = run + __shfl_sync(0xffffffffu, incl - x, src);
+          break;
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      __syncwarp();
+      nd.below += found_before;
+      nd.prefix = (nd.prefix << nd.width) | found_b;
+      if (nd.shift == 0) {
+        nd.v = nd.lo + nd.prefix;
+        nd.less = nd.below;
+        nd.tleft = k - nd.less;
+        nd.width = 0;
+        break;
+      }
+      const uint32_t w = uint32_t(nd.shift) < kMedD ? uint32_t(nd.shift) : kMedD;
+      nd.shift -= int32_t(w);
+      nd.width = w;
+    }
+    if (lane == 0) nodes[j] = nd;
+  }
+}
+
 template <typename C>
 cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   const uint64_t count = 1ull << a.level;
@@ -258,6 +365,22 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   }
   const int axis = a.level % 3;
   const C *codes = static_cast<const C *>(a.src[axis]);
+  if (a.warp_median) {
+    const size_t msm = sizeof(uint32_t) * kMedBins * kMedWarps;
+    cudaError_t e = cudaFuncSetAttribute(k_median<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(msm));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_median<C>, kMedWarps * 32, msm);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = uint64_t(per_sm < 1 ? 1 : per_sm) * uint64_t(device_sm_count());
+    const uint64_t need = (count + kMedWarps - 1) / kMedWarps;
+    if (grid > need) grid = need;
+    {
+      TraceScope ts("k_median", st);
+      k_median<C><<<unsigned(grid), kMedWarps * 32, msm, st>>>(codes, a.nodes, a.n, a.level);
+    }
+    return launch_scatter(a, st);
+  }
   const size_t hsm = sizeof(uint32_t) << a.digit_bits;
   for (uint32_t p = 0; p < a.passes; ++p) {
     {

@@ -346,7 +346,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.code_bytes = cb;
       la.with_idx = p.idx;
       la.leaf_size = p.r;
-      la.digit_bits = digit_bits_for(l);
+      // levels of at least 2048 nodes of at most kMedMaxNode particles: one warp per node
+      la.warp_median = (1ull << l) >= 2048 && ((n + (1ull << l) - 1) >> l) <= kMedMaxNode;
+      la.digit_bits = la.warp_median ? kMedD : digit_bits_for(l);
       const uint32_t bits = bit_length(L.qmax[l % 3]);
       la.passes = (bits + la.digit_bits - 1) / la.digit_bits;
       la.tiles_per_node = uint32_t(tiles_per_node(n, l, scatter_tile(cb, p.idx)));

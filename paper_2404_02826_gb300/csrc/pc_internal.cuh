@@ -20,6 +20,11 @@ enum : uint32_t { kErrTimeout = 1u, kErrCorrupt = 2u, kErrInternal = 4u };
 // With a 64 ns back-off this is about one second before the wait gives up.
 constexpr uint32_t kSpinLimit = 1u << 24;
 
+// Radix digit of the warp-per-node median (levels of many small nodes).
+constexpr uint32_t kMedD = 10;
+// Largest node handled by one warp.
+constexpr uint64_t kMedMaxNode = 1ull << 16;
+
 // Result of the range reduction (Sec. 3: per-axis min / max, Delta_max).
 struct RangeResult {
   double lo[3];
@@ -216,6 +221,7 @@ struct LevelLaunch {
   bool with_idx;
   uint32_t leaf_size;     // nodes of at most this many particles are leaves (copied unchanged)
   uint32_t digit_bits;
+  bool warp_median;       // one warp per node runs the whole radix select (k_median, kMedD-bit digits)
   uint32_t passes;
   uint32_t tiles_per_node;
   uint32_t root_hi[3];    // level 0: the codes of axis d lie in [0, root_hi[d]]
