@@ -381,6 +381,20 @@ __global__ void __launch_bounds__(1024) k_tilescan(LevelLaunch a) {
   }
 }
 
+// The same scan for nodes of few tiles: one thread per node.
+__global__ void k_tilescan_small(LevelLaunch a) {
+  const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= (1ull << a.level)) return;
+  const uint32_t T = a.tiles_per_node;
+  unsigned long long *s = a.tile_state + j * T;
+  unsigned long long run = 0;
+  for (uint32_t t = 0; t < T; ++t) {
+    const unsigned long long x = s[t];
+    s[t] = run;
+    run += x;
+  }
+}
+
 template <typename C, bool IDX, int AXIS>
 cudaError_t scatter_launch(const LevelLaunch &a, uint32_t tiles, cudaStream_t st) {
   const size_t smem = sizeof(Smem<C, IDX>);
@@ -407,7 +421,10 @@ cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
   }
   {
     TraceScope ts("k_tilescan", st);
-    k_tilescan<<<unsigned(1ull << a.level), 1024, 0, st>>>(a);
+    if (a.tiles_per_node <= 16)
+      k_tilescan_small<<<unsigned(((1ull << a.level) + 255) / 256), 256, 0, st>>>(a);
+    else
+      k_tilescan<<<unsigned(1ull << a.level), 1024, 0, st>>>(a);
   }
   switch (a.level % 3) {
     case 0: return scatter_launch<C, IDX, 0>(a, uint32_t(tiles), st);
