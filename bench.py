@@ -43,6 +43,7 @@ WORKLOADS = {
     "uniform-2^20-f32-rel1e-3": ("uniform", 1 << 20, "f32", "rel", 1e-3),
     "fluid-2^24-f64-abs1e-4": ("fluid", 1 << 24, "f64", "abs", 1e-4),
     "cosmology-2^24-f32-rel1e-4": ("cosmology", 1 << 24, "f32", "rel", 1e-4),
+    "cosmology-2^25-f32-rel1e-4": ("cosmology", 1 << 25, "f32", "rel", 1e-4),
 }
 DEFAULT_WORKLOAD = "cosmology-2^27-f32-rel1e-4"
 CPU_SAMPLE = 1 << 22        # particles of the oracle's timed sample (cpu_baseline)
@@ -192,8 +193,11 @@ def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False):
         "k_range": 3 * esz * n,
         "k_quantize": 3 * esz * n + 3 * cb * n + idx * n,
         "k_hist": cb * n,
+        "k_median": cb * n,
+        "k_count": cb * n,
         "k_scatter": 2 * (3 * cb + idx) * n,
-        "k_subtree": (3 * cb + idx) * n + stream_bytes,
+        "k_leafbox": 3 * cb * n,
+        "k_leafpack": 3 * cb * n + stream_bytes,
         "k_decode": stream_bytes + 3 * esz * n,
     }.get(kernel)
 

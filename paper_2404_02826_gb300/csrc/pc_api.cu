@@ -455,7 +455,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
     return PC_ERR_ARG;
   if (stream_bytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
   uint8_t h[PC_HEADER_BYTES];
-  PC_TRY(cudaMemcpyAsync(h, stream_data, PC_HEADER_BYTES, cudaMemcpyDeviceToHost, st));
+  PC_TRY(cudaMemcpyAsync(h, stream_data, PC_HEADER_BYTES, cudaMemcpyDefault, st));
   PC_TRY(cudaStreamSynchronize(st));
   pc_info I;
   int rc = parse_header(h, PC_HEADER_BYTES, &I);

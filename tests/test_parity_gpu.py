@@ -217,16 +217,22 @@ def test_corrupt_streams_are_rejected(pc, oracle_mod):
     assert e.value.status == pc.PC_ERR_CAPACITY
 
 
-def test_host_buffer_entry_points(pc, oracle_mod):
-    pos = synth.cosmology(80_000, seed=31)
-    hp = torch.from_numpy(pos).pin_memory()
-    ws = torch.empty(pc.pc_compress_host_workspace_size(80_000, pc.PC_F32), dtype=torch.uint8, device="cuda")
-    hout = torch.empty(pc.pc_compress_bound(80_000, pc.PC_F32), dtype=torch.uint8).pin_memory()
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_host_buffer_entry_points(pc, oracle_mod, pinned, dtype):
+    """Host-buffer entry points, pinned and pageable, float and double: the
+    oracle's stream and positions."""
+    n = 80_000
+    pos = synth.cosmology(n, seed=31, dtype=dtype)
+    pdt = pc.PC_F32 if dtype == np.float32 else pc.PC_F64
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    hp = pin(torch.from_numpy(pos))
+    ws = torch.empty(pc.pc_compress_host_workspace_size(n, pdt), dtype=torch.uint8, device="cuda")
+    hout = pin(torch.empty(pc.pc_compress_bound(n, pdt), dtype=torch.uint8))
     size = pc.pc_compress_host(hp, pc.PC_EB_REL, 1e-4, hout, ws)
     ref, _ = oracle_mod.compress(pos, oracle_mod.REL, 1e-4)
     assert hout[:size].numpy().tobytes() == ref
-    dws = torch.empty(pc.pc_decompress_host_workspace_size(80_000, pc.PC_F32, size), dtype=torch.uint8,
-                      device="cuda")
-    hdec = torch.empty((80_000, 3), dtype=torch.float32).pin_memory()
+    dws = torch.empty(pc.pc_decompress_host_workspace_size(n, pdt, size), dtype=torch.uint8, device="cuda")
+    hdec = pin(torch.empty((n, 3), dtype=hp.dtype))
     pc.pc_decompress_host(hout, size, hdec, dws)
     assert hdec.numpy().tobytes() == oracle_mod.decompress(ref).tobytes()
