@@ -155,14 +155,21 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """Largest value over the ranks (the timed region of the slowest rank)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_gbs(world: int, bytes_per_rank_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's bytes over the slowest rank's time."""
+    return world * bytes_per_rank_step * steps / (max_ms / 1e3) / 1e9
 
 
 def source_hash(paths):
@@ -321,12 +328,11 @@ def run_ours(args, spec):
     time.sleep(0.1)
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
-    total_ms = ev[0][0].elapsed_time(ev[-1][2])
-    comp_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
-    dec_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
-    total_ms = max_over_ranks(total_ms, world)
+    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][2]), world)
+    comp_ms = max_over_ranks(sum(e[0].elapsed_time(e[1]) for e in ev), world)
+    dec_ms = max_over_ranks(sum(e[1].elapsed_time(e[2]) for e in ev), world)
     nbytes = 3 * esz * n
-    value = world * nbytes * args.steps / (total_ms / 1e3) / 1e9
+    value = whole_job_gbs(world, nbytes, args.steps, total_ms)
 
     table = pc.trace_table()
     launches = int(sum(v[0] for v in table.values()))
@@ -359,8 +365,8 @@ def run_ours(args, spec):
             "config": {"workload": args.workload, "generator": gen, "particles": n, "eb_mode": mode, "eb": eb,
                        "leaf_size": args.leaf_size, "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)", "code_bytes": cb},
-            "compress_gbs": round(world * nbytes * args.steps / (comp_ms / 1e3) / 1e9, 3),
-            "decompress_gbs": round(world * nbytes * args.steps / (dec_ms / 1e3) / 1e9, 3),
+            "compress_gbs": round(whole_job_gbs(world, nbytes, args.steps, comp_ms), 3),
+            "decompress_gbs": round(whole_job_gbs(world, nbytes, args.steps, dec_ms), 3),
             "compression_ratio": round(nbytes / size, 4), "bits_per_particle": round(8 * size / n, 4),
             "step_hbm_frac_algorithmic": round(step_alg / (total_ms / args.steps / 1e3) / 1e9 / peak, 4),
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,

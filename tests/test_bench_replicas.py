@@ -1,0 +1,63 @@
+"""Multi-process host logic of bench.py on CPU (gloo, world size 2).
+
+bench.py runs one independent snapshot per rank (replicas: the path has no
+data exchange), takes the slowest rank's time and sums the ranks' bytes.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    bench.barrier(world)
+    ms = 10.0 + 5.0 * rank  # the slower rank decides
+    got = bench.max_over_ranks(ms, world)
+    value = bench.whole_job_gbs(world, 1_000_000_000, 4, got)
+    out[rank] = (got, value)
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_value():
+    import torch.multiprocessing as mp
+
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn", join=True)
+    for rank in range(world):
+        got, value = out[rank]
+        assert got == 15.0
+        assert value == pytest.approx(2 * 1.0 * 4 / 0.015)
+
+
+def test_reference_arm_under_torchrun_rank0_only():
+    """`bench.py --impl reference` launched like the driver's N > 1 runs: rank 0
+    prints the one JSON line, the other rank exits 0 without work."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "1"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
