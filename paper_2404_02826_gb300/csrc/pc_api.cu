@@ -103,7 +103,7 @@ uint64_t tiles_per_node(uint64_t n, int level, uint32_t tile) {
   return t ? t : 1;
 }
 
-// smallest scatter tile over code widths: sizes the look-back state for any data
+// smallest scatter tile over code widths: sizes the per-tile counts for any data
 uint32_t min_scatter_tile(bool idx) {
   const uint32_t a = scatter_tile(2, idx), b = scatter_tile(4, idx);
   return a < b ? a : b;

@@ -16,10 +16,6 @@ constexpr int64_t kCodeLimit = int64_t(1) << 30;  // codes < 2^30, so m_d <= 31
 // Bits of the device error word.
 enum : uint32_t { kErrTimeout = 1u, kErrCorrupt = 2u, kErrInternal = 4u };
 
-// Spin limit of every device-side wait (look-back on a predecessor's state).
-// With a 64 ns back-off this is about one second before the wait gives up.
-constexpr uint32_t kSpinLimit = 1u << 24;
-
 // Radix digit of the warp-per-node median (levels of many small nodes).
 constexpr uint32_t kMedD = 10;
 // Largest node handled by one warp.
@@ -68,77 +64,6 @@ struct LeafRec {
   uint64_t word_off;  // first payload word
   uint64_t pad;
 };
-
-// Look-back state words: flag in the top two bits, value below.
-constexpr unsigned long long kFlagA = 1ull << 62;  // aggregate published
-constexpr unsigned long long kFlagP = 2ull << 62;  // inclusive prefix published
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
-
-#ifdef __CUDACC__
-__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Warp-wide decoupled look-back, called by all 32 lanes of one warp.  Item t
-// publishes its aggregate, sums its predecessors 32 at a time back to the
-// nearest published inclusive prefix (items before `first` count as an empty
-// prefix), publishes its own inclusive prefix and returns the exclusive one.
-// Every wait is bounded: on expiry the error word gets kErrTimeout and the item
-// publishes what it has so that its successors do not wait.
-__device__ __forceinline__ unsigned long long warp_lookback(unsigned long long *state, int64_t t, int64_t first,
-                                                            unsigned long long agg, uint32_t *err) {
-  const int lane = threadIdx.x & 31;
-  if (t == first) {
-    if (lane == 0) st_release(&state[t], kFlagP | agg);
-    return 0;
-  }
-  if (lane == 0) st_release(&state[t], kFlagA | agg);
-  unsigned long long excl = 0;
-  int64_t end = t - 1;
-  for (;;) {
-    const int64_t pred = end - lane;
-    const bool inside = pred >= first;
-    unsigned long long s = kFlagP;
-    uint32_t spins = 0;
-    bool timed_out = false;
-    for (;;) {
-      if (inside) s = ld_acquire(&state[pred]);
-      if (__all_sync(0xffffffffu, (s >> 62) != 0)) break;
-      if (++spins > kSpinLimit || (ld_relaxed(err) & kErrTimeout)) {
-        timed_out = true;
-        break;
-      }
-      __nanosleep(64);
-    }
-    if (__any_sync(0xffffffffu, timed_out)) {
-      if (lane == 0) {
-        atomicOr(err, kErrTimeout);
-        st_release(&state[t], kFlagP | ((excl + agg) & kValMask));
-      }
-      return excl;
-    }
-    const uint32_t pmask = __ballot_sync(0xffffffffu, (s & ~kValMask) == kFlagP);
-    const int cut = pmask ? (__ffs(pmask) - 1) : 31;
-    unsigned long long v = lane <= cut ? (s & kValMask) : 0ull;
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    excl += v;
-    if (pmask) break;
-    end -= 32;
-  }
-  if (lane == 0) st_release(&state[t], kFlagP | ((excl + agg) & kValMask));
-  return excl;
-}
-#endif
 
 // Offset and size of node j at depth `level` of the median tree over n
 // particles: the left child takes floor(c/2), the right ceil(c/2) (Sec. 4.1).
