@@ -163,6 +163,18 @@ def num_bits(R: int) -> int:
     return int(lib().oracle_num_bits(int(R)))
 
 
+def quantize_on(pos, o, s: float) -> np.ndarray:
+    """Sec. 3: lattice codes q[n, 3] (int64) on a given lattice (origin o, step s)."""
+    pos = _positions(pos)
+    cb = _Bound()
+    cb.o[:] = tuple(float(x) for x in o)
+    cb.s = float(s)
+    q = np.zeros((pos.shape[0], 3), np.int64)
+    lib().oracle_quantize(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), ctypes.byref(cb),
+                          q.ctypes.data)
+    return q
+
+
 def bitbox(leafq: np.ndarray):
     """Sec. 4.1: (centre position, lo[3], hi[3], q_ref[3], m[3]) of one leaf."""
     leafq = np.ascontiguousarray(leafq, dtype=np.int64).reshape(-1, 3)

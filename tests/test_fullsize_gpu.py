@@ -1,0 +1,110 @@
+"""Parity at the benchmark's full size: 2^27 cosmology positions, float32,
+value-range-relative eb 1e-4, leaf size 4096, compressed and decompressed
+with the same launch configuration bench.py times.
+
+The oracle cannot build the whole stream at this size in test time, so the
+result is checked by what holds at any size and by samples the oracle
+computes one at a time:
+  * header: eps, s and origin equal the oracle's error bound of the input;
+  * every decoded coordinate lies within eps of its input (Sec. 3);
+  * the partition (Sec. 4.1): on every level, every node's left half precedes
+    its right half in (code on the split axis, original index) order, and the
+    leaf table lists 2^15 leaves of 4096 particles;
+  * 64 sampled leaves: the oracle's bit box of the leaf's particles (centre
+    code and m per axis, Eq. 2) equals the leaf record, and the leaf's packed
+    codes equal q - q_ref + 2^(m-1) - 1 of its particles in leaf order.
+"""
+import struct
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 1 << 27
+LEAF = 4096
+EB = 1e-4
+
+
+@pytest.fixture(scope="module")
+def run():
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as b
+
+    b.build()
+    pc.load()
+    dev = torch.device("cuda:0")
+    pos_h = synth.cosmology(N, seed=0)
+    pos = torch.from_numpy(pos_h).to(dev)
+    c = pc.Compressor(N, pc.PC_F32, leaf_size=LEAF, with_perm=True, device=dev)
+    size = c.compress(pos, pc.PC_EB_REL, EB)
+    dec = torch.empty_like(pos)
+    c.decompress(c.out, dec, size)
+    torch.cuda.synchronize()
+    return pc, pos_h, pos, c.out[:size], c.perm[:N].long(), dec
+
+
+def test_header_matches_oracle_error_bound(run, oracle_mod):
+    pc, pos_h, _, stream, _, _ = run
+    info = pc.pc_stream_info(stream[:96].cpu().numpy().tobytes())
+    b = oracle_mod.error_bound(pos_h, oracle_mod.REL, EB)
+    assert info.n == N and info.num_leaves == N // LEAF
+    assert info.eps == b.eps and info.s == b.s and tuple(info.o) == tuple(b.o)
+
+
+def test_every_coordinate_within_eps(run):
+    pc, _, pos, stream, perm, dec = run
+    info = pc.pc_stream_info(stream[:96].cpu().numpy().tobytes())
+    err = (pos[perm].double() - dec.double()).abs().max().item()
+    assert err <= info.eps
+    assert torch.equal(torch.sort(perm).values, torch.arange(N, device=perm.device))
+
+
+def test_partition_on_every_level(run):
+    pc, _, pos, stream, perm, _ = run
+    info = pc.pc_stream_info(stream[:96].cpu().numpy().tobytes())
+    o = torch.tensor(info.o, dtype=torch.float64, device=pos.device)
+    # the definition, evaluated independently with torch: rint(((double)p - o) / s), half to even
+    q = torch.round((pos.double() - o) / info.s).long()
+    levels = int(np.log2(N // LEAF))
+    for level in range(levels):
+        axis = level % 3
+        key = (q[perm, axis] << 32) | perm  # output order; codes < 2^30
+        halves = key.view(1 << level, 2, N >> (level + 1))
+        assert bool((halves[:, 0, :].amax(1) < halves[:, 1, :].amin(1)).all()), f"level {level}"
+    recs = np.frombuffer(stream[96: 96 + 32 * (N // LEAF)].cpu().numpy().tobytes(), np.uint64).reshape(-1, 4)
+    assert np.array_equal(recs[:, 0], np.arange(N // LEAF, dtype=np.uint64) * LEAF)
+
+
+def test_sampled_leaves_against_oracle(run, oracle_mod):
+    pc, pos_h, _, stream, perm, _ = run
+    buf = stream.cpu().numpy().tobytes()
+    info = pc.pc_stream_info(buf[:96])
+    L = info.num_leaves
+    words = np.frombuffer(buf, "<u4", count=info.payload_words, offset=96 + 32 * L)
+    perm_h = perm.cpu().numpy()
+    rng = np.random.default_rng(1)
+    for leaf in sorted(rng.choice(L, 64, replace=False)):
+        po, wo, qx, qy, qz, mx, my, mz, z = struct.unpack_from("<QQiii4B", buf, 96 + 32 * int(leaf))
+        idx = perm_h[po: po + LEAF]  # decoded order: centre first, then the rest in leaf order
+        order = np.sort(idx)  # leaf order: partitions are stable, so original-index order
+        q = oracle_mod.quantize_on(pos_h[order], info.o, info.s)
+        cpos, lo, hi, qref, m = oracle_mod.bitbox(q)
+        assert np.array_equal(idx, np.concatenate([order[cpos:cpos + 1], np.delete(order, cpos)]))
+        assert tuple(qref) == (qx, qy, qz) and tuple(m) == (mx, my, mz) and z == 0
+        others = np.delete(q, cpos, axis=0)
+        # packed codes of the non-centre particles, particle-major, LSB first
+        w = mx + my + mz
+        nwords = (w * (LEAF - 1) + 31) // 32
+        bits = np.unpackbits(words[wo: wo + nwords].view(np.uint8), bitorder="little").astype(np.int64)
+        start = 0
+        for d, md in enumerate((mx, my, mz)):
+            if md:
+                at = np.arange(LEAF - 1)[:, None] * w + start + np.arange(md)[None, :]
+                got = (bits[at] << np.arange(md)[None, :]).sum(1)
+                want = others[:, d] - (qx, qy, qz)[d] + (1 << (md - 1)) - 1
+                assert np.array_equal(got, want)
+            start += md
