@@ -167,6 +167,107 @@ int pc_decompress_host_workspace_size(uint64_t n, int dtype, uint64_t stream_byt
 int pc_decompress_host(const void *host_stream, uint64_t stream_bytes, void *host_positions,
                        uint64_t out_capacity_bytes, void *workspace, uint64_t workspace_bytes, void *stream);
 
+/* ---- Many snapshots --------------------------------------------------------
+ * The paper compresses one snapshot at a time; nothing below has a
+ * counterpart in it.  These calls run many independent snapshots on one GPU
+ * through `lanes` CUDA streams, each driven by its own host thread and owning
+ * one slice of the workspace.  Items are taken largest first, so small
+ * snapshots overlap on the device with each other and with large ones.  Each
+ * item's stream (or positions) is byte-identical to a plain pc_compress (or
+ * pc_decompress) of the same input: the same kernels run in the same order
+ * within an item.  Work queued on `stream` before the call completes before
+ * any item starts; every item is complete when the call returns.  The call
+ * returns PC_OK when every item succeeded, else the status of the failed item
+ * with the lowest index; every item carries its own status. */
+typedef struct {
+    const void *positions;  /* device, T[n][3] */
+    uint64_t n;
+    int32_t dtype;          /* pc_dtype */
+    int32_t eb_mode;        /* pc_eb_mode */
+    double eb;
+    uint32_t leaf_size;     /* 0 = PC_DEFAULT_LEAF_SIZE */
+    uint32_t reserved;      /* 0 */
+    void *out;              /* device, out_capacity bytes (pc_compress_bound suffices) */
+    uint64_t out_capacity;
+    uint64_t out_size;      /* written: stream bytes */
+    int32_t status;         /* written */
+    int32_t reserved2;
+} pc_compress_item;
+
+typedef struct {
+    const void *stream_data;  /* device, 16-byte aligned */
+    uint64_t stream_bytes;
+    uint64_t n;               /* particles of the stream (pc_info.n) */
+    void *out_positions;      /* device */
+    uint64_t out_capacity_bytes;
+    int32_t status;           /* written */
+    int32_t reserved;
+} pc_decompress_item;
+
+/* Device scratch for a batch: `lanes` slices, each the largest workspace any
+ * item needs (host only).  lanes = 0 picks min(count, 8). */
+int pc_compress_batch_workspace_size(const pc_compress_item *items, uint32_t count, uint32_t lanes,
+                                     uint64_t *out_bytes);
+int pc_compress_batch(pc_compress_item *items, uint32_t count, uint32_t lanes, void *workspace,
+                      uint64_t workspace_bytes, void *stream);
+int pc_decompress_batch_workspace_size(const pc_decompress_item *items, uint32_t count, uint32_t lanes,
+                                       uint64_t *out_bytes);
+int pc_decompress_batch(pc_decompress_item *items, uint32_t count, uint32_t lanes, void *workspace,
+                        uint64_t workspace_bytes, void *stream);
+
+/* ---- Serving loop ------------------------------------------------------------
+ * A server owns `lanes` worker threads, each with its own CUDA stream, and a
+ * caller-provided device arena.  Submitted requests queue in arrival order;
+ * a free lane admits the oldest request as soon as the arena has room for its
+ * workspace and its output (first fit, 256-byte aligned), so requests that
+ * arrive while others run overlap with them on the device.  A request that
+ * can never fit completes with PC_ERR_CAPACITY.  Outputs stay in the arena
+ * until pc_server_release.  Results are identical to plain calls on the same
+ * inputs.  Inputs must stay valid and unchanged until their completion is
+ * polled.  All server calls are thread-safe. */
+typedef struct pc_server pc_server;
+
+enum { PC_REQ_COMPRESS = 0, PC_REQ_DECOMPRESS = 1 };
+
+typedef struct {
+    int32_t kind;           /* PC_REQ_COMPRESS or PC_REQ_DECOMPRESS */
+    int32_t dtype;          /* pc_dtype of the positions (decompress: as in the stream header) */
+    int32_t eb_mode;        /* compress: pc_eb_mode */
+    uint32_t leaf_size;     /* compress: 0 = PC_DEFAULT_LEAF_SIZE */
+    double eb;              /* compress */
+    const void *input;      /* device: positions (compress) or stream (decompress) */
+    uint64_t n;             /* particles */
+    uint64_t input_bytes;   /* decompress: stream bytes */
+    uint64_t tag;           /* caller's identifier, echoed in the completion */
+} pc_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;
+    int32_t kind;
+    void *output;           /* device, inside the arena: the stream or the positions */
+    uint64_t output_bytes;
+    double t_submit;        /* seconds on the host's steady clock */
+    double t_start;         /* admitted to a lane */
+    double t_done;          /* result complete on the device */
+} pc_completion;
+
+int pc_server_create(void *arena, uint64_t arena_bytes, uint32_t lanes, pc_server **out);
+int pc_server_submit(pc_server *server, const pc_request *request);
+/* Up to `max` completions in completion order; with wait != 0 blocks until at
+ * least one is available or nothing is queued or running. */
+int pc_server_poll(pc_server *server, pc_completion *out, uint32_t max, uint32_t *got, int wait);
+/* Returns an output's arena space (the `output` pointer of a completion). */
+int pc_server_release(pc_server *server, void *output);
+/* Requests queued or running, and arena bytes in use. */
+int pc_server_stats(pc_server *server, uint64_t *pending, uint64_t *arena_in_use);
+/* Waits for running requests and admits queued ones while they fit; queued
+ * requests that no longer can (outputs still held) complete with
+ * PC_ERR_CAPACITY.  Then frees the server; unpolled completions are dropped. */
+int pc_server_destroy(pc_server *server);
+/* Host seconds on the clock the completions use. */
+double pc_server_now(void);
+
 /* Kernel tracing.  While enabled, every kernel launch of the library is
  * bracketed by CUDA events recorded on the launching stream; elapsed times are
  * accumulated per kernel name when a call synchronises (compress and

@@ -44,7 +44,12 @@ EXPORTS = (
     "pc_decompress_workspace_size", "pc_decompress", "pc_compress_host_workspace_size", "pc_compress_host",
     "pc_decompress_host_workspace_size", "pc_decompress_host", "pc_error_string", "pc_format_version",
     "pc_trace_enable", "pc_trace_reset", "pc_trace_count", "pc_trace_get", "pc_compress_noalloc",
+    "pc_compress_batch_workspace_size", "pc_compress_batch", "pc_decompress_batch_workspace_size",
+    "pc_decompress_batch", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_release",
+    "pc_server_stats", "pc_server_destroy", "pc_server_now",
 )
+PC_REQ_COMPRESS = 0
+PC_REQ_DECOMPRESS = 1
 PC_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -64,6 +69,31 @@ class pc_info(ctypes.Structure):
                 ("eb", ctypes.c_double), ("eps", ctypes.c_double), ("s", ctypes.c_double),
                 ("o", ctypes.c_double * 3), ("num_leaves", ctypes.c_uint64), ("payload_words", ctypes.c_uint64),
                 ("leaf_size", ctypes.c_uint32), ("total_bytes", ctypes.c_uint64)]
+
+
+class pc_compress_item(ctypes.Structure):
+    _fields_ = [("positions", ctypes.c_void_p), ("n", ctypes.c_uint64), ("dtype", ctypes.c_int32),
+                ("eb_mode", ctypes.c_int32), ("eb", ctypes.c_double), ("leaf_size", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("out", ctypes.c_void_p), ("out_capacity", ctypes.c_uint64),
+                ("out_size", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+
+
+class pc_decompress_item(ctypes.Structure):
+    _fields_ = [("stream_data", ctypes.c_void_p), ("stream_bytes", ctypes.c_uint64), ("n", ctypes.c_uint64),
+                ("out_positions", ctypes.c_void_p), ("out_capacity_bytes", ctypes.c_uint64),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class pc_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("eb_mode", ctypes.c_int32),
+                ("leaf_size", ctypes.c_uint32), ("eb", ctypes.c_double), ("input", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("input_bytes", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
+
+
+class pc_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("output", ctypes.c_void_p), ("output_bytes", ctypes.c_uint64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 _LIB = None
@@ -97,6 +127,19 @@ def _lib():
         L.pc_trace_reset.argtypes = []
         L.pc_trace_count.argtypes = []
         L.pc_trace_get.argtypes = [i32, ctypes.POINTER(ctypes.c_char_p), pu64, ctypes.POINTER(dbl)]
+        u32 = ctypes.c_uint32
+        L.pc_compress_batch_workspace_size.argtypes = [ctypes.POINTER(pc_compress_item), u32, u32, pu64]
+        L.pc_compress_batch.argtypes = [ctypes.POINTER(pc_compress_item), u32, u32, vp, u64, vp]
+        L.pc_decompress_batch_workspace_size.argtypes = [ctypes.POINTER(pc_decompress_item), u32, u32, pu64]
+        L.pc_decompress_batch.argtypes = [ctypes.POINTER(pc_decompress_item), u32, u32, vp, u64, vp]
+        L.pc_server_create.argtypes = [vp, u64, u32, ctypes.POINTER(vp)]
+        L.pc_server_submit.argtypes = [vp, ctypes.POINTER(pc_request)]
+        L.pc_server_poll.argtypes = [vp, ctypes.POINTER(pc_completion), u32, ctypes.POINTER(u32), i32]
+        L.pc_server_release.argtypes = [vp, vp]
+        L.pc_server_stats.argtypes = [vp, pu64, pu64]
+        L.pc_server_destroy.argtypes = [vp]
+        L.pc_server_now.argtypes = []
+        L.pc_server_now.restype = dbl
         _LIB = L
     return _LIB
 
@@ -279,6 +322,121 @@ def trace_table() -> dict:
 # ---------------------------------------------------------------------------
 # convenience wrappers that take buffers from torch's allocator
 # ---------------------------------------------------------------------------
+
+def _items(cls, rows):
+    arr = (cls * max(len(rows), 1))()
+    for i, r in enumerate(rows):
+        arr[i] = r
+    return arr
+
+
+def pc_compress_batch(jobs, outs, workspace=None, lanes: int = 0, stream=None):
+    """Compress many device snapshots in one call.
+
+    jobs: sequence of (positions tensor, eb_mode, eb, leaf_size); outs: device
+    uint8 tensors (pc_compress_bound bytes).  Returns (stream sizes, item
+    statuses); raises when the call itself fails.  The workspace (device
+    uint8) is allocated here when not given."""
+    import torch
+    rows = [pc_compress_item(p.data_ptr() if p.shape[0] else None, p.shape[0], _dtype_of(p), int(m), float(eb),
+                             int(leaf), 0, o.data_ptr(), o.numel(), 0, 0, 0)
+            for (p, m, eb, leaf), o in zip(jobs, outs)]
+    arr = _items(pc_compress_item, rows)
+    if workspace is None:
+        need = ctypes.c_uint64()
+        _check(_lib().pc_compress_batch_workspace_size(arr, len(rows), lanes, ctypes.byref(need)),
+               "pc_compress_batch_workspace_size")
+        workspace = torch.empty(need.value, dtype=torch.uint8, device=outs[0].device if outs else "cuda")
+    rc = _lib().pc_compress_batch(arr, len(rows), lanes, workspace.data_ptr(), workspace.numel(),
+                                  _stream_handle(stream))
+    statuses = [arr[i].status for i in range(len(rows))]
+    if rc != PC_OK and all(st == PC_OK for st in statuses):
+        _check(rc, "pc_compress_batch")
+    return [arr[i].out_size for i in range(len(rows))], statuses
+
+
+def pc_compress_batch_workspace_size(ns_dtypes_leaves, lanes: int = 0) -> int:
+    """Workspace bytes for snapshots given as (n, dtype, leaf_size)."""
+    rows = [pc_compress_item(None, n, dt, 0, 0.0, leaf, 0, None, 0, 0, 0, 0) for n, dt, leaf in ns_dtypes_leaves]
+    need = ctypes.c_uint64()
+    _check(_lib().pc_compress_batch_workspace_size(_items(pc_compress_item, rows), len(rows), lanes,
+                                                   ctypes.byref(need)), "pc_compress_batch_workspace_size")
+    return need.value
+
+
+def pc_decompress_batch(streams, sizes, outs, workspace=None, lanes: int = 0, stream=None):
+    """Decompress many device streams into device position tensors in one call;
+    returns the item statuses."""
+    import torch
+    rows = []
+    for st, nb, o in zip(streams, sizes, outs):
+        rows.append(pc_decompress_item(st.data_ptr(), int(nb), o.shape[0], o.data_ptr(),
+                                       o.numel() * o.element_size(), 0, 0))
+    arr = _items(pc_decompress_item, rows)
+    if workspace is None:
+        need = ctypes.c_uint64()
+        _check(_lib().pc_decompress_batch_workspace_size(arr, len(rows), lanes, ctypes.byref(need)),
+               "pc_decompress_batch_workspace_size")
+        workspace = torch.empty(need.value, dtype=torch.uint8, device=outs[0].device if outs else "cuda")
+    rc = _lib().pc_decompress_batch(arr, len(rows), lanes, workspace.data_ptr(), workspace.numel(),
+                                    _stream_handle(stream))
+    statuses = [arr[i].status for i in range(len(rows))]
+    if rc != PC_OK and all(st == PC_OK for st in statuses):
+        _check(rc, "pc_decompress_batch")
+    return statuses
+
+
+class Server:
+    """The serving loop of the library (pc_server_*): worker lanes admit queued
+    requests into a device arena as room frees up; outputs stay in the arena
+    until released."""
+
+    def __init__(self, arena, lanes: int = 4):
+        self.arena = arena  # device uint8 tensor, kept alive here
+        h = ctypes.c_void_p()
+        _check(_lib().pc_server_create(arena.data_ptr(), arena.numel(), lanes, ctypes.byref(h)), "pc_server_create")
+        self.h = h
+
+    def submit_compress(self, positions, eb_mode: int, eb: float, tag: int, leaf_size: int = 0):
+        r = pc_request(PC_REQ_COMPRESS, _dtype_of(positions), int(eb_mode), int(leaf_size), float(eb),
+                       positions.data_ptr(), positions.shape[0], 0, int(tag))
+        _check(_lib().pc_server_submit(self.h, ctypes.byref(r)), "pc_server_submit")
+
+    def submit_decompress(self, stream_data, nbytes: int, n: int, dtype: int, tag: int):
+        r = pc_request(PC_REQ_DECOMPRESS, int(dtype), 0, 0, 0.0, stream_data.data_ptr(), int(n), int(nbytes),
+                       int(tag))
+        _check(_lib().pc_server_submit(self.h, ctypes.byref(r)), "pc_server_submit")
+
+    def poll(self, wait: bool = False, max_items: int = 256):
+        buf = (pc_completion * max_items)()
+        got = ctypes.c_uint32()
+        _check(_lib().pc_server_poll(self.h, buf, max_items, ctypes.byref(got), 1 if wait else 0), "pc_server_poll")
+        return [buf[i] for i in range(got.value)]
+
+    def output(self, c, dtype=None):
+        """A view of a completion's output in the arena (uint8, or positions [n, 3] given dtype)."""
+        import torch
+        off = c.output - self.arena.data_ptr()
+        v = self.arena[off: off + c.output_bytes]
+        return v if dtype is None else v.view(dtype).view(-1, 3)
+
+    def release(self, c):
+        _check(_lib().pc_server_release(self.h, c.output), "pc_server_release")
+
+    def stats(self):
+        p, u = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib().pc_server_stats(self.h, ctypes.byref(p), ctypes.byref(u)), "pc_server_stats")
+        return p.value, u.value
+
+    def close(self):
+        if self.h:
+            _check(_lib().pc_server_destroy(self.h), "pc_server_destroy")
+            self.h = None
+
+    @staticmethod
+    def now() -> float:
+        return _lib().pc_server_now()
+
 
 class Compressor:
     """Holds device buffers sized for one problem size and reuses them."""

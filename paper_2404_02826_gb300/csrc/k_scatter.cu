@@ -398,11 +398,8 @@ __global__ void k_tilescan_small(LevelLaunch a) {
 template <typename C, bool IDX, int AXIS>
 cudaError_t scatter_launch(const LevelLaunch &a, uint32_t tiles, cudaStream_t st) {
   const size_t smem = sizeof(Smem<C, IDX>);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_scatter<C, IDX, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<C, IDX, AXIS>, kThreads, smem);
+  cudaError_t e = resident_blocks<k_scatter<C, IDX, AXIS>>(kThreads, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   uint64_t grid = uint64_t(per_sm) * uint64_t(device_sm_count());

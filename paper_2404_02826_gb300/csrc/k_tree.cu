@@ -367,10 +367,8 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   const C *codes = static_cast<const C *>(a.src[axis]);
   if (a.warp_median) {
     const size_t msm = sizeof(uint32_t) * kMedBins * kMedWarps;
-    cudaError_t e = cudaFuncSetAttribute(k_median<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(msm));
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_median<C>, kMedWarps * 32, msm);
+    cudaError_t e = resident_blocks<k_median<C>>(kMedWarps * 32, msm, &per_sm);
     if (e != cudaSuccess) return e;
     uint64_t grid = uint64_t(per_sm < 1 ? 1 : per_sm) * uint64_t(device_sm_count());
     const uint64_t need = (count + kMedWarps - 1) / kMedWarps;

@@ -13,11 +13,13 @@ namespace pcx {
 int device_sm_count() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
-  static int cache[64] = {0};
-  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  static std::atomic<int> cache[64];
+  const int slot = dev & 63;
+  const int known = cache[slot].load(std::memory_order_relaxed);
+  if (known > 0) return known;
   int v = 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-  if (dev >= 0 && dev < 64) cache[dev] = v;
+  cache[slot].store(v, std::memory_order_relaxed);
   return v;
 }
 

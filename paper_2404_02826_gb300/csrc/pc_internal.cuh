@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/pc.h"
@@ -219,6 +221,32 @@ uint64_t decode_table_bytes();
 uint64_t decode_chunk_bytes(uint64_t n);
 
 int device_sm_count();
+
+// Blocks of kernel F resident per SM with `smem` bytes of dynamic shared
+// memory, after raising the kernel's dynamic shared-memory limit to `smem`.
+// Both are done once per device and kernel (F itself is the template
+// argument, so every kernel has its own cache); safe from several host threads.
+template <auto F>
+cudaError_t resident_blocks(int threads, size_t smem, int *per_sm) {
+  static std::atomic<int> cache[64];  // per device: blocks per SM + 1, 0 = not yet known
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int slot = dev & 63;
+  const int known = cache[slot].load(std::memory_order_acquire);
+  if (known > 0) {
+    *per_sm = known - 1;
+    return cudaSuccess;
+  }
+  e = cudaFuncSetAttribute(F, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int v = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, F, threads, smem);
+  if (e != cudaSuccess) return e;
+  cache[slot].store(v + 1, std::memory_order_release);
+  *per_sm = v;
+  return cudaSuccess;
+}
 
 // pc_compress without the optional permutation, on a caller-provided workspace.
 int compress_device(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
