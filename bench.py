@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch-256", "serve-2000"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--leaf-size", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
@@ -410,8 +410,232 @@ def measure_e2e(pc, pos_h, pdt, emode, eb, args, world):
             "api": "pc_compress_host + pc_decompress_host (pinned host buffers)"}
 
 
+BATCH_WORKLOAD = "batch-256"
+SERVE_WORKLOAD = "serve-2000"
+
+
+def _pools(dev, size, gens, dtypes):
+    """Device copies of one synthetic snapshot per generator and dtype; requests take slices of them."""
+    import numpy as np
+    import torch
+
+    out = {}
+    for g in gens:
+        for dt in dtypes:
+            out[(g, dt)] = torch.from_numpy(generate(g, size, dt, seed=0)).to(dev)
+    return out
+
+
+def run_batch(args):
+    """Many snapshots of uneven size, dtype and bound: one pc_compress_batch (and
+    pc_decompress_batch) call against one plain call per snapshot."""
+    import numpy as np
+    import torch
+
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as pcbuild
+
+    world, rank, local = dist_setup(args)
+    if rank == 0:
+        pcbuild.build()
+    barrier(world)
+    pc.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(rank)
+    pool_n = 1 << 24
+    pools = _pools(dev, pool_n, ("cosmology", "fluid"), ("f32", "f64"))
+    jobs = []
+    for _ in range(256):
+        n = int(round(10 ** rng.uniform(4, 7)))
+        g = "cosmology" if rng.random() < 0.5 else "fluid"
+        dt = "f32" if rng.random() < 0.5 else "f64"
+        eb = float(rng.choice([1e-2, 1e-3, 1e-4]))
+        off = int(rng.integers(0, pool_n - n + 1))
+        jobs.append((pools[(g, dt)][off: off + n], pc.PC_EB_REL, eb, args.leaf_size))
+    dtype_of = lambda t: pc.PC_F32 if t.dtype == torch.float32 else pc.PC_F64
+    outs = [torch.empty(pc.pc_compress_bound(p.shape[0], dtype_of(p), leaf), dtype=torch.uint8, device=dev)
+            for p, _, _, leaf in jobs]
+    lanes = 8
+    ws = torch.empty(pc.pc_compress_batch_workspace_size([(p.shape[0], dtype_of(p), leaf) for p, _, _, leaf in jobs],
+                                                         lanes), dtype=torch.uint8, device=dev)
+    decs = [torch.empty_like(p) for p, _, _, _ in jobs]
+    nbytes = sum(p.numel() * p.element_size() for p, _, _, _ in jobs)
+    particles = sum(p.shape[0] for p, _, _, _ in jobs)
+
+    def batched():
+        sizes, st = pc.pc_compress_batch(jobs, outs, workspace=ws, lanes=lanes)
+        assert all(x == pc.PC_OK for x in st)
+        t1 = time.perf_counter()
+        st = pc.pc_decompress_batch(outs, sizes, decs, lanes=lanes)
+        assert all(x == pc.PC_OK for x in st)
+        return sizes, t1
+
+    big = max(jobs, key=lambda j: j[0].shape[0])[0]
+    seq = pc.Compressor(big.shape[0], pc.PC_F64, leaf_size=args.leaf_size, device=dev)
+
+    def sequential():
+        sizes = []
+        for (p, m, eb, leaf), o in zip(jobs, outs):
+            sizes.append(pc.pc_compress(p, m, eb, o, seq.ws, leaf))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for o, sz, d in zip(outs, sizes, decs):
+            pc.pc_decompress(o, d, seq.dws, sz)
+        return sizes, t1
+
+    results = {}
+    for name, fn in (("sequential", sequential), ("batched", batched)):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        tc = td = 0.0
+        for _ in range(args.steps):
+            barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sizes, t1 = fn()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            tc += t1 - t0
+            td += t2 - t1
+        tc = max_over_ranks(tc, world)
+        td = max_over_ranks(td, world)
+        results[name] = {"compress_gbs": round(whole_job_gbs(world, nbytes, args.steps, 1e3 * tc), 3),
+                         "decompress_gbs": round(whole_job_gbs(world, nbytes, args.steps, 1e3 * td), 3),
+                         "round_trip_gbs": round(whole_job_gbs(world, nbytes, args.steps, 1e3 * (tc + td)), 3),
+                         "ms_per_batch": round(1e3 * (tc + td) / args.steps, 3)}
+        results[name + "_sizes"] = sizes
+    # the batched streams are the plain calls' streams
+    same = results["batched_sizes"] == results["sequential_sizes"]
+    if rank == 0:
+        b, q = results["batched"], results["sequential"]
+        line = {
+            "metric": "batched compress+decompress throughput (uncompressed bytes)", "value": b["round_trip_gbs"],
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": b["ms_per_batch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "snapshots": len(jobs), "particles": particles,
+                       "sizes": "round(10^U(4,7))", "generators": "cosmology or fluid slices, p = 1/2",
+                       "eb": "rel, one of 1e-2 1e-3 1e-4", "leaf_size": args.leaf_size, "lanes": lanes,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
+            "batched": b, "one_call_per_snapshot": q,
+            "speedup_round_trip": round(b["round_trip_gbs"] / q["round_trip_gbs"], 3),
+            "identical_sizes": bool(same),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_serve(args, lanes_list=(8, 1)):
+    """Poisson arrivals of compress (70 %) and decompress (30 %) requests through
+    the library's serving loop; latency from submission to completion.  The
+    same trace also runs saturated (every request submitted at once), where the
+    overlap of several lanes shows as throughput."""
+    import numpy as np
+    import torch
+
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as pcbuild
+
+    world, rank, local = dist_setup(args)
+    if rank == 0:
+        pcbuild.build()
+    barrier(world)
+    pc.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(rank)
+    pool_n = 50_000_000
+    pool = torch.from_numpy(generate("cosmology", pool_n, "f32", seed=0)).to(dev)
+    count, rate = 2000, 200.0
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+    kinds = rng.random(count) < 0.7
+    sizes = np.round(10 ** rng.uniform(5, np.log10(5e7), count)).astype(np.int64)
+    ebs = rng.choice([1e-3, 1e-4], count)
+    offs = [int(rng.integers(0, pool_n - n + 1)) for n in sizes]
+    arena = torch.empty(40 << 30, dtype=torch.uint8, device=dev)
+    report = {}
+    runs = [(lanes, 1.0) for lanes in lanes_list] + [(lanes, 0.0) for lanes in lanes_list]
+    for lanes, stretch in runs:
+        srv = pc.Server(arena, lanes=lanes)
+        kept = []  # completed compress outputs kept for decompress requests: (completion, n)
+        busy = {}  # tag -> kept entry a decompress request reads
+        lat, done_bytes, t_first, t_last = [], 0, None, None
+        submitted = completed = 0
+        t0 = pc.Server.now() + 0.2
+        while completed < count:
+            now = pc.Server.now()
+            while submitted < count and t0 + stretch * arrivals[submitted] <= now:
+                i = submitted
+                if kinds[i] or not kept:
+                    n = int(sizes[i])
+                    srv.submit_compress(pool[offs[i]: offs[i] + n], pc.PC_EB_REL, float(ebs[i]), tag=i)
+                else:
+                    k = kept[int(rng.integers(0, len(kept)))]
+                    busy[i] = k
+                    k[2] += 1
+                    srv.submit_decompress(srv.output(k[0]), k[0].output_bytes, k[1], pc.PC_F32, tag=i)
+                submitted += 1
+            cs = srv.poll(wait=False)
+            for c in cs:
+                assert c.status == pc.PC_OK, (c.tag, c.status)
+                completed += 1
+                lat.append(c.t_done - c.t_submit)
+                t_first = c.t_submit if t_first is None else min(t_first, c.t_submit)
+                t_last = c.t_done if t_last is None else max(t_last, c.t_done)
+                if c.kind == pc.PC_REQ_COMPRESS:
+                    done_bytes += int(sizes[c.tag]) * 12
+                    kept.append([c, int(sizes[c.tag]), 0])
+                    while len(kept) > 16 and kept[0][2] == 0:
+                        srv.release(kept.pop(0)[0])
+                else:
+                    k = busy.pop(c.tag)
+                    done_bytes += k[1] * 12
+                    k[2] -= 1
+                    srv.release(c)
+            if not cs:
+                time.sleep(0.0002)
+        for k in kept:
+            srv.release(k[0])
+        srv.close()
+        lat_ms = np.array(lat) * 1e3
+        report[(lanes, stretch)] = {"p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                         "mean_ms": round(float(lat_ms.mean()), 3),
+                         "gbs": round(done_bytes / (t_last - t_first) / 1e9, 3)}
+    if rank == 0:
+        best = report[(lanes_list[0], 1.0)]
+        line = {
+            "metric": "served compress/decompress latency p99 (arrival to completion)", "value": best["p99_ms"],
+            "unit": "ms", "n_gpus": world, "steps": count, "warmup": 0, "ms_per_step": best["mean_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "requests": count, "arrivals": "Poisson, 200 per s",
+                       "mix": "70 % compress, 30 % decompress of a completed stream",
+                       "sizes": "round(10^U(5, log10 5e7)) particles, slices of one cosmology snapshot",
+                       "eb": "rel 1e-3 or 1e-4", "arena_bytes": 40 << 30, "lanes": lanes_list[0]},
+            "served": best, "one_lane": report[(lanes_list[-1], 1.0)],
+            "saturated": {"lanes": report[(lanes_list[0], 0.0)], "one_lane": report[(lanes_list[-1], 0.0)],
+                          "note": "all requests submitted at once"},
+            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "throughput_gbs": best["gbs"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.workload == BATCH_WORKLOAD:
+        run_batch(args)
+        return
+    if args.workload == SERVE_WORKLOAD:
+        run_serve(args)
+        return
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, spec)
