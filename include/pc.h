@@ -74,9 +74,23 @@ typedef enum { PC_EB_ABS = 0, PC_EB_REL = 1 } pc_eb_mode;
 
 /* Tuning knobs.  A NULL config means defaults. */
 typedef struct {
-    uint32_t leaf_size; /* r of Sec. 4.1: largest leaf; 0 = 4096; valid 1..PC_MAX_LEAF_SIZE */
-    uint32_t flags;     /* reserved, must be 0 */
+    uint32_t leaf_size; /* r of Sec. 4.1: largest leaf; 0 = 4096; valid 1..PC_MAX_LEAF_SIZE.
+                           With PC_FLAG_AUTOTUNE_LEAF: the largest candidate (0 = PC_MAX_LEAF_SIZE) */
+    uint32_t flags;     /* 0 or PC_FLAG_AUTOTUNE_LEAF */
 } pc_config;
+
+/* Leaf-size autotuning (no counterpart in the paper, which fixes r by hand,
+ * Sec. 5): the leaves of the median tree for r = ceil(n / 2^d) are its nodes
+ * at depth d, so the tree for a smaller leaf size extends the one for a larger
+ * size.  With this flag compression builds the tree level by level from the
+ * largest candidate depth on, computes the exact stream size of every
+ * candidate depth d (leaf records + packed words) as it reaches it, and keeps
+ * descending while the size shrinks; the stream uses the last depth before it
+ * grows, r = ceil(n / 2^d), within [min(PC_AUTOTUNE_MIN_LEAF, max), max] with
+ * max = leaf_size.  The header records that r, and a plain call with it
+ * gives the same stream. */
+#define PC_FLAG_AUTOTUNE_LEAF 1u
+#define PC_AUTOTUNE_MIN_LEAF 1024u
 
 #define PC_DEFAULT_LEAF_SIZE 4096u
 #define PC_MAX_LEAF_SIZE 12000u
@@ -185,8 +199,8 @@ typedef struct {
     int32_t dtype;          /* pc_dtype */
     int32_t eb_mode;        /* pc_eb_mode */
     double eb;
-    uint32_t leaf_size;     /* 0 = PC_DEFAULT_LEAF_SIZE */
-    uint32_t reserved;      /* 0 */
+    uint32_t leaf_size;     /* as pc_config.leaf_size */
+    uint32_t flags;         /* as pc_config.flags */
     void *out;              /* device, out_capacity bytes (pc_compress_bound suffices) */
     uint64_t out_capacity;
     uint64_t out_size;      /* written: stream bytes */
@@ -233,7 +247,9 @@ typedef struct {
     int32_t kind;           /* PC_REQ_COMPRESS or PC_REQ_DECOMPRESS */
     int32_t dtype;          /* pc_dtype of the positions (decompress: as in the stream header) */
     int32_t eb_mode;        /* compress: pc_eb_mode */
-    uint32_t leaf_size;     /* compress: 0 = PC_DEFAULT_LEAF_SIZE */
+    uint32_t leaf_size;     /* compress: as pc_config.leaf_size */
+    uint32_t flags;         /* compress: as pc_config.flags */
+    uint32_t reserved;      /* 0 */
     double eb;              /* compress */
     const void *input;      /* device: positions (compress) or stream (decompress) */
     uint64_t n;             /* particles */

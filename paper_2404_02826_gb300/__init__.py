@@ -37,6 +37,9 @@ PC_DEFAULT_LEAF_SIZE = 4096
 PC_MAX_LEAF_SIZE = 12000
 PC_HEADER_BYTES = 96
 PC_LEAF_BYTES = 32
+PC_FLAG_AUTOTUNE_LEAF = 1
+PC_AUTOTUNE_MIN_LEAF = 1024
+LEAF_AUTO = -1  # leaf_size argument: autotune with candidates up to PC_MAX_LEAF_SIZE
 
 # every entry point declared in include/pc.h
 EXPORTS = (
@@ -74,7 +77,7 @@ class pc_info(ctypes.Structure):
 class pc_compress_item(ctypes.Structure):
     _fields_ = [("positions", ctypes.c_void_p), ("n", ctypes.c_uint64), ("dtype", ctypes.c_int32),
                 ("eb_mode", ctypes.c_int32), ("eb", ctypes.c_double), ("leaf_size", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("out", ctypes.c_void_p), ("out_capacity", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("out", ctypes.c_void_p), ("out_capacity", ctypes.c_uint64),
                 ("out_size", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
@@ -86,7 +89,8 @@ class pc_decompress_item(ctypes.Structure):
 
 class pc_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("eb_mode", ctypes.c_int32),
-                ("leaf_size", ctypes.c_uint32), ("eb", ctypes.c_double), ("input", ctypes.c_void_p),
+                ("leaf_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("eb", ctypes.c_double), ("input", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("input_bytes", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
 
 
@@ -155,7 +159,12 @@ def _check(rc: int, where: str):
 
 
 def _cfg(leaf_size: int) -> pc_config:
-    return pc_config(int(leaf_size), 0)
+    """leaf_size >= 0: that leaf size (0 = default); leaf_size < 0: autotuned
+    (PC_FLAG_AUTOTUNE_LEAF) with largest candidate -leaf_size (LEAF_AUTO: the default maximum)."""
+    leaf_size = int(leaf_size)
+    if leaf_size < 0:
+        return pc_config(0 if leaf_size == LEAF_AUTO else -leaf_size, PC_FLAG_AUTOTUNE_LEAF)
+    return pc_config(leaf_size, 0)
 
 
 def _dtype_of(t) -> int:
@@ -338,9 +347,11 @@ def pc_compress_batch(jobs, outs, workspace=None, lanes: int = 0, stream=None):
     statuses); raises when the call itself fails.  The workspace (device
     uint8) is allocated here when not given."""
     import torch
-    rows = [pc_compress_item(p.data_ptr() if p.shape[0] else None, p.shape[0], _dtype_of(p), int(m), float(eb),
-                             int(leaf), 0, o.data_ptr(), o.numel(), 0, 0, 0)
-            for (p, m, eb, leaf), o in zip(jobs, outs)]
+    rows = []
+    for (p, m, eb, leaf), o in zip(jobs, outs):
+        c = _cfg(leaf)
+        rows.append(pc_compress_item(p.data_ptr() if p.shape[0] else None, p.shape[0], _dtype_of(p), int(m), float(eb),
+                                     c.leaf_size, c.flags, o.data_ptr(), o.numel(), 0, 0, 0))
     arr = _items(pc_compress_item, rows)
     if workspace is None:
         need = ctypes.c_uint64()
@@ -357,7 +368,8 @@ def pc_compress_batch(jobs, outs, workspace=None, lanes: int = 0, stream=None):
 
 def pc_compress_batch_workspace_size(ns_dtypes_leaves, lanes: int = 0) -> int:
     """Workspace bytes for snapshots given as (n, dtype, leaf_size)."""
-    rows = [pc_compress_item(None, n, dt, 0, 0.0, leaf, 0, None, 0, 0, 0, 0) for n, dt, leaf in ns_dtypes_leaves]
+    rows = [pc_compress_item(None, n, dt, 0, 0.0, _cfg(leaf).leaf_size, _cfg(leaf).flags, None, 0, 0, 0, 0)
+            for n, dt, leaf in ns_dtypes_leaves]
     need = ctypes.c_uint64()
     _check(_lib().pc_compress_batch_workspace_size(_items(pc_compress_item, rows), len(rows), lanes,
                                                    ctypes.byref(need)), "pc_compress_batch_workspace_size")
@@ -398,12 +410,13 @@ class Server:
         self.h = h
 
     def submit_compress(self, positions, eb_mode: int, eb: float, tag: int, leaf_size: int = 0):
-        r = pc_request(PC_REQ_COMPRESS, _dtype_of(positions), int(eb_mode), int(leaf_size), float(eb),
+        c = _cfg(leaf_size)
+        r = pc_request(PC_REQ_COMPRESS, _dtype_of(positions), int(eb_mode), c.leaf_size, c.flags, 0, float(eb),
                        positions.data_ptr(), positions.shape[0], 0, int(tag))
         _check(_lib().pc_server_submit(self.h, ctypes.byref(r)), "pc_server_submit")
 
     def submit_decompress(self, stream_data, nbytes: int, n: int, dtype: int, tag: int):
-        r = pc_request(PC_REQ_DECOMPRESS, int(dtype), 0, 0, 0.0, stream_data.data_ptr(), int(n), int(nbytes),
+        r = pc_request(PC_REQ_DECOMPRESS, int(dtype), 0, 0, 0, 0, 0.0, stream_data.data_ptr(), int(n), int(nbytes),
                        int(tag))
         _check(_lib().pc_server_submit(self.h, ctypes.byref(r)), "pc_server_submit")
 

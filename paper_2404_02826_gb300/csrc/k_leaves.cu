@@ -299,6 +299,7 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
     TraceScope ts("k_leafscan", st);
     k_leafscan<<<1, 1024, 0, st>>>(a.recs, a.num_leaves, a.total_words);
   }
+  if (a.cost_only) return cudaGetLastError();
   TraceScope ts("k_leafpack", st);
   k_leafpack<C, IDX><<<unsigned(a.num_leaves), kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out, a.num_leaves,
                                                                       a.perm);

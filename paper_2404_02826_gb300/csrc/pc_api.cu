@@ -73,6 +73,9 @@ struct Plan {
   uint64_t off_zero = 0, zero_bytes = 0;  // zeroed at every call:
   uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_err = 0, off_total = 0;
   uint64_t off_groups = 0;
+  bool tune = false;  // leaf size chosen by descending from r_hi while the stream shrinks (sized for r)
+  uint32_t r_hi = 0;
+  int tune_first = 0, tune_last = 0;  // candidate depths
   uint64_t total = 0;
   int range_blocks = 0;
 };
@@ -115,9 +118,17 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_ARG;
   if (n > PC_MAX_PARTICLES) return PC_ERR_ARG;
   uint32_t r = PC_DEFAULT_LEAF_SIZE;
+  p.tune = false;
   if (cfg) {
-    if (cfg->flags != 0) return PC_ERR_ARG;
+    if (cfg->flags & ~PC_FLAG_AUTOTUNE_LEAF) return PC_ERR_ARG;
     if (cfg->leaf_size) r = cfg->leaf_size;
+    if (cfg->flags & PC_FLAG_AUTOTUNE_LEAF) {
+      // candidates: depths d with ceil(n / 2^d) in [min(PC_AUTOTUNE_MIN_LEAF, max), max]
+      p.tune = true;
+      p.r_hi = cfg->leaf_size ? cfg->leaf_size : PC_MAX_LEAF_SIZE;
+      if (p.r_hi < 16 || p.r_hi > PC_MAX_LEAF_SIZE) return PC_ERR_ARG;
+      r = p.r_hi < PC_AUTOTUNE_MIN_LEAF ? p.r_hi : PC_AUTOTUNE_MIN_LEAF;
+    }
   }
   if (r < 1 || r > PC_MAX_LEAF_SIZE) return PC_ERR_ARG;
   p.n = n;
@@ -126,6 +137,14 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   p.idx = idx;
   p.num_leaves = leaves_for(n, r);
   p.levels = split_levels(n, r);
+  if (p.tune) {
+    // the first candidate has the largest leaves <= r_hi; descend while leaves stay >= r.
+    // Leaves of >= 16 particles make every candidate a whole depth of the tree: no node
+    // above it is already that small.
+    p.tune_first = split_levels(n, p.r_hi);
+    p.tune_last = p.tune_first;
+    while (((n + (2ull << p.tune_last) - 1) >> (p.tune_last + 1)) >= r) ++p.tune_last;
+  }
   p.range_blocks = 4 * (sm_count > 0 ? sm_count : 148);
   if (p.range_blocks > 1024) p.range_blocks = 1024;
 
@@ -335,13 +354,55 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     qa.blocks = 8 * device_sm_count();
     PC_TRY(launch_quantize(qa, st));
 
-    // a3: the k-d levels, down to the leaves
-    const int levels = p.levels;
+    // a3: the k-d levels, down to the leaves (autotuning: down to the deepest candidate at most)
+    const int levels = p.tune ? p.tune_last : p.levels;
+    // a4-a5 on the arrangement at depth `depth` (leaves = its 2^depth nodes when split_level = depth - 1)
+    auto leaf_launch = [&](void *const *codes, const uint32_t *idxs, int split_level, uint32_t r,
+                           uint64_t num_leaves, bool cost_only) {
+      LeafLaunch lf = {};
+      lf.n = n;
+      lf.split_level = split_level;
+      lf.code_bytes = cb;
+      lf.leaf_size = r;
+      lf.num_leaves = num_leaves;
+      for (int d = 0; d < 3; ++d) lf.codes[d] = codes[d];
+      lf.idx = idxs;
+      lf.out = static_cast<uint8_t *>(out);
+      lf.perm = perm;
+      lf.recs = reinterpret_cast<LeafRec *>(ws + p.off_leafrec);
+      lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
+      lf.cost_only = cost_only;
+      return launch_leaves(lf, st);
+    };
+    // autotuning: stream bytes of the leaves at `depth` (every node there is a leaf)
+    auto depth_cost = [&](void *const *codes, int depth, uint64_t *bytes) -> int {
+      const uint64_t r = (n + (1ull << depth) - 1) >> depth;
+      PC_TRY(leaf_launch(codes, nullptr, depth - 1, uint32_t(r), 1ull << depth, true));
+      uint64_t words = 0;
+      PC_TRY(cudaMemcpyAsync(&words, ws + p.off_words, 8, cudaMemcpyDeviceToHost, st));
+      PC_TRY(cudaStreamSynchronize(st));
+      *bytes = uint64_t(PC_LEAF_BYTES) * (1ull << depth) + 4 * words;
+      return PC_OK;
+    };
+    int chosen = -1;            // autotuning: depth of the chosen leaves
+    uint64_t best_bytes = 0;    // stream bytes (without header) at the shallower candidate
+    const int first_depth = p.tune_first;
     LevelNode *nodes = reinterpret_cast<LevelNode *>(ws + p.off_nodes);
     uint64_t node_base = 0, tile_base = 0;
     void **src = codes_a, **dst = codes_b;
     uint32_t *isrc = idx_a, *idst = idx_b;
     for (int l = 0; l < levels; ++l) {
+      if (p.tune && l >= first_depth) {
+        // src holds the arrangement at depth l, dst the one at depth l - 1
+        uint64_t bytes = 0;
+        rc = depth_cost(src, l, &bytes);
+        if (rc) return rc;
+        if (l > first_depth && bytes >= best_bytes) {
+          chosen = l - 1;
+          break;
+        }
+        best_bytes = bytes;
+      }
       LevelLaunch la = {};
       la.n = n;
       la.level = l;
@@ -381,20 +442,30 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     }
 
     // a4-a5: bit boxes, payload offsets, packing
-    LeafLaunch lf = {};
-    lf.n = n;
-    lf.split_level = levels - 1;
-    lf.code_bytes = cb;
-    lf.leaf_size = p.r;
-    lf.num_leaves = p.num_leaves;
-    for (int d = 0; d < 3; ++d) lf.codes[d] = src[d];
-    lf.idx = isrc;
-    lf.out = static_cast<uint8_t *>(out);
-    lf.perm = perm;
-    lf.recs = reinterpret_cast<LeafRec *>(ws + p.off_leafrec);
-    lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
-    PC_TRY(launch_leaves(lf, st));
-    hl.total_words = lf.total_words;
+    if (!p.tune) {
+      PC_TRY(leaf_launch(src, isrc, levels - 1, p.r, p.num_leaves, false));
+    } else {
+      // the loop stopped at the first depth whose stream is not smaller, or built
+      // every level: then the smallest candidate (depth `levels`, in src) is compared too
+      if (chosen < 0) {
+        chosen = levels;
+        if (levels > first_depth) {
+          uint64_t bytes = 0;
+          rc = depth_cost(src, levels, &bytes);
+          if (rc) return rc;
+          if (bytes >= best_bytes) chosen = levels - 1;
+        }
+      }
+      const int depth = chosen;
+      const bool deepest = depth == levels;  // src holds depth `levels`, dst depth `levels - 1`
+      void **codes = deepest ? src : dst;
+      uint32_t *idxs = deepest ? isrc : idst;
+      const uint64_t r = depth ? (n + (1ull << depth) - 1) >> depth : n;
+      hl.leaf_size = uint32_t(r);
+      hl.num_leaves = 1ull << depth;
+      PC_TRY(leaf_launch(codes, idxs, depth - 1, uint32_t(r), 1ull << depth, false));
+    }
+    hl.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
   }
   hl.eps = L.eps;
   hl.s = L.s;

@@ -38,8 +38,8 @@ uint32_t pick_lanes(uint32_t lanes, uint32_t count) {
   return lanes ? lanes : 1;
 }
 
-uint64_t compress_scratch(uint64_t n, int dtype, uint32_t leaf_size, uint64_t *bytes) {
-  pc_config cfg = {leaf_size, 0};
+uint64_t compress_scratch(uint64_t n, int dtype, uint32_t leaf_size, uint32_t flags, uint64_t *bytes) {
+  pc_config cfg = {leaf_size, flags};
   return uint64_t(pc_compress_workspace_size(n, dtype, &cfg, 0, bytes));
 }
 
@@ -178,7 +178,7 @@ struct pc_server {
   // Arena bytes a request needs while it runs (scratch) and after (output).
   static int needs(const pc_request &r, uint64_t *scratch, uint64_t *output) {
     if (r.kind == PC_REQ_COMPRESS) {
-      pc_config cfg = {r.leaf_size, 0};
+      pc_config cfg = {r.leaf_size, r.flags};
       int rc = pc_compress_workspace_size(r.n, r.dtype, &cfg, 0, scratch);
       if (rc) return rc;
       return pc_compress_bound(r.n, r.dtype, &cfg, output);
@@ -249,7 +249,7 @@ struct pc_server {
       c.output = base + ooff;
       const pc_request &r = job.req;
       if (r.kind == PC_REQ_COMPRESS) {
-        pc_config cfg = {r.leaf_size, 0};
+        pc_config cfg = {r.leaf_size, r.flags};
         uint64_t size = 0;
         c.status = pcx::compress_device(r.input, r.n, r.dtype, r.eb_mode, r.eb, &cfg, base + ooff, obytes, &size,
                                         base + soff, sbytes, s);
@@ -283,7 +283,7 @@ int pc_compress_batch_workspace_size(const pc_compress_item *items, uint32_t cou
   uint64_t slice = kArenaAlign;
   for (uint32_t i = 0; i < count; ++i) {
     uint64_t b = 0;
-    int rc = int(compress_scratch(items[i].n, items[i].dtype, items[i].leaf_size, &b));
+    int rc = int(compress_scratch(items[i].n, items[i].dtype, items[i].leaf_size, items[i].flags, &b));
     if (rc) return rc;
     slice = std::max(slice, align_up(b));
   }
@@ -307,7 +307,7 @@ int pc_compress_batch(pc_compress_item *items, uint32_t count, uint32_t lanes, v
   uint8_t *ws = static_cast<uint8_t *>(workspace);
   rc = run_lanes(lanes, order, static_cast<cudaStream_t>(stream), [&](uint32_t lane, cudaStream_t s, uint32_t i) {
     pc_compress_item &it = items[i];
-    pc_config cfg = {it.leaf_size, 0};
+    pc_config cfg = {it.leaf_size, it.flags};
     uint64_t size = 0;
     it.status = pcx::compress_device(it.positions, it.n, it.dtype, it.eb_mode, it.eb, &cfg, it.out, it.out_capacity,
                                      &size, ws + lane * slice, slice, s);

@@ -87,3 +87,20 @@ def test_argument_errors_without_gpu(pc):
     assert e.value.status == pc.PC_ERR_CORRUPT
     with pytest.raises(pc.PCError):
         pc.pc_compress_bound(1 << 31, pc.PC_F32)
+
+
+def test_autotune_flag_sizes_and_rejections(pc):
+    """Autotuning sizes the stream bound and the workspace for its smallest
+    candidate (PC_AUTOTUNE_MIN_LEAF); unknown flag bits and maxima below 16 are
+    rejected."""
+    n = 1_000_000
+    auto = pc.pc_compress_bound(n, pc.PC_F32, pc.LEAF_AUTO)
+    assert auto == pc.pc_compress_bound(n, pc.PC_F32, pc.PC_AUTOTUNE_MIN_LEAF)
+    assert pc.pc_compress_workspace_size(n, pc.PC_F32, pc.LEAF_AUTO) >= pc.pc_compress_workspace_size(n, pc.PC_F32)
+    assert pc.pc_compress_bound(n, pc.PC_F32, -512) == pc.pc_compress_bound(n, pc.PC_F32, 512)
+    cfg = pc.pc_config(0, 2)
+    out = pc.ctypes.c_uint64()
+    assert pc.load().pc_compress_bound(n, pc.PC_F32, pc.ctypes.byref(cfg), pc.ctypes.byref(out)) == pc.PC_ERR_ARG
+    with pytest.raises(pc.PCError) as e:
+        pc.pc_compress_bound(n, pc.PC_F32, -8)
+    assert e.value.status == pc.PC_ERR_ARG

@@ -143,6 +143,37 @@ def test_parity_float64_wide_codes(pc, oracle_mod):
     check_against_oracle(pc, oracle_mod, pos, pc.PC_EB_ABS, 1e-9, 4096)
 
 
+@pytest.mark.parametrize("gen,n,dtype,mode,eb", [
+    ("cosmology", 300_000, np.float32, "rel", 1e-4),
+    ("uniform", 200_003, np.float32, "rel", 1e-3),
+    ("fluid", 150_000, np.float64, "abs", 1e-4),
+])
+def test_autotuned_leaf_size(pc, oracle_mod, gen, n, dtype, mode, eb):
+    """The autotuned stream is the oracle's stream at the leaf size it records,
+    and that leaf size is a local minimum of the stream size over the candidate
+    depths (ceil(n / 2^d) between PC_AUTOTUNE_MIN_LEAF and PC_MAX_LEAF_SIZE)."""
+    pos = synth.by_name(gen, n, seed=11, dtype=dtype)
+    m = pc.PC_EB_ABS if mode == "abs" else pc.PC_EB_REL
+    om = oracle_mod.ABS if mode == "abs" else oracle_mod.REL
+    got, perm, dec = run_gpu(pc, pos, m, eb, pc.LEAF_AUTO)
+    r = pc.pc_stream_info(got[:96]).leaf_size
+    ref, ref_perm = oracle_mod.compress(pos, om, eb, leaf_size=r)
+    assert got == ref and np.array_equal(perm, ref_perm)
+    assert dec.tobytes() == oracle_mod.decompress(ref).tobytes()
+    ceil_at = lambda d: -(-n // (1 << d))
+    depths = [d for d in range(40) if ceil_at(d) <= pc.PC_MAX_LEAF_SIZE]
+    first = depths[0]
+    cands = [first] + [d for d in depths[1:] if ceil_at(d) >= pc.PC_AUTOTUNE_MIN_LEAF]
+    chosen = [d for d in cands if ceil_at(d) == r]
+    assert len(chosen) == 1
+    d = chosen[0]
+    size = len(ref)
+    if d - 1 in cands:
+        assert len(oracle_mod.compress(pos, om, eb, leaf_size=ceil_at(d - 1), want_perm=False)[0]) > size
+    if d + 1 in cands:
+        assert len(oracle_mod.compress(pos, om, eb, leaf_size=ceil_at(d + 1), want_perm=False)[0]) >= size
+
+
 def test_parity_without_perm(pc, oracle_mod):
     pos = synth.cosmology(120_000, seed=8)
     check_against_oracle(pc, oracle_mod, pos, pc.PC_EB_REL, 1e-4, 4096, with_perm=False)
