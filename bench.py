@@ -452,7 +452,7 @@ def run_batch(args):
         dt = "f32" if rng.random() < 0.5 else "f64"
         eb = float(rng.choice([1e-2, 1e-3, 1e-4]))
         off = int(rng.integers(0, pool_n - n + 1))
-        jobs.append((pools[(g, dt)][off: off + n], pc.PC_EB_REL, eb, args.leaf_size))
+        jobs.append((pools[(g, dt)][off: off + n], pc.PC_EB_REL, eb, pc.LEAF_AUTO))
     dtype_of = lambda t: pc.PC_F32 if t.dtype == torch.float32 else pc.PC_F64
     outs = [torch.empty(pc.pc_compress_bound(p.shape[0], dtype_of(p), leaf), dtype=torch.uint8, device=dev)
             for p, _, _, leaf in jobs]
@@ -472,7 +472,7 @@ def run_batch(args):
         return sizes, t1
 
     big = max(jobs, key=lambda j: j[0].shape[0])[0]
-    seq = pc.Compressor(big.shape[0], pc.PC_F64, leaf_size=args.leaf_size, device=dev)
+    seq = pc.Compressor(big.shape[0], pc.PC_F64, leaf_size=pc.LEAF_AUTO, device=dev)
 
     def sequential():
         sizes = []
@@ -516,11 +516,12 @@ def run_batch(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "snapshots": len(jobs), "particles": particles,
                        "sizes": "round(10^U(4,7))", "generators": "cosmology or fluid slices, p = 1/2",
-                       "eb": "rel, one of 1e-2 1e-3 1e-4", "leaf_size": args.leaf_size, "lanes": lanes,
+                       "eb": "rel, one of 1e-2 1e-3 1e-4", "leaf_size": "autotuned (1024..12000)", "lanes": lanes,
                        "parallelism": f"replicas x{world}" if world > 1 else "single"},
             "batched": b, "one_call_per_snapshot": q,
             "speedup_round_trip": round(b["round_trip_gbs"] / q["round_trip_gbs"], 3),
             "identical_sizes": bool(same),
+            "compression_ratio": round(nbytes / sum(results["batched_sizes"]), 4),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
