@@ -11,8 +11,10 @@
 //   k_leafscan   exclusive scan of the payload words: each leaf's first word;
 //   k_leafpack   one CTA per leaf: its 32-byte record, its payload and the
 //                optional permutation.  A warp packs 32 consecutive particles
-//                at a time; 32 particles of w bits fill exactly w words, so each
-//                lane assembles whole words from the staged w-bit values.
+//                at a time; 32 particles of w bits fill exactly w words: each
+//                lane shifts its w-bit value to its bit offset (funnel shifts
+//                on 32-bit limbs) and ORs the pieces into the warp's words in
+//                shared memory, which then go out as whole, contiguous words.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__
                                                            const C *__restrict__ q2, const uint32_t *__restrict__ idx,
                                                            const LeafRec *__restrict__ recs, uint8_t *out,
                                                            uint64_t num_leaves, uint32_t *perm) {
-  __shared__ uint32_t sv[kPackWarps][32][3];
+  __shared__ uint32_t swords[kPackWarps][96];  // one chunk's words per warp (w <= 93)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const LeafRec rec = recs[blockIdx.x];
   const uint32_t off = rec.off, cnt = rec.cnt, centre = rec.centre;
@@ -246,36 +248,44 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__
   const uint32_t slots = cnt - 1;
   const uint32_t words = rec.words;
   const uint32_t chunks = (slots + 31) / 32;
+  uint32_t *sw = swords[warp];
   for (uint32_t ch = warp; ch < chunks; ch += kPackWarps) {
-    // this lane's particle as one w-bit value: c_x | c_y << m_x | c_z << (m_x + m_y)
+    // this lane's particle as one w-bit value c_x | c_y << m_x | c_z << (m_x + m_y), in three 32-bit limbs
     const uint32_t s = ch * 32 + lane;
-    unsigned __int128 V = 0;
+    uint32_t v0 = 0, v1 = 0, v2 = 0;
     if (s < slots) {
       const uint32_t p = off + (s < centre ? s : s + 1);
       const uint32_t cx = m0 ? uint32_t(q0[p]) - r0 + h0 : 0u;
       const uint32_t cy = m1 ? uint32_t(q1[p]) - r1 + h1 : 0u;
       const uint32_t cz = m2 ? uint32_t(q2[p]) - r2 + h2 : 0u;
-      V = (unsigned __int128)cx | ((unsigned __int128)cy << m0) | ((unsigned __int128)cz << (m0 + m1));
+      const unsigned long long y = (unsigned long long)cy << m0;  // m_x <= 31
+      v0 = cx | uint32_t(y);
+      v1 = uint32_t(y >> 32);
+      const uint32_t s2 = m0 + m1;  // <= 62
+      const unsigned long long z = (unsigned long long)cz << (s2 & 31);
+      if (s2 < 32) {
+        v0 |= uint32_t(z);
+        v1 |= uint32_t(z >> 32);
+      } else {
+        v1 |= uint32_t(z);
+        v2 = uint32_t(z >> 32);
+      }
     }
-    sv[warp][lane][0] = uint32_t(V);
-    sv[warp][lane][1] = uint32_t(V >> 32);
-    sv[warp][lane][2] = uint32_t(V >> 64);
+    // the 32 values fill exactly w words of this chunk; lane i's value starts at bit i * w
+    for (uint32_t t = lane; t < w; t += 32) sw[t] = 0;
     __syncwarp();
-    // the 32 values occupy exactly w words of this chunk
+    if (s < slots) {
+      const uint32_t b = lane * w, k0 = b >> 5, sh = b & 31;
+      const uint32_t nw = (sh + w + 31) >> 5;  // words this value touches, <= 4
+      atomicOr(&sw[k0], v0 << sh);
+      if (nw > 1) atomicOr(&sw[k0 + 1], __funnelshift_l(v0, v1, sh));
+      if (nw > 2) atomicOr(&sw[k0 + 2], __funnelshift_l(v1, v2, sh));
+      if (nw > 3) atomicOr(&sw[k0 + 3], __funnelshift_l(v2, 0u, sh));
+    }
+    __syncwarp();
     for (uint32_t t = lane; t < w; t += 32) {
       const uint32_t gw = ch * w + t;
-      if (gw >= words) break;
-      const uint32_t b0 = 32 * t;
-      const uint32_t i0 = b0 / w, i1 = min((b0 + 31) / w, 31u);
-      uint32_t word = 0;
-      for (uint32_t i = i0; i <= i1; ++i) {
-        const unsigned __int128 Vi = (unsigned __int128)sv[warp][i][0] | ((unsigned __int128)sv[warp][i][1] << 32) |
-                                     ((unsigned __int128)sv[warp][i][2] << 64);
-        const uint32_t start = i * w;  // bit of this value within the chunk
-        if (start >= b0) word |= uint32_t(Vi << (start - b0));
-        else word |= uint32_t(Vi >> (b0 - start));
-      }
-      __stcs(payload + gw, word);
+      if (gw < words) __stcs(payload + gw, sw[t]);
     }
     __syncwarp();
   }
