@@ -218,15 +218,38 @@ def oracle_round_trip(pos, mode, eb, leaf_size):
     return len(stream)
 
 
+def oracle_round_trip_parallel(pos, mode, eb, leaf_size):
+    import oracle
+
+    m = oracle.REL if mode == "rel" else oracle.ABS
+    stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=True)
+    oracle.decompress(stream, parallel=True)
+    return len(stream)
+
+
 def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE):
     gen, n, dtype, mode, eb = spec
     pos = generate(gen, n_sample, dtype, seed=0)
     t0 = time.perf_counter()
     oracle_round_trip(pos, mode, eb, leaf_size)
     dt = time.perf_counter() - t0
-    return {"value": round(pos.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_sample} particles of the {gen} generator ({dtype}, {mode} eb {eb}), one compress + "
-                      f"decompress in {dt:.2f} s"}
+    out = {"value": round(pos.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n_sample} particles of the {gen} generator ({dtype}, {mode} eb {eb}), one compress + "
+                     f"decompress in {dt:.2f} s"}
+    # the same oracle source built with OpenMP, on every host core, on a 4x larger sample
+    import oracle
+
+    oracle.build(parallel=True)
+    big = generate(gen, 4 * n_sample, dtype, seed=0)
+    oracle_round_trip_parallel(big[: 1 << 16], mode, eb, leaf_size)  # thread pool start-up
+    t0 = time.perf_counter()
+    oracle_round_trip_parallel(big, mode, eb, leaf_size)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out["parallel"] = {"value": round(big.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": cores,
+                       "kind": "oracle, OpenMP build of the same source",
+                       "sample": f"{4 * n_sample} particles, one compress + decompress in {dt:.2f} s"}
+    return out
 
 
 def run_reference(args, spec):

@@ -24,6 +24,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "_liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_liboracle_omp.so")  # the same source built with -fopenmp
 
 OK, ERR_ARG, ERR_NONFINITE, ERR_EB_TOO_SMALL, ERR_RANGE, ERR_CAPACITY, ERR_CORRUPT = range(7)
 F32, F64 = 0, 1
@@ -36,16 +37,18 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no floating-point contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no floating-point contraction); with
+    parallel=True the same source with -fopenmp."""
+    target = _LIB_OMP if parallel else _LIB
+    if not force and os.path.exists(target) and os.path.getmtime(target) >= os.path.getmtime(_SRC):
+        return target
+    tmp = target + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"] + \
+          (["-fopenmp"] if parallel else []) + ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, target)
+    return target
 
 
 class _Bound(ctypes.Structure):
@@ -54,14 +57,13 @@ class _Bound(ctypes.Structure):
                 ("o", ctypes.c_double * 3), ("qmax", ctypes.c_int64 * 3)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+def lib(parallel: bool = False):
+    """The oracle library; parallel=True loads the OpenMP build of the same source."""
+    if parallel not in _libs:
+        L = ctypes.CDLL(build(parallel=parallel))
         u64, i32, dbl, vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
         L.oracle_error_bound.argtypes = [vp, u64, i32, i32, dbl, ctypes.POINTER(_Bound)]
         L.oracle_quantize.argtypes = [vp, u64, i32, ctypes.POINTER(_Bound), vp]
@@ -82,8 +84,8 @@ def lib():
         L.oracle_num_leaves.argtypes = [u64, u64]
         L.oracle_num_leaves.restype = u64
         L.oracle_free.argtypes = [vp]
-        _lib = L
-    return _lib
+        _libs[parallel] = L
+    return _libs[parallel]
 
 
 def _dtype_code(arr: np.ndarray) -> int:
@@ -188,25 +190,26 @@ def bitbox(leafq: np.ndarray):
     return int(c.value), lo, hi, qref, m.astype(np.int64)
 
 
-def compress(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: bool = True):
+def compress(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: bool = True, parallel: bool = False):
     """Full compression.  Returns (stream bytes, perm) with perm[decoded i] = original index."""
     pos = _positions(pos)
     out = ctypes.c_void_p()
     nbytes = ctypes.c_uint64()
     perm = ctypes.c_void_p()
-    rc = lib().oracle_compress(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), eb_mode,
+    L = lib(parallel)
+    rc = L.oracle_compress(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), eb_mode,
                                float(eb), leaf_size, ctypes.byref(out), ctypes.byref(nbytes),
                                ctypes.byref(perm) if want_perm else None)
     if rc:
         raise OracleError(rc, "compress")
     stream = ctypes.string_at(out, nbytes.value)
-    lib().oracle_free(out)
+    L.oracle_free(out)
     p = None
     if want_perm:
         n = pos.shape[0]
         p = np.ctypeslib.as_array(ctypes.cast(perm, ctypes.POINTER(ctypes.c_uint64)), (n,)).astype(np.int64) \
             if n else np.zeros(0, np.int64)
-        lib().oracle_free(perm)
+        L.oracle_free(perm)
     return stream, p
 
 
@@ -221,12 +224,12 @@ def stream_header(stream: bytes):
     return n.value, dt.value, nl.value, nw.value
 
 
-def decompress(stream: bytes) -> np.ndarray:
+def decompress(stream: bytes, parallel: bool = False) -> np.ndarray:
     """Sec. 3 dequantization of every sequence; returns positions [n, 3] in stream order."""
     n, dt, _, _ = stream_header(stream)
     out = np.zeros((n, 3), np.float32 if dt == F32 else np.float64)
     buf = ctypes.create_string_buffer(stream, len(stream))
-    rc = lib().oracle_decompress(buf, len(stream), out.ctypes.data if n else None, out.nbytes)
+    rc = lib(parallel).oracle_decompress(buf, len(stream), out.ctypes.data if n else None, out.nbytes)
     if rc:
         raise OracleError(rc, "decompress")
     return out

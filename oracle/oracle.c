@@ -3,9 +3,13 @@
  * Ren, Di, Zhang, Zhao, Guo, "An Error-Bounded Lossy Compression Method with
  * Bit-Adaptive Quantization for Particle Data" (arXiv 2404.02826).
  *
- * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-threaded CPU
- * restatement of the method, in double precision, written to check the CUDA
- * library against.  Only tests/, __graft_entry__.smoke() and the CPU-baseline
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow CPU restatement of the
+ * method, in double precision, written to check the CUDA library against.
+ * Compiled as usual it is single-threaded.  The same source compiled with
+ * -fopenmp runs its independent loops in parallel (particles in the range
+ * and quantization, the two halves of every split, leaves in the bit boxes,
+ * the packing and the decoding); every particle's arithmetic and every
+ * output byte are the same, and the leaves are listed in the same order.  Only tests/, __graft_entry__.smoke() and the CPU-baseline
  * legs of bench.py load it; the product path never calls it.  It shares no
  * code, header, table or helper with the CUDA library.
  *
@@ -113,17 +117,26 @@ int oracle_error_bound(const void *pos, uint64_t n, int dtype, int eb_mode, doub
         b->eb_prime = b->eps;
         return OR_OK;
     }
-    for (int d = 0; d < 3; d++) {
-        b->lo[d] = INFINITY;
-        b->hi[d] = -INFINITY;
+    double lo0 = INFINITY, lo1 = INFINITY, lo2 = INFINITY, hi0 = -INFINITY, hi1 = -INFINITY, hi2 = -INFINITY;
+    int bad = 0;
+#pragma omp parallel for reduction(min : lo0, lo1, lo2) reduction(max : hi0, hi1, hi2) reduction(| : bad)
+    for (uint64_t i = 0; i < n; i++) {
+        double x = coord(pos, dtype, i, 0), y = coord(pos, dtype, i, 1), z = coord(pos, dtype, i, 2);
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) bad = 1;
+        if (x < lo0) lo0 = x;
+        if (x > hi0) hi0 = x;
+        if (y < lo1) lo1 = y;
+        if (y > hi1) hi1 = y;
+        if (z < lo2) lo2 = z;
+        if (z > hi2) hi2 = z;
     }
-    for (uint64_t i = 0; i < n; i++)
-        for (int d = 0; d < 3; d++) {
-            double v = coord(pos, dtype, i, d);
-            if (!isfinite(v)) return OR_ERR_NONFINITE;
-            if (v < b->lo[d]) b->lo[d] = v;
-            if (v > b->hi[d]) b->hi[d] = v;
-        }
+    if (bad) return OR_ERR_NONFINITE;
+    b->lo[0] = lo0;
+    b->lo[1] = lo1;
+    b->lo[2] = lo2;
+    b->hi[0] = hi0;
+    b->hi[1] = hi1;
+    b->hi[2] = hi2;
     /* A zero extremum is taken as +0, so that the result does not depend on
      * whether -0 or +0 was met first. */
     for (int d = 0; d < 3; d++) {
@@ -169,6 +182,7 @@ int oracle_error_bound(const void *pos, uint64_t n, int dtype, int eb_mode, doub
 
 int oracle_quantize(const void *pos, uint64_t n, int dtype, const oracle_bound *b, int64_t *q)
 {
+#pragma omp parallel for
     for (uint64_t i = 0; i < n; i++)
         for (int d = 0; d < 3; d++) q[3 * i + d] = quantize_one(coord(pos, dtype, i, d), b->o[d], b->s);
     return OR_OK;
@@ -224,11 +238,11 @@ static int leaf_push(leaf_list *l, uint64_t off, uint64_t cnt)
  * with at most r particles is a subregion (leaf).  Otherwise the node is split
  * by the median on axis depth mod 3: sorting the node by (code, index), the
  * first floor(cnt/2) particles form the left child, so the median itself lies
- * on the side with larger coordinates.  Both children keep index order. */
-static int split_node(const int64_t *q, uint64_t *ids, uint64_t base, uint64_t cnt, int depth, uint64_t r,
-                      leaf_list *leaves)
+ * on the side with larger coordinates.  Both children keep index order.  The
+ * two children own disjoint ranges of ids, so they may be ordered at once. */
+static int split_node(const int64_t *q, uint64_t *ids, uint64_t base, uint64_t cnt, int depth, uint64_t r)
 {
-    if (cnt <= r) return leaf_push(leaves, base, cnt);
+    if (cnt <= r) return OR_OK;
     int axis = depth % 3;
     keyed *tmp = malloc(cnt * sizeof(keyed));
     if (!tmp) return OR_ERR_NOMEM;
@@ -242,9 +256,23 @@ static int split_node(const int64_t *q, uint64_t *ids, uint64_t base, uint64_t c
     free(tmp);
     qsort(ids + base, k, sizeof(uint64_t), by_index);
     qsort(ids + base + k, cnt - k, sizeof(uint64_t), by_index);
-    int rc = split_node(q, ids, base, k, depth + 1, r, leaves);
+    int rc_left = OR_OK, rc_right = OR_OK;
+#pragma omp task shared(rc_left) if (cnt > 65536)
+    rc_left = split_node(q, ids, base, k, depth + 1, r);
+    rc_right = split_node(q, ids, base + k, cnt - k, depth + 1, r);
+#pragma omp taskwait
+    return rc_left ? rc_left : rc_right;
+}
+
+/* The subregions of the same recursion, left to right: they depend only on the
+ * node sizes, floor(cnt/2) and the rest. */
+static int collect_leaves(uint64_t base, uint64_t cnt, uint64_t r, leaf_list *leaves)
+{
+    if (cnt <= r) return leaf_push(leaves, base, cnt);
+    uint64_t k = cnt / 2;
+    int rc = collect_leaves(base, k, r, leaves);
     if (rc) return rc;
-    return split_node(q, ids, base + k, cnt - k, depth + 1, r, leaves);
+    return collect_leaves(base + k, cnt - k, r, leaves);
 }
 
 /* order[0..n): original indices, leaves concatenated left to right.
@@ -256,7 +284,12 @@ int oracle_kdtree(const int64_t *q, uint64_t n, uint64_t r, uint64_t *order, uin
     leaf_list l = {0};
     for (uint64_t i = 0; i < n; i++) order[i] = i;
     int rc = OR_OK;
-    if (n > 0) rc = split_node(q, order, 0, n, 0, r, &l);
+    if (n > 0) {
+#pragma omp parallel
+#pragma omp single
+        rc = split_node(q, order, 0, n, 0, r);
+        if (!rc) rc = collect_leaves(0, n, r, &l);
+    }
     if (rc) {
         free(l.leaf_off);
         free(l.leaf_cnt);
@@ -438,25 +471,32 @@ int oracle_compress(const void *pos, uint64_t n, int dtype, int eb_mode, double 
     wofs = malloc((nl ? nl : 1) * sizeof(uint64_t));
     qref = malloc((nl ? nl : 1) * 3 * sizeof(int64_t));
     mm = malloc((nl ? nl : 1) * 3 * sizeof(uint32_t));
-    uint64_t maxleaf = leaf_size < n ? leaf_size : n;
-    int64_t *leafq = malloc((maxleaf ? maxleaf : 1) * 3 * sizeof(int64_t));
-    if (!centre || !wofs || !qref || !mm || !leafq) {
-        free(leafq);
-        goto done;
-    }
+    if (!centre || !wofs || !qref || !mm) goto done;
     /* Bit boxes, and the size of each leaf's code block: storage-cost term (3)
      * of Sec. 4.2, (m_x + m_y + m_z)(n_s - 1) bits, rounded up to words. */
+    uint64_t maxleaf = leaf_size < n ? leaf_size : n;
+    int nomem = 0;
+#pragma omp parallel reduction(| : nomem)
+    {
+        int64_t *leafq = malloc((maxleaf ? maxleaf : 1) * 3 * sizeof(int64_t));
+        if (!leafq) nomem = 1;
+#pragma omp for schedule(dynamic, 16)
+        for (uint64_t L = 0; L < nl; L++) {
+            if (!leafq) continue;
+            for (uint64_t i = 0; i < lcnt[L]; i++)
+                for (int d = 0; d < 3; d++) leafq[3 * i + d] = q[3 * order[loff[L] + i] + d];
+            int64_t lo[3], hi[3];
+            oracle_bitbox(leafq, lcnt[L], &centre[L], lo, hi, &qref[3 * L], &mm[3 * L]);
+        }
+        free(leafq);
+    }
+    if (nomem) goto done;
     uint64_t total_words = 0;
     for (uint64_t L = 0; L < nl; L++) {
-        for (uint64_t i = 0; i < lcnt[L]; i++)
-            for (int d = 0; d < 3; d++) leafq[3 * i + d] = q[3 * order[loff[L] + i] + d];
-        int64_t lo[3], hi[3];
-        oracle_bitbox(leafq, lcnt[L], &centre[L], lo, hi, &qref[3 * L], &mm[3 * L]);
         uint64_t bits = (uint64_t)(mm[3 * L] + mm[3 * L + 1] + mm[3 * L + 2]) * (lcnt[L] - 1);
         wofs[L] = total_words;
         total_words += (bits + 31) / 32;
     }
-    free(leafq);
 
     uint64_t bytes = OR_HEADER_BYTES + OR_LEAF_BYTES * nl + 4 * total_words;
     buf = calloc(bytes, 1);
@@ -476,7 +516,9 @@ int oracle_compress(const void *pos, uint64_t n, int dtype, int eb_mode, double 
     words = calloc(total_words ? total_words : 1, sizeof(uint32_t));
     if (!words) goto done;
 
-    uint64_t outpos = 0;
+    /* Every leaf owns its words (it starts on a fresh one) and its decoded
+     * positions (from its first particle on), so leaves are written apart. */
+#pragma omp parallel for schedule(dynamic, 16)
     for (uint64_t L = 0; L < nl; L++) {
         uint8_t *rec = buf + OR_HEADER_BYTES + OR_LEAF_BYTES * L;
         put_u64(rec + 0, loff[L]);
@@ -484,6 +526,7 @@ int oracle_compress(const void *pos, uint64_t n, int dtype, int eb_mode, double 
         for (int d = 0; d < 3; d++) put_u32(rec + 16 + 4 * d, (uint32_t)(int32_t)qref[3 * L + d]);
         for (int d = 0; d < 3; d++) rec[28 + d] = (uint8_t)mm[3 * L + d];
         /* Decoded order: the centre first, then the rest in leaf order. */
+        uint64_t outpos = loff[L];
         perm[outpos++] = order[loff[L] + centre[L]];
         uint64_t bitpos = 32 * wofs[L];
         for (uint64_t i = 0; i < lcnt[L]; i++) {
@@ -564,45 +607,57 @@ int oracle_decompress(const uint8_t *st, uint64_t bytes, void *out, uint64_t out
     uint32_t *words = malloc((nw ? nw : 1) * sizeof(uint32_t));
     if (!words) return OR_ERR_NOMEM;
     for (uint64_t w = 0; w < nw; w++) words[w] = get_u32(pay + 4 * w);
+    /* Check every record first, then decode the leaves (each writes its own
+     * positions only). */
     uint64_t expect_word = 0;
     rc = OR_OK;
-    for (uint64_t L = 0; L < nl && rc == OR_OK; L++) {
+    for (uint64_t L = 0; L < nl; L++) {
         const uint8_t *rec = tab + OR_LEAF_BYTES * L;
         uint64_t po = get_u64(rec), wo = get_u64(rec + 8);
         uint64_t pend = (L + 1 < nl) ? get_u64(rec + OR_LEAF_BYTES) : n;
-        int64_t qref[3];
         uint32_t m[3];
-        for (int d = 0; d < 3; d++) {
-            qref[d] = (int32_t)get_u32(rec + 16 + 4 * d);
-            m[d] = rec[28 + d];
-        }
+        for (int d = 0; d < 3; d++) m[d] = rec[28 + d];
         if ((L == 0 && po != 0) || pend <= po || pend > n || wo != expect_word || m[0] > 31 || m[1] > 31 ||
             m[2] > 31) {
             rc = OR_ERR_CORRUPT;
             break;
         }
-        uint64_t cnt = pend - po;
-        uint64_t bits = (uint64_t)(m[0] + m[1] + m[2]) * (cnt - 1);
+        uint64_t bits = (uint64_t)(m[0] + m[1] + m[2]) * (pend - po - 1);
         expect_word = wo + (bits + 31) / 32;
         if (expect_word > nw) {
             rc = OR_ERR_CORRUPT;
             break;
         }
-        uint64_t bitpos = 32 * wo;
-        for (uint64_t i = 0; i < cnt; i++) {
+    }
+    if (rc == OR_OK) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (uint64_t L = 0; L < nl; L++) {
+            const uint8_t *rec = tab + OR_LEAF_BYTES * L;
+            uint64_t po = get_u64(rec), wo = get_u64(rec + 8);
+            uint64_t pend = (L + 1 < nl) ? get_u64(rec + OR_LEAF_BYTES) : n;
+            int64_t qref[3];
+            uint32_t m[3];
             for (int d = 0; d < 3; d++) {
-                int64_t qd = qref[d];
-                if (i > 0 && m[d] > 0) {
-                    uint64_t c = read_bits(words, bitpos, m[d]);
-                    bitpos += m[d];
-                    qd = qref[d] + (int64_t)c - ((1LL << (m[d] - 1)) - 1);
+                qref[d] = (int32_t)get_u32(rec + 16 + 4 * d);
+                m[d] = rec[28 + d];
+            }
+            uint64_t cnt = pend - po;
+            uint64_t bitpos = 32 * wo;
+            for (uint64_t i = 0; i < cnt; i++) {
+                for (int d = 0; d < 3; d++) {
+                    int64_t qd = qref[d];
+                    if (i > 0 && m[d] > 0) {
+                        uint64_t c = read_bits(words, bitpos, m[d]);
+                        bitpos += m[d];
+                        qd = qref[d] + (int64_t)c - ((1LL << (m[d] - 1)) - 1);
+                    }
+                    double y = s * (double)qd;
+                    double z = o[d] + y;
+                    if (dtype == OR_F32)
+                        ((float *)out)[3 * (po + i) + d] = (float)z;
+                    else
+                        ((double *)out)[3 * (po + i) + d] = z;
                 }
-                double y = s * (double)qd;
-                double z = o[d] + y;
-                if (dtype == OR_F32)
-                    ((float *)out)[3 * (po + i) + d] = (float)z;
-                else
-                    ((double *)out)[3 * (po + i) + d] = z;
             }
         }
     }
