@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch-256", "serve-2000"], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch-256", "serve-2000", "leaf-sweep"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--leaf-size", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
@@ -425,8 +425,9 @@ def measure_e2e(pc, pos_h, pdt, emode, eb, args, world):
     hdec = torch.empty_like(hp).pin_memory()
     ws_c = torch.empty(pc.pc_compress_host_workspace_size(n, pdt, args.leaf_size), dtype=torch.uint8, device=dev)
     ws_d = torch.empty(pc.pc_decompress_host_workspace_size(n, pdt, bound), dtype=torch.uint8, device=dev)
-    size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, args.leaf_size)  # warm-up
-    pc.pc_decompress_host(hstream, size, hdec, ws_d)
+    for _ in range(3):  # warm-up: the first transfers from freshly pinned pages run slower
+        size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, args.leaf_size)
+        pc.pc_decompress_host(hstream, size, hdec, ws_d)
     times = []
     for _ in range(args.e2e_steps):
         barrier(world)
@@ -446,6 +447,30 @@ def measure_e2e(pc, pos_h, pdt, emode, eb, args, world):
 
 BATCH_WORKLOAD = "batch-256"
 SERVE_WORKLOAD = "serve-2000"
+SWEEP_WORKLOAD = "leaf-sweep"
+
+
+def run_sweep(args):
+    """Stream size and parts against the leaf size on the default workload's data
+    (one descent of the tree per error bound); prints one JSON line."""
+    import torch
+
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as pcbuild
+
+    pcbuild.build()
+    pc.load()
+    gen, n, dtype, mode, eb0 = WORKLOADS[DEFAULT_WORKLOAD]
+    pos = torch.from_numpy(generate(gen, n, dtype, seed=0)).cuda()
+    out = {}
+    for eb in (1e-3, 1e-4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pts = pc.pc_leaf_size_sweep(pos, pc.PC_EB_REL, eb, r_min=64, r_max=pc.PC_MAX_LEAF_SIZE)
+        dt = time.perf_counter() - t0
+        out[str(eb)] = {"points": pts, "seconds": round(dt, 3)}
+    print(json.dumps({"metric": "stream bytes against leaf size", "workload": DEFAULT_WORKLOAD, "particles": n,
+                      "sweeps": out}), flush=True)
 
 
 def _pools(dev, size, gens, dtypes):
@@ -550,7 +575,7 @@ def run_batch(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "snapshots": len(jobs), "particles": particles,
                        "sizes": "round(10^U(4,7))", "generators": "cosmology or fluid slices, p = 1/2",
-                       "eb": "rel, one of 1e-2 1e-3 1e-4", "leaf_size": "autotuned (1024..12000)", "lanes": lanes,
+                       "eb": "rel, one of 1e-2 1e-3 1e-4", "leaf_size": "autotuned (64..12000)", "lanes": lanes,
                        "parallelism": f"replicas x{world}" if world > 1 else "single"},
             "batched": b, "one_call_per_snapshot": q,
             "speedup_round_trip": round(b["round_trip_gbs"] / q["round_trip_gbs"], 3),
@@ -670,6 +695,9 @@ def main():
         return
     if args.workload == SERVE_WORKLOAD:
         run_serve(args)
+        return
+    if args.workload == SWEEP_WORKLOAD:
+        run_sweep(args)
         return
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -90,7 +90,7 @@ typedef struct {
  * max = leaf_size.  The header records that r, and a plain call with it
  * gives the same stream. */
 #define PC_FLAG_AUTOTUNE_LEAF 1u
-#define PC_AUTOTUNE_MIN_LEAF 1024u
+#define PC_AUTOTUNE_MIN_LEAF 64u
 
 #define PC_DEFAULT_LEAF_SIZE 4096u
 #define PC_MAX_LEAF_SIZE 12000u
@@ -180,6 +180,29 @@ int pc_compress_host(const void *host_positions, uint64_t n, int dtype, int eb_m
 int pc_decompress_host_workspace_size(uint64_t n, int dtype, uint64_t stream_bytes, uint64_t *out_bytes);
 int pc_decompress_host(const void *host_stream, uint64_t stream_bytes, void *host_positions,
                        uint64_t out_capacity_bytes, void *workspace, uint64_t workspace_bytes, void *stream);
+
+/* ---- Leaf-size sweep -----------------------------------------------------------
+ * The stream size and its parts for every leaf size r = ceil(n / 2^d) in
+ * [r_min, r_max] (16 <= r_min <= r_max <= PC_MAX_LEAF_SIZE), from one descent
+ * of the median tree: the paper's study of the layout size against the leaf
+ * fraction r / n (Sec. 4.2 storage cost, Sec. 5 parameter analysis), here
+ * for this stream format.  Writes no stream.  points[i] for the i-th
+ * candidate from the largest leaves down, at most `capacity`; *count is the
+ * number of candidates. */
+typedef struct {
+    uint32_t leaf_size;      /* ceil(n / 2^depth) */
+    uint32_t depth;
+    uint64_t leaves;         /* 2^depth sequences */
+    uint64_t header_bytes;   /* 96 */
+    uint64_t table_bytes;    /* 32 per sequence: centre code, widths, offsets */
+    uint64_t payload_bytes;  /* packed codes, each sequence rounded up to words */
+    uint64_t total_bytes;
+} pc_sweep_point;
+
+int pc_leaf_size_sweep_workspace_size(uint64_t n, int dtype, uint32_t r_min, uint32_t r_max, uint64_t *out_bytes);
+int pc_leaf_size_sweep(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, uint32_t r_min,
+                       uint32_t r_max, pc_sweep_point *points, uint32_t capacity, uint32_t *count, void *workspace,
+                       uint64_t workspace_bytes, void *stream);
 
 /* ---- Many snapshots --------------------------------------------------------
  * The paper compresses one snapshot at a time; nothing below has a

@@ -38,7 +38,7 @@ PC_MAX_LEAF_SIZE = 12000
 PC_HEADER_BYTES = 96
 PC_LEAF_BYTES = 32
 PC_FLAG_AUTOTUNE_LEAF = 1
-PC_AUTOTUNE_MIN_LEAF = 1024
+PC_AUTOTUNE_MIN_LEAF = 64
 LEAF_AUTO = -1  # leaf_size argument: autotune with candidates up to PC_MAX_LEAF_SIZE
 
 # every entry point declared in include/pc.h
@@ -49,7 +49,8 @@ EXPORTS = (
     "pc_trace_enable", "pc_trace_reset", "pc_trace_count", "pc_trace_get", "pc_compress_noalloc",
     "pc_compress_batch_workspace_size", "pc_compress_batch", "pc_decompress_batch_workspace_size",
     "pc_decompress_batch", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_release",
-    "pc_server_stats", "pc_server_destroy", "pc_server_now",
+    "pc_server_stats", "pc_server_destroy", "pc_server_now", "pc_leaf_size_sweep_workspace_size",
+    "pc_leaf_size_sweep",
 )
 PC_REQ_COMPRESS = 0
 PC_REQ_DECOMPRESS = 1
@@ -85,6 +86,12 @@ class pc_decompress_item(ctypes.Structure):
     _fields_ = [("stream_data", ctypes.c_void_p), ("stream_bytes", ctypes.c_uint64), ("n", ctypes.c_uint64),
                 ("out_positions", ctypes.c_void_p), ("out_capacity_bytes", ctypes.c_uint64),
                 ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class pc_sweep_point(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_uint32), ("depth", ctypes.c_uint32), ("leaves", ctypes.c_uint64),
+                ("header_bytes", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
+                ("payload_bytes", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
 
 
 class pc_request(ctypes.Structure):
@@ -142,6 +149,9 @@ def _lib():
         L.pc_server_release.argtypes = [vp, vp]
         L.pc_server_stats.argtypes = [vp, pu64, pu64]
         L.pc_server_destroy.argtypes = [vp]
+        L.pc_leaf_size_sweep_workspace_size.argtypes = [u64, i32, u32, u32, pu64]
+        L.pc_leaf_size_sweep.argtypes = [vp, u64, i32, i32, dbl, u32, u32, ctypes.POINTER(pc_sweep_point), u32,
+                                         ctypes.POINTER(u32), vp, u64, vp]
         L.pc_server_now.argtypes = []
         L.pc_server_now.restype = dbl
         _LIB = L
@@ -396,6 +406,25 @@ def pc_decompress_batch(streams, sizes, outs, workspace=None, lanes: int = 0, st
     if rc != PC_OK and all(st == PC_OK for st in statuses):
         _check(rc, "pc_decompress_batch")
     return statuses
+
+
+def pc_leaf_size_sweep(positions, eb_mode: int, eb: float, r_min: int = 1024, r_max: int = PC_MAX_LEAF_SIZE,
+                       workspace=None, stream=None):
+    """Stream size and parts for every candidate leaf size ceil(n / 2^d) in [r_min, r_max], largest first."""
+    import torch
+    n = positions.shape[0]
+    dt = _dtype_of(positions)
+    if workspace is None:
+        need = ctypes.c_uint64()
+        _check(_lib().pc_leaf_size_sweep_workspace_size(n, dt, r_min, r_max, ctypes.byref(need)),
+               "pc_leaf_size_sweep_workspace_size")
+        workspace = torch.empty(max(need.value, 1), dtype=torch.uint8, device=positions.device)
+    pts = (pc_sweep_point * 64)()
+    cnt = ctypes.c_uint32()
+    _check(_lib().pc_leaf_size_sweep(positions.data_ptr() if n else None, n, dt, int(eb_mode), float(eb), int(r_min),
+                                     int(r_max), pts, 64, ctypes.byref(cnt), workspace.data_ptr(), workspace.numel(),
+                                     _stream_handle(stream)), "pc_leaf_size_sweep")
+    return [{f: getattr(pts[i], f) for f, _ in pc_sweep_point._fields_} for i in range(min(cnt.value, 64))]
 
 
 class Server:

@@ -114,7 +114,7 @@ uint32_t min_scatter_tile(bool idx) {
   return a < b ? a : b;
 }
 
-int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_count, Plan &p) {
+int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_count, Plan &p, uint32_t r_min = 0) {
   if (dtype != PC_F32 && dtype != PC_F64) return PC_ERR_ARG;
   if (n > PC_MAX_PARTICLES) return PC_ERR_ARG;
   uint32_t r = PC_DEFAULT_LEAF_SIZE;
@@ -127,7 +127,8 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
       p.tune = true;
       p.r_hi = cfg->leaf_size ? cfg->leaf_size : PC_MAX_LEAF_SIZE;
       if (p.r_hi < 16 || p.r_hi > PC_MAX_LEAF_SIZE) return PC_ERR_ARG;
-      r = p.r_hi < PC_AUTOTUNE_MIN_LEAF ? p.r_hi : PC_AUTOTUNE_MIN_LEAF;
+      const uint32_t lo = r_min ? r_min : PC_AUTOTUNE_MIN_LEAF;
+      r = p.r_hi < lo ? p.r_hi : lo;
     }
   }
   if (r < 1 || r > PC_MAX_LEAF_SIZE) return PC_ERR_ARG;
@@ -269,21 +270,35 @@ int lattice_from_range(const RangeResult &rr, int dtype, int mode, double eb, La
     if (e_ != cudaSuccess) return PC_ERR_CUDA; \
   } while (0)
 
+// With `sweep`, the leaf-size candidates are only measured: every candidate
+// depth's stream size is recorded (sweep->count entries) and no stream is written.
+struct Sweep {
+  pc_sweep_point *points;
+  uint32_t capacity, count;
+  uint32_t r_min;
+};
+
 int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                   void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
-                  uint32_t *perm, cudaStream_t st) {
-  if (!out || !out_size || (n > 0 && !positions)) return PC_ERR_ARG;
+                  uint32_t *perm, cudaStream_t st, Sweep *sweep = nullptr) {
+  if (sweep) {
+    if (!cfg || !(cfg->flags & PC_FLAG_AUTOTUNE_LEAF) || perm) return PC_ERR_ARG;
+  } else if (!out || !out_size) {
+    return PC_ERR_ARG;
+  }
+  if (n > 0 && !positions) return PC_ERR_ARG;
+  if (sweep && n == 0) return PC_OK;
   if (eb_mode != PC_EB_ABS && eb_mode != PC_EB_REL) return PC_ERR_ARG;
   if (!(eb > 0.0) || !std::isfinite(eb)) return PC_ERR_ARG;
-  if (reinterpret_cast<uintptr_t>(out) % 16) return PC_ERR_ARG;
+  if (!sweep && reinterpret_cast<uintptr_t>(out) % 16) return PC_ERR_ARG;
   const size_t esz = dtype == PC_F32 ? 4 : 8;
   if (n > 0 && reinterpret_cast<uintptr_t>(positions) % esz) return PC_ERR_ARG;
   Plan p;
-  int rc = make_plan(n, dtype, cfg, perm != nullptr, device_sm_count(), p);
+  int rc = make_plan(n, dtype, cfg, perm != nullptr, device_sm_count(), p, sweep ? sweep->r_min : 0);
   if (rc) return rc;
   if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign) return PC_ERR_ARG;
   if (workspace_bytes < p.total) return PC_ERR_CAPACITY;
-  if (out_capacity < stream_bound(n, p.num_leaves)) return PC_ERR_CAPACITY;
+  if (!sweep && out_capacity < stream_bound(n, p.num_leaves)) return PC_ERR_CAPACITY;
   uint8_t *ws = static_cast<uint8_t *>(workspace);
   uint32_t *err = reinterpret_cast<uint32_t *>(ws + p.off_err);
   uint64_t *total_dev = reinterpret_cast<uint64_t *>(ws + p.off_total);
@@ -384,6 +399,19 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       *bytes = uint64_t(PC_LEAF_BYTES) * (1ull << depth) + 4 * words;
       return PC_OK;
     };
+    auto record = [&](int depth, uint64_t bytes) {
+      if (sweep->count < sweep->capacity) {
+        pc_sweep_point &pt = sweep->points[sweep->count];
+        pt.leaf_size = uint32_t((n + (1ull << depth) - 1) >> depth);
+        pt.depth = uint32_t(depth);
+        pt.leaves = 1ull << depth;
+        pt.header_bytes = PC_HEADER_BYTES;
+        pt.table_bytes = uint64_t(PC_LEAF_BYTES) << depth;
+        pt.payload_bytes = bytes - pt.table_bytes;
+        pt.total_bytes = PC_HEADER_BYTES + bytes;
+      }
+      ++sweep->count;
+    };
     int chosen = -1;            // autotuning: depth of the chosen leaves
     uint64_t best_bytes = 0;    // stream bytes (without header) at the shallower candidate
     const int first_depth = p.tune_first;
@@ -397,7 +425,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
         uint64_t bytes = 0;
         rc = depth_cost(src, l, &bytes);
         if (rc) return rc;
-        if (l > first_depth && bytes >= best_bytes) {
+        if (sweep) {
+          record(l, bytes);
+        } else if (l > first_depth && bytes >= best_bytes) {
           chosen = l - 1;
           break;
         }
@@ -441,6 +471,16 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       idst = ti;
     }
 
+    if (sweep) {
+      // the deepest candidate, then nothing is written
+      uint64_t bytes = 0;
+      rc = depth_cost(src, levels, &bytes);
+      if (rc) return rc;
+      if (levels >= first_depth) record(levels, bytes);
+      PC_TRY(cudaStreamSynchronize(st));
+      trace_flush();
+      return PC_OK;
+    }
     // a4-a5: bit boxes, payload offsets, packing
     if (!p.tune) {
       PC_TRY(leaf_launch(src, isrc, levels - 1, p.r, p.num_leaves, false));
@@ -617,6 +657,29 @@ int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, doubl
 int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info) {
   if (!host_header || !info) return PC_ERR_ARG;
   return parse_header(static_cast<const uint8_t *>(host_header), header_bytes, info);
+}
+
+int pc_leaf_size_sweep_workspace_size(uint64_t n, int dtype, uint32_t r_min, uint32_t r_max, uint64_t *out_bytes) {
+  if (!out_bytes || r_min < 16 || r_max < r_min || r_max > PC_MAX_LEAF_SIZE) return PC_ERR_ARG;
+  pc_config cfg = {r_max, PC_FLAG_AUTOTUNE_LEAF};
+  Plan p;
+  int rc = make_plan(n, dtype, &cfg, false, 256, p, r_min);  // the largest block count a device may use
+  if (rc) return rc;
+  *out_bytes = p.total;
+  return PC_OK;
+}
+
+int pc_leaf_size_sweep(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, uint32_t r_min,
+                       uint32_t r_max, pc_sweep_point *points, uint32_t capacity, uint32_t *count, void *workspace,
+                       uint64_t workspace_bytes, void *stream) {
+  if (!count || (capacity && !points) || r_min < 16 || r_max < r_min || r_max > PC_MAX_LEAF_SIZE)
+    return PC_ERR_ARG;
+  pc_config cfg = {r_max, PC_FLAG_AUTOTUNE_LEAF};
+  Sweep sw = {points, capacity, 0, r_min};
+  int rc = compress_impl(positions, n, dtype, eb_mode, eb, &cfg, nullptr, 0, nullptr, workspace, workspace_bytes,
+                         nullptr, static_cast<cudaStream_t>(stream), &sw);
+  *count = sw.count;
+  return rc;
 }
 
 int pc_decompress_workspace_size(uint64_t n, uint64_t *out_bytes) {

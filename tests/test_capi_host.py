@@ -97,7 +97,7 @@ def test_autotune_flag_sizes_and_rejections(pc):
     auto = pc.pc_compress_bound(n, pc.PC_F32, pc.LEAF_AUTO)
     assert auto == pc.pc_compress_bound(n, pc.PC_F32, pc.PC_AUTOTUNE_MIN_LEAF)
     assert pc.pc_compress_workspace_size(n, pc.PC_F32, pc.LEAF_AUTO) >= pc.pc_compress_workspace_size(n, pc.PC_F32)
-    assert pc.pc_compress_bound(n, pc.PC_F32, -512) == pc.pc_compress_bound(n, pc.PC_F32, 512)
+    assert pc.pc_compress_bound(n, pc.PC_F32, -512) == pc.pc_compress_bound(n, pc.PC_F32, pc.PC_AUTOTUNE_MIN_LEAF)
     cfg = pc.pc_config(0, 2)
     out = pc.ctypes.c_uint64()
     assert pc.load().pc_compress_bound(n, pc.PC_F32, pc.ctypes.byref(cfg), pc.ctypes.byref(out)) == pc.PC_ERR_ARG

@@ -174,6 +174,29 @@ def test_autotuned_leaf_size(pc, oracle_mod, gen, n, dtype, mode, eb):
         assert len(oracle_mod.compress(pos, om, eb, leaf_size=ceil_at(d + 1), want_perm=False)[0]) >= size
 
 
+def test_leaf_size_sweep_matches_oracle_sizes(pc, oracle_mod):
+    """Every sweep point is the size of the oracle's stream at that leaf size,
+    split into header, leaf table and packed codes; the autotuned stream is the
+    first point whose successor is not smaller."""
+    pos = synth.cosmology(200_000, seed=21)
+    dpos = torch.from_numpy(pos).cuda()
+    pts = pc.pc_leaf_size_sweep(dpos, pc.PC_EB_REL, 1e-4, r_min=256, r_max=12000)
+    assert [p["leaf_size"] for p in pts] == sorted((p["leaf_size"] for p in pts), reverse=True)
+    assert pts[0]["leaf_size"] <= 12000 and pts[-1]["leaf_size"] >= 256
+    for p in pts:
+        ref, _ = oracle_mod.compress(pos, oracle_mod.REL, 1e-4, leaf_size=p["leaf_size"], want_perm=False)
+        n, _, nl, nw = oracle_mod.stream_header(ref)
+        assert p["total_bytes"] == len(ref)
+        assert p["leaves"] == nl and p["table_bytes"] == 32 * nl and p["payload_bytes"] == 4 * nw
+    auto = pc.pc_leaf_size_sweep(dpos, pc.PC_EB_REL, 1e-4, r_min=1024, r_max=12000)
+    got, _, _ = run_gpu(pc, pos, pc.PC_EB_REL, 1e-4, pc.LEAF_AUTO, with_perm=False)
+    k = 0
+    while k + 1 < len(auto) and auto[k + 1]["total_bytes"] < auto[k]["total_bytes"]:
+        k += 1
+    assert len(got) == auto[k]["total_bytes"]
+    assert pc.pc_stream_info(got[:96]).leaf_size == auto[k]["leaf_size"]
+
+
 def test_parity_without_perm(pc, oracle_mod):
     pos = synth.cosmology(120_000, seed=8)
     check_against_oracle(pc, oracle_mod, pos, pc.PC_EB_REL, 1e-4, 4096, with_perm=False)
