@@ -25,6 +25,7 @@ namespace {
 constexpr int kBoxThreads = 256;
 constexpr int kPackThreads = 256;
 constexpr int kPackWarps = kPackThreads / 32;
+constexpr uint32_t kSmallLeaf = 1024;  // leaves of at most this many particles: one warp each
 
 __global__ void k_leaftable(uint64_t n, int level, uint32_t r, LeafRec *recs, uint64_t num_leaves) {
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -182,6 +183,145 @@ __global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q
   }
 }
 
+// The same bit box with one warp per leaf (small leaves).
+template <typename C>
+__global__ void __launch_bounds__(256) k_leafbox_warp(const C *__restrict__ q0, const C *__restrict__ q1,
+                                                      const C *__restrict__ q2, LeafRec *recs, uint64_t num_leaves) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = uint64_t(gridDim.x) * 8;
+  for (uint64_t L = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5); L < num_leaves; L += warps) {
+    LeafRec rec = recs[L];
+    const uint32_t off = rec.off, cnt = rec.cnt;
+    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+    for (uint32_t i = lane; i < cnt; i += 32) {
+      const uint32_t x[3] = {uint32_t(q0[off + i]), uint32_t(q1[off + i]), uint32_t(q2[off + i])};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = min(lo[d], x[d]);
+        hi[d] = max(hi[d], x[d]);
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = __reduce_min_sync(0xffffffffu, lo[d]);
+      hi[d] = __reduce_max_sync(0xffffffffu, hi[d]);
+    }
+    // centre: least squared distance to the AABB centre, lowest position on ties
+    unsigned long long bd = ~0ull;
+    uint32_t bp = 0xffffffffu;
+    const long long s0 = (long long)lo[0] + hi[0], s1 = (long long)lo[1] + hi[1], s2 = (long long)lo[2] + hi[2];
+    for (uint32_t i = lane; i < cnt; i += 32) {
+      const long long a = 2ll * q0[off + i] - s0, b = 2ll * q1[off + i] - s1, c = 2ll * q2[off + i] - s2;
+      const unsigned long long d2 =
+          (unsigned long long)(a * a) + (unsigned long long)(b * b) + (unsigned long long)(c * c);
+      if (d2 < bd) {  // positions rise within a lane: the first minimum is the lowest
+        bd = d2;
+        bp = i;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (od < bd || (od == bd && op < bp)) {
+        bd = od;
+        bp = op;
+      }
+    }
+    if (lane == 0) {
+      const uint32_t c = bp;
+      const uint32_t qc[3] = {uint32_t(q0[off + c]), uint32_t(q1[off + c]), uint32_t(q2[off + c])};
+      uint32_t m[3];
+      for (int d = 0; d < 3; ++d) {
+        m[d] = bits_for_range(max(qc[d] - lo[d], hi[d] - qc[d]));
+        rec.qref[d] = int32_t(qc[d]);
+      }
+      rec.centre = c;
+      rec.m = m[0] | (m[1] << 8) | (m[2] << 16);
+      rec.words = uint32_t((uint64_t(m[0] + m[1] + m[2]) * (cnt - 1) + 31) >> 5);
+      recs[L] = rec;
+    }
+  }
+}
+
+// Payload word offsets over many leaves, in three steps: each block scans its
+// slice of leaves (offsets within the slice, slice total), one block scans the
+// slice totals, each block adds its slice's base.
+constexpr uint32_t kScanSlice = 8192;  // leaves per block
+
+__global__ void __launch_bounds__(1024) k_leafscan_slices(LeafRec *recs, uint64_t num_leaves, uint64_t *slice_tot) {
+  __shared__ unsigned long long wt[33];
+  const uint64_t s0 = uint64_t(blockIdx.x) * kScanSlice;
+  const uint64_t s1 = (s0 + kScanSlice) < num_leaves ? (s0 + kScanSlice) : num_leaves;
+  constexpr uint32_t per = kScanSlice / 1024;
+  const uint64_t l0 = s0 + uint64_t(threadIdx.x) * per;
+  const uint64_t l1 = (l0 + per) < s1 ? (l0 + per) : s1;
+  unsigned long long sum = 0;
+  for (uint64_t l = l0; l < l1; ++l) sum += recs[l].words;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wt[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long x = wt[lane];
+    unsigned long long xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    wt[lane] = xi - x;
+    if (lane == 31) slice_tot[blockIdx.x] = xi;
+  }
+  __syncthreads();
+  unsigned long long run = wt[warp] + incl - sum;
+  for (uint64_t l = l0; l < l1; ++l) {
+    recs[l].word_off = run;
+    run += recs[l].words;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_leafscan_totals(uint64_t *slice_tot, uint64_t slices, uint64_t *total_words) {
+  // slices <= 1024 * 64: a sequential run per thread, then a block scan
+  __shared__ unsigned long long wt[33];
+  const uint64_t per = (slices + 1023) / 1024;
+  const uint64_t t0 = threadIdx.x * per, t1 = (t0 + per) < slices ? (t0 + per) : slices;
+  unsigned long long sum = 0;
+  for (uint64_t t = t0; t < t1; ++t) sum += slice_tot[t];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wt[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long x = wt[lane];
+    unsigned long long xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    wt[lane] = xi - x;
+    if (lane == 31) *total_words = xi;
+  }
+  __syncthreads();
+  unsigned long long run = wt[warp] + incl - sum;
+  for (uint64_t t = t0; t < t1; ++t) {
+    const unsigned long long x = slice_tot[t];
+    slice_tot[t] = run;
+    run += x;
+  }
+}
+
+__global__ void k_leafscan_add(LeafRec *recs, uint64_t num_leaves, const uint64_t *slice_base) {
+  const uint64_t l = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l < num_leaves) recs[l].word_off += slice_base[l / kScanSlice];
+}
+
 // Exclusive scan of the leaves' payload words (one block).
 __global__ void __launch_bounds__(1024) k_leafscan(LeafRec *recs, uint64_t num_leaves, uint64_t *total_words) {
   __shared__ unsigned long long wt[33];
@@ -216,25 +356,25 @@ __global__ void __launch_bounds__(1024) k_leafscan(LeafRec *recs, uint64_t num_l
   if (threadIdx.x == 0) *total_words = wt[32];
 }
 
+// One leaf by a group of `nw` warps (this thread is lane `lane` of warp `warp`
+// of the group, thread `tid` of its nw * 32); sw: this warp's 96 staged words.
 template <typename C, bool IDX>
-__global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__ q0, const C *__restrict__ q1,
-                                                           const C *__restrict__ q2, const uint32_t *__restrict__ idx,
-                                                           const LeafRec *__restrict__ recs, uint8_t *out,
-                                                           uint64_t num_leaves, uint32_t *perm) {
-  __shared__ uint32_t swords[kPackWarps][96];  // one chunk's words per warp (w <= 93)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const LeafRec rec = recs[blockIdx.x];
+__device__ __forceinline__ void pack_leaf(const C *__restrict__ q0, const C *__restrict__ q1, const C *__restrict__ q2,
+                                          const uint32_t *__restrict__ idx, const LeafRec &rec, uint64_t leaf,
+                                          uint8_t *out, uint64_t num_leaves, uint32_t *perm, int lane, int warp, int nw,
+                                          uint32_t *sw) {
+  const uint32_t tid = uint32_t(warp) * 32 + lane, group = uint32_t(nw) * 32;
   const uint32_t off = rec.off, cnt = rec.cnt, centre = rec.centre;
   const uint32_t m0 = rec.m & 0xffu, m1 = (rec.m >> 8) & 0xffu, m2 = (rec.m >> 16) & 0xffu;
   const uint32_t w = m0 + m1 + m2;
-  if (threadIdx.x == 0) {
-    uint4 *r = reinterpret_cast<uint4 *>(out + kHeaderBytes + uint64_t(kLeafBytes) * blockIdx.x);
+  if (tid == 0) {
+    uint4 *r = reinterpret_cast<uint4 *>(out + kHeaderBytes + uint64_t(kLeafBytes) * leaf);
     const uint64_t po = off, wo = rec.word_off;
     r[0] = make_uint4(uint32_t(po), uint32_t(po >> 32), uint32_t(wo), uint32_t(wo >> 32));
     r[1] = make_uint4(uint32_t(rec.qref[0]), uint32_t(rec.qref[1]), uint32_t(rec.qref[2]), rec.m);
   }
   if (IDX && perm) {
-    for (uint32_t i = threadIdx.x; i < cnt; i += kPackThreads) {
+    for (uint32_t i = tid; i < cnt; i += group) {
       const uint32_t src = i == 0 ? centre : (i - 1 < centre ? i - 1 : i);
       perm[off + i] = idx[off + src];
     }
@@ -248,8 +388,7 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__
   const uint32_t slots = cnt - 1;
   const uint32_t words = rec.words;
   const uint32_t chunks = (slots + 31) / 32;
-  uint32_t *sw = swords[warp];
-  for (uint32_t ch = warp; ch < chunks; ch += kPackWarps) {
+  for (uint32_t ch = warp; ch < chunks; ch += nw) {
     // this lane's particle as one w-bit value c_x | c_y << m_x | c_z << (m_x + m_y), in three 32-bit limbs
     const uint32_t s = ch * 32 + lane;
     uint32_t v0 = 0, v1 = 0, v2 = 0;
@@ -291,6 +430,31 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__
   }
 }
 
+// One CTA per leaf (large leaves).
+template <typename C, bool IDX>
+__global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__ q0, const C *__restrict__ q1,
+                                                           const C *__restrict__ q2, const uint32_t *__restrict__ idx,
+                                                           const LeafRec *__restrict__ recs, uint8_t *out,
+                                                           uint64_t num_leaves, uint32_t *perm) {
+  __shared__ uint32_t swords[kPackWarps][96];  // one chunk's words per warp (w <= 93)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  pack_leaf<C, IDX>(q0, q1, q2, idx, recs[blockIdx.x], blockIdx.x, out, num_leaves, perm, lane, warp, kPackWarps,
+                    swords[warp]);
+}
+
+// One warp per leaf (small leaves).
+template <typename C, bool IDX>
+__global__ void __launch_bounds__(kPackThreads) k_leafpack_warp(const C *__restrict__ q0, const C *__restrict__ q1,
+                                                                const C *__restrict__ q2,
+                                                                const uint32_t *__restrict__ idx,
+                                                                const LeafRec *__restrict__ recs, uint8_t *out,
+                                                                uint64_t num_leaves, uint32_t *perm) {
+  __shared__ uint32_t swords[kPackWarps][96];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t L = uint64_t(blockIdx.x) * kPackWarps + warp; L < num_leaves; L += uint64_t(gridDim.x) * kPackWarps)
+    pack_leaf<C, IDX>(q0, q1, q2, idx, recs[L], L, out, num_leaves, perm, lane, 0, 1, swords[warp]);
+}
+
 template <typename C, bool IDX>
 cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
   const C *q0 = static_cast<const C *>(a.codes[0]), *q1 = static_cast<const C *>(a.codes[1]),
@@ -301,18 +465,36 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
     k_leaftable<<<unsigned((nodes + 255) / 256), 256, 0, st>>>(a.n, a.split_level, a.leaf_size, a.recs,
                                                                a.num_leaves);
   }
+  // threads per leaf: a CTA for large leaves, a warp for small ones
+  const bool small = a.leaf_size <= kSmallLeaf;
+  const uint64_t warp_blocks = (a.num_leaves + 7) / 8;
+  const unsigned wgrid = unsigned(warp_blocks < uint64_t(device_sm_count()) * 32 ? warp_blocks
+                                                                                 : uint64_t(device_sm_count()) * 32);
   {
     TraceScope ts("k_leafbox", st);
-    k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs);
+    if (small)
+      k_leafbox_warp<C><<<wgrid, 256, 0, st>>>(q0, q1, q2, a.recs, a.num_leaves);
+    else
+      k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs);
   }
   {
     TraceScope ts("k_leafscan", st);
-    k_leafscan<<<1, 1024, 0, st>>>(a.recs, a.num_leaves, a.total_words);
+    if (a.num_leaves <= kScanSlice) {
+      k_leafscan<<<1, 1024, 0, st>>>(a.recs, a.num_leaves, a.total_words);
+    } else {
+      const uint64_t slices = (a.num_leaves + kScanSlice - 1) / kScanSlice;
+      k_leafscan_slices<<<unsigned(slices), 1024, 0, st>>>(a.recs, a.num_leaves, a.slice_tot);
+      k_leafscan_totals<<<1, 1024, 0, st>>>(a.slice_tot, slices, a.total_words);
+      k_leafscan_add<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.recs, a.num_leaves, a.slice_tot);
+    }
   }
   if (a.cost_only) return cudaGetLastError();
   TraceScope ts("k_leafpack", st);
-  k_leafpack<C, IDX><<<unsigned(a.num_leaves), kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out, a.num_leaves,
-                                                                      a.perm);
+  if (small)
+    k_leafpack_warp<C, IDX><<<wgrid, kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out, a.num_leaves, a.perm);
+  else
+    k_leafpack<C, IDX><<<unsigned(a.num_leaves), kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out,
+                                                                        a.num_leaves, a.perm);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kBarSpinLimit = 1u << 22;
+constexpr uint64_t kSmallNode = 2048;  // levels whose nodes are at most this large: a warp per node
 
 template <typename C, bool IDX>
 struct Cfg {
@@ -395,6 +396,61 @@ __global__ void k_tilescan_small(LevelLaunch a) {
   }
 }
 
+// Levels of small nodes (at most kSmallNode particles): one warp partitions a
+// whole node in one pass, 32 consecutive particles per round, carrying the
+// counts of "code < v" and "code == v" from round to round - no tiles, no
+// count pass, no tile scan.  Same placement rule as k_scatter.
+template <typename C, bool IDX, int AXIS>
+__global__ void __launch_bounds__(256) k_scatter_node(LevelLaunch a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t count = 1ull << a.level;
+  const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  const C *s0 = static_cast<const C *>(a.src[0]), *s1 = static_cast<const C *>(a.src[1]),
+          *s2 = static_cast<const C *>(a.src[2]);
+  for (uint64_t j = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); j < count; j += warps) {
+    uint64_t off64, cnt64;
+    node_range(a.n, a.level, j, off64, cnt64);
+    const uint32_t off = uint32_t(off64), cnt = uint32_t(cnt64), k = cnt >> 1;
+    const uint32_t v = a.nodes[j].v, tl = a.nodes[j].tleft;
+    C *n0 = static_cast<C *>(a.dst[0]) + off, *n1 = static_cast<C *>(a.dst[1]) + off,
+      *n2 = static_cast<C *>(a.dst[2]) + off;
+    uint32_t *ni = IDX ? a.dst_idx + off : nullptr;
+    uint32_t run_l = 0, run_t = 0;  // particles below v and equal to v before this round
+    for (uint32_t base = 0; base < cnt; base += 32) {
+      const uint32_t i = base + lane;
+      const bool valid = i < cnt;
+      C x0 = 0, x1 = 0, x2 = 0;
+      uint32_t xi = 0;
+      if (valid) {
+        x0 = s0[off + i];
+        x1 = s1[off + i];
+        x2 = s2[off + i];
+        if (IDX) xi = a.src_idx[off + i];
+      }
+      const uint32_t q = AXIS == 0 ? x0 : (AXIS == 1 ? x1 : x2);
+      const bool isless = valid && q < v, istie = valid && q == v;
+      const uint32_t lm = __ballot_sync(0xffffffffu, isless), tm = __ballot_sync(0xffffffffu, istie);
+      const uint32_t tie_rank = run_t + __popc(tm & lt_mask);
+      const bool left = isless || (istie && tie_rank < tl);
+      const uint32_t glrank = run_l + __popc(lm & lt_mask) + min(tie_rank, tl);  // left-going before this one
+      if (valid) {
+        const uint32_t dst = left ? glrank : k + (i - glrank);
+        if (dst < cnt) {
+          __stcg(n0 + dst, x0);
+          __stcg(n1 + dst, x1);
+          __stcg(n2 + dst, x2);
+          if (IDX) __stcg(ni + dst, xi);
+        } else {
+          atomicOr(a.err, kErrInternal);
+        }
+      }
+      run_l += __popc(lm);
+      run_t += __popc(tm);
+    }
+  }
+}
+
 template <typename C, bool IDX, int AXIS>
 cudaError_t scatter_launch(const LevelLaunch &a, uint32_t tiles, cudaStream_t st) {
   const size_t smem = sizeof(Smem<C, IDX>);
@@ -409,8 +465,26 @@ cudaError_t scatter_launch(const LevelLaunch &a, uint32_t tiles, cudaStream_t st
   return cudaGetLastError();
 }
 
+template <typename C, bool IDX, int AXIS>
+cudaError_t scatter_node_launch(const LevelLaunch &a, cudaStream_t st) {
+  const uint64_t nodes = 1ull << a.level;
+  uint64_t grid = (nodes + 7) / 8;  // 8 warps per block, a warp per node
+  const uint64_t cap = uint64_t(device_sm_count()) * 8 * 4;
+  if (grid > cap) grid = cap;
+  TraceScope ts("k_scatter_node", st);
+  k_scatter_node<C, IDX, AXIS><<<unsigned(grid), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename C, bool IDX>
 cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
+  if (((a.n + (1ull << a.level) - 1) >> a.level) <= kSmallNode) {
+    switch (a.level % 3) {
+      case 0: return scatter_node_launch<C, IDX, 0>(a, st);
+      case 1: return scatter_node_launch<C, IDX, 1>(a, st);
+      default: return scatter_node_launch<C, IDX, 2>(a, st);
+    }
+  }
   const uint64_t tiles = (1ull << a.level) * a.tiles_per_node;
   {
     TraceScope ts("k_count", st);

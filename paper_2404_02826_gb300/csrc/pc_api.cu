@@ -72,7 +72,7 @@ struct Plan {
   uint64_t off_nodes = 0, off_leafrec = 0, off_words = 0;
   uint64_t off_zero = 0, zero_bytes = 0;  // zeroed at every call:
   uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_err = 0, off_total = 0;
-  uint64_t off_groups = 0;
+  uint64_t off_groups = 0, off_slices = 0;
   bool tune = false;  // leaf size chosen by descending from r_hi while the stream shrinks (sized for r)
   uint32_t r_hi = 0;
   int tune_first = 0, tune_last = 0;  // candidate depths
@@ -172,6 +172,8 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafRec));
   p.off_words = o;
   o = align_up(o + 8);
+  p.off_slices = o;  // slice totals of the many-leaf word scan
+  o = align_up(o + 8 * ((p.num_leaves + 8191) / 8192 + 1));
   // group records of the scatter's classification, one level at a time
   uint64_t group_bytes = 16;
   for (int l = 0; l < p.levels; ++l)
@@ -386,6 +388,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       lf.perm = perm;
       lf.recs = reinterpret_cast<LeafRec *>(ws + p.off_leafrec);
       lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
+      lf.slice_tot = reinterpret_cast<uint64_t *>(ws + p.off_slices);
       lf.cost_only = cost_only;
       return launch_leaves(lf, st);
     };

@@ -182,6 +182,7 @@ struct LeafLaunch {
   uint32_t *perm;           // optional
   LeafRec *recs;            // [num_leaves]
   uint64_t *total_words;    // device slot: payload words of the stream
+  uint64_t *slice_tot;      // [ceil(num_leaves / 8192)] scratch of the many-leaf word scan
   bool cost_only;           // bit boxes and payload words only (leaf-size autotuning)
 };
 cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st);
