@@ -188,7 +188,7 @@ def test_leaf_size_sweep_matches_oracle_sizes(pc, oracle_mod):
         n, _, nl, nw = oracle_mod.stream_header(ref)
         assert p["total_bytes"] == len(ref)
         assert p["leaves"] == nl and p["table_bytes"] == 32 * nl and p["payload_bytes"] == 4 * nw
-    auto = pc.pc_leaf_size_sweep(dpos, pc.PC_EB_REL, 1e-4, r_min=1024, r_max=12000)
+    auto = pc.pc_leaf_size_sweep(dpos, pc.PC_EB_REL, 1e-4, r_min=pc.PC_AUTOTUNE_MIN_LEAF, r_max=12000)
     got, _, _ = run_gpu(pc, pos, pc.PC_EB_REL, 1e-4, pc.LEAF_AUTO, with_perm=False)
     k = 0
     while k + 1 < len(auto) and auto[k + 1]["total_bytes"] < auto[k]["total_bytes"]:
