@@ -74,6 +74,8 @@ def lib(parallel: bool = False):
         L.oracle_bitbox.argtypes = [vp, u64, ctypes.POINTER(u64), vp, vp, vp, vp]
         L.oracle_compress.argtypes = [vp, u64, i32, i32, dbl, u64, ctypes.POINTER(vp), ctypes.POINTER(u64),
                                       ctypes.POINTER(vp)]
+        L.oracle_compress_reduced.argtypes = [vp, u64, i32, i32, dbl, u64, ctypes.POINTER(vp), ctypes.POINTER(u64),
+                                              ctypes.POINTER(vp), ctypes.POINTER(u64)]
         L.oracle_stream_header.argtypes = [vp, u64, ctypes.POINTER(u64), ctypes.POINTER(i32),
                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.oracle_decompress.argtypes = [vp, u64, vp, u64]
@@ -211,6 +213,32 @@ def compress(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: boo
             if n else np.zeros(0, np.int64)
         L.oracle_free(perm)
     return stream, p
+
+
+def compress_reduced(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: bool = True,
+                     parallel: bool = False):
+    """Compression with the bit-box reduction in rounds (Sec. 4.1, Alg. 1; see oracle.c).
+    Returns (stream bytes, perm, rounds)."""
+    pos = _positions(pos)
+    out = ctypes.c_void_p()
+    nbytes = ctypes.c_uint64()
+    perm = ctypes.c_void_p()
+    rounds = ctypes.c_uint64()
+    L = lib(parallel)
+    rc = L.oracle_compress_reduced(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), eb_mode,
+                                   float(eb), leaf_size, ctypes.byref(out), ctypes.byref(nbytes),
+                                   ctypes.byref(perm) if want_perm else None, ctypes.byref(rounds))
+    if rc:
+        raise OracleError(rc, "compress_reduced")
+    stream = ctypes.string_at(out, nbytes.value)
+    L.oracle_free(out)
+    p = None
+    if want_perm:
+        n = pos.shape[0]
+        p = np.ctypeslib.as_array(ctypes.cast(perm, ctypes.POINTER(ctypes.c_uint64)), (n,)).astype(np.int64) \
+            if n else np.zeros(0, np.int64)
+        L.oracle_free(perm)
+    return stream, p, rounds.value
 
 
 def stream_header(stream: bytes):

@@ -570,6 +570,250 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Bit-box reduction (Sec. 4.1, "bit box reduction and bit box intersection */
+/* update"; Alg. 1), in rounds.                                              */
+/*                                                                          */
+/* A bit box is the set of codes a sequence with centre code q_ref and       */
+/* widths m can hold: |q_d - q_ref_d| <= 2^(m_d - 1) - 1 on every axis (the  */
+/* centre alone when m_d = 0).  Starting from the leaves' boxes (step 4),    */
+/* each round selects every alive box whose key (sum of m_d, box index) is   */
+/* smaller than the key of every other alive box its box intersects; such    */
+/* boxes are pairwise disjoint.  In increasing index, each selected box      */
+/* takes from the intersecting alive boxes that are not selected the         */
+/* particles inside its bit box (by source box, then position), and becomes  */
+/* a sequence: its centre, its remaining own particles in order, then the    */
+/* particles it took.  Boxes that lost particles are rebuilt from what they  */
+/* keep (step 4 rules) or vanish when empty.  Rounds repeat until no box is  */
+/* alive; sequences are written in round order, then box index.  The paper  */
+/* removes one box (the smallest sum of m_d) at a time; selecting all local  */
+/* minima per round is this implementation's reading, so that rounds run in  */
+/* parallel.                                                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t qref[3], blo[3], bhi[3];
+    uint32_t m[3];
+    uint32_t key;     /* m_x + m_y + m_z */
+    uint64_t centre;  /* particle id */
+    int alive;
+} rbox;
+
+static int boxes_meet(const rbox *a, const rbox *b)
+{
+    for (int d = 0; d < 3; d++)
+        if (a->blo[d] > b->bhi[d] || b->blo[d] > a->bhi[d]) return 0;
+    return 1;
+}
+
+static int inside_box(const rbox *b, const int64_t *qp)
+{
+    for (int d = 0; d < 3; d++)
+        if (qp[d] < b->blo[d] || qp[d] > b->bhi[d]) return 0;
+    return 1;
+}
+
+static int key_less(const rbox *box, uint64_t a, uint64_t b)
+{
+    if (box[a].key != box[b].key) return box[a].key < box[b].key;
+    return a < b;
+}
+
+/* Bit box of the live particles ids[0..cnt) (in order), as in step 4. */
+static void rebuild_box(const int64_t *q, const uint64_t *ids, const unsigned char *live, uint64_t cnt,
+                        int64_t *scratch, uint64_t *slot, rbox *b)
+{
+    uint64_t k = 0;
+    for (uint64_t i = 0; i < cnt; i++)
+        if (live[i]) {
+            for (int d = 0; d < 3; d++) scratch[3 * k + d] = q[3 * ids[i] + d];
+            slot[k++] = i;
+        }
+    if (k == 0) {
+        b->alive = 0;
+        return;
+    }
+    uint64_t c;
+    int64_t lo[3], hi[3];
+    oracle_bitbox(scratch, k, &c, lo, hi, b->qref, b->m);
+    b->centre = ids[slot[c]];
+    b->key = b->m[0] + b->m[1] + b->m[2];
+    for (int d = 0; d < 3; d++) {
+        int64_t h = b->m[d] ? ((1LL << (b->m[d] - 1)) - 1) : 0;
+        b->blo[d] = b->qref[d] - h;
+        b->bhi[d] = b->qref[d] + h;
+    }
+    b->alive = 1;
+}
+
+int oracle_compress_reduced(const void *pos, uint64_t n, int dtype, int eb_mode, double eb, uint64_t leaf_size,
+                            uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out, uint64_t *rounds_out)
+{
+    *out = NULL;
+    *out_bytes = 0;
+    if (perm_out) *perm_out = NULL;
+    if (rounds_out) *rounds_out = 0;
+    if (leaf_size < 1) return OR_ERR_ARG;
+    oracle_bound b;
+    int rc = oracle_error_bound(pos, n, dtype, eb_mode, eb, &b);
+    if (rc) return rc;
+    int64_t *q = NULL, *scratch = NULL, *sq = NULL;
+    uint64_t *order = NULL, *loff = NULL, *lcnt = NULL, *perm = NULL, *slot = NULL, *seq_ids = NULL;
+    uint64_t *seq_first = NULL, *seq_wofs = NULL, nl = 0;
+    unsigned char *live = NULL, *selected = NULL;
+    rbox *box = NULL, *seq_box = NULL;
+    uint32_t *words = NULL;
+    uint8_t *buf = NULL;
+    rc = OR_ERR_NOMEM;
+    q = malloc((n ? n : 1) * 3 * sizeof(int64_t));
+    order = malloc((n ? n : 1) * sizeof(uint64_t));
+    perm = malloc((n ? n : 1) * sizeof(uint64_t));
+    live = malloc(n ? n : 1);
+    seq_ids = malloc((n ? n : 1) * sizeof(uint64_t));
+    if (!q || !order || !perm || !live || !seq_ids) goto done;
+    oracle_quantize(pos, n, dtype, &b, q);
+    rc = oracle_kdtree(q, n, leaf_size, order, &loff, &lcnt, &nl);
+    if (rc) goto done;
+    rc = OR_ERR_NOMEM;
+    uint64_t maxleaf = 1;
+    for (uint64_t L = 0; L < nl; L++)
+        if (lcnt[L] > maxleaf) maxleaf = lcnt[L];
+    box = calloc(nl ? nl : 1, sizeof(rbox));
+    seq_box = calloc(nl ? nl : 1, sizeof(rbox));
+    seq_first = malloc((nl + 1) * sizeof(uint64_t));
+    seq_wofs = malloc((nl ? nl : 1) * sizeof(uint64_t));
+    selected = calloc(nl ? nl : 1, 1);
+    scratch = malloc(maxleaf * 3 * sizeof(int64_t));
+    sq = malloc(maxleaf * 3 * sizeof(int64_t));
+    slot = malloc(maxleaf * sizeof(uint64_t));
+    if (!box || !seq_box || !seq_first || !seq_wofs || !selected || !scratch || !sq || !slot) goto done;
+    /* initial boxes: the leaves' (live[i] is particle slot i of the leaf order) */
+    for (uint64_t i = 0; i < n; i++) live[i] = 1;
+    for (uint64_t L = 0; L < nl; L++)
+        rebuild_box(q, order + loff[L], live + loff[L], lcnt[L], scratch, slot, &box[L]);
+
+    uint64_t nseq = 0, filled = 0, rounds = 0, alive = nl;
+    while (alive) {
+        rounds++;
+        for (uint64_t a = 0; a < nl; a++) {
+            selected[a] = 0;
+            if (!box[a].alive) continue;
+            int minimal = 1;
+            for (uint64_t c = 0; c < nl && minimal; c++)
+                if (c != a && box[c].alive && boxes_meet(&box[a], &box[c]) && key_less(box, c, a)) minimal = 0;
+            selected[a] = (unsigned char)minimal;
+        }
+        for (uint64_t a = 0; a < nl; a++) {
+            if (!selected[a]) continue;
+            /* the sequence: centre, its own live particles, then what it takes */
+            seq_box[nseq] = box[a];
+            seq_first[nseq] = filled;
+            seq_ids[filled++] = box[a].centre;
+            for (uint64_t i = 0; i < lcnt[a]; i++) {
+                uint64_t id = order[loff[a] + i];
+                if (live[loff[a] + i] && id != box[a].centre) seq_ids[filled++] = id;
+                live[loff[a] + i] = 0;
+            }
+            for (uint64_t c = 0; c < nl; c++) {
+                if (c == a || !box[c].alive || selected[c] || !boxes_meet(&box[a], &box[c])) continue;
+                int lost = 0;
+                for (uint64_t i = 0; i < lcnt[c]; i++) {
+                    uint64_t id = order[loff[c] + i];
+                    if (live[loff[c] + i] && inside_box(&box[a], &q[3 * id])) {
+                        seq_ids[filled++] = id;
+                        live[loff[c] + i] = 0;
+                        lost = 1;
+                    }
+                }
+                if (lost) box[c].alive = 2; /* to be rebuilt after this round */
+            }
+            nseq++;
+        }
+        for (uint64_t a = 0; a < nl; a++) {
+            if (selected[a]) box[a].alive = 0;
+            if (box[a].alive == 2) rebuild_box(q, order + loff[a], live + loff[a], lcnt[a], scratch, slot, &box[a]);
+        }
+        alive = 0;
+        for (uint64_t a = 0; a < nl; a++) alive += box[a].alive ? 1 : 0;
+    }
+    seq_first[nseq] = filled;
+
+    /* the stream, as in step 5, with the sequences in place of the leaves */
+    uint64_t total_words = 0;
+    for (uint64_t k = 0; k < nseq; k++) {
+        uint64_t cnt = seq_first[k + 1] - seq_first[k];
+        uint64_t bits = (uint64_t)(seq_box[k].m[0] + seq_box[k].m[1] + seq_box[k].m[2]) * (cnt - 1);
+        seq_wofs[k] = total_words;
+        total_words += (bits + 31) / 32;
+    }
+    uint64_t bytes = OR_HEADER_BYTES + OR_LEAF_BYTES * nseq + 4 * total_words;
+    buf = calloc(bytes, 1);
+    words = calloc(total_words ? total_words : 1, sizeof(uint32_t));
+    if (!buf || !words) goto done;
+    memcpy(buf, "PCB1", 4);
+    put_u16(buf + 4, 1);
+    buf[6] = (uint8_t)dtype;
+    buf[7] = (uint8_t)eb_mode;
+    put_u64(buf + 8, n);
+    put_f64(buf + 16, eb);
+    put_f64(buf + 24, b.eps);
+    put_f64(buf + 32, b.s);
+    for (int d = 0; d < 3; d++) put_f64(buf + 40 + 8 * d, b.o[d]);
+    put_u64(buf + 64, nseq);
+    put_u64(buf + 72, total_words);
+    put_u32(buf + 80, (uint32_t)leaf_size);
+    for (uint64_t k = 0; k < nseq; k++) {
+        const rbox *sb = &seq_box[k];
+        uint8_t *rec = buf + OR_HEADER_BYTES + OR_LEAF_BYTES * k;
+        put_u64(rec + 0, seq_first[k]);
+        put_u64(rec + 8, seq_wofs[k]);
+        for (int d = 0; d < 3; d++) put_u32(rec + 16 + 4 * d, (uint32_t)(int32_t)sb->qref[d]);
+        for (int d = 0; d < 3; d++) rec[28 + d] = (uint8_t)sb->m[d];
+        uint64_t bitpos = 32 * seq_wofs[k];
+        for (uint64_t i = seq_first[k]; i < seq_first[k + 1]; i++) {
+            uint64_t id = seq_ids[i];
+            perm[i] = id;
+            if (i == seq_first[k]) continue; /* the centre */
+            for (int d = 0; d < 3; d++) {
+                uint32_t md = sb->m[d];
+                if (md == 0) continue;
+                int64_t c = (q[3 * id + d] - sb->qref[d]) + ((1LL << (md - 1)) - 1);
+                write_bits(words, &bitpos, (uint64_t)c, md);
+            }
+        }
+    }
+    for (uint64_t w = 0; w < total_words; w++)
+        put_u32(buf + OR_HEADER_BYTES + OR_LEAF_BYTES * nseq + 4 * w, words[w]);
+    *out = buf;
+    buf = NULL;
+    *out_bytes = bytes;
+    if (perm_out) {
+        *perm_out = perm;
+        perm = NULL;
+    }
+    if (rounds_out) *rounds_out = rounds;
+    rc = OR_OK;
+done:
+    free(q);
+    free(order);
+    free(loff);
+    free(lcnt);
+    free(perm);
+    free(live);
+    free(seq_ids);
+    free(box);
+    free(seq_box);
+    free(seq_first);
+    free(seq_wofs);
+    free(selected);
+    free(scratch);
+    free(sq);
+    free(slot);
+    free(words);
+    free(buf);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Step 6: decoding (Sec. 3).  The reconstruction of code q on axis d is     */
 /* (T)(o_d + s*q): one double multiply, one double add, one rounding to T.   */
 /* ------------------------------------------------------------------------ */
