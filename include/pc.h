@@ -76,7 +76,7 @@ typedef enum { PC_EB_ABS = 0, PC_EB_REL = 1 } pc_eb_mode;
 typedef struct {
     uint32_t leaf_size; /* r of Sec. 4.1: largest leaf; 0 = 4096; valid 1..PC_MAX_LEAF_SIZE.
                            With PC_FLAG_AUTOTUNE_LEAF: the largest candidate (0 = PC_MAX_LEAF_SIZE) */
-    uint32_t flags;     /* 0 or PC_FLAG_AUTOTUNE_LEAF */
+    uint32_t flags;     /* 0, or PC_FLAG_AUTOTUNE_LEAF and/or PC_FLAG_BOX_REDUCTION */
 } pc_config;
 
 /* Leaf-size autotuning (no counterpart in the paper, which fixes r by hand,
@@ -90,6 +90,24 @@ typedef struct {
  * max = leaf_size.  The header records that r, and a plain call with it
  * gives the same stream. */
 #define PC_FLAG_AUTOTUNE_LEAF 1u
+
+/* Bit-box reduction (Sec. 4.1, "bit box reduction and bit box intersection
+ * update"; Alg. 1).  Starting from the leaves' bit boxes, boxes are emitted as
+ * sequences in rounds: a round takes every alive box whose key (m_x + m_y +
+ * m_z, then box index) is smaller than that of every other alive box its bit
+ * box meets (such boxes are pairwise disjoint).  Each taken box becomes a
+ * sequence holding its centre, its remaining particles, then the particles of
+ * the other boxes it meets that lie inside its bit box (by source box, then
+ * leaf order), coded with its widths.  Boxes that lost particles get the bit
+ * box of what they keep (the leaf rules); empty boxes vanish.  Sequences are
+ * written in round order, then box index, in place of the leaves: the stream
+ * format and the decoder are unchanged, a sequence may hold more than r
+ * particles, and there are at most as many sequences as leaves.  The paper
+ * takes one box (the smallest key) at a time; taking all local minima per
+ * round is this library's reading, which lets a round run in parallel.
+ * Combined with PC_FLAG_AUTOTUNE_LEAF, the leaf size is chosen first (on the
+ * plain stream size) and the reduction runs on those leaves. */
+#define PC_FLAG_BOX_REDUCTION 2u
 #define PC_AUTOTUNE_MIN_LEAF 64u
 
 #define PC_DEFAULT_LEAF_SIZE 4096u

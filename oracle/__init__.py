@@ -74,7 +74,7 @@ def lib(parallel: bool = False):
         L.oracle_bitbox.argtypes = [vp, u64, ctypes.POINTER(u64), vp, vp, vp, vp]
         L.oracle_compress.argtypes = [vp, u64, i32, i32, dbl, u64, ctypes.POINTER(vp), ctypes.POINTER(u64),
                                       ctypes.POINTER(vp)]
-        L.oracle_compress_reduced.argtypes = [vp, u64, i32, i32, dbl, u64, ctypes.POINTER(vp), ctypes.POINTER(u64),
+        L.oracle_compress_reduced.argtypes = [vp, u64, i32, i32, dbl, u64, i32, ctypes.POINTER(vp), ctypes.POINTER(u64),
                                               ctypes.POINTER(vp), ctypes.POINTER(u64)]
         L.oracle_stream_header.argtypes = [vp, u64, ctypes.POINTER(u64), ctypes.POINTER(i32),
                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]
@@ -216,8 +216,9 @@ def compress(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: boo
 
 
 def compress_reduced(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: bool = True,
-                     parallel: bool = False):
+                     parallel: bool = False, one_per_round: bool = False):
     """Compression with the bit-box reduction in rounds (Sec. 4.1, Alg. 1; see oracle.c).
+    one_per_round removes a single box (the smallest key) per round, the paper's order.
     Returns (stream bytes, perm, rounds)."""
     pos = _positions(pos)
     out = ctypes.c_void_p()
@@ -226,7 +227,7 @@ def compress_reduced(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_p
     rounds = ctypes.c_uint64()
     L = lib(parallel)
     rc = L.oracle_compress_reduced(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), eb_mode,
-                                   float(eb), leaf_size, ctypes.byref(out), ctypes.byref(nbytes),
+                                   float(eb), leaf_size, int(one_per_round), ctypes.byref(out), ctypes.byref(nbytes),
                                    ctypes.byref(perm) if want_perm else None, ctypes.byref(rounds))
     if rc:
         raise OracleError(rc, "compress_reduced")

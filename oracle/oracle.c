@@ -587,7 +587,8 @@ done:
 /* alive; sequences are written in round order, then box index.  The paper  */
 /* removes one box (the smallest sum of m_d) at a time; selecting all local  */
 /* minima per round is this implementation's reading, so that rounds run in  */
-/* parallel.                                                                 */
+/* parallel.  one_per_round != 0 selects only the alive box of smallest key  */
+/* per round, which is the paper's order (for comparing the two).            */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -646,7 +647,8 @@ static void rebuild_box(const int64_t *q, const uint64_t *ids, const unsigned ch
 }
 
 int oracle_compress_reduced(const void *pos, uint64_t n, int dtype, int eb_mode, double eb, uint64_t leaf_size,
-                            uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out, uint64_t *rounds_out)
+                            int one_per_round, uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out,
+                            uint64_t *rounds_out)
 {
     *out = NULL;
     *out_bytes = 0;
@@ -694,13 +696,23 @@ int oracle_compress_reduced(const void *pos, uint64_t n, int dtype, int eb_mode,
     uint64_t nseq = 0, filled = 0, rounds = 0, alive = nl;
     while (alive) {
         rounds++;
-        for (uint64_t a = 0; a < nl; a++) {
-            selected[a] = 0;
-            if (!box[a].alive) continue;
-            int minimal = 1;
-            for (uint64_t c = 0; c < nl && minimal; c++)
-                if (c != a && box[c].alive && boxes_meet(&box[a], &box[c]) && key_less(box, c, a)) minimal = 0;
-            selected[a] = (unsigned char)minimal;
+        if (one_per_round) {
+            /* the paper's order: only the alive box of smallest key */
+            uint64_t best = nl;
+            for (uint64_t a = 0; a < nl; a++) {
+                selected[a] = 0;
+                if (box[a].alive && (best == nl || key_less(box, a, best))) best = a;
+            }
+            selected[best] = 1;
+        } else {
+            for (uint64_t a = 0; a < nl; a++) {
+                selected[a] = 0;
+                if (!box[a].alive) continue;
+                int minimal = 1;
+                for (uint64_t c = 0; c < nl && minimal; c++)
+                    if (c != a && box[c].alive && boxes_meet(&box[a], &box[c]) && key_less(box, c, a)) minimal = 0;
+                selected[a] = (unsigned char)minimal;
+            }
         }
         for (uint64_t a = 0; a < nl; a++) {
             if (!selected[a]) continue;

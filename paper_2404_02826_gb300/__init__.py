@@ -38,6 +38,7 @@ PC_MAX_LEAF_SIZE = 12000
 PC_HEADER_BYTES = 96
 PC_LEAF_BYTES = 32
 PC_FLAG_AUTOTUNE_LEAF = 1
+PC_FLAG_BOX_REDUCTION = 2
 PC_AUTOTUNE_MIN_LEAF = 64
 LEAF_AUTO = -1  # leaf_size argument: autotune with candidates up to PC_MAX_LEAF_SIZE
 
@@ -168,9 +169,19 @@ def _check(rc: int, where: str):
         raise PCError(rc, where)
 
 
-def _cfg(leaf_size: int) -> pc_config:
+def config(leaf_size: int = 0, autotune: bool = False, reduce: bool = False) -> pc_config:
+    """A pc_config: leaf size r (0 = default; with autotune the largest candidate,
+    0 = PC_MAX_LEAF_SIZE), PC_FLAG_AUTOTUNE_LEAF and PC_FLAG_BOX_REDUCTION."""
+    return pc_config(int(leaf_size), (PC_FLAG_AUTOTUNE_LEAF if autotune else 0) |
+                     (PC_FLAG_BOX_REDUCTION if reduce else 0))
+
+
+def _cfg(leaf_size) -> pc_config:
     """leaf_size >= 0: that leaf size (0 = default); leaf_size < 0: autotuned
-    (PC_FLAG_AUTOTUNE_LEAF) with largest candidate -leaf_size (LEAF_AUTO: the default maximum)."""
+    (PC_FLAG_AUTOTUNE_LEAF) with largest candidate -leaf_size (LEAF_AUTO: the default maximum);
+    a pc_config (see config()) is used as given."""
+    if isinstance(leaf_size, pc_config):
+        return leaf_size
     leaf_size = int(leaf_size)
     if leaf_size < 0:
         return pc_config(0 if leaf_size == LEAF_AUTO else -leaf_size, PC_FLAG_AUTOTUNE_LEAF)

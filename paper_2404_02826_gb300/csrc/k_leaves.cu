@@ -459,7 +459,7 @@ template <typename C, bool IDX>
 cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
   const C *q0 = static_cast<const C *>(a.codes[0]), *q1 = static_cast<const C *>(a.codes[1]),
           *q2 = static_cast<const C *>(a.codes[2]);
-  {
+  if (!a.recs_ready) {
     TraceScope ts("k_leaftable", st);
     const uint64_t nodes = a.split_level < 0 ? 1 : (1ull << a.split_level);
     k_leaftable<<<unsigned((nodes + 255) / 256), 256, 0, st>>>(a.n, a.split_level, a.leaf_size, a.recs,
@@ -470,7 +470,7 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
   const uint64_t warp_blocks = (a.num_leaves + 7) / 8;
   const unsigned wgrid = unsigned(warp_blocks < uint64_t(device_sm_count()) * 32 ? warp_blocks
                                                                                  : uint64_t(device_sm_count()) * 32);
-  {
+  if (!a.recs_ready) {
     TraceScope ts("k_leafbox", st);
     if (small)
       k_leafbox_warp<C><<<wgrid, 256, 0, st>>>(q0, q1, q2, a.recs, a.num_leaves);
@@ -499,6 +499,15 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t launch_leaftable(uint64_t n, int split_level, uint32_t leaf_size, LeafRec *recs, uint64_t num_leaves,
+                             cudaStream_t st) {
+  if (n == 0 || num_leaves == 0) return cudaSuccess;
+  TraceScope ts("k_leaftable", st);
+  const uint64_t nodes = split_level < 0 ? 1 : (1ull << split_level);
+  k_leaftable<<<unsigned((nodes + 255) / 256), 256, 0, st>>>(n, split_level, leaf_size, recs, num_leaves);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st) {
   if (a.n == 0 || a.num_leaves == 0) return cudaSuccess;

@@ -1,0 +1,812 @@
+// Bit-box reduction (Sec. 4.1, "bit box reduction and bit box intersection
+// update"; Alg. 1 of arXiv 2404.02826), in rounds of pairwise disjoint boxes.
+//
+// Input: the codes after the last k-d level, stored leaf after leaf ("slots").
+// Every leaf starts as a box: the bit box of its particles that are not yet in
+// a sequence ("live").  dest[slot] is the output position of a particle once a
+// sequence holds it (kLive before).
+//
+// Intersection query: a 32-ary tree over the box indices.  Level 0 are the
+// boxes; node j of level k >= 1 holds the union of the alive bit boxes below
+// its children [32j, 32j + 32) of level k - 1 and the least (key, index) of
+// those boxes (key = m_x + m_y + m_z).  It is refitted bottom-up after every
+// round (the paper's bottom-up update) and searched top-down by one warp that
+// tests 32 children at a time, depth first, so that boxes come out in
+// increasing index.
+//
+// One round:
+//   select   a warp per alive box a: a is taken when no other alive box with a
+//            smaller (key, index) meets its bit box.  Taken boxes are pairwise
+//            disjoint, so no particle lies in two of them.
+//   count    a block per taken box: its live particles, plus, for every alive
+//            box c that is not taken and meets it, the live particles of c
+//            inside its bit box.
+//   scan     one block: each taken box's sequence index and first output
+//            position, in box order, after the sequences of earlier rounds.
+//   place    a block per taken box: output positions of its centre, its other
+//            live particles in slot order, then the particles it takes, by
+//            source box and slot; boxes that lost particles are listed.
+//   rebuild  a block per listed box: the bit box of what it keeps (the leaf
+//            rules: AABB, the particle closest to its centre, Eq. 2); taken and
+//            emptied boxes die.
+//   refit    the tree over the new boxes.
+// The host reads the alive count back every few rounds; rounds issued after
+// the last box died return at once.  A final pass moves codes and input
+// indices into sequence order for the packing kernels.
+#include <climits>
+#include <cstdint>
+
+#include "pc_internal.cuh"
+
+namespace pcx {
+namespace {
+
+constexpr int kMaxLevels = 8;  // 32^7 > 2^32 boxes
+constexpr uint32_t kLive = 0xffffffffu;
+constexpr uint32_t kAlive = 1u, kTaken = 2u;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kListCap = 512;  // boxes met by a taken box, per batch
+constexpr int kRoundsPerCheck = 4;
+
+struct RBox {            // what the tree tests, 32 bytes
+  int32_t lo[3], hi[3];  // bit box: q_ref -/+ (2^(m-1) - 1) per axis (q_ref where m = 0)
+  uint32_t key;          // m_x + m_y + m_z
+  uint32_t state;        // kAlive | kTaken
+};
+struct TNode {           // 32 bytes
+  int32_t lo[3], hi[3];  // union of the alive bit boxes below (lo > hi: none)
+  unsigned long long min;  // least key << 32 | index below, ~0 for none
+};
+struct RInfo {  // the rest of a box, 64 bytes
+  int32_t qref[3];
+  uint32_t m;       // m_x | m_y << 8 | m_z << 16
+  uint32_t centre;  // slot of the centre
+  uint32_t live;    // live particles
+  uint32_t off, cnt;  // the leaf's slots
+  uint32_t tlo[3], thi[3];  // AABB of the live particles
+  uint32_t lost;    // set while listed for a rebuild
+  uint32_t pad;
+};
+static_assert(sizeof(RBox) == 32 && sizeof(TNode) == 32 && sizeof(RInfo) == 64, "box layouts");
+
+struct RCounters {
+  uint32_t alive, taken, nlost, nseq, filled, rounds, pad[2];
+};
+
+struct Tree {
+  RBox *box;
+  TNode *node[kMaxLevels];       // node[k], 1 <= k <= top
+  uint32_t *ticket[kMaxLevels];  // ticket[k], 2 <= k <= top: children of node j refitted so far
+  uint32_t count[kMaxLevels];    // count[0] = boxes, count[top] = 1
+  int top;
+};
+
+struct State {
+  Tree t;
+  RInfo *info;
+  uint32_t *dest;     // [n]
+  uint32_t *seq_cnt;  // [boxes] particles of a taken box's sequence, 0 otherwise
+  uint32_t *seq_pos;  // [boxes] first output position of a taken box's sequence
+  uint32_t *taken;    // [boxes] boxes taken in the round, any order
+  uint32_t *lost;     // [boxes] boxes that lost particles in the round, any order
+  RCounters *ctr;
+  uint32_t nl;
+};
+
+struct Layout {
+  uint64_t dest, box, info, node[kMaxLevels], ticket[kMaxLevels], seq_cnt, seq_pos, taken, lost, ctr;
+  uint64_t zero_begin, zero_end, total;
+  uint32_t count[kMaxLevels];
+  int top;
+};
+
+inline uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
+
+Layout layout_of(uint64_t n, uint64_t nl) {
+  Layout L = {};
+  L.count[0] = uint32_t(nl);
+  int k = 0;
+  do {
+    L.count[k + 1] = (L.count[k] + 31) / 32;
+    ++k;
+  } while (L.count[k] > 1);
+  L.top = k;
+  uint64_t o = 0;
+  L.dest = o;
+  o = align256(o + 4 * n);
+  L.box = o;
+  o = align256(o + sizeof(RBox) * nl);
+  L.info = o;
+  o = align256(o + sizeof(RInfo) * nl);
+  for (int l = 1; l <= L.top; ++l) {
+    L.node[l] = o;
+    o = align256(o + sizeof(TNode) * L.count[l]);
+  }
+  L.seq_pos = o;
+  o = align256(o + 4 * nl);
+  L.taken = o;
+  o = align256(o + 4 * nl);
+  L.lost = o;
+  o = align256(o + 4 * nl);
+  L.zero_begin = o;  // zeroed once per call
+  for (int l = 2; l <= L.top; ++l) {
+    L.ticket[l] = o;
+    o = align256(o + 4 * uint64_t(L.count[l]));
+  }
+  L.seq_cnt = o;
+  o = align256(o + 4 * nl);
+  L.ctr = o;
+  o = align256(o + sizeof(RCounters));
+  L.zero_end = o;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+
+// A bit box in registers.
+struct Box6 {
+  int32_t lo[3], hi[3];
+};
+// Does the box stored as (p, q) = (lo0 lo1 lo2 hi0, hi1 hi2 ...) meet `a`?
+__device__ __forceinline__ bool meets(const Box6 &a, const int4 &p, const int4 &q) {
+  return a.lo[0] <= p.w && p.x <= a.hi[0] && a.lo[1] <= q.x && p.y <= a.hi[1] && a.lo[2] <= q.y && p.z <= a.hi[2];
+}
+
+// ---- top-down search ----------------------------------------------------
+
+struct Descent {
+  uint32_t mask[kMaxLevels];  // children of the current node at each level still to visit
+  uint32_t base[kMaxLevels];  // index of child 0 at each level
+  int lvl;
+  bool done;
+};
+
+// One warp tests the children [first, first + 32) of level `level`.
+template <class NodeOk, class BoxOk>
+__device__ __forceinline__ uint32_t test_children(const Tree &t, int level, uint32_t first, NodeOk nok, BoxOk bok) {
+  const uint32_t i = first + (threadIdx.x & 31);
+  bool ok = false;
+  if (i < t.count[level]) {
+    if (level == 0) {
+      const int4 *p = reinterpret_cast<const int4 *>(t.box + i);
+      ok = bok(i, p[0], p[1]);
+    } else {
+      const int4 *p = reinterpret_cast<const int4 *>(t.node[level] + i);
+      ok = nok(p[0], p[1]);
+    }
+  }
+  return __ballot_sync(0xffffffffu, ok);
+}
+
+template <class NodeOk, class BoxOk>
+__device__ void descent_start(Descent &d, const Tree &t, NodeOk nok, BoxOk bok) {
+  d.lvl = t.top - 1;
+  d.base[d.lvl] = 0;
+  d.mask[d.lvl] = test_children(t, d.lvl, 0, nok, bok);
+  d.done = false;
+}
+
+// Continues the search.  take(first, mask) gets each nonempty group of wanted
+// boxes (bit i: box first + i) in increasing index and returns true to pause;
+// returns true when paused, false when the search is complete.
+template <class NodeOk, class BoxOk, class Take>
+__device__ bool descent_run(Descent &d, const Tree &t, NodeOk nok, BoxOk bok, Take take) {
+  while (!d.done) {
+    const int l = d.lvl;
+    const uint32_t m = d.mask[l];
+    if (m == 0) {
+      if (l + 1 >= t.top)
+        d.done = true;
+      else
+        d.lvl = l + 1;
+      continue;
+    }
+    if (l == 0) {
+      d.mask[0] = 0;
+      if (take(d.base[0], m)) return true;
+      continue;
+    }
+    d.mask[l] = m & (m - 1);
+    const uint32_t first = (d.base[l] + uint32_t(__ffs(int(m)) - 1)) * 32;
+    d.base[l - 1] = first;
+    d.mask[l - 1] = test_children(t, l - 1, first, nok, bok);
+    d.lvl = l - 1;
+  }
+  return false;
+}
+
+// ---- refit ----------------------------------------------------------------
+
+__device__ __forceinline__ void warp_union(int32_t lo[3], int32_t hi[3], unsigned long long &mn) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = __reduce_min_sync(0xffffffffu, lo[d]);
+    hi[d] = __reduce_max_sync(0xffffffffu, hi[d]);
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mn, o);
+    mn = y < mn ? y : mn;
+  }
+}
+
+// A warp per node of level 1; the warp that completes the last child of a
+// node (ticket) goes on to compute that node, up to the root.
+__global__ void __launch_bounds__(kThreads) k_rd_refit(State S) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.ctr->taken = 0;
+    S.ctr->nlost = 0;
+  }
+  if (S.ctr->alive == 0) return;
+  const int lane = threadIdx.x & 31;
+  uint32_t j = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+  if (j >= S.t.count[1]) return;
+  {
+    const uint32_t c = j * 32 + lane;
+    int32_t lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    unsigned long long mn = ~0ull;
+    if (c < S.t.count[0]) {
+      const RBox b = S.t.box[c];
+      if (b.state & kAlive) {
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = b.lo[d];
+          hi[d] = b.hi[d];
+        }
+        mn = (static_cast<unsigned long long>(b.key) << 32) | c;
+      }
+    }
+    warp_union(lo, hi, mn);
+    if (lane == 0) S.t.node[1][j] = TNode{{lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, mn};
+  }
+  for (int l = 1; l < S.t.top; ++l) {
+    const uint32_t p = j >> 5;
+    const uint32_t kids = min(32u, S.t.count[l] - p * 32);
+    uint32_t tk = 0;
+    if (lane == 0) {
+      __threadfence();
+      tk = atomicAdd(S.t.ticket[l + 1] + p, 1u);
+    }
+    tk = __shfl_sync(0xffffffffu, tk, 0);
+    if (tk + 1 != kids) return;
+    if (lane == 0) S.t.ticket[l + 1][p] = 0;  // ready for the next refit
+    __threadfence();
+    const uint32_t c = p * 32 + lane;
+    int32_t lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    unsigned long long mn = ~0ull;
+    if (c < S.t.count[l]) {
+      const int4 *q = reinterpret_cast<const int4 *>(S.t.node[l] + c);
+      const int4 a = __ldcg(q), b = __ldcg(q + 1);
+      lo[0] = a.x;
+      lo[1] = a.y;
+      lo[2] = a.z;
+      hi[0] = a.w;
+      hi[1] = b.x;
+      hi[2] = b.y;
+      mn = (static_cast<unsigned long long>(uint32_t(b.w)) << 32) | uint32_t(b.z);
+    }
+    warp_union(lo, hi, mn);
+    if (lane == 0) S.t.node[l + 1][p] = TNode{{lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, mn};
+    j = p;
+  }
+}
+
+// ---- select ---------------------------------------------------------------
+
+__device__ __forceinline__ Box6 box6(const RBox &b) {
+  Box6 x;
+  for (int d = 0; d < 3; ++d) {
+    x.lo[d] = b.lo[d];
+    x.hi[d] = b.hi[d];
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(kThreads) k_rd_select(State S) {
+  if (S.ctr->alive == 0) return;
+  const uint32_t a = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+  if (a >= S.nl) return;
+  const RBox A = S.t.box[a];
+  if (!(A.state & kAlive)) return;
+  const unsigned long long ka = (static_cast<unsigned long long>(A.key) << 32) | a;
+  const Box6 bx = box6(A);
+  auto nok = [&](const int4 &p, const int4 &q) {
+    const unsigned long long mn = (static_cast<unsigned long long>(uint32_t(q.w)) << 32) | uint32_t(q.z);
+    return mn < ka && meets(bx, p, q);
+  };
+  auto bok = [&](uint32_t c, const int4 &p, const int4 &q) {
+    const unsigned long long kc = (static_cast<unsigned long long>(uint32_t(q.z)) << 32) | c;
+    return (uint32_t(q.w) & kAlive) && kc < ka && meets(bx, p, q);
+  };
+  Descent d;
+  descent_start(d, S.t, nok, bok);
+  const bool blocked = descent_run(d, S.t, nok, bok, [](uint32_t, uint32_t) { return true; });
+  if (!blocked && (threadIdx.x & 31) == 0) {
+    atomicOr(&S.t.box[a].state, kTaken);
+    S.taken[atomicAdd(&S.ctr->taken, 1u)] = a;
+  }
+}
+
+// ---- count and place ------------------------------------------------------
+
+template <typename C>
+__device__ __forceinline__ bool inside(const Box6 &b, const C *q0, const C *q1, const C *q2, uint32_t s) {
+  const int32_t x = int32_t(q0[s]), y = int32_t(q1[s]), z = int32_t(q2[s]);
+  return b.lo[0] <= x && x <= b.hi[0] && b.lo[1] <= y && y <= b.hi[1] && b.lo[2] <= z && z <= b.hi[2];
+}
+
+// Live particles of box c inside bit box b, by one warp; with PLACE they get
+// the output positions pos, pos + 1, ... in slot order.  Returns the count.
+template <typename C, bool PLACE>
+__device__ uint32_t warp_take(const State &S, const C *q0, const C *q1, const C *q2, uint32_t c, const Box6 &b,
+                              uint32_t pos) {
+  const RInfo I = S.info[c];
+  bool meet = true, all = true;
+  for (int d = 0; d < 3; ++d) {
+    const int32_t lo = int32_t(I.tlo[d]), hi = int32_t(I.thi[d]);
+    if (lo > b.hi[d] || hi < b.lo[d]) meet = false;
+    if (lo < b.lo[d] || hi > b.hi[d]) all = false;
+  }
+  if (!meet) return 0;
+  const uint32_t end = I.off + I.cnt;
+  if (!PLACE) {
+    if (all) return I.live;
+    uint32_t k = 0;
+    for (uint32_t s = I.off + (threadIdx.x & 31); s < end; s += 32)
+      if (S.dest[s] == kLive && inside(b, q0, q1, q2, s)) ++k;
+    return __reduce_add_sync(0xffffffffu, k);
+  }
+  uint32_t k = 0;
+  for (uint32_t s0 = I.off; s0 < end; s0 += 32) {
+    const uint32_t s = s0 + (threadIdx.x & 31);
+    bool in = false;
+    if (s < end && S.dest[s] == kLive) in = all || inside(b, q0, q1, q2, s);
+    const uint32_t bal = __ballot_sync(0xffffffffu, in);
+    if (in) S.dest[s] = pos + k + __popc(bal & lanemask_lt());
+    k += __popc(bal);
+  }
+  return k;
+}
+
+// A block per taken box.  PLACE = false: the particles of its sequence into
+// seq_cnt; PLACE = true: their output positions from seq_pos on.
+template <typename C, bool PLACE>
+__global__ void __launch_bounds__(kThreads) k_rd_take(State S, const C *__restrict__ q0, const C *__restrict__ q1,
+                                                      const C *__restrict__ q2) {
+  __shared__ uint32_t list[kListCap];
+  __shared__ uint32_t lpos[kListCap];
+  __shared__ uint32_t s_n, s_done, s_sum;
+  __shared__ uint32_t s_w[kWarps];
+  if (S.ctr->alive == 0) return;
+  const uint32_t ntaken = S.ctr->taken;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t i = blockIdx.x; i < ntaken; i += gridDim.x) {
+    const uint32_t a = S.taken[i];
+    const RBox A = S.t.box[a];
+    const Box6 bx = box6(A);
+    const RInfo IA = S.info[a];
+    uint32_t pos = 0;
+    if (PLACE) {
+      // the centre, then the box's other live particles in slot order
+      pos = S.seq_pos[a];
+      const uint32_t per = ((IA.cnt + kWarps - 1) / kWarps + 31) / 32 * 32;
+      const uint32_t w0 = IA.off + min(IA.cnt, uint32_t(warp) * per);
+      const uint32_t w1 = IA.off + min(IA.cnt, uint32_t(warp + 1) * per);
+      uint32_t k = 0;
+      for (uint32_t s = w0 + lane; s < w1; s += 32) k += (S.dest[s] == kLive && s != IA.centre) ? 1u : 0u;
+      k = __reduce_add_sync(0xffffffffu, k);
+      if (lane == 0) s_w[warp] = k;
+      __syncthreads();
+      uint32_t before = 0;
+      for (int w = 0; w < warp; ++w) before += s_w[w];
+      uint32_t r = pos + 1 + before;
+      for (uint32_t s0 = w0; s0 < w1; s0 += 32) {
+        const uint32_t s = s0 + lane;
+        const bool in = s < w1 && S.dest[s] == kLive && s != IA.centre;
+        const uint32_t bal = __ballot_sync(0xffffffffu, in);
+        if (in) S.dest[s] = r + __popc(bal & lanemask_lt());
+        r += __popc(bal);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) S.dest[IA.centre] = pos;
+      pos += IA.live;
+    }
+    uint32_t total = IA.live;
+    // the alive boxes that are not taken and meet this one, in index order, in batches
+    auto nok = [&](const int4 &p, const int4 &q) { return meets(bx, p, q); };
+    auto bok = [&](uint32_t c, const int4 &p, const int4 &q) {
+      return (uint32_t(q.w) & (kAlive | kTaken)) == kAlive && meets(bx, p, q);
+    };
+    Descent d;
+    if (warp == 0) descent_start(d, S.t, nok, bok);
+    for (;;) {
+      if (warp == 0) {
+        uint32_t nlist = 0;
+        descent_run(d, S.t, nok, bok, [&](uint32_t first, uint32_t m) {
+          if ((m >> lane) & 1u) list[nlist + __popc(m & lanemask_lt())] = first + lane;
+          nlist += __popc(m);
+          return nlist + 32 > kListCap;
+        });
+        if (lane == 0) {
+          s_n = nlist;
+          s_done = d.done ? 1u : 0u;
+        }
+      }
+      __syncthreads();
+      const uint32_t nlist = s_n;
+      const bool done = s_done != 0;
+      for (uint32_t j = warp; j < nlist; j += kWarps) {
+        const uint32_t k = warp_take<C, false>(S, q0, q1, q2, list[j], bx, 0);
+        if (lane == 0) lpos[j] = k;
+      }
+      __syncthreads();
+      if (warp == 0) {  // exclusive scan of the counts (PLACE) and their sum
+        uint32_t run = 0;
+        for (uint32_t j0 = 0; j0 < nlist; j0 += 32) {
+          const uint32_t x = j0 + lane < nlist ? lpos[j0 + lane] : 0u;
+          uint32_t incl = x;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          if (PLACE && j0 + lane < nlist) lpos[j0 + lane] = run + incl - x;
+          run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) s_sum = run;
+      }
+      __syncthreads();
+      if (PLACE) {
+        for (uint32_t j = warp; j < nlist; j += kWarps) {
+          const uint32_t c = list[j];
+          const uint32_t k = warp_take<C, true>(S, q0, q1, q2, c, bx, pos + lpos[j]);
+          if (k && lane == 0 && atomicExch(&S.info[c].lost, 1u) == 0u) S.lost[atomicAdd(&S.ctr->nlost, 1u)] = c;
+        }
+      }
+      pos += s_sum;
+      total += s_sum;
+      __syncthreads();  // the batch's shared state is reused
+      if (done) break;
+    }
+    if (!PLACE && threadIdx.x == 0) S.seq_cnt[a] = total;
+  }
+}
+
+// ---- scan -----------------------------------------------------------------
+
+// Sequence index and first position of every taken box, in box order.
+__global__ void __launch_bounds__(1024) k_rd_scan(State S, LeafRec *seqs) {
+  __shared__ uint32_t ws[32], wc[32];
+  if (S.ctr->alive == 0) return;
+  const uint32_t filled = S.ctr->filled, nseq = S.ctr->nseq;
+  const uint32_t nl = S.nl;
+  const uint32_t per = (nl + 1023) / 1024;
+  const uint32_t b0 = min(nl, threadIdx.x * per), b1 = min(nl, b0 + per);
+  uint32_t sum = 0, cnt = 0;
+  for (uint32_t a = b0; a < b1; ++a) {
+    const uint32_t x = S.seq_cnt[a];
+    sum += x;
+    cnt += x ? 1u : 0u;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t is = sum, ic = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t ys = __shfl_up_sync(0xffffffffu, is, o), yc = __shfl_up_sync(0xffffffffu, ic, o);
+    if (lane >= o) {
+      is += ys;
+      ic += yc;
+    }
+  }
+  if (lane == 31) {
+    ws[warp] = is;
+    wc[warp] = ic;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t xs = ws[lane], xc = wc[lane];
+    uint32_t js = xs, jc = xc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t ys = __shfl_up_sync(0xffffffffu, js, o), yc = __shfl_up_sync(0xffffffffu, jc, o);
+      if (lane >= o) {
+        js += ys;
+        jc += yc;
+      }
+    }
+    ws[lane] = js - xs;
+    wc[lane] = jc - xc;
+    if (lane == 31) {  // every thread has read the counters above
+      S.ctr->filled = filled + js;
+      S.ctr->nseq = nseq + jc;
+      S.ctr->rounds += 1;
+    }
+  }
+  __syncthreads();
+  uint32_t pos = filled + ws[warp] + is - sum, seq = nseq + wc[warp] + ic - cnt;
+  for (uint32_t a = b0; a < b1; ++a) {
+    const uint32_t x = S.seq_cnt[a];
+    if (!x) continue;
+    S.seq_cnt[a] = 0;
+    S.seq_pos[a] = pos;
+    const RInfo I = S.info[a];
+    LeafRec r = {};
+    r.off = pos;
+    r.cnt = x;
+    r.centre = 0;
+    r.m = I.m;
+    for (int d = 0; d < 3; ++d) r.qref[d] = I.qref[d];
+    const uint64_t w = (I.m & 0xffu) + ((I.m >> 8) & 0xffu) + ((I.m >> 16) & 0xffu);
+    r.words = uint32_t((w * (x - 1) + 31) >> 5);
+    seqs[seq] = r;
+    pos += x;
+    ++seq;
+  }
+}
+
+// ---- rebuild --------------------------------------------------------------
+
+// INIT: every leaf's first box (all particles live; the counters start).
+// Otherwise: the boxes listed by place get the bit box of their live
+// particles or die when none is left; taken boxes die.
+template <typename C, bool INIT>
+__global__ void __launch_bounds__(kThreads) k_rd_rebuild(State S, const C *__restrict__ q0, const C *__restrict__ q1,
+                                                         const C *__restrict__ q2, const LeafRec *__restrict__ leafs) {
+  __shared__ uint32_t red[7][kWarps];
+  __shared__ unsigned long long rd[kWarps];
+  __shared__ uint32_t rp[kWarps];
+  if (INIT) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *S.ctr = RCounters{S.nl, 0, 0, 0, 0, 0, {0, 0}};
+  } else if (S.ctr->alive == 0) {
+    return;
+  }
+  const uint32_t nlost = INIT ? S.nl : S.ctr->nlost;
+  const uint32_t ntaken = INIT ? 0u : S.ctr->taken;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t i = blockIdx.x; i < nlost + ntaken; i += gridDim.x) {
+    if (i >= nlost) {
+      if (threadIdx.x == 0) {
+        S.t.box[S.taken[i - nlost]].state = 0;
+        atomicSub(&S.ctr->alive, 1u);
+      }
+      continue;
+    }
+    const uint32_t c = INIT ? i : S.lost[i];
+    uint32_t off, cnt;
+    if (INIT) {
+      off = leafs[c].off;
+      cnt = leafs[c].cnt;
+    } else {
+      off = S.info[c].off;
+      cnt = S.info[c].cnt;
+    }
+    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0}, live = 0;
+    for (uint32_t s = off + threadIdx.x; s < off + cnt; s += kThreads) {
+      if (!INIT && S.dest[s] != kLive) continue;
+      const uint32_t x[3] = {uint32_t(q0[s]), uint32_t(q1[s]), uint32_t(q2[s])};
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = min(lo[d], x[d]);
+        hi[d] = max(hi[d], x[d]);
+      }
+      ++live;
+    }
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = __reduce_min_sync(0xffffffffu, lo[d]);
+      hi[d] = __reduce_max_sync(0xffffffffu, hi[d]);
+    }
+    live = __reduce_add_sync(0xffffffffu, live);
+    if (lane == 0) {
+      for (int d = 0; d < 3; ++d) {
+        red[2 * d][warp] = lo[d];
+        red[2 * d + 1][warp] = hi[d];
+      }
+      red[6][warp] = live;
+    }
+    __syncthreads();
+    live = 0;
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = red[2 * d][0];
+      hi[d] = red[2 * d + 1][0];
+    }
+    for (int w = 0; w < kWarps; ++w) {
+      live += red[6][w];
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = min(lo[d], red[2 * d][w]);
+        hi[d] = max(hi[d], red[2 * d + 1][w]);
+      }
+    }
+    if (live == 0) {  // emptied by the round
+      if (threadIdx.x == 0) {
+        S.t.box[c].state = 0;
+        S.info[c].live = 0;
+        S.info[c].lost = 0;
+        atomicSub(&S.ctr->alive, 1u);
+      }
+      __syncthreads();
+      continue;
+    }
+    // centre: least squared distance to the AABB centre, lowest slot on ties
+    unsigned long long bd = ~0ull;
+    uint32_t bp = 0xffffffffu;
+    const long long s0 = (long long)lo[0] + hi[0], s1 = (long long)lo[1] + hi[1], s2 = (long long)lo[2] + hi[2];
+    for (uint32_t s = off + threadIdx.x; s < off + cnt; s += kThreads) {
+      if (!INIT && S.dest[s] != kLive) continue;
+      const long long a = 2ll * q0[s] - s0, b = 2ll * q1[s] - s1, e = 2ll * q2[s] - s2;
+      const unsigned long long d2 =
+          (unsigned long long)(a * a) + (unsigned long long)(b * b) + (unsigned long long)(e * e);
+      if (d2 < bd) {  // slots rise within a thread: the first minimum is the lowest
+        bd = d2;
+        bp = s;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (od < bd || (od == bd && op < bp)) {
+        bd = od;
+        bp = op;
+      }
+    }
+    if (lane == 0) {
+      rd[warp] = bd;
+      rp[warp] = bp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kWarps; ++w)
+        if (rd[w] < bd || (rd[w] == bd && rp[w] < bp)) {
+          bd = rd[w];
+          bp = rp[w];
+        }
+      const uint32_t qc[3] = {uint32_t(q0[bp]), uint32_t(q1[bp]), uint32_t(q2[bp])};
+      RInfo I = {};
+      RBox B = {};
+      uint32_t m[3];
+      for (int d = 0; d < 3; ++d) {
+        m[d] = bits_for_range(max(qc[d] - lo[d], hi[d] - qc[d]));
+        const int32_t h = m[d] ? int32_t((1u << (m[d] - 1)) - 1u) : 0;
+        I.qref[d] = int32_t(qc[d]);
+        I.tlo[d] = lo[d];
+        I.thi[d] = hi[d];
+        B.lo[d] = int32_t(qc[d]) - h;
+        B.hi[d] = int32_t(qc[d]) + h;
+      }
+      I.m = m[0] | (m[1] << 8) | (m[2] << 16);
+      I.centre = bp;
+      I.live = live;
+      I.off = off;
+      I.cnt = cnt;
+      I.lost = 0;
+      B.key = m[0] + m[1] + m[2];
+      B.state = kAlive;
+      S.info[c] = I;
+      S.t.box[c] = B;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- sequence order ---------------------------------------------------------
+
+template <typename C>
+__global__ void k_rd_gather(State S, uint64_t n, const C *__restrict__ q0, const C *__restrict__ q1,
+                            const C *__restrict__ q2, C *o0, C *o1, C *o2, const uint32_t *__restrict__ idx,
+                            uint32_t *oidx, uint32_t *err) {
+  for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t p = S.dest[s];
+    if (p >= n) {  // every particle is in exactly one sequence
+      atomicOr(err, kErrInternal);
+      continue;
+    }
+    o0[p] = q0[s];
+    o1[p] = q1[s];
+    o2[p] = q2[s];
+    if (idx) oidx[p] = idx[s];
+  }
+}
+
+template <typename C>
+cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *num_seq, uint64_t *rounds) {
+  const Layout L = layout_of(a.n, a.num_leaves);
+  uint8_t *base = static_cast<uint8_t *>(a.scratch);
+  State S = {};
+  S.t.box = reinterpret_cast<RBox *>(base + L.box);
+  for (int l = 1; l <= L.top; ++l) S.t.node[l] = reinterpret_cast<TNode *>(base + L.node[l]);
+  for (int l = 2; l <= L.top; ++l) S.t.ticket[l] = reinterpret_cast<uint32_t *>(base + L.ticket[l]);
+  for (int l = 0; l <= L.top; ++l) S.t.count[l] = L.count[l];
+  S.t.top = L.top;
+  S.info = reinterpret_cast<RInfo *>(base + L.info);
+  S.dest = reinterpret_cast<uint32_t *>(base + L.dest);
+  S.seq_cnt = reinterpret_cast<uint32_t *>(base + L.seq_cnt);
+  S.seq_pos = reinterpret_cast<uint32_t *>(base + L.seq_pos);
+  S.taken = reinterpret_cast<uint32_t *>(base + L.taken);
+  S.lost = reinterpret_cast<uint32_t *>(base + L.lost);
+  S.ctr = reinterpret_cast<RCounters *>(base + L.ctr);
+  S.nl = uint32_t(a.num_leaves);
+  const C *q0 = static_cast<const C *>(a.codes[0]), *q1 = static_cast<const C *>(a.codes[1]),
+          *q2 = static_cast<const C *>(a.codes[2]);
+
+  cudaError_t e = cudaMemsetAsync(S.dest, 0xff, 4 * a.n, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(base + L.zero_begin, 0, L.zero_end - L.zero_begin, st);
+  if (e != cudaSuccess) return e;
+  e = launch_leaftable(a.n, a.split_level, a.leaf_size, a.leafs, a.num_leaves, st);
+  if (e != cudaSuccess) return e;
+
+  const uint32_t sms = uint32_t(device_sm_count());
+  const unsigned box_blocks = unsigned(a.num_leaves < 4ull * sms ? a.num_leaves : 4ull * sms);
+  const unsigned refit_blocks = unsigned((uint64_t(L.count[1]) + kWarps - 1) / kWarps);
+  const unsigned select_blocks = unsigned((a.num_leaves + kWarps - 1) / kWarps);
+  {
+    TraceScope ts("k_rd_rebuild", st);
+    k_rd_rebuild<C, true><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
+  }
+  {
+    TraceScope ts("k_rd_refit", st);
+    k_rd_refit<<<refit_blocks, kThreads, 0, st>>>(S);
+  }
+  uint64_t issued = 0;
+  for (;;) {
+    for (int k = 0; k < kRoundsPerCheck; ++k) {
+      {
+        TraceScope ts("k_rd_select", st);
+        k_rd_select<<<select_blocks, kThreads, 0, st>>>(S);
+      }
+      {
+        TraceScope ts("k_rd_count", st);
+        k_rd_take<C, false><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2);
+      }
+      {
+        TraceScope ts("k_rd_scan", st);
+        k_rd_scan<<<1, 1024, 0, st>>>(S, a.seqs);
+      }
+      {
+        TraceScope ts("k_rd_place", st);
+        k_rd_take<C, true><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2);
+      }
+      {
+        TraceScope ts("k_rd_rebuild", st);
+        k_rd_rebuild<C, false><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
+      }
+      {
+        TraceScope ts("k_rd_refit", st);
+        k_rd_refit<<<refit_blocks, kThreads, 0, st>>>(S);
+      }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    issued += kRoundsPerCheck;
+    RCounters h;
+    e = cudaMemcpyAsync(&h, S.ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (h.alive == 0) {
+      *num_seq = h.nseq;
+      *rounds = h.rounds;
+      break;
+    }
+    // every round takes at least the alive box of least key
+    if (issued > a.num_leaves + kRoundsPerCheck) return cudaErrorUnknown;
+  }
+  {
+    TraceScope ts("k_rd_gather", st);
+    const uint64_t blocks = (a.n + 255) / 256;
+    const unsigned grid = unsigned(blocks < 16ull * sms ? blocks : 16ull * sms);
+    k_rd_gather<C><<<grid, 256, 0, st>>>(S, a.n, q0, q1, q2, static_cast<C *>(a.out_codes[0]),
+                                        static_cast<C *>(a.out_codes[1]), static_cast<C *>(a.out_codes[2]), a.idx,
+                                        a.out_idx, a.err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+uint64_t reduce_scratch_bytes(uint64_t n, uint64_t num_leaves) { return layout_of(n, num_leaves).total; }
+
+cudaError_t launch_reduce(const ReduceLaunch &a, cudaStream_t st, uint64_t *num_seq, uint64_t *rounds) {
+  *num_seq = 0;
+  *rounds = 0;
+  if (a.n == 0 || a.num_leaves == 0) return cudaSuccess;
+  if (a.code_bytes == 2) return reduce_dispatch<uint16_t>(a, st, num_seq, rounds);
+  return reduce_dispatch<uint32_t>(a, st, num_seq, rounds);
+}
+
+}  // namespace pcx

@@ -73,6 +73,8 @@ struct Plan {
   uint64_t off_zero = 0, zero_bytes = 0;  // zeroed at every call:
   uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_err = 0, off_total = 0;
   uint64_t off_groups = 0, off_slices = 0;
+  uint64_t off_reduce = 0, off_seqrec = 0;  // bit-box reduction: its scratch and the sequence records
+  bool reduce = false;
   bool tune = false;  // leaf size chosen by descending from r_hi while the stream shrinks (sized for r)
   uint32_t r_hi = 0;
   int tune_first = 0, tune_last = 0;  // candidate depths
@@ -120,7 +122,8 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   uint32_t r = PC_DEFAULT_LEAF_SIZE;
   p.tune = false;
   if (cfg) {
-    if (cfg->flags & ~PC_FLAG_AUTOTUNE_LEAF) return PC_ERR_ARG;
+    if (cfg->flags & ~(PC_FLAG_AUTOTUNE_LEAF | PC_FLAG_BOX_REDUCTION)) return PC_ERR_ARG;
+    p.reduce = (cfg->flags & PC_FLAG_BOX_REDUCTION) != 0;
     if (cfg->leaf_size) r = cfg->leaf_size;
     if (cfg->flags & PC_FLAG_AUTOTUNE_LEAF) {
       // candidates: depths d with ceil(n / 2^d) in [min(PC_AUTOTUNE_MIN_LEAF, max), max]
@@ -183,6 +186,12 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
     }
   p.off_groups = o;
   o = align_up(o + group_bytes);
+  if (p.reduce) {
+    p.off_seqrec = o;
+    o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafRec));
+    p.off_reduce = o;
+    o = align_up(o + reduce_scratch_bytes(n, p.num_leaves));
+  }
   // zeroed region
   p.off_zero = o;
   uint64_t hist_bins = 0, tiles = 0;
@@ -484,9 +493,54 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       trace_flush();
       return PC_OK;
     }
+    // Sec. 4.1 bit-box reduction, then the packing of its sequences: codes and
+    // indices go to the spare arrangement in sequence order
+    auto reduce_launch = [&](void *const *codes, const uint32_t *idxs, void *const *spare, uint32_t *spare_idx,
+                             int split_level, uint32_t r, uint64_t num_leaves) -> int {
+      ReduceLaunch rl = {};
+      rl.n = n;
+      rl.code_bytes = cb;
+      rl.split_level = split_level;
+      rl.leaf_size = r;
+      rl.num_leaves = num_leaves;
+      for (int d = 0; d < 3; ++d) {
+        rl.codes[d] = codes[d];
+        rl.out_codes[d] = spare[d];
+      }
+      rl.idx = idxs;
+      rl.out_idx = idxs ? spare_idx : nullptr;
+      rl.leafs = reinterpret_cast<LeafRec *>(ws + p.off_leafrec);
+      rl.seqs = reinterpret_cast<LeafRec *>(ws + p.off_seqrec);
+      rl.scratch = ws + p.off_reduce;
+      rl.err = err;
+      uint64_t num_seq = 0, rounds = 0;
+      PC_TRY(launch_reduce(rl, st, &num_seq, &rounds));
+      LeafLaunch lf = {};
+      lf.n = n;
+      lf.split_level = split_level;
+      lf.code_bytes = cb;
+      lf.leaf_size = r;
+      lf.num_leaves = num_seq;
+      for (int d = 0; d < 3; ++d) lf.codes[d] = spare[d];
+      lf.idx = rl.out_idx;
+      lf.out = static_cast<uint8_t *>(out);
+      lf.perm = perm;
+      lf.recs = rl.seqs;
+      lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
+      lf.slice_tot = reinterpret_cast<uint64_t *>(ws + p.off_slices);
+      lf.recs_ready = true;
+      PC_TRY(launch_leaves(lf, st));
+      hl.num_leaves = num_seq;
+      return PC_OK;
+    };
     // a4-a5: bit boxes, payload offsets, packing
     if (!p.tune) {
-      PC_TRY(leaf_launch(src, isrc, levels - 1, p.r, p.num_leaves, false));
+      if (p.reduce) {
+        rc = reduce_launch(src, isrc, dst, idst, levels - 1, p.r, p.num_leaves);
+        if (rc) return rc;
+      } else {
+        PC_TRY(leaf_launch(src, isrc, levels - 1, p.r, p.num_leaves, false));
+      }
     } else {
       // the loop stopped at the first depth whose stream is not smaller, or built
       // every level: then the smallest candidate (depth `levels`, in src) is compared too
@@ -506,7 +560,13 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       const uint64_t r = depth ? (n + (1ull << depth) - 1) >> depth : n;
       hl.leaf_size = uint32_t(r);
       hl.num_leaves = 1ull << depth;
-      PC_TRY(leaf_launch(codes, idxs, depth - 1, uint32_t(r), 1ull << depth, false));
+      if (p.reduce) {
+        rc = reduce_launch(codes, idxs, deepest ? dst : src, deepest ? idst : isrc, depth - 1, uint32_t(r),
+                           1ull << depth);
+        if (rc) return rc;
+      } else {
+        PC_TRY(leaf_launch(codes, idxs, depth - 1, uint32_t(r), 1ull << depth, false));
+      }
     }
     hl.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
   }
