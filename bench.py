@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch-256", "serve-2000", "leaf-sweep"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--leaf-size", type=int, default=4096)
+    ap.add_argument("--reduce", action="store_true",
+                    help="compress with the bit-box reduction (Sec. 4.1, Alg. 1) in place of plain leaves")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -194,9 +196,13 @@ def measured_traffic(kernel: str, workload: str, n: int):
         return None
 
 
-def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False):
-    """Bytes a launch must move at minimum (per-kernel figures, stated in the design notes)."""
+def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False, launches=1):
+    """Bytes a launch must move at minimum (per-kernel figures, stated in the design notes).
+    The reduction's take kernel runs once per round: over all rounds it must read
+    every particle's codes once and write its sequence and rank once."""
     idx = 4 if with_idx else 0
+    if kernel == "k_rd_take":
+        return (3 * cb + 8) * n / max(launches, 1)
     return {
         "k_range": 3 * esz * n,
         "k_quantize": 3 * esz * n + 3 * cb * n + idx * n,
@@ -210,29 +216,35 @@ def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False):
     }.get(kernel)
 
 
-def oracle_round_trip(pos, mode, eb, leaf_size):
+def oracle_round_trip(pos, mode, eb, leaf_size, reduce=False):
     import oracle
 
     m = oracle.REL if mode == "rel" else oracle.ABS
-    stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False)
+    if reduce:
+        stream, _, _ = oracle.compress_reduced(pos, m, eb, leaf_size=leaf_size, want_perm=False)
+    else:
+        stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False)
     oracle.decompress(stream)
     return len(stream)
 
 
-def oracle_round_trip_parallel(pos, mode, eb, leaf_size):
+def oracle_round_trip_parallel(pos, mode, eb, leaf_size, reduce=False):
     import oracle
 
     m = oracle.REL if mode == "rel" else oracle.ABS
-    stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=True)
+    if reduce:
+        stream, _, _ = oracle.compress_reduced(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=True)
+    else:
+        stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=True)
     oracle.decompress(stream, parallel=True)
     return len(stream)
 
 
-def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE):
+def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False):
     gen, n, dtype, mode, eb = spec
     pos = generate(gen, n_sample, dtype, seed=0)
     t0 = time.perf_counter()
-    oracle_round_trip(pos, mode, eb, leaf_size)
+    oracle_round_trip(pos, mode, eb, leaf_size, reduce)
     dt = time.perf_counter() - t0
     out = {"value": round(pos.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
            "sample": f"{n_sample} particles of the {gen} generator ({dtype}, {mode} eb {eb}), one compress + "
@@ -241,15 +253,17 @@ def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE):
     import oracle
 
     oracle.build(parallel=True)
-    big = generate(gen, 4 * n_sample, dtype, seed=0)
-    oracle_round_trip_parallel(big[: 1 << 16], mode, eb, leaf_size)  # thread pool start-up
+    big = generate(gen, (1 if reduce else 4) * n_sample, dtype, seed=0)
+    oracle_round_trip_parallel(big[: 1 << 16], mode, eb, leaf_size, reduce)  # thread pool start-up
     t0 = time.perf_counter()
-    oracle_round_trip_parallel(big, mode, eb, leaf_size)
+    oracle_round_trip_parallel(big, mode, eb, leaf_size, reduce)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out["parallel"] = {"value": round(big.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": cores,
                        "kind": "oracle, OpenMP build of the same source",
-                       "sample": f"{4 * n_sample} particles, one compress + decompress in {dt:.2f} s"}
+                       "sample": f"{big.shape[0]} particles, one compress + decompress in {dt:.2f} s"}
+    if reduce:
+        out["sample"] += " (bit-box reduction)"
     return out
 
 
@@ -264,11 +278,11 @@ def run_reference(args, spec):
     oracle.build()
     samples = [generate(gen, REF_SAMPLE, dtype, seed=s) for s in range(2)]
     for i in range(args.warmup):
-        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size)
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce)
     times = []
     for i in range(args.steps):
         t0 = time.perf_counter()
-        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size)
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     units = samples[0].nbytes * args.steps
@@ -278,6 +292,7 @@ def run_reference(args, spec):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": args.workload, "sample_particles_per_step": REF_SAMPLE, "leaf_size": args.leaf_size,
+                   "box_reduction": bool(args.reduce),
                    "note": "the oracle (plain single-threaded C, double precision) on host cores"},
         "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{REF_SAMPLE} particles of the {gen} generator per step"},
@@ -307,7 +322,8 @@ def run_ours(args, spec):
     emode = pc.PC_EB_REL if mode == "rel" else pc.PC_EB_ABS
     esz = 4 if dtype == "f32" else 8
     pos = torch.from_numpy(pos_h).to(dev)
-    comp = pc.Compressor(n, pdt, leaf_size=args.leaf_size, device=dev)
+    cfg = pc.config(args.leaf_size, reduce=args.reduce)
+    comp = pc.Compressor(n, pdt, leaf_size=cfg, device=dev)
     dec = torch.empty_like(pos)
 
     def step():
@@ -372,7 +388,7 @@ def run_ours(args, spec):
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(table.items(), key=lambda kv: -kv[1][1])}
     top = max(table, key=lambda k: table[k][1])
     per_launch_ms = table[top][1] / table[top][0]
-    alg = algorithmic_bytes(top, n, esz, cb, size)
+    alg = algorithmic_bytes(top, n, esz, cb, size, launches=table[top][0])
     peak, peak_kind = peaks()
     roofline = None
     if alg is not None:
@@ -386,10 +402,10 @@ def run_ours(args, spec):
     step_alg = 2 * (nbytes + size)
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
-        e2e = measure_e2e(pc, pos_h, pdt, emode, eb, args, world)
+        e2e = measure_e2e(pc, pos_h, pdt, emode, eb, args, world, cfg)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(spec, args.leaf_size)
+        cpu = cpu_baseline(spec, args.leaf_size, CPU_SAMPLE // 4 if args.reduce else CPU_SAMPLE, args.reduce)
 
     if rank == 0:
         line = {
@@ -397,7 +413,8 @@ def run_ours(args, spec):
             "warmup": max(args.warmup, 3), "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "generator": gen, "particles": n, "eb_mode": mode, "eb": eb,
-                       "leaf_size": args.leaf_size, "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "leaf_size": args.leaf_size, "box_reduction": bool(args.reduce),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)", "code_bytes": cb},
             "compress_gbs": round(whole_job_gbs(world, nbytes, args.steps, comp_ms), 3),
             "decompress_gbs": round(whole_job_gbs(world, nbytes, args.steps, dec_ms), 3),
@@ -413,27 +430,27 @@ def run_ours(args, spec):
         dist.destroy_process_group()
 
 
-def measure_e2e(pc, pos_h, pdt, emode, eb, args, world):
+def measure_e2e(pc, pos_h, pdt, emode, eb, args, world, cfg):
     """Round trips through the host-buffer entry points, copies inside the timing."""
     import torch
 
     n = pos_h.shape[0]
     dev = torch.cuda.current_device()
     hp = torch.from_numpy(pos_h).pin_memory()
-    bound = pc.pc_compress_bound(n, pdt, args.leaf_size)
+    bound = pc.pc_compress_bound(n, pdt, cfg)
     hstream = torch.empty(bound, dtype=torch.uint8).pin_memory()
     hdec = torch.empty_like(hp).pin_memory()
-    ws_c = torch.empty(pc.pc_compress_host_workspace_size(n, pdt, args.leaf_size), dtype=torch.uint8, device=dev)
+    ws_c = torch.empty(pc.pc_compress_host_workspace_size(n, pdt, cfg), dtype=torch.uint8, device=dev)
     ws_d = torch.empty(pc.pc_decompress_host_workspace_size(n, pdt, bound), dtype=torch.uint8, device=dev)
     for _ in range(3):  # warm-up: the first transfers from freshly pinned pages run slower
-        size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, args.leaf_size)
+        size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, cfg)
         pc.pc_decompress_host(hstream, size, hdec, ws_d)
     times = []
     for _ in range(args.e2e_steps):
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, args.leaf_size)
+        size = pc.pc_compress_host(hp, emode, eb, hstream, ws_c, cfg)
         pc.pc_decompress_host(hstream, size, hdec, ws_d)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)

@@ -3,8 +3,9 @@
 //
 // Input: the codes after the last k-d level, stored leaf after leaf ("slots").
 // Every leaf starts as a box: the bit box of its particles that are not yet in
-// a sequence ("live").  dest[slot] is the output position of a particle once a
-// sequence holds it (kLive before).
+// a sequence ("live", one bit per slot).  Once a sequence holds a particle,
+// owner[slot] is the box whose sequence it is and rank[slot] its place in it;
+// the output position is the sequence's first position plus the rank.
 //
 // Intersection query: a 32-ary tree over the box indices.  Level 0 are the
 // boxes; node j of level k >= 1 holds the union of the alive bit boxes below
@@ -18,21 +19,20 @@
 //   select   a warp per alive box a: a is taken when no other alive box with a
 //            smaller (key, index) meets its bit box.  Taken boxes are pairwise
 //            disjoint, so no particle lies in two of them.
-//   count    a block per taken box: its live particles, plus, for every alive
-//            box c that is not taken and meets it, the live particles of c
-//            inside its bit box.
+//   take     a block per taken box: ranks in its sequence for its centre, its
+//            other live particles in slot order, then, for every alive box c
+//            that is not taken and meets it, the live particles of c inside
+//            its bit box, by c and slot (counted first, then ranked); boxes
+//            that lost particles are listed.
 //   scan     one block: each taken box's sequence index and first output
 //            position, in box order, after the sequences of earlier rounds.
-//   place    a block per taken box: output positions of its centre, its other
-//            live particles in slot order, then the particles it takes, by
-//            source box and slot; boxes that lost particles are listed.
 //   rebuild  a block per listed box: the bit box of what it keeps (the leaf
 //            rules: AABB, the particle closest to its centre, Eq. 2); taken and
 //            emptied boxes die.
 //   refit    the tree over the new boxes.
 // The host reads the alive count back every few rounds; rounds issued after
 // the last box died return at once.  A final pass moves codes and input
-// indices into sequence order for the packing kernels.
+// indices to their output positions for the packing kernels.
 #include <climits>
 #include <cstdint>
 
@@ -42,12 +42,11 @@ namespace pcx {
 namespace {
 
 constexpr int kMaxLevels = 8;  // 32^7 > 2^32 boxes
-constexpr uint32_t kLive = 0xffffffffu;
 constexpr uint32_t kAlive = 1u, kTaken = 2u;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kListCap = 512;  // boxes met by a taken box, per batch
-constexpr int kRoundsPerCheck = 4;
+constexpr int kRoundsPerCheck = 8;
 
 struct RBox {            // what the tree tests, 32 bytes
   int32_t lo[3], hi[3];  // bit box: q_ref -/+ (2^(m-1) - 1) per axis (q_ref where m = 0)
@@ -85,17 +84,20 @@ struct Tree {
 struct State {
   Tree t;
   RInfo *info;
-  uint32_t *dest;     // [n]
+  uint32_t *live;     // [n / 32 + 1] bit s: slot s is live
+  uint32_t *dest;     // [n] the box whose sequence holds the particle
+  uint32_t *rank;     // [n] place in that sequence
   uint32_t *seq_cnt;  // [boxes] particles of a taken box's sequence, 0 otherwise
   uint32_t *seq_pos;  // [boxes] first output position of a taken box's sequence
   uint32_t *taken;    // [boxes] boxes taken in the round, any order
   uint32_t *lost;     // [boxes] boxes that lost particles in the round, any order
+  uint32_t *tbits;    // [boxes / 32] bitmap of the boxes taken in the round
   RCounters *ctr;
   uint32_t nl;
 };
 
 struct Layout {
-  uint64_t dest, box, info, node[kMaxLevels], ticket[kMaxLevels], seq_cnt, seq_pos, taken, lost, ctr;
+  uint64_t live, dest, rank, box, info, node[kMaxLevels], ticket[kMaxLevels], seq_cnt, seq_pos, taken, lost, tbits, ctr;
   uint64_t zero_begin, zero_end, total;
   uint32_t count[kMaxLevels];
   int top;
@@ -113,7 +115,11 @@ Layout layout_of(uint64_t n, uint64_t nl) {
   } while (L.count[k] > 1);
   L.top = k;
   uint64_t o = 0;
+  L.live = o;
+  o = align256(o + 4 * (n / 32 + 2));
   L.dest = o;
+  o = align256(o + 4 * n + 16);  // whole groups of four slots are read
+  L.rank = o;
   o = align256(o + 4 * n);
   L.box = o;
   o = align256(o + sizeof(RBox) * nl);
@@ -136,6 +142,8 @@ Layout layout_of(uint64_t n, uint64_t nl) {
   }
   L.seq_cnt = o;
   o = align256(o + 4 * nl);
+  L.tbits = o;
+  o = align256(o + 4 * ((nl + 31) / 32));
   L.ctr = o;
   o = align256(o + sizeof(RCounters));
   L.zero_end = o;
@@ -323,23 +331,122 @@ __global__ void __launch_bounds__(kThreads) k_rd_select(State S) {
   const bool blocked = descent_run(d, S.t, nok, bok, [](uint32_t, uint32_t) { return true; });
   if (!blocked && (threadIdx.x & 31) == 0) {
     atomicOr(&S.t.box[a].state, kTaken);
+    atomicOr(S.tbits + (a >> 5), 1u << (a & 31));
     S.taken[atomicAdd(&S.ctr->taken, 1u)] = a;
   }
 }
 
 // ---- count and place ------------------------------------------------------
 
+constexpr int kTakeThreads = 1024;
+constexpr int kTakeWarps = kTakeThreads / 32;
+
 template <typename C>
-__device__ __forceinline__ bool inside(const Box6 &b, const C *q0, const C *q1, const C *q2, uint32_t s) {
-  const int32_t x = int32_t(q0[s]), y = int32_t(q1[s]), z = int32_t(q2[s]);
-  return b.lo[0] <= x && x <= b.hi[0] && b.lo[1] <= y && y <= b.hi[1] && b.lo[2] <= z && z <= b.hi[2];
+struct Codes4;  // the codes of the aligned group of four slots g, as loaded (two or four words)
+template <>
+struct Codes4<uint16_t> {
+  using Raw = uint2;
+  static __device__ __forceinline__ Raw load(const uint16_t *q, uint32_t g) {
+    return __ldg(reinterpret_cast<const uint2 *>(q) + g);
+  }
+  static __device__ __forceinline__ uint32_t at(const Raw &w, int j) {
+    const uint32_t x = j < 2 ? w.x : w.y;
+    return (j & 1) ? (x >> 16) : (x & 0xffffu);
+  }
+};
+template <>
+struct Codes4<uint32_t> {
+  using Raw = uint4;
+  static __device__ __forceinline__ Raw load(const uint32_t *q, uint32_t g) {
+    return __ldg(reinterpret_cast<const uint4 *>(q) + g);
+  }
+  static __device__ __forceinline__ uint32_t at(const Raw &w, int j) {
+    return j == 0 ? w.x : (j == 1 ? w.y : (j == 2 ? w.z : w.w));
+  }
+};
+
+// One warp walks the live slots of [off, end) in aligned groups of four (lane
+// i takes every 32nd group), a few groups per lane at a time: all their loads
+// are issued first (indices clamped into the range, so no load waits on a
+// branch), then the slots are tested.  want(s, x, y, z) picks live slot s (x,
+// y, z its codes when CODES).  Returns how many were picked; with PLACE they
+// also stop being live and get dest[s] = tag and rank[s] = pos, pos + 1, ...
+// in slot order.
+template <typename C, bool CODES, bool PLACE, class Want>
+__device__ __forceinline__ uint32_t warp_walk(const State &S, uint32_t tag, const C *q0, const C *q1, const C *q2,
+                                              uint32_t off, uint32_t end, uint32_t pos, Want want) {
+  using Raw = typename Codes4<C>::Raw;
+  constexpr int kUnroll = sizeof(C) == 2 ? 4 : 2;  // the same bytes in flight for both code widths
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t g0 = off >> 2, g1 = (end + 3) >> 2;
+  uint32_t k = 0;
+  for (uint32_t gb = g0; gb < g1; gb += 32 * kUnroll) {
+    uint32_t lw[kUnroll];
+    Raw cx[kUnroll], cy[kUnroll], cz[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t g = min(gb + uint32_t(u) * 32 + lane, g1 - 1);
+      lw[u] = __ldcg(S.live + (g >> 3));
+      if (CODES) {
+        cx[u] = Codes4<C>::load(q0, g);
+        cy[u] = Codes4<C>::load(q1, g);
+        cz[u] = Codes4<C>::load(q2, g);
+      }
+    }
+    uint32_t bits[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t g = gb + uint32_t(u) * 32 + lane;
+      const uint32_t lb = g < g1 ? (lw[u] >> (4 * (g & 7))) & 0xfu : 0u;
+      bits[u] = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t s = 4 * g + uint32_t(j);
+        if (!((lb >> j) & 1u) || s < off || s >= end) continue;
+        uint32_t x = 0, y = 0, z = 0;
+        if (CODES) {
+          x = Codes4<C>::at(cx[u], j);
+          y = Codes4<C>::at(cy[u], j);
+          z = Codes4<C>::at(cz[u], j);
+        }
+        if (want(s, x, y, z)) bits[u] |= 1u << j;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t c = __popc(bits[u]);
+      if (!PLACE) {
+        k += c;
+        continue;
+      }
+      uint32_t incl = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= uint32_t(o)) incl += y;
+      }
+      uint32_t p = pos + k + incl - c;
+      const uint32_t g = gb + uint32_t(u) * 32 + lane;
+      if (bits[u]) atomicAnd(S.live + (g >> 3), ~(bits[u] << (4 * (g & 7))));
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if ((bits[u] >> j) & 1u) {
+          S.dest[4 * g + uint32_t(j)] = tag;
+          S.rank[4 * g + uint32_t(j)] = p++;
+        }
+      k += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (!PLACE) k = __reduce_add_sync(0xffffffffu, k);
+  return k;
 }
 
-// Live particles of box c inside bit box b, by one warp; with PLACE they get
-// the output positions pos, pos + 1, ... in slot order.  Returns the count.
+// Live particles of part t of `parts` of box c's slots inside bit box b, by
+// one warp (parts split the slots in whole groups of four, in slot order); with
+// PLACE they go to box `tag`'s sequence with ranks pos, pos + 1, ... in slot
+// order.  Returns the count.
 template <typename C, bool PLACE>
-__device__ uint32_t warp_take(const State &S, const C *q0, const C *q1, const C *q2, uint32_t c, const Box6 &b,
-                              uint32_t pos) {
+__device__ uint32_t warp_take(const State &S, const C *q0, const C *q1, const C *q2, uint32_t c, uint32_t t,
+                              uint32_t parts, const Box6 &b, uint32_t tag, uint32_t pos) {
   const RInfo I = S.info[c];
   bool meet = true, all = true;
   for (int d = 0; d < 3; ++d) {
@@ -348,35 +455,42 @@ __device__ uint32_t warp_take(const State &S, const C *q0, const C *q1, const C 
     if (lo < b.lo[d] || hi > b.hi[d]) all = false;
   }
   if (!meet) return 0;
-  const uint32_t end = I.off + I.cnt;
-  if (!PLACE) {
-    if (all) return I.live;
-    uint32_t k = 0;
-    for (uint32_t s = I.off + (threadIdx.x & 31); s < end; s += 32)
-      if (S.dest[s] == kLive && inside(b, q0, q1, q2, s)) ++k;
-    return __reduce_add_sync(0xffffffffu, k);
+  const uint32_t g0 = I.off >> 2, ng = ((I.off + I.cnt + 3) >> 2) - g0;  // ng * parts < 2^32
+  const uint32_t off = max(I.off, 4 * (g0 + ng * t / parts));
+  const uint32_t end = min(I.off + I.cnt, 4 * (g0 + ng * (t + 1) / parts));
+  if (off >= end) return 0;
+  if (all) {  // every live particle of c is inside
+    if (!PLACE && parts == 1) return I.live;
+    return warp_walk<C, false, PLACE>(S, tag, q0, q1, q2, off, end, pos,
+                                      [](uint32_t, uint32_t, uint32_t, uint32_t) { return true; });
   }
-  uint32_t k = 0;
-  for (uint32_t s0 = I.off; s0 < end; s0 += 32) {
-    const uint32_t s = s0 + (threadIdx.x & 31);
-    bool in = false;
-    if (s < end && S.dest[s] == kLive) in = all || inside(b, q0, q1, q2, s);
-    const uint32_t bal = __ballot_sync(0xffffffffu, in);
-    if (in) S.dest[s] = pos + k + __popc(bal & lanemask_lt());
-    k += __popc(bal);
-  }
-  return k;
+  return warp_walk<C, true, PLACE>(S, tag, q0, q1, q2, off, end, pos,
+                                   [&](uint32_t, uint32_t x, uint32_t y, uint32_t z) {
+                                     return b.lo[0] <= int32_t(x) && int32_t(x) <= b.hi[0] &&
+                                            b.lo[1] <= int32_t(y) && int32_t(y) <= b.hi[1] &&
+                                            b.lo[2] <= int32_t(z) && int32_t(z) <= b.hi[2];
+                                   });
 }
 
-// A block per taken box.  PLACE = false: the particles of its sequence into
-// seq_cnt; PLACE = true: their output positions from seq_pos on.
-template <typename C, bool PLACE>
-__global__ void __launch_bounds__(kThreads) k_rd_take(State S, const C *__restrict__ q0, const C *__restrict__ q1,
-                                                      const C *__restrict__ q2) {
-  __shared__ uint32_t list[kListCap];
+// Barrier of the first `nthreads` threads of the block (whole warps), apart
+// from __syncthreads: the search warps meet here while the last warp ranks
+// the taken box's own particles.
+__device__ __forceinline__ void search_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
+
+// A block per taken box: the ranks of its sequence, its length into seq_cnt.
+// The last warp ranks the box's own particles while the others search the
+// tree breadth first (one level per step, all nodes of a level at once; a
+// level of more than kListCap boxes falls back to a depth-first search in
+// batches by warp 0).  Then every warp counts, and after a scan ranks, pieces
+// of the boxes met.
+template <typename C>
+__global__ void __launch_bounds__(kTakeThreads) k_rd_take(State S, const C *__restrict__ q0,
+                                                          const C *__restrict__ q1, const C *__restrict__ q2) {
+  constexpr int kSearchWarps = kTakeWarps - 1;
+  __shared__ uint32_t fr[2][kListCap];  // search frontiers; the boxes met end in one of them
+  __shared__ uint32_t fmask[kListCap];
   __shared__ uint32_t lpos[kListCap];
-  __shared__ uint32_t s_n, s_done, s_sum;
-  __shared__ uint32_t s_w[kWarps];
+  __shared__ uint32_t s_nf, s_over, s_cur, s_n, s_done, s_sum;
   if (S.ctr->alive == 0) return;
   const uint32_t ntaken = S.ctr->taken;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -385,107 +499,151 @@ __global__ void __launch_bounds__(kThreads) k_rd_take(State S, const C *__restri
     const RBox A = S.t.box[a];
     const Box6 bx = box6(A);
     const RInfo IA = S.info[a];
-    uint32_t pos = 0;
-    if (PLACE) {
-      // the centre, then the box's other live particles in slot order
-      pos = S.seq_pos[a];
-      const uint32_t per = ((IA.cnt + kWarps - 1) / kWarps + 31) / 32 * 32;
-      const uint32_t w0 = IA.off + min(IA.cnt, uint32_t(warp) * per);
-      const uint32_t w1 = IA.off + min(IA.cnt, uint32_t(warp + 1) * per);
-      uint32_t k = 0;
-      for (uint32_t s = w0 + lane; s < w1; s += 32) k += (S.dest[s] == kLive && s != IA.centre) ? 1u : 0u;
-      k = __reduce_add_sync(0xffffffffu, k);
-      if (lane == 0) s_w[warp] = k;
-      __syncthreads();
-      uint32_t before = 0;
-      for (int w = 0; w < warp; ++w) before += s_w[w];
-      uint32_t r = pos + 1 + before;
-      for (uint32_t s0 = w0; s0 < w1; s0 += 32) {
-        const uint32_t s = s0 + lane;
-        const bool in = s < w1 && S.dest[s] == kLive && s != IA.centre;
-        const uint32_t bal = __ballot_sync(0xffffffffu, in);
-        if (in) S.dest[s] = r + __popc(bal & lanemask_lt());
-        r += __popc(bal);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) S.dest[IA.centre] = pos;
-      pos += IA.live;
-    }
-    uint32_t total = IA.live;
-    // the alive boxes that are not taken and meet this one, in index order, in batches
     auto nok = [&](const int4 &p, const int4 &q) { return meets(bx, p, q); };
-    auto bok = [&](uint32_t c, const int4 &p, const int4 &q) {
+    auto bok = [&](uint32_t, const int4 &p, const int4 &q) {
       return (uint32_t(q.w) & (kAlive | kTaken)) == kAlive && meets(bx, p, q);
     };
-    Descent d;
-    if (warp == 0) descent_start(d, S.t, nok, bok);
-    for (;;) {
+    if (warp == kTakeWarps - 1) {  // the centre, then the box's other live particles in slot order
+      const uint32_t centre = IA.centre;
+      warp_walk<C, false, true>(S, a, q0, q1, q2, IA.off, IA.off + IA.cnt, 1,
+                                [=](uint32_t s, uint32_t, uint32_t, uint32_t) { return s != centre; });
+      if (lane == 0) {
+        atomicAnd(S.live + (centre >> 5), ~(1u << (centre & 31)));
+        S.dest[centre] = a;
+        S.rank[centre] = 0;
+      }
+    } else {
+      const Tree &t = S.t;
+      int cur = 0;
       if (warp == 0) {
-        uint32_t nlist = 0;
-        descent_run(d, S.t, nok, bok, [&](uint32_t first, uint32_t m) {
-          if ((m >> lane) & 1u) list[nlist + __popc(m & lanemask_lt())] = first + lane;
-          nlist += __popc(m);
-          return nlist + 32 > kListCap;
-        });
+        const uint32_t m = test_children(t, t.top - 1, 0, nok, bok);
+        if ((m >> lane) & 1u) fr[0][__popc(m & lanemask_lt())] = lane;
         if (lane == 0) {
-          s_n = nlist;
-          s_done = d.done ? 1u : 0u;
+          s_nf = __popc(m);
+          s_over = 0;
         }
       }
-      __syncthreads();
-      const uint32_t nlist = s_n;
-      const bool done = s_done != 0;
-      for (uint32_t j = warp; j < nlist; j += kWarps) {
-        const uint32_t k = warp_take<C, false>(S, q0, q1, q2, list[j], bx, 0);
-        if (lane == 0) lpos[j] = k;
+      search_sync(kSearchWarps * 32);
+      for (int l = t.top - 1; l >= 1; --l) {  // fr[cur] holds the nodes of level l to expand
+        const uint32_t nf = s_nf;
+        for (uint32_t j = warp; j < nf; j += kSearchWarps) {
+          const uint32_t m = test_children(t, l - 1, fr[cur][j] * 32, nok, bok);
+          if (lane == 0) fmask[j] = m;
+        }
+        search_sync(kSearchWarps * 32);
+        if (warp == 0) {
+          uint32_t run = 0;
+          for (uint32_t j0 = 0; j0 < nf; j0 += 32) {
+            const uint32_t x = j0 + lane < nf ? __popc(fmask[j0 + lane]) : 0u;
+            uint32_t incl = x;
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= o) incl += y;
+            }
+            if (j0 + lane < nf) lpos[j0 + lane] = run + incl - x;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+          }
+          if (lane == 0) {
+            s_nf = run;
+            s_over = run > kListCap ? 1u : 0u;
+          }
+        }
+        search_sync(kSearchWarps * 32);
+        if (s_over) break;
+        for (uint32_t j = warp; j < nf; j += kSearchWarps) {
+          const uint32_t m = fmask[j];
+          if ((m >> lane) & 1u) fr[cur ^ 1][lpos[j] + __popc(m & lanemask_lt())] = fr[cur][j] * 32 + lane;
+        }
+        search_sync(kSearchWarps * 32);
+        cur ^= 1;
+      }
+      if (threadIdx.x == 0) s_cur = uint32_t(cur);
+    }
+    __syncthreads();
+    uint32_t pos = IA.live;
+    // counts, then ranks, of `parts` pieces of each of the nlist boxes in list
+    auto batch = [&](const uint32_t *list, uint32_t nlist) {
+      const uint32_t parts = nlist ? max(1u, min(16u, uint32_t(kTakeWarps) / nlist)) : 1u;
+      const uint32_t items = nlist * parts;
+      for (uint32_t it = warp; it < items; it += kTakeWarps) {
+        const uint32_t k = warp_take<C, false>(S, q0, q1, q2, list[it / parts], it % parts, parts, bx, a, 0);
+        if (lane == 0) lpos[it] = k;
       }
       __syncthreads();
-      if (warp == 0) {  // exclusive scan of the counts (PLACE) and their sum
+      if (warp == 0) {  // exclusive scan of the counts and their sum
         uint32_t run = 0;
-        for (uint32_t j0 = 0; j0 < nlist; j0 += 32) {
-          const uint32_t x = j0 + lane < nlist ? lpos[j0 + lane] : 0u;
+        for (uint32_t j0 = 0; j0 < items; j0 += 32) {
+          const uint32_t x = j0 + lane < items ? lpos[j0 + lane] : 0u;
           uint32_t incl = x;
           for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
           }
-          if (PLACE && j0 + lane < nlist) lpos[j0 + lane] = run + incl - x;
+          if (j0 + lane < items) lpos[j0 + lane] = run + incl - x;
           run += __shfl_sync(0xffffffffu, incl, 31);
         }
         if (lane == 0) s_sum = run;
       }
       __syncthreads();
-      if (PLACE) {
-        for (uint32_t j = warp; j < nlist; j += kWarps) {
-          const uint32_t c = list[j];
-          const uint32_t k = warp_take<C, true>(S, q0, q1, q2, c, bx, pos + lpos[j]);
-          if (k && lane == 0 && atomicExch(&S.info[c].lost, 1u) == 0u) S.lost[atomicAdd(&S.ctr->nlost, 1u)] = c;
-        }
+      for (uint32_t it = warp; it < items; it += kTakeWarps) {
+        const uint32_t c = list[it / parts];
+        const uint32_t k = warp_take<C, true>(S, q0, q1, q2, c, it % parts, parts, bx, a, pos + lpos[it]);
+        if (k && lane == 0 && atomicExch(&S.info[c].lost, 1u) == 0u) S.lost[atomicAdd(&S.ctr->nlost, 1u)] = c;
       }
       pos += s_sum;
-      total += s_sum;
       __syncthreads();  // the batch's shared state is reused
-      if (done) break;
+    };
+    if (!s_over) {
+      batch(fr[s_cur], s_nf);
+    } else {
+      // more boxes than a batch holds: depth first, in batches, by warp 0
+      Descent d;
+      if (warp == 0) descent_start(d, S.t, nok, bok);
+      for (;;) {
+        if (warp == 0) {
+          uint32_t nlist = 0;
+          descent_run(d, S.t, nok, bok, [&](uint32_t first, uint32_t m) {
+            if ((m >> lane) & 1u) fr[0][nlist + __popc(m & lanemask_lt())] = first + lane;
+            nlist += __popc(m);
+            return nlist + 32 > kListCap;
+          });
+          if (lane == 0) {
+            s_n = nlist;
+            s_done = d.done ? 1u : 0u;
+          }
+        }
+        __syncthreads();
+        const uint32_t nlist = s_n;
+        const bool done = s_done != 0;
+        batch(fr[0], nlist);
+        if (done) break;
+      }
     }
-    if (!PLACE && threadIdx.x == 0) S.seq_cnt[a] = total;
+    if (threadIdx.x == 0) S.seq_cnt[a] = pos;
+    __syncthreads();
   }
 }
 
 // ---- scan -----------------------------------------------------------------
 
-// Sequence index and first position of every taken box, in box order.
+// Sequence index and first position of every taken box, in box order: one
+// block over the bitmap of taken boxes, which it clears for the next round.
 __global__ void __launch_bounds__(1024) k_rd_scan(State S, LeafRec *seqs) {
   __shared__ uint32_t ws[32], wc[32];
   if (S.ctr->alive == 0) return;
   const uint32_t filled = S.ctr->filled, nseq = S.ctr->nseq;
-  const uint32_t nl = S.nl;
-  const uint32_t per = (nl + 1023) / 1024;
-  const uint32_t b0 = min(nl, threadIdx.x * per), b1 = min(nl, b0 + per);
+  const uint32_t nw = (S.nl + 31) / 32;
+  const uint32_t per = (nw + 1023) / 1024;
+  const uint32_t w0 = min(nw, threadIdx.x * per), w1 = min(nw, w0 + per);
   uint32_t sum = 0, cnt = 0;
-  for (uint32_t a = b0; a < b1; ++a) {
-    const uint32_t x = S.seq_cnt[a];
-    sum += x;
-    cnt += x ? 1u : 0u;
+  for (uint32_t w = w0; w < w1; ++w) {
+    uint32_t b = S.tbits[w];
+    cnt += __popc(b);
+    while (b) {
+      const uint32_t a = 32 * w + uint32_t(__ffs(int(b)) - 1);
+      b &= b - 1;
+      sum += S.seq_cnt[a];
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t is = sum, ic = cnt;
@@ -521,37 +679,81 @@ __global__ void __launch_bounds__(1024) k_rd_scan(State S, LeafRec *seqs) {
   }
   __syncthreads();
   uint32_t pos = filled + ws[warp] + is - sum, seq = nseq + wc[warp] + ic - cnt;
-  for (uint32_t a = b0; a < b1; ++a) {
-    const uint32_t x = S.seq_cnt[a];
-    if (!x) continue;
-    S.seq_cnt[a] = 0;
-    S.seq_pos[a] = pos;
-    const RInfo I = S.info[a];
-    LeafRec r = {};
-    r.off = pos;
-    r.cnt = x;
-    r.centre = 0;
-    r.m = I.m;
-    for (int d = 0; d < 3; ++d) r.qref[d] = I.qref[d];
-    const uint64_t w = (I.m & 0xffu) + ((I.m >> 8) & 0xffu) + ((I.m >> 16) & 0xffu);
-    r.words = uint32_t((w * (x - 1) + 31) >> 5);
-    seqs[seq] = r;
-    pos += x;
-    ++seq;
+  for (uint32_t w = w0; w < w1; ++w) {
+    uint32_t b = S.tbits[w];
+    if (!b) continue;
+    S.tbits[w] = 0;
+    while (b) {
+      const uint32_t a = 32 * w + uint32_t(__ffs(int(b)) - 1);
+      b &= b - 1;
+      const uint32_t x = S.seq_cnt[a];
+      S.seq_pos[a] = pos;
+      const RInfo I = S.info[a];
+      LeafRec r = {};
+      r.off = pos;
+      r.cnt = x;
+      r.centre = 0;
+      r.m = I.m;
+      for (int d = 0; d < 3; ++d) r.qref[d] = I.qref[d];
+      const uint64_t wb = (I.m & 0xffu) + ((I.m >> 8) & 0xffu) + ((I.m >> 16) & 0xffu);
+      r.words = uint32_t((wb * (x - 1) + 31) >> 5);
+      seqs[seq] = r;
+      pos += x;
+      ++seq;
+    }
   }
 }
 
 // ---- rebuild --------------------------------------------------------------
 
+constexpr int kBoxThreads = 128;
+constexpr int kBoxWarps = kBoxThreads / 32;
+
+// The block's threads visit the live slots of [off, end) (every slot when
+// INIT) in aligned groups of four, four groups per thread at a time with their
+// loads issued first; f(s, x, y, z) sees each slot in increasing order per thread.
+template <typename C, bool INIT, class F>
+__device__ __forceinline__ void box_walk(const State &S, const C *q0, const C *q1, const C *q2, uint32_t off,
+                                         uint32_t end, F f) {
+  using Raw = typename Codes4<C>::Raw;
+  constexpr int U = 4;
+  const uint32_t g0 = off >> 2, g1 = (end + 3) >> 2;
+  for (uint32_t gb = g0; gb < g1; gb += U * kBoxThreads) {
+    uint32_t lw[U];
+    Raw cx[U], cy[U], cz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t g = min(gb + uint32_t(u) * kBoxThreads + threadIdx.x, g1 - 1);
+      lw[u] = INIT ? 0xffffffffu : __ldcg(S.live + (g >> 3));
+      cx[u] = Codes4<C>::load(q0, g);
+      cy[u] = Codes4<C>::load(q1, g);
+      cz[u] = Codes4<C>::load(q2, g);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t g = gb + uint32_t(u) * kBoxThreads + threadIdx.x;
+      if (g >= g1) continue;
+      const uint32_t lb = (lw[u] >> (4 * (g & 7))) & 0xfu;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t s = 4 * g + uint32_t(j);
+        if (!((lb >> j) & 1u) || s < off || s >= end) continue;
+        f(s, Codes4<C>::at(cx[u], j), Codes4<C>::at(cy[u], j), Codes4<C>::at(cz[u], j));
+      }
+    }
+  }
+}
+
 // INIT: every leaf's first box (all particles live; the counters start).
 // Otherwise: the boxes listed by place get the bit box of their live
 // particles or die when none is left; taken boxes die.
 template <typename C, bool INIT>
-__global__ void __launch_bounds__(kThreads) k_rd_rebuild(State S, const C *__restrict__ q0, const C *__restrict__ q1,
-                                                         const C *__restrict__ q2, const LeafRec *__restrict__ leafs) {
-  __shared__ uint32_t red[7][kWarps];
-  __shared__ unsigned long long rd[kWarps];
-  __shared__ uint32_t rp[kWarps];
+__global__ void __launch_bounds__(kBoxThreads) k_rd_rebuild(State S, const C *__restrict__ q0,
+                                                            const C *__restrict__ q1, const C *__restrict__ q2,
+                                                            const LeafRec *__restrict__ leafs) {
+  __shared__ uint32_t red[7][kBoxWarps];
+  __shared__ unsigned long long rd[kBoxWarps];
+  __shared__ uint32_t rp[kBoxWarps];
   if (INIT) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *S.ctr = RCounters{S.nl, 0, 0, 0, 0, 0, {0, 0}};
   } else if (S.ctr->alive == 0) {
@@ -577,16 +779,17 @@ __global__ void __launch_bounds__(kThreads) k_rd_rebuild(State S, const C *__res
       off = S.info[c].off;
       cnt = S.info[c].cnt;
     }
+    const uint32_t end = off + cnt;
     uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0}, live = 0;
-    for (uint32_t s = off + threadIdx.x; s < off + cnt; s += kThreads) {
-      if (!INIT && S.dest[s] != kLive) continue;
-      const uint32_t x[3] = {uint32_t(q0[s]), uint32_t(q1[s]), uint32_t(q2[s])};
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = min(lo[d], x[d]);
-        hi[d] = max(hi[d], x[d]);
-      }
+    box_walk<C, INIT>(S, q0, q1, q2, off, end, [&](uint32_t, uint32_t x, uint32_t y, uint32_t z) {
+      lo[0] = min(lo[0], x);
+      hi[0] = max(hi[0], x);
+      lo[1] = min(lo[1], y);
+      hi[1] = max(hi[1], y);
+      lo[2] = min(lo[2], z);
+      hi[2] = max(hi[2], z);
       ++live;
-    }
+    });
     for (int d = 0; d < 3; ++d) {
       lo[d] = __reduce_min_sync(0xffffffffu, lo[d]);
       hi[d] = __reduce_max_sync(0xffffffffu, hi[d]);
@@ -605,7 +808,7 @@ __global__ void __launch_bounds__(kThreads) k_rd_rebuild(State S, const C *__res
       lo[d] = red[2 * d][0];
       hi[d] = red[2 * d + 1][0];
     }
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < kBoxWarps; ++w) {
       live += red[6][w];
       for (int d = 0; d < 3; ++d) {
         lo[d] = min(lo[d], red[2 * d][w]);
@@ -626,16 +829,15 @@ __global__ void __launch_bounds__(kThreads) k_rd_rebuild(State S, const C *__res
     unsigned long long bd = ~0ull;
     uint32_t bp = 0xffffffffu;
     const long long s0 = (long long)lo[0] + hi[0], s1 = (long long)lo[1] + hi[1], s2 = (long long)lo[2] + hi[2];
-    for (uint32_t s = off + threadIdx.x; s < off + cnt; s += kThreads) {
-      if (!INIT && S.dest[s] != kLive) continue;
-      const long long a = 2ll * q0[s] - s0, b = 2ll * q1[s] - s1, e = 2ll * q2[s] - s2;
+    box_walk<C, INIT>(S, q0, q1, q2, off, end, [&](uint32_t s, uint32_t x, uint32_t y, uint32_t z) {
+      const long long a = 2ll * x - s0, b = 2ll * y - s1, e = 2ll * z - s2;
       const unsigned long long d2 =
           (unsigned long long)(a * a) + (unsigned long long)(b * b) + (unsigned long long)(e * e);
       if (d2 < bd) {  // slots rise within a thread: the first minimum is the lowest
         bd = d2;
         bp = s;
       }
-    }
+    });
     for (int o = 16; o; o >>= 1) {
       const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
       const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
@@ -650,7 +852,7 @@ __global__ void __launch_bounds__(kThreads) k_rd_rebuild(State S, const C *__res
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < kWarps; ++w)
+      for (int w = 1; w < kBoxWarps; ++w)
         if (rd[w] < bd || (rd[w] == bd && rp[w] < bp)) {
           bd = rd[w];
           bp = rp[w];
@@ -690,7 +892,8 @@ __global__ void k_rd_gather(State S, uint64_t n, const C *__restrict__ q0, const
                             const C *__restrict__ q2, C *o0, C *o1, C *o2, const uint32_t *__restrict__ idx,
                             uint32_t *oidx, uint32_t *err) {
   for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += uint64_t(gridDim.x) * blockDim.x) {
-    const uint32_t p = S.dest[s];
+    const uint32_t a = S.dest[s];
+    const uint64_t p = a < S.nl ? uint64_t(S.seq_pos[a]) + S.rank[s] : n;
     if (p >= n) {  // every particle is in exactly one sequence
       atomicOr(err, kErrInternal);
       continue;
@@ -713,17 +916,22 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
   for (int l = 0; l <= L.top; ++l) S.t.count[l] = L.count[l];
   S.t.top = L.top;
   S.info = reinterpret_cast<RInfo *>(base + L.info);
+  S.live = reinterpret_cast<uint32_t *>(base + L.live);
   S.dest = reinterpret_cast<uint32_t *>(base + L.dest);
+  S.rank = reinterpret_cast<uint32_t *>(base + L.rank);
   S.seq_cnt = reinterpret_cast<uint32_t *>(base + L.seq_cnt);
   S.seq_pos = reinterpret_cast<uint32_t *>(base + L.seq_pos);
   S.taken = reinterpret_cast<uint32_t *>(base + L.taken);
   S.lost = reinterpret_cast<uint32_t *>(base + L.lost);
+  S.tbits = reinterpret_cast<uint32_t *>(base + L.tbits);
   S.ctr = reinterpret_cast<RCounters *>(base + L.ctr);
   S.nl = uint32_t(a.num_leaves);
   const C *q0 = static_cast<const C *>(a.codes[0]), *q1 = static_cast<const C *>(a.codes[1]),
           *q2 = static_cast<const C *>(a.codes[2]);
 
-  cudaError_t e = cudaMemsetAsync(S.dest, 0xff, 4 * a.n, st);
+  cudaError_t e = cudaMemsetAsync(S.live, 0xff, 4 * (a.n / 32 + 2), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(S.dest, 0xff, 4 * a.n, st);  // no owner yet: the final pass checks every slot got one
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(base + L.zero_begin, 0, L.zero_end - L.zero_begin, st);
   if (e != cudaSuccess) return e;
@@ -731,12 +939,13 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
   if (e != cudaSuccess) return e;
 
   const uint32_t sms = uint32_t(device_sm_count());
-  const unsigned box_blocks = unsigned(a.num_leaves < 4ull * sms ? a.num_leaves : 4ull * sms);
+  const unsigned box_blocks = unsigned(a.num_leaves < 16ull * sms ? a.num_leaves : 16ull * sms);
+  const unsigned take_blocks = unsigned(a.num_leaves < 2ull * sms ? a.num_leaves : 2ull * sms);
   const unsigned refit_blocks = unsigned((uint64_t(L.count[1]) + kWarps - 1) / kWarps);
   const unsigned select_blocks = unsigned((a.num_leaves + kWarps - 1) / kWarps);
   {
     TraceScope ts("k_rd_rebuild", st);
-    k_rd_rebuild<C, true><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
+    k_rd_rebuild<C, true><<<box_blocks, kBoxThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
   }
   {
     TraceScope ts("k_rd_refit", st);
@@ -750,20 +959,16 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
         k_rd_select<<<select_blocks, kThreads, 0, st>>>(S);
       }
       {
-        TraceScope ts("k_rd_count", st);
-        k_rd_take<C, false><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2);
+        TraceScope ts("k_rd_take", st);
+        k_rd_take<C><<<take_blocks, kTakeThreads, 0, st>>>(S, q0, q1, q2);
       }
       {
         TraceScope ts("k_rd_scan", st);
         k_rd_scan<<<1, 1024, 0, st>>>(S, a.seqs);
       }
       {
-        TraceScope ts("k_rd_place", st);
-        k_rd_take<C, true><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2);
-      }
-      {
         TraceScope ts("k_rd_rebuild", st);
-        k_rd_rebuild<C, false><<<box_blocks, kThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
+        k_rd_rebuild<C, false><<<box_blocks, kBoxThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
       }
       {
         TraceScope ts("k_rd_refit", st);

@@ -129,3 +129,15 @@ def test_reduction_empty(pc):
     c = pc.Compressor(0, pc.PC_F32, leaf_size=pc.config(64, reduce=True), device=dev)
     size = c.compress(torch.empty((0, 3), dtype=torch.float32, device=dev), pc.PC_EB_ABS, 1e-3)
     assert size == 96
+
+
+def test_reduction_more_boxes_met_than_a_batch(pc, oracle_mod):
+    """625 leaves of identical points: the first box taken meets all 624 others,
+    more than one search batch holds."""
+    pos = np.full((40_000, 3), -3.5, np.float64)
+    got, rounds = check(pc, oracle_mod, pos, pc.PC_EB_ABS, 1e-3, 64)
+    assert rounds == 1 and parse(got, with_codes=False).num_leaves == 1
+    base = synth.uniform(400, seed=8, box=2.0)
+    pos = np.concatenate([base] * 100)
+    pos = pos[np.random.default_rng(8).permutation(len(pos))]
+    check(pc, oracle_mod, pos, pc.PC_EB_ABS, 5e-3, 50)
