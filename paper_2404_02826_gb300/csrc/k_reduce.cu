@@ -37,6 +37,7 @@
 #include <cstdint>
 
 #include "pc_internal.cuh"
+#include "pc_reduce.cuh"
 
 namespace pcx {
 namespace {

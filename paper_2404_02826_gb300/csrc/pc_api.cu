@@ -7,6 +7,7 @@
 
 #include "../../include/pc.h"
 #include "pc_internal.cuh"
+#include "pc_reduce.cuh"
 
 namespace pcx {
 
