@@ -10,10 +10,10 @@
 // Intersection query: a 32-ary tree over the box indices.  Level 0 are the
 // boxes; node j of level k >= 1 holds the union of the alive bit boxes below
 // its children [32j, 32j + 32) of level k - 1 and the least (key, index) of
-// those boxes (key = m_x + m_y + m_z).  It is refitted bottom-up after every
-// round (the paper's bottom-up update) and searched top-down by one warp that
-// tests 32 children at a time, depth first, so that boxes come out in
-// increasing index.
+// those boxes (key = m_x + m_y + m_z).  It is updated bottom-up after every
+// round (the paper's bottom-up update: only nodes above changed boxes, each
+// by the warp that settles its last pending change) and searched top-down,
+// 32 children per warp-wide test, so that boxes come out in increasing index.
 //
 // One round:
 //   select   a warp per alive box a: a is taken when no other alive box with a
@@ -28,8 +28,7 @@
 //            position, in box order, after the sequences of earlier rounds.
 //   rebuild  a block per listed box: the bit box of what it keeps (the leaf
 //            rules: AABB, the particle closest to its centre, Eq. 2); taken and
-//            emptied boxes die.
-//   refit    the tree over the new boxes.
+//            emptied boxes die; the tree nodes above them are recomputed.
 // The host reads the alive count back every few rounds; rounds issued after
 // the last box died return at once.  A final pass moves codes and input
 // indices to their output positions for the packing kernels.
@@ -71,13 +70,14 @@ struct RInfo {  // the rest of a box, 64 bytes
 static_assert(sizeof(RBox) == 32 && sizeof(TNode) == 32 && sizeof(RInfo) == 64, "box layouts");
 
 struct RCounters {
-  uint32_t alive, taken, nlost, nseq, filled, rounds, pad[2];
+  uint32_t alive, taken, nlost, nseq, filled, rounds, done, pad;
 };
 
 struct Tree {
   RBox *box;
   TNode *node[kMaxLevels];       // node[k], 1 <= k <= top
   uint32_t *ticket[kMaxLevels];  // ticket[k], 2 <= k <= top: children of node j refitted so far
+  uint32_t *pend[kMaxLevels];    // pend[k], 1 <= k < top: changes below node j not yet settled
   uint32_t count[kMaxLevels];    // count[0] = boxes, count[top] = 1
   int top;
 };
@@ -98,7 +98,8 @@ struct State {
 };
 
 struct Layout {
-  uint64_t live, dest, rank, box, info, node[kMaxLevels], ticket[kMaxLevels], seq_cnt, seq_pos, taken, lost, tbits, ctr;
+  uint64_t live, dest, rank, box, info, node[kMaxLevels], ticket[kMaxLevels], pend[kMaxLevels], seq_cnt, seq_pos,
+      taken, lost, tbits, ctr;
   uint64_t zero_begin, zero_end, total;
   uint32_t count[kMaxLevels];
   int top;
@@ -139,6 +140,10 @@ Layout layout_of(uint64_t n, uint64_t nl) {
   L.zero_begin = o;  // zeroed once per call
   for (int l = 2; l <= L.top; ++l) {
     L.ticket[l] = o;
+    o = align256(o + 4 * uint64_t(L.count[l]));
+  }
+  for (int l = 1; l < L.top; ++l) {
+    L.pend[l] = o;
     o = align256(o + 4 * uint64_t(L.count[l]));
   }
   L.seq_cnt = o;
@@ -240,34 +245,73 @@ __device__ __forceinline__ void warp_union(int32_t lo[3], int32_t hi[3], unsigne
   }
 }
 
-// A warp per node of level 1; the warp that completes the last child of a
-// node (ticket) goes on to compute that node, up to the root.
-__global__ void __launch_bounds__(kThreads) k_rd_refit(State S) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S.ctr->taken = 0;
-    S.ctr->nlost = 0;
+// Child c of level l (a box when l = 0) as its part of a node: bounds and
+// key << 32 | index of an alive box, the node itself above; nothing otherwise.
+__device__ __forceinline__ void load_child(const Tree &t, int l, uint32_t c, int32_t lo[3], int32_t hi[3],
+                                           unsigned long long &mn) {
+  lo[0] = lo[1] = lo[2] = INT_MAX;
+  hi[0] = hi[1] = hi[2] = INT_MIN;
+  mn = ~0ull;
+  if (c >= t.count[l]) return;
+  const int4 *q = l == 0 ? reinterpret_cast<const int4 *>(t.box + c) : reinterpret_cast<const int4 *>(t.node[l] + c);
+  const int4 a = __ldcg(q), b = __ldcg(q + 1);
+  if (l == 0 && !(uint32_t(b.w) & kAlive)) return;
+  lo[0] = a.x;
+  lo[1] = a.y;
+  lo[2] = a.z;
+  hi[0] = a.w;
+  hi[1] = b.x;
+  hi[2] = b.y;
+  mn = l == 0 ? (static_cast<unsigned long long>(uint32_t(b.z)) << 32) | c
+              : (static_cast<unsigned long long>(uint32_t(b.w)) << 32) | uint32_t(b.z);
+}
+
+// One warp recomputes node j of level l >= 1 from its 32 children.
+__device__ __forceinline__ void warp_refit_node(const Tree &t, int l, uint32_t j) {
+  int32_t lo[3], hi[3];
+  unsigned long long mn;
+  load_child(t, l - 1, j * 32 + (threadIdx.x & 31), lo, hi, mn);
+  warp_union(lo, hi, mn);
+  if ((threadIdx.x & 31) == 0) t.node[l][j] = TNode{{lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, mn};
+}
+
+// A box about to change this round (taken, or losing particles): one more
+// pending change below each of its nodes that was clean (one thread).
+__device__ __forceinline__ void mark_dirty(const Tree &t, uint32_t c) {
+  uint32_t j = c;
+  for (int l = 1; l < t.top; ++l) {
+    j >>= 5;
+    if (atomicAdd(t.pend[l] + j, 1u) != 0u) return;
   }
-  if (S.ctr->alive == 0) return;
+}
+
+// After box c's new record is written: one pending change fewer; the warp
+// that settles the last change below a node recomputes it and goes on up
+// (the root is never searched and is not kept up to date).
+__device__ __forceinline__ void warp_settle(const Tree &t, uint32_t c) {
+  uint32_t j = c;
+  for (int l = 1; l < t.top; ++l) {
+    j >>= 5;
+    uint32_t old = 0;
+    if ((threadIdx.x & 31) == 0) {
+      __threadfence();
+      old = atomicSub(t.pend[l] + j, 1u);
+    }
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != 1u) return;
+    __threadfence();
+    warp_refit_node(t, l, j);
+  }
+}
+
+// The whole tree (after the first boxes): a warp per node of level 1; the
+// warp that completes the last child of a node (ticket) goes on to compute
+// that node, up to the root.
+__global__ void __launch_bounds__(kThreads) k_rd_refit(State S) {
   const int lane = threadIdx.x & 31;
   uint32_t j = (blockIdx.x * kThreads + threadIdx.x) >> 5;
   if (j >= S.t.count[1]) return;
-  {
-    const uint32_t c = j * 32 + lane;
-    int32_t lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    unsigned long long mn = ~0ull;
-    if (c < S.t.count[0]) {
-      const RBox b = S.t.box[c];
-      if (b.state & kAlive) {
-        for (int d = 0; d < 3; ++d) {
-          lo[d] = b.lo[d];
-          hi[d] = b.hi[d];
-        }
-        mn = (static_cast<unsigned long long>(b.key) << 32) | c;
-      }
-    }
-    warp_union(lo, hi, mn);
-    if (lane == 0) S.t.node[1][j] = TNode{{lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, mn};
-  }
+  warp_refit_node(S.t, 1, j);
   for (int l = 1; l < S.t.top; ++l) {
     const uint32_t p = j >> 5;
     const uint32_t kids = min(32u, S.t.count[l] - p * 32);
@@ -278,24 +322,9 @@ __global__ void __launch_bounds__(kThreads) k_rd_refit(State S) {
     }
     tk = __shfl_sync(0xffffffffu, tk, 0);
     if (tk + 1 != kids) return;
-    if (lane == 0) S.t.ticket[l + 1][p] = 0;  // ready for the next refit
+    if (lane == 0) S.t.ticket[l + 1][p] = 0;
     __threadfence();
-    const uint32_t c = p * 32 + lane;
-    int32_t lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    unsigned long long mn = ~0ull;
-    if (c < S.t.count[l]) {
-      const int4 *q = reinterpret_cast<const int4 *>(S.t.node[l] + c);
-      const int4 a = __ldcg(q), b = __ldcg(q + 1);
-      lo[0] = a.x;
-      lo[1] = a.y;
-      lo[2] = a.z;
-      hi[0] = a.w;
-      hi[1] = b.x;
-      hi[2] = b.y;
-      mn = (static_cast<unsigned long long>(uint32_t(b.w)) << 32) | uint32_t(b.z);
-    }
-    warp_union(lo, hi, mn);
-    if (lane == 0) S.t.node[l + 1][p] = TNode{{lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, mn};
+    warp_refit_node(S.t, l + 1, p);
     j = p;
   }
 }
@@ -334,6 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_rd_select(State S) {
     atomicOr(&S.t.box[a].state, kTaken);
     atomicOr(S.tbits + (a >> 5), 1u << (a & 31));
     S.taken[atomicAdd(&S.ctr->taken, 1u)] = a;
+    mark_dirty(S.t, a);
   }
 }
 
@@ -366,26 +396,36 @@ struct Codes4<uint32_t> {
   }
 };
 
+// A warp's picks over slots [off, end), recorded for the ranking pass: per
+// lane, four bits (one group of four slots) for each group the lane visited,
+// in visiting order.  Leaves hold at most PC_MAX_LEAF_SIZE particles, so a
+// lane visits at most kRecWords * 8 groups of one leaf.
+constexpr int kRecWords = 12;
+template <typename C>
+constexpr int kPickUnroll = sizeof(C) == 2 ? 4 : 2;  // groups per lane in flight: the same bytes for both widths
+static_assert(((PC_MAX_LEAF_SIZE + 3) / 4 + 1 + 31) / 32 <= kRecWords * 8, "pick record too small");
+struct Picks {
+  uint32_t w[kRecWords];
+};
+
 // One warp walks the live slots of [off, end) in aligned groups of four (lane
 // i takes every 32nd group), a few groups per lane at a time: all their loads
 // are issued first (indices clamped into the range, so no load waits on a
 // branch), then the slots are tested.  want(s, x, y, z) picks live slot s (x,
-// y, z its codes when CODES).  Returns how many were picked; with PLACE they
-// also stop being live and get dest[s] = tag and rank[s] = pos, pos + 1, ...
-// in slot order.
-template <typename C, bool CODES, bool PLACE, class Want>
-__device__ __forceinline__ uint32_t warp_walk(const State &S, uint32_t tag, const C *q0, const C *q1, const C *q2,
-                                              uint32_t off, uint32_t end, uint32_t pos, Want want) {
+// y, z its codes when CODES).  Records the picks and returns their number.
+template <typename C, bool CODES, class Want>
+__device__ __forceinline__ uint32_t warp_pick(const State &S, const C *q0, const C *q1, const C *q2, uint32_t off,
+                                              uint32_t end, Want want, Picks &rec) {
   using Raw = typename Codes4<C>::Raw;
-  constexpr int kUnroll = sizeof(C) == 2 ? 4 : 2;  // the same bytes in flight for both code widths
+  constexpr int U = kPickUnroll<C>;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t g0 = off >> 2, g1 = (end + 3) >> 2;
-  uint32_t k = 0;
-  for (uint32_t gb = g0; gb < g1; gb += 32 * kUnroll) {
-    uint32_t lw[kUnroll];
-    Raw cx[kUnroll], cy[kUnroll], cz[kUnroll];
+  uint32_t k = 0, nib = 0;
+  for (uint32_t gb = g0; gb < g1; gb += 32 * U) {
+    uint32_t lw[U];
+    Raw cx[U], cy[U], cz[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const uint32_t g = min(gb + uint32_t(u) * 32 + lane, g1 - 1);
       lw[u] = __ldcg(S.live + (g >> 3));
       if (CODES) {
@@ -394,12 +434,11 @@ __device__ __forceinline__ uint32_t warp_walk(const State &S, uint32_t tag, cons
         cz[u] = Codes4<C>::load(q2, g);
       }
     }
-    uint32_t bits[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u, ++nib) {
       const uint32_t g = gb + uint32_t(u) * 32 + lane;
       const uint32_t lb = g < g1 ? (lw[u] >> (4 * (g & 7))) & 0xfu : 0u;
-      bits[u] = 0;
+      uint32_t bits = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const uint32_t s = 4 * g + uint32_t(j);
@@ -410,67 +449,82 @@ __device__ __forceinline__ uint32_t warp_walk(const State &S, uint32_t tag, cons
           y = Codes4<C>::at(cy[u], j);
           z = Codes4<C>::at(cz[u], j);
         }
-        if (want(s, x, y, z)) bits[u] |= 1u << j;
+        if (want(s, x, y, z)) bits |= 1u << j;
       }
+      if ((nib & 7) == 0) rec.w[nib >> 3] = 0;
+      rec.w[nib >> 3] |= bits << (4 * (nib & 7));
+      k += __popc(bits);
     }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t c = __popc(bits[u]);
-      if (!PLACE) {
-        k += c;
-        continue;
-      }
+  }
+  return __reduce_add_sync(0xffffffffu, k);
+}
+
+// Replays a warp's picks over [off, end): they stop being live and get
+// dest[s] = tag and rank[s] = pos, pos + 1, ... in slot order.
+__device__ __forceinline__ void warp_place(const State &S, uint32_t tag, uint32_t off, uint32_t end, uint32_t pos,
+                                           const Picks &rec, int unroll) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t g0 = off >> 2, g1 = (end + 3) >> 2;
+  uint32_t nib = 0;
+  for (uint32_t gb = g0; gb < g1; gb += 32 * uint32_t(unroll)) {
+    for (int u = 0; u < unroll; ++u, ++nib) {
+      const uint32_t bits = (rec.w[nib >> 3] >> (4 * (nib & 7))) & 0xfu;
+      const uint32_t c = __popc(bits);
       uint32_t incl = c;
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= uint32_t(o)) incl += y;
       }
-      uint32_t p = pos + k + incl - c;
+      uint32_t p = pos + incl - c;
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+      if (!bits) continue;
       const uint32_t g = gb + uint32_t(u) * 32 + lane;
-      if (bits[u]) atomicAnd(S.live + (g >> 3), ~(bits[u] << (4 * (g & 7))));
+      atomicAnd(S.live + (g >> 3), ~(bits << (4 * (g & 7))));
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if ((bits[u] >> j) & 1u) {
+        if ((bits >> j) & 1u) {
           S.dest[4 * g + uint32_t(j)] = tag;
           S.rank[4 * g + uint32_t(j)] = p++;
         }
-      k += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
-  if (!PLACE) k = __reduce_add_sync(0xffffffffu, k);
-  return k;
 }
 
-// Live particles of part t of `parts` of box c's slots inside bit box b, by
-// one warp (parts split the slots in whole groups of four, in slot order); with
-// PLACE they go to box `tag`'s sequence with ranks pos, pos + 1, ... in slot
-// order.  Returns the count.
-template <typename C, bool PLACE>
-__device__ uint32_t warp_take(const State &S, const C *q0, const C *q1, const C *q2, uint32_t c, uint32_t t,
-                              uint32_t parts, const Box6 &b, uint32_t tag, uint32_t pos) {
-  const RInfo I = S.info[c];
-  bool meet = true, all = true;
+// The slots of part t of `parts` of box c (whole groups of four, in slot
+// order), or an empty range when c's live particles miss bit box b; `all`
+// tells that every live particle of c lies inside b.
+__device__ __forceinline__ void take_range(const RInfo &I, uint32_t t, uint32_t parts, const Box6 &b, uint32_t &off,
+                                           uint32_t &end, bool &all) {
+  bool meet = true;
+  all = true;
   for (int d = 0; d < 3; ++d) {
     const int32_t lo = int32_t(I.tlo[d]), hi = int32_t(I.thi[d]);
     if (lo > b.hi[d] || hi < b.lo[d]) meet = false;
     if (lo < b.lo[d] || hi > b.hi[d]) all = false;
   }
-  if (!meet) return 0;
+  off = end = 0;
+  if (!meet) return;
   const uint32_t g0 = I.off >> 2, ng = ((I.off + I.cnt + 3) >> 2) - g0;  // ng * parts < 2^32
-  const uint32_t off = max(I.off, 4 * (g0 + ng * t / parts));
-  const uint32_t end = min(I.off + I.cnt, 4 * (g0 + ng * (t + 1) / parts));
+  off = max(I.off, 4 * (g0 + ng * t / parts));
+  end = min(I.off + I.cnt, 4 * (g0 + ng * (t + 1) / parts));
+  if (off > end) off = end;
+}
+
+// Live particles of slots [off, end) of a box inside bit box b (every live
+// one when `all`), by one warp; records them for warp_place.
+template <typename C>
+__device__ __forceinline__ uint32_t warp_pick_inside(const State &S, const C *q0, const C *q1, const C *q2,
+                                                     uint32_t off, uint32_t end, bool all, const Box6 &b, Picks &rec) {
   if (off >= end) return 0;
-  if (all) {  // every live particle of c is inside
-    if (!PLACE && parts == 1) return I.live;
-    return warp_walk<C, false, PLACE>(S, tag, q0, q1, q2, off, end, pos,
-                                      [](uint32_t, uint32_t, uint32_t, uint32_t) { return true; });
-  }
-  return warp_walk<C, true, PLACE>(S, tag, q0, q1, q2, off, end, pos,
-                                   [&](uint32_t, uint32_t x, uint32_t y, uint32_t z) {
-                                     return b.lo[0] <= int32_t(x) && int32_t(x) <= b.hi[0] &&
-                                            b.lo[1] <= int32_t(y) && int32_t(y) <= b.hi[1] &&
-                                            b.lo[2] <= int32_t(z) && int32_t(z) <= b.hi[2];
-                                   });
+  if (all)
+    return warp_pick<C, false>(S, q0, q1, q2, off, end, [](uint32_t, uint32_t, uint32_t, uint32_t) { return true; },
+                               rec);
+  return warp_pick<C, true>(S, q0, q1, q2, off, end,
+                            [&](uint32_t, uint32_t x, uint32_t y, uint32_t z) {
+                              return b.lo[0] <= int32_t(x) && int32_t(x) <= b.hi[0] && b.lo[1] <= int32_t(y) &&
+                                     int32_t(y) <= b.hi[1] && b.lo[2] <= int32_t(z) && int32_t(z) <= b.hi[2];
+                            },
+                            rec);
 }
 
 // Barrier of the first `nthreads` threads of the block (whole warps), apart
@@ -506,8 +560,10 @@ __global__ void __launch_bounds__(kTakeThreads) k_rd_take(State S, const C *__re
     };
     if (warp == kTakeWarps - 1) {  // the centre, then the box's other live particles in slot order
       const uint32_t centre = IA.centre;
-      warp_walk<C, false, true>(S, a, q0, q1, q2, IA.off, IA.off + IA.cnt, 1,
-                                [=](uint32_t s, uint32_t, uint32_t, uint32_t) { return s != centre; });
+      Picks rec;
+      warp_pick<C, false>(S, q0, q1, q2, IA.off, IA.off + IA.cnt,
+                          [=](uint32_t s, uint32_t, uint32_t, uint32_t) { return s != centre; }, rec);
+      warp_place(S, a, IA.off, IA.off + IA.cnt, 1, rec, kPickUnroll<C>);
       if (lane == 0) {
         atomicAnd(S.live + (centre >> 5), ~(1u << (centre & 31)));
         S.dest[centre] = a;
@@ -562,37 +618,44 @@ __global__ void __launch_bounds__(kTakeThreads) k_rd_take(State S, const C *__re
     }
     __syncthreads();
     uint32_t pos = IA.live;
-    // counts, then ranks, of `parts` pieces of each of the nlist boxes in list
+    // counts, then ranks, of `parts` pieces of each of the nlist boxes in list,
+    // at most one piece per warp at a time (its picks stay in the warp's registers)
     auto batch = [&](const uint32_t *list, uint32_t nlist) {
       const uint32_t parts = nlist ? max(1u, min(16u, uint32_t(kTakeWarps) / nlist)) : 1u;
       const uint32_t items = nlist * parts;
-      for (uint32_t it = warp; it < items; it += kTakeWarps) {
-        const uint32_t k = warp_take<C, false>(S, q0, q1, q2, list[it / parts], it % parts, parts, bx, a, 0);
-        if (lane == 0) lpos[it] = k;
-      }
-      __syncthreads();
-      if (warp == 0) {  // exclusive scan of the counts and their sum
-        uint32_t run = 0;
-        for (uint32_t j0 = 0; j0 < items; j0 += 32) {
-          const uint32_t x = j0 + lane < items ? lpos[j0 + lane] : 0u;
+      for (uint32_t i0 = 0; i0 < items; i0 += kTakeWarps) {
+        const uint32_t it = i0 + uint32_t(warp);
+        uint32_t c = 0, off = 0, end = 0, k = 0;
+        Picks rec;
+        if (it < items) {
+          c = list[it / parts];
+          bool all;
+          take_range(S.info[c], it % parts, parts, bx, off, end, all);
+          k = warp_pick_inside<C>(S, q0, q1, q2, off, end, all, bx, rec);
+        }
+        if (lane == 0) lpos[warp] = k;
+        __syncthreads();
+        if (warp == 0) {  // exclusive scan of the pieces' counts
+          const uint32_t x = lpos[lane];
           uint32_t incl = x;
           for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
           }
-          if (j0 + lane < items) lpos[j0 + lane] = run + incl - x;
-          run += __shfl_sync(0xffffffffu, incl, 31);
+          lpos[lane] = incl - x;
+          if (lane == 31) s_sum = incl;
         }
-        if (lane == 0) s_sum = run;
+        __syncthreads();
+        if (k) {
+          warp_place(S, a, off, end, pos + lpos[warp], rec, kPickUnroll<C>);
+          if (lane == 0 && atomicExch(&S.info[c].lost, 1u) == 0u) {
+            S.lost[atomicAdd(&S.ctr->nlost, 1u)] = c;
+            mark_dirty(S.t, c);
+          }
+        }
+        pos += s_sum;
+        __syncthreads();  // lpos and s_sum are reused
       }
-      __syncthreads();
-      for (uint32_t it = warp; it < items; it += kTakeWarps) {
-        const uint32_t c = list[it / parts];
-        const uint32_t k = warp_take<C, true>(S, q0, q1, q2, c, it % parts, parts, bx, a, pos + lpos[it]);
-        if (k && lane == 0 && atomicExch(&S.info[c].lost, 1u) == 0u) S.lost[atomicAdd(&S.ctr->nlost, 1u)] = c;
-      }
-      pos += s_sum;
-      __syncthreads();  // the batch's shared state is reused
     };
     if (!s_over) {
       batch(fr[s_cur], s_nf);
@@ -756,7 +819,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_rd_rebuild(State S, const C *__
   __shared__ unsigned long long rd[kBoxWarps];
   __shared__ uint32_t rp[kBoxWarps];
   if (INIT) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *S.ctr = RCounters{S.nl, 0, 0, 0, 0, 0, {0, 0}};
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.ctr->alive = S.nl;  // the rest starts zeroed
   } else if (S.ctr->alive == 0) {
     return;
   }
@@ -765,9 +828,13 @@ __global__ void __launch_bounds__(kBoxThreads) k_rd_rebuild(State S, const C *__
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t i = blockIdx.x; i < nlost + ntaken; i += gridDim.x) {
     if (i >= nlost) {
-      if (threadIdx.x == 0) {
-        S.t.box[S.taken[i - nlost]].state = 0;
-        atomicSub(&S.ctr->alive, 1u);
+      if (warp == 0) {
+        const uint32_t a = S.taken[i - nlost];
+        if (lane == 0) {
+          S.t.box[a].state = 0;
+          atomicSub(&S.ctr->alive, 1u);
+        }
+        warp_settle(S.t, a);
       }
       continue;
     }
@@ -823,6 +890,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_rd_rebuild(State S, const C *__
         S.info[c].lost = 0;
         atomicSub(&S.ctr->alive, 1u);
       }
+      if (warp == 0) warp_settle(S.t, c);
       __syncthreads();
       continue;
     }
@@ -882,7 +950,17 @@ __global__ void __launch_bounds__(kBoxThreads) k_rd_rebuild(State S, const C *__
       S.info[c] = I;
       S.t.box[c] = B;
     }
+    if (!INIT && warp == 0) warp_settle(S.t, c);
     __syncthreads();
+  }
+  // the last block to finish empties the round's lists for the next round
+  if (!INIT && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&S.ctr->done, 1u) == gridDim.x - 1) {
+      S.ctr->taken = 0;
+      S.ctr->nlost = 0;
+      S.ctr->done = 0;
+    }
   }
 }
 
@@ -914,6 +992,7 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
   S.t.box = reinterpret_cast<RBox *>(base + L.box);
   for (int l = 1; l <= L.top; ++l) S.t.node[l] = reinterpret_cast<TNode *>(base + L.node[l]);
   for (int l = 2; l <= L.top; ++l) S.t.ticket[l] = reinterpret_cast<uint32_t *>(base + L.ticket[l]);
+  for (int l = 1; l < L.top; ++l) S.t.pend[l] = reinterpret_cast<uint32_t *>(base + L.pend[l]);
   for (int l = 0; l <= L.top; ++l) S.t.count[l] = L.count[l];
   S.t.top = L.top;
   S.info = reinterpret_cast<RInfo *>(base + L.info);
@@ -970,10 +1049,6 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
       {
         TraceScope ts("k_rd_rebuild", st);
         k_rd_rebuild<C, false><<<box_blocks, kBoxThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
-      }
-      {
-        TraceScope ts("k_rd_refit", st);
-        k_rd_refit<<<refit_blocks, kThreads, 0, st>>>(S);
       }
     }
     e = cudaGetLastError();
