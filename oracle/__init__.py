@@ -76,6 +76,11 @@ def lib(parallel: bool = False):
                                       ctypes.POINTER(vp)]
         L.oracle_compress_reduced.argtypes = [vp, u64, i32, i32, dbl, u64, i32, ctypes.POINTER(vp), ctypes.POINTER(u64),
                                               ctypes.POINTER(vp), ctypes.POINTER(u64)]
+        L.oracle_reorder.argtypes = [vp, u64, vp, ctypes.POINTER(vp), ctypes.POINTER(u64), vp, vp]
+        L.oracle_rindex.argtypes = [vp, vp, vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.oracle_rindex.restype = None
+        L.oracle_axis_order.argtypes = [vp, u64, vp, vp]
+        L.oracle_axis_order.restype = None
         L.oracle_stream_header.argtypes = [vp, u64, ctypes.POINTER(u64), ctypes.POINTER(i32),
                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.oracle_decompress.argtypes = [vp, u64, vp, u64]
@@ -240,6 +245,45 @@ def compress_reduced(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_p
             if n else np.zeros(0, np.int64)
         L.oracle_free(perm)
     return stream, p, rounds.value
+
+
+def rindex(c, m, order) -> int:
+    """Sec. 4.2: the R-index of codes c[3] of widths m[3], axes in `order` (most significant first)."""
+    cc = np.asarray(c, np.uint32)
+    mm = np.asarray(m, np.uint32)
+    oo = np.asarray(order, np.int32)
+    hi, lo = ctypes.c_uint64(), ctypes.c_uint64()
+    lib().oracle_rindex(cc.ctypes.data, mm.ctypes.data, oo.ctypes.data, ctypes.byref(hi), ctypes.byref(lo))
+    return (hi.value << 64) | lo.value
+
+
+def axis_order(m):
+    """Sec. 4.2: axes in increasing entropy of their m_d over sequences (m: k x 3). Returns (order, entropies)."""
+    mm = np.ascontiguousarray(m, np.uint32).reshape(-1, 3)
+    order = np.zeros(3, np.int32)
+    ent = np.zeros(3, np.float64)
+    lib().oracle_axis_order(mm.ctypes.data, mm.shape[0], order.ctypes.data, ent.ctypes.data)
+    return tuple(int(x) for x in order), ent
+
+
+def reorder(stream: bytes, perm=None):
+    """Sec. 4.2 reordering of a stream: sequences by sum m_d, particles by R-index.
+    Returns (stream, perm, axis order); perm maps new positions to input indices
+    (to the old positions when perm is None)."""
+    n, _, _, _ = stream_header(stream)
+    buf = ctypes.create_string_buffer(bytes(stream), len(stream))
+    pin = None if perm is None else np.ascontiguousarray(perm, np.uint64)
+    pout = np.zeros(max(n, 1), np.uint64)
+    order = np.zeros(3, np.int32)
+    out = ctypes.c_void_p()
+    nbytes = ctypes.c_uint64()
+    rc = lib().oracle_reorder(buf, len(stream), None if pin is None else pin.ctypes.data, ctypes.byref(out),
+                              ctypes.byref(nbytes), pout.ctypes.data, order.ctypes.data)
+    if rc:
+        raise OracleError(rc, "reorder")
+    res = ctypes.string_at(out, nbytes.value)
+    lib().oracle_free(out)
+    return res, pout[:n].astype(np.int64), tuple(int(x) for x in order)
 
 
 def stream_header(stream: bytes):

@@ -826,6 +826,192 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Reordering for the entropy coder (Sec. 4.2, after Fig. 4): the sequences   */
+/* are put in increasing order of sum m_d, and the particles of a sequence    */
+/* (its centre staying first) in increasing order of their R-index.  The      */
+/* R-index joins a particle's three codes, most significant first, in the     */
+/* order of the axes' entropy levels: the entropy of the distribution of m_d  */
+/* over all sequences, lowest first (the paper's example: x, then z, then y). */
+/* Readings: entropies within 1e-9 of each other tie and keep the x, y, z     */
+/* order (a stable insertion sort of the three axes); equal sums of m_d and   */
+/* equal R-indices keep the previous order.  Decoding ignores the order, so   */
+/* the stream format is unchanged; only positions move.                       */
+/* ------------------------------------------------------------------------ */
+
+int oracle_stream_header(const uint8_t *st, uint64_t bytes, uint64_t *n, int *dtype, uint64_t *num_leaves,
+                         uint64_t *payload_words);
+
+/* R-index of codes c[3] of widths m[3]: c[order[0]] (highest bits), then
+ * c[order[1]], then c[order[2]] (lowest bits); up to 93 bits, as hi:lo. */
+void oracle_rindex(const uint32_t c[3], const uint32_t m[3], const int order[3], uint64_t *hi, uint64_t *lo)
+{
+    uint64_t h = 0, l = 0;
+    for (int k = 0; k < 3; k++) {
+        uint32_t w = m[order[k]];
+        /* (h:l) <<= w, then add the code */
+        if (w) {
+            if (w >= 64) {
+                h = l << (w - 64);
+                l = 0;
+            } else {
+                h = (h << w) | (l >> (64 - w));
+                l <<= w;
+            }
+        }
+        l |= (uint64_t)c[order[k]];
+    }
+    *hi = h;
+    *lo = l;
+}
+
+/* Axis order by increasing entropy of the m_d distributions of nseq sequences
+ * (m is nseq x 3). */
+void oracle_axis_order(const uint32_t *m, uint64_t nseq, int order[3], double ent[3])
+{
+    for (int d = 0; d < 3; d++) {
+        uint64_t cnt[32] = {0};
+        for (uint64_t k = 0; k < nseq; k++) cnt[m[3 * k + d] & 31]++;
+        double h = 0.0;
+        for (int v = 0; v < 32; v++)
+            if (cnt[v]) {
+                double pr = (double)cnt[v] / (double)nseq;
+                h -= pr * log2(pr);
+            }
+        ent[d] = h;
+        order[d] = d;
+    }
+    for (int i = 1; i < 3; i++)
+        for (int j = i; j > 0 && ent[order[j]] < ent[order[j - 1]] - 1e-9; j--) {
+            int t = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = t;
+        }
+}
+
+typedef struct {
+    uint64_t hi, lo, pos; /* R-index, then the particle's place in its sequence */
+} rkey;
+
+static int rkey_cmp(const void *a, const void *b)
+{
+    const rkey *x = a, *y = b;
+    if (x->hi != y->hi) return x->hi < y->hi ? -1 : 1;
+    if (x->lo != y->lo) return x->lo < y->lo ? -1 : 1;
+    return x->pos < y->pos ? -1 : (x->pos > y->pos);
+}
+
+typedef struct {
+    uint32_t key;
+    uint64_t seq;
+} skey;
+
+static int skey_cmp(const void *a, const void *b)
+{
+    const skey *x = a, *y = b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->seq < y->seq ? -1 : (x->seq > y->seq);
+}
+
+int oracle_reorder(const uint8_t *st, uint64_t bytes, const uint64_t *perm_in, uint8_t **out, uint64_t *out_bytes,
+                   uint64_t *perm_out, int order_out[3])
+{
+    *out = NULL;
+    *out_bytes = 0;
+    uint64_t n, nl, nw;
+    int dtype;
+    int rc = oracle_stream_header(st, bytes, &n, &dtype, &nl, &nw);
+    if (rc) return rc;
+    const uint8_t *tab = st + OR_HEADER_BYTES;
+    const uint8_t *pay = tab + OR_LEAF_BYTES * nl;
+    uint32_t *words = malloc((nw ? nw : 1) * sizeof(uint32_t));
+    uint32_t *nwords = calloc(nw ? nw : 1, sizeof(uint32_t));
+    uint32_t *m = malloc((nl ? nl : 1) * 3 * sizeof(uint32_t));
+    uint64_t *po = malloc((nl + 1) * sizeof(uint64_t)), *wo = malloc((nl ? nl : 1) * sizeof(uint64_t));
+    skey *sk = malloc((nl ? nl : 1) * sizeof(skey));
+    uint32_t *codes = malloc((n ? n : 1) * 3 * sizeof(uint32_t));
+    rkey *rk = malloc((n ? n : 1) * sizeof(rkey));
+    uint8_t *buf = malloc(bytes);
+    rc = OR_ERR_NOMEM;
+    if (!words || !nwords || !m || !po || !wo || !sk || !codes || !rk || !buf) goto done;
+    for (uint64_t w = 0; w < nw; w++) words[w] = get_u32(pay + 4 * w);
+    rc = OR_ERR_CORRUPT;
+    for (uint64_t L = 0; L < nl; L++) {
+        const uint8_t *rec = tab + OR_LEAF_BYTES * L;
+        po[L] = get_u64(rec);
+        wo[L] = get_u64(rec + 8);
+        for (int d = 0; d < 3; d++) m[3 * L + d] = rec[28 + d];
+        if (m[3 * L] > 31 || m[3 * L + 1] > 31 || m[3 * L + 2] > 31) goto done;
+    }
+    po[nl] = n;
+    for (uint64_t L = 0; L < nl; L++) {
+        if (po[L + 1] <= po[L]) goto done;
+        uint64_t cnt = po[L + 1] - po[L];
+        uint64_t need = wo[L] + (((uint64_t)(m[3 * L] + m[3 * L + 1] + m[3 * L + 2]) * (cnt - 1) + 31) / 32);
+        if (need > nw) goto done;
+        uint64_t bitpos = 32 * wo[L];
+        for (uint64_t i = 1; i < cnt; i++)
+            for (int d = 0; d < 3; d++) {
+                uint32_t md = m[3 * L + d];
+                codes[3 * (po[L] + i) + d] = md ? (uint32_t)read_bits(words, bitpos, md) : 0u;
+                bitpos += md;
+            }
+    }
+    int order[3];
+    double ent[3];
+    oracle_axis_order(m, nl, order, ent);
+    for (int d = 0; d < 3; d++) order_out[d] = order[d];
+    for (uint64_t L = 0; L < nl; L++) {
+        sk[L].key = m[3 * L] + m[3 * L + 1] + m[3 * L + 2];
+        sk[L].seq = L;
+    }
+    qsort(sk, nl, sizeof(skey), skey_cmp);
+    memcpy(buf, st, OR_HEADER_BYTES);
+    uint64_t off = 0, woff = 0;
+    for (uint64_t k = 0; k < nl; k++) {
+        uint64_t L = sk[k].seq, cnt = po[L + 1] - po[L];
+        const uint8_t *rec = tab + OR_LEAF_BYTES * L;
+        uint8_t *nrec = buf + OR_HEADER_BYTES + OR_LEAF_BYTES * k;
+        memcpy(nrec, rec, OR_LEAF_BYTES);
+        put_u64(nrec, off);
+        put_u64(nrec + 8, woff);
+        /* the centre stays first; the others by R-index, then place */
+        for (uint64_t i = 1; i < cnt; i++) {
+            oracle_rindex(codes + 3 * (po[L] + i), m + 3 * L, order, &rk[i].hi, &rk[i].lo);
+            rk[i].pos = i;
+        }
+        qsort(rk + 1, cnt - 1, sizeof(rkey), rkey_cmp);
+        if (perm_out) perm_out[off] = perm_in ? perm_in[po[L]] : po[L];
+        uint64_t bitpos = 32 * woff;
+        for (uint64_t i = 1; i < cnt; i++) {
+            uint64_t src = po[L] + rk[i].pos;
+            if (perm_out) perm_out[off + i] = perm_in ? perm_in[src] : src;
+            for (int d = 0; d < 3; d++) {
+                uint32_t md = m[3 * L + d];
+                if (md) write_bits(nwords, &bitpos, codes[3 * src + d], md);
+            }
+        }
+        off += cnt;
+        woff += ((uint64_t)(m[3 * L] + m[3 * L + 1] + m[3 * L + 2]) * (cnt - 1) + 31) / 32;
+    }
+    for (uint64_t w = 0; w < nw; w++) put_u32(buf + OR_HEADER_BYTES + OR_LEAF_BYTES * nl + 4 * w, nwords[w]);
+    *out = buf;
+    buf = NULL;
+    *out_bytes = bytes;
+    rc = OR_OK;
+done:
+    free(words);
+    free(nwords);
+    free(m);
+    free(po);
+    free(wo);
+    free(sk);
+    free(codes);
+    free(rk);
+    free(buf);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Step 6: decoding (Sec. 3).  The reconstruction of code q on axis d is     */
 /* (T)(o_d + s*q): one double multiply, one double add, one rounding to T.   */
 /* ------------------------------------------------------------------------ */
