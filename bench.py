@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--leaf-size", type=int, default=4096)
     ap.add_argument("--reduce", action="store_true",
                     help="compress with the bit-box reduction (Sec. 4.1, Alg. 1) in place of plain leaves")
+    ap.add_argument("--reorder", action="store_true",
+                    help="reorder sequences by sum m_d and particles by R-index (Sec. 4.2) before packing")
+    ap.add_argument("--lossless", action="store_true",
+                    help="after the timed steps, compress the stream once more on the host with zlib (DEFLATE: "
+                         "LZ77 + Huffman, standing in for Huffman + ZSTD) and report that ratio separately")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -216,35 +221,29 @@ def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False, launches
     }.get(kernel)
 
 
-def oracle_round_trip(pos, mode, eb, leaf_size, reduce=False):
+def oracle_round_trip(pos, mode, eb, leaf_size, reduce=False, reorder=False, parallel=False):
     import oracle
 
     m = oracle.REL if mode == "rel" else oracle.ABS
     if reduce:
-        stream, _, _ = oracle.compress_reduced(pos, m, eb, leaf_size=leaf_size, want_perm=False)
+        stream, _, _ = oracle.compress_reduced(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=parallel)
     else:
-        stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False)
-    oracle.decompress(stream)
+        stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=parallel)
+    if reorder:
+        stream, _, _ = oracle.reorder(stream)
+    oracle.decompress(stream, parallel=parallel)
     return len(stream)
 
 
-def oracle_round_trip_parallel(pos, mode, eb, leaf_size, reduce=False):
-    import oracle
-
-    m = oracle.REL if mode == "rel" else oracle.ABS
-    if reduce:
-        stream, _, _ = oracle.compress_reduced(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=True)
-    else:
-        stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=True)
-    oracle.decompress(stream, parallel=True)
-    return len(stream)
+def oracle_round_trip_parallel(pos, mode, eb, leaf_size, reduce=False, reorder=False):
+    return oracle_round_trip(pos, mode, eb, leaf_size, reduce, reorder, parallel=True)
 
 
-def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False):
+def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False, reorder=False):
     gen, n, dtype, mode, eb = spec
     pos = generate(gen, n_sample, dtype, seed=0)
     t0 = time.perf_counter()
-    oracle_round_trip(pos, mode, eb, leaf_size, reduce)
+    oracle_round_trip(pos, mode, eb, leaf_size, reduce, reorder)
     dt = time.perf_counter() - t0
     out = {"value": round(pos.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
            "sample": f"{n_sample} particles of the {gen} generator ({dtype}, {mode} eb {eb}), one compress + "
@@ -254,9 +253,9 @@ def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False):
 
     oracle.build(parallel=True)
     big = generate(gen, (1 if reduce else 4) * n_sample, dtype, seed=0)
-    oracle_round_trip_parallel(big[: 1 << 16], mode, eb, leaf_size, reduce)  # thread pool start-up
+    oracle_round_trip_parallel(big[: 1 << 16], mode, eb, leaf_size, reduce, reorder)  # thread pool start-up
     t0 = time.perf_counter()
-    oracle_round_trip_parallel(big, mode, eb, leaf_size, reduce)
+    oracle_round_trip_parallel(big, mode, eb, leaf_size, reduce, reorder)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out["parallel"] = {"value": round(big.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": cores,
@@ -264,6 +263,8 @@ def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False):
                        "sample": f"{big.shape[0]} particles, one compress + decompress in {dt:.2f} s"}
     if reduce:
         out["sample"] += " (bit-box reduction)"
+    if reorder:
+        out["sample"] += " (reordered)"
     return out
 
 
@@ -278,11 +279,11 @@ def run_reference(args, spec):
     oracle.build()
     samples = [generate(gen, REF_SAMPLE, dtype, seed=s) for s in range(2)]
     for i in range(args.warmup):
-        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce)
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce, args.reorder)
     times = []
     for i in range(args.steps):
         t0 = time.perf_counter()
-        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce)
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce, args.reorder)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     units = samples[0].nbytes * args.steps
@@ -292,7 +293,7 @@ def run_reference(args, spec):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": args.workload, "sample_particles_per_step": REF_SAMPLE, "leaf_size": args.leaf_size,
-                   "box_reduction": bool(args.reduce),
+                   "box_reduction": bool(args.reduce), "reorder": bool(args.reorder),
                    "note": "the oracle (plain single-threaded C, double precision) on host cores"},
         "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{REF_SAMPLE} particles of the {gen} generator per step"},
@@ -322,7 +323,7 @@ def run_ours(args, spec):
     emode = pc.PC_EB_REL if mode == "rel" else pc.PC_EB_ABS
     esz = 4 if dtype == "f32" else 8
     pos = torch.from_numpy(pos_h).to(dev)
-    cfg = pc.config(args.leaf_size, reduce=args.reduce)
+    cfg = pc.config(args.leaf_size, reduce=args.reduce, reorder=args.reorder)
     comp = pc.Compressor(n, pdt, leaf_size=cfg, device=dev)
     dec = torch.empty_like(pos)
 
@@ -403,9 +404,21 @@ def run_ours(args, spec):
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
         e2e = measure_e2e(pc, pos_h, pdt, emode, eb, args, world, cfg)
+    lossless = None
+    if rank == 0 and args.lossless:
+        import zlib
+
+        data = comp.out[:size].cpu().numpy().tobytes()
+        t0 = time.perf_counter()
+        z = len(zlib.compress(data, 6))
+        lossless = {"codec": "zlib level 6 on the host (DEFLATE: LZ77 + Huffman)", "stream_bytes": int(size),
+                    "coded_bytes": z, "ratio_over_stream": round(size / z, 4),
+                    "compression_ratio_after": round(nbytes / z, 4), "seconds": round(time.perf_counter() - t0, 2),
+                    "timed": False}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(spec, args.leaf_size, CPU_SAMPLE // 4 if args.reduce else CPU_SAMPLE, args.reduce)
+        cpu = cpu_baseline(spec, args.leaf_size, CPU_SAMPLE // 4 if args.reduce else CPU_SAMPLE, args.reduce,
+                           args.reorder)
 
     if rank == 0:
         line = {
@@ -414,6 +427,7 @@ def run_ours(args, spec):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "generator": gen, "particles": n, "eb_mode": mode, "eb": eb,
                        "leaf_size": args.leaf_size, "box_reduction": bool(args.reduce),
+                       "reorder": bool(args.reorder),
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)", "code_bytes": cb},
             "compress_gbs": round(whole_job_gbs(world, nbytes, args.steps, comp_ms), 3),
@@ -423,6 +437,8 @@ def run_ours(args, spec):
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
             "e2e": e2e, "cpu_baseline": cpu,
         }
+        if lossless:
+            line["lossless"] = lossless
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

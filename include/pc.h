@@ -76,7 +76,7 @@ typedef enum { PC_EB_ABS = 0, PC_EB_REL = 1 } pc_eb_mode;
 typedef struct {
     uint32_t leaf_size; /* r of Sec. 4.1: largest leaf; 0 = 4096; valid 1..PC_MAX_LEAF_SIZE.
                            With PC_FLAG_AUTOTUNE_LEAF: the largest candidate (0 = PC_MAX_LEAF_SIZE) */
-    uint32_t flags;     /* 0, or PC_FLAG_AUTOTUNE_LEAF and/or PC_FLAG_BOX_REDUCTION */
+    uint32_t flags;     /* 0, or any of PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION, PC_FLAG_REORDER */
 } pc_config;
 
 /* Leaf-size autotuning (no counterpart in the paper, which fixes r by hand,
@@ -108,6 +108,18 @@ typedef struct {
  * Combined with PC_FLAG_AUTOTUNE_LEAF, the leaf size is chosen first (on the
  * plain stream size) and the reduction runs on those leaves. */
 #define PC_FLAG_BOX_REDUCTION 2u
+
+/* Reordering for an entropy coder (Sec. 4.2, after Fig. 4): the sequences
+ * (leaves, or the reduction's sequences) are written in increasing order of
+ * m_x + m_y + m_z, and the particles of each sequence, centre first, in
+ * increasing order of their R-index: the particle's three codes joined, most
+ * significant first, in the order of the axes' entropy levels (the entropy of
+ * the distribution of m_d over all sequences, lowest first; entropies within
+ * 1e-9 keep x, y, z order).  Equal keys keep their previous order.  The stream
+ * format, its size and the decoder are unchanged (the decoded set is the
+ * same, in another order; perm follows it).  The paper then entropy-codes the
+ * stream (Huffman, ZSTD); that step is not part of this library. */
+#define PC_FLAG_REORDER 4u
 #define PC_AUTOTUNE_MIN_LEAF 64u
 
 #define PC_DEFAULT_LEAF_SIZE 4096u

@@ -477,6 +477,7 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
     else
       k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs);
   }
+  if (a.box_only) return cudaGetLastError();
   {
     TraceScope ts("k_leafscan", st);
     if (a.num_leaves <= kScanSlice) {

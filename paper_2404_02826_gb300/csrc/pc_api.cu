@@ -8,6 +8,7 @@
 #include "../../include/pc.h"
 #include "pc_internal.cuh"
 #include "pc_reduce.cuh"
+#include "pc_reorder.cuh"
 
 namespace pcx {
 
@@ -75,7 +76,8 @@ struct Plan {
   uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_err = 0, off_total = 0;
   uint64_t off_groups = 0, off_slices = 0;
   uint64_t off_reduce = 0, off_seqrec = 0;  // bit-box reduction: its scratch and the sequence records
-  bool reduce = false;
+  uint64_t off_rorecs = 0, off_roscratch = 0;  // reordering: the records in the new order, its scratch
+  bool reduce = false, reorder = false;
   bool tune = false;  // leaf size chosen by descending from r_hi while the stream shrinks (sized for r)
   uint32_t r_hi = 0;
   int tune_first = 0, tune_last = 0;  // candidate depths
@@ -123,8 +125,9 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   uint32_t r = PC_DEFAULT_LEAF_SIZE;
   p.tune = false;
   if (cfg) {
-    if (cfg->flags & ~(PC_FLAG_AUTOTUNE_LEAF | PC_FLAG_BOX_REDUCTION)) return PC_ERR_ARG;
+    if (cfg->flags & ~(PC_FLAG_AUTOTUNE_LEAF | PC_FLAG_BOX_REDUCTION | PC_FLAG_REORDER)) return PC_ERR_ARG;
     p.reduce = (cfg->flags & PC_FLAG_BOX_REDUCTION) != 0;
+    p.reorder = (cfg->flags & PC_FLAG_REORDER) != 0;
     if (cfg->leaf_size) r = cfg->leaf_size;
     if (cfg->flags & PC_FLAG_AUTOTUNE_LEAF) {
       // candidates: depths d with ceil(n / 2^d) in [min(PC_AUTOTUNE_MIN_LEAF, max), max]
@@ -192,6 +195,14 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
     o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafRec));
     p.off_reduce = o;
     o = align_up(o + reduce_scratch_bytes(n, p.num_leaves));
+  }
+  if (p.reorder) {
+    // a sequence holds at most r particles (the largest candidate when tuning), any number after the reduction
+    const uint64_t most = p.reduce ? n : (p.tune ? p.r_hi : p.r);
+    p.off_rorecs = o;
+    o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafRec));
+    p.off_roscratch = o;
+    o = align_up(o + reorder_scratch_bytes(p.num_leaves, most < n ? most : n));
   }
   // zeroed region
   p.off_zero = o;
@@ -385,7 +396,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     const int levels = p.tune ? p.tune_last : p.levels;
     // a4-a5 on the arrangement at depth `depth` (leaves = its 2^depth nodes when split_level = depth - 1)
     auto leaf_launch = [&](void *const *codes, const uint32_t *idxs, int split_level, uint32_t r,
-                           uint64_t num_leaves, bool cost_only) {
+                           uint64_t num_leaves, bool cost_only, bool box_only = false) {
       LeafLaunch lf = {};
       lf.n = n;
       lf.split_level = split_level;
@@ -400,7 +411,49 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
       lf.slice_tot = reinterpret_cast<uint64_t *>(ws + p.off_slices);
       lf.cost_only = cost_only;
+      lf.box_only = box_only;
       return launch_leaves(lf, st);
+    };
+    // a5 from ready records: payload offsets and packing, after the reordering
+    // when asked (from `codes` into `spare`, Sec. 4.2)
+    auto pack_ready = [&](LeafRec *recs, uint64_t num_seq, void *const *codes, uint32_t *idxs, void *const *spare,
+                          uint32_t *spare_idx, uint32_t r) -> int {
+      if (p.reorder) {
+        ReorderLaunch ro = {};
+        ro.n = n;
+        ro.code_bytes = cb;
+        ro.num_seq = num_seq;
+        ro.recs = recs;
+        ro.out_recs = reinterpret_cast<LeafRec *>(ws + p.off_rorecs);
+        for (int d = 0; d < 3; ++d) {
+          ro.codes[d] = codes[d];
+          ro.out_codes[d] = spare[d];
+        }
+        ro.idx = idxs;
+        ro.out_idx = idxs ? spare_idx : nullptr;
+        const uint64_t most = p.reduce ? n : (p.tune ? p.r_hi : p.r);
+        ro.max_cnt = most < n ? most : n;
+        ro.scratch = ws + p.off_roscratch;
+        PC_TRY(launch_reorder(ro, st));
+        recs = ro.out_recs;
+        codes = spare;
+        idxs = ro.out_idx;
+      }
+      LeafLaunch lf = {};
+      lf.n = n;
+      lf.code_bytes = cb;
+      lf.leaf_size = r;
+      lf.num_leaves = num_seq;
+      for (int d = 0; d < 3; ++d) lf.codes[d] = codes[d];
+      lf.idx = idxs;
+      lf.out = static_cast<uint8_t *>(out);
+      lf.perm = perm;
+      lf.recs = recs;
+      lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
+      lf.slice_tot = reinterpret_cast<uint64_t *>(ws + p.off_slices);
+      lf.recs_ready = true;
+      PC_TRY(launch_leaves(lf, st));
+      return PC_OK;
     };
     // autotuning: stream bytes of the leaves at `depth` (every node there is a leaf)
     auto depth_cost = [&](void *const *codes, int depth, uint64_t *bytes) -> int {
@@ -516,28 +569,24 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       rl.err = err;
       uint64_t num_seq = 0, rounds = 0;
       PC_TRY(launch_reduce(rl, st, &num_seq, &rounds));
-      LeafLaunch lf = {};
-      lf.n = n;
-      lf.split_level = split_level;
-      lf.code_bytes = cb;
-      lf.leaf_size = r;
-      lf.num_leaves = num_seq;
-      for (int d = 0; d < 3; ++d) lf.codes[d] = spare[d];
-      lf.idx = rl.out_idx;
-      lf.out = static_cast<uint8_t *>(out);
-      lf.perm = perm;
-      lf.recs = rl.seqs;
-      lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
-      lf.slice_tot = reinterpret_cast<uint64_t *>(ws + p.off_slices);
-      lf.recs_ready = true;
-      PC_TRY(launch_leaves(lf, st));
       hl.num_leaves = num_seq;
-      return PC_OK;
+      // the leaf-ordered arrangement is free now: the reordering may write into it
+      return pack_ready(rl.seqs, num_seq, spare, rl.out_idx, codes, const_cast<uint32_t *>(idxs), r);
+    };
+    // the leaves' bit boxes, then reordering and packing
+    auto reorder_launch = [&](void *const *codes, uint32_t *idxs, void *const *spare, uint32_t *spare_idx,
+                              int split_level, uint32_t r, uint64_t num_leaves) -> int {
+      PC_TRY(leaf_launch(codes, idxs, split_level, r, num_leaves, false, true));
+      return pack_ready(reinterpret_cast<LeafRec *>(ws + p.off_leafrec), num_leaves, codes, idxs, spare, spare_idx,
+                        r);
     };
     // a4-a5: bit boxes, payload offsets, packing
     if (!p.tune) {
       if (p.reduce) {
         rc = reduce_launch(src, isrc, dst, idst, levels - 1, p.r, p.num_leaves);
+        if (rc) return rc;
+      } else if (p.reorder) {
+        rc = reorder_launch(src, isrc, dst, idst, levels - 1, p.r, p.num_leaves);
         if (rc) return rc;
       } else {
         PC_TRY(leaf_launch(src, isrc, levels - 1, p.r, p.num_leaves, false));
@@ -564,6 +613,10 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       if (p.reduce) {
         rc = reduce_launch(codes, idxs, deepest ? dst : src, deepest ? idst : isrc, depth - 1, uint32_t(r),
                            1ull << depth);
+        if (rc) return rc;
+      } else if (p.reorder) {
+        rc = reorder_launch(codes, idxs, deepest ? dst : src, deepest ? idst : isrc, depth - 1, uint32_t(r),
+                            1ull << depth);
         if (rc) return rc;
       } else {
         PC_TRY(leaf_launch(codes, idxs, depth - 1, uint32_t(r), 1ull << depth, false));

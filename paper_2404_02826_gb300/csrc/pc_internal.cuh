@@ -185,6 +185,7 @@ struct LeafLaunch {
   uint64_t *slice_tot;      // [ceil(num_leaves / 8192)] scratch of the many-leaf word scan
   bool cost_only;           // bit boxes and payload words only (leaf-size autotuning)
   bool recs_ready;          // recs already hold off, cnt, centre, m, q_ref, words (the box reduction's sequences)
+  bool box_only;            // leaf table and bit boxes only (the records are reordered before packing)
 };
 cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st);
 // The leaf ranges alone (off, cnt of every leaf; the other fields zero).
