@@ -14,8 +14,11 @@
 //               counts in the new order) and the records;
 //   k_ro_sort   a block per sequence: keys R-index << 32 | position sorted in
 //               shared memory (bitonic), then the codes and indices moved;
-//               sequences too large for shared memory go to k_ro_sort_big, one
-//               block sorting them one after the other in global memory.
+//               longer sequences with 8-byte keys are merge-sorted in global
+//               memory (k_ro_big_*: runs of kSmemSort keys sorted in shared
+//               memory, then merged pairwise, each key finding its place in the
+//               other run by binary search); longer ones with 16-byte keys go
+//               to k_ro_sort_big, one block sorting them one after the other.
 #include <cstdint>
 
 #include "pc_internal.cuh"
@@ -26,7 +29,8 @@ namespace {
 
 constexpr int kSums = 94;            // sum of m_d: 0 .. 93
 constexpr int kRankThreads = 256;
-constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory (16 bytes each)
+constexpr uint32_t kSmemSort = 16384;  // keys sorted in shared memory: 8-byte keys (128 KB)
+constexpr uint32_t kSmemWide = 8192;   // 16-byte keys (128 KB)
 constexpr int kSortThreads = 1024;
 
 struct RoPlan {
@@ -34,13 +38,16 @@ struct RoPlan {
   uint32_t hist_sum[kSums];
   uint32_t start[kSums];
   uint32_t max_cnt;
+  uint32_t nbig;   // sequences left to k_ro_sort_big (16-byte keys)
+  uint32_t nbign;  // sequences left to the k_ro_big_* merge sort (8-byte keys)
   int32_t order[3];
+  unsigned long long big_keys, big_runs;  // keys and runs of the merge sort
 };
 
 inline uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
 
 struct RoLayout {
-  uint64_t plan, seq_at, off, big, total;
+  uint64_t plan, seq_at, off, big_list, big_list_n, kbase, rbase, keys_a, keys_b, big, total;
 };
 constexpr int kScanThreads = 1024;
 
@@ -50,7 +57,7 @@ uint64_t next_pow2(uint64_t x) {
   return p;
 }
 
-RoLayout ro_layout(uint64_t num_seq, uint64_t max_cnt) {
+RoLayout ro_layout(uint64_t n, uint64_t num_seq, uint64_t max_cnt) {
   RoLayout L = {};
   uint64_t o = 0;
   L.plan = o;
@@ -59,8 +66,20 @@ RoLayout ro_layout(uint64_t num_seq, uint64_t max_cnt) {
   o = align256(o + 4 * (num_seq ? num_seq : 1));
   L.off = o;
   o = align256(o + 4 * (num_seq ? num_seq : 1));
-  L.big = o;  // global keys of a sequence above kSmemSort particles
-  const uint64_t big = max_cnt > kSmemSort + 1 ? next_pow2(max_cnt - 1) : 1;
+  L.big_list = o;  // [num_seq] 16-byte-key sequences, then [num_seq] 8-byte-key ones
+  o = align256(o + 8 * (num_seq ? num_seq : 1));
+  L.big_list_n = L.big_list;
+  L.kbase = o;  // first key of each merge-sorted sequence, then its first run (u64 each, one more than sequences)
+  o = align256(o + 8 * (num_seq + 1));
+  L.rbase = o;
+  o = align256(o + 8 * (num_seq + 1));
+  const uint64_t merge_keys = max_cnt > kSmemSort + 1 ? n : 1;  // the merge-sorted keys, at most all particles
+  L.keys_a = o;
+  o = align256(o + 8 * merge_keys);
+  L.keys_b = o;
+  o = align256(o + 8 * merge_keys);
+  L.big = o;  // global keys of a 16-byte-key sequence too long for shared memory
+  const uint64_t big = max_cnt > kSmemWide + 1 ? next_pow2(max_cnt - 1) : 1;
   o = align256(o + 16 * big);
   L.total = o;
   return L;
@@ -68,6 +87,19 @@ RoLayout ro_layout(uint64_t num_seq, uint64_t max_cnt) {
 
 __device__ __forceinline__ uint32_t m_of(const LeafRec &r, int d) { return (r.m >> (8 * d)) & 0xffu; }
 __device__ __forceinline__ uint32_t msum(const LeafRec &r) { return m_of(r, 0) + m_of(r, 1) + m_of(r, 2); }
+// Bits of a position within the sequence (positions < cnt).
+__device__ __forceinline__ uint32_t pos_bits(uint32_t cnt) {
+  uint32_t b = 1;
+  while ((1u << b) < cnt) ++b;
+  return b;
+}
+// Do the R-index and the position fit one 64-bit key?
+__device__ __forceinline__ bool narrow_keys(const LeafRec &r) { return msum(r) + pos_bits(r.cnt) <= 64; }
+// Sorted by k_ro_sort (shared memory) rather than k_ro_sort_big?
+__device__ __forceinline__ bool fits_smem(const LeafRec &r, uint32_t cap) {
+  const uint32_t L = r.cnt - 1;
+  return narrow_keys(r) ? L <= cap : L <= (cap < kSmemWide ? cap : kSmemWide);
+}
 
 __global__ void k_ro_stats(const LeafRec *__restrict__ recs, uint64_t num_seq, RoPlan *plan) {
   __shared__ uint32_t hm[3][32], hs[kSums];
@@ -346,6 +378,27 @@ __device__ void sort_narrow(const LeafRec &r, uint32_t P, uint32_t pbits, const 
   __syncthreads();
 }
 
+// The same for more keys than the block's registers hold: all in shared memory.
+template <typename C>
+__device__ void sort_narrow_smem(const LeafRec &r, uint32_t P, uint32_t pbits, const int32_t order[3], const C *q0,
+                                 const C *q1, const C *q2, unsigned long long *sm) {
+  const uint32_t L = r.cnt - 1;
+  for (uint32_t e = threadIdx.x; e < P; e += blockDim.x) {
+    unsigned long long v = ~0ull;
+    if (e < L) {
+      const uint32_t p = e < r.centre ? e : e + 1;
+      uint32_t q[3];
+      load_q(q0, q1, q2, uint64_t(r.off) + p, q);
+      unsigned long long h, l;
+      rkey(q, r, order, p, h, l);
+      v = (((h << 32) | (l >> 32)) << pbits) | p;
+    }
+    sm[e] = v;
+  }
+  __syncthreads();
+  block_bitonic64(sm, P);
+}
+
 // Sorts sequence j's keys in kh/kl (capacity P) and moves its particles.  When
 // the R-index and the position fit in 64 bits together (sum m_d + bits of the
 // count <= 64) the keys are R-index << pbits | position in kl alone.
@@ -397,21 +450,32 @@ __global__ void __launch_bounds__(kSortThreads) k_ro_sort(const LeafRec *__restr
                                                           const uint32_t *__restrict__ seq_at,
                                                           const uint32_t *__restrict__ off, const RoPlan *plan,
                                                           const C *q0, const C *q1, const C *q2, const uint32_t *idx,
-                                                          C *o0, C *o1, C *o2, uint32_t *oidx, uint32_t cap) {
-  extern __shared__ unsigned long long keys[];  // [2][cap]
+                                                          C *o0, C *o1, C *o2, uint32_t *oidx, uint32_t cap,
+                                                          RoPlan *wplan, uint32_t *big_list) {
+  extern __shared__ unsigned long long keys[];
   const int32_t order[3] = {plan->order[0], plan->order[1], plan->order[2]};
   for (uint64_t j = blockIdx.x; j < num_seq; j += gridDim.x) {
     const LeafRec r = recs[seq_at[j]];
     const uint32_t L = r.cnt - 1;
-    if (L > cap) continue;  // k_ro_sort_big
+    if (!fits_smem(r, cap)) {  // left to the merge sort or to k_ro_sort_big
+      if (threadIdx.x == 0) {
+        if (narrow_keys(r))
+          big_list[num_seq + atomicAdd(&wplan->nbign, 1u)] = uint32_t(j);
+        else
+          big_list[atomicAdd(&wplan->nbig, 1u)] = uint32_t(j);
+      }
+      continue;
+    }
     uint32_t P = 1;
     while (P < L) P <<= 1;
-    uint32_t pbits = 1;
-    while ((1u << pbits) < r.cnt) ++pbits;
-    if (msum(r) + pbits <= 64 && P <= E * blockDim.x) {
-      // narrow keys in registers (padded to a warp's worth at least)
+    const uint32_t pbits = pos_bits(r.cnt);
+    if (narrow_keys(r)) {
+      // narrow keys: in registers (padded to a warp's worth at least), or all in shared memory
       const uint32_t Pw = P < 32u * E ? 32u * E : P;
-      sort_narrow<E, C>(r, Pw, pbits, order, q0, q1, q2, keys);
+      if (Pw <= E * blockDim.x)
+        sort_narrow<E, C>(r, Pw, pbits, order, q0, q1, q2, keys);
+      else
+        sort_narrow_smem<C>(r, P, pbits, order, q0, q1, q2, keys);
       const unsigned long long pmask = (1ull << pbits) - 1;
       const uint32_t dst = off[j];
       for (uint32_t i = threadIdx.x; i <= L; i += blockDim.x) {
@@ -424,7 +488,8 @@ __global__ void __launch_bounds__(kSortThreads) k_ro_sort(const LeafRec *__restr
       }
       __syncthreads();
     } else {
-      sort_one<C, IDX>(r, off[j], order, q0, q1, q2, idx, o0, o1, o2, oidx, keys, keys + cap, P);
+      const uint32_t capw = cap < kSmemWide ? cap : kSmemWide;
+      sort_one<C, IDX>(r, off[j], order, q0, q1, q2, idx, o0, o1, o2, oidx, keys, keys + capw, P);
     }
   }
 }
@@ -435,12 +500,13 @@ __global__ void __launch_bounds__(kSortThreads) k_ro_sort_big(const LeafRec *__r
                                                               const uint32_t *__restrict__ off, const RoPlan *plan,
                                                               const C *q0, const C *q1, const C *q2,
                                                               const uint32_t *idx, C *o0, C *o1, C *o2, uint32_t *oidx,
-                                                              uint32_t cap, unsigned long long *big, uint64_t big_cap) {
+                                                              uint32_t cap, unsigned long long *big, uint64_t big_cap,
+                                                              const uint32_t *big_list) {
   const int32_t order[3] = {plan->order[0], plan->order[1], plan->order[2]};
-  for (uint64_t j = 0; j < num_seq; ++j) {
+  for (uint32_t b = 0; b < plan->nbig; ++b) {
+    const uint32_t j = big_list[b];
     const LeafRec r = recs[seq_at[j]];
     const uint32_t L = r.cnt - 1;
-    if (L <= cap) continue;
     uint32_t P = 1;
     while (P < L) P <<= 1;
     if (P > big_cap) continue;  // sized for the largest sequence: cannot happen
@@ -448,9 +514,144 @@ __global__ void __launch_bounds__(kSortThreads) k_ro_sort_big(const LeafRec *__r
   }
 }
 
+// ---- merge sort of the long sequences with 8-byte keys --------------------
+
+// Index b of the sequence whose range [base[b], base[b + 1]) holds t.
+__device__ __forceinline__ uint32_t find_range(const unsigned long long *base, uint32_t count, unsigned long long t) {
+  uint32_t lo = 0, hi = count;  // base[lo] <= t < base[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (base[mid] <= t)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// One block: first key and first run of every long sequence.
+__global__ void __launch_bounds__(1024) k_ro_big_plan(const LeafRec *__restrict__ recs, const uint32_t *seq_at,
+                                                      const uint32_t *list, RoPlan *plan, unsigned long long *kbase,
+                                                      unsigned long long *rbase) {
+  if (threadIdx.x != 0) return;
+  unsigned long long k = 0, r = 0;
+  for (uint32_t b = 0; b < plan->nbign; ++b) {
+    const uint32_t L = recs[seq_at[list[b]]].cnt - 1;
+    kbase[b] = k;
+    rbase[b] = r;
+    k += L;
+    r += (L + kSmemSort - 1) / kSmemSort;
+  }
+  kbase[plan->nbign] = k;
+  rbase[plan->nbign] = r;
+  plan->big_keys = k;
+  plan->big_runs = r;
+}
+
+__global__ void k_ro_big_keys(const LeafRec *__restrict__ recs, const uint32_t *seq_at, const uint32_t *list,
+                              const RoPlan *plan, const unsigned long long *kbase, const void *c0, const void *c1,
+                              const void *c2, int code_bytes, unsigned long long *keys) {
+  const int32_t order[3] = {plan->order[0], plan->order[1], plan->order[2]};
+  const unsigned long long T = plan->big_keys;
+  for (unsigned long long t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < T;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t b = find_range(kbase, plan->nbign, t);
+    const LeafRec r = recs[seq_at[list[b]]];
+    const uint32_t e = uint32_t(t - kbase[b]);
+    const uint32_t p = e < r.centre ? e : e + 1;
+    uint32_t q[3];
+    if (code_bytes == 2)
+      load_q(static_cast<const uint16_t *>(c0), static_cast<const uint16_t *>(c1),
+             static_cast<const uint16_t *>(c2), uint64_t(r.off) + p, q);
+    else
+      load_q(static_cast<const uint32_t *>(c0), static_cast<const uint32_t *>(c1),
+             static_cast<const uint32_t *>(c2), uint64_t(r.off) + p, q);
+    unsigned long long h, l;
+    rkey(q, r, order, p, h, l);
+    keys[t] = (((h << 32) | (l >> 32)) << pos_bits(r.cnt)) | p;
+  }
+}
+
+// A block per run of up to kSmemSort keys: sorted in shared memory.
+__global__ void __launch_bounds__(kSortThreads) k_ro_big_runs(const LeafRec *__restrict__ recs, const uint32_t *seq_at,
+                                                              const uint32_t *list, const RoPlan *plan,
+                                                              const unsigned long long *kbase,
+                                                              const unsigned long long *rbase,
+                                                              unsigned long long *keys) {
+  extern __shared__ unsigned long long sm[];
+  const unsigned long long R = plan->big_runs;
+  for (unsigned long long g = blockIdx.x; g < R; g += gridDim.x) {
+    const uint32_t b = find_range(rbase, plan->nbign, g);
+    const uint32_t L = recs[seq_at[list[b]]].cnt - 1;
+    const uint32_t k0 = uint32_t(g - rbase[b]) * kSmemSort;
+    const uint32_t len = min(kSmemSort, L - k0);
+    uint32_t P = 1;
+    while (P < len) P <<= 1;
+    unsigned long long *run = keys + kbase[b] + k0;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sm[i] = i < len ? run[i] : ~0ull;
+    __syncthreads();
+    block_bitonic64(sm, P);
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) run[i] = sm[i];
+    __syncthreads();
+  }
+}
+
+// Runs of w keys merged pairwise into runs of 2w: a key's place is its place
+// in its run plus the number of smaller keys in the other run (keys differ).
+__global__ void k_ro_big_merge(const LeafRec *__restrict__ recs, const uint32_t *seq_at, const uint32_t *list,
+                               const RoPlan *plan, const unsigned long long *kbase, const unsigned long long *in,
+                               unsigned long long *out, uint32_t w) {
+  const unsigned long long T = plan->big_keys;
+  for (unsigned long long t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < T;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t b = find_range(kbase, plan->nbign, t);
+    const uint32_t L = recs[seq_at[list[b]]].cnt - 1;
+    const unsigned long long *s = in + kbase[b];
+    const uint32_t e = uint32_t(t - kbase[b]);
+    const uint32_t r = e / w, start = (r & ~1u) * w;
+    const unsigned long long key = s[e];
+    // the other run of the pair
+    const uint32_t o0 = (r & 1u) ? start : min(L, start + w);
+    const uint32_t o1 = (r & 1u) ? start + w : min(L, start + 2 * w);
+    uint32_t lo = o0, hi = o1;  // first key >= key in [o0, o1)
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (s[mid] < key)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    out[kbase[b] + start + (e - r * w) + (lo - o0)] = key;
+  }
+}
+
+template <typename C, bool IDX>
+__global__ void k_ro_big_write(const LeafRec *__restrict__ recs, const uint32_t *seq_at, const uint32_t *list,
+                               const RoPlan *plan, const unsigned long long *kbase, const unsigned long long *keys,
+                               const uint32_t *__restrict__ off, const C *q0, const C *q1, const C *q2,
+                               const uint32_t *idx, C *o0, C *o1, C *o2, uint32_t *oidx) {
+  const unsigned long long T = plan->big_keys;
+  for (unsigned long long t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < T;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t b = find_range(kbase, plan->nbign, t);
+    const uint32_t j = list[b];
+    const LeafRec r = recs[seq_at[j]];
+    const uint32_t e = uint32_t(t - kbase[b]);
+    const uint32_t p = uint32_t(keys[t] & ((1ull << pos_bits(r.cnt)) - 1));
+    for (int k = 0; k < (e == 0 ? 2 : 1); ++k) {  // the first key's thread also moves the centre
+      const uint32_t src_p = k ? r.centre : p;
+      const uint64_t src = uint64_t(r.off) + src_p, d = uint64_t(off[j]) + (k ? 0 : e + 1);
+      o0[d] = q0[src];
+      o1[d] = q1[src];
+      o2[d] = q2[src];
+      if (IDX) oidx[d] = idx[src];
+    }
+  }
+}
+
 template <typename C, bool IDX>
 cudaError_t reorder_dispatch(const ReorderLaunch &a, cudaStream_t st) {
-  const RoLayout L = ro_layout(a.num_seq, a.max_cnt);
+  const RoLayout L = ro_layout(a.n, a.num_seq, a.max_cnt);
   uint8_t *base = static_cast<uint8_t *>(a.scratch);
   RoPlan *plan = reinterpret_cast<RoPlan *>(base + L.plan);
   uint32_t *seq_at = reinterpret_cast<uint32_t *>(base + L.seq_at);
@@ -497,11 +698,15 @@ cudaError_t reorder_dispatch(const ReorderLaunch &a, cudaStream_t st) {
   while (cap < (longest < kSmemSort ? longest : kSmemSort)) cap <<= 1;
   {
     TraceScope ts("k_ro_sort", st);
-    // E keys per thread in registers: cap / E threads (a warp at least), 4 keys below 2048, 8 from there
-    // (fewer threads per sequence, two sequences per SM)
-    const size_t smem = size_t(cap < 256 ? 256 : cap) * 16;
+    // E keys per thread in registers: cap / E threads (a warp at least, 1024 at most), 4 keys below 2048,
+    // 8 from there; shared memory for 8-byte keys up to cap and 16-byte keys up to kSmemWide
+    const uint32_t c2 = cap < 256 ? 256 : cap;
+    const size_t smem = size_t(c2) * 8 > size_t(c2 < kSmemWide ? c2 : kSmemWide) * 16
+                            ? size_t(c2) * 8
+                            : size_t(c2 < kSmemWide ? c2 : kSmemWide) * 16;
     const bool wide = cap >= 2048;
-    const int threads = int(cap / (wide ? 8 : 4) < 32 ? 32 : cap / (wide ? 8 : 4));
+    const uint32_t tpc = cap / (wide ? 8 : 4);
+    const int threads = int(tpc < 32 ? 32 : (tpc > uint32_t(kSortThreads) ? kSortThreads : tpc));
     auto kern = wide ? k_ro_sort<C, IDX, 8> : k_ro_sort<C, IDX, 4>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -511,22 +716,52 @@ cudaError_t reorder_dispatch(const ReorderLaunch &a, cudaStream_t st) {
     if (per_sm < 1) per_sm = 1;
     const uint64_t grid = uint64_t(per_sm) * sms;
     kern<<<unsigned(a.num_seq < grid ? a.num_seq : grid), threads, smem, st>>>(
-        a.recs, a.num_seq, seq_at, off, plan, q0, q1, q2, a.idx, o0, o1, o2, a.out_idx, cap < 256 ? 256 : cap);
+        a.recs, a.num_seq, seq_at, off, plan, q0, q1, q2, a.idx, o0, o1, o2, a.out_idx, c2, plan,
+        reinterpret_cast<uint32_t *>(base + L.big_list));
   }
-  if (longest > cap) {
+  if (longest > kSmemSort) {  // the merge sort of long sequences with 8-byte keys, if any
+    const uint32_t *list = reinterpret_cast<const uint32_t *>(base + L.big_list) + a.num_seq;
+    auto *kbase = reinterpret_cast<unsigned long long *>(base + L.kbase);
+    auto *rbase = reinterpret_cast<unsigned long long *>(base + L.rbase);
+    auto *ka = reinterpret_cast<unsigned long long *>(base + L.keys_a);
+    auto *kb = reinterpret_cast<unsigned long long *>(base + L.keys_b);
+    if (L.keys_b - L.keys_a < 8 * a.n) return cudaErrorInvalidValue;  // the scratch bound was too small
+    TraceScope ts("k_ro_big", st);
+    const unsigned grid = 8 * sms;
+    k_ro_big_plan<<<1, 32, 0, st>>>(a.recs, seq_at, list, plan, kbase, rbase);
+    k_ro_big_keys<<<grid, 256, 0, st>>>(a.recs, seq_at, list, plan, kbase, a.codes[0], a.codes[1], a.codes[2],
+                                        a.code_bytes, ka);
+    const size_t smem = size_t(kSmemSort) * 8;
+    e = cudaFuncSetAttribute(k_ro_big_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_ro_big_runs<<<2 * sms, kSortThreads, smem, st>>>(a.recs, seq_at, list, plan, kbase, rbase, ka);
+    for (uint64_t w = kSmemSort; w < longest; w *= 2) {
+      k_ro_big_merge<<<grid, 256, 0, st>>>(a.recs, seq_at, list, plan, kbase, ka, kb, uint32_t(w));
+      auto *t = ka;
+      ka = kb;
+      kb = t;
+    }
+    k_ro_big_write<C, IDX><<<grid, 256, 0, st>>>(a.recs, seq_at, list, plan, kbase, ka, off, q0, q1, q2, a.idx, o0,
+                                                 o1, o2, a.out_idx);
+  }
+  if (longest > kSmemWide) {  // 16-byte-key sequences left to the global-memory bitonic sort, if any
+    cap = cap < 256 ? 256 : cap;
     const uint64_t big_cap = next_pow2(longest);
     if (L.total - L.big < 16 * big_cap) return cudaErrorInvalidValue;  // the scratch bound was too small
     TraceScope ts("k_ro_sort_big", st);
     k_ro_sort_big<C, IDX><<<1, kSortThreads, 0, st>>>(a.recs, a.num_seq, seq_at, off, plan, q0, q1, q2, a.idx, o0,
                                                      o1, o2, a.out_idx, cap,
-                                                     reinterpret_cast<unsigned long long *>(base + L.big), big_cap);
+                                                     reinterpret_cast<unsigned long long *>(base + L.big), big_cap,
+                                                     reinterpret_cast<const uint32_t *>(base + L.big_list));
   }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-uint64_t reorder_scratch_bytes(uint64_t num_seq, uint64_t max_cnt) { return ro_layout(num_seq, max_cnt).total; }
+uint64_t reorder_scratch_bytes(uint64_t n, uint64_t num_seq, uint64_t max_cnt) {
+  return ro_layout(n, num_seq, max_cnt).total;
+}
 
 cudaError_t launch_reorder(const ReorderLaunch &a, cudaStream_t st) {
   if (a.n == 0 || a.num_seq == 0) return cudaSuccess;

@@ -202,7 +202,7 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
     p.off_rorecs = o;
     o = align_up(o + (p.num_leaves ? p.num_leaves : 1) * sizeof(LeafRec));
     p.off_roscratch = o;
-    o = align_up(o + reorder_scratch_bytes(p.num_leaves, most < n ? most : n));
+    o = align_up(o + reorder_scratch_bytes(n, p.num_leaves, most < n ? most : n));
   }
   // zeroed region
   p.off_zero = o;

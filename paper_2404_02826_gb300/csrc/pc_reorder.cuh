@@ -19,9 +19,9 @@ struct ReorderLaunch {
   void *out_codes[3];    // codes at their new positions (written)
   uint32_t *out_idx;     // input indices at their new positions (written when idx is given)
   uint64_t max_cnt;      // a bound on the particles of one sequence (sizes the scratch)
-  void *scratch;         // reorder_scratch_bytes(num_seq, max_cnt), 256-byte aligned
+  void *scratch;         // reorder_scratch_bytes(n, num_seq, max_cnt), 256-byte aligned
 };
-uint64_t reorder_scratch_bytes(uint64_t num_seq, uint64_t max_cnt);
+uint64_t reorder_scratch_bytes(uint64_t n, uint64_t num_seq, uint64_t max_cnt);
 cudaError_t launch_reorder(const ReorderLaunch &a, cudaStream_t st);
 
 }  // namespace pcx

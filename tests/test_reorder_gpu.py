@@ -70,7 +70,8 @@ CASES = [
     ("fluid", 100_003, np.float64, "abs", 1e-6, 1000, False),       # u32 codes
     ("cosmology", 200_000, np.float64, "rel", 1e-7, 2048, False),   # u32 codes, wide R-indices
     ("uniform", 40_000, np.float32, "rel", 1e-3, 1, False),         # one particle per sequence
-    ("cosmology", 150_000, np.float32, "rel", 1e-4, 12000, False),  # sequences above the shared-memory sort
+    ("cosmology", 150_000, np.float32, "rel", 1e-4, 12000, False),  # 8-byte keys of sequences above 8192
+    ("uniform", 24_000, np.float64, "rel", 1e-8, 12000, False),     # 16-byte keys above 8192: global memory
     ("cosmology", 50_000, np.float32, "rel", 1e-3, 128, True),
     ("fluid", 1 << 18, np.float64, "abs", 1e-4, 4096, True),
     ("uniform", 65_537, np.float32, "abs", 0.5, 64, True),
