@@ -208,6 +208,8 @@ def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False, launches
     idx = 4 if with_idx else 0
     if kernel == "k_rd_take":
         return (3 * cb + 8) * n / max(launches, 1)
+    if kernel == "k_ro_sort":  # reads and writes every particle's codes (and index) once
+        return 2 * (3 * cb + idx) * n
     return {
         "k_range": 3 * esz * n,
         "k_quantize": 3 * esz * n + 3 * cb * n + idx * n,

@@ -75,6 +75,36 @@ def test_batch_compress_equals_alone(pc, oracle_mod, lanes):
             assert torch.equal(d, alone)
 
 
+def test_batch_with_reduction_and_reordering(pc, oracle_mod):
+    """Items with the reduction, the reordering, both, and autotuned leaves: each
+    stream equals the same call alone, and the small ones the oracle's."""
+    dev = torch.device("cuda:0")
+    cfgs = [pc.config(256, reduce=True), pc.config(512, reorder=True), pc.config(300, reduce=True, reorder=True),
+            pc.config(0, autotune=True, reduce=True), pc.config(4096)]
+    jobs = []
+    for i, cfg in enumerate(cfgs * 2):
+        n = [3_000, 40_000, 250_000][i % 3]
+        pos = synth.by_name("cosmology" if i % 2 else "fluid", n, seed=40 + i,
+                            dtype=np.float32 if i % 4 < 2 else np.float64)
+        jobs.append((pos, pc.PC_EB_REL, 1e-3, cfg))
+    dpos = [torch.from_numpy(p).to(dev) for p, _, _, _ in jobs]
+    outs = [torch.empty(pc.pc_compress_bound(p.shape[0], pc.PC_F32 if p.dtype == torch.float32 else pc.PC_F64, cfg),
+                        dtype=torch.uint8, device=dev) for p, (_, _, _, cfg) in zip(dpos, jobs)]
+    sizes, statuses = pc.pc_compress_batch([(p, m, eb, cfg) for p, (_, m, eb, cfg) in zip(dpos, jobs)], outs,
+                                           lanes=4)
+    assert statuses == [pc.PC_OK] * len(jobs)
+    for (pos, m, eb, cfg), p, o, sz in zip(jobs, dpos, outs, sizes):
+        assert torch.equal(o[:sz], _alone(pc, p, m, eb, cfg))
+        if pos.shape[0] <= 3_000 and not (cfg.flags & pc.PC_FLAG_AUTOTUNE_LEAF):
+            if cfg.flags & pc.PC_FLAG_BOX_REDUCTION:
+                ref, _, _ = oracle_mod.compress_reduced(pos, oracle_mod.REL, eb, leaf_size=cfg.leaf_size)
+            else:
+                ref, _ = oracle_mod.compress(pos, oracle_mod.REL, eb, leaf_size=cfg.leaf_size)
+            if cfg.flags & pc.PC_FLAG_REORDER:
+                ref, _, _ = oracle_mod.reorder(ref)
+            assert o[:sz].cpu().numpy().tobytes() == ref
+
+
 def test_batch_reports_failed_items(pc):
     dev = torch.device("cuda:0")
     good = torch.from_numpy(synth.uniform(5000, seed=1)).to(dev)
