@@ -69,12 +69,17 @@ def lib(parallel: bool = False):
         L.oracle_quantize.argtypes = [vp, u64, i32, ctypes.POINTER(_Bound), vp]
         L.oracle_kdtree.argtypes = [vp, u64, u64, vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     ctypes.POINTER(u64)]
+        L.oracle_kdtree_rule.argtypes = [vp, u64, u64, i32, vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(u64)]
+        L.oracle_compress_rule.argtypes = [vp, u64, i32, i32, dbl, u64, i32, ctypes.POINTER(vp), ctypes.POINTER(u64),
+                                           ctypes.POINTER(vp)]
         L.oracle_num_bits.argtypes = [u64]
         L.oracle_num_bits.restype = ctypes.c_uint32
         L.oracle_bitbox.argtypes = [vp, u64, ctypes.POINTER(u64), vp, vp, vp, vp]
         L.oracle_compress.argtypes = [vp, u64, i32, i32, dbl, u64, ctypes.POINTER(vp), ctypes.POINTER(u64),
                                       ctypes.POINTER(vp)]
-        L.oracle_compress_reduced.argtypes = [vp, u64, i32, i32, dbl, u64, i32, ctypes.POINTER(vp), ctypes.POINTER(u64),
+        L.oracle_compress_reduced.argtypes = [vp, u64, i32, i32, dbl, u64, i32, i32, ctypes.POINTER(vp),
+                                              ctypes.POINTER(u64),
                                               ctypes.POINTER(vp), ctypes.POINTER(u64)]
         L.oracle_reorder.argtypes = [vp, u64, vp, ctypes.POINTER(vp), ctypes.POINTER(u64), vp, vp]
         L.oracle_rindex.argtypes = [vp, vp, vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
@@ -146,15 +151,16 @@ def quantize(pos, eb_mode: int, eb: float) -> np.ndarray:
     return q
 
 
-def kdtree(q: np.ndarray, leaf_size: int):
-    """Sec. 4.1: returns (order, leaf_off, leaf_cnt); order lists original indices leaf by leaf."""
+def kdtree(q: np.ndarray, leaf_size: int, widest: bool = False):
+    """Sec. 4.1: returns (order, leaf_off, leaf_cnt); order lists original indices leaf by leaf.
+    widest: split each node on the axis of its widest cell instead of depth mod 3."""
     q = np.ascontiguousarray(q, dtype=np.int64).reshape(-1, 3)
     n = q.shape[0]
     order = np.zeros(max(n, 1), np.uint64)
     po, pc = ctypes.c_void_p(), ctypes.c_void_p()
     nl = ctypes.c_uint64()
-    rc = lib().oracle_kdtree(q.ctypes.data, n, leaf_size, order.ctypes.data, ctypes.byref(po), ctypes.byref(pc),
-                             ctypes.byref(nl))
+    rc = lib().oracle_kdtree_rule(q.ctypes.data, n, leaf_size, int(widest), order.ctypes.data, ctypes.byref(po),
+                                  ctypes.byref(pc), ctypes.byref(nl))
     if rc:
         raise OracleError(rc, "kdtree")
     k = nl.value
@@ -197,16 +203,18 @@ def bitbox(leafq: np.ndarray):
     return int(c.value), lo, hi, qref, m.astype(np.int64)
 
 
-def compress(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: bool = True, parallel: bool = False):
-    """Full compression.  Returns (stream bytes, perm) with perm[decoded i] = original index."""
+def compress(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: bool = True, parallel: bool = False,
+             widest: bool = False):
+    """Full compression.  Returns (stream bytes, perm) with perm[decoded i] = original index.
+    widest: split each node on the axis of its widest cell instead of depth mod 3."""
     pos = _positions(pos)
     out = ctypes.c_void_p()
     nbytes = ctypes.c_uint64()
     perm = ctypes.c_void_p()
     L = lib(parallel)
-    rc = L.oracle_compress(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), eb_mode,
-                               float(eb), leaf_size, ctypes.byref(out), ctypes.byref(nbytes),
-                               ctypes.byref(perm) if want_perm else None)
+    rc = L.oracle_compress_rule(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), eb_mode,
+                                float(eb), leaf_size, int(widest), ctypes.byref(out), ctypes.byref(nbytes),
+                                ctypes.byref(perm) if want_perm else None)
     if rc:
         raise OracleError(rc, "compress")
     stream = ctypes.string_at(out, nbytes.value)
@@ -221,7 +229,7 @@ def compress(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: boo
 
 
 def compress_reduced(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_perm: bool = True,
-                     parallel: bool = False, one_per_round: bool = False):
+                     parallel: bool = False, one_per_round: bool = False, widest: bool = False):
     """Compression with the bit-box reduction in rounds (Sec. 4.1, Alg. 1; see oracle.c).
     one_per_round removes a single box (the smallest key) per round, the paper's order.
     Returns (stream bytes, perm, rounds)."""
@@ -232,7 +240,8 @@ def compress_reduced(pos, eb_mode: int, eb: float, leaf_size: int = 4096, want_p
     rounds = ctypes.c_uint64()
     L = lib(parallel)
     rc = L.oracle_compress_reduced(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos), eb_mode,
-                                   float(eb), leaf_size, int(one_per_round), ctypes.byref(out), ctypes.byref(nbytes),
+                                   float(eb), leaf_size, int(widest), int(one_per_round), ctypes.byref(out),
+                                   ctypes.byref(nbytes),
                                    ctypes.byref(perm) if want_perm else None, ctypes.byref(rounds))
     if rc:
         raise OracleError(rc, "compress_reduced")

@@ -236,14 +236,28 @@ static int leaf_push(leaf_list *l, uint64_t off, uint64_t cnt)
 
 /* ids[0..cnt) holds the node's particles in increasing original index.  A node
  * with at most r particles is a subregion (leaf).  Otherwise the node is split
- * by the median on axis depth mod 3: sorting the node by (code, index), the
- * first floor(cnt/2) particles form the left child, so the median itself lies
- * on the side with larger coordinates.  Both children keep index order.  The
- * two children own disjoint ranges of ids, so they may be ordered at once. */
-static int split_node(const int64_t *q, uint64_t *ids, uint64_t base, uint64_t cnt, int depth, uint64_t r)
+ * by the median on its axis: sorting the node by (code, index), the first
+ * floor(cnt/2) particles form the left child, so the median itself lies on the
+ * side with larger coordinates.  Both children keep index order.  The two
+ * children own disjoint ranges of ids, so they may be ordered at once.
+ * The axis is depth mod 3 (rule 0), or (rule 1) the axis of the node's widest
+ * cell: the root's cell spans codes [0, max code] per axis, and a split at
+ * median code v gives the left child the cell up to v and the right child the
+ * cell from v on that axis; equal widths go to the lowest axis. */
+typedef struct {
+    int64_t lo[3], hi[3];
+} cell;
+
+static int split_node(const int64_t *q, uint64_t *ids, uint64_t base, uint64_t cnt, int depth, uint64_t r, int rule,
+                      cell box)
 {
     if (cnt <= r) return OR_OK;
     int axis = depth % 3;
+    if (rule == 1) {
+        axis = 0;
+        for (int d = 1; d < 3; d++)
+            if (box.hi[d] - box.lo[d] > box.hi[axis] - box.lo[axis]) axis = d;
+    }
     keyed *tmp = malloc(cnt * sizeof(keyed));
     if (!tmp) return OR_ERR_NOMEM;
     for (uint64_t i = 0; i < cnt; i++) {
@@ -252,14 +266,18 @@ static int split_node(const int64_t *q, uint64_t *ids, uint64_t base, uint64_t c
     }
     qsort(tmp, cnt, sizeof(keyed), by_key_then_index);
     uint64_t k = cnt / 2;
+    int64_t v = tmp[k].key; /* the median code */
     for (uint64_t i = 0; i < cnt; i++) ids[base + i] = tmp[i].idx;
     free(tmp);
+    cell left = box, right = box;
+    left.hi[axis] = v;
+    right.lo[axis] = v;
     qsort(ids + base, k, sizeof(uint64_t), by_index);
     qsort(ids + base + k, cnt - k, sizeof(uint64_t), by_index);
     int rc_left = OR_OK, rc_right = OR_OK;
 #pragma omp task shared(rc_left) if (cnt > 65536)
-    rc_left = split_node(q, ids, base, k, depth + 1, r);
-    rc_right = split_node(q, ids, base + k, cnt - k, depth + 1, r);
+    rc_left = split_node(q, ids, base, k, depth + 1, r, rule, left);
+    rc_right = split_node(q, ids, base + k, cnt - k, depth + 1, r, rule, right);
 #pragma omp taskwait
     return rc_left ? rc_left : rc_right;
 }
@@ -277,17 +295,25 @@ static int collect_leaves(uint64_t base, uint64_t cnt, uint64_t r, leaf_list *le
 
 /* order[0..n): original indices, leaves concatenated left to right.
  * leaf_off / leaf_cnt: allocated here (free with oracle_free). */
-int oracle_kdtree(const int64_t *q, uint64_t n, uint64_t r, uint64_t *order, uint64_t **leaf_off,
-                  uint64_t **leaf_cnt, uint64_t *num_leaves)
+int oracle_kdtree_rule(const int64_t *q, uint64_t n, uint64_t r, int rule, uint64_t *order, uint64_t **leaf_off,
+                       uint64_t **leaf_cnt, uint64_t *num_leaves)
 {
-    if (r < 1) return OR_ERR_ARG;
+    if (r < 1 || rule < 0 || rule > 1) return OR_ERR_ARG;
     leaf_list l = {0};
     for (uint64_t i = 0; i < n; i++) order[i] = i;
     int rc = OR_OK;
     if (n > 0) {
+        cell root;
+        for (int d = 0; d < 3; d++) {
+            root.lo[d] = 0;
+            root.hi[d] = 0;
+        }
+        for (uint64_t i = 0; i < n; i++)
+            for (int d = 0; d < 3; d++)
+                if (q[3 * i + d] > root.hi[d]) root.hi[d] = q[3 * i + d];
 #pragma omp parallel
 #pragma omp single
-        rc = split_node(q, order, 0, n, 0, r);
+        rc = split_node(q, order, 0, n, 0, r, rule, root);
         if (!rc) rc = collect_leaves(0, n, r, &l);
     }
     if (rc) {
@@ -299,6 +325,12 @@ int oracle_kdtree(const int64_t *q, uint64_t n, uint64_t r, uint64_t *order, uin
     *leaf_cnt = l.leaf_cnt;
     *num_leaves = l.num_leaves;
     return OR_OK;
+}
+
+int oracle_kdtree(const int64_t *q, uint64_t n, uint64_t r, uint64_t *order, uint64_t **leaf_off,
+                  uint64_t **leaf_cnt, uint64_t *num_leaves)
+{
+    return oracle_kdtree_rule(q, n, r, 0, order, leaf_off, leaf_cnt, num_leaves);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -439,8 +471,8 @@ static uint64_t leaves_for(uint64_t n, uint64_t r)
 /* Full compression.  On success *out (malloc'd) holds the stream and *perm
  * (malloc'd, may be NULL on request) maps each decoded particle to its
  * original index. */
-int oracle_compress(const void *pos, uint64_t n, int dtype, int eb_mode, double eb, uint64_t leaf_size,
-                    uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out)
+int oracle_compress_rule(const void *pos, uint64_t n, int dtype, int eb_mode, double eb, uint64_t leaf_size,
+                         int rule, uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out)
 {
     *out = NULL;
     *out_bytes = 0;
@@ -463,7 +495,7 @@ int oracle_compress(const void *pos, uint64_t n, int dtype, int eb_mode, double 
     perm = malloc((n ? n : 1) * sizeof(uint64_t));
     if (!q || !order || !perm) goto done;
     oracle_quantize(pos, n, dtype, &b, q);
-    rc = oracle_kdtree(q, n, leaf_size, order, &loff, &lcnt, &nl);
+    rc = oracle_kdtree_rule(q, n, leaf_size, rule, order, &loff, &lcnt, &nl);
     if (rc) goto done;
     rc = OR_ERR_NOMEM;
 
@@ -569,6 +601,12 @@ done:
     return rc;
 }
 
+int oracle_compress(const void *pos, uint64_t n, int dtype, int eb_mode, double eb, uint64_t leaf_size,
+                    uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out)
+{
+    return oracle_compress_rule(pos, n, dtype, eb_mode, eb, leaf_size, 0, out, out_bytes, perm_out);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Bit-box reduction (Sec. 4.1, "bit box reduction and bit box intersection */
 /* update"; Alg. 1), in rounds.                                              */
@@ -647,7 +685,7 @@ static void rebuild_box(const int64_t *q, const uint64_t *ids, const unsigned ch
 }
 
 int oracle_compress_reduced(const void *pos, uint64_t n, int dtype, int eb_mode, double eb, uint64_t leaf_size,
-                            int one_per_round, uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out,
+                            int rule, int one_per_round, uint8_t **out, uint64_t *out_bytes, uint64_t **perm_out,
                             uint64_t *rounds_out)
 {
     *out = NULL;
@@ -673,7 +711,7 @@ int oracle_compress_reduced(const void *pos, uint64_t n, int dtype, int eb_mode,
     seq_ids = malloc((n ? n : 1) * sizeof(uint64_t));
     if (!q || !order || !perm || !live || !seq_ids) goto done;
     oracle_quantize(pos, n, dtype, &b, q);
-    rc = oracle_kdtree(q, n, leaf_size, order, &loff, &lcnt, &nl);
+    rc = oracle_kdtree_rule(q, n, leaf_size, rule, order, &loff, &lcnt, &nl);
     if (rc) goto done;
     rc = OR_ERR_NOMEM;
     uint64_t maxleaf = 1;

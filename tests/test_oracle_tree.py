@@ -117,3 +117,57 @@ def test_left_keys_below_right_keys(oracle_mod):
         check(lo + k, hi, depth + 1)
 
     check(0, len(q), 0)
+
+
+def brute_tree_widest(q, r):
+    """The widest-cell rule written again: the root cell spans codes [0, max] per
+    axis; a node splits on the axis of its widest cell (the lowest of equal
+    widths) at the median code v, the left child's cell ending at v and the
+    right child's starting there."""
+    leaves = []
+
+    def rec(ids, lo, hi):
+        if len(ids) <= r:
+            leaves.append(sorted(ids))
+            return
+        ext = [hi[d] - lo[d] for d in range(3)]
+        axis = ext.index(max(ext))
+        ids = np.asarray(ids)
+        order = np.lexsort((ids, q[ids, axis]))
+        k = len(ids) // 2
+        v = int(q[ids[order[k]], axis])
+        lhi, rlo = list(hi), list(lo)
+        lhi[axis] = v
+        rlo[axis] = v
+        rec(sorted(ids[order[:k]].tolist()), lo, lhi)
+        rec(sorted(ids[order[k:]].tolist()), rlo, hi)
+
+    if len(q):
+        rec(list(range(len(q))), [0, 0, 0], [int(q[:, d].max()) for d in range(3)])
+    return leaves
+
+
+@pytest.mark.parametrize("kind,n,r", INPUTS)
+def test_widest_tree_matches_brute_force(oracle_mod, kind, n, r):
+    if kind == "ties":
+        q = tie_heavy(n, 3)
+    else:
+        pos = synth.by_name(kind, n, seed=1)
+        q = oracle_mod.quantize(pos, oracle_mod.REL, 1e-3)
+    order, off, cnt = oracle_mod.kdtree(q, r, widest=True)
+    got = [order[o:o + c].tolist() for o, c in zip(off, cnt)]
+    assert got == brute_tree_widest(q, r)
+
+
+def test_widest_rule_follows_the_long_side(oracle_mod):
+    """A slab 64 x 8 x 1 units: the first two cuts are both across x (halving x
+    leaves 32 > 8), which depth mod 3 would not do, and the leaves differ."""
+    rng = np.random.default_rng(4)
+    pos = (rng.random((4096, 3)) * np.array([64.0, 8.0, 1.0])).astype(np.float32)
+    q = oracle_mod.quantize(pos, oracle_mod.ABS, 0.01)
+    order, off, cnt = oracle_mod.kdtree(q, 1024, widest=True)
+    xs = [q[order[o:o + c], 0] for o, c in zip(off, cnt)]
+    # four leaves, ordered along x: each leaf's x range lies below the next one's
+    assert len(xs) == 4 and all(xs[i].max() <= xs[i + 1].min() for i in range(3))
+    o2, f2, c2 = oracle_mod.kdtree(q, 1024)
+    assert [order[o:o + c].tolist() for o, c in zip(off, cnt)] != [o2[o:o + c].tolist() for o, c in zip(f2, c2)]
