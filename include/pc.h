@@ -76,7 +76,8 @@ typedef enum { PC_EB_ABS = 0, PC_EB_REL = 1 } pc_eb_mode;
 typedef struct {
     uint32_t leaf_size; /* r of Sec. 4.1: largest leaf; 0 = 4096; valid 1..PC_MAX_LEAF_SIZE.
                            With PC_FLAG_AUTOTUNE_LEAF: the largest candidate (0 = PC_MAX_LEAF_SIZE) */
-    uint32_t flags;     /* 0, or any of PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION, PC_FLAG_REORDER */
+    uint32_t flags;     /* 0, or any of PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION, PC_FLAG_REORDER,
+                           PC_FLAG_WIDEST_AXIS */
 } pc_config;
 
 /* Leaf-size autotuning (no counterpart in the paper, which fixes r by hand,
@@ -120,6 +121,15 @@ typedef struct {
  * same, in another order; perm follows it).  The paper then entropy-codes the
  * stream (Huffman, ZSTD); that step is not part of this library. */
 #define PC_FLAG_REORDER 4u
+
+/* Split-axis variant of the k-d partition (Sec. 4.1 leaves the axis open;
+ * the default is depth mod 3): every node splits on the axis along which its
+ * cell is widest, the lowest axis of equal widths.  The root's cell spans the
+ * codes [0, max code] per axis; a split at median code v gives the left child
+ * the cell up to v and the right child the cell from v on, on that axis.  The
+ * median rule, the leaves and the stream format are unchanged; the decoder
+ * does not need to know the rule. */
+#define PC_FLAG_WIDEST_AXIS 8u
 #define PC_AUTOTUNE_MIN_LEAF 64u
 
 #define PC_DEFAULT_LEAF_SIZE 4096u

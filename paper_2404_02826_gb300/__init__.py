@@ -40,6 +40,7 @@ PC_LEAF_BYTES = 32
 PC_FLAG_AUTOTUNE_LEAF = 1
 PC_FLAG_BOX_REDUCTION = 2
 PC_FLAG_REORDER = 4
+PC_FLAG_WIDEST_AXIS = 8
 PC_AUTOTUNE_MIN_LEAF = 64
 LEAF_AUTO = -1  # leaf_size argument: autotune with candidates up to PC_MAX_LEAF_SIZE
 
@@ -170,11 +171,14 @@ def _check(rc: int, where: str):
         raise PCError(rc, where)
 
 
-def config(leaf_size: int = 0, autotune: bool = False, reduce: bool = False, reorder: bool = False) -> pc_config:
+def config(leaf_size: int = 0, autotune: bool = False, reduce: bool = False, reorder: bool = False,
+           widest: bool = False) -> pc_config:
     """A pc_config: leaf size r (0 = default; with autotune the largest candidate,
-    0 = PC_MAX_LEAF_SIZE), PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION and PC_FLAG_REORDER."""
+    0 = PC_MAX_LEAF_SIZE), PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION, PC_FLAG_REORDER and
+    PC_FLAG_WIDEST_AXIS."""
     return pc_config(int(leaf_size), (PC_FLAG_AUTOTUNE_LEAF if autotune else 0) |
-                     (PC_FLAG_BOX_REDUCTION if reduce else 0) | (PC_FLAG_REORDER if reorder else 0))
+                     (PC_FLAG_BOX_REDUCTION if reduce else 0) | (PC_FLAG_REORDER if reorder else 0) |
+                     (PC_FLAG_WIDEST_AXIS if widest else 0))
 
 
 def _cfg(leaf_size) -> pc_config:

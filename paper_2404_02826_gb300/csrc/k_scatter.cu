@@ -273,16 +273,17 @@ __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
   static_assert(kPerWarp <= 32 && kLoads * kGroupsPerLoad == kPerWarp, "group layout");
   __shared__ uint32_t wtot[8];
   __shared__ TileGeom sg;
-  __shared__ uint32_t sv;
+  __shared__ uint32_t sv, sax;
   if (threadIdx.x == 0) {
     sg = tile_geom(a, blockIdx.x);
     sv = a.nodes[sg.j].v;
+    sax = a.nodes[sg.j].axis;
   }
   __syncthreads();
   const TileGeom g = sg;
   const uint32_t v = sv;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const C *q = static_cast<const C *>(a.src[a.level % 3]);
+  const C *q = static_cast<const C *>(a.src[sax]);
   const uint32_t w0 = g.tb & ~15u;
   const uint32_t ngrp = (g.te - w0 + 31) >> 5;
   const uint32_t run0 = w0 + uint32_t(warp) * (32u * kPerWarp);  // first slot of this warp's run
@@ -399,7 +400,8 @@ __global__ void k_tilescan_small(LevelLaunch a) {
 // Levels of small nodes (at most kSmallNode particles): one warp partitions a
 // whole node in one pass, 32 consecutive particles per round, carrying the
 // counts of "code < v" and "code == v" from round to round - no tiles, no
-// count pass, no tile scan.  Same placement rule as k_scatter.
+// count pass, no tile scan.  Same placement rule as k_scatter.  AXIS is the
+// level's split axis, or 3 for each node's own (widest-cell variant).
 template <typename C, bool IDX, int AXIS>
 __global__ void __launch_bounds__(256) k_scatter_node(LevelLaunch a) {
   const int lane = threadIdx.x & 31;
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(256) k_scatter_node(LevelLaunch a) {
     uint64_t off64, cnt64;
     node_range(a.n, a.level, j, off64, cnt64);
     const uint32_t off = uint32_t(off64), cnt = uint32_t(cnt64), k = cnt >> 1;
-    const uint32_t v = a.nodes[j].v, tl = a.nodes[j].tleft;
+    const uint32_t v = a.nodes[j].v, tl = a.nodes[j].tleft, ax = AXIS == 3 ? a.nodes[j].axis : uint32_t(AXIS);
     C *n0 = static_cast<C *>(a.dst[0]) + off, *n1 = static_cast<C *>(a.dst[1]) + off,
       *n2 = static_cast<C *>(a.dst[2]) + off;
     uint32_t *ni = IDX ? a.dst_idx + off : nullptr;
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(256) k_scatter_node(LevelLaunch a) {
         x2 = s2[off + i];
         if (IDX) xi = a.src_idx[off + i];
       }
-      const uint32_t q = AXIS == 0 ? x0 : (AXIS == 1 ? x1 : x2);
+      const uint32_t q = ax == 0 ? x0 : (ax == 1 ? x1 : x2);
       const bool isless = valid && q < v, istie = valid && q == v;
       const uint32_t lm = __ballot_sync(0xffffffffu, isless), tm = __ballot_sync(0xffffffffu, istie);
       const uint32_t tie_rank = run_t + __popc(tm & lt_mask);
@@ -479,6 +481,7 @@ cudaError_t scatter_node_launch(const LevelLaunch &a, cudaStream_t st) {
 template <typename C, bool IDX>
 cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
   if (((a.n + (1ull << a.level) - 1) >> a.level) <= kSmallNode) {
+    if (a.widest) return scatter_node_launch<C, IDX, 3>(a, st);
     switch (a.level % 3) {
       case 0: return scatter_node_launch<C, IDX, 0>(a, st);
       case 1: return scatter_node_launch<C, IDX, 1>(a, st);

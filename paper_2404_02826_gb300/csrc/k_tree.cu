@@ -1,6 +1,8 @@
 // Global levels of the median k-d partition (Sec. 4.1 of arXiv 2404.02826).
 //
-// A node at depth l splits on axis l mod 3.  Sorting its particles by
+// A node at depth l splits on axis l mod 3, or (widest-cell variant) on the
+// axis along which its cell (the root's code bounds cut by its ancestors'
+// splits) is widest, the lowest of equal widths.  Sorting its particles by
 // (code, original index), the first floor(c/2) go left, so the median lies on
 // the larger-coordinate side.  Particles of a node are stored contiguously and
 // in original-index order (every partition is stable), so "original index" is
@@ -33,7 +35,7 @@ constexpr uint32_t kMedBins = 1u << kMedD;    // private histogram of one warp
 // prep: bounds of every node from its parent's split, then its first digit
 // --------------------------------------------------------------------------
 __global__ void k_prep(LevelNode *nodes, const LevelNode *parents, uint64_t n, int level, uint32_t digit_bits,
-                       LevelLaunch::RootHi root_hi, uint32_t leaf_size) {
+                       LevelLaunch::RootHi root_hi, uint32_t leaf_size, bool widest) {
   const uint64_t count = 1ull << level;
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= count) return;
@@ -50,12 +52,18 @@ __global__ void k_prep(LevelNode *nodes, const LevelNode *parents, uint64_t n, i
       nd.bhi[d] = p.bhi[d];
     }
     if (p.v != 0xffffffffu) {  // the parent was split at p.v on its axis
-      const int pa = (level - 1) % 3;
+      const int pa = int(p.axis);
       if (j & 1) nd.blo[pa] = p.v;
       else nd.bhi[pa] = p.v;
     }
   }
-  const int axis = level % 3;
+  int axis = level % 3;
+  if (widest) {
+    axis = 0;
+    for (int d = 1; d < 3; ++d)
+      if (nd.bhi[d] - nd.blo[d] > nd.bhi[axis] - nd.blo[axis]) axis = d;
+  }
+  nd.axis = uint32_t(axis);
   nd.lo = nd.blo[axis];
   nd.hi = nd.bhi[axis];
   uint64_t off, cnt;
@@ -85,7 +93,8 @@ __global__ void k_prep(LevelNode *nodes, const LevelNode *parents, uint64_t n, i
 // hist: each block walks a contiguous, 16-aligned range node by node
 // --------------------------------------------------------------------------
 template <typename C>
-__global__ void __launch_bounds__(kHistThreads) k_hist(const C *__restrict__ codes, const LevelNode *__restrict__ nodes,
+__global__ void __launch_bounds__(kHistThreads) k_hist(const C *__restrict__ q0, const C *__restrict__ q1,
+                                                       const C *__restrict__ q2, const LevelNode *__restrict__ nodes,
                                                        uint32_t *__restrict__ hist, uint64_t n, int level,
                                                        uint32_t digit_bits) {
   extern __shared__ uint32_t sh[];
@@ -109,6 +118,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const C *__restrict__ cod
     const uint64_t seg_end = (off + cnt) < end ? (off + cnt) : end;
     const LevelNode nd = nodes[j];
     if (nd.width) {
+      const C *codes = nd.axis == 0 ? q0 : (nd.axis == 1 ? q1 : q2);
       const uint32_t nb = 1u << nd.width, mask = nb - 1;
       const uint32_t lo_c = nd.lo, prefix = nd.prefix, width = nd.width;
       const int shift = nd.shift;
@@ -255,7 +265,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(LevelNode *nodes, uint32
 // median: one warp per node, all digits (levels of many small nodes)
 // --------------------------------------------------------------------------
 template <typename C>
-__global__ void __launch_bounds__(kMedWarps * 32) k_median(const C *__restrict__ codes, LevelNode *nodes, uint64_t n,
+__global__ void __launch_bounds__(kMedWarps * 32) k_median(const C *__restrict__ q0, const C *__restrict__ q1,
+                                                            const C *__restrict__ q2, LevelNode *nodes, uint64_t n,
                                                             int level) {
   extern __shared__ uint32_t med_hist[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -265,6 +276,7 @@ __global__ void __launch_bounds__(kMedWarps * 32) k_median(const C *__restrict__
   for (uint64_t j = uint64_t(blockIdx.x) * kMedWarps + warp; j < count; j += uint64_t(gridDim.x) * kMedWarps) {
     LevelNode nd = nodes[j];
     if (nd.width == 0) continue;  // a leaf, or all codes equal: prep has decided
+    const C *codes = nd.axis == 0 ? q0 : (nd.axis == 1 ? q1 : q2);
     uint64_t off64, cnt64;
     node_range(n, level, j, off64, cnt64);
     const uint32_t off = uint32_t(off64), cnt = uint32_t(cnt64), k = cnt >> 1;
@@ -361,10 +373,10 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
     LevelLaunch::RootHi rh;
     for (int d = 0; d < 3; ++d) rh.v[d] = a.root_hi[d];
     k_prep<<<unsigned((count + 255) / 256), 256, 0, st>>>(a.nodes, a.parents, a.n, a.level, a.digit_bits, rh,
-                                                          a.leaf_size);
+                                                          a.leaf_size, a.widest);
   }
-  const int axis = a.level % 3;
-  const C *codes = static_cast<const C *>(a.src[axis]);
+  const C *q0 = static_cast<const C *>(a.src[0]), *q1 = static_cast<const C *>(a.src[1]),
+          *q2 = static_cast<const C *>(a.src[2]);
   if (a.warp_median) {
     const size_t msm = sizeof(uint32_t) * kMedBins * kMedWarps;
     int per_sm = 0;
@@ -375,7 +387,7 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
     if (grid > need) grid = need;
     {
       TraceScope ts("k_median", st);
-      k_median<C><<<unsigned(grid), kMedWarps * 32, msm, st>>>(codes, a.nodes, a.n, a.level);
+      k_median<C><<<unsigned(grid), kMedWarps * 32, msm, st>>>(q0, q1, q2, a.nodes, a.n, a.level);
     }
     return launch_scatter(a, st);
   }
@@ -383,7 +395,7 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   for (uint32_t p = 0; p < a.passes; ++p) {
     {
       TraceScope ts("k_hist", st);
-      k_hist<C><<<a.hist_blocks, kHistThreads, hsm, st>>>(codes, a.nodes, a.hist, a.n, a.level, a.digit_bits);
+      k_hist<C><<<a.hist_blocks, kHistThreads, hsm, st>>>(q0, q1, q2, a.nodes, a.hist, a.n, a.level, a.digit_bits);
     }
     TraceScope ts("k_select", st);
     k_select<<<unsigned(count), kSelThreads, 0, st>>>(a.nodes, a.hist, a.n, a.level, a.digit_bits);

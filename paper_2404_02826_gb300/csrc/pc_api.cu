@@ -77,7 +77,7 @@ struct Plan {
   uint64_t off_groups = 0, off_slices = 0;
   uint64_t off_reduce = 0, off_seqrec = 0;  // bit-box reduction: its scratch and the sequence records
   uint64_t off_rorecs = 0, off_roscratch = 0;  // reordering: the records in the new order, its scratch
-  bool reduce = false, reorder = false;
+  bool reduce = false, reorder = false, widest = false;
   bool tune = false;  // leaf size chosen by descending from r_hi while the stream shrinks (sized for r)
   uint32_t r_hi = 0;
   int tune_first = 0, tune_last = 0;  // candidate depths
@@ -125,7 +125,9 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   uint32_t r = PC_DEFAULT_LEAF_SIZE;
   p.tune = false;
   if (cfg) {
-    if (cfg->flags & ~(PC_FLAG_AUTOTUNE_LEAF | PC_FLAG_BOX_REDUCTION | PC_FLAG_REORDER)) return PC_ERR_ARG;
+    if (cfg->flags & ~(PC_FLAG_AUTOTUNE_LEAF | PC_FLAG_BOX_REDUCTION | PC_FLAG_REORDER | PC_FLAG_WIDEST_AXIS))
+      return PC_ERR_ARG;
+    p.widest = (cfg->flags & PC_FLAG_WIDEST_AXIS) != 0;
     p.reduce = (cfg->flags & PC_FLAG_BOX_REDUCTION) != 0;
     p.reorder = (cfg->flags & PC_FLAG_REORDER) != 0;
     if (cfg->leaf_size) r = cfg->leaf_size;
@@ -508,7 +510,10 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       // levels of at least 2048 nodes of at most kMedMaxNode particles: one warp per node
       la.warp_median = (1ull << l) >= 2048 && ((n + (1ull << l) - 1) >> l) <= kMedMaxNode;
       la.digit_bits = la.warp_median ? kMedD : digit_bits_for(l);
-      const uint32_t bits = bit_length(L.qmax[l % 3]);
+      const uint32_t widest_q = L.qmax[0] > L.qmax[1] ? (L.qmax[0] > L.qmax[2] ? L.qmax[0] : L.qmax[2])
+                                                      : (L.qmax[1] > L.qmax[2] ? L.qmax[1] : L.qmax[2]);
+      const uint32_t bits = bit_length(p.widest ? widest_q : L.qmax[l % 3]);
+      la.widest = p.widest;
       la.passes = (bits + la.digit_bits - 1) / la.digit_bits;
       la.tiles_per_node = uint32_t(tiles_per_node(n, l, scatter_tile(cb, p.idx)));
       for (int d = 0; d < 3; ++d) la.root_hi[d] = L.qmax[d];

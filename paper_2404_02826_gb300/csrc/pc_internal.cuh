@@ -52,7 +52,7 @@ struct LevelNode {
   uint32_t tleft;    // particles with code == v that go left (first in index order)
   uint32_t blo[3];   // code bounds on every axis, inherited from the ancestors' splits:
   uint32_t bhi[3];   //   the left child of a split at v has codes <= v, the right child >= v
-  uint32_t pad;
+  uint32_t axis;     // split axis of the node
 };
 
 // Per-leaf facts kept between the bit-box pass and the packing pass.
@@ -152,6 +152,7 @@ struct LevelLaunch {
   uint32_t passes;
   uint32_t tiles_per_node;
   uint32_t root_hi[3];    // level 0: the codes of axis d lie in [0, root_hi[d]]
+  bool widest;            // split every node on the axis of its widest cell (else depth mod 3)
   const void *src[3];
   void *dst[3];
   const uint32_t *src_idx;

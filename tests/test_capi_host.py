@@ -98,7 +98,7 @@ def test_autotune_flag_sizes_and_rejections(pc):
     assert auto == pc.pc_compress_bound(n, pc.PC_F32, pc.PC_AUTOTUNE_MIN_LEAF)
     assert pc.pc_compress_workspace_size(n, pc.PC_F32, pc.LEAF_AUTO) >= pc.pc_compress_workspace_size(n, pc.PC_F32)
     assert pc.pc_compress_bound(n, pc.PC_F32, -512) == pc.pc_compress_bound(n, pc.PC_F32, pc.PC_AUTOTUNE_MIN_LEAF)
-    cfg = pc.pc_config(0, 8)  # no such flag
+    cfg = pc.pc_config(0, 16)  # no such flag
     out = pc.ctypes.c_uint64()
     assert pc.load().pc_compress_bound(n, pc.PC_F32, pc.ctypes.byref(cfg), pc.ctypes.byref(out)) == pc.PC_ERR_ARG
     # the bit-box reduction writes no more sequences than leaves, and needs more scratch
