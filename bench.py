@@ -64,6 +64,8 @@ def parse():
                     help="compress with the bit-box reduction (Sec. 4.1, Alg. 1) in place of plain leaves")
     ap.add_argument("--reorder", action="store_true",
                     help="reorder sequences by sum m_d and particles by R-index (Sec. 4.2) before packing")
+    ap.add_argument("--widest", action="store_true",
+                    help="split every k-d node on the axis of its widest cell (else depth mod 3)")
     ap.add_argument("--lossless", action="store_true",
                     help="after the timed steps, compress the stream once more on the host with zlib (DEFLATE: "
                          "LZ77 + Huffman, standing in for Huffman + ZSTD) and report that ratio separately")
@@ -223,29 +225,31 @@ def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False, launches
     }.get(kernel)
 
 
-def oracle_round_trip(pos, mode, eb, leaf_size, reduce=False, reorder=False, parallel=False):
+def oracle_round_trip(pos, mode, eb, leaf_size, reduce=False, reorder=False, parallel=False, widest=False):
     import oracle
 
     m = oracle.REL if mode == "rel" else oracle.ABS
     if reduce:
-        stream, _, _ = oracle.compress_reduced(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=parallel)
+        stream, _, _ = oracle.compress_reduced(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=parallel,
+                                               widest=widest)
     else:
-        stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=parallel)
+        stream, _ = oracle.compress(pos, m, eb, leaf_size=leaf_size, want_perm=False, parallel=parallel,
+                                    widest=widest)
     if reorder:
         stream, _, _ = oracle.reorder(stream)
     oracle.decompress(stream, parallel=parallel)
     return len(stream)
 
 
-def oracle_round_trip_parallel(pos, mode, eb, leaf_size, reduce=False, reorder=False):
-    return oracle_round_trip(pos, mode, eb, leaf_size, reduce, reorder, parallel=True)
+def oracle_round_trip_parallel(pos, mode, eb, leaf_size, reduce=False, reorder=False, widest=False):
+    return oracle_round_trip(pos, mode, eb, leaf_size, reduce, reorder, parallel=True, widest=widest)
 
 
-def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False, reorder=False):
+def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False, reorder=False, widest=False):
     gen, n, dtype, mode, eb = spec
     pos = generate(gen, n_sample, dtype, seed=0)
     t0 = time.perf_counter()
-    oracle_round_trip(pos, mode, eb, leaf_size, reduce, reorder)
+    oracle_round_trip(pos, mode, eb, leaf_size, reduce, reorder, widest=widest)
     dt = time.perf_counter() - t0
     out = {"value": round(pos.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
            "sample": f"{n_sample} particles of the {gen} generator ({dtype}, {mode} eb {eb}), one compress + "
@@ -255,9 +259,9 @@ def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False, reorder=Fal
 
     oracle.build(parallel=True)
     big = generate(gen, (1 if reduce else 4) * n_sample, dtype, seed=0)
-    oracle_round_trip_parallel(big[: 1 << 16], mode, eb, leaf_size, reduce, reorder)  # thread pool start-up
+    oracle_round_trip_parallel(big[: 1 << 16], mode, eb, leaf_size, reduce, reorder, widest)  # thread pool start-up
     t0 = time.perf_counter()
-    oracle_round_trip_parallel(big, mode, eb, leaf_size, reduce, reorder)
+    oracle_round_trip_parallel(big, mode, eb, leaf_size, reduce, reorder, widest)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out["parallel"] = {"value": round(big.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": cores,
@@ -267,6 +271,8 @@ def cpu_baseline(spec, leaf_size, n_sample=CPU_SAMPLE, reduce=False, reorder=Fal
         out["sample"] += " (bit-box reduction)"
     if reorder:
         out["sample"] += " (reordered)"
+    if widest:
+        out["sample"] += " (widest-cell split axis)"
     return out
 
 
@@ -281,11 +287,11 @@ def run_reference(args, spec):
     oracle.build()
     samples = [generate(gen, REF_SAMPLE, dtype, seed=s) for s in range(2)]
     for i in range(args.warmup):
-        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce, args.reorder)
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce, args.reorder, widest=args.widest)
     times = []
     for i in range(args.steps):
         t0 = time.perf_counter()
-        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce, args.reorder)
+        oracle_round_trip(samples[i % 2], mode, eb, args.leaf_size, args.reduce, args.reorder, widest=args.widest)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     units = samples[0].nbytes * args.steps
@@ -296,6 +302,7 @@ def run_reference(args, spec):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": args.workload, "sample_particles_per_step": REF_SAMPLE, "leaf_size": args.leaf_size,
                    "box_reduction": bool(args.reduce), "reorder": bool(args.reorder),
+                   "widest_axis": bool(args.widest),
                    "note": "the oracle (plain single-threaded C, double precision) on host cores"},
         "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{REF_SAMPLE} particles of the {gen} generator per step"},
@@ -325,7 +332,7 @@ def run_ours(args, spec):
     emode = pc.PC_EB_REL if mode == "rel" else pc.PC_EB_ABS
     esz = 4 if dtype == "f32" else 8
     pos = torch.from_numpy(pos_h).to(dev)
-    cfg = pc.config(args.leaf_size, reduce=args.reduce, reorder=args.reorder)
+    cfg = pc.config(args.leaf_size, reduce=args.reduce, reorder=args.reorder, widest=args.widest)
     comp = pc.Compressor(n, pdt, leaf_size=cfg, device=dev)
     dec = torch.empty_like(pos)
 
@@ -420,7 +427,7 @@ def run_ours(args, spec):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, args.leaf_size, CPU_SAMPLE // 4 if args.reduce else CPU_SAMPLE, args.reduce,
-                           args.reorder)
+                           args.reorder, args.widest)
 
     if rank == 0:
         line = {
@@ -429,7 +436,7 @@ def run_ours(args, spec):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "generator": gen, "particles": n, "eb_mode": mode, "eb": eb,
                        "leaf_size": args.leaf_size, "box_reduction": bool(args.reduce),
-                       "reorder": bool(args.reorder),
+                       "reorder": bool(args.reorder), "widest_axis": bool(args.widest),
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)", "code_bytes": cb},
             "compress_gbs": round(whole_job_gbs(world, nbytes, args.steps, comp_ms), 3),
