@@ -17,7 +17,8 @@
 //
 // One round:
 //   select   a warp per alive box a: a is taken when no other alive box with a
-//            smaller (key, index) meets its bit box.  Taken boxes are pairwise
+//            smaller (key, index) meets its bit box (the box found blocking it
+//            in an earlier round is checked first).  Taken boxes are pairwise
 //            disjoint, so no particle lies in two of them.
 //   take     a block per taken box: ranks in its sequence for its centre, its
 //            other live particles in slot order, then, for every alive box c
@@ -93,12 +94,13 @@ struct State {
   uint32_t *taken;    // [boxes] boxes taken in the round, any order
   uint32_t *lost;     // [boxes] boxes that lost particles in the round, any order
   uint32_t *tbits;    // [boxes / 32] bitmap of the boxes taken in the round
+  uint32_t *blocker;  // [boxes] the box found blocking this one in an earlier round (~0: none yet)
   RCounters *ctr;
   uint32_t nl;
 };
 
 struct Layout {
-  uint64_t live, dest, rank, box, info, node[kMaxLevels], ticket[kMaxLevels], pend[kMaxLevels], seq_cnt, seq_pos,
+  uint64_t live, dest, rank, blocker, box, info, node[kMaxLevels], ticket[kMaxLevels], pend[kMaxLevels], seq_cnt, seq_pos,
       taken, lost, tbits, ctr;
   uint64_t zero_begin, zero_end, total;
   uint32_t count[kMaxLevels];
@@ -123,6 +125,8 @@ Layout layout_of(uint64_t n, uint64_t nl) {
   o = align256(o + 4 * n + 16);  // whole groups of four slots are read
   L.rank = o;
   o = align256(o + 4 * n);
+  L.blocker = o;
+  o = align256(o + 4 * nl);
   L.box = o;
   o = align256(o + sizeof(RBox) * nl);
   L.info = o;
@@ -348,6 +352,14 @@ __global__ void __launch_bounds__(kThreads) k_rd_select(State S) {
   if (!(A.state & kAlive)) return;
   const unsigned long long ka = (static_cast<unsigned long long>(A.key) << 32) | a;
   const Box6 bx = box6(A);
+  // the box that blocked this one before usually still does: alive, a smaller key, meeting it
+  const uint32_t bl = S.blocker[a];
+  if (bl != 0xffffffffu) {
+    const int4 *q = reinterpret_cast<const int4 *>(S.t.box + bl);
+    const int4 p0 = q[0], p1 = q[1];
+    const unsigned long long kb = (static_cast<unsigned long long>(uint32_t(p1.z)) << 32) | bl;
+    if ((uint32_t(p1.w) & kAlive) && kb < ka && meets(bx, p0, p1)) return;
+  }
   auto nok = [&](const int4 &p, const int4 &q) {
     const unsigned long long mn = (static_cast<unsigned long long>(uint32_t(q.w)) << 32) | uint32_t(q.z);
     return mn < ka && meets(bx, p, q);
@@ -358,7 +370,12 @@ __global__ void __launch_bounds__(kThreads) k_rd_select(State S) {
   };
   Descent d;
   descent_start(d, S.t, nok, bok);
-  const bool blocked = descent_run(d, S.t, nok, bok, [](uint32_t, uint32_t) { return true; });
+  uint32_t found = 0xffffffffu;
+  const bool blocked = descent_run(d, S.t, nok, bok, [&](uint32_t first, uint32_t m) {
+    found = first + uint32_t(__ffs(int(m)) - 1);
+    return true;
+  });
+  if (blocked && (threadIdx.x & 31) == 0) S.blocker[a] = found;
   if (!blocked && (threadIdx.x & 31) == 0) {
     atomicOr(&S.t.box[a].state, kTaken);
     atomicOr(S.tbits + (a >> 5), 1u << (a & 31));
@@ -1004,6 +1021,7 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
   S.taken = reinterpret_cast<uint32_t *>(base + L.taken);
   S.lost = reinterpret_cast<uint32_t *>(base + L.lost);
   S.tbits = reinterpret_cast<uint32_t *>(base + L.tbits);
+  S.blocker = reinterpret_cast<uint32_t *>(base + L.blocker);
   S.ctr = reinterpret_cast<RCounters *>(base + L.ctr);
   S.nl = uint32_t(a.num_leaves);
   const C *q0 = static_cast<const C *>(a.codes[0]), *q1 = static_cast<const C *>(a.codes[1]),
@@ -1012,6 +1030,8 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
   cudaError_t e = cudaMemsetAsync(S.live, 0xff, 4 * (a.n / 32 + 2), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(S.dest, 0xff, 4 * a.n, st);  // no owner yet: the final pass checks every slot got one
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(S.blocker, 0xff, 4 * a.num_leaves, st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(base + L.zero_begin, 0, L.zero_end - L.zero_begin, st);
   if (e != cudaSuccess) return e;
