@@ -413,6 +413,22 @@ def run_ours(args, spec):
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
         e2e = measure_e2e(pc, pos_h, pdt, emode, eb, args, world, cfg)
+    # reconstruction quality (Sec. 5.1), from one more untimed round trip with the permutation
+    quality = None
+    if rank == 0:
+        qc = pc.Compressor(n, pdt, leaf_size=cfg, with_perm=True, device=dev)
+        qsize = qc.compress(pos, emode, eb)
+        qdec = torch.empty_like(pos)
+        qc.decompress(qc.out, qdec, qsize)
+        qinfo = pc.pc_stream_info(qc.out[:96].cpu().numpy().tobytes())
+        err = (pos[qc.perm[:n].long()].double() - qdec.double()).abs()
+        dmax = float((pos.double().amax(0) - pos.double().amin(0)).max())
+        nrmse = float(torch.sqrt(torch.mean((err / dmax) ** 2))) if dmax > 0 else 0.0
+        quality = {"max_err_over_eps": round(float(err.max()) / qinfo.eps, 6),
+                   "violations": int((err > qinfo.eps).sum()), "nrmse": nrmse,
+                   "psnr_db": round(-20.0 * float(np.log10(nrmse)), 3) if nrmse > 0 else None,
+                   "eps": qinfo.eps, "timed": False}
+        del qc, qdec, err
     lossless = None
     if rank == 0 and args.lossless:
         import zlib
@@ -444,7 +460,7 @@ def run_ours(args, spec):
             "compression_ratio": round(nbytes / size, 4), "bits_per_particle": round(8 * size / n, 4),
             "step_hbm_frac_algorithmic": round(step_alg / (total_ms / args.steps / 1e3) / 1e9 / peak, 4),
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
-            "e2e": e2e, "cpu_baseline": cpu,
+            "quality": quality, "e2e": e2e, "cpu_baseline": cpu,
         }
         if lossless:
             line["lossless"] = lossless

@@ -1,10 +1,13 @@
-// Kernel tracing: CUDA events around each launch, accumulated per kernel name.
+// Kernel tracing: CUDA events around each launch, accumulated per kernel name;
+// every launch also opens an NVTX range of the kernel's name for profilers.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pc.h"
 #include "pc_internal.cuh"
@@ -52,6 +55,7 @@ void add(const char *name, double ms) {
 }  // namespace
 
 TraceScope::TraceScope(const char *name, cudaStream_t st) : name_(name), st_(st), a_(nullptr), b_(nullptr) {
+  nvtxRangePushA(name);  // a range per launch for profilers (no-op without one)
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return;
   a_ = take_event();
@@ -60,6 +64,7 @@ TraceScope::TraceScope(const char *name, cudaStream_t st) : name_(name), st_(st)
 }
 
 TraceScope::~TraceScope() {
+  nvtxRangePop();
   if (!a_ || !b_) return;
   cudaEventRecord(static_cast<cudaEvent_t>(b_), st_);
   std::lock_guard<std::mutex> lk(g_mu);
