@@ -192,6 +192,14 @@ int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, doubl
 int pc_compress_noalloc(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                         void *out, uint64_t out_capacity, uint64_t *out_size, void *stream);
 
+/* Self-test of the library's bounded device waits (no counterpart in the
+ * paper): one block waits on a shared-memory barrier that nothing completes,
+ * through the same bounded wait the partition uses for its tile copies (with a
+ * short poll limit).  The wait gives up, the kernel returns, and the call
+ * returns PC_ERR_TIMEOUT with the context intact; any other status means the
+ * mechanism failed.  Synchronous on `stream`. */
+int pc_selftest_wait_timeout(void *stream);
+
 /* Parse a stream header held in host memory (the first 96 bytes suffice). */
 int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info);
 

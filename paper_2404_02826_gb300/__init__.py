@@ -53,7 +53,7 @@ EXPORTS = (
     "pc_compress_batch_workspace_size", "pc_compress_batch", "pc_decompress_batch_workspace_size",
     "pc_decompress_batch", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_release",
     "pc_server_stats", "pc_server_destroy", "pc_server_now", "pc_leaf_size_sweep_workspace_size",
-    "pc_leaf_size_sweep",
+    "pc_leaf_size_sweep", "pc_selftest_wait_timeout",
 )
 PC_REQ_COMPRESS = 0
 PC_REQ_DECOMPRESS = 1
@@ -319,6 +319,13 @@ def pc_decompress_host(host_stream, nbytes: int, host_positions, workspace, stre
                                    host_positions.numel() * host_positions.element_size(), workspace.data_ptr(),
                                    workspace.numel(), _stream_handle(stream))
     _check(rc, "pc_decompress_host")
+
+
+def pc_selftest_wait_timeout(stream=None) -> int:
+    """Runs the bounded-wait self-test; returns its status (PC_ERR_TIMEOUT when the mechanism works)."""
+    L = _lib()
+    L.pc_selftest_wait_timeout.argtypes = [ctypes.c_void_p]
+    return int(L.pc_selftest_wait_timeout(_stream_handle(stream)))
 
 
 def pc_error_string(status: int) -> str:

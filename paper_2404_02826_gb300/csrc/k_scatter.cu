@@ -20,13 +20,13 @@
 #include <cstdint>
 
 #include "pc_internal.cuh"
+#include "pc_mbar.cuh"
 
 namespace pcx {
 namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kBarSpinLimit = 1u << 22;
 constexpr uint64_t kSmallNode = 2048;  // levels whose nodes are at most this large: a warp per node
 
 template <typename C, bool IDX>
@@ -62,49 +62,6 @@ struct Smem {
   uint32_t tleft[2];
   TileGeom geo[2];
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Waits for the copy into one buffer; bounded: on expiry the error bit is set
-// and the wait is repeated once more (the copy itself always completes).
-__device__ __forceinline__ void wait_buffer(unsigned long long *bar, uint32_t parity, uint32_t *err) {
-  uint32_t spins = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if (++spins > kBarSpinLimit) {
-      if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
-      spins = 0;
-      while (!mbar_try_wait(bar, parity) && ++spins < kBarSpinLimit) {
-      }
-      return;
-    }
-  }
-}
 
 __device__ __forceinline__ TileGeom tile_geom(const LevelLaunch &a, uint32_t t) {
   TileGeom g;
