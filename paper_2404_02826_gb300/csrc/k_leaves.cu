@@ -362,8 +362,12 @@ template <typename C, bool IDX>
 __device__ __forceinline__ void pack_leaf(const C *__restrict__ q0, const C *__restrict__ q1, const C *__restrict__ q2,
                                           const uint32_t *__restrict__ idx, const LeafRec &rec, uint64_t leaf,
                                           uint8_t *out, uint64_t num_leaves, uint32_t *perm, int lane, int warp, int nw,
-                                          uint32_t *sw) {
+                                          uint32_t *sw, uint64_t n, uint64_t payload_cap, uint32_t *err) {
   const uint32_t tid = uint32_t(warp) * 32 + lane, group = uint32_t(nw) * 32;
+  if (uint64_t(rec.off) + rec.cnt > n || rec.word_off + rec.words > payload_cap) {  // inconsistent: never written
+    if (tid == 0) atomicOr(err, kErrInternal);
+    return;
+  }
   const uint32_t off = rec.off, cnt = rec.cnt, centre = rec.centre;
   const uint32_t m0 = rec.m & 0xffu, m1 = (rec.m >> 8) & 0xffu, m2 = (rec.m >> 16) & 0xffu;
   const uint32_t w = m0 + m1 + m2;
@@ -435,11 +439,12 @@ template <typename C, bool IDX>
 __global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__ q0, const C *__restrict__ q1,
                                                            const C *__restrict__ q2, const uint32_t *__restrict__ idx,
                                                            const LeafRec *__restrict__ recs, uint8_t *out,
-                                                           uint64_t num_leaves, uint32_t *perm) {
+                                                           uint64_t num_leaves, uint32_t *perm, uint64_t n,
+                                                           uint64_t payload_cap, uint32_t *err) {
   __shared__ uint32_t swords[kPackWarps][96];  // one chunk's words per warp (w <= 93)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   pack_leaf<C, IDX>(q0, q1, q2, idx, recs[blockIdx.x], blockIdx.x, out, num_leaves, perm, lane, warp, kPackWarps,
-                    swords[warp]);
+                    swords[warp], n, payload_cap, err);
 }
 
 // One warp per leaf (small leaves).
@@ -448,11 +453,13 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack_warp(const C *__restr
                                                                 const C *__restrict__ q2,
                                                                 const uint32_t *__restrict__ idx,
                                                                 const LeafRec *__restrict__ recs, uint8_t *out,
-                                                                uint64_t num_leaves, uint32_t *perm) {
+                                                                uint64_t num_leaves, uint32_t *perm, uint64_t n,
+                                                                uint64_t payload_cap, uint32_t *err) {
   __shared__ uint32_t swords[kPackWarps][96];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t L = uint64_t(blockIdx.x) * kPackWarps + warp; L < num_leaves; L += uint64_t(gridDim.x) * kPackWarps)
-    pack_leaf<C, IDX>(q0, q1, q2, idx, recs[L], L, out, num_leaves, perm, lane, 0, 1, swords[warp]);
+    pack_leaf<C, IDX>(q0, q1, q2, idx, recs[L], L, out, num_leaves, perm, lane, 0, 1, swords[warp], n, payload_cap,
+                      err);
 }
 
 template <typename C, bool IDX>
@@ -492,10 +499,12 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
   if (a.cost_only) return cudaGetLastError();
   TraceScope ts("k_leafpack", st);
   if (small)
-    k_leafpack_warp<C, IDX><<<wgrid, kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out, a.num_leaves, a.perm);
+    k_leafpack_warp<C, IDX><<<wgrid, kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out, a.num_leaves, a.perm,
+                                                            a.n, a.payload_cap, a.err);
   else
     k_leafpack<C, IDX><<<unsigned(a.num_leaves), kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out,
-                                                                        a.num_leaves, a.perm);
+                                                                        a.num_leaves, a.perm, a.n, a.payload_cap,
+                                                                        a.err);
   return cudaGetLastError();
 }
 

@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(kThreads) k_rd_select(State S) {
 
 constexpr int kTakeThreads = 1024;
 constexpr int kTakeWarps = kTakeThreads / 32;
+static_assert(kTakeWarps >= 2 && kTakeWarps <= 32, "take: a search warp and an own-particle warp, one scan warp");
 
 template <typename C>
 struct Codes4;  // the codes of the aligned group of four slots g, as loaded (two or four words)
@@ -652,8 +653,8 @@ __global__ void __launch_bounds__(kTakeThreads) k_rd_take(State S, const C *__re
         }
         if (lane == 0) lpos[warp] = k;
         __syncthreads();
-        if (warp == 0) {  // exclusive scan of the pieces' counts
-          const uint32_t x = lpos[lane];
+        if (warp == 0) {  // exclusive scan of the pieces' counts (one per warp of the block)
+          const uint32_t x = lane < kTakeWarps ? lpos[lane] : 0u;
           uint32_t incl = x;
           for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);

@@ -303,6 +303,13 @@ struct Sweep {
   uint32_t r_min;
 };
 
+// Payload words an output of `capacity` bytes holds after the header and a
+// table of `leaves` entries (0 when it holds not even those).
+static uint64_t payload_words(uint64_t capacity, uint64_t leaves) {
+  const uint64_t fixed = PC_HEADER_BYTES + uint64_t(PC_LEAF_BYTES) * leaves;
+  return capacity > fixed ? (capacity - fixed) / 4 : 0;
+}
+
 int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                   void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
                   uint32_t *perm, cudaStream_t st, Sweep *sweep = nullptr) {
@@ -414,6 +421,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       lf.slice_tot = reinterpret_cast<uint64_t *>(ws + p.off_slices);
       lf.cost_only = cost_only;
       lf.box_only = box_only;
+      lf.payload_cap = payload_words(out_capacity, num_leaves);
+      lf.err = err;
       return launch_leaves(lf, st);
     };
     // a5 from ready records: payload offsets and packing, after the reordering
@@ -454,6 +463,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       lf.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
       lf.slice_tot = reinterpret_cast<uint64_t *>(ws + p.off_slices);
       lf.recs_ready = true;
+      lf.payload_cap = payload_words(out_capacity, num_seq);
+      lf.err = err;
       PC_TRY(launch_leaves(lf, st));
       return PC_OK;
     };

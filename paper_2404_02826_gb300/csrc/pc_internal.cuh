@@ -187,6 +187,8 @@ struct LeafLaunch {
   bool cost_only;           // bit boxes and payload words only (leaf-size autotuning)
   bool recs_ready;          // recs already hold off, cnt, centre, m, q_ref, words (the box reduction's sequences)
   bool box_only;            // leaf table and bit boxes only (the records are reordered before packing)
+  uint64_t payload_cap;     // payload words the output holds after the header and the leaf table
+  uint32_t *err;            // device error word: a record that would write past n or the payload is skipped
 };
 cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st);
 // The leaf ranges alone (off, cnt of every leaf; the other fields zero).
