@@ -35,6 +35,7 @@ PC_EB_ABS = 0
 PC_EB_REL = 1
 PC_DEFAULT_LEAF_SIZE = 4096
 PC_MAX_LEAF_SIZE = 12000
+PC_MAX_PARTICLES = (1 << 31) - 1
 PC_HEADER_BYTES = 96
 PC_LEAF_BYTES = 32
 PC_FLAG_AUTOTUNE_LEAF = 1
