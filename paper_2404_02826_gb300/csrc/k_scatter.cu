@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
   __syncthreads();
   const TileGeom g = sg;
   const uint32_t v = sv;
+  const uint32_t vc = v < 0x7fffffffu ? v : 0x7fffffffu, vc1 = vc + 1u;  // a leaf's v: above every code
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const C *q = static_cast<const C *>(a.src[sax]);
   const uint32_t w0 = g.tb & ~15u;
@@ -259,13 +260,17 @@ __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
     const int vlo = min(max(int(g.tb) - int(s0), 0), kPerLane), vhi = min(max(int(g.te) - int(s0), 0), kPerLane);
     const uint32_t vm = ((1u << vhi) - 1u) & ~((1u << vlo) - 1u);
     const uint32_t w[4] = {raw[i].x, raw[i].y, raw[i].z, raw[i].w};
-    uint32_t l = 0, t = 0;
+    // Codes are below 2^30 and vc, vc + 1 at most 2^31, so the sign bit of
+    // x - vc is x < vc and that of x - (vc + 1) is x <= vc; each bit is
+    // shifted into its mask (code c at bit c), and the ties are le & ~lt.
+    uint32_t l = 0, le = 0;
 #pragma unroll
-    for (int c = 0; c < kPerLane; ++c) {
+    for (int c = kPerLane - 1; c >= 0; --c) {
       const uint32_t x = sizeof(C) == 2 ? ((w[c >> 1] >> (16 * (c & 1))) & 0xffffu) : w[c];
-      l |= uint32_t(x < v) << c;
-      t |= uint32_t(x == v) << c;
+      l = __funnelshift_l(x - vc, l, 1);
+      le = __funnelshift_l(x - vc1, le, 1);
     }
+    uint32_t t = le & ~l;
     const int sh = kPerLane * (lane % kLanesPerGroup);
     l = (l & vm) << sh;
     t = (t & vm) << sh;
