@@ -2,7 +2,9 @@
 
 - An independent restatement of the round rule in plain Python on tiny inputs
   (boxes, selection, taken particles, rebuilt boxes, sequence order) gives the
-  same sequences as the oracle.
+  same sequences as the oracle; with one box per round (the least sum of m_d,
+  lowest index on ties: Alg. 1's own order) it gives the oracle's
+  one-per-round sequences, one round per sequence.
 - Boxes that meet no other box: one round, and the stream is the plain one.
 - Every particle is in exactly one sequence, every code fits its sequence's
   widths, and every decoded coordinate is within eps.
@@ -25,8 +27,9 @@ def _box(oracle_mod, q, ids):
             "key": int(sum(m)), "lo": [int(qref[d]) - h[d] for d in range(3)], "hi": [int(qref[d]) + h[d] for d in range(3)]}
 
 
-def _reference_sequences(oracle_mod, pos, mode, eb, r):
-    """The reduction rule restated: returns [(centre id, qref, m, [ids in stream order])]."""
+def _reference_sequences(oracle_mod, pos, mode, eb, r, strict=False):
+    """The reduction rule restated: returns [(centre id, qref, m, [ids in stream order])].
+    strict: one box per round, the alive box of least (sum m_d, index), as Alg. 1 removes them."""
     q = oracle_mod.quantize(pos, mode, eb)
     order, loff, lcnt = oracle_mod.kdtree(q, r)
     boxes = [_box(oracle_mod, q, order[o: o + c]) for o, c in zip(loff, lcnt)]
@@ -34,8 +37,11 @@ def _reference_sequences(oracle_mod, pos, mode, eb, r):
     seqs = []
     while any(alive):
         live = [i for i in range(len(boxes)) if alive[i]]
-        sel = [a for a in live if all(not (c != a and _meet(boxes[a], boxes[c])
-                                           and (boxes[c]["key"], c) < (boxes[a]["key"], a)) for c in live)]
+        if strict:
+            sel = [min(live, key=lambda a: (boxes[a]["key"], a))]
+        else:
+            sel = [a for a in live if all(not (c != a and _meet(boxes[a], boxes[c])
+                                               and (boxes[c]["key"], c) < (boxes[a]["key"], a)) for c in live)]
         lost = set()
         for a in sel:
             A = boxes[a]
@@ -75,6 +81,22 @@ def test_rounds_match_an_independent_restatement(oracle_mod, gen, n, r, eb):
         assert tuple(lf.q_ref) == tuple(qref) and tuple(lf.m) == tuple(m)
         assert np.array_equal(perm[lf.particle_offset: lf.particle_offset + lf.count], ids)
     assert rounds >= 1
+
+
+@pytest.mark.parametrize("gen,n,r,eb", [("cosmology", 300, 20, 1e-2), ("uniform", 200, 16, 5e-2),
+                                        ("fluid", 360, 30, 1e-3)])
+def test_one_box_per_round_matches_alg1_restated(oracle_mod, gen, n, r, eb):
+    pos = synth.by_name(gen, n, seed=n + 2 * r)
+    stream, perm, rounds = oracle_mod.compress_reduced(pos, oracle_mod.REL, eb, leaf_size=r, one_per_round=True)
+    st = parse(stream)
+    seqs = _reference_sequences(oracle_mod, pos, oracle_mod.REL, eb, r, strict=True)
+    assert st.num_leaves == len(seqs) == rounds
+    for lf, (centre, qref, m, ids) in zip(st.leaves, seqs):
+        assert tuple(lf.q_ref) == tuple(qref) and tuple(lf.m) == tuple(m)
+        assert np.array_equal(perm[lf.particle_offset: lf.particle_offset + lf.count], ids)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    b = oracle_mod.error_bound(pos, oracle_mod.REL, eb)
+    assert np.abs(pos[perm].astype(np.float64) - oracle_mod.decompress(stream).astype(np.float64)).max() <= b.eps
 
 
 def test_separated_boxes_give_the_plain_stream(oracle_mod):
