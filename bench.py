@@ -457,6 +457,7 @@ def run_ours(args, spec):
                        "l2": "inputs larger than L2 (no flush)", "code_bytes": cb},
             "compress_gbs": round(whole_job_gbs(world, nbytes, args.steps, comp_ms), 3),
             "decompress_gbs": round(whole_job_gbs(world, nbytes, args.steps, dec_ms), 3),
+            "particles_per_s": round(world * n * args.steps / (total_ms / 1e3), 1),
             "compression_ratio": round(nbytes / size, 4), "bits_per_particle": round(8 * size / n, 4),
             "step_hbm_frac_algorithmic": round(step_alg / (total_ms / args.steps / 1e3) / 1e9 / peak, 4),
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
