@@ -17,6 +17,7 @@ computes one at a time):
   * 16 sampled leaves: the oracle's bit box (Eq. 2) of the leaf's particles
     equals the leaf record, and the packed codes equal q - q_ref + 2^(m-1) - 1.
 """
+import os
 import struct
 
 import numpy as np
@@ -62,6 +63,15 @@ def run():
     pc.load()
     n = pc.PC_MAX_PARTICLES
     dev = torch.device("cuda:0")
+    # device: input and decoded copy, stream bound, workspaces, permutation; host: the input
+    need = (2 * 12 * n + pc.pc_compress_bound(n, pc.PC_F32, LEAF) + pc.pc_decompress_workspace_size(n)
+            + pc.pc_compress_workspace_size(n, pc.PC_F32, LEAF, True) + 4 * n + (16 << 30))
+    torch.cuda.empty_cache()  # earlier modules' cached blocks
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < need:
+        pytest.skip(f"needs {need >> 30} GiB of device memory, {free >> 30} GiB free")
+    if os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") < 3 * 12 * n:
+        pytest.skip("not enough host memory for the input")
     pos_h = uniform_f32(n, seed=3)
     pos = torch.from_numpy(pos_h).to(dev)
     c = pc.Compressor(n, pc.PC_F32, leaf_size=LEAF, with_perm=True, device=dev)
