@@ -2,7 +2,7 @@
 
 Each translation unit is compiled for sm_103a in parallel, then linked into one
 shared library with the CUDA runtime linked statically, so the library only
-needs the driver at run time.
+needs the NVIDIA kernel-mode driver's libcuda at run time.
 """
 from __future__ import annotations
 

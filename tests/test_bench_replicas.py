@@ -49,7 +49,7 @@ def test_max_over_ranks_and_whole_job_value():
 
 
 def test_reference_arm_under_torchrun_rank0_only():
-    """`bench.py --impl reference` launched like the driver's N > 1 runs: rank 0
+    """`bench.py --impl reference` launched under torchrun with two ranks: rank 0
     prints the one JSON line, the other rank exits 0 without work."""
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
