@@ -86,6 +86,15 @@ def test_parity_generators(pc, oracle_mod, gen, n, dtype, mode, eb, r):
     check_against_oracle(pc, oracle_mod, pos, m, eb, r)
 
 
+def test_parity_fluid_workload_full_size(pc, oracle_mod):
+    """The fluid workload at its full size, as bench.py generates and runs it (2^24 float64
+    lattice, seed 0, absolute eb 1e-4, leaf size 4096): the whole stream, the permutation
+    and the decoded floats byte for byte."""
+    pos = synth.by_name("fluid", 1 << 24, seed=0, dtype=np.float64)
+    _, info = check_against_oracle(pc, oracle_mod, pos, pc.PC_EB_ABS, 1e-4, 4096)
+    assert info.n == 1 << 24 and info.num_leaves == 1 << 12
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 31, 32, 33, 1000, 4095, 4096, 4097, 8193, 16383, 16384, 16385,
                                32767, 32768, 32769, 65536 + 17, 131072 * 3 + 1])
 def test_parity_ragged_sizes(pc, oracle_mod, n):
