@@ -1,0 +1,852 @@
+// The deep levels of the median k-d partition, the leaves' bit boxes and the
+// packed sequences in one kernel (Sec. 4.1 and 4.2, Fig. 4 of arXiv 2404.02826).
+//
+// Once every node of a level fits in shared memory, a CTA takes one node (in
+// ticket order), copies its code arrays in with bulk copies and finishes its
+// subtree on chip, without returning to HBM:
+//   - every remaining level: per subnode a radix select of the median code on
+//     its split axis (histograms in shared memory), then a stable two-way
+//     partition of every subnode (the median rule of Sec. 4.1: code < v, then
+//     the first `tleft` codes equal to v in index order, go left), from warp
+//     ballots and one block-wide scan, moved in place through registers;
+//   - the leaves' bit boxes (AABB, the particle closest to its centre, Eq. 2);
+//   - the CTA's first payload word, from the payload sizes of the CTAs before
+//     it (decoupled look-back over one status word per node, bounded waits);
+//   - the leaf records and the packed payload (Fig. 4), straight from shared
+//     memory, and the optional permutation.
+// The subnodes of a level are served by equal groups of warps: at relative
+// depth k there are 2^k subnodes and 32 / 2^k warps each, and a thread takes
+// positions row * (1024 / 2^k) + its index in the group, so it always holds at
+// most kRows positions whatever k is.
+#include <cstdint>
+
+#include "pc_internal.cuh"
+#include "pc_mbar.cuh"
+
+namespace pcx {
+namespace {
+
+constexpr int kT = 1024;  // threads of a CTA
+constexpr int kLgWarps = 5;
+constexpr int kWarps = 1 << kLgWarps;
+constexpr int kSubMaxLevels = kLgWarps + 1;  // splits inside a CTA: at least one warp per splitting subnode
+constexpr uint32_t kSubBins = 2048;  // radix bins of a level, shared by its subnodes
+constexpr uint32_t kLookSpin = 1u << 20;  // polls of a predecessor's status before giving up
+constexpr uint32_t kTmemCols = 512;       // tensor-memory columns of a CTA (one CTA per SM)
+
+// One subnode of the CTA's subtree at the current level.
+struct SubNode {
+  uint32_t off, cnt;        // position in the CTA's node, particles
+  uint32_t blo[3], bhi[3];  // cell: code bounds on every axis, from the ancestors' splits
+  uint32_t axis, split;     // split axis; 1 if the subnode splits (more than r particles)
+  uint32_t lo, prefix, below, width;  // radix select: lowest code, chosen digits, count below them, digit bits
+  int32_t shift;
+  uint32_t v, tleft;        // split code; particles equal to v that go left
+};
+
+struct SubLeaf {
+  uint32_t off, cnt, centre, m;
+  int32_t qref[3];
+  uint32_t words;
+  unsigned long long word_off;
+  uint32_t lo[3], hi[3];
+};
+
+struct SubMisc {
+  unsigned long long bar;
+  unsigned long long prefix;    // payload words of the nodes before this one
+  unsigned long long wd[kWarps][2];
+  uint32_t wp[kWarps][2];
+  unsigned long long off, cnt;  // the node: first particle, particles
+  uint32_t j, nl, lead, ilead, tmem;
+  uint32_t wt[kWarps];          // warp totals of the scans
+  uint32_t gb[kWarps];          // scan value at the first entry of each group
+  uint32_t fb[kWarps], fbefore[kWarps];
+};
+
+__host__ __device__ constexpr uint32_t al128(uint32_t x) { return (x + 127u) & ~127u; }
+
+// Shared-memory layout of one CTA: the code arrays of a node of up to
+// kRows * 1024 particles (each with room for the lead and tail of a 16-byte
+// aligned window), the optional index array, the radix bins, the partition's
+// masks and scan (reused as the packing's word staging), the subnode and leaf
+// records.  All offsets are compile-time constants.
+template <typename C, bool IDX>
+struct SubL {
+  static constexpr int R = sizeof(C) == 2 ? (IDX ? 16 : 32) : (IDX ? 12 : 16);  // positions per thread
+  // tensor-memory columns of one thread: every array's values of its positions, 32 bits per column
+  static constexpr int kCodeCols = sizeof(C) == 2 ? R / 2 : R;
+  static constexpr int kCols = 3 * kCodeCols + (IDX ? R : 0);
+  static_assert(kCodeCols % 4 == 0 && (kWarps / 4) * kCols <= 512, "tensor-memory columns");
+  static constexpr uint32_t kCap = uint32_t(R) * kT;
+  static constexpr uint32_t kSlots = kCap + 16;
+  static constexpr uint32_t kCodeStride = al128(kSlots * uint32_t(sizeof(C)));
+  static constexpr uint32_t kIdx = 3 * kCodeStride;
+  static constexpr uint32_t kBins = kIdx + (IDX ? al128(kSlots * 4) : 0u);
+  static constexpr uint32_t kStage = kBins + al128(kSubBins * 4);
+  static constexpr uint32_t kPart = 3u * uint32_t(R) * kWarps * 4, kPack = kWarps * 96u * 4;
+  static constexpr uint32_t kSn0 = kStage + al128(kPart > kPack ? kPart : kPack);
+  static constexpr uint32_t kSn1 = kSn0 + al128(kWarps * sizeof(SubNode));
+  static constexpr uint32_t kLeaf = kSn1 + al128(kWarps * sizeof(SubNode));
+  static constexpr uint32_t kMisc = kLeaf + al128(2 * kWarps * sizeof(SubLeaf));
+  static constexpr uint32_t kTotal = kMisc + al128(sizeof(SubMisc));
+  static_assert(kTotal <= 232448, "shared memory of one CTA");
+};
+
+constexpr unsigned long long kStAgg = 1ull << 62, kStIncl = 2ull << 62, kStVal = (1ull << 62) - 1;
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t widest_axis(const uint32_t *blo, const uint32_t *bhi) {
+  uint32_t ax = 0;
+  for (uint32_t d = 1; d < 3; ++d)
+    if (bhi[d] - blo[d] > bhi[ax] - blo[ax]) ax = d;
+  return ax;
+}
+
+// Radix-select state of a splitting subnode from its cell (k_prep's rule):
+// all codes equal on the axis decides at once, else digits of at most hb bits.
+__device__ __forceinline__ void sub_select_init(SubNode &s, uint32_t hb) {
+  s.lo = s.blo[s.axis];
+  const uint32_t B = bit_length(s.bhi[s.axis] - s.lo);
+  s.prefix = 0;
+  s.below = 0;
+  if (!s.split) {
+    s.width = 0;
+  } else if (B == 0) {
+    s.width = 0;
+    s.v = s.lo;
+    s.tleft = s.cnt >> 1;
+  } else {
+    s.width = B < hb ? B : hb;
+    s.shift = int32_t(B - s.width);
+  }
+}
+
+// ---- tensor memory (TMEM) as the staging area of the in-place moves ----
+// A move must read every position of an array before it writes any.  The
+// values wait in tensor memory instead of registers: each thread stores its
+// values to its own lane (tcgen05.st, a warp's 32 lanes of its lane quarter,
+// 32 bits per column), the block synchronises once for all arrays, and each
+// thread loads them back (tcgen05.ld) while it writes them to their places.
+// One warp allocates the columns at the start and frees them at the end.
+// Every tcgen05 instruction here is .sync.aligned: all 32 lanes of the warp
+// must execute it together, so each helper first reconverges the warp (the
+// code before it may have diverged, e.g. one lane issuing copies).
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+  __syncwarp();
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  __syncwarp();
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 8 (or 4) consecutive columns of this thread's lane; complete when the call returns
+__device__ __forceinline__ void tmem_st8(uint32_t t, const uint32_t *v) {
+  __syncwarp();
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(t),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t t, const uint32_t *v) {
+  __syncwarp();
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(t),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t t, uint32_t *v) {
+  __syncwarp();
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+      : "r"(t)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t t, uint32_t *v) {
+  __syncwarp();
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+      : "r"(t)
+      : "memory");
+}
+
+// Stages the positions p = r * Tg + ltid, r < nv, of one array of a subnode in
+// the thread's columns from `taddr`: column c holds rows 2c and 2c + 1 (16-bit
+// values) or row c (32-bit values).
+template <int R, typename E>
+__device__ __forceinline__ void stage_rows(const E *A, uint32_t nv, uint32_t Tg, uint32_t ltid, uint32_t taddr) {
+  constexpr int NC = sizeof(E) == 2 ? R / 2 : R;
+#pragma unroll
+  for (int c0 = 0; c0 < NC; c0 += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      v[c] = 0;
+      if (c0 + c < NC) {
+        if constexpr (sizeof(E) == 2) {
+          const int r = 2 * (c0 + c);
+          const uint32_t p0 = uint32_t(r) * Tg + ltid;
+          const uint32_t x0 = uint32_t(r) < nv ? uint32_t(A[p0]) : 0u;
+          const uint32_t x1 = uint32_t(r + 1) < nv ? uint32_t(A[p0 + Tg]) : 0u;
+          v[c] = x0 | (x1 << 16);
+        } else {
+          const int r = c0 + c;
+          v[c] = uint32_t(r) < nv ? uint32_t(A[uint32_t(r) * Tg + ltid]) : 0u;
+        }
+      }
+    }
+    if (c0 + 8 <= NC) tmem_st8(taddr + uint32_t(c0), v);
+    else tmem_st4(taddr + uint32_t(c0), v);
+  }
+}
+
+// The halves of a packed word as opaque operations: the moves of a level
+// unpack the same destinations, and sharing the unpacked values between them
+// would double the registers they hold.
+__device__ __forceinline__ uint32_t half_lo(uint32_t x) {
+  uint32_t y;
+  asm volatile("and.b32 %0, %1, 0xffff;" : "=r"(y) : "r"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t half_hi(uint32_t x) {
+  uint32_t y;
+  asm volatile("shr.b32 %0, %1, 16;" : "=r"(y) : "r"(x));
+  return y;
+}
+
+// Writes an array's staged values to their destinations dpk (two 16-bit
+// positions per word: rows 2i and 2i + 1 in word i).
+template <int R, typename E>
+__device__ __forceinline__ void unstage_rows(E *A, const uint32_t *dpk, uint32_t nv, uint32_t taddr) {
+  constexpr int NC = sizeof(E) == 2 ? R / 2 : R;
+#pragma unroll
+  for (int c0 = 0; c0 < NC; c0 += 8) {
+    uint32_t v[8];
+    if (c0 + 8 <= NC) tmem_ld8(taddr + uint32_t(c0), v);
+    else tmem_ld4(taddr + uint32_t(c0), v);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c0 + c < NC) {
+        if constexpr (sizeof(E) == 2) {
+          const int r = 2 * (c0 + c);
+          if (uint32_t(r) < nv) A[half_lo(dpk[r >> 1])] = E(v[c] & 0xffffu);
+          if (uint32_t(r + 1) < nv) A[half_hi(dpk[r >> 1])] = E(v[c] >> 16);
+        } else {
+          const int r = c0 + c;
+          if (uint32_t(r) < nv) A[(r & 1) ? half_hi(dpk[r >> 1]) : half_lo(dpk[r >> 1])] = E(v[c]);
+        }
+      }
+    }
+  }
+}
+
+template <typename C, bool IDX, bool WIDEST>
+__global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
+  using L = SubL<C, IDX>;
+  constexpr int R = L::R;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint32_t *bins = reinterpret_cast<uint32_t *>(sm + L::kBins);
+  uint32_t *LM = reinterpret_cast<uint32_t *>(sm + L::kStage);  // [R][32] masks of code < v
+  uint32_t *TM = LM + R * kWarps;                                // [R][32] masks of code == v
+  uint32_t *PRE = TM + R * kWarps;                               // [R][32] scan of the packed counts
+  SubNode *cur = reinterpret_cast<SubNode *>(sm + L::kSn0);
+  SubNode *nxt = reinterpret_cast<SubNode *>(sm + L::kSn1);
+  SubLeaf *LF = reinterpret_cast<SubLeaf *>(sm + L::kLeaf);
+  SubMisc &M = *reinterpret_cast<SubMisc *>(sm + L::kMisc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t ltm = (1u << lane) - 1u;
+
+  // ---- the node: ticket order, so every node before it has started ----
+  if (threadIdx.x == 0) {
+    M.j = atomicAdd(a.ticket, 1u);
+    mbar_init(&M.bar, 1);
+    mbar_fence_init();
+  }
+  constexpr uint32_t kV = 16 / sizeof(C);  // codes per 16 bytes
+  if (threadIdx.x == 0) {
+    const uint32_t j = M.j;
+    uint64_t off64, cnt64;
+    node_range(a.n, a.depth, j, off64, cnt64);
+    M.off = off64;
+    M.cnt = cnt64;
+    const uint32_t lead = uint32_t(off64) & (kV - 1u), ilead = uint32_t(off64) & 3u;
+    M.lead = lead;
+    M.ilead = ilead;
+    const uint32_t noff = uint32_t(off64), ncnt = uint32_t(cnt64);
+    const uint32_t nwin = (lead + ncnt + kV - 1u) & ~(kV - 1u);
+    const uint32_t niw = (ilead + ncnt + 3u) & ~3u;
+    const bool ok = ncnt <= L::kCap;
+    const uint32_t bytes = ok ? 3 * nwin * uint32_t(sizeof(C)) + (IDX ? 4 * niw : 0u) : 0u;
+    if (!ok) atomicOr(a.err, kErrInternal);
+    mbar_expect_tx(&M.bar, bytes);
+    if (bytes) {
+      for (int d = 0; d < 3; ++d)
+        bulk_g2s(sm + d * L::kCodeStride, static_cast<const C *>(a.codes[d]) + (noff - lead),
+                 nwin * uint32_t(sizeof(C)), &M.bar);
+      if (IDX) bulk_g2s(sm + L::kIdx, a.idx + (noff - ilead), 4 * niw, &M.bar);
+    }
+    // the root of the subtree: its cell from the parent's split (k_prep's rule)
+    SubNode &s = cur[0];
+    if (a.depth == 0) {
+      for (int d = 0; d < 3; ++d) {
+        s.blo[d] = 0;
+        s.bhi[d] = a.root_hi[d];
+      }
+    } else {
+      const LevelNode &p = a.parents[j >> 1];
+      for (int d = 0; d < 3; ++d) {
+        s.blo[d] = p.blo[d];
+        s.bhi[d] = p.bhi[d];
+      }
+      if (p.v != 0xffffffffu) {
+        if (j & 1) s.blo[p.axis] = p.v;
+        else s.bhi[p.axis] = p.v;
+      }
+    }
+    s.off = 0;
+    s.cnt = ok ? ncnt : 0u;
+    s.axis = WIDEST ? widest_axis(s.blo, s.bhi) : uint32_t(a.depth % 3);
+    s.split = s.cnt > a.leaf_size;
+  }
+  // the radix bins start at zero (every select pass leaves them zero again)
+  for (uint32_t b = threadIdx.x; b < kSubBins; b += kT) bins[b] = 0;
+  if (warp == 0) tmem_alloc(&M.tmem, kTmemCols);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  // this thread's tensor-memory columns: lane quarter warp % 4, columns by warpgroup
+  const uint32_t tcol = M.tmem + ((32u * (uint32_t(warp) & 3u)) << 16) + (uint32_t(warp) >> 2) * uint32_t(L::kCols);
+  wait_buffer(&M.bar, 0, a.err);
+  // element i of the node (any array) sits at slot lead + i
+  C *const X0 = reinterpret_cast<C *>(sm) + M.lead;
+
+  // ---- the levels inside the CTA ----
+  for (int k = 0; k < a.levels; ++k) {
+    const int lgW = kLgWarps - k;  // log2 of the warps per group
+    const uint32_t G = 1u << k;
+    const int g = warp >> lgW;
+    const uint32_t Tg = uint32_t(kT) >> k;
+    const uint32_t ltid = threadIdx.x & (Tg - 1u);
+    const uint32_t BPG = kSubBins >> k, hb = 11u - uint32_t(k);
+    if (threadIdx.x < G) sub_select_init(cur[threadIdx.x], hb);
+    // radix select of every splitting subnode, one digit per pass
+    bool any = __syncthreads_or(threadIdx.x < G && cur[threadIdx.x].width != 0);
+    while (any) {
+      const uint32_t width = cur[g].width;
+      const bool act = width != 0;
+      if (act) {
+        const uint32_t soff = cur[g].off, scnt = cur[g].cnt, lo = cur[g].lo, prefix = cur[g].prefix;
+        const uint32_t shift = uint32_t(cur[g].shift);
+        const C *A = X0 + cur[g].axis * (L::kCodeStride / sizeof(C)) + soff;
+        const uint32_t mask = (1u << width) - 1u;
+        uint32_t *hg = bins + uint32_t(g) * BPG;
+#pragma unroll 4
+        for (int r = 0; r < R; ++r) {
+          const uint32_t p = uint32_t(r) * Tg + ltid;
+          if (p < scnt) {
+            const uint32_t hbk = (uint32_t(A[p]) - lo) >> shift;
+            if ((hbk >> width) == prefix) atomicAdd(&hg[hbk & mask], 1u);
+          }
+        }
+      }
+      __syncthreads();
+      // the bucket holding rank cnt/2 - below: kBinsPer bins per thread, scanned within the group
+      constexpr uint32_t kBinsPer = kSubBins / kT;
+      const uint32_t b0 = kBinsPer * threadIdx.x;  // bins of this thread (in its own group's region)
+      uint32_t h[kBinsPer], x = 0;
+#pragma unroll
+      for (uint32_t e = 0; e < kBinsPer; ++e) {
+        h[e] = bins[b0 + e];
+        bins[b0 + e] = 0;
+        x += h[e];
+      }
+      if (!act) x = 0;
+      uint32_t incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) M.wt[warp] = incl;
+      __syncthreads();
+      if (act) {
+        uint32_t base = 0;
+        for (int w = g << lgW; w < warp; ++w) base += M.wt[w];
+        uint32_t ex = base + incl - x;
+        const uint32_t target = (cur[g].cnt >> 1) - cur[g].below;
+        if (x && ex <= target && target < ex + x) {
+          uint32_t e = 0;
+          while (e + 1 < kBinsPer && target >= ex + h[e]) ex += h[e++];
+          M.fb[g] = b0 - uint32_t(g) * BPG + e;
+          M.fbefore[g] = ex;
+        }
+      }
+      __syncthreads();
+      bool still = false;
+      if (act && ltid == 0) {
+        SubNode &u = cur[g];
+        u.below += M.fbefore[g];
+        u.prefix = (u.prefix << u.width) | M.fb[g];
+        if (u.shift == 0) {
+          u.v = u.lo + u.prefix;
+          u.tleft = (u.cnt >> 1) - u.below;
+          u.width = 0;
+        } else {
+          const uint32_t w = uint32_t(u.shift) < hb ? uint32_t(u.shift) : hb;
+          u.shift -= int32_t(w);
+          u.width = w;
+          still = true;
+        }
+      }
+      any = __syncthreads_or(still);
+    }
+
+    const uint32_t soff = cur[g].off, scnt = cur[g].cnt;
+    const bool split = cur[g].split != 0;
+    // classification: masks of code < v and code == v per (row, warp)
+    {
+      const C *A = X0 + cur[g].axis * (L::kCodeStride / sizeof(C)) + soff;
+      const uint32_t v = cur[g].v;
+#pragma unroll 4
+      for (int r = 0; r < R; ++r) {
+        const uint32_t p = uint32_t(r) * Tg + ltid;
+        const bool valid = split && p < scnt;
+        const uint32_t c = valid ? uint32_t(A[p]) : 0u;
+        const uint32_t lm = __ballot_sync(0xffffffffu, valid && c < v);
+        const uint32_t tm = __ballot_sync(0xffffffffu, valid && c == v);
+        if (lane == 0) {
+          LM[r * kWarps + warp] = lm;
+          TM[r * kWarps + warp] = tm;
+        }
+      }
+    }
+    __syncthreads();
+    // one block-wide exclusive scan over the entries (group, row, warp of the group),
+    // the order of the positions within each subnode; kEPT consecutive entries per thread
+    {
+      constexpr uint32_t kE = uint32_t(R) * kWarps, kEPT = (kE + kT - 1) / kT;
+      const uint32_t per_group = uint32_t(R) << lgW;
+      uint32_t cx[kEPT], slot[kEPT], sum = 0;
+#pragma unroll
+      for (uint32_t e = 0; e < kEPT; ++e) {
+        const uint32_t i = threadIdx.x * kEPT + e;
+        cx[e] = 0;
+        slot[e] = 0;
+        if (i < kE) {
+          const uint32_t gi = i / per_group;
+          const uint32_t rem = i - gi * per_group;
+          const uint32_t row = rem >> lgW, w = rem & ((1u << lgW) - 1u);
+          slot[e] = row * kWarps + (gi << lgW) + w;
+          cx[e] = (uint32_t(__popc(LM[slot[e]])) << 16) | uint32_t(__popc(TM[slot[e]]));
+        }
+        sum += cx[e];
+      }
+      uint32_t inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) M.wt[warp] = inc;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t t = lane < kWarps ? M.wt[lane] : 0u;
+        uint32_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+          if (lane >= o) ti += y;
+        }
+        if (lane < kWarps) M.wt[lane] = ti - t;
+      }
+      __syncthreads();
+      uint32_t ex = M.wt[warp] + inc - sum;
+#pragma unroll
+      for (uint32_t e = 0; e < kEPT; ++e) {
+        const uint32_t i = threadIdx.x * kEPT + e;
+        if (i < kE) {
+          PRE[slot[e]] = ex;
+          if (i % per_group == 0) M.gb[i / per_group] = ex;
+        }
+        ex += cx[e];
+      }
+    }
+    __syncthreads();
+    // destinations within the subnode, two 16-bit positions per register
+    uint32_t dpk[R / 2];
+    const uint32_t nv = scnt > ltid ? (scnt - ltid + Tg - 1u) / Tg : 0u;  // rows of this thread inside the subnode
+    {
+      const uint32_t kk = scnt >> 1, gbase = M.gb[g], tleft = cur[g].tleft;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t p = uint32_t(r) * Tg + ltid;
+        uint32_t dst = p;
+        if (split) {
+          const uint32_t P = PRE[r * kWarps + warp] - gbase;
+          const uint32_t lm = LM[r * kWarps + warp], tm = TM[r * kWarps + warp];
+          const uint32_t lb = (P >> 16) + uint32_t(__popc(lm & ltm));
+          const uint32_t tb = (P & 0xffffu) + uint32_t(__popc(tm & ltm));
+          const bool left = ((lm >> lane) & 1u) || (((tm >> lane) & 1u) && tb < tleft);
+          const uint32_t gl = lb + min(tb, tleft);
+          dst = left ? gl : kk + p - gl;
+          if (uint32_t(r) < nv && dst >= scnt) {
+            atomicOr(a.err, kErrInternal);
+            dst = p;
+          }
+        }
+        if (r & 1) dpk[r >> 1] |= dst << 16;
+        else dpk[r >> 1] = dst & 0xffffu;
+      }
+    }
+    // the moves: every array staged in tensor memory, one barrier, then written to its place
+    {
+      constexpr uint32_t S = L::kCodeStride / sizeof(C);
+      uint32_t *XI = reinterpret_cast<uint32_t *>(sm + L::kIdx) + M.ilead;
+      stage_rows<R>(X0 + soff, nv, Tg, ltid, tcol);
+      stage_rows<R>(X0 + S + soff, nv, Tg, ltid, tcol + L::kCodeCols);
+      stage_rows<R>(X0 + 2 * S + soff, nv, Tg, ltid, tcol + 2 * L::kCodeCols);
+      if (IDX) stage_rows<R>(XI + soff, nv, Tg, ltid, tcol + 3 * L::kCodeCols);
+      __syncthreads();
+      unstage_rows<R>(X0 + soff, dpk, nv, tcol);
+      unstage_rows<R>(X0 + S + soff, dpk, nv, tcol + L::kCodeCols);
+      unstage_rows<R>(X0 + 2 * S + soff, dpk, nv, tcol + 2 * L::kCodeCols);
+      if (IDX) unstage_rows<R>(XI + soff, dpk, nv, tcol + 3 * L::kCodeCols);
+      __syncthreads();
+    }
+    // children of every subnode (every subnode above the last level splits)
+    if (k + 1 < a.levels) {
+      if (threadIdx.x < G) {
+        const SubNode &u = cur[threadIdx.x];
+        if (!u.split) atomicOr(a.err, kErrInternal);
+        const uint32_t kk = u.cnt >> 1;
+        SubNode &cl = nxt[2 * threadIdx.x], &cr = nxt[2 * threadIdx.x + 1];
+        for (int d = 0; d < 3; ++d) {
+          cl.blo[d] = cr.blo[d] = u.blo[d];
+          cl.bhi[d] = cr.bhi[d] = u.bhi[d];
+        }
+        cl.bhi[u.axis] = u.v;
+        cr.blo[u.axis] = u.v;
+        cl.off = u.off;
+        cl.cnt = kk;
+        cr.off = u.off + kk;
+        cr.cnt = u.cnt - kk;
+        const uint32_t ax = uint32_t((a.depth + k + 1) % 3);
+        cl.axis = WIDEST ? widest_axis(cl.blo, cl.bhi) : ax;
+        cr.axis = WIDEST ? widest_axis(cr.blo, cr.bhi) : ax;
+        cl.split = cl.cnt > a.leaf_size;
+        cr.split = cr.cnt > a.leaf_size;
+      }
+      __syncthreads();
+      SubNode *t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+
+  // ---- leaves: the last level's subnodes, split or not, in order ----
+  if (threadIdx.x == 0) {
+    const uint32_t G = a.levels > 0 ? 1u << (a.levels - 1) : 1u;
+    uint32_t nl = 0;
+    for (uint32_t t = 0; t < G; ++t) {
+      const SubNode &u = cur[t];
+      if (u.split) {
+        const uint32_t kk = u.cnt >> 1;
+        LF[nl].off = u.off;
+        LF[nl++].cnt = kk;
+        LF[nl].off = u.off + kk;
+        LF[nl++].cnt = u.cnt - kk;
+      } else {
+        LF[nl].off = u.off;
+        LF[nl++].cnt = u.cnt;
+      }
+    }
+    M.nl = nl;
+  }
+  __syncthreads();
+  const uint32_t nl = M.nl;
+  if (threadIdx.x < nl) {
+    for (int d = 0; d < 3; ++d) {
+      LF[threadIdx.x].lo[d] = 0xffffffffu;
+      LF[threadIdx.x].hi[d] = 0;
+    }
+  }
+  // kWarps >> lgwl leaf slots of 2^lgwl warps; more leaves than warps: a warp per leaf, in turns
+  uint32_t lgwl = kLgWarps;
+  while (lgwl > 0 && (uint32_t(kWarps) >> lgwl) < nl) --lgwl;
+  const uint32_t WL = 1u << lgwl, slots = uint32_t(kWarps) >> lgwl;
+  const uint32_t lw = uint32_t(warp) & (WL - 1u);  // warp within its leaf group
+  const uint32_t lt = lw * 32 + lane, lstep = WL * 32;
+  const C *const Y0 = X0, *const Y1 = X0 + L::kCodeStride / sizeof(C), *const Y2 = X0 + 2 * (L::kCodeStride / sizeof(C));
+  __syncthreads();
+  // bit boxes: AABB
+  for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots) {
+    const uint32_t off = LF[f].off, cnt = LF[f].cnt;
+    uint32_t mn0 = 0xffffffffu, mn1 = 0xffffffffu, mn2 = 0xffffffffu, mx0 = 0, mx1 = 0, mx2 = 0;
+    for (uint32_t i = lt; i < cnt; i += lstep) {
+      const uint32_t c0 = Y0[off + i], c1 = Y1[off + i], c2 = Y2[off + i];
+      mn0 = min(mn0, c0);
+      mx0 = max(mx0, c0);
+      mn1 = min(mn1, c1);
+      mx1 = max(mx1, c1);
+      mn2 = min(mn2, c2);
+      mx2 = max(mx2, c2);
+    }
+    mn0 = __reduce_min_sync(0xffffffffu, mn0);
+    mn1 = __reduce_min_sync(0xffffffffu, mn1);
+    mn2 = __reduce_min_sync(0xffffffffu, mn2);
+    mx0 = __reduce_max_sync(0xffffffffu, mx0);
+    mx1 = __reduce_max_sync(0xffffffffu, mx1);
+    mx2 = __reduce_max_sync(0xffffffffu, mx2);
+    if (lane == 0) {
+      atomicMin(&LF[f].lo[0], mn0);
+      atomicMin(&LF[f].lo[1], mn1);
+      atomicMin(&LF[f].lo[2], mn2);
+      atomicMax(&LF[f].hi[0], mx0);
+      atomicMax(&LF[f].hi[1], mx1);
+      atomicMax(&LF[f].hi[2], mx2);
+    }
+  }
+  __syncthreads();
+  // centre: least squared distance to the AABB centre, first position on ties
+  {
+    int it = 0;
+    for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots, ++it) {
+      const uint32_t off = LF[f].off, cnt = LF[f].cnt;
+      const long long s0 = (long long)LF[f].lo[0] + LF[f].hi[0], s1 = (long long)LF[f].lo[1] + LF[f].hi[1],
+                      s2 = (long long)LF[f].lo[2] + LF[f].hi[2];
+      unsigned long long bd = ~0ull;
+      uint32_t bp = 0xffffffffu;
+      for (uint32_t i = lt; i < cnt; i += lstep) {
+        const long long e0 = 2ll * Y0[off + i] - s0, e1 = 2ll * Y1[off + i] - s1, e2 = 2ll * Y2[off + i] - s2;
+        const unsigned long long d2 =
+            (unsigned long long)(e0 * e0) + (unsigned long long)(e1 * e1) + (unsigned long long)(e2 * e2);
+        if (d2 < bd) {  // positions rise within a thread: the first minimum is the lowest
+          bd = d2;
+          bp = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (od < bd || (od == bd && op < bp)) {
+          bd = od;
+          bp = op;
+        }
+      }
+      if (lane == 0) {
+        M.wd[warp][it] = bd;
+        M.wp[warp][it] = bp;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nl) {
+    const uint32_t f = threadIdx.x;
+    unsigned long long bd = ~0ull;
+    uint32_t bp = 0xffffffffu;
+    const bool turns = nl > uint32_t(kWarps);
+    const uint32_t w0 = turns ? (f % kWarps) : (f << lgwl), wn = turns ? 1u : WL, it = turns ? (f / kWarps) : 0u;
+    for (uint32_t w = w0; w < w0 + wn; ++w) {
+      const unsigned long long od = M.wd[w][it];
+      const uint32_t op = M.wp[w][it];
+      if (od < bd || (od == bd && op < bp)) {
+        bd = od;
+        bp = op;
+      }
+    }
+    SubLeaf &lf = LF[f];
+    const uint32_t c = bp < lf.cnt ? bp : 0u;
+    const uint32_t q0 = Y0[lf.off + c], q1 = Y1[lf.off + c], q2 = Y2[lf.off + c];
+    const uint32_t m0 = bits_for_range(max(q0 - lf.lo[0], lf.hi[0] - q0));
+    const uint32_t m1 = bits_for_range(max(q1 - lf.lo[1], lf.hi[1] - q1));
+    const uint32_t m2 = bits_for_range(max(q2 - lf.lo[2], lf.hi[2] - q2));
+    lf.qref[0] = int32_t(q0);
+    lf.qref[1] = int32_t(q1);
+    lf.qref[2] = int32_t(q2);
+    lf.centre = c;
+    lf.m = m0 | (m1 << 8) | (m2 << 16);
+    lf.words = uint32_t((uint64_t(m0 + m1 + m2) * (lf.cnt ? lf.cnt - 1 : 0) + 31) >> 5);
+  }
+  __syncthreads();
+
+  // ---- payload words before this node: decoupled look-back ----
+  const uint32_t j = M.j;
+  if (warp == 0) {
+    unsigned long long agg = 0;
+    for (uint32_t f = lane; f < nl; f += 32) agg += LF[f].words;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) agg += __shfl_xor_sync(0xffffffffu, agg, o);
+    if (lane == 0) st_release_u64(a.status + j, (j == 0 ? kStIncl : kStAgg) | agg);
+    unsigned long long prefix = 0;
+    if (j > 0) {
+      long long i = (long long)j - 1;
+      uint32_t spins = 0;
+      for (;;) {
+        const long long q = i - lane;
+        const unsigned long long st = q >= 0 ? ld_acquire_u64(a.status + q) : kStIncl;
+        const unsigned long long flag = st >> 62;
+        const uint32_t incl = __ballot_sync(0xffffffffu, flag == 2), zero = __ballot_sync(0xffffffffu, flag == 0);
+        const int fi = incl ? __ffs(incl) - 1 : 32;
+        const uint32_t rel = fi >= 31 ? 0xffffffffu : ((2u << fi) - 1u);
+        if (zero & rel) {
+          if (++spins > kLookSpin) {
+            if (lane == 0) atomicOr(a.err, kErrTimeout);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        unsigned long long v = lane <= fi ? (st & kStVal) : 0ull;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (fi < 32) break;
+        i -= 32;
+      }
+      if (lane == 0) st_release_u64(a.status + j, kStIncl | (prefix + agg));
+    }
+    if (lane == 0) {
+      if (uint64_t(j) + 1 == (1ull << a.depth)) *a.total_words = prefix + agg;
+      unsigned long long run = prefix;
+      for (uint32_t f = 0; f < nl; ++f) {
+        LF[f].word_off = run;
+        run += LF[f].words;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- leaf records, permutation and packed payload ----
+  const uint64_t off64 = M.off;
+  const uint64_t leaf0 =
+      uint64_t(j) * a.leaves_small + (off64 - uint64_t(j) * (a.n >> a.depth)) * (a.leaves_big - a.leaves_small);
+  uint32_t *sw = reinterpret_cast<uint32_t *>(sm + L::kStage) + warp * 96;
+  uint32_t *payload0 = reinterpret_cast<uint32_t *>(a.out + kHeaderBytes + uint64_t(kLeafBytes) * a.num_leaves);
+  for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots) {
+    const uint32_t foff = LF[f].off, fcnt = LF[f].cnt, centre = LF[f].centre, fm = LF[f].m, words = LF[f].words;
+    const unsigned long long word_off = LF[f].word_off;
+    const uint64_t gl = leaf0 + f, goff = off64 + foff;
+    if (gl >= a.num_leaves || goff + fcnt > a.n || word_off + words > a.payload_cap) {
+      if (lt == 0) atomicOr(a.err, kErrInternal);
+      continue;
+    }
+    const uint32_t r0 = uint32_t(LF[f].qref[0]), r1 = uint32_t(LF[f].qref[1]), r2 = uint32_t(LF[f].qref[2]);
+    if (lt == 0) {
+      uint4 *rec = reinterpret_cast<uint4 *>(a.out + kHeaderBytes + uint64_t(kLeafBytes) * gl);
+      rec[0] = make_uint4(uint32_t(goff), uint32_t(goff >> 32), uint32_t(word_off), uint32_t(word_off >> 32));
+      rec[1] = make_uint4(r0, r1, r2, fm);
+    }
+    if (IDX && a.perm) {
+      const uint32_t *XI = reinterpret_cast<const uint32_t *>(sm + L::kIdx) + M.ilead + foff;
+      for (uint32_t i = lt; i < fcnt; i += lstep) {
+        const uint32_t src = i == 0 ? centre : (i - 1 < centre ? i - 1 : i);
+        a.perm[goff + i] = XI[src];
+      }
+    }
+    const uint32_t m0 = fm & 0xffu, m1 = (fm >> 8) & 0xffu, m2 = (fm >> 16) & 0xffu;
+    const uint32_t w = m0 + m1 + m2;
+    if (w == 0 || fcnt < 2) continue;
+    uint32_t *payload = payload0 + word_off;
+    const uint32_t h0 = m0 ? (1u << (m0 - 1)) - 1u : 0u;
+    const uint32_t h1 = m1 ? (1u << (m1 - 1)) - 1u : 0u;
+    const uint32_t h2 = m2 ? (1u << (m2 - 1)) - 1u : 0u;
+    const uint32_t nsl = fcnt - 1, chunks = (nsl + 31) / 32;
+    const C *x0 = Y0 + foff, *x1 = Y1 + foff, *x2 = Y2 + foff;
+    for (uint32_t ch = lw; ch < chunks; ch += WL) {
+      // this lane's particle as one w-bit value c_x | c_y << m_x | c_z << (m_x + m_y), in three limbs
+      const uint32_t sl = ch * 32 + lane;
+      uint32_t v0 = 0, v1 = 0, v2 = 0;
+      if (sl < nsl) {
+        const uint32_t p = sl < centre ? sl : sl + 1;
+        const uint32_t cx = m0 ? uint32_t(x0[p]) - r0 + h0 : 0u;
+        const uint32_t cy = m1 ? uint32_t(x1[p]) - r1 + h1 : 0u;
+        const uint32_t cz = m2 ? uint32_t(x2[p]) - r2 + h2 : 0u;
+        const unsigned long long y = (unsigned long long)cy << m0;
+        v0 = cx | uint32_t(y);
+        v1 = uint32_t(y >> 32);
+        const uint32_t s2 = m0 + m1;
+        const unsigned long long z = (unsigned long long)cz << (s2 & 31);
+        if (s2 < 32) {
+          v0 |= uint32_t(z);
+          v1 |= uint32_t(z >> 32);
+        } else {
+          v1 |= uint32_t(z);
+          v2 = uint32_t(z >> 32);
+        }
+      }
+      for (uint32_t t = lane; t < w; t += 32) sw[t] = 0;
+      __syncwarp();
+      if (sl < nsl) {
+        const uint32_t b = lane * w, k0 = b >> 5, sh = b & 31;
+        const uint32_t nwd = (sh + w + 31) >> 5;
+        atomicOr(&sw[k0], v0 << sh);
+        if (nwd > 1) atomicOr(&sw[k0 + 1], __funnelshift_l(v0, v1, sh));
+        if (nwd > 2) atomicOr(&sw[k0 + 2], __funnelshift_l(v1, v2, sh));
+        if (nwd > 3) atomicOr(&sw[k0 + 3], __funnelshift_l(v2, 0u, sh));
+      }
+      __syncwarp();
+      for (uint32_t t = lane; t < w; t += 32) {
+        const uint32_t gw = ch * w + t;
+        if (gw < words) __stcs(payload + gw, sw[t]);
+      }
+      __syncwarp();
+    }
+  }
+  // every warp is done with tensor memory before warp 0 frees it
+  tmem_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tmem_fence_after();
+    tmem_dealloc(M.tmem, kTmemCols);
+  }
+}
+
+template <typename C, bool IDX, bool WIDEST>
+cudaError_t subtree_launch(const SubtreeLaunch &a, cudaStream_t st) {
+  const uint32_t smem = SubL<C, IDX>::kTotal;
+  int per_sm = 0;
+  cudaError_t e = resident_blocks<k_subtree<C, IDX, WIDEST>>(kT, smem, &per_sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  TraceScope ts("k_subtree", st);
+  k_subtree<C, IDX, WIDEST><<<unsigned(1ull << a.depth), kT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t subtree_capacity(int code_bytes, bool with_idx) {
+  return code_bytes == 2 ? (with_idx ? SubL<uint16_t, true>::kCap : SubL<uint16_t, false>::kCap)
+                         : (with_idx ? SubL<uint32_t, true>::kCap : SubL<uint32_t, false>::kCap);
+}
+
+cudaError_t launch_subtree(const SubtreeLaunch &a, cudaStream_t st) {
+  if (a.code_bytes == 2) {
+    if (a.idx) return a.widest ? subtree_launch<uint16_t, true, true>(a, st) : subtree_launch<uint16_t, true, false>(a, st);
+    return a.widest ? subtree_launch<uint16_t, false, true>(a, st) : subtree_launch<uint16_t, false, false>(a, st);
+  }
+  if (a.idx) return a.widest ? subtree_launch<uint32_t, true, true>(a, st) : subtree_launch<uint32_t, true, false>(a, st);
+  return a.widest ? subtree_launch<uint32_t, false, true>(a, st) : subtree_launch<uint32_t, false, false>(a, st);
+}
+
+}  // namespace pcx

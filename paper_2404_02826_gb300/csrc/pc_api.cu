@@ -74,6 +74,7 @@ struct Plan {
   uint64_t off_nodes = 0, off_leafrec = 0, off_words = 0;
   uint64_t off_zero = 0, zero_bytes = 0;  // zeroed at every call:
   uint64_t off_hist = 0, off_tiles = 0, off_tickets = 0, off_err = 0, off_total = 0;
+  uint64_t off_status = 0;  // look-back words of the on-chip subtree kernel
   uint64_t off_groups = 0, off_slices = 0;
   uint64_t off_reduce = 0, off_seqrec = 0;  // bit-box reduction: its scratch and the sequence records
   uint64_t off_rorecs = 0, off_roscratch = 0;  // reordering: the records in the new order, its scratch
@@ -84,6 +85,35 @@ struct Plan {
   uint64_t total = 0;
   int range_blocks = 0;
 };
+
+// The on-chip subtree kernel (k_subtree.cu) takes the nodes of one depth D, a
+// CTA each, and finishes their subtrees: the splits of D .. L - 1, the bit
+// boxes and the packing.  D is the shallowest depth whose nodes fit one CTA and
+// that leaves at most kSubMaxLevels splits to it, and at most L - 1 (so every
+// CTA holds a node of the tree, split once more or a leaf); within that, deep
+// enough to give every SM a node where the tree allows.  -1: not used.
+constexpr int kSubMaxLevels = 6;
+constexpr int kSubMaxDepth = 20;  // at most 2^20 CTAs (and look-back words)
+
+uint64_t subtree_status_entries(int levels) {
+  const int d = levels >= 1 ? (levels - 1 < kSubMaxDepth ? levels - 1 : kSubMaxDepth) : 0;
+  return 1ull << d;
+}
+
+int subtree_depth(uint64_t n, uint32_t r, int levels, int code_bytes, bool idx, int sms) {
+  if (n == 0) return -1;
+  const uint64_t cap = subtree_capacity(code_bytes, idx);
+  const int hi = levels >= 1 ? levels - 1 : 0;
+  int lo = levels - kSubMaxLevels > 0 ? levels - kSubMaxLevels : 0;
+  while (lo <= hi && ((n + (1ull << lo) - 1) >> lo) > cap) ++lo;
+  if (lo > hi || lo > kSubMaxDepth || r > cap) return -1;
+  int want = 0;
+  while ((1 << want) < sms) ++want;
+  int d = lo;
+  if (d < want) d = want < hi ? want : hi;
+  if (d > kSubMaxDepth) d = kSubMaxDepth;
+  return d;
+}
 
 // Levels of the median tree that split nodes: node sizes at depth l are
 // floor(n / 2^l) or ceil(n / 2^l), and a node of at most r particles is a leaf.
@@ -220,6 +250,8 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   o = align_up(o + 8 * (tiles ? tiles : 1));
   p.off_tickets = o;
   o = align_up(o + 4 * (p.levels + 1));
+  p.off_status = o;
+  o = align_up(o + 8 * subtree_status_entries(p.levels));
   p.off_err = o;
   o = align_up(o + 4);
   p.off_total = o;
@@ -401,8 +433,13 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     qa.blocks = 8 * device_sm_count();
     PC_TRY(launch_quantize(qa, st));
 
-    // a3: the k-d levels, down to the leaves (autotuning: down to the deepest candidate at most)
+    // a3: the k-d levels, down to the leaves (autotuning: down to the deepest candidate at most);
+    // the deep levels, bit boxes and packing on chip when the plain stream is asked for
     const int levels = p.tune ? p.tune_last : p.levels;
+    const int sub_depth = (p.tune || p.reduce || p.reorder || sweep)
+                              ? -1
+                              : subtree_depth(n, p.r, p.levels, cb, p.idx, device_sm_count());
+    const int global_levels = sub_depth >= 0 ? sub_depth : levels;
     // a4-a5 on the arrangement at depth `depth` (leaves = its 2^depth nodes when split_level = depth - 1)
     auto leaf_launch = [&](void *const *codes, const uint32_t *idxs, int split_level, uint32_t r,
                            uint64_t num_leaves, bool cost_only, bool box_only = false) {
@@ -498,7 +535,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     uint64_t node_base = 0, tile_base = 0;
     void **src = codes_a, **dst = codes_b;
     uint32_t *isrc = idx_a, *idst = idx_b;
-    for (int l = 0; l < levels; ++l) {
+    for (int l = 0; l < global_levels; ++l) {
       if (p.tune && l >= first_depth) {
         // src holds the arrangement at depth l, dst the one at depth l - 1
         uint64_t bytes = 0;
@@ -597,7 +634,32 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
                         r);
     };
     // a4-a5: bit boxes, payload offsets, packing
-    if (!p.tune) {
+    if (sub_depth >= 0) {
+      SubtreeLaunch sa = {};
+      sa.n = n;
+      sa.depth = sub_depth;
+      sa.levels = p.levels - sub_depth;
+      sa.code_bytes = cb;
+      sa.leaf_size = p.r;
+      sa.widest = p.widest;
+      for (int d = 0; d < 3; ++d) {
+        sa.root_hi[d] = L.qmax[d];
+        sa.codes[d] = src[d];
+      }
+      sa.parents = sub_depth > 0 ? nodes + ((1ull << (sub_depth - 1)) - 1) : nullptr;
+      sa.idx = isrc;
+      sa.out = static_cast<uint8_t *>(out);
+      sa.perm = perm;
+      sa.num_leaves = p.num_leaves;
+      sa.leaves_small = leaves_for(n >> sub_depth, p.r);
+      sa.leaves_big = leaves_for((n >> sub_depth) + 1, p.r);
+      sa.status = reinterpret_cast<unsigned long long *>(ws + p.off_status);
+      sa.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + p.levels;
+      sa.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
+      sa.payload_cap = payload_words(out_capacity, p.num_leaves);
+      sa.err = err;
+      PC_TRY(launch_subtree(sa, st));
+    } else if (!p.tune) {
       if (p.reduce) {
         rc = reduce_launch(src, isrc, dst, idst, levels - 1, p.r, p.num_leaves);
         if (rc) return rc;

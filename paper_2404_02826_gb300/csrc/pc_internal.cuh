@@ -195,6 +195,32 @@ cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st);
 cudaError_t launch_leaftable(uint64_t n, int split_level, uint32_t leaf_size, LeafRec *recs, uint64_t num_leaves,
                              cudaStream_t st);
 
+// The deep levels, bit boxes and packing of every node at depth `depth` in
+// one kernel (k_subtree.cu): a CTA per node, `levels` splits inside it.
+struct SubtreeLaunch {
+  uint64_t n;
+  int depth;                  // depth of the CTAs' nodes; the levels above ran as global levels
+  int levels;                 // splits inside a CTA (0: the nodes are the leaves)
+  int code_bytes;
+  uint32_t leaf_size;
+  bool widest;                // widest-cell split axis (else depth mod 3)
+  uint32_t root_hi[3];        // codes of axis d lie in [0, root_hi[d]]
+  const LevelNode *parents;   // the records of depth - 1 (null at depth 0)
+  const void *codes[3];       // arrangement at `depth`
+  const uint32_t *idx;        // input indices in the same arrangement (optional)
+  uint8_t *out;               // stream base
+  uint32_t *perm;             // optional
+  uint64_t num_leaves;
+  uint64_t leaves_small, leaves_big;  // leaves under a node of n >> depth particles, and of one more
+  unsigned long long *status; // [2^depth] look-back words, zero on entry
+  uint32_t *ticket;           // zero on entry
+  uint64_t *total_words;      // written by the last node
+  uint64_t payload_cap;
+  uint32_t *err;
+};
+cudaError_t launch_subtree(const SubtreeLaunch &a, cudaStream_t st);
+uint32_t subtree_capacity(int code_bytes, bool with_idx);  // largest node of one CTA
+
 struct HeaderLaunch {
   uint8_t *out;
   uint64_t n;
