@@ -84,7 +84,7 @@ struct SubL {
   static constexpr uint32_t kIdx = 3 * kCodeStride;
   static constexpr uint32_t kBins = kIdx + (IDX ? al128(kSlots * 4) : 0u);
   static constexpr uint32_t kStage = kBins + al128(kSubBins * 4);
-  static constexpr uint32_t kPart = 3u * uint32_t(R) * kWarps * 4, kPack = kWarps * 96u * 4;
+  static constexpr uint32_t kPart = uint32_t(R) * kWarps * 16, kPack = kWarps * 96u * 4;
   static constexpr uint32_t kSn0 = kStage + al128(kPart > kPack ? kPart : kPack);
   static constexpr uint32_t kSn1 = kSn0 + al128(kWarps * sizeof(SubNode));
   static constexpr uint32_t kLeaf = kSn1 + al128(kWarps * sizeof(SubNode));
@@ -130,16 +130,15 @@ __device__ __forceinline__ void sub_select_init(SubNode &s, uint32_t hb) {
   }
 }
 
-// ---- tensor memory (TMEM) as the staging area of the in-place moves ----
-// A move must read every position of an array before it writes any.  The
-// values wait in tensor memory instead of registers: each thread stores its
-// values to its own lane (tcgen05.st, a warp's 32 lanes of its lane quarter,
-// 32 bits per column), the block synchronises once for all arrays, and each
-// thread loads them back (tcgen05.ld) while it writes them to their places.
-// One warp allocates the columns at the start and frees them at the end.
-// Every tcgen05 instruction here is .sync.aligned: all 32 lanes of the warp
-// must execute it together, so each helper first reconverges the warp (the
-// code before it may have diverged, e.g. one lane issuing copies).
+// ---- tensor memory (TMEM): where each thread keeps its rows between levels ----
+// Between two levels a thread's positions (its rows of its group's subnode)
+// live in its own TMEM lane (tcgen05.st / tcgen05.ld, shape 32x32b: a warp
+// reaches the 32 lanes of its lane quarter, 32 bits per column).  Shared
+// memory only serves the exchange of a level's move: every thread writes its
+// values to their destinations, the block synchronises, and every thread reads
+// its rows of the next level back into TMEM.  One warp allocates the columns
+// at the start and frees them at the end.  Every tcgen05 instruction is
+// .sync.aligned, so each helper first reconverges the warp.
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
   __syncwarp();
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
@@ -153,23 +152,18 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// 8 (or 4) consecutive columns of this thread's lane; complete when the call returns
-__device__ __forceinline__ void tmem_st8(uint32_t t, const uint32_t *v) {
+// 4 consecutive columns of this thread's lane; completes by tmem_wait_st()
+__device__ __forceinline__ void tmem_st4(uint32_t t, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   __syncwarp();
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
-      "tcgen05.wait::st.sync.aligned;" ::"r"(t),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-      : "memory");
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(t), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
 }
-__device__ __forceinline__ void tmem_st4(uint32_t t, const uint32_t *v) {
+__device__ __forceinline__ void tmem_wait_st() {
   __syncwarp();
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n\t"
-      "tcgen05.wait::st.sync.aligned;" ::"r"(t),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
-      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+// 8 consecutive columns, complete when the call returns
 __device__ __forceinline__ void tmem_ld8(uint32_t t, uint32_t *v) {
   __syncwarp();
   asm volatile(
@@ -177,6 +171,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t t, uint32_t *v) {
       "tcgen05.wait::ld.sync.aligned;"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
       : "r"(t)
+      : "memory");
+}
+// 4 columns from each of three places (the x, y, z values of the same rows), one wait
+__device__ __forceinline__ void tmem_ld4x3(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t *v) {
+  __syncwarp();
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%12];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%13];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%14];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11])
+      : "r"(t0), "r"(t1), "r"(t2)
       : "memory");
 }
 __device__ __forceinline__ void tmem_ld4(uint32_t t, uint32_t *v) {
@@ -189,73 +196,45 @@ __device__ __forceinline__ void tmem_ld4(uint32_t t, uint32_t *v) {
       : "memory");
 }
 
-// Stages the positions p = r * Tg + ltid, r < nv, of one array of a subnode in
-// the thread's columns from `taddr`: column c holds rows 2c and 2c + 1 (16-bit
-// values) or row c (32-bit values).
-template <int R, typename E>
-__device__ __forceinline__ void stage_rows(const E *A, uint32_t nv, uint32_t Tg, uint32_t ltid, uint32_t taddr) {
-  constexpr int NC = sizeof(E) == 2 ? R / 2 : R;
-#pragma unroll
-  for (int c0 = 0; c0 < NC; c0 += 8) {
-    uint32_t v[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      v[c] = 0;
-      if (c0 + c < NC) {
-        if constexpr (sizeof(E) == 2) {
-          const int r = 2 * (c0 + c);
-          const uint32_t p0 = uint32_t(r) * Tg + ltid;
-          const uint32_t x0 = uint32_t(r) < nv ? uint32_t(A[p0]) : 0u;
-          const uint32_t x1 = uint32_t(r + 1) < nv ? uint32_t(A[p0 + Tg]) : 0u;
-          v[c] = x0 | (x1 << 16);
-        } else {
-          const int r = c0 + c;
-          v[c] = uint32_t(r) < nv ? uint32_t(A[uint32_t(r) * Tg + ltid]) : 0u;
-        }
-      }
-    }
-    if (c0 + 8 <= NC) tmem_st8(taddr + uint32_t(c0), v);
-    else tmem_st4(taddr + uint32_t(c0), v);
+// Up to 8 columns (`left` of them remain in the array; a compile-time value
+// after unrolling), the rest zero.
+__device__ __forceinline__ void tmem_ld_cols(uint32_t t, uint32_t *v, int left) {
+  if (left >= 8) {
+    tmem_ld8(t, v);
+  } else {
+    tmem_ld4(t, v);
+    v[4] = v[5] = v[6] = v[7] = 0;
   }
 }
 
-// The halves of a packed word as opaque operations: the moves of a level
-// unpack the same destinations, and sharing the unpacked values between them
-// would double the registers they hold.
-__device__ __forceinline__ uint32_t half_lo(uint32_t x) {
-  uint32_t y;
-  asm volatile("and.b32 %0, %1, 0xffff;" : "=r"(y) : "r"(x));
-  return y;
-}
-__device__ __forceinline__ uint32_t half_hi(uint32_t x) {
-  uint32_t y;
-  asm volatile("shr.b32 %0, %1, 16;" : "=r"(y) : "r"(x));
-  return y;
+// Value of row r of a thread's array from its columns: 16-bit values two rows
+// per column (rows 2c and 2c + 1 in column c), 32-bit values one row each.
+template <typename E>
+__device__ __forceinline__ uint32_t row_of(const uint32_t *cols, int r) {
+  if constexpr (sizeof(E) == 2) return (cols[r >> 1] >> (16 * (r & 1))) & 0xffffu;
+  else return cols[r];
 }
 
-// Writes an array's staged values to their destinations dpk (two 16-bit
-// positions per word: rows 2i and 2i + 1 in word i).
+// Reads the rows p = r * Tg + ltid (r < nv) of one array of a subnode from
+// shared memory into the thread's columns from `taddr` (completion:
+// tmem_wait_st).
 template <int R, typename E>
-__device__ __forceinline__ void unstage_rows(E *A, const uint32_t *dpk, uint32_t nv, uint32_t taddr) {
+__device__ __forceinline__ void load_rows(const E *A, uint32_t nv, uint32_t Tg, uint32_t ltid, uint32_t taddr) {
   constexpr int NC = sizeof(E) == 2 ? R / 2 : R;
+  constexpr int RPC = sizeof(E) == 2 ? 2 : 1;  // rows per column
 #pragma unroll
-  for (int c0 = 0; c0 < NC; c0 += 8) {
-    uint32_t v[8];
-    if (c0 + 8 <= NC) tmem_ld8(taddr + uint32_t(c0), v);
-    else tmem_ld4(taddr + uint32_t(c0), v);
+  for (int c0 = 0; c0 < NC; c0 += 4) {
+    uint32_t v[4];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if (c0 + c < NC) {
-        if constexpr (sizeof(E) == 2) {
-          const int r = 2 * (c0 + c);
-          if (uint32_t(r) < nv) A[half_lo(dpk[r >> 1])] = E(v[c] & 0xffffu);
-          if (uint32_t(r + 1) < nv) A[half_hi(dpk[r >> 1])] = E(v[c] >> 16);
-        } else {
-          const int r = c0 + c;
-          if (uint32_t(r) < nv) A[(r & 1) ? half_hi(dpk[r >> 1]) : half_lo(dpk[r >> 1])] = E(v[c]);
-        }
+    for (int c = 0; c < 4; ++c) {
+      v[c] = 0;
+#pragma unroll
+      for (int h = 0; h < RPC; ++h) {
+        const int r = RPC * (c0 + c) + h;
+        if (uint32_t(r) < nv) v[c] |= uint32_t(A[uint32_t(r) * Tg + ltid]) << (16 * h);
       }
     }
+    tmem_st4(taddr + uint32_t(c0), v[0], v[1], v[2], v[3]);
   }
 }
 
@@ -265,9 +244,8 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
   constexpr int R = L::R;
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t *bins = reinterpret_cast<uint32_t *>(sm + L::kBins);
-  uint32_t *LM = reinterpret_cast<uint32_t *>(sm + L::kStage);  // [R][32] masks of code < v
-  uint32_t *TM = LM + R * kWarps;                                // [R][32] masks of code == v
-  uint32_t *PRE = TM + R * kWarps;                               // [R][32] scan of the packed counts
+  // per (row, warp): scan of the packed counts, mask of code < v, mask of code == v
+  uint4 *S4 = reinterpret_cast<uint4 *>(sm + L::kStage);
   SubNode *cur = reinterpret_cast<SubNode *>(sm + L::kSn0);
   SubNode *nxt = reinterpret_cast<SubNode *>(sm + L::kSn1);
   SubLeaf *LF = reinterpret_cast<SubLeaf *>(sm + L::kLeaf);
@@ -340,6 +318,19 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
   C *const X0 = reinterpret_cast<C *>(sm) + M.lead;
 
   // ---- the levels inside the CTA ----
+  constexpr int NC = L::kCodeCols;                 // TMEM columns of one code array
+  constexpr int RPC = sizeof(C) == 2 ? 2 : 1;      // rows per column
+  constexpr uint32_t S = L::kCodeStride / sizeof(C);
+  uint32_t *const XI = reinterpret_cast<uint32_t *>(sm + L::kIdx) + M.ilead;
+  if (a.levels > 0) {  // the root's rows into TMEM (level 0: one group of all warps)
+    const uint32_t cnt0 = cur[0].cnt;
+    const uint32_t nv0 = cnt0 > threadIdx.x ? (cnt0 - threadIdx.x + kT - 1u) / kT : 0u;
+    load_rows<R>(X0, nv0, kT, threadIdx.x, tcol);
+    load_rows<R>(X0 + S, nv0, kT, threadIdx.x, tcol + NC);
+    load_rows<R>(X0 + 2 * S, nv0, kT, threadIdx.x, tcol + 2 * NC);
+    if (IDX) load_rows<R>(XI, nv0, kT, threadIdx.x, tcol + 3 * NC);
+    tmem_wait_st();
+  }
   for (int k = 0; k < a.levels; ++k) {
     const int lgW = kLgWarps - k;  // log2 of the warps per group
     const uint32_t G = 1u << k;
@@ -347,24 +338,30 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
     const uint32_t Tg = uint32_t(kT) >> k;
     const uint32_t ltid = threadIdx.x & (Tg - 1u);
     const uint32_t BPG = kSubBins >> k, hb = 11u - uint32_t(k);
+    const uint32_t soff = cur[g].off, scnt = cur[g].cnt;
+    const uint32_t nv = scnt > ltid ? (scnt - ltid + Tg - 1u) / Tg : 0u;  // rows of this thread in its subnode
+    const uint32_t tax = tcol + cur[g].axis * NC;                           // columns of the split axis
     if (threadIdx.x < G) sub_select_init(cur[threadIdx.x], hb);
-    // radix select of every splitting subnode, one digit per pass
+    // radix select of every splitting subnode, one digit per pass, from the rows in TMEM
     bool any = __syncthreads_or(threadIdx.x < G && cur[threadIdx.x].width != 0);
     while (any) {
       const uint32_t width = cur[g].width;
       const bool act = width != 0;
       if (act) {
-        const uint32_t soff = cur[g].off, scnt = cur[g].cnt, lo = cur[g].lo, prefix = cur[g].prefix;
-        const uint32_t shift = uint32_t(cur[g].shift);
-        const C *A = X0 + cur[g].axis * (L::kCodeStride / sizeof(C)) + soff;
+        const uint32_t lo = cur[g].lo, prefix = cur[g].prefix, shift = uint32_t(cur[g].shift);
         const uint32_t mask = (1u << width) - 1u;
         uint32_t *hg = bins + uint32_t(g) * BPG;
-#pragma unroll 4
-        for (int r = 0; r < R; ++r) {
-          const uint32_t p = uint32_t(r) * Tg + ltid;
-          if (p < scnt) {
-            const uint32_t hbk = (uint32_t(A[p]) - lo) >> shift;
-            if ((hbk >> width) == prefix) atomicAdd(&hg[hbk & mask], 1u);
+#pragma unroll
+        for (int c0 = 0; c0 < NC; c0 += 8) {
+          uint32_t v[8];
+          tmem_ld_cols(tax + uint32_t(c0), v, NC - c0);
+#pragma unroll
+          for (int i = 0; i < 8 * RPC; ++i) {
+            const int r = RPC * c0 + i;
+            if (r < R && uint32_t(r) < nv) {
+              const uint32_t hbk = (row_of<C>(v, i) - lo) >> shift;
+              if ((hbk >> width) == prefix) atomicAdd(&hg[hbk & mask], 1u);
+            }
           }
         }
       }
@@ -392,7 +389,7 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
         uint32_t base = 0;
         for (int w = g << lgW; w < warp; ++w) base += M.wt[w];
         uint32_t ex = base + incl - x;
-        const uint32_t target = (cur[g].cnt >> 1) - cur[g].below;
+        const uint32_t target = (scnt >> 1) - cur[g].below;
         if (x && ex <= target && target < ex + x) {
           uint32_t e = 0;
           while (e + 1 < kBinsPer && target >= ex + h[e]) ex += h[e++];
@@ -420,22 +417,26 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
       any = __syncthreads_or(still);
     }
 
-    const uint32_t soff = cur[g].off, scnt = cur[g].cnt;
     const bool split = cur[g].split != 0;
     // classification: masks of code < v and code == v per (row, warp)
     {
-      const C *A = X0 + cur[g].axis * (L::kCodeStride / sizeof(C)) + soff;
       const uint32_t v = cur[g].v;
-#pragma unroll 4
-      for (int r = 0; r < R; ++r) {
-        const uint32_t p = uint32_t(r) * Tg + ltid;
-        const bool valid = split && p < scnt;
-        const uint32_t c = valid ? uint32_t(A[p]) : 0u;
-        const uint32_t lm = __ballot_sync(0xffffffffu, valid && c < v);
-        const uint32_t tm = __ballot_sync(0xffffffffu, valid && c == v);
-        if (lane == 0) {
-          LM[r * kWarps + warp] = lm;
-          TM[r * kWarps + warp] = tm;
+#pragma unroll
+      for (int c0 = 0; c0 < NC; c0 += 8) {
+        uint32_t cv[8];
+        tmem_ld_cols(tax + uint32_t(c0), cv, NC - c0);
+#pragma unroll
+        for (int i = 0; i < 8 * RPC; ++i) {
+          const int r = RPC * c0 + i;
+          if (r >= R) break;
+          const bool valid = split && uint32_t(r) < nv;
+          const uint32_t c = row_of<C>(cv, i);
+          const uint32_t lm = __ballot_sync(0xffffffffu, valid && c < v);
+          const uint32_t tm = __ballot_sync(0xffffffffu, valid && c == v);
+          if (lane == 0) {
+            S4[r * kWarps + warp].y = lm;
+            S4[r * kWarps + warp].z = tm;
+          }
         }
       }
     }
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
           const uint32_t rem = i - gi * per_group;
           const uint32_t row = rem >> lgW, w = rem & ((1u << lgW) - 1u);
           slot[e] = row * kWarps + (gi << lgW) + w;
-          cx[e] = (uint32_t(__popc(LM[slot[e]])) << 16) | uint32_t(__popc(TM[slot[e]]));
+          cx[e] = (uint32_t(__popc(S4[slot[e]].y)) << 16) | uint32_t(__popc(S4[slot[e]].z));
         }
         sum += cx[e];
       }
@@ -484,81 +485,99 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
       for (uint32_t e = 0; e < kEPT; ++e) {
         const uint32_t i = threadIdx.x * kEPT + e;
         if (i < kE) {
-          PRE[slot[e]] = ex;
+          S4[slot[e]].x = ex;
           if (i % per_group == 0) M.gb[i / per_group] = ex;
         }
         ex += cx[e];
       }
     }
     __syncthreads();
-    // destinations within the subnode, two 16-bit positions per register
-    uint32_t dpk[R / 2];
-    const uint32_t nv = scnt > ltid ? (scnt - ltid + Tg - 1u) / Tg : 0u;  // rows of this thread inside the subnode
+    // the move: every row from TMEM to its destination in shared memory
     {
       const uint32_t kk = scnt >> 1, gbase = M.gb[g], tleft = cur[g].tleft;
+      C *const A0 = X0 + soff, *const A1 = X0 + S + soff, *const A2 = X0 + 2 * S + soff;
+      uint32_t *const AI = XI + soff;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const uint32_t p = uint32_t(r) * Tg + ltid;
-        uint32_t dst = p;
-        if (split) {
-          const uint32_t P = PRE[r * kWarps + warp] - gbase;
-          const uint32_t lm = LM[r * kWarps + warp], tm = TM[r * kWarps + warp];
-          const uint32_t lb = (P >> 16) + uint32_t(__popc(lm & ltm));
-          const uint32_t tb = (P & 0xffffu) + uint32_t(__popc(tm & ltm));
-          const bool left = ((lm >> lane) & 1u) || (((tm >> lane) & 1u) && tb < tleft);
-          const uint32_t gl = lb + min(tb, tleft);
-          dst = left ? gl : kk + p - gl;
-          if (uint32_t(r) < nv && dst >= scnt) {
-            atomicOr(a.err, kErrInternal);
-            dst = p;
+      for (int c0 = 0; c0 < NC; c0 += 4) {
+        uint32_t v[12];
+        tmem_ld4x3(tcol + uint32_t(c0), tcol + uint32_t(NC + c0), tcol + uint32_t(2 * NC + c0), v);
+        uint32_t vi[4 * RPC];
+        if (IDX) {
+          tmem_ld4(tcol + uint32_t(3 * NC + RPC * c0), vi);
+          if (RPC == 2) tmem_ld4(tcol + uint32_t(3 * NC + RPC * c0 + 4), vi + 4);
+        }
+#pragma unroll
+        for (int i = 0; i < 4 * RPC; ++i) {
+          const int r = RPC * c0 + i;
+          if (uint32_t(r) < nv) {
+            const uint32_t p = uint32_t(r) * Tg + ltid;
+            uint32_t dst = p;
+            if (split) {
+              const uint4 e = S4[r * kWarps + warp];
+              const uint32_t P = e.x - gbase;
+              const uint32_t lb = (P >> 16) + uint32_t(__popc(e.y & ltm));
+              uint32_t gl;
+              bool left;
+              if (e.z == 0) {  // no code of this warp's row equals v
+                gl = lb + min(P & 0xffffu, tleft);
+                left = (e.y >> lane) & 1u;
+              } else {
+                const uint32_t tb = (P & 0xffffu) + uint32_t(__popc(e.z & ltm));
+                left = ((e.y >> lane) & 1u) || (((e.z >> lane) & 1u) && tb < tleft);
+                gl = lb + min(tb, tleft);
+              }
+              dst = left ? gl : kk + p - gl;
+              if (dst >= scnt) {
+                atomicOr(a.err, kErrInternal);
+                dst = p;
+              }
+            }
+            A0[dst] = C(row_of<C>(v, i));
+            A1[dst] = C(row_of<C>(v + 4, i));
+            A2[dst] = C(row_of<C>(v + 8, i));
+            if (IDX) AI[dst] = vi[i];
           }
         }
-        if (r & 1) dpk[r >> 1] |= dst << 16;
-        else dpk[r >> 1] = dst & 0xffffu;
       }
-    }
-    // the moves: every array staged in tensor memory, one barrier, then written to its place
-    {
-      constexpr uint32_t S = L::kCodeStride / sizeof(C);
-      uint32_t *XI = reinterpret_cast<uint32_t *>(sm + L::kIdx) + M.ilead;
-      stage_rows<R>(X0 + soff, nv, Tg, ltid, tcol);
-      stage_rows<R>(X0 + S + soff, nv, Tg, ltid, tcol + L::kCodeCols);
-      stage_rows<R>(X0 + 2 * S + soff, nv, Tg, ltid, tcol + 2 * L::kCodeCols);
-      if (IDX) stage_rows<R>(XI + soff, nv, Tg, ltid, tcol + 3 * L::kCodeCols);
-      __syncthreads();
-      unstage_rows<R>(X0 + soff, dpk, nv, tcol);
-      unstage_rows<R>(X0 + S + soff, dpk, nv, tcol + L::kCodeCols);
-      unstage_rows<R>(X0 + 2 * S + soff, dpk, nv, tcol + 2 * L::kCodeCols);
-      if (IDX) unstage_rows<R>(XI + soff, dpk, nv, tcol + 3 * L::kCodeCols);
-      __syncthreads();
     }
     // children of every subnode (every subnode above the last level splits)
-    if (k + 1 < a.levels) {
-      if (threadIdx.x < G) {
-        const SubNode &u = cur[threadIdx.x];
-        if (!u.split) atomicOr(a.err, kErrInternal);
-        const uint32_t kk = u.cnt >> 1;
-        SubNode &cl = nxt[2 * threadIdx.x], &cr = nxt[2 * threadIdx.x + 1];
-        for (int d = 0; d < 3; ++d) {
-          cl.blo[d] = cr.blo[d] = u.blo[d];
-          cl.bhi[d] = cr.bhi[d] = u.bhi[d];
-        }
-        cl.bhi[u.axis] = u.v;
-        cr.blo[u.axis] = u.v;
-        cl.off = u.off;
-        cl.cnt = kk;
-        cr.off = u.off + kk;
-        cr.cnt = u.cnt - kk;
-        const uint32_t ax = uint32_t((a.depth + k + 1) % 3);
-        cl.axis = WIDEST ? widest_axis(cl.blo, cl.bhi) : ax;
-        cr.axis = WIDEST ? widest_axis(cr.blo, cr.bhi) : ax;
-        cl.split = cl.cnt > a.leaf_size;
-        cr.split = cr.cnt > a.leaf_size;
+    if (k + 1 < a.levels && threadIdx.x < G) {
+      const SubNode &u = cur[threadIdx.x];
+      if (!u.split) atomicOr(a.err, kErrInternal);
+      const uint32_t kk = u.cnt >> 1;
+      SubNode &cl = nxt[2 * threadIdx.x], &cr = nxt[2 * threadIdx.x + 1];
+      for (int d = 0; d < 3; ++d) {
+        cl.blo[d] = cr.blo[d] = u.blo[d];
+        cl.bhi[d] = cr.bhi[d] = u.bhi[d];
       }
-      __syncthreads();
+      cl.bhi[u.axis] = u.v;
+      cr.blo[u.axis] = u.v;
+      cl.off = u.off;
+      cl.cnt = kk;
+      cr.off = u.off + kk;
+      cr.cnt = u.cnt - kk;
+      const uint32_t ax = uint32_t((a.depth + k + 1) % 3);
+      cl.axis = WIDEST ? widest_axis(cl.blo, cl.bhi) : ax;
+      cr.axis = WIDEST ? widest_axis(cr.blo, cr.bhi) : ax;
+      cl.split = cl.cnt > a.leaf_size;
+      cr.split = cr.cnt > a.leaf_size;
+    }
+    __syncthreads();  // the level's arrangement is complete in shared memory
+    if (k + 1 < a.levels) {
       SubNode *t = cur;
       cur = nxt;
       nxt = t;
+      // this thread's rows of the next level back into TMEM
+      const int g2 = warp >> (lgW - 1);
+      const uint32_t Tg2 = Tg >> 1, ltid2 = threadIdx.x & (Tg2 - 1u);
+      const uint32_t off2 = cur[g2].off, cnt2 = cur[g2].cnt;
+      const uint32_t nv2 = cnt2 > ltid2 ? (cnt2 - ltid2 + Tg2 - 1u) / Tg2 : 0u;
+      load_rows<R>(X0 + off2, nv2, Tg2, ltid2, tcol);
+      load_rows<R>(X0 + S + off2, nv2, Tg2, ltid2, tcol + NC);
+      load_rows<R>(X0 + 2 * S + off2, nv2, Tg2, ltid2, tcol + 2 * NC);
+      if (IDX) load_rows<R>(XI + off2, nv2, Tg2, ltid2, tcol + 3 * NC);
+      tmem_wait_st();
+      // the next level's moves overwrite shared memory only after its selection's barriers
     }
   }
 
@@ -626,31 +645,52 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
     }
   }
   __syncthreads();
-  // centre: least squared distance to the AABB centre, first position on ties
+  // centre: least squared distance to the AABB centre, first position on ties.
+  // When every side of the box is below 2^15 codes, |2q - lo - hi| < 2^15 and
+  // the squared distance is exact in 32 bits; otherwise it is formed in 64.
   {
     int it = 0;
     for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots, ++it) {
       const uint32_t off = LF[f].off, cnt = LF[f].cnt;
-      const long long s0 = (long long)LF[f].lo[0] + LF[f].hi[0], s1 = (long long)LF[f].lo[1] + LF[f].hi[1],
-                      s2 = (long long)LF[f].lo[2] + LF[f].hi[2];
-      unsigned long long bd = ~0ull;
-      uint32_t bp = 0xffffffffu;
-      for (uint32_t i = lt; i < cnt; i += lstep) {
-        const long long e0 = 2ll * Y0[off + i] - s0, e1 = 2ll * Y1[off + i] - s1, e2 = 2ll * Y2[off + i] - s2;
-        const unsigned long long d2 =
-            (unsigned long long)(e0 * e0) + (unsigned long long)(e1 * e1) + (unsigned long long)(e2 * e2);
-        if (d2 < bd) {  // positions rise within a thread: the first minimum is the lowest
-          bd = d2;
-          bp = i;
+      const uint32_t l0 = LF[f].lo[0], l1 = LF[f].lo[1], l2 = LF[f].lo[2];
+      const uint32_t u0 = LF[f].hi[0], u1 = LF[f].hi[1], u2 = LF[f].hi[2];
+      unsigned long long bd;
+      uint32_t bp;
+      if (max(u0 - l0, max(u1 - l1, u2 - l2)) < 32768u) {
+        const int s0 = int(l0 + u0), s1 = int(l1 + u1), s2 = int(l2 + u2);
+        uint32_t md = 0xffffffffu, mp = 0xffffffffu;
+        for (uint32_t i = lt; i < cnt; i += lstep) {
+          const int e0 = 2 * int(Y0[off + i]) - s0, e1 = 2 * int(Y1[off + i]) - s1, e2 = 2 * int(Y2[off + i]) - s2;
+          const uint32_t d2 = uint32_t(e0 * e0) + uint32_t(e1 * e1) + uint32_t(e2 * e2);
+          if (d2 < md) {  // positions rise within a thread: the first minimum is the lowest
+            md = d2;
+            mp = i;
+          }
         }
-      }
+        const uint32_t wmd = __reduce_min_sync(0xffffffffu, md);
+        bp = __reduce_min_sync(0xffffffffu, md == wmd ? mp : 0xffffffffu);
+        bd = wmd;
+      } else {
+        const long long s0 = (long long)l0 + u0, s1 = (long long)l1 + u1, s2 = (long long)l2 + u2;
+        bd = ~0ull;
+        bp = 0xffffffffu;
+        for (uint32_t i = lt; i < cnt; i += lstep) {
+          const long long e0 = 2ll * Y0[off + i] - s0, e1 = 2ll * Y1[off + i] - s1, e2 = 2ll * Y2[off + i] - s2;
+          const unsigned long long d2 =
+              (unsigned long long)(e0 * e0) + (unsigned long long)(e1 * e1) + (unsigned long long)(e2 * e2);
+          if (d2 < bd) {
+            bd = d2;
+            bp = i;
+          }
+        }
 #pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
-        const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
-        if (od < bd || (od == bd && op < bp)) {
-          bd = od;
-          bp = op;
+        for (int o = 16; o; o >>= 1) {
+          const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+          const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+          if (od < bd || (od == bd && op < bp)) {
+            bd = od;
+            bp = op;
+          }
         }
       }
       if (lane == 0) {
@@ -771,6 +811,10 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
     const uint32_t h1 = m1 ? (1u << (m1 - 1)) - 1u : 0u;
     const uint32_t h2 = m2 ? (1u << (m2 - 1)) - 1u : 0u;
     const uint32_t nsl = fcnt - 1, chunks = (nsl + 31) / 32;
+    // w <= 32: word k of a chunk takes bits from lanes i0 = 32k / w on (at most nit of them)
+    const uint32_t i0 = w <= 32 ? (32u * lane) / w : 0u;
+    const int sh0 = int(i0 * w) - int(32u * lane);
+    const uint32_t nit = w <= 32 ? (31u + w) / w + 1u : 0u;
     const C *x0 = Y0 + foff, *x1 = Y1 + foff, *x2 = Y2 + foff;
     for (uint32_t ch = lw; ch < chunks; ch += WL) {
       // this lane's particle as one w-bit value c_x | c_y << m_x | c_z << (m_x + m_y), in three limbs
@@ -794,22 +838,35 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
           v2 = uint32_t(z >> 32);
         }
       }
-      for (uint32_t t = lane; t < w; t += 32) sw[t] = 0;
-      __syncwarp();
-      if (sl < nsl) {
-        const uint32_t b = lane * w, k0 = b >> 5, sh = b & 31;
-        const uint32_t nwd = (sh + w + 31) >> 5;
-        atomicOr(&sw[k0], v0 << sh);
-        if (nwd > 1) atomicOr(&sw[k0 + 1], __funnelshift_l(v0, v1, sh));
-        if (nwd > 2) atomicOr(&sw[k0 + 2], __funnelshift_l(v1, v2, sh));
-        if (nwd > 3) atomicOr(&sw[k0 + 3], __funnelshift_l(v2, 0u, sh));
+      if (w <= 32) {
+        // lane k assembles word k of the chunk from the lanes whose values overlap it
+        uint32_t word = 0;
+        for (uint32_t t = 0; t < nit; ++t) {
+          const uint32_t i = i0 + t;
+          const uint32_t vi = __shfl_sync(0xffffffffu, v0, i & 31u);
+          const int sh = sh0 + int(t * w);
+          if (i < 32 && sh < 32) word |= sh >= 0 ? (vi << sh) : (vi >> -sh);
+        }
+        const uint32_t gw = ch * w + lane;
+        if (lane < w && gw < words) __stcs(payload + gw, word);
+      } else {
+        for (uint32_t t = lane; t < w; t += 32) sw[t] = 0;
+        __syncwarp();
+        if (sl < nsl) {
+          const uint32_t b = lane * w, k0 = b >> 5, sh = b & 31;
+          const uint32_t nwd = (sh + w + 31) >> 5;
+          atomicOr(&sw[k0], v0 << sh);
+          if (nwd > 1) atomicOr(&sw[k0 + 1], __funnelshift_l(v0, v1, sh));
+          if (nwd > 2) atomicOr(&sw[k0 + 2], __funnelshift_l(v1, v2, sh));
+          if (nwd > 3) atomicOr(&sw[k0 + 3], __funnelshift_l(v2, 0u, sh));
+        }
+        __syncwarp();
+        for (uint32_t t = lane; t < w; t += 32) {
+          const uint32_t gw = ch * w + t;
+          if (gw < words) __stcs(payload + gw, sw[t]);
+        }
+        __syncwarp();
       }
-      __syncwarp();
-      for (uint32_t t = lane; t < w; t += 32) {
-        const uint32_t gw = ch * w + t;
-        if (gw < words) __stcs(payload + gw, sw[t]);
-      }
-      __syncwarp();
     }
   }
   // every warp is done with tensor memory before warp 0 frees it
