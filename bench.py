@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the untimed extras of the default run: the other workloads' one-line results, "
+                         "the batch-256 and serve-2000 summaries")
     return ap.parse_args()
 
 
@@ -222,6 +225,8 @@ def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False, launches
         "k_leafbox": 3 * cb * n,
         "k_leafpack": 3 * cb * n + stream_bytes,
         "k_decode": stream_bytes + 3 * esz * n,
+        # the deep levels, bit boxes and packing on chip: every particle's codes read once, the stream written
+        "k_subtree": 3 * cb * n + idx * n + stream_bytes,
     }.get(kernel)
 
 
@@ -445,6 +450,12 @@ def run_ours(args, spec):
         cpu = cpu_baseline(spec, args.leaf_size, CPU_SAMPLE // 4 if args.reduce else CPU_SAMPLE, args.reduce,
                            args.reorder, args.widest)
 
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == DEFAULT_WORKLOAD:
+        del comp, dec
+        torch.cuda.empty_cache()
+        extras = run_extras(pc, dev, pos, args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -460,11 +471,16 @@ def run_ours(args, spec):
             "particles_per_s": round(world * n * args.steps / (total_ms / 1e3), 1),
             "compression_ratio": round(nbytes / size, 4), "bits_per_particle": round(8 * size / n, 4),
             "step_hbm_frac_algorithmic": round(step_alg / (total_ms / args.steps / 1e3) / 1e9 / peak, 4),
+            # each direction's algorithmic bytes (positions read + stream written; stream read +
+            # positions written) over its own time, against the measured HBM copy bandwidth
+            "compress_hbm_frac_algorithmic": round((nbytes + size) / (comp_ms / args.steps / 1e3) / 1e9 / peak, 4),
+            "decompress_hbm_frac_algorithmic": round((nbytes + size) / (dec_ms / args.steps / 1e3) / 1e9 / peak, 4),
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
             "quality": quality, "e2e": e2e, "cpu_baseline": cpu,
         }
         if lossless:
             line["lossless"] = lossless
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -502,6 +518,70 @@ def measure_e2e(pc, pos_h, pdt, emode, eb, args, world, cfg):
     return {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": int(hp.nbytes + size),
             "d2h_bytes_per_step": int(size + hp.nbytes), "steps": args.e2e_steps,
             "api": "pc_compress_host + pc_decompress_host (pinned host buffers)"}
+
+
+def direction_times(pc, pos, pdt, emode, eb, steps, warmup=3):
+    """Compress and decompress GB/s (uncompressed bytes) and the compression ratio of one
+    snapshot resident on the device, CUDA events on the current stream."""
+    import torch
+
+    n = pos.shape[0]
+    comp = pc.Compressor(n, pdt, device=pos.device)
+    dec = torch.empty_like(pos)
+    st = torch.cuda.current_stream()
+    size = 0
+    for _ in range(warmup):
+        size = comp.compress(pos, emode, eb)
+        comp.decompress(comp.out, dec, size)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for e in ev:
+        e[0].record(st)
+        size = comp.compress(pos, emode, eb)
+        e[1].record(st)
+        comp.decompress(comp.out, dec, size)
+        e[2].record(st)
+    torch.cuda.synchronize()
+    c_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    d_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+    nbytes = pos.numel() * pos.element_size()
+    peak, _ = peaks()
+    del comp, dec
+    return {"compress_gbs": round(nbytes / c_ms / 1e6, 3), "decompress_gbs": round(nbytes / d_ms / 1e6, 3),
+            "round_trip_gbs": round(nbytes / (c_ms + d_ms) / 1e6, 3), "compression_ratio": round(nbytes / size, 4),
+            "compress_hbm_frac_algorithmic": round((nbytes + size) / c_ms / 1e6 / peak, 4),
+            "decompress_hbm_frac_algorithmic": round((nbytes + size) / d_ms / 1e6 / peak, 4), "steps": steps}
+
+
+def run_extras(pc, dev, pos, args):
+    """Untimed extras of the default run (they do not enter `value`): the other bound of the
+    cosmology workload on the same snapshot, the fluid workload, and compact batch-256 and
+    serve-2000 summaries (the full lines come from --workload batch-256 / serve-2000)."""
+    import torch
+
+    out = {"workloads": {}}
+    out["workloads"]["cosmology-2^27-f32-rel1e-3"] = direction_times(pc, pos, pc.PC_F32, pc.PC_EB_REL, 1e-3, 5)
+    gen, n, dtype, mode, eb = WORKLOADS["fluid-2^24-f64-abs1e-4"]
+    fl = torch.from_numpy(generate(gen, n, dtype, seed=0)).to(dev)
+    out["workloads"]["fluid-2^24-f64-abs1e-4"] = direction_times(pc, fl, pc.PC_F64, pc.PC_EB_ABS, eb, 5)
+    del fl
+    torch.cuda.empty_cache()
+    b = batch_measure(pc, dev, 1, 0, steps=2, warmup=1)
+    out["batch"] = {"workload": BATCH_WORKLOAD, "snapshots": b["snapshots"], "particles": b["particles"],
+                    "lanes": b["lanes"], "batched_round_trip_gbs": b["batched"]["round_trip_gbs"],
+                    "one_call_per_snapshot_round_trip_gbs": b["one_call_per_snapshot"]["round_trip_gbs"],
+                    "speedup_round_trip": b["speedup_round_trip"], "identical_sizes": b["identical_sizes"],
+                    "compression_ratio": b["compression_ratio"], "steps": 2}
+    torch.cuda.empty_cache()
+    v = serve_measure(pc, dev, 1, 0)
+    out["serve"] = {"workload": SERVE_WORKLOAD, "requests": v["requests"], "lanes": v["lanes"],
+                    "p50_ms": v["served"]["p50_ms"], "p99_ms": v["served"]["p99_ms"],
+                    "one_lane_p50_ms": v["one_lane"]["p50_ms"], "one_lane_p99_ms": v["one_lane"]["p99_ms"],
+                    "saturated_gbs": v["saturated"]["lanes"]["gbs"],
+                    "saturated_one_lane_gbs": v["saturated"]["one_lane"]["gbs"]}
+    torch.cuda.empty_cache()
+    return out
 
 
 BATCH_WORKLOAD = "batch-256"
@@ -544,22 +624,12 @@ def _pools(dev, size, gens, dtypes):
     return out
 
 
-def run_batch(args):
+def batch_measure(pc, dev, world, rank, steps, warmup):
     """Many snapshots of uneven size, dtype and bound: one pc_compress_batch (and
     pc_decompress_batch) call against one plain call per snapshot."""
     import numpy as np
     import torch
 
-    import paper_2404_02826_gb300 as pc
-    from paper_2404_02826_gb300 import build as pcbuild
-
-    world, rank, local = dist_setup(args)
-    if rank == 0:
-        pcbuild.build()
-    barrier(world)
-    pc.load()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     rng = np.random.default_rng(rank)
     pool_n = 1 << 24
     pools = _pools(dev, pool_n, ("cosmology", "fluid"), ("f32", "f64"))
@@ -604,10 +674,10 @@ def run_batch(args):
 
     results = {}
     for name, fn in (("sequential", sequential), ("batched", batched)):
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             fn()
         tc = td = 0.0
-        for _ in range(args.steps):
+        for _ in range(steps):
             barrier(world)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -618,42 +688,22 @@ def run_batch(args):
             td += t2 - t1
         tc = max_over_ranks(tc, world)
         td = max_over_ranks(td, world)
-        results[name] = {"compress_gbs": round(whole_job_gbs(world, nbytes, args.steps, 1e3 * tc), 3),
-                         "decompress_gbs": round(whole_job_gbs(world, nbytes, args.steps, 1e3 * td), 3),
-                         "round_trip_gbs": round(whole_job_gbs(world, nbytes, args.steps, 1e3 * (tc + td)), 3),
-                         "ms_per_batch": round(1e3 * (tc + td) / args.steps, 3)}
+        results[name] = {"compress_gbs": round(whole_job_gbs(world, nbytes, steps, 1e3 * tc), 3),
+                         "decompress_gbs": round(whole_job_gbs(world, nbytes, steps, 1e3 * td), 3),
+                         "round_trip_gbs": round(whole_job_gbs(world, nbytes, steps, 1e3 * (tc + td)), 3),
+                         "ms_per_batch": round(1e3 * (tc + td) / steps, 3)}
         results[name + "_sizes"] = sizes
-    # the batched streams are the plain calls' streams
-    same = results["batched_sizes"] == results["sequential_sizes"]
-    if rank == 0:
-        b, q = results["batched"], results["sequential"]
-        line = {
-            "metric": "batched compress+decompress throughput (uncompressed bytes)", "value": b["round_trip_gbs"],
-            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 1),
-            "ms_per_step": b["ms_per_batch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "snapshots": len(jobs), "particles": particles,
-                       "sizes": "round(10^U(4,7))", "generators": "cosmology or fluid slices, p = 1/2",
-                       "eb": "rel, one of 1e-2 1e-3 1e-4", "leaf_size": "autotuned (64..12000)", "lanes": lanes,
-                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
-            "batched": b, "one_call_per_snapshot": q,
-            "speedup_round_trip": round(b["round_trip_gbs"] / q["round_trip_gbs"], 3),
-            "identical_sizes": bool(same),
-            "compression_ratio": round(nbytes / sum(results["batched_sizes"]), 4),
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.destroy_process_group()
+    b, q = results["batched"], results["sequential"]
+    out = {"snapshots": len(jobs), "particles": particles, "lanes": lanes, "batched": b, "one_call_per_snapshot": q,
+           "speedup_round_trip": round(b["round_trip_gbs"] / q["round_trip_gbs"], 3),
+           # the batched streams are the plain calls' streams
+           "identical_sizes": bool(results["batched_sizes"] == results["sequential_sizes"]),
+           "compression_ratio": round(nbytes / sum(results["batched_sizes"]), 4)}
+    del pools, jobs, outs, ws, decs, seq
+    return out
 
 
-def run_serve(args, lanes_list=(8, 1)):
-    """Poisson arrivals of compress (70 %) and decompress (30 %) requests through
-    the library's serving loop; latency from submission to completion.  The
-    same trace also runs saturated (every request submitted at once), where the
-    overlap of several lanes shows as throughput."""
-    import numpy as np
+def run_batch(args):
     import torch
 
     import paper_2404_02826_gb300 as pc
@@ -666,6 +716,37 @@ def run_serve(args, lanes_list=(8, 1)):
     pc.load()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    r = batch_measure(pc, dev, world, rank, args.steps, args.warmup)
+    if rank == 0:
+        b = r["batched"]
+        line = {
+            "metric": "batched compress+decompress throughput (uncompressed bytes)", "value": b["round_trip_gbs"],
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": b["ms_per_batch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "snapshots": r["snapshots"], "particles": r["particles"],
+                       "sizes": "round(10^U(4,7))", "generators": "cosmology or fluid slices, p = 1/2",
+                       "eb": "rel, one of 1e-2 1e-3 1e-4", "leaf_size": "autotuned (64..12000)", "lanes": r["lanes"],
+                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
+            "batched": b, "one_call_per_snapshot": r["one_call_per_snapshot"],
+            "speedup_round_trip": r["speedup_round_trip"], "identical_sizes": r["identical_sizes"],
+            "compression_ratio": r["compression_ratio"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def serve_measure(pc, dev, world, rank, lanes_list=(8, 1)):
+    """Poisson arrivals of compress (70 %) and decompress (30 %) requests through
+    the library's serving loop; latency from submission to completion.  The
+    same trace also runs saturated (every request submitted at once), where the
+    overlap of several lanes shows as throughput."""
+    import numpy as np
+    import torch
+
     rng = np.random.default_rng(rank)
     pool_n = 50_000_000
     pool = torch.from_numpy(generate("cosmology", pool_n, "f32", seed=0)).to(dev)
@@ -725,19 +806,38 @@ def run_serve(args, lanes_list=(8, 1)):
                          "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
                          "mean_ms": round(float(lat_ms.mean()), 3),
                          "gbs": round(done_bytes / (t_last - t_first) / 1e9, 3)}
+    del arena, pool
+    return {"requests": count, "lanes": lanes_list[0], "served": report[(lanes_list[0], 1.0)],
+            "one_lane": report[(lanes_list[-1], 1.0)],
+            "saturated": {"lanes": report[(lanes_list[0], 0.0)], "one_lane": report[(lanes_list[-1], 0.0)],
+                          "note": "all requests submitted at once"}}
+
+
+def run_serve(args):
+    import torch
+
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as pcbuild
+
+    world, rank, local = dist_setup(args)
     if rank == 0:
-        best = report[(lanes_list[0], 1.0)]
+        pcbuild.build()
+    barrier(world)
+    pc.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    r = serve_measure(pc, dev, world, rank)
+    if rank == 0:
+        best = r["served"]
         line = {
             "metric": "served compress/decompress latency p99 (arrival to completion)", "value": best["p99_ms"],
-            "unit": "ms", "n_gpus": world, "steps": count, "warmup": 0, "ms_per_step": best["mean_ms"],
+            "unit": "ms", "n_gpus": world, "steps": r["requests"], "warmup": 0, "ms_per_step": best["mean_ms"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": SERVE_WORKLOAD, "requests": count, "arrivals": "Poisson, 200 per s",
+            "config": {"workload": SERVE_WORKLOAD, "requests": r["requests"], "arrivals": "Poisson, 200 per s",
                        "mix": "70 % compress, 30 % decompress of a completed stream",
                        "sizes": "round(10^U(5, log10 5e7)) particles, slices of one cosmology snapshot",
-                       "eb": "rel 1e-3 or 1e-4", "arena_bytes": 40 << 30, "lanes": lanes_list[0]},
-            "served": best, "one_lane": report[(lanes_list[-1], 1.0)],
-            "saturated": {"lanes": report[(lanes_list[0], 0.0)], "one_lane": report[(lanes_list[-1], 0.0)],
-                          "note": "all requests submitted at once"},
+                       "eb": "rel 1e-3 or 1e-4", "arena_bytes": 40 << 30, "lanes": r["lanes"]},
+            "served": best, "one_lane": r["one_lane"], "saturated": r["saturated"],
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "throughput_gbs": best["gbs"],
         }
         print(json.dumps(line), flush=True)
