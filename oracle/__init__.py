@@ -54,7 +54,8 @@ def build(force: bool = False, parallel: bool = False) -> str:
 class _Bound(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("delta_max", ctypes.c_double),
                 ("eps", ctypes.c_double), ("eb_prime", ctypes.c_double), ("s", ctypes.c_double),
-                ("o", ctypes.c_double * 3), ("qmax", ctypes.c_int64 * 3)]
+                ("o", ctypes.c_double * 3), ("qmax", ctypes.c_int64 * 3), ("raw", ctypes.c_uint32),
+                ("raw_cause", ctypes.c_int)]
 
 
 _libs = {}
@@ -125,6 +126,8 @@ class Bound:
     s: float
     o: tuple
     qmax: tuple
+    raw: int = 0        # bit d: axis d stored losslessly (Sec. 4.1, m_d > M)
+    raw_cause: int = 0  # EB_TOO_SMALL (no lattice meets eps) or RANGE (codes of 2^30 or more)
 
 
 def error_bound(pos, eb_mode: int, eb: float) -> Bound:
@@ -135,16 +138,20 @@ def error_bound(pos, eb_mode: int, eb: float) -> Bound:
                                   eb_mode, float(eb), ctypes.byref(b))
     if rc:
         raise OracleError(rc, "error_bound")
-    return Bound(tuple(b.lo), tuple(b.hi), b.delta_max, b.eps, b.eb_prime, b.s, tuple(b.o), tuple(b.qmax))
+    return Bound(tuple(b.lo), tuple(b.hi), b.delta_max, b.eps, b.eb_prime, b.s, tuple(b.o), tuple(b.qmax), b.raw,
+                 b.raw_cause)
 
 
 def quantize(pos, eb_mode: int, eb: float) -> np.ndarray:
-    """Sec. 3: lattice codes q[n, 3] (int64)."""
+    """Sec. 3: lattice codes q[n, 3] (int64); on an axis stored losslessly, its split key."""
     pos = _positions(pos)
     b = error_bound(pos, eb_mode, eb)
     cb = _Bound()
     cb.o[:] = b.o
     cb.s = b.s
+    cb.lo[:] = b.lo
+    cb.hi[:] = b.hi
+    cb.raw = b.raw
     q = np.zeros((pos.shape[0], 3), np.int64)
     lib().oracle_quantize(pos.ctypes.data if pos.size else None, pos.shape[0], _dtype_code(pos),
                           ctypes.byref(cb), q.ctypes.data)

@@ -36,7 +36,13 @@
  *     distance to the AABB centre, first in leaf order on ties;
  *   - a zero minimum or maximum is taken as +0 (signed zeros compare equal);
  *   - the centre is stored as its lattice code (not as a lossless float) and the
- *     particle count replaces the end mark; see the stream layout below.
+ *     particle count replaces the end mark; see the stream layout below;
+ *   - lossless axes (Sec. 4.1: a dimension whose m_d exceeds M is stored as the
+ *     original coordinates): codes here stay below 2^30 (m_d <= 31), so an axis
+ *     whose code range reaches 2^30, or every axis when no lattice meets eps
+ *     within the type's resolution (eb' <= 0), is stored losslessly in every
+ *     leaf; the tree splits such an axis on the key
+ *     floor((p - lo) / (hi - lo) * 2^29), monotone in the coordinate.
  *
  * Precision: compile with -ffp-contract=off so that no multiply-add is fused.
  */
@@ -61,6 +67,7 @@
 #define OR_REL 1
 
 #define OR_CODE_LIMIT (1LL << 30) /* codes must be < 2^30, so m_d <= 31 */
+#define OR_RAW_KEY_TOP 536870912.0 /* 2^29: largest split key of a lossless axis */
 #define OR_HEADER_BYTES 96u
 #define OR_LEAF_BYTES 32u
 
@@ -75,7 +82,9 @@ typedef struct {
     double eb_prime;      /* eps minus the rounding margin                        */
     double s;             /* lattice step = 2 * eb'                               */
     double o[3];          /* lattice origin = per-axis minimum                    */
-    int64_t qmax[3];      /* largest code per axis                                */
+    int64_t qmax[3];      /* largest code per axis (split key of a lossless axis) */
+    uint32_t raw;         /* bit d: axis d stored losslessly (Sec. 4.1, m_d > M)   */
+    int raw_cause;        /* why: OR_ERR_EB_TOO_SMALL (no lattice) or OR_ERR_RANGE  */
 } oracle_bound;
 
 static double coord(const void *pos, int dtype, uint64_t i, int d)
@@ -101,6 +110,18 @@ static int64_t quantize_one(double p, double o, double s)
 {
     double t = (p - o) / s;
     return (int64_t)nearbyint(t);
+}
+
+/* Split key of a coordinate on a lossless axis: its place in [lo, hi] on a
+ * grid of 2^29 steps (monotone in p; the coordinate itself is stored). */
+static int64_t raw_key(double p, double lo, double hi)
+{
+    double span = hi - lo;
+    if (!(span > 0.0)) return 0;
+    double t = floor(((p - lo) / span) * OR_RAW_KEY_TOP);
+    if (t < 0.0) t = 0.0;
+    if (t > OR_RAW_KEY_TOP) t = OR_RAW_KEY_TOP;
+    return (int64_t)t;
 }
 
 int oracle_error_bound(const void *pos, uint64_t n, int dtype, int eb_mode, double eb,
@@ -167,12 +188,24 @@ int oracle_error_bound(const void *pos, uint64_t n, int dtype, int eb_mode, doub
     double ulp_t = (dtype == OR_F32) ? grid_spacing(m2, 24, -126) : grid_spacing(m2, 53, -1022);
     double ulp_d = grid_spacing(m2, 53, -1022);
     b->eb_prime = b->eps - ulp_t - 4.0 * ulp_d;
-    if (!(b->eb_prime > 0.0)) return OR_ERR_EB_TOO_SMALL;
-    b->s = 2.0 * b->eb_prime;
-    for (int d = 0; d < 3; d++) {
-        b->qmax[d] = quantize_one(b->hi[d], b->o[d], b->s);
-        if (b->qmax[d] >= OR_CODE_LIMIT) return OR_ERR_RANGE;
+    if (!(b->eb_prime > 0.0)) {
+        /* No lattice keeps the bound through the rounding to the type: every
+         * axis is stored losslessly (the step is then unused and 1). */
+        b->raw = 7u;
+        b->raw_cause = OR_ERR_EB_TOO_SMALL;
+        b->s = 1.0;
+    } else {
+        b->s = 2.0 * b->eb_prime;
+        for (int d = 0; d < 3; d++) {
+            b->qmax[d] = quantize_one(b->hi[d], b->o[d], b->s);
+            if (b->qmax[d] >= OR_CODE_LIMIT) { /* wider than the codes: this axis losslessly */
+                b->raw |= 1u << d;
+                b->raw_cause = OR_ERR_RANGE;
+            }
+        }
     }
+    for (int d = 0; d < 3; d++)
+        if (b->raw & (1u << d)) b->qmax[d] = raw_key(b->hi[d], b->lo[d], b->hi[d]);
     return OR_OK;
 }
 
@@ -184,7 +217,9 @@ int oracle_quantize(const void *pos, uint64_t n, int dtype, const oracle_bound *
 {
 #pragma omp parallel for
     for (uint64_t i = 0; i < n; i++)
-        for (int d = 0; d < 3; d++) q[3 * i + d] = quantize_one(coord(pos, dtype, i, d), b->o[d], b->s);
+        for (int d = 0; d < 3; d++)
+            q[3 * i + d] = (b->raw & (1u << d)) ? raw_key(coord(pos, dtype, i, d), b->lo[d], b->hi[d])
+                                                 : quantize_one(coord(pos, dtype, i, d), b->o[d], b->s);
     return OR_OK;
 }
 
@@ -391,13 +426,17 @@ int oracle_bitbox(const int64_t *leafq, uint64_t n, uint64_t *centre, int64_t lo
 /* Header, 96 bytes, little-endian:                                          */
 /*   0 "PCB1"  4 u16 version=1  6 u8 dtype  7 u8 eb_mode  8 u64 n             */
 /*   16 f64 eb as given  24 f64 eps  32 f64 s  40 f64 o[3]                    */
-/*   64 u64 num_leaves  72 u64 payload_words  80 u32 leaf_size  84..95 zero   */
+/*   64 u64 num_leaves  72 u64 payload_words  80 u32 leaf_size                 */
+/*   84 u8 lossless-axis mask (bit d: axis d)  85..95 zero                     */
 /* Leaf table, 32 bytes per sequence (leaf), in leaf order:                  */
 /*   0 u64 first output particle  8 u64 first payload word                   */
 /*   16 i32 q_ref[3] (centre code)  28 u8 m[3]  31 u8 zero                    */
 /* Payload: u32 words.  Each leaf starts on a fresh word; its non-centre      */
 /* particles follow in leaf order, each as c_x (m_x bits), c_y, c_z, packed   */
 /* least-significant bit first.  c_d = (q_d - q_ref_d) + 2^(m_d-1) - 1.        */
+/* With a nonzero lossless-axis mask every leaf lists all its particles, the   */
+/* centre first, then the rest in leaf order; a lossless axis has m_d = M      */
+/* (32 or 64) and q_ref_d = 0, and its field is the coordinate's M-bit pattern. */
 /* ------------------------------------------------------------------------ */
 
 static void put_u16(uint8_t *p, uint16_t v)
@@ -523,9 +562,19 @@ int oracle_compress_rule(const void *pos, uint64_t n, int dtype, int eb_mode, do
         free(leafq);
     }
     if (nomem) goto done;
+    /* Lossless axes (Sec. 4.1, m_d > M): M bits of the coordinate for every
+     * particle of the leaf, the centre included. */
+    const uint32_t M = dtype == OR_F32 ? 32u : 64u;
+    for (uint64_t L = 0; L < nl; L++)
+        for (int d = 0; d < 3; d++)
+            if (b.raw & (1u << d)) {
+                mm[3 * L + d] = M;
+                qref[3 * L + d] = 0;
+            }
     uint64_t total_words = 0;
     for (uint64_t L = 0; L < nl; L++) {
-        uint64_t bits = (uint64_t)(mm[3 * L] + mm[3 * L + 1] + mm[3 * L + 2]) * (lcnt[L] - 1);
+        uint64_t w = (uint64_t)(mm[3 * L] + mm[3 * L + 1] + mm[3 * L + 2]);
+        uint64_t bits = b.raw ? w * lcnt[L] : w * (lcnt[L] - 1);
         wofs[L] = total_words;
         total_words += (bits + 31) / 32;
     }
@@ -545,6 +594,7 @@ int oracle_compress_rule(const void *pos, uint64_t n, int dtype, int eb_mode, do
     put_u64(buf + 64, nl);
     put_u64(buf + 72, total_words);
     put_u32(buf + 80, (uint32_t)leaf_size);
+    buf[84] = (uint8_t)b.raw;
     words = calloc(total_words ? total_words : 1, sizeof(uint32_t));
     if (!words) goto done;
 
@@ -561,6 +611,32 @@ int oracle_compress_rule(const void *pos, uint64_t n, int dtype, int eb_mode, do
         uint64_t outpos = loff[L];
         perm[outpos++] = order[loff[L] + centre[L]];
         uint64_t bitpos = 32 * wofs[L];
+        if (b.raw) {
+            /* every particle, the centre first: lossless axes as M-bit patterns */
+            for (uint64_t k = 0; k < lcnt[L]; k++) {
+                uint64_t i = k == 0 ? centre[L] : (k - 1 < centre[L] ? k - 1 : k);
+                uint64_t id = order[loff[L] + i];
+                if (k > 0) perm[outpos++] = id;
+                for (int d = 0; d < 3; d++) {
+                    uint32_t md = mm[3 * L + d];
+                    if (b.raw & (1u << d)) {
+                        uint64_t bitsval;
+                        if (dtype == OR_F32) {
+                            uint32_t u;
+                            memcpy(&u, (const float *)pos + 3 * id + d, 4);
+                            bitsval = u;
+                        } else {
+                            memcpy(&bitsval, (const double *)pos + 3 * id + d, 8);
+                        }
+                        write_bits(words, &bitpos, bitsval, md);
+                    } else if (md) {
+                        int64_t c = (q[3 * id + d] - qref[3 * L + d]) + ((1LL << (md - 1)) - 1);
+                        write_bits(words, &bitpos, (uint64_t)c, md);
+                    }
+                }
+            }
+            continue;
+        }
         for (uint64_t i = 0; i < lcnt[L]; i++) {
             if (i == centre[L]) continue;
             uint64_t id = order[loff[L] + i];
@@ -696,6 +772,7 @@ int oracle_compress_reduced(const void *pos, uint64_t n, int dtype, int eb_mode,
     oracle_bound b;
     int rc = oracle_error_bound(pos, n, dtype, eb_mode, eb, &b);
     if (rc) return rc;
+    if (b.raw) return b.raw_cause; /* the reduction needs codes on every axis */
     int64_t *q = NULL, *scratch = NULL, *sq = NULL;
     uint64_t *order = NULL, *loff = NULL, *lcnt = NULL, *perm = NULL, *slot = NULL, *seq_ids = NULL;
     uint64_t *seq_first = NULL, *seq_wofs = NULL, nl = 0;
@@ -959,6 +1036,7 @@ int oracle_reorder(const uint8_t *st, uint64_t bytes, const uint64_t *perm_in, u
     int dtype;
     int rc = oracle_stream_header(st, bytes, &n, &dtype, &nl, &nw);
     if (rc) return rc;
+    if (st[84]) return OR_ERR_ARG; /* R-indices need codes on every axis */
     const uint8_t *tab = st + OR_HEADER_BYTES;
     const uint8_t *pay = tab + OR_LEAF_BYTES * nl;
     uint32_t *words = malloc((nw ? nw : 1) * sizeof(uint32_t));
@@ -1082,6 +1160,10 @@ int oracle_decompress(const uint8_t *st, uint64_t bytes, void *out, uint64_t out
     if (out_capacity_bytes < 3 * esz * n) return OR_ERR_CAPACITY;
     double s = get_f64(st + 32), o[3];
     for (int d = 0; d < 3; d++) o[d] = get_f64(st + 40 + 8 * d);
+    const uint32_t raw = st[84], M = dtype == OR_F32 ? 32u : 64u;
+    if (raw > 7u) return OR_ERR_CORRUPT;
+    for (int i = 85; i < 96; i++)
+        if (st[i]) return OR_ERR_CORRUPT;
     const uint8_t *tab = st + OR_HEADER_BYTES;
     const uint8_t *pay = tab + OR_LEAF_BYTES * nl;
     uint32_t *words = malloc((nw ? nw : 1) * sizeof(uint32_t));
@@ -1096,13 +1178,16 @@ int oracle_decompress(const uint8_t *st, uint64_t bytes, void *out, uint64_t out
         uint64_t po = get_u64(rec), wo = get_u64(rec + 8);
         uint64_t pend = (L + 1 < nl) ? get_u64(rec + OR_LEAF_BYTES) : n;
         uint32_t m[3];
-        for (int d = 0; d < 3; d++) m[d] = rec[28 + d];
-        if ((L == 0 && po != 0) || pend <= po || pend > n || wo != expect_word || m[0] > 31 || m[1] > 31 ||
-            m[2] > 31) {
+        int bad = 0;
+        for (int d = 0; d < 3; d++) {
+            m[d] = rec[28 + d];
+            bad |= (raw & (1u << d)) ? m[d] != M : m[d] > 31;
+        }
+        if ((L == 0 && po != 0) || pend <= po || pend > n || wo != expect_word || bad) {
             rc = OR_ERR_CORRUPT;
             break;
         }
-        uint64_t bits = (uint64_t)(m[0] + m[1] + m[2]) * (pend - po - 1);
+        uint64_t bits = (uint64_t)(m[0] + m[1] + m[2]) * (raw ? pend - po : pend - po - 1);
         expect_word = wo + (bits + 31) / 32;
         if (expect_word > nw) {
             rc = OR_ERR_CORRUPT;
@@ -1125,8 +1210,19 @@ int oracle_decompress(const uint8_t *st, uint64_t bytes, void *out, uint64_t out
             uint64_t bitpos = 32 * wo;
             for (uint64_t i = 0; i < cnt; i++) {
                 for (int d = 0; d < 3; d++) {
+                    if (raw & (1u << d)) { /* the coordinate's own bits */
+                        uint64_t u = read_bits(words, bitpos, M);
+                        bitpos += M;
+                        if (dtype == OR_F32) {
+                            uint32_t u32 = (uint32_t)u;
+                            memcpy((float *)out + 3 * (po + i) + d, &u32, 4);
+                        } else {
+                            memcpy((double *)out + 3 * (po + i) + d, &u, 8);
+                        }
+                        continue;
+                    }
                     int64_t qd = qref[d];
-                    if (i > 0 && m[d] > 0) {
+                    if ((i > 0 || raw) && m[d] > 0) {
                         uint64_t c = read_bits(words, bitpos, m[d]);
                         bitpos += m[d];
                         qd = qref[d] + (int64_t)c - ((1LL << (m[d] - 1)) - 1);

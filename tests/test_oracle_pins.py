@@ -296,15 +296,23 @@ def test_rejections(oracle_mod):
     with pytest.raises(oracle_mod.OracleError) as e:
         oracle_mod.compress(bad, oracle_mod.ABS, 0.1)
     assert e.value.code == oracle_mod.ERR_NONFINITE
-    # eps below the float32 spacing at the data's magnitude
+    # eps below the float32 spacing at the data's magnitude: no lattice keeps the
+    # bound, every axis is stored losslessly (Sec. 4.1, m_d > M); the bit-box
+    # reduction, which needs codes, still refuses with the cause
     far = np.array([[1e6, 0, 0], [1e6 + 64, 1, 1]], np.float32)
+    assert oracle_mod.error_bound(far, oracle_mod.ABS, 1e-3).raw == 7
+    stream, perm = oracle_mod.compress(far, oracle_mod.ABS, 1e-3)
+    assert oracle_mod.decompress(stream).tobytes() == far[perm].tobytes()
     with pytest.raises(oracle_mod.OracleError) as e:
-        oracle_mod.compress(far, oracle_mod.ABS, 1e-3)
+        oracle_mod.compress_reduced(far, oracle_mod.ABS, 1e-3)
     assert e.value.code == oracle_mod.ERR_EB_TOO_SMALL
-    # codes beyond 2^30
+    # codes beyond 2^30 on x only: x losslessly, y and z as codes
     wide = np.array([[0, 0, 0], [1.0, 0, 0]], np.float64)
+    assert oracle_mod.error_bound(wide, oracle_mod.ABS, 1e-10).raw == 1
+    stream, perm = oracle_mod.compress(wide, oracle_mod.ABS, 1e-10)
+    assert oracle_mod.decompress(stream)[:, 0].tobytes() == wide[perm][:, 0].tobytes()
     with pytest.raises(oracle_mod.OracleError) as e:
-        oracle_mod.compress(wide, oracle_mod.ABS, 1e-10)
+        oracle_mod.compress_reduced(wide, oracle_mod.ABS, 1e-10)
     assert e.value.code == oracle_mod.ERR_RANGE
 
 
