@@ -31,15 +31,26 @@
  *      8 u64 n            16 f64 eb (as given)          24 f64 eps (absolute bound)
  *     32 f64 s (lattice step)                           40 f64 o[3] (origin)
  *     64 u64 num_leaves   72 u64 payload_words          80 u32 leaf_size
- *     84..95 zero
+ *     84 u8 lossless-axis mask (bit d: axis d)              85..95 zero
  *   leaf table, 32 bytes per leaf (one sequence of Fig. 4 each), in k-d order:
  *      0 u64 index of the leaf's first decoded particle
  *      8 u64 index of the leaf's first payload word
- *     16 i32 q_ref[3] (lattice code of the bit-box centre)
- *     28 u8 m[3] (bits per axis, 0..31)   31 u8 zero
+ *     16 i32 q_ref[3] (lattice code of the bit-box centre; 0 on a lossless axis)
+ *     28 u8 m[3] (bits per axis, 0..31; M = 32 or 64 on a lossless axis)   31 u8 zero
  *   payload: u32 words.  Each leaf starts on a word boundary; its non-centre
  *     particles follow in leaf order as c_x (m_x bits), c_y, c_z, packed least
  *     significant bit first, with c_d = (q_d - q_ref_d) + 2^(m_d-1) - 1.
+ *   Lossless axes (Sec. 4.1: a dimension whose m_d would exceed M, M = 32 for
+ *     float and 64 for double, is stored as the original coordinates).  Codes
+ *     here have at most 30 bits (m_d <= 31); an axis whose code range reaches
+ *     2^30, or every axis when eps is below the rounding margin of the type
+ *     (no lattice keeps the bound through the rounding to T), is stored
+ *     losslessly in every leaf.  Then every leaf's payload holds all its
+ *     particles, the centre first, and a lossless field is the coordinate's
+ *     M-bit pattern.  The tree splits such an axis on the key
+ *     floor((p - min) / (max - min) * 2^29).  The bit-box reduction, the
+ *     reordering and the leaf-size search need codes on every axis and return
+ *     PC_ERR_EB_TOO_SMALL or PC_ERR_RANGE for such inputs.
  *   Stream size = 96 + 32 * num_leaves + 4 * payload_words bytes.
  *   Decoding emits, leaf by leaf, the centre and then the other particles;
  *   particle order is not preserved (the paper keeps positions only, Sec. 2).
@@ -58,8 +69,11 @@ typedef enum {
     PC_OK = 0,
     PC_ERR_ARG = 1,          /* null pointer, bad dtype/mode, eb <= 0 or not finite, n >= 2^31, bad leaf size, misalignment */
     PC_ERR_NONFINITE = 2,    /* NaN or Inf among the positions */
-    PC_ERR_EB_TOO_SMALL = 3, /* eb' = eps - ulp_T(M2) - 4 ulp_f64(M2) <= 0, M2 = 2 max(max|p|, eps) */
-    PC_ERR_RANGE = 4,        /* some code >= 2^30, or M2 above the largest finite T */
+    PC_ERR_EB_TOO_SMALL = 3, /* eb' = eps - ulp_T(M2) - 4 ulp_f64(M2) <= 0, M2 = 2 max(max|p|, eps), with the
+                                bit-box reduction, the reordering or the leaf-size search (the plain stream
+                                stores such axes losslessly) */
+    PC_ERR_RANGE = 4,        /* M2 above the largest finite T; or some code >= 2^30 with the reduction,
+                                the reordering or the leaf-size search */
     PC_ERR_CAPACITY = 5,     /* output or workspace too small */
     PC_ERR_CORRUPT = 6,      /* stream fails validation (magic, version, sizes, widths, offsets) */
     PC_ERR_TIMEOUT = 7,      /* a bounded device wait expired; the output is invalid */
@@ -151,13 +165,16 @@ typedef struct {
     uint64_t payload_words;
     uint32_t leaf_size;
     uint64_t total_bytes; /* 96 + 32 num_leaves + 4 payload_words */
+    uint32_t lossless_axes; /* bit d: axis d stored as the original coordinates (Sec. 4.1, m_d > M) */
 } pc_info;
 
 /* Worst-case stream size for n particles with this config, in bytes (host only). */
 int pc_compress_bound(uint64_t n, int dtype, const pc_config *cfg, uint64_t *out_bytes);
 
-/* Device scratch needed by pc_compress, in bytes (host only).  with_perm != 0
- * sizes it for the optional permutation output. */
+/* Device scratch needed by pc_compress, in bytes (host only).  It always has
+ * room for the input indices (the permutation output needs them, and so do
+ * lossless axes, which only the value range reveals); with_perm is accepted
+ * for compatibility and does not change the size. */
 int pc_compress_workspace_size(uint64_t n, int dtype, const pc_config *cfg, int with_perm, uint64_t *out_bytes);
 
 /* Compress n particles (Sec. 3, Sec. 4.1, Sec. 4.2).
@@ -178,17 +195,19 @@ int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, doubl
  * output buffers, and latency-critical paths where cudaMalloc / cudaFree could
  * synchronise the device.  It behaves like pc_compress without `perm`, but its
  * scratch is a library-owned static device array of PC_NOALLOC_SCRATCH_BYTES
- * (32 MiB) that each GPU using it keeps until the process exits:
+ * (48 MiB) that each GPU using it keeps until the process exits:
  *   - problems whose scratch exceeds the array (above about 2^20 particles at
  *     the default leaf size; pc_compress_workspace_size tells) return
  *     PC_ERR_CAPACITY before any work;
  *   - the first call on a device looks up the array's device address and
- *     caches it: make that first call before any stream capture;
+ *     caches it: make that first call before any stream capture; a
+ *     cudaDeviceReset of that device invalidates the cached address, so the
+ *     entry point must not be called on it after such a reset;
  *   - all calls on a device share the array; what must start at zero is
  *     cleared by every call, but calls that overlap on the GPU race on it and
  *     must be serialised by the caller;
  *   - no allocation happens while kernel tracing (pc_trace_enable) is off. */
-#define PC_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define PC_NOALLOC_SCRATCH_BYTES (48u << 20)
 int pc_compress_noalloc(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                         void *out, uint64_t out_capacity, uint64_t *out_size, void *stream);
 

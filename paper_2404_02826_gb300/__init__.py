@@ -58,7 +58,7 @@ EXPORTS = (
 )
 PC_REQ_COMPRESS = 0
 PC_REQ_DECOMPRESS = 1
-PC_NOALLOC_SCRATCH_BYTES = 32 << 20
+PC_NOALLOC_SCRATCH_BYTES = 48 << 20
 
 
 class PCError(RuntimeError):
@@ -76,7 +76,7 @@ class pc_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("dtype", ctypes.c_uint32), ("eb_mode", ctypes.c_uint32),
                 ("eb", ctypes.c_double), ("eps", ctypes.c_double), ("s", ctypes.c_double),
                 ("o", ctypes.c_double * 3), ("num_leaves", ctypes.c_uint64), ("payload_words", ctypes.c_uint64),
-                ("leaf_size", ctypes.c_uint32), ("total_bytes", ctypes.c_uint64)]
+                ("leaf_size", ctypes.c_uint32), ("total_bytes", ctypes.c_uint64), ("lossless_axes", ctypes.c_uint32)]
 
 
 class pc_compress_item(ctypes.Structure):
@@ -239,7 +239,7 @@ def pc_compress(positions, eb_mode: int, eb: float, out, workspace, leaf_size: i
 def pc_compress_noalloc(positions, eb_mode: int, eb: float, out, leaf_size: int = 0, stream=None) -> int:
     """Compress with the library's static scratch (no device allocation by the library).
 
-    For callers that may not allocate device memory; the scratch is a 32 MiB
+    For callers that may not allocate device memory; the scratch is a 48 MiB
     array per GPU shared by all calls, so calls must not overlap on the GPU.
     Problems that do not fit raise PCError with PC_ERR_CAPACITY."""
     n = positions.shape[0] if positions.dim() == 2 else positions.numel() // 3
@@ -264,6 +264,7 @@ class StreamInfo:
     payload_words: int
     leaf_size: int
     total_bytes: int
+    lossless_axes: int = 0  # bit d: axis d stored as the original coordinates (Sec. 4.1, m_d > M)
 
 
 def pc_stream_info(header: bytes) -> StreamInfo:
@@ -271,7 +272,7 @@ def pc_stream_info(header: bytes) -> StreamInfo:
     buf = ctypes.create_string_buffer(bytes(header), len(header))
     _check(_lib().pc_stream_info(buf, len(header), ctypes.byref(info)), "pc_stream_info")
     return StreamInfo(info.n, info.dtype, info.eb_mode, info.eb, info.eps, info.s, tuple(info.o), info.num_leaves,
-                      info.payload_words, info.leaf_size, info.total_bytes)
+                      info.payload_words, info.leaf_size, info.total_bytes, info.lossless_axes)
 
 
 def pc_decompress_workspace_size(n: int) -> int:

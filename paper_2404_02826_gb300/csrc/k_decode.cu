@@ -71,7 +71,7 @@ struct ChunkInfo {
 // per axis (any m-bit field, the unused all-ones one included), is reduced
 // per warp into qb: qb[d] = min(0, lowest code), qb[3 + d] = max(0, highest).
 __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves, uint64_t words,
-                           ChunkInfo *info, uint32_t *err, int32_t *qb) {
+                           ChunkInfo *info, uint32_t *err, int32_t *qb, uint32_t raw, uint32_t M) {
   const uint64_t L = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool mine = L < num_leaves;
   const uint8_t *table = stream + kHeaderBytes;
@@ -79,10 +79,13 @@ __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint6
   if (mine) {
     const Rec r = load_rec(table, L);
     const uint64_t pend = (L + 1 < num_leaves) ? load_rec(table, L + 1).po : n;
-    bool ok = r.zero == 0 && r.m[0] <= 31 && r.m[1] <= 31 && r.m[2] <= 31 && pend > r.po && pend <= n;
+    bool ok = r.zero == 0 && pend > r.po && pend <= n;
+    for (int d = 0; d < 3; ++d) ok = ok && ((raw >> d) & 1u ? r.m[d] == M : r.m[d] <= 31);
     if (L == 0) ok = ok && r.po == 0 && r.wo == 0;
     if (ok) {
-      const uint64_t wend = r.wo + leaf_words(r, pend - r.po);
+      // with lossless axes every particle of the leaf, the centre included, is in the payload
+      const uint64_t wend = r.wo + (raw ? ((uint64_t)(r.m[0] + r.m[1] + r.m[2]) * (pend - r.po) + 31) >> 5
+                                        : leaf_words(r, pend - r.po));
       const uint64_t wnext = (L + 1 < num_leaves) ? load_rec(table, L + 1).wo : words;
       ok = r.wo <= words && wend == wnext;
     }
@@ -106,6 +109,7 @@ __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint6
         info[c].last = uint32_t(L);
       }
       for (int d = 0; d < 3; ++d) {
+        if ((raw >> d) & 1u) continue;  // a lossless axis has no codes
         const int64_t half = r.m[d] ? (int64_t(1) << (r.m[d] - 1)) : 0;
         const int64_t lo = int64_t(r.q[d]) - (half ? half - 1 : 0), hi = int64_t(r.q[d]) + half;
         low[d] = int32_t(lo >= 0 ? 0 : (lo < -0x7fffffffll ? -0x7fffffffll : lo));
@@ -416,6 +420,50 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
   }
 }
 
+// Decoding of a stream with lossless axes, one thread per particle: its leaf
+// by binary search within its chunk's leaves, every particle in the payload
+// (entry i of the leaf, the centre first), x, y, z fields of m_d bits (coded:
+// q = q_ref + c - (2^(m-1) - 1), then (T)(o + s q)) or M bits (the
+// coordinate's own pattern).
+template <typename T>
+__global__ void __launch_bounds__(kDecThreads) k_decode_lossless(DecodeLaunch a) {
+  if (*a.err) return;
+  const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g >= a.n) return;
+  const uint8_t *table = a.stream + kHeaderBytes;
+  const uint32_t *words = reinterpret_cast<const uint32_t *>(table + uint64_t(kLeafBytes) * a.num_leaves);
+  const ChunkInfo ci = static_cast<const ChunkInfo *>(a.chunks)[g / kChunk];
+  uint64_t lo = ci.first, hi = ci.last;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    if (load_rec(table, mid).po <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const Rec r = load_rec(table, lo);
+  const uint32_t w = r.m[0] + r.m[1] + r.m[2];
+  uint64_t bit = 32ull * r.wo + (g - r.po) * uint64_t(w);
+  T *out = static_cast<T *>(a.out) + 3 * g;
+  for (int d = 0; d < 3; ++d) {
+    const uint32_t md = r.m[d];
+    uint64_t v = 0;
+    for (uint32_t t = 0; t < md; t += 32) {  // md bits from `bit` on, 32 at a time
+      const uint32_t nb = min(32u, md - t);
+      const uint64_t b = bit + t, wi = b >> 5;
+      const uint32_t x = __funnelshift_r(word_at(words, a.payload_words, wi), word_at(words, a.payload_words, wi + 1),
+                                         uint32_t(b & 31));
+      v |= uint64_t(nb < 32 ? x & ((1u << nb) - 1u) : x) << t;
+    }
+    bit += md;
+    if ((a.raw >> d) & 1u) {
+      if (sizeof(T) == 4) out[d] = T(__uint_as_float(uint32_t(v)));
+      else out[d] = T(__longlong_as_double((long long)v));
+    } else {
+      const int32_t q = r.q[d] + (md ? int32_t(v) - int32_t((1u << (md - 1)) - 1u) : 0);
+      out[d] = dequant_particle<T, false>(a, d, q);
+    }
+  }
+}
+
 __global__ void k_header(HeaderLaunch a) {
   const uint64_t words = a.total_words ? *a.total_words : 0;
   __align__(16) uint8_t h[kHeaderBytes];
@@ -439,6 +487,7 @@ __global__ void k_header(HeaderLaunch a) {
   put64(64, a.num_leaves);
   put64(72, words);
   for (int i = 0; i < 4; ++i) h[80 + i] = uint8_t(a.leaf_size >> (8 * i));
+  h[84] = uint8_t(a.raw);
   uint4 *dst = reinterpret_cast<uint4 *>(a.out);
   const uint4 *src = reinterpret_cast<const uint4 *>(h);
   for (int i = 0; i < int(kHeaderBytes / 16); ++i) dst[i] = src[i];
@@ -478,7 +527,15 @@ cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st) {
   {
     TraceScope ts("k_validate", st);
     k_validate<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
-                                                                        static_cast<ChunkInfo *>(a.chunks), a.err, a.qb);
+                                                                        static_cast<ChunkInfo *>(a.chunks), a.err, a.qb,
+                                                                        a.raw, a.dtype == 0 ? 32u : 64u);
+  }
+  if (a.raw) {
+    TraceScope ts("k_decode", st);
+    const unsigned grid = unsigned((a.n + kDecThreads - 1) / kDecThreads);
+    if (a.dtype == 0) k_decode_lossless<float><<<grid, kDecThreads, 0, st>>>(a);
+    else k_decode_lossless<double><<<grid, kDecThreads, 0, st>>>(a);
+    return cudaGetLastError();
   }
   if (a.dtype == 0) return a.fast ? decode_dispatch<float, true>(a, st) : decode_dispatch<float, false>(a, st);
   return decode_dispatch<double, false>(a, st);

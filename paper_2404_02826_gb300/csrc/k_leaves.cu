@@ -100,9 +100,30 @@ __device__ __forceinline__ void for_leaf(const C *q0, const C *q1, const C *q2, 
   }
 }
 
+// Widths of a leaf: m_d by Eq. 2, or M on a lossless axis (q_ref_d then 0);
+// payload words: (sum m)(n - 1) bits, or (sum widths) * n when the stream has
+// lossless axes (every particle, the centre included, is in the payload).
+__device__ __forceinline__ void leaf_widths(LeafRec &rec, const uint32_t qc[3], const uint32_t lo[3],
+                                            const uint32_t hi[3], uint32_t cnt, uint32_t raw, uint32_t M) {
+  uint32_t m[3];
+  for (int d = 0; d < 3; ++d) {
+    if ((raw >> d) & 1u) {
+      m[d] = M;
+      rec.qref[d] = 0;
+    } else {
+      m[d] = bits_for_range(max(qc[d] - lo[d], hi[d] - qc[d]));
+      rec.qref[d] = int32_t(qc[d]);
+    }
+  }
+  rec.m = m[0] | (m[1] << 8) | (m[2] << 16);
+  const uint64_t w = m[0] + m[1] + m[2];
+  rec.words = uint32_t((w * (raw ? uint64_t(cnt) : uint64_t(cnt - 1)) + 31) >> 5);
+}
+
 template <typename C>
 __global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q0, const C *__restrict__ q1,
-                                                         const C *__restrict__ q2, LeafRec *recs) {
+                                                         const C *__restrict__ q2, LeafRec *recs, uint32_t raw,
+                                                         uint32_t M) {
   __shared__ uint32_t red[6][kBoxThreads / 32];
   __shared__ unsigned long long rd[kBoxThreads / 32];
   __shared__ uint32_t rp[kBoxThreads / 32];
@@ -169,16 +190,8 @@ __global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q
       }
     const uint32_t c = bp;
     const uint32_t qc[3] = {uint32_t(q0[off + c]), uint32_t(q1[off + c]), uint32_t(q2[off + c])};
-    uint32_t m[3];
-    for (int d = 0; d < 3; ++d) {
-      const uint32_t R = max(qc[d] - lo[d], hi[d] - qc[d]);
-      m[d] = bits_for_range(R);
-      rec.qref[d] = int32_t(qc[d]);
-    }
     rec.centre = c;
-    rec.m = m[0] | (m[1] << 8) | (m[2] << 16);
-    const uint64_t bits = uint64_t(m[0] + m[1] + m[2]) * (cnt - 1);
-    rec.words = uint32_t((bits + 31) >> 5);
+    leaf_widths(rec, qc, lo, hi, cnt, raw, M);
     recs[blockIdx.x] = rec;
   }
 }
@@ -186,7 +199,8 @@ __global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q
 // The same bit box with one warp per leaf (small leaves).
 template <typename C>
 __global__ void __launch_bounds__(256) k_leafbox_warp(const C *__restrict__ q0, const C *__restrict__ q1,
-                                                      const C *__restrict__ q2, LeafRec *recs, uint64_t num_leaves) {
+                                                      const C *__restrict__ q2, LeafRec *recs, uint64_t num_leaves,
+                                                      uint32_t raw, uint32_t M) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = uint64_t(gridDim.x) * 8;
   for (uint64_t L = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5); L < num_leaves; L += warps) {
@@ -230,14 +244,8 @@ __global__ void __launch_bounds__(256) k_leafbox_warp(const C *__restrict__ q0, 
     if (lane == 0) {
       const uint32_t c = bp;
       const uint32_t qc[3] = {uint32_t(q0[off + c]), uint32_t(q1[off + c]), uint32_t(q2[off + c])};
-      uint32_t m[3];
-      for (int d = 0; d < 3; ++d) {
-        m[d] = bits_for_range(max(qc[d] - lo[d], hi[d] - qc[d]));
-        rec.qref[d] = int32_t(qc[d]);
-      }
       rec.centre = c;
-      rec.m = m[0] | (m[1] << 8) | (m[2] << 16);
-      rec.words = uint32_t((uint64_t(m[0] + m[1] + m[2]) * (cnt - 1) + 31) >> 5);
+      leaf_widths(rec, qc, lo, hi, cnt, raw, M);
       recs[L] = rec;
     }
   }
@@ -462,6 +470,87 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack_warp(const C *__restr
                       err);
 }
 
+// Packing of a stream with lossless axes (Sec. 4.1, m_d > M), one warp per
+// leaf: every particle of the leaf, the centre first, as x, y, z fields of m_d
+// bits (coded axes, Fig. 2 codes) or M bits (the coordinate's own bit pattern,
+// read through the input index).  32 particles of w bits fill w words: each
+// lane assembles its particle's bits (up to 192) and ORs them into the warp's
+// staged words, which then go out whole.
+template <typename T>
+__global__ void __launch_bounds__(kPackThreads) k_leafpack_lossless(
+    const uint32_t *__restrict__ q0, const uint32_t *__restrict__ q1, const uint32_t *__restrict__ q2,
+    const uint32_t *__restrict__ idx, const LeafRec *__restrict__ recs, uint8_t *out, uint64_t num_leaves,
+    uint32_t *perm, uint64_t n, uint64_t payload_cap, uint32_t *err, const T *__restrict__ pos, uint32_t raw) {
+  constexpr uint32_t kMaxW = 3 * 8 * sizeof(T);  // widest particle: three lossless axes
+  __shared__ uint32_t swords[kPackWarps][kMaxW + 8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *sw = swords[warp];
+  const uint32_t *qs[3] = {q0, q1, q2};
+  for (uint64_t L = uint64_t(blockIdx.x) * kPackWarps + warp; L < num_leaves; L += uint64_t(gridDim.x) * kPackWarps) {
+    const LeafRec rec = recs[L];
+    if (uint64_t(rec.off) + rec.cnt > n || rec.word_off + rec.words > payload_cap) {
+      if (lane == 0) atomicOr(err, kErrInternal);
+      continue;
+    }
+    const uint32_t off = rec.off, cnt = rec.cnt, centre = rec.centre;
+    const uint32_t m[3] = {rec.m & 0xffu, (rec.m >> 8) & 0xffu, (rec.m >> 16) & 0xffu};
+    const uint32_t w = m[0] + m[1] + m[2];
+    if (lane == 0) {
+      uint4 *r = reinterpret_cast<uint4 *>(out + kHeaderBytes + uint64_t(kLeafBytes) * L);
+      const uint64_t po = off, wo = rec.word_off;
+      r[0] = make_uint4(uint32_t(po), uint32_t(po >> 32), uint32_t(wo), uint32_t(wo >> 32));
+      r[1] = make_uint4(uint32_t(rec.qref[0]), uint32_t(rec.qref[1]), uint32_t(rec.qref[2]), rec.m);
+    }
+    uint32_t *payload =
+        reinterpret_cast<uint32_t *>(out + kHeaderBytes + uint64_t(kLeafBytes) * num_leaves) + rec.word_off;
+    for (uint32_t c0 = 0; c0 < cnt; c0 += 32) {
+      const uint32_t k = c0 + lane;  // payload entry: 0 is the centre, then leaf order without it
+      uint32_t lim[kMaxW / 32] = {};
+      if (k < cnt) {
+        const uint32_t src = k == 0 ? centre : (k - 1 < centre ? k - 1 : k);
+        const uint32_t id = idx[off + src];
+        if (perm) perm[off + k] = id;
+        uint32_t bp = 0;
+        for (int d = 0; d < 3; ++d) {
+          uint64_t v;
+          if ((raw >> d) & 1u) {
+            v = sizeof(T) == 4 ? uint64_t(__float_as_uint(float(pos[3 * uint64_t(id) + d])))
+                               : uint64_t(__double_as_longlong(double(pos[3 * uint64_t(id) + d])));
+          } else if (m[d]) {
+            v = uint64_t(qs[d][off + src] - uint32_t(rec.qref[d]) + ((1u << (m[d] - 1)) - 1u));
+          } else {
+            continue;
+          }
+          for (uint32_t t = 0; t < m[d]; t += 32) {
+            const uint32_t nb = min(32u, m[d] - t);
+            uint32_t part = uint32_t(v >> t);
+            if (nb < 32) part &= (1u << nb) - 1u;
+            const uint32_t wj = bp >> 5, sh = bp & 31;
+            lim[wj] |= part << sh;
+            if (sh && wj + 1 < kMaxW / 32) lim[wj + 1] |= part >> (32 - sh);
+            bp += nb;
+          }
+        }
+      }
+      for (uint32_t t = lane; t < w + 8; t += 32) sw[t] = 0;
+      __syncwarp();
+      if (k < cnt) {
+        for (uint32_t j = 0; 32 * j < w; ++j) {
+          const uint32_t g = lane * w + 32 * j, k0 = g >> 5, sh = g & 31;
+          atomicOr(&sw[k0], lim[j] << sh);
+          if (sh) atomicOr(&sw[k0 + 1], lim[j] >> (32 - sh));
+        }
+      }
+      __syncwarp();
+      for (uint32_t t = lane; t < w; t += 32) {
+        const uint32_t gw = (c0 >> 5) * w + t;
+        if (gw < rec.words) __stcs(payload + gw, sw[t]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
 template <typename C, bool IDX>
 cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
   const C *q0 = static_cast<const C *>(a.codes[0]), *q1 = static_cast<const C *>(a.codes[1]),
@@ -479,10 +568,11 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
                                                                                  : uint64_t(device_sm_count()) * 32);
   if (!a.recs_ready) {
     TraceScope ts("k_leafbox", st);
+    const uint32_t M = a.dtype == 0 ? 32u : 64u;
     if (small)
-      k_leafbox_warp<C><<<wgrid, 256, 0, st>>>(q0, q1, q2, a.recs, a.num_leaves);
+      k_leafbox_warp<C><<<wgrid, 256, 0, st>>>(q0, q1, q2, a.recs, a.num_leaves, a.raw, M);
     else
-      k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs);
+      k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs, a.raw, M);
   }
   if (a.box_only) return cudaGetLastError();
   {
@@ -498,6 +588,20 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
   }
   if (a.cost_only) return cudaGetLastError();
   TraceScope ts("k_leafpack", st);
+  if (a.raw) {  // lossless axes: u32 codes and the input index are always there
+    if (sizeof(C) != 4 || !IDX || !a.pos) return cudaErrorInvalidValue;
+    const uint32_t *u0 = reinterpret_cast<const uint32_t *>(q0), *u1 = reinterpret_cast<const uint32_t *>(q1),
+                   *u2 = reinterpret_cast<const uint32_t *>(q2);
+    if (a.dtype == 0)
+      k_leafpack_lossless<float><<<wgrid, kPackThreads, 0, st>>>(u0, u1, u2, a.idx, a.recs, a.out, a.num_leaves,
+                                                                  a.perm, a.n, a.payload_cap, a.err,
+                                                                  static_cast<const float *>(a.pos), a.raw);
+    else
+      k_leafpack_lossless<double><<<wgrid, kPackThreads, 0, st>>>(u0, u1, u2, a.idx, a.recs, a.out, a.num_leaves,
+                                                                   a.perm, a.n, a.payload_cap, a.err,
+                                                                   static_cast<const double *>(a.pos), a.raw);
+    return cudaGetLastError();
+  }
   if (small)
     k_leafpack_warp<C, IDX><<<wgrid, kPackThreads, 0, st>>>(q0, q1, q2, a.idx, a.recs, a.out, a.num_leaves, a.perm,
                                                             a.n, a.payload_cap, a.err);

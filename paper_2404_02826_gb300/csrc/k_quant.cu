@@ -384,6 +384,35 @@ __global__ void __launch_bounds__(kThreads) k_quant_f64(const double *__restrict
   }
 }
 
+// Streams with lossless axes (Sec. 4.1, m_d > M): a coded axis takes the
+// definition's code, a lossless axis the split key floor((p - lo) / span * 2^29)
+// in [0, 2^29] (the coordinate itself is stored by the packing).  Codes are u32.
+__device__ __forceinline__ uint32_t raw_key(double p, double lo, double span) {
+  if (!(span > 0.0)) return 0u;
+  double t = floor(__dmul_rn(__ddiv_rn(__dsub_rn(p, lo), span), 536870912.0));
+  t = t < 0.0 ? 0.0 : (t > 536870912.0 ? 536870912.0 : t);
+  return uint32_t(t);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_quant_lossless(const T *__restrict__ pos, uint64_t n, QuantParams qp,
+                                                             uint32_t *__restrict__ qx, uint32_t *__restrict__ qy,
+                                                             uint32_t *__restrict__ qz, uint32_t *__restrict__ idx) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double p = (double)pos[3 * i + d];
+      q[d] = (qp.raw >> d) & 1u ? raw_key(p, qp.lo[d], qp.span[d]) : quant_exact(p, qp.o[d], qp.s);
+    }
+    qx[i] = q[0];
+    qy[i] = q[1];
+    qz[i] = q[2];
+    if (idx) idx[i] = uint32_t(i);
+  }
+}
+
 template <typename C>
 cudaError_t quant_dispatch(const QuantLaunch &a, cudaStream_t st) {
   C *qx = static_cast<C *>(a.q[0]), *qy = static_cast<C *>(a.q[1]), *qz = static_cast<C *>(a.q[2]);
@@ -426,6 +455,19 @@ cudaError_t launch_range(const RangeLaunch &a, cudaStream_t st) {
 
 cudaError_t launch_quantize(const QuantLaunch &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
+  if (a.qp.raw) {
+    if (a.code_bytes != 4) return cudaErrorInvalidValue;
+    uint32_t *qx = static_cast<uint32_t *>(a.q[0]), *qy = static_cast<uint32_t *>(a.q[1]),
+             *qz = static_cast<uint32_t *>(a.q[2]);
+    TraceScope ts("k_quantize", st);
+    if (a.dtype == 0)
+      k_quant_lossless<float><<<a.blocks, kThreads, 0, st>>>(static_cast<const float *>(a.pos), a.n, a.qp, qx, qy,
+                                                              qz, a.idx);
+    else
+      k_quant_lossless<double><<<a.blocks, kThreads, 0, st>>>(static_cast<const double *>(a.pos), a.n, a.qp, qx,
+                                                               qy, qz, a.idx);
+    return cudaGetLastError();
+  }
   return a.code_bytes == 2 ? quant_dispatch<uint16_t>(a, st) : quant_dispatch<uint32_t>(a, st);
 }
 

@@ -197,12 +197,13 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   o = align_up(o + 3 * code_stride(n));
   p.off_codes_b = o;
   o = align_up(o + 3 * code_stride(n));
-  if (idx) {
-    p.off_idx_a = o;
-    o = align_up(o + 4 * n);
-    p.off_idx_b = o;
-    o = align_up(o + 4 * n);
-  }
+  // input indices carried through the partition: for the permutation output,
+  // and for the lossless axes (the packing reads their coordinates through them),
+  // which only the value range can reveal, so room for them is always planned
+  p.off_idx_a = o;
+  o = align_up(o + 4 * n);
+  p.off_idx_b = o;
+  o = align_up(o + 4 * n);
   uint64_t node_count = 0;
   for (int l = 0; l <= p.levels; ++l) node_count += 1ull << l;
   p.off_nodes = o;
@@ -216,10 +217,11 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   // group records of the scatter's classification, one level at a time
   uint64_t group_bytes = 16;
   for (int l = 0; l < p.levels; ++l)
-    for (int cb = 2; cb <= 4; cb += 2) {
-      const uint64_t g = (1ull << l) * tiles_per_node(n, l, scatter_tile(cb, idx)) * scatter_groups(cb, idx) * 16;
-      if (g > group_bytes) group_bytes = g;
-    }
+    for (int cb = 2; cb <= 4; cb += 2)
+      for (int wi = 0; wi < 2; ++wi) {
+        const uint64_t g = (1ull << l) * tiles_per_node(n, l, scatter_tile(cb, wi)) * scatter_groups(cb, wi) * 16;
+        if (g > group_bytes) group_bytes = g;
+      }
   p.off_groups = o;
   o = align_up(o + group_bytes);
   if (p.reduce) {
@@ -242,7 +244,7 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   for (int l = 0; l < p.levels; ++l) {
     const uint64_t b = (1ull << l) << digit_bits_for(l);
     if (b > hist_bins) hist_bins = b;
-    tiles += (1ull << l) * tiles_per_node(n, l, min_scatter_tile(idx));
+    tiles += (1ull << l) * tiles_per_node(n, l, min_scatter_tile(true));
   }
   p.off_hist = o;
   o = align_up(o + 4 * (hist_bins ? hist_bins : 1));
@@ -261,9 +263,11 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   return PC_OK;
 }
 
-uint64_t stream_bound(uint64_t n, uint64_t leaves) {
-  // widths are at most 31 bits per axis: 93 bits per non-centre particle
-  return PC_HEADER_BYTES + 36ull * leaves + 4ull * ((93ull * n + 31) / 32);
+uint64_t stream_bound(uint64_t n, uint64_t leaves, int dtype) {
+  // codes are at most 31 bits per axis (93 per particle); with lossless axes a
+  // particle takes up to 3 M bits (96 for float, 192 for double), the centre included
+  const uint64_t bits = dtype == PC_F64 ? 192 : 96;
+  return PC_HEADER_BYTES + 36ull * leaves + 4ull * ((bits * n + 31) / 32);
 }
 
 // Spacing of the floating-point grid with `prec` significand bits at x > 0.
@@ -278,7 +282,13 @@ double grid_spacing(double x, int prec, int emin) {
 struct Lattice {
   double eps = 0, s = 1, o[3] = {0, 0, 0};
   uint32_t qmax[3] = {0, 0, 0};
+  double lo[3] = {0, 0, 0}, span[3] = {0, 0, 0};  // split keys of lossless axes
+  uint32_t raw = 0;  // bit d: axis d stored losslessly (Sec. 4.1, m_d > M)
+  int raw_cause = PC_OK;
 };
+
+// Split key of the largest coordinate of a lossless axis (k_quant.cu's rule).
+uint32_t raw_key_top(double span) { return span > 0.0 ? (1u << 29) : 0u; }
 
 // Sec. 3: eps from the absolute or value-range-relative bound; the lattice
 // step s = 2 eb' keeps |p - (T)(o + s q)| <= eps after every rounding.
@@ -311,12 +321,27 @@ int lattice_from_range(const RangeResult &rr, int dtype, int mode, double eb, La
   const double ulp_t = dtype == PC_F32 ? grid_spacing(m2, 24, -126) : grid_spacing(m2, 53, -1022);
   const double ulp_d = grid_spacing(m2, 53, -1022);
   const double ebp = L.eps - ulp_t - 4.0 * ulp_d;
-  if (!(ebp > 0.0)) return PC_ERR_EB_TOO_SMALL;
-  L.s = 2.0 * ebp;
+  if (!(ebp > 0.0)) {
+    // no lattice keeps the bound through the rounding to T: every axis losslessly
+    L.raw = 7u;
+    L.raw_cause = PC_ERR_EB_TOO_SMALL;
+    L.s = 1.0;
+  } else {
+    L.s = 2.0 * ebp;
+    for (int d = 0; d < 3; ++d) {
+      const double q = std::nearbyint((hi[d] - lo[d]) / L.s);
+      if (!(q < double(kCodeLimit))) {  // codes of 2^30 or more: this axis losslessly
+        L.raw |= 1u << d;
+        L.raw_cause = PC_ERR_RANGE;
+      } else {
+        L.qmax[d] = uint32_t(q);
+      }
+    }
+  }
   for (int d = 0; d < 3; ++d) {
-    const double q = std::nearbyint((hi[d] - lo[d]) / L.s);
-    if (!(q < double(kCodeLimit))) return PC_ERR_RANGE;
-    L.qmax[d] = uint32_t(q);
+    L.lo[d] = lo[d];
+    L.span[d] = hi[d] - lo[d];
+    if ((L.raw >> d) & 1u) L.qmax[d] = raw_key_top(L.span[d]);
   }
   return PC_OK;
 }
@@ -362,7 +387,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
   if (rc) return rc;
   if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign) return PC_ERR_ARG;
   if (workspace_bytes < p.total) return PC_ERR_CAPACITY;
-  if (!sweep && out_capacity < stream_bound(n, p.num_leaves)) return PC_ERR_CAPACITY;
+  if (!sweep && out_capacity < stream_bound(n, p.num_leaves, dtype)) return PC_ERR_CAPACITY;
   uint8_t *ws = static_cast<uint8_t *>(workspace);
   uint32_t *err = reinterpret_cast<uint32_t *>(ws + p.off_err);
   uint64_t *total_dev = reinterpret_cast<uint64_t *>(ws + p.off_total);
@@ -398,17 +423,22 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     PC_TRY(cudaStreamSynchronize(st));
     rc = lattice_from_range(rr, dtype, eb_mode, eb, L);
     if (rc) return rc;
+    // lossless axes (Sec. 4.1, m_d > M): the plain stream only; the reduction,
+    // the reordering and the leaf-size search need codes on every axis
+    if (L.raw && (p.tune || p.reduce || p.reorder || sweep)) return L.raw_cause;
+    const bool use_idx = p.idx || L.raw != 0;  // lossless axes are read through the input indices
+    hl.raw = L.raw;
 
     const uint32_t qmax = L.qmax[0] > L.qmax[1] ? (L.qmax[0] > L.qmax[2] ? L.qmax[0] : L.qmax[2])
                                                  : (L.qmax[1] > L.qmax[2] ? L.qmax[1] : L.qmax[2]);
-    const int cb = qmax < 65536u ? 2 : 4;
+    const int cb = (qmax < 65536u && !L.raw) ? 2 : 4;
     void *codes_a[3], *codes_b[3];
     for (int d = 0; d < 3; ++d) {
       codes_a[d] = ws + p.off_codes_a + uint64_t(d) * code_stride(n);
       codes_b[d] = ws + p.off_codes_b + uint64_t(d) * code_stride(n);
     }
-    uint32_t *idx_a = p.idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_a) : nullptr;
-    uint32_t *idx_b = p.idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_b) : nullptr;
+    uint32_t *idx_a = use_idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_a) : nullptr;
+    uint32_t *idx_b = use_idx ? reinterpret_cast<uint32_t *>(ws + p.off_idx_b) : nullptr;
 
     // a2: quantize
     QuantLaunch qa = {};
@@ -429,6 +459,11 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     qa.qp.inv = inv;
     qa.fast = dtype == PC_F32 ? (qmax < (1u << 22) && inv > 0x1p-100 && inv < 0x1p100)
                               : (inv > 0x1p-1000 && inv < 0x1p1000);
+    qa.qp.raw = L.raw;
+    for (int d = 0; d < 3; ++d) {
+      qa.qp.lo[d] = L.lo[d];
+      qa.qp.span[d] = L.span[d];
+    }
     qa.idx = idx_a;
     qa.blocks = 8 * device_sm_count();
     PC_TRY(launch_quantize(qa, st));
@@ -436,9 +471,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     // a3: the k-d levels, down to the leaves (autotuning: down to the deepest candidate at most);
     // the deep levels, bit boxes and packing on chip when the plain stream is asked for
     const int levels = p.tune ? p.tune_last : p.levels;
-    const int sub_depth = (p.tune || p.reduce || p.reorder || sweep)
+    const int sub_depth = (p.tune || p.reduce || p.reorder || sweep || L.raw)
                               ? -1
-                              : subtree_depth(n, p.r, p.levels, cb, p.idx, device_sm_count());
+                              : subtree_depth(n, p.r, p.levels, cb, use_idx, device_sm_count());
     const int global_levels = sub_depth >= 0 ? sub_depth : levels;
     // a4-a5 on the arrangement at depth `depth` (leaves = its 2^depth nodes when split_level = depth - 1)
     auto leaf_launch = [&](void *const *codes, const uint32_t *idxs, int split_level, uint32_t r,
@@ -460,6 +495,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       lf.box_only = box_only;
       lf.payload_cap = payload_words(out_capacity, num_leaves);
       lf.err = err;
+      lf.raw = L.raw;
+      lf.pos = positions;
+      lf.dtype = dtype;
       return launch_leaves(lf, st);
     };
     // a5 from ready records: payload offsets and packing, after the reordering
@@ -553,7 +591,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.n = n;
       la.level = l;
       la.code_bytes = cb;
-      la.with_idx = p.idx;
+      la.with_idx = use_idx;
       la.leaf_size = p.r;
       // levels of at least 2048 nodes of at most kMedMaxNode particles: one warp per node
       la.warp_median = (1ull << l) >= 2048 && ((n + (1ull << l) - 1) >> l) <= kMedMaxNode;
@@ -563,7 +601,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       const uint32_t bits = bit_length(p.widest ? widest_q : L.qmax[l % 3]);
       la.widest = p.widest;
       la.passes = (bits + la.digit_bits - 1) / la.digit_bits;
-      la.tiles_per_node = uint32_t(tiles_per_node(n, l, scatter_tile(cb, p.idx)));
+      la.tiles_per_node = uint32_t(tiles_per_node(n, l, scatter_tile(cb, use_idx)));
       for (int d = 0; d < 3; ++d) la.root_hi[d] = L.qmax[d];
       for (int d = 0; d < 3; ++d) {
         la.src[d] = src[d];
@@ -744,7 +782,9 @@ int parse_header(const uint8_t *h, uint64_t avail, pc_info *info) {
   std::memcpy(&I.num_leaves, h + 64, 8);
   std::memcpy(&I.payload_words, h + 72, 8);
   std::memcpy(&I.leaf_size, h + 80, 4);
-  for (int i = 84; i < 96; ++i)
+  I.lossless_axes = h[84];  // Sec. 4.1, m_d > M: axes stored as the original coordinates
+  if (I.lossless_axes > 7u) return PC_ERR_CORRUPT;
+  for (int i = 85; i < 96; ++i)
     if (h[i]) return PC_ERR_CORRUPT;
   if (I.n > PC_MAX_PARTICLES || I.num_leaves > I.n || ((I.n > 0) != (I.num_leaves > 0))) return PC_ERR_CORRUPT;
   if (I.payload_words > (1ull << 40)) return PC_ERR_CORRUPT;
@@ -798,6 +838,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   da.qb = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(workspace) + 32);
   da.tab = static_cast<uint8_t *>(workspace) + kAlign;
   da.chunks = static_cast<uint8_t *>(workspace) + kAlign + align_up(decode_table_bytes());
+  da.raw = I.lossless_axes;
   PC_TRY(launch_decode(da, st));
   uint32_t e = 0;
   PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
@@ -828,7 +869,7 @@ int pc_compress_bound(uint64_t n, int dtype, const pc_config *cfg, uint64_t *out
   Plan p;
   int rc = make_plan(n, dtype, cfg, false, 148, p);
   if (rc) return rc;
-  *out_bytes = stream_bound(n, p.num_leaves);
+  *out_bytes = stream_bound(n, p.num_leaves, dtype);
   return PC_OK;
 }
 

@@ -38,6 +38,9 @@ struct QuantParams {
   float of[3];   // origin as float (exact for float input)
   float rh, rl;  // 1/s as an unevaluated float sum rh + rl
   double inv;    // fl(1/s)
+  uint32_t raw;      // bit d: axis d stored losslessly; its code is the split key
+  double lo[3];      //   floor((p - lo) / span * 2^29) (span = hi - lo; 0 when span is 0)
+  double span[3];
 };
 
 // Per-node state of one global k-d level (Sec. 4.1 median split by radix select).
@@ -189,6 +192,10 @@ struct LeafLaunch {
   bool box_only;            // leaf table and bit boxes only (the records are reordered before packing)
   uint64_t payload_cap;     // payload words the output holds after the header and the leaf table
   uint32_t *err;            // device error word: a record that would write past n or the payload is skipped
+  uint32_t raw;             // lossless axes: m_d = M and q_ref_d = 0 in the record, every particle in the
+                            // payload (centre first), the coordinate's M-bit pattern read through idx from pos
+  const void *pos;          // input positions (lossless axes)
+  int dtype;
 };
 cudaError_t launch_leaves(const LeafLaunch &a, cudaStream_t st);
 // The leaf ranges alone (off, cnt of every leaf; the other fields zero).
@@ -231,6 +238,7 @@ struct HeaderLaunch {
   const uint64_t *total_words;  // null when there are no leaves
   uint64_t *total_bytes;        // device slot read back by the host
   uint32_t *err;
+  uint32_t raw;                 // lossless-axis mask (header byte 84)
 };
 cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st);
 
@@ -250,6 +258,7 @@ struct DecodeLaunch {
   int32_t *qb;           // [6], zero on entry: per axis min(0, lowest code), then max(0, highest code)
   void *tab;             // [decode_table_bytes()]: dequantized value of every code, when they fit
   void *chunks;          // [decode_chunk_bytes(n)]: per decode chunk, its leaves and payload words
+  uint32_t raw;          // lossless-axis mask: those axes hold M-bit patterns, every particle in the payload
 };
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
 uint64_t decode_chunks(uint64_t n);

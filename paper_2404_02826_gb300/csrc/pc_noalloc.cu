@@ -10,13 +10,15 @@
 // the positions and the output buffer.
 //
 // Rules of use (also stated in include/pc.h):
-//   - the array is kPcNoallocScratchBytes (32 MiB); every GPU that loads this
+//   - the array is kPcNoallocScratchBytes (48 MiB); every GPU that loads this
 //     part of the library keeps it until the process exits;
 //   - a problem whose scratch does not fit (above about 2^20 particles at the
 //     default leaf size) is rejected with PC_ERR_CAPACITY before any work;
 //   - the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress, with that device current) and caches it, so make
-//     that first call before any stream capture;
+//     that first call before any stream capture; a cudaDeviceReset invalidates
+//     the cached address (the module is loaded again), so the entry point must
+//     not be called on a device after a reset;
 //   - every call on a device uses the same array, which keeps the contents of
 //     the last call; the parts that must start at zero are cleared on every
 //     call, but calls whose work overlaps on the GPU (two streams, two host

@@ -72,8 +72,11 @@ def test_leaf_count_rule_matches_oracle(pc, oracle_mod):
         n = int(rng.integers(0, 1 << 22))
         r = int(rng.integers(1, 12001))
         L = oracle_mod.num_leaves(n, r)
+        # at most 3 M bits per particle: lossless axes store M-bit coordinates (Sec. 4.1)
         b = pc.pc_compress_bound(n, pc.PC_F32, r)
-        assert b == 96 + 36 * L + 4 * ((93 * n + 31) // 32)
+        assert b == 96 + 36 * L + 4 * ((96 * n + 31) // 32)
+        b = pc.pc_compress_bound(n, pc.PC_F64, r)
+        assert b == 96 + 36 * L + 4 * ((192 * n + 31) // 32)
 
 
 def test_argument_errors_without_gpu(pc):

@@ -239,10 +239,18 @@ def test_status_codes(pc):
         with pytest.raises(pc.PCError) as e:
             c.compress(pos, pc.PC_EB_REL, eb)
         assert e.value.status == pc.PC_ERR_ARG
+    # eps below the float spacing of the data: stored losslessly (Sec. 4.1, m_d > M),
+    # refused by the bit-box reduction, which needs codes
     far = torch.tensor([[1e6, 0, 0], [1e6 + 64, 1, 1]], device=dev)
     c2 = pc.Compressor(2, pc.PC_F32, device=dev)
+    size2 = c2.compress(far, pc.PC_EB_ABS, 1e-3)
+    assert pc.pc_stream_info(c2.out[:96].cpu().numpy().tobytes()).lossless_axes == 7
+    back = torch.empty_like(far)
+    c2.decompress(c2.out, back, size2)
+    assert sorted(map(tuple, back.cpu().tolist())) == sorted(map(tuple, far.cpu().tolist()))
+    c3 = pc.Compressor(2, pc.PC_F32, leaf_size=pc.config(4096, reduce=True), device=dev)
     with pytest.raises(pc.PCError) as e:
-        c2.compress(far, pc.PC_EB_ABS, 1e-3)
+        c3.compress(far, pc.PC_EB_ABS, 1e-3)
     assert e.value.status == pc.PC_ERR_EB_TOO_SMALL
     small_out = torch.empty(100, dtype=torch.uint8, device=dev)
     with pytest.raises(pc.PCError) as e:

@@ -2,7 +2,7 @@
 
 Such callers (code inside another framework's memory pool, latency-critical
 paths where cudaMalloc could synchronise the device) get the scratch from a
-static 32 MiB device array in the library instead of a workspace argument.
+static 48 MiB device array in the library instead of a workspace argument.
 The stream must be identical, byte for byte, to the one pc_compress writes,
 on two calls in a row (the array keeps the previous call's contents).
 """
