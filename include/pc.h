@@ -219,6 +219,19 @@ int pc_compress_noalloc(const void *positions, uint64_t n, int dtype, int eb_mod
  * mechanism failed.  Synchronous on `stream`. */
 int pc_selftest_wait_timeout(void *stream);
 
+/* Self-test of the partition's behaviour when a tile copy never lands (no
+ * counterpart in the paper): one pc_compress of the given positions (value-
+ * range-relative bound 1e-3, default configuration) in which the partition's
+ * scatter issues no tile copy and waits at most 2^12 polls for each.  Every
+ * scatter block gives up on its first tile and leaves; the kernels after it
+ * see the error word and do nothing; the call returns PC_ERR_TIMEOUT and the
+ * context stays usable.  Arguments and workspace as for pc_compress (device
+ * pointers); the output holds nothing valid afterwards.  The copies are
+ * dropped only for calls made from the calling host thread while this one
+ * runs.  n must exceed 2^16, so that the first level runs the tiled scatter. */
+int pc_selftest_scatter_timeout(const void *positions, uint64_t n, int dtype, void *out, uint64_t out_capacity,
+                                void *workspace, uint64_t workspace_bytes, void *stream);
+
 /* Parse a stream header held in host memory (the first 96 bytes suffice). */
 int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info);
 

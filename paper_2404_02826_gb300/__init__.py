@@ -54,7 +54,7 @@ EXPORTS = (
     "pc_compress_batch_workspace_size", "pc_compress_batch", "pc_decompress_batch_workspace_size",
     "pc_decompress_batch", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_release",
     "pc_server_stats", "pc_server_destroy", "pc_server_now", "pc_leaf_size_sweep_workspace_size",
-    "pc_leaf_size_sweep", "pc_selftest_wait_timeout",
+    "pc_leaf_size_sweep", "pc_selftest_wait_timeout", "pc_selftest_scatter_timeout",
 )
 PC_REQ_COMPRESS = 0
 PC_REQ_DECOMPRESS = 1
@@ -328,6 +328,18 @@ def pc_selftest_wait_timeout(stream=None) -> int:
     L = _lib()
     L.pc_selftest_wait_timeout.argtypes = [ctypes.c_void_p]
     return int(L.pc_selftest_wait_timeout(_stream_handle(stream)))
+
+
+def pc_selftest_scatter_timeout(positions, out, workspace, stream=None) -> int:
+    """Runs one compress of device positions [n, 3] (n > 2^16) whose scatter tile copies
+    are dropped; returns its status (PC_ERR_TIMEOUT when the failure path works)."""
+    n = positions.shape[0]
+    L = _lib()
+    L.pc_selftest_scatter_timeout.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+    return int(L.pc_selftest_scatter_timeout(positions.data_ptr(), n, _dtype_of(positions), out.data_ptr(),
+                                             out.numel() * out.element_size(), workspace.data_ptr(),
+                                             workspace.numel() * workspace.element_size(), _stream_handle(stream)))
 
 
 def pc_error_string(status: int) -> str:

@@ -123,10 +123,11 @@ __device__ __forceinline__ void leaf_widths(LeafRec &rec, const uint32_t qc[3], 
 template <typename C>
 __global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q0, const C *__restrict__ q1,
                                                          const C *__restrict__ q2, LeafRec *recs, uint32_t raw,
-                                                         uint32_t M) {
+                                                         uint32_t M, const uint32_t *err) {
   __shared__ uint32_t red[6][kBoxThreads / 32];
   __shared__ unsigned long long rd[kBoxThreads / 32];
   __shared__ uint32_t rp[kBoxThreads / 32];
+  if (call_failed(err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   LeafRec rec = recs[blockIdx.x];
   const uint32_t off = rec.off, cnt = rec.cnt;
@@ -200,7 +201,8 @@ __global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q
 template <typename C>
 __global__ void __launch_bounds__(256) k_leafbox_warp(const C *__restrict__ q0, const C *__restrict__ q1,
                                                       const C *__restrict__ q2, LeafRec *recs, uint64_t num_leaves,
-                                                      uint32_t raw, uint32_t M) {
+                                                      uint32_t raw, uint32_t M, const uint32_t *err) {
+  if (call_failed(err)) return;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = uint64_t(gridDim.x) * 8;
   for (uint64_t L = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5); L < num_leaves; L += warps) {
@@ -450,6 +452,7 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack(const C *__restrict__
                                                            uint64_t num_leaves, uint32_t *perm, uint64_t n,
                                                            uint64_t payload_cap, uint32_t *err) {
   __shared__ uint32_t swords[kPackWarps][96];  // one chunk's words per warp (w <= 93)
+  if (call_failed(err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   pack_leaf<C, IDX>(q0, q1, q2, idx, recs[blockIdx.x], blockIdx.x, out, num_leaves, perm, lane, warp, kPackWarps,
                     swords[warp], n, payload_cap, err);
@@ -464,6 +467,7 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack_warp(const C *__restr
                                                                 uint64_t num_leaves, uint32_t *perm, uint64_t n,
                                                                 uint64_t payload_cap, uint32_t *err) {
   __shared__ uint32_t swords[kPackWarps][96];
+  if (call_failed(err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t L = uint64_t(blockIdx.x) * kPackWarps + warp; L < num_leaves; L += uint64_t(gridDim.x) * kPackWarps)
     pack_leaf<C, IDX>(q0, q1, q2, idx, recs[L], L, out, num_leaves, perm, lane, 0, 1, swords[warp], n, payload_cap,
@@ -483,6 +487,7 @@ __global__ void __launch_bounds__(kPackThreads) k_leafpack_lossless(
     uint32_t *perm, uint64_t n, uint64_t payload_cap, uint32_t *err, const T *__restrict__ pos, uint32_t raw) {
   constexpr uint32_t kMaxW = 3 * 8 * sizeof(T);  // widest particle: three lossless axes
   __shared__ uint32_t swords[kPackWarps][kMaxW + 8];
+  if (call_failed(err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *sw = swords[warp];
   const uint32_t *qs[3] = {q0, q1, q2};
@@ -570,9 +575,9 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
     TraceScope ts("k_leafbox", st);
     const uint32_t M = a.dtype == 0 ? 32u : 64u;
     if (small)
-      k_leafbox_warp<C><<<wgrid, 256, 0, st>>>(q0, q1, q2, a.recs, a.num_leaves, a.raw, M);
+      k_leafbox_warp<C><<<wgrid, 256, 0, st>>>(q0, q1, q2, a.recs, a.num_leaves, a.raw, M, a.err);
     else
-      k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs, a.raw, M);
+      k_leafbox<C><<<unsigned(a.num_leaves), kBoxThreads, 0, st>>>(q0, q1, q2, a.recs, a.raw, M, a.err);
   }
   if (a.box_only) return cudaGetLastError();
   {

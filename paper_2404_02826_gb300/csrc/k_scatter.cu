@@ -95,8 +95,10 @@ __device__ __forceinline__ void issue_tile(const LevelLaunch &a, Smem<C, IDX> &S
   const uint32_t nwin = (g.te - w0 + 15) & ~15u;
   const uint32_t bytes = nwin * uint32_t(sizeof(C));
   const uint32_t ngrp = (g.te - w0 + 31) >> 5;
-  mbar_expect_tx(&S.bar[b], 3 * bytes + (IDX ? 4 * nwin : 0) + ngrp * uint32_t(sizeof(GroupRec)));
-  if (nwin) {
+  if (!a.drop_copies) {
+    mbar_expect_tx(&S.bar[b], 3 * bytes + (IDX ? 4 * nwin : 0) + ngrp * uint32_t(sizeof(GroupRec)));
+  }
+  if (nwin && !a.drop_copies) {
     for (int d = 0; d < 3; ++d) bulk_g2s(S.in[b][d], static_cast<const C *>(a.src[d]) + w0, bytes, &S.bar[b]);
     if (IDX) bulk_g2s(S.idx[b], a.src_idx + w0, 4 * nwin, &S.bar[b]);
     bulk_g2s(S.grp[b], static_cast<const GroupRec *>(a.groups) + uint64_t(t) * Cfg<C, IDX>::kGroups,
@@ -115,10 +117,14 @@ __device__ __forceinline__ void publish(Smem<C, IDX> &S, int b, const Pending &p
 // Persistent CTA.  Thread 0 keeps one ticket and one tile copy ahead of the
 // tile being partitioned, so neither the ticket atomic nor the copy is waited
 // for; three block barriers per tile.  AXIS is the split axis of the level.
+// When the wait for a tile's copy gives up, the block lets the copy of the
+// next tile land (bounded) and leaves the loop: it issues no further copy and
+// takes no further ticket, so one stuck copy costs one bounded wait per block.
 template <typename C, bool IDX, int AXIS>
 __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t tiles) {
   extern __shared__ __align__(128) unsigned char smraw[];
   Smem<C, IDX> &S = *reinterpret_cast<Smem<C, IDX> *>(smraw);
+  if (call_failed(a.err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Pending pend = {};
   uint32_t next_t = tiles;  // thread 0: the tile after the one in flight
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
         after = atomicAdd(a.ticket, 1u);
       }
     }
-    wait_buffer(&S.bar[b], b ? phase1 : phase0, a.err);
+    const bool late = wait_buffer(&S.bar[b], b ? phase1 : phase0, a.err, a.wait_limit);
     if (b) phase1 ^= 1u;
     else phase0 ^= 1u;
 
@@ -208,7 +214,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter(LevelLaunch a, uint32_t
       if (prefetched) publish(S, b ^ 1, pend);
       next_t = after;
     }
-    __syncthreads();  // the next tile's state is published; this tile's buffer may be refilled
+    // the next tile's state is published; this tile's buffer may be refilled.
+    // A wait that gave up (the stores above then wrote only inside this node,
+    // from data never copied; the call fails) ends the block's work here.
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0 && prefetched) drain_buffer(&S.bar[b ^ 1], b ? phase0 : phase1, a.wait_limit);
+      break;
+    }
     b ^= 1;
   }
 }
@@ -231,6 +243,7 @@ __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
   __shared__ uint32_t wtot[8];
   __shared__ TileGeom sg;
   __shared__ uint32_t sv, sax;
+  if (call_failed(a.err)) return;
   if (threadIdx.x == 0) {
     sg = tile_geom(a, blockIdx.x);
     sv = a.nodes[sg.j].v;
@@ -313,6 +326,7 @@ __global__ void __launch_bounds__(256) k_count(LevelLaunch a) {
 // Per node: exclusive scan of its tiles' (less << 31 | tie) counts, in place.
 __global__ void __launch_bounds__(1024) k_tilescan(LevelLaunch a) {
   __shared__ unsigned long long wt[33];
+  if (call_failed(a.err)) return;
   const uint64_t T = a.tiles_per_node;
   unsigned long long *s = a.tile_state + blockIdx.x * T;
   const uint64_t per = (T + blockDim.x - 1) / blockDim.x;
@@ -347,6 +361,7 @@ __global__ void __launch_bounds__(1024) k_tilescan(LevelLaunch a) {
 
 // The same scan for nodes of few tiles: one thread per node.
 __global__ void k_tilescan_small(LevelLaunch a) {
+  if (call_failed(a.err)) return;
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= (1ull << a.level)) return;
   const uint32_t T = a.tiles_per_node;
@@ -366,6 +381,7 @@ __global__ void k_tilescan_small(LevelLaunch a) {
 // level's split axis, or 3 for each node's own (widest-cell variant).
 template <typename C, bool IDX, int AXIS>
 __global__ void __launch_bounds__(256) k_scatter_node(LevelLaunch a) {
+  if (call_failed(a.err)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint64_t count = 1ull << a.level;

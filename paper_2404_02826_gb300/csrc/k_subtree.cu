@@ -59,6 +59,7 @@ struct SubMisc {
   uint32_t wp[kWarps][2];
   unsigned long long off, cnt;  // the node: first particle, particles
   uint32_t j, nl, lead, ilead, tmem;
+  uint32_t skip;                // an earlier kernel of the call failed: the node is not worked
   uint32_t wt[kWarps];          // warp totals of the scans
   uint32_t gb[kWarps];          // scan value at the first entry of each group
   uint32_t fb[kWarps], fbefore[kWarps];
@@ -272,9 +273,11 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
     const uint32_t noff = uint32_t(off64), ncnt = uint32_t(cnt64);
     const uint32_t nwin = (lead + ncnt + kV - 1u) & ~(kV - 1u);
     const uint32_t niw = (ilead + ncnt + 3u) & ~3u;
-    const bool ok = ncnt <= L::kCap;
+    const bool dead = *reinterpret_cast<const volatile uint32_t *>(a.err) != 0u;
+    M.skip = dead ? 1u : 0u;
+    const bool ok = ncnt <= L::kCap && !dead;
     const uint32_t bytes = ok ? 3 * nwin * uint32_t(sizeof(C)) + (IDX ? 4 * niw : 0u) : 0u;
-    if (!ok) atomicOr(a.err, kErrInternal);
+    if (!ok && !dead) atomicOr(a.err, kErrInternal);
     mbar_expect_tx(&M.bar, bytes);
     if (bytes) {
       for (int d = 0; d < 3; ++d)
@@ -282,9 +285,10 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
                  nwin * uint32_t(sizeof(C)), &M.bar);
       if (IDX) bulk_g2s(sm + L::kIdx, a.idx + (noff - ilead), 4 * niw, &M.bar);
     }
-    // the root of the subtree: its cell from the parent's split (k_prep's rule)
+    // the root of the subtree: its cell from the parent's split (k_prep's rule);
+    // in a failed call the parents' records were never written and are not read
     SubNode &s = cur[0];
-    if (a.depth == 0) {
+    if (a.depth == 0 || dead) {
       for (int d = 0; d < 3; ++d) {
         s.blo[d] = 0;
         s.bhi[d] = a.root_hi[d];
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
         s.blo[d] = p.blo[d];
         s.bhi[d] = p.bhi[d];
       }
-      if (p.v != 0xffffffffu) {
+      if (p.v != 0xffffffffu && p.axis < 3u) {
         if (j & 1) s.blo[p.axis] = p.v;
         else s.bhi[p.axis] = p.v;
       }
@@ -313,7 +317,20 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
   tmem_fence_after();
   // this thread's tensor-memory columns: lane quarter warp % 4, columns by warpgroup
   const uint32_t tcol = M.tmem + ((32u * (uint32_t(warp) & 3u)) << 16) + (uint32_t(warp) >> 2) * uint32_t(L::kCols);
-  wait_buffer(&M.bar, 0, a.err);
+  // A failed call (an earlier kernel, or this copy's wait giving up): the
+  // node's status is published as complete, so that no later node waits for
+  // it, and the CTA leaves.
+  const bool late = wait_buffer(&M.bar, 0, a.err);
+  if (__syncthreads_or(late || M.skip != 0u)) {
+    if (threadIdx.x == 0) st_release_u64(a.status + M.j, kStIncl);
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tmem_fence_after();
+      tmem_dealloc(M.tmem, kTmemCols);
+    }
+    return;
+  }
   // element i of the node (any array) sits at slot lead + i
   C *const X0 = reinterpret_cast<C *>(sm) + M.lead;
 

@@ -35,7 +35,8 @@ constexpr uint32_t kMedBins = 1u << kMedD;    // private histogram of one warp
 // prep: bounds of every node from its parent's split, then its first digit
 // --------------------------------------------------------------------------
 __global__ void k_prep(LevelNode *nodes, const LevelNode *parents, uint64_t n, int level, uint32_t digit_bits,
-                       LevelLaunch::RootHi root_hi, uint32_t leaf_size, bool widest) {
+                       LevelLaunch::RootHi root_hi, uint32_t leaf_size, bool widest, const uint32_t *err) {
+  if (call_failed(err)) return;
   const uint64_t count = 1ull << level;
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= count) return;
@@ -96,8 +97,9 @@ template <typename C>
 __global__ void __launch_bounds__(kHistThreads) k_hist(const C *__restrict__ q0, const C *__restrict__ q1,
                                                        const C *__restrict__ q2, const LevelNode *__restrict__ nodes,
                                                        uint32_t *__restrict__ hist, uint64_t n, int level,
-                                                       uint32_t digit_bits) {
+                                                       uint32_t digit_bits, const uint32_t *err) {
   extern __shared__ uint32_t sh[];
+  if (call_failed(err)) return;
   uint64_t start = ((n * blockIdx.x / gridDim.x) + 15) & ~15ull;
   uint64_t end = blockIdx.x + 1 == gridDim.x ? n : (((n * (blockIdx.x + 1) / gridDim.x) + 15) & ~15ull);
   if (end > n) end = n;
@@ -202,9 +204,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *warp_t
 // select: one block per node; finds the bucket of rank floor(c/2)
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSelThreads) k_select(LevelNode *nodes, uint32_t *hist, uint64_t n, int level,
-                                                        uint32_t digit_bits) {
+                                                        uint32_t digit_bits, const uint32_t *err) {
   __shared__ uint32_t warp_tot[33];
   __shared__ uint32_t found_b, found_before;
+  if (call_failed(err)) return;
   const uint64_t j = blockIdx.x;
   LevelNode nd = nodes[j];
   if (nd.width == 0) return;
@@ -267,8 +270,9 @@ __global__ void __launch_bounds__(kSelThreads) k_select(LevelNode *nodes, uint32
 template <typename C>
 __global__ void __launch_bounds__(kMedWarps * 32) k_median(const C *__restrict__ q0, const C *__restrict__ q1,
                                                             const C *__restrict__ q2, LevelNode *nodes, uint64_t n,
-                                                            int level) {
+                                                            int level, const uint32_t *err) {
   extern __shared__ uint32_t med_hist[];
+  if (call_failed(err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *h = med_hist + warp * kMedBins;
   const uint64_t count = 1ull << level;
@@ -373,7 +377,7 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
     LevelLaunch::RootHi rh;
     for (int d = 0; d < 3; ++d) rh.v[d] = a.root_hi[d];
     k_prep<<<unsigned((count + 255) / 256), 256, 0, st>>>(a.nodes, a.parents, a.n, a.level, a.digit_bits, rh,
-                                                          a.leaf_size, a.widest);
+                                                          a.leaf_size, a.widest, a.err);
   }
   const C *q0 = static_cast<const C *>(a.src[0]), *q1 = static_cast<const C *>(a.src[1]),
           *q2 = static_cast<const C *>(a.src[2]);
@@ -387,7 +391,7 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
     if (grid > need) grid = need;
     {
       TraceScope ts("k_median", st);
-      k_median<C><<<unsigned(grid), kMedWarps * 32, msm, st>>>(q0, q1, q2, a.nodes, a.n, a.level);
+      k_median<C><<<unsigned(grid), kMedWarps * 32, msm, st>>>(q0, q1, q2, a.nodes, a.n, a.level, a.err);
     }
     return launch_scatter(a, st);
   }
@@ -395,10 +399,11 @@ cudaError_t level_dispatch(const LevelLaunch &a, cudaStream_t st) {
   for (uint32_t p = 0; p < a.passes; ++p) {
     {
       TraceScope ts("k_hist", st);
-      k_hist<C><<<a.hist_blocks, kHistThreads, hsm, st>>>(q0, q1, q2, a.nodes, a.hist, a.n, a.level, a.digit_bits);
+      k_hist<C><<<a.hist_blocks, kHistThreads, hsm, st>>>(q0, q1, q2, a.nodes, a.hist, a.n, a.level, a.digit_bits,
+                                                               a.err);
     }
     TraceScope ts("k_select", st);
-    k_select<<<unsigned(count), kSelThreads, 0, st>>>(a.nodes, a.hist, a.n, a.level, a.digit_bits);
+    k_select<<<unsigned(count), kSelThreads, 0, st>>>(a.nodes, a.hist, a.n, a.level, a.digit_bits, a.err);
   }
   return launch_scatter(a, st);
 }

@@ -12,6 +12,12 @@
 
 namespace pcx {
 
+namespace {
+thread_local bool t_drop_tile_copies = false;
+}  // namespace
+
+void set_drop_tile_copies(bool on) { t_drop_tile_copies = on; }
+
 int device_sm_count() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -543,8 +549,19 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       PC_TRY(launch_leaves(lf, st));
       return PC_OK;
     };
+    // The error word so far, read back: the paths that read back anyway (the
+    // leaf-size search, the reduction, the reordering) stop before working on
+    // the partition of a call that has failed.
+    auto error_so_far = [&]() -> int {
+      uint32_t e = 0;
+      PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+      PC_TRY(cudaStreamSynchronize(st));
+      return (e & kErrTimeout) ? PC_ERR_TIMEOUT : (e ? PC_ERR_CUDA : PC_OK);
+    };
     // autotuning: stream bytes of the leaves at `depth` (every node there is a leaf)
     auto depth_cost = [&](void *const *codes, int depth, uint64_t *bytes) -> int {
+      const int failed = error_so_far();
+      if (failed) return failed;
       const uint64_t r = (n + (1ull << depth) - 1) >> depth;
       PC_TRY(leaf_launch(codes, nullptr, depth - 1, uint32_t(r), 1ull << depth, true));
       uint64_t words = 0;
@@ -617,6 +634,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + l;
       la.err = err;
       la.hist_blocks = 2 * device_sm_count();
+      la.drop_copies = t_drop_tile_copies;
+      la.wait_limit = t_drop_tile_copies ? kSelftestSpinLimit : kBarSpinLimit;
       PC_TRY(launch_level(la, st));
       node_base += 1ull << l;
       tile_base += (1ull << l) * la.tiles_per_node;
@@ -642,6 +661,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     // indices go to the spare arrangement in sequence order
     auto reduce_launch = [&](void *const *codes, const uint32_t *idxs, void *const *spare, uint32_t *spare_idx,
                              int split_level, uint32_t r, uint64_t num_leaves) -> int {
+      const int failed = error_so_far();
+      if (failed) return failed;
       ReduceLaunch rl = {};
       rl.n = n;
       rl.code_bytes = cb;
@@ -667,6 +688,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     // the leaves' bit boxes, then reordering and packing
     auto reorder_launch = [&](void *const *codes, uint32_t *idxs, void *const *spare, uint32_t *spare_idx,
                               int split_level, uint32_t r, uint64_t num_leaves) -> int {
+      const int failed = error_so_far();
+      if (failed) return failed;
       PC_TRY(leaf_launch(codes, idxs, split_level, r, num_leaves, false, true));
       return pack_ready(reinterpret_cast<LeafRec *>(ws + p.off_leafrec), num_leaves, codes, idxs, spare, spare_idx,
                         r);

@@ -15,8 +15,21 @@ constexpr uint32_t kHeaderBytes = 96;
 constexpr uint32_t kLeafBytes = 32;
 constexpr int64_t kCodeLimit = int64_t(1) << 30;  // codes < 2^30, so m_d <= 31
 
+// Polls of a tile copy's barrier before a wait gives up, and the short limit
+// of the self-test that drops the copies.
+constexpr uint32_t kBarSpinLimit = 1u << 22;
+constexpr uint32_t kSelftestSpinLimit = 1u << 12;
+
 // Bits of the device error word.
 enum : uint32_t { kErrTimeout = 1u, kErrCorrupt = 2u, kErrInternal = 4u };
+
+// Whether an earlier kernel of this call has set the error word (a wait that
+// gave up, an inconsistency).  The partition's and the leaves' kernels then do
+// nothing, so that no step reads data that was never written and a failed
+// call ends promptly.  Block-uniform: every thread calls it at kernel entry.
+__device__ __forceinline__ bool call_failed(const uint32_t *err) {
+  return __syncthreads_or(threadIdx.x == 0 && *reinterpret_cast<const volatile uint32_t *>(err) != 0u) != 0;
+}
 
 // Radix digit of the warp-per-node median (levels of many small nodes).
 constexpr uint32_t kMedD = 10;
@@ -168,6 +181,8 @@ struct LevelLaunch {
   uint32_t *ticket;
   uint32_t *err;
   int hist_blocks;
+  uint32_t wait_limit;    // polls of a tile copy's barrier before the scatter gives up
+  bool drop_copies;       // self-test only: the scatter issues no tile copy, so its first wait gives up
 };
 cudaError_t launch_level(const LevelLaunch &a, cudaStream_t st);
 cudaError_t launch_scatter(const LevelLaunch &a, cudaStream_t st);
@@ -293,6 +308,9 @@ cudaError_t resident_blocks(int threads, size_t smem, int *per_sm) {
   return cudaSuccess;
 }
 
+// Self-test switch of the calling host thread: its compress calls issue no
+// tile copy in the partition's scatter (pc_selftest_scatter_timeout).
+void set_drop_tile_copies(bool on);
 // pc_compress without the optional permutation, on a caller-provided workspace.
 int compress_device(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                     void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,

@@ -9,9 +9,6 @@
 
 namespace pcx {
 
-// polls of a barrier before a wait gives up (well under a second at the SM clock)
-constexpr uint32_t kBarSpinLimit = 1u << 22;
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
@@ -42,8 +39,9 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 // Waits for the copy into one buffer; bounded: after `limit` polls the error
 // bit is set and the wait is repeated once more, as long, before it returns
-// (a copy in flight always completes; the second wait lets it land).
-__device__ __forceinline__ void wait_buffer(unsigned long long *bar, uint32_t parity, uint32_t *err,
+// (a copy in flight always completes; the second wait lets it land).  Returns
+// whether the wait gave up; the caller then stops using the buffer.
+__device__ __forceinline__ bool wait_buffer(unsigned long long *bar, uint32_t parity, uint32_t *err,
                                             uint32_t limit = kBarSpinLimit) {
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
@@ -52,8 +50,17 @@ __device__ __forceinline__ void wait_buffer(unsigned long long *bar, uint32_t pa
       spins = 0;
       while (!mbar_try_wait(bar, parity) && ++spins < limit) {
       }
-      return;
+      return true;
     }
+  }
+  return false;
+}
+
+// Waits, bounded, for a copy whose data will not be used (a block leaving
+// early lets its copies in flight land first); sets no error bit.
+__device__ __forceinline__ void drain_buffer(unsigned long long *bar, uint32_t parity, uint32_t limit = kBarSpinLimit) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity) && ++spins < limit) {
   }
 }
 

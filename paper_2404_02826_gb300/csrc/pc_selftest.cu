@@ -1,4 +1,5 @@
-// Self-test of the bounded device waits (include/pc.h, pc_selftest_wait_timeout).
+// Self-tests of the bounded device waits (include/pc.h, pc_selftest_wait_timeout
+// and pc_selftest_scatter_timeout).
 // One block waits on a shared-memory barrier that nothing completes, through
 // the wait the partition uses for its tile copies; the wait gives up, sets the
 // error bit and returns, the kernel ends and the host reads the status.  No
@@ -42,4 +43,19 @@ extern "C" int pc_selftest_wait_timeout(void *stream) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return PC_ERR_CUDA;
   if (err & pcx::kErrTimeout) return PC_ERR_TIMEOUT;
   return err ? PC_ERR_CUDA : PC_OK;
+}
+
+// A compress call whose scatter copies are dropped on the calling thread: the
+// scatter's waits give up after kSelftestSpinLimit polls, every block leaves
+// on its first tile, and the kernels after it find the error word set.
+extern "C" int pc_selftest_scatter_timeout(const void *positions, uint64_t n, int dtype, void *out,
+                                           uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                                           void *stream) {
+  if (n <= (1ull << 16)) return PC_ERR_ARG;
+  uint64_t size = 0;
+  pcx::set_drop_tile_copies(true);
+  const int rc = pcx::compress_device(positions, n, dtype, PC_EB_REL, 1e-3, nullptr, out, out_capacity, &size,
+                                      workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+  pcx::set_drop_tile_copies(false);
+  return rc;
 }

@@ -90,3 +90,39 @@ def test_c_program_matches_the_binding(tmp_path, lib):
     assert sizes[2] == sizes[1]
     assert int(lines[2]) == pc.pc_format_version()
     assert lines[3] == pc.pc_error_string(pc.PC_ERR_ARG) and lines[4] == pc.pc_error_string(pc.PC_ERR_CORRUPT)
+
+
+LAYOUT_STRUCTS = ("pc_config", "pc_info", "pc_compress_item", "pc_decompress_item", "pc_sweep_point", "pc_request",
+                  "pc_completion")
+
+
+def test_struct_layouts_match_the_binding(tmp_path, lib):
+    """Every struct of the header, as a C compiler lays it out (size and the
+    offset of each field), equals the binding's ctypes declaration."""
+    _need("gcc")
+    pc = lib
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pc.h"', "int main(void) {"]
+    for name in LAYOUT_STRUCTS:
+        st = getattr(pc, name)
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in st._fields_:
+            lines.append(f'    printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", INC, str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stderr
+    import ctypes
+
+    seen = 0
+    for line in run.stdout.splitlines():
+        name, field, value = line.split()
+        st = getattr(pc, name)
+        want = ctypes.sizeof(st) if field == "size" else getattr(st, field).offset
+        assert int(value) == want, (name, field)
+        seen += 1
+    assert seen == sum(len(getattr(pc, s)._fields_) + 1 for s in LAYOUT_STRUCTS)

@@ -129,3 +129,23 @@ def test_reduced_stream_is_valid(oracle_mod, gen, n, r, mode, eb):
     assert np.array_equal(decoded_codes(st), oracle_mod.quantize(pos, m, eb)[perm])
     plain, _ = oracle_mod.compress(pos, m, eb, leaf_size=r)
     assert st.num_leaves <= parse(plain, with_codes=False).num_leaves
+
+
+@pytest.mark.parametrize("gen,n,r,mode,eb", [("cosmology", 1 << 18, 2048, "rel", 1e-3),
+                                             ("cosmology", 1 << 18, 2048, "rel", 1e-4),
+                                             ("uniform", 1 << 17, 1024, "rel", 1e-3),
+                                             ("fluid", 1 << 17, 1024, "abs", 1e-4)])
+def test_rounds_stay_close_to_the_one_box_order(oracle_mod, gen, n, r, mode, eb):
+    """The rounds reading of Alg. 1 (every box whose key is below that of every
+    box it meets goes in the same round) against Alg. 1's own order (one box,
+    least sum m_d, per round): both shrink the plain stream, and their sizes
+    differ by at most 0.6 % (measured on these sets: 0.30 %, 0.06 %, 0.55 %,
+    0.12 %; at 2^20 with r = 4096: 0.08 %, 0.35 %, 0.02 %)."""
+    pos = synth.by_name(gen, n, seed=3)
+    m = oracle_mod.ABS if mode == "abs" else oracle_mod.REL
+    plain, _ = oracle_mod.compress(pos, m, eb, leaf_size=r, want_perm=False)
+    rounds, _, nr = oracle_mod.compress_reduced(pos, m, eb, leaf_size=r, want_perm=False)
+    one, _, n1 = oracle_mod.compress_reduced(pos, m, eb, leaf_size=r, want_perm=False, one_per_round=True)
+    assert len(rounds) < len(plain) and len(one) < len(plain)
+    assert nr < n1  # rounds take several boxes at once
+    assert abs(len(rounds) / len(one) - 1.0) <= 0.006
