@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "pc_internal.cuh"
+#include "pc_mbar.cuh"
 
 namespace pcx {
 namespace {
@@ -35,9 +36,8 @@ struct Rec {
   uint32_t zero;
 };
 
-__device__ __forceinline__ Rec load_rec(const uint8_t *table, uint64_t L) {
-  const uint4 *p = reinterpret_cast<const uint4 *>(table + uint64_t(kLeafBytes) * L);
-  const uint4 a = __ldg(p), b = __ldg(p + 1);
+// A leaf record as stored (32 bytes, Fig. 4 layout of this format).
+__device__ __forceinline__ Rec rec_from(const uint4 a, const uint4 b) {
   Rec r;
   r.po = uint64_t(a.x) | (uint64_t(a.y) << 32);
   r.wo = uint64_t(a.z) | (uint64_t(a.w) << 32);
@@ -49,6 +49,11 @@ __device__ __forceinline__ Rec load_rec(const uint8_t *table, uint64_t L) {
   r.m[2] = (b.w >> 16) & 0xffu;
   r.zero = b.w >> 24;
   return r;
+}
+
+__device__ __forceinline__ Rec load_rec(const uint8_t *table, uint64_t L) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(table + uint64_t(kLeafBytes) * L);
+  return rec_from(__ldg(p), __ldg(p + 1));
 }
 
 __device__ __forceinline__ uint64_t leaf_words(const Rec &r, uint64_t cnt) {
@@ -186,10 +191,22 @@ struct LeafC {
   uint32_t pad[2];
 };
 
-template <typename T>
+// One chunk's staging area: its payload words, from a 16-byte aligned word
+// (room for the copy rounded up to whole 16 bytes), and its leaf records as
+// stored in the stream.
+struct DecBuf {
+  uint32_t sw[kWordCap + 4];
+  uint4 rec[2 * kChunkLeaves];
+};
+
+// Persistent decoder: two staging areas filled by bulk copies, the leaf
+// constants of each, the chunk descriptors and the copies' barriers.
 struct DecSmem {
-  uint32_t sw[kWordCap];
-  LeafC lc[kChunkLeaves];
+  DecBuf buf[2];
+  LeafC lc[2][kChunkLeaves];
+  ChunkInfo ci[2];
+  unsigned long long bar[2];
+  uint32_t ncopy[2];  // words each area's copy brings
 };
 
 // Whether the code ranges [lo_d, hi_d] of the three axes fit kTabEntries
@@ -255,48 +272,96 @@ __global__ void k_dtable(DecodeLaunch a) {
   }
 }
 
-// One block per chunk of kChunk consecutive particles.
+// Whether a chunk is decoded from shared memory: at most kChunkLeaves leaves
+// and a payload span that fits the staging area.
+__device__ __forceinline__ bool chunk_staged(const ChunkInfo &ci) {
+  return ci.last - ci.first + 1 <= uint32_t(kChunkLeaves) && ci.end - ci.lo <= uint64_t(kWordCap);
+}
+
+// Thread 0: starts the bulk copies of a chunk into staging area b - its
+// payload words in whole 16-byte units as far as the payload reaches, and its
+// leaf records - or, for a chunk that is not staged, only arrives on b's
+// barrier.  Source and destination are 16-byte aligned: the stream starts on
+// 16 bytes, the leaf table at byte 96 in 32-byte records, the payload after
+// it, and a chunk's first staged word is a multiple of 4.
+__device__ __forceinline__ void dec_issue(const DecodeLaunch &a, DecSmem &S, int b, const ChunkInfo &ci,
+                                          const uint32_t *words, const uint8_t *table) {
+  S.ci[b] = ci;
+  uint32_t nw = 0, bytes = 0;
+  const bool staged = chunk_staged(ci);
+  if (staged) {
+    const uint64_t up = (ci.end - ci.lo + 3) & ~3ull;
+    const uint64_t avail = a.payload_words > ci.lo ? a.payload_words - ci.lo : 0;
+    nw = uint32_t(up <= avail ? up : (avail & ~3ull));
+    bytes = 4 * nw + uint32_t(kLeafBytes) * (ci.last - ci.first + 1);
+  }
+  S.ncopy[b] = nw;
+  mbar_expect_tx(&S.bar[b], bytes);
+  if (staged) {
+    if (nw) bulk_g2s(S.buf[b].sw, words + ci.lo, 4 * nw, &S.bar[b]);
+    bulk_g2s(S.buf[b].rec, table + uint64_t(kLeafBytes) * ci.first, uint32_t(kLeafBytes) * (ci.last - ci.first + 1),
+             &S.bar[b]);
+  }
+}
+
+// Persistent blocks; block k decodes chunks k, k + G, k + 2G, ... of kChunk
+// consecutive particles (G = grid size).
+//  * Thread 0 starts the copies of the block's next chunk into the other
+//    staging area while the current one is decoded, and keeps the descriptor
+//    of the chunk after that in flight; one block barrier per chunk.
 //  * Dequantization reads the code tables (k_dtable) when they exist; the
 //    particles of a leaf have nearby codes, so a warp's lookups touch few
 //    cache lines.
-//  * When the chunk holds at most kChunkLeaves leaves (always, unless leaves
-//    are tiny), the payload words it spans are staged in shared memory with
-//    coalesced loads and each particle's fields are cut from a 96-bit window
-//    with funnel shifts and per-leaf masks.  Otherwise each particle searches
-//    the leaf table and reads its words from global memory.
+//  * Each particle's fields are cut from a 96-bit window of the staged words
+//    with funnel shifts and per-leaf masks.  A chunk of more than
+//    kChunkLeaves leaves (tiny leaves) or a longer span searches the leaf table
+//    and reads its words from global memory instead.
+//  * A copy whose wait gives up ends the block's work (error word set).
 template <typename T, bool FAST, bool VEC>
 __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
-  __shared__ __align__(16) DecSmem<T> S;
-  if (*a.err) return;  // validation failed: write nothing
+  __shared__ __align__(16) DecSmem S;
+  if (call_failed(a.err)) return;  // validation failed: write nothing
+  const uint64_t nchunks = (a.n + kChunk - 1) / kChunk;
+  uint64_t chunk = blockIdx.x;
+  if (chunk >= nchunks) return;
   const uint8_t *table = a.stream + kHeaderBytes;
   const uint32_t *words = reinterpret_cast<const uint32_t *>(table + uint64_t(kLeafBytes) * a.num_leaves);
+  const ChunkInfo *cinfo = static_cast<const ChunkInfo *>(a.chunks);
   uint32_t tb[3], te = 0;
   const bool use_table = table_fits(a.qb, tb, te);
   // table of axis d indexed by the code itself: its start minus the lowest code
   const T *tabs = static_cast<const T *>(a.tab);
   const T *tab0 = tabs + (int64_t(tb[0]) - a.qb[0]), *tab1 = tabs + (int64_t(tb[1]) - a.qb[1]),
           *tab2 = tabs + (int64_t(tb[2]) - a.qb[2]);
-  {
-    const uint64_t chunk = blockIdx.x;
-    const uint64_t c0 = chunk * kChunk;
-    const uint64_t c1 = (c0 + kChunk) < a.n ? (c0 + kChunk) : a.n;
-    const ChunkInfo ci = static_cast<const ChunkInfo *>(a.chunks)[chunk];
+  const int32_t qlow0 = a.qb[0], qlow1 = a.qb[1], qlow2 = a.qb[2];
+  const uint64_t G = gridDim.x;
+  ChunkInfo ahead = {};  // thread 0: the descriptor of the chunk after the next one
+  if (threadIdx.x == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    mbar_fence_init();
+    dec_issue(a, S, 0, cinfo[chunk], words, table);
+    if (chunk + G < nchunks) ahead = cinfo[chunk + G];
+  }
+  __syncthreads();
+  uint32_t ph0 = 0u, ph1 = 0u;
+  for (int b = 0; chunk < nchunks; chunk += G, b ^= 1) {
+    const bool late = wait_buffer(&S.bar[b], b ? ph1 : ph0, a.err);
+    if (b) ph1 ^= 1u;
+    else ph0 ^= 1u;
+    const ChunkInfo ci = S.ci[b];
     const uint32_t count = ci.last - ci.first + 1;
-    const bool staged = count <= uint32_t(kChunkLeaves) && ci.end - ci.lo <= uint64_t(kWordCap);
-    const int32_t nloc = int32_t(c1 - c0);
-    __align__(16) T vals[3 * kDecPer];
-    int32_t qs[3 * kDecPer];  // codes of the run; unused slots hold the lowest code, a valid table index
-#pragma unroll
-    for (int v = 0; v < 3 * kDecPer; ++v) qs[v] = a.qb[v % 3];
-    if (staged) {
-      const uint64_t lo = ci.lo, hi = ci.end < a.payload_words ? ci.end : a.payload_words;
+    const bool staged = chunk_staged(ci);
+    const uint64_t c0 = chunk * kChunk;
+    const int32_t nloc = int32_t(((c0 + kChunk) < a.n ? (c0 + kChunk) : a.n) - c0);
+    if (staged && !late) {
       if (threadIdx.x < count) {
         const int L = threadIdx.x;
-        const Rec r = load_rec(table, ci.first + L);
+        const Rec r = rec_from(S.buf[b].rec[2 * L], S.buf[b].rec[2 * L + 1]);
         LeafC lc;
         lc.rel = int32_t(int64_t(r.po) - int64_t(c0));
         lc.w = r.m[0] + r.m[1] + r.m[2];
-        lc.base = int32_t(int64_t(32 * r.wo) - int64_t(32 * lo) - int64_t(lc.w));
+        lc.base = int32_t(int64_t(32 * r.wo) - int64_t(32 * ci.lo) - int64_t(lc.w));
         lc.m0 = r.m[0];
         lc.s2 = r.m[0] + r.m[1];
 #pragma unroll
@@ -306,36 +371,46 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
           lc.off[d] = r.q[d] - int32_t(r.m[d] ? (1u << (r.m[d] - 1)) - 1u : 0u);
         }
         lc.pad[0] = lc.pad[1] = 0;
-        S.lc[L] = lc;
+        S.lc[b][L] = lc;
       }
-      const uint32_t nst = uint32_t(ci.end - lo);
-      const uint32_t nreal = hi > lo ? uint32_t(hi - lo) : 0u;
-      if ((reinterpret_cast<uintptr_t>(words) & 15) == 0) {
-        const uint32_t nvec = nreal >> 2;
-        const uint4 *src = reinterpret_cast<const uint4 *>(words + lo);
-        uint4 *dst = reinterpret_cast<uint4 *>(S.sw);
-        for (uint32_t v = threadIdx.x; v < nvec; v += kDecThreads) dst[v] = __ldg(src + v);
-        for (uint32_t w = 4 * nvec + threadIdx.x; w < nst; w += kDecThreads)
-          S.sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
-      } else {
-        for (uint32_t w = threadIdx.x; w < nst; w += kDecThreads) S.sw[w] = w < nreal ? __ldg(words + lo + w) : 0u;
-      }
-      __syncthreads();
+      // the words the copy did not bring (the last chunks only): the payload's tail, then zeros
+      const uint32_t nst = uint32_t(ci.end - ci.lo);
+      for (uint32_t w = S.ncopy[b] + threadIdx.x; w < nst; w += kDecThreads)
+        S.buf[b].sw[w] = ci.lo + w < a.payload_words ? __ldg(words + ci.lo + w) : 0u;
+    }
+    // this chunk's constants are in place; every thread is done with the other staging area
+    if (__syncthreads_or(late)) break;
+    if (threadIdx.x == 0 && chunk + G < nchunks) {
+      fence_proxy_async();  // earlier generic reads of that area precede the async writes
+      dec_issue(a, S, b ^ 1, ahead, words, table);
+      if (chunk + 2 * G < nchunks) ahead = cinfo[chunk + 2 * G];
+    }
+    __align__(16) T vals[3 * kDecPer];
+    int32_t qs[3 * kDecPer];  // codes of the run; unused slots hold the lowest code, a valid table index
+#pragma unroll
+    for (int v = 0; v < 3 * kDecPer; v += 3) {
+      qs[v] = qlow0;
+      qs[v + 1] = qlow1;
+      qs[v + 2] = qlow2;
+    }
+    const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
+    if (staged) {
+      const uint32_t *sw = S.buf[b].sw;
+      const LeafC *lcs = S.lc[b];
       // kDecPer consecutive particles per thread: one leaf lookup for the run
-      const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
       if (sl0 < nloc) {
         int L = 0;
-        while (L + 1 < int(count) && S.lc[L + 1].rel <= sl0) ++L;
-        LeafC lc = S.lc[L];
-        int32_t next = L + 1 < int(count) ? S.lc[L + 1].rel : 0x7fffffff;
+        while (L + 1 < int(count) && lcs[L + 1].rel <= sl0) ++L;
+        LeafC lc = lcs[L];
+        int32_t next = L + 1 < int(count) ? lcs[L + 1].rel : 0x7fffffff;
 #pragma unroll
         for (int k = 0; k < kDecPer; ++k) {
           const int32_t sl = sl0 + k;
           if (sl >= nloc) continue;
           if (sl >= next) {  // the run crosses into the next leaf
             ++L;
-            lc = S.lc[L];
-            next = L + 1 < int(count) ? S.lc[L + 1].rel : 0x7fffffff;
+            lc = lcs[L];
+            next = L + 1 < int(count) ? lcs[L + 1].rel : 0x7fffffff;
           }
           const uint32_t i = uint32_t(sl) - uint32_t(lc.rel);
           int32_t q0, q1, q2;
@@ -346,7 +421,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
           } else {
             const uint32_t bit = uint32_t(lc.base) + i * lc.w;  // modulo 2^32; the result is below 2^17
             const uint32_t wi = bit >> 5, r0 = bit & 31u;
-            const uint32_t a0 = S.sw[wi], a1 = S.sw[wi + 1], a2 = S.sw[wi + 2], a3 = S.sw[wi + 3];
+            const uint32_t a0 = sw[wi], a1 = sw[wi + 1], a2 = sw[wi + 2], a3 = sw[wi + 3];
             const uint32_t v0 = __funnelshift_r(a0, a1, r0);  // bits [bit, bit + 96) of the payload
             const uint32_t v1 = __funnelshift_r(a1, a2, r0);
             const uint32_t v2 = __funnelshift_r(a2, a3, r0);
@@ -361,7 +436,6 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
         }
       }
     } else {
-      const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
 #pragma unroll
       for (int k = 0; k < kDecPer; ++k) {
         const int32_t sl = sl0 + k;
@@ -401,7 +475,6 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
       for (int v = 0; v < 3 * kDecPer; ++v) vals[v] = dequant_particle<T, FAST>(a, v % 3, qs[v]);
     }
     // the run's 3 * kDecPer values are consecutive in the output
-    const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
     if (sl0 < nloc) {
       T *out = static_cast<T *>(a.out) + 3 * (c0 + uint64_t(sl0));
       if (VEC && sl0 + kDecPer <= nloc) {
@@ -500,8 +573,14 @@ cudaError_t decode_launch(const DecodeLaunch &a, cudaStream_t st) {
     TraceScope ts("k_dtable", st);
     k_dtable<T, FAST><<<unsigned((kTabEntries + 255) / 256), 256, 0, st>>>(a);
   }
+  // persistent: as many blocks as stay resident, at most one per chunk
+  int per_sm = 0;
+  const cudaError_t e = resident_blocks<k_decode<T, FAST, VEC>>(kDecThreads, 0, &per_sm);
+  if (e != cudaSuccess) return e;
+  uint64_t grid = uint64_t(per_sm < 1 ? 1 : per_sm) * uint64_t(device_sm_count());
+  if (grid > decode_chunks(a.n)) grid = decode_chunks(a.n);
   TraceScope ts("k_decode", st);
-  k_decode<T, FAST, VEC><<<unsigned(decode_chunks(a.n)), kDecThreads, 0, st>>>(a);
+  k_decode<T, FAST, VEC><<<unsigned(grid), kDecThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -526,9 +605,10 @@ cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   {
     TraceScope ts("k_validate", st);
-    k_validate<<<unsigned((a.num_leaves + 255) / 256), 256, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
-                                                                        static_cast<ChunkInfo *>(a.chunks), a.err, a.qb,
-                                                                        a.raw, a.dtype == 0 ? 32u : 64u);
+    // 64 threads a block: the leaves spread over every SM (each thread waits on its records)
+    k_validate<<<unsigned((a.num_leaves + 63) / 64), 64, 0, st>>>(a.stream, a.n, a.num_leaves, a.payload_words,
+                                                                      static_cast<ChunkInfo *>(a.chunks), a.err, a.qb,
+                                                                      a.raw, a.dtype == 0 ? 32u : 64u);
   }
   if (a.raw) {
     TraceScope ts("k_decode", st);
