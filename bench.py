@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch-256", "serve-2000", "leaf-sweep"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--leaf-size", type=int, default=4096)
+    ap.add_argument("--autotune", action="store_true",
+                    help="leaf size chosen by the autotuner (then --leaf-size is the largest candidate, "
+                         "0 = PC_MAX_LEAF_SIZE)")
     ap.add_argument("--reduce", action="store_true",
                     help="compress with the bit-box reduction (Sec. 4.1, Alg. 1) in place of plain leaves")
     ap.add_argument("--reorder", action="store_true",
@@ -337,7 +340,8 @@ def run_ours(args, spec):
     emode = pc.PC_EB_REL if mode == "rel" else pc.PC_EB_ABS
     esz = 4 if dtype == "f32" else 8
     pos = torch.from_numpy(pos_h).to(dev)
-    cfg = pc.config(args.leaf_size, reduce=args.reduce, reorder=args.reorder, widest=args.widest)
+    cfg = pc.config(args.leaf_size, autotune=args.autotune, reduce=args.reduce, reorder=args.reorder,
+                    widest=args.widest)
     comp = pc.Compressor(n, pdt, leaf_size=cfg, device=dev)
     dec = torch.empty_like(pos)
 
@@ -447,7 +451,8 @@ def run_ours(args, spec):
                     "timed": False}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(spec, args.leaf_size, CPU_SAMPLE // 4 if args.reduce else CPU_SAMPLE, args.reduce,
+        cpu = cpu_baseline(spec, info.leaf_size if args.autotune else args.leaf_size,
+                           CPU_SAMPLE // 4 if args.reduce else CPU_SAMPLE, args.reduce,
                            args.reorder, args.widest)
 
     extras = {}
@@ -462,7 +467,8 @@ def run_ours(args, spec):
             "warmup": max(args.warmup, 3), "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "generator": gen, "particles": n, "eb_mode": mode, "eb": eb,
-                       "leaf_size": args.leaf_size, "box_reduction": bool(args.reduce),
+                       "leaf_size": info.leaf_size if args.autotune else args.leaf_size,
+                       "autotuned_leaf_size": bool(args.autotune), "box_reduction": bool(args.reduce),
                        "reorder": bool(args.reorder), "widest_axis": bool(args.widest),
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)", "code_bytes": cb},
