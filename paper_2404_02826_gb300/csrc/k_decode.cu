@@ -66,7 +66,8 @@ __device__ __forceinline__ uint64_t leaf_words(const Rec &r, uint64_t cnt) {
 struct ChunkInfo {
   uint64_t lo, end;     // staged words [lo, end) of the payload
   uint32_t first, last;  // leaves of the chunk's first and last particle
-  uint32_t pad[2];
+  uint32_t tag;          // a batch: index of the chunk's stream
+  uint32_t pad;
 };
 
 // One thread per leaf: every field and every neighbour relation is checked,
@@ -75,9 +76,11 @@ struct ChunkInfo {
 // The range of codes a leaf can produce, [q_ref - 2^(m-1) + 1, q_ref + 2^(m-1)]
 // per axis (any m-bit field, the unused all-ones one included), is reduced
 // per warp into qb: qb[d] = min(0, lowest code), qb[3 + d] = max(0, highest).
-__global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves, uint64_t words,
-                           ChunkInfo *info, uint32_t *err, int32_t *qb, uint32_t raw, uint32_t M) {
-  const uint64_t L = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+// Leaf L of one stream (a lane past its last leaf takes part in the warp
+// reductions only).
+__device__ __forceinline__ void validate_leaf(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves,
+                                              uint64_t words, ChunkInfo *info, uint32_t *err, int32_t *qb,
+                                              uint32_t raw, uint32_t M, uint64_t L) {
   const bool mine = L < num_leaves;
   const uint8_t *table = stream + kHeaderBytes;
   int32_t low[3] = {0, 0, 0}, top[3] = {0, 0, 0};
@@ -134,6 +137,11 @@ __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint6
       if (top[d]) atomicMax(qb + 3 + d, top[d]);
     }
   }
+}
+
+__global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint64_t num_leaves, uint64_t words,
+                           ChunkInfo *info, uint32_t *err, int32_t *qb, uint32_t raw, uint32_t M) {
+  validate_leaf(stream, n, num_leaves, words, info, err, qb, raw, M, uint64_t(blockIdx.x) * blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ uint32_t word_at(const uint32_t *__restrict__ w, uint64_t nwords, uint64_t i) {
@@ -260,8 +268,7 @@ __device__ __forceinline__ void add_fields(uint32_t w0, uint32_t w1, uint32_t w2
 // table after another: the dequantization of a particle becomes three
 // lookups, and the double expression is evaluated once per code.
 template <typename T, bool FAST>
-__global__ void k_dtable(DecodeLaunch a) {
-  if (*a.err) return;
+__device__ __forceinline__ void fill_table(const DecodeLaunch &a) {
   uint32_t tb[3], te;
   if (!table_fits(a.qb, tb, te)) return;
   T *tab = static_cast<T *>(a.tab);
@@ -270,6 +277,11 @@ __global__ void k_dtable(DecodeLaunch a) {
     const int32_t q = a.qb[d] + int32_t(e - tb[d]);
     tab[e] = dequant<T, FAST>(a, d, q);
   }
+}
+template <typename T, bool FAST>
+__global__ void k_dtable(DecodeLaunch a) {
+  if (*a.err) return;
+  fill_table<T, FAST>(a);
 }
 
 // Whether a chunk is decoded from shared memory: at most kChunkLeaves leaves
@@ -284,14 +296,14 @@ __device__ __forceinline__ bool chunk_staged(const ChunkInfo &ci) {
 // barrier.  Source and destination are 16-byte aligned: the stream starts on
 // 16 bytes, the leaf table at byte 96 in 32-byte records, the payload after
 // it, and a chunk's first staged word is a multiple of 4.
-__device__ __forceinline__ void dec_issue(const DecodeLaunch &a, DecSmem &S, int b, const ChunkInfo &ci,
+__device__ __forceinline__ void dec_issue(uint64_t payload_words, DecSmem &S, int b, const ChunkInfo &ci,
                                           const uint32_t *words, const uint8_t *table) {
   S.ci[b] = ci;
   uint32_t nw = 0, bytes = 0;
   const bool staged = chunk_staged(ci);
   if (staged) {
     const uint64_t up = (ci.end - ci.lo + 3) & ~3ull;
-    const uint64_t avail = a.payload_words > ci.lo ? a.payload_words - ci.lo : 0;
+    const uint64_t avail = payload_words > ci.lo ? payload_words - ci.lo : 0;
     nw = uint32_t(up <= avail ? up : (avail & ~3ull));
     bytes = 4 * nw + uint32_t(kLeafBytes) * (ci.last - ci.first + 1);
   }
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
     mbar_init(&S.bar[0], 1);
     mbar_init(&S.bar[1], 1);
     mbar_fence_init();
-    dec_issue(a, S, 0, cinfo[chunk], words, table);
+    dec_issue(a.payload_words, S, 0, cinfo[chunk], words, table);
     if (chunk + G < nchunks) ahead = cinfo[chunk + G];
   }
   __syncthreads();
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
     if (__syncthreads_or(late)) break;
     if (threadIdx.x == 0 && chunk + G < nchunks) {
       fence_proxy_async();  // earlier generic reads of that area precede the async writes
-      dec_issue(a, S, b ^ 1, ahead, words, table);
+      dec_issue(a.payload_words, S, b ^ 1, ahead, words, table);
       if (chunk + 2 * G < nchunks) ahead = cinfo[chunk + 2 * G];
     }
     __align__(16) T vals[3 * kDecPer];
@@ -589,6 +601,292 @@ cudaError_t decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
   return a.vec ? decode_launch<T, FAST, true>(a, st) : decode_launch<T, FAST, false>(a, st);
 }
 
+
+// ---- many streams: one set of launches for a batch ----
+
+__global__ void k_gather_headers(const uint8_t *const *streams, uint32_t count, uint8_t *dst) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte word of one header
+  if (i >= count * (kHeaderBytes / 16)) return;
+  const uint32_t item = i / (kHeaderBytes / 16), w = i % (kHeaderBytes / 16);
+  reinterpret_cast<uint4 *>(dst)[i] = __ldg(reinterpret_cast<const uint4 *>(streams[item]) + w);
+}
+
+// The batch's leaf space, a warp per step: a warp's leaves belong to one
+// stream (streams start on multiples of 32), found by binary search.
+__global__ void k_validate_batch(const DecItem *items, const uint64_t *leaf_start, uint32_t count, uint64_t leaves) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x; base < leaves; base += stride) {
+    const uint64_t wbase = base + (threadIdx.x & ~31u);
+    uint32_t lo = 0, hi = count - 1;  // the last stream whose leaves start at or before the warp's
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (leaf_start[mid] <= wbase) lo = mid;
+      else hi = mid - 1;
+    }
+    const DecodeLaunch &a = items[lo].a;
+    validate_leaf(a.stream, a.n, a.num_leaves, a.payload_words, static_cast<ChunkInfo *>(a.chunks), a.err, a.qb,
+                  a.raw, a.dtype == 0 ? 32u : 64u, base + threadIdx.x - leaf_start[lo]);
+  }
+}
+
+// Every chunk descriptor of a stream names the stream (one grid row per
+// stream), whatever its validation finds: the batched decoder reads the tag
+// before it trusts anything else in a descriptor.
+__global__ void k_tag_chunks(const DecItem *items, uint32_t first) {
+  const uint32_t item = first + blockIdx.y;
+  const DecodeLaunch &a = items[item].a;
+  ChunkInfo *info = static_cast<ChunkInfo *>(a.chunks);
+  const uint64_t chunks = (a.n + kChunk - 1) / kChunk;
+  for (uint64_t c = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < chunks; c += uint64_t(gridDim.x) * blockDim.x)
+    info[c].tag = item;
+}
+
+// One grid row per stream.
+__global__ void k_dtable_batch(const DecItem *items) {
+  const DecodeLaunch &a = items[blockIdx.y].a;
+  if (*a.err || a.raw) return;
+  if (a.dtype == 0) {
+    if (a.fast) fill_table<float, true>(a);
+    else fill_table<float, false>(a);
+  } else {
+    fill_table<double, false>(a);
+  }
+}
+
+// What every thread needs of the stream of a staged chunk (thread 0 writes it
+// with the chunk's copies).
+struct BatchMeta {
+  const DecodeLaunch *a;  // the stream's launch fields
+  const uint8_t *table;   // its leaf table
+  const uint32_t *words;  // its payload
+  uint64_t payload_words;
+  void *out;
+  const void *tab[3];     // code tables indexed by the code itself (with use_table)
+  uint64_t c0;            // first particle of the chunk in its stream
+  int32_t nloc;           // particles of the chunk
+  int32_t qlow[3];
+  uint32_t use_table;
+  uint32_t failed;        // the stream's validation failed: its chunks are not decoded
+};
+struct DecBatchSmem {
+  DecSmem d;
+  BatchMeta meta[2];
+  // thread 0's own state, kept here rather than in every thread's registers:
+  // the stream it last described and the descriptor of the chunk after the next
+  BatchMeta st;
+  uint64_t chunk0, n;
+  uint32_t cur;
+  ChunkInfo ahead;
+};
+
+// The batch's decoder for the streams of one kind: persistent blocks take the
+// kind's chunks k, k + G, ... as the single-stream decoder does; a chunk's
+// descriptor names its stream (written by the validation), and thread 0
+// refreshes what it keeps of a stream only when the stream changes.
+template <typename T, bool FAST, bool VEC>
+__global__ void __launch_bounds__(kDecThreads, 5) k_decode_batch(const DecItem *items, const ChunkInfo *cinfo,
+                                                              uint64_t nchunks) {
+  __shared__ __align__(16) DecBatchSmem S;
+  uint64_t chunk = blockIdx.x;
+  if (chunk >= nchunks) return;
+  const uint64_t G = gridDim.x;
+  BatchMeta &st = S.st;
+  auto issue = [&](int b, uint64_t g, const ChunkInfo &ci) {
+    if (ci.tag != S.cur) {
+      S.cur = ci.tag;
+      const DecodeLaunch &a = items[S.cur].a;
+      st.a = &a;
+      st.table = a.stream + kHeaderBytes;
+      st.words = reinterpret_cast<const uint32_t *>(st.table + uint64_t(kLeafBytes) * a.num_leaves);
+      st.payload_words = a.payload_words;
+      st.out = a.out;
+      uint32_t tb[3], te = 0;
+      st.use_table = table_fits(a.qb, tb, te) ? 1u : 0u;
+      const T *tabs = static_cast<const T *>(a.tab);
+      for (int d = 0; d < 3; ++d) {
+        st.qlow[d] = a.qb[d];
+        st.tab[d] = tabs + (int64_t(tb[d]) - a.qb[d]);
+      }
+      S.chunk0 = items[S.cur].chunk0;
+      S.n = a.n;
+      st.failed = *reinterpret_cast<const volatile uint32_t *>(a.err) != 0u ? 1u : 0u;
+    }
+    st.c0 = (g - S.chunk0) * kChunk;
+    st.nloc = int32_t(((st.c0 + kChunk) < S.n ? (st.c0 + kChunk) : S.n) - st.c0);
+    S.meta[b] = st;
+    if (st.failed) {  // nothing of the descriptor is used: an arrival without copies
+      S.d.ci[b] = ci;
+      S.d.ncopy[b] = 0;
+      mbar_expect_tx(&S.d.bar[b], 0);
+    } else {
+      dec_issue(st.payload_words, S.d, b, ci, st.words, st.table);
+    }
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&S.d.bar[0], 1);
+    mbar_init(&S.d.bar[1], 1);
+    mbar_fence_init();
+    S.cur = 0xffffffffu;
+    issue(0, chunk, cinfo[chunk]);
+    if (chunk + G < nchunks) S.ahead = cinfo[chunk + G];
+  }
+  __syncthreads();
+  uint32_t ph0 = 0u, ph1 = 0u;
+  for (int b = 0; chunk < nchunks; chunk += G, b ^= 1) {
+    const bool late = wait_buffer(&S.d.bar[b], b ? ph1 : ph0, S.meta[b].a->err);
+    if (b) ph1 ^= 1u;
+    else ph0 ^= 1u;
+    const ChunkInfo ci = S.d.ci[b];
+    const BatchMeta &M = S.meta[b];
+    const DecodeLaunch &A = *M.a;
+    const bool failed = M.failed != 0;  // the descriptor may be stale: nothing of it is read
+    const uint32_t count = ci.last - ci.first + 1;
+    const bool staged = !failed && chunk_staged(ci);
+    const uint64_t c0 = M.c0;
+    const int32_t nloc = M.nloc;
+    const bool use_table = M.use_table != 0;
+    const T *tab0 = static_cast<const T *>(M.tab[0]), *tab1 = static_cast<const T *>(M.tab[1]),
+            *tab2 = static_cast<const T *>(M.tab[2]);
+    const int32_t qlow0 = M.qlow[0], qlow1 = M.qlow[1], qlow2 = M.qlow[2];
+    if (staged && !late) {
+      if (threadIdx.x < count) {
+        const int L = threadIdx.x;
+        const Rec r = rec_from(S.d.buf[b].rec[2 * L], S.d.buf[b].rec[2 * L + 1]);
+        LeafC lc;
+        lc.rel = int32_t(int64_t(r.po) - int64_t(c0));
+        lc.w = r.m[0] + r.m[1] + r.m[2];
+        lc.base = int32_t(int64_t(32 * r.wo) - int64_t(32 * ci.lo) - int64_t(lc.w));
+        lc.m0 = r.m[0];
+        lc.s2 = r.m[0] + r.m[1];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          lc.mask[d] = (1u << r.m[d]) - 1u;
+          lc.qref[d] = r.q[d];
+          lc.off[d] = r.q[d] - int32_t(r.m[d] ? (1u << (r.m[d] - 1)) - 1u : 0u);
+        }
+        lc.pad[0] = lc.pad[1] = 0;
+        S.d.lc[b][L] = lc;
+      }
+      // the words the copy did not bring (the stream's last chunks only): its payload's tail, then zeros
+      const uint32_t nst = uint32_t(ci.end - ci.lo);
+      for (uint32_t w = S.d.ncopy[b] + threadIdx.x; w < nst; w += kDecThreads)
+        S.d.buf[b].sw[w] = ci.lo + w < M.payload_words ? __ldg(M.words + ci.lo + w) : 0u;
+    }
+    // this chunk's constants are in place; every thread is done with the other staging area
+    if (__syncthreads_or(late)) break;
+    if (threadIdx.x == 0 && chunk + G < nchunks) {
+      fence_proxy_async();  // earlier generic reads of that area precede the async writes
+      issue(b ^ 1, chunk + G, S.ahead);
+      if (chunk + 2 * G < nchunks) S.ahead = cinfo[chunk + 2 * G];
+    }
+    if (failed) continue;
+    __align__(16) T vals[3 * kDecPer];
+    int32_t qs[3 * kDecPer];  // codes of the run; unused slots hold the lowest code, a valid table index
+#pragma unroll
+    for (int v = 0; v < 3 * kDecPer; v += 3) {
+      qs[v] = qlow0;
+      qs[v + 1] = qlow1;
+      qs[v + 2] = qlow2;
+    }
+    const int32_t sl0 = int32_t(threadIdx.x) * kDecPer;
+    if (staged) {
+      const uint32_t *sw = S.d.buf[b].sw;
+      const LeafC *lcs = S.d.lc[b];
+      // kDecPer consecutive particles per thread: one leaf lookup for the run
+      if (sl0 < nloc) {
+        int L = 0;
+        while (L + 1 < int(count) && lcs[L + 1].rel <= sl0) ++L;
+        LeafC lc = lcs[L];
+        int32_t next = L + 1 < int(count) ? lcs[L + 1].rel : 0x7fffffff;
+#pragma unroll
+        for (int k = 0; k < kDecPer; ++k) {
+          const int32_t sl = sl0 + k;
+          if (sl >= nloc) continue;
+          if (sl >= next) {  // the run crosses into the next leaf
+            ++L;
+            lc = lcs[L];
+            next = L + 1 < int(count) ? lcs[L + 1].rel : 0x7fffffff;
+          }
+          const uint32_t i = uint32_t(sl) - uint32_t(lc.rel);
+          int32_t q0, q1, q2;
+          if (i == 0) {
+            q0 = lc.qref[0];
+            q1 = lc.qref[1];
+            q2 = lc.qref[2];
+          } else {
+            const uint32_t bit = uint32_t(lc.base) + i * lc.w;  // modulo 2^32; the result is below 2^17
+            const uint32_t wi = bit >> 5, r0 = bit & 31u;
+            const uint32_t a0 = sw[wi], a1 = sw[wi + 1], a2 = sw[wi + 2], a3 = sw[wi + 3];
+            const uint32_t v0 = __funnelshift_r(a0, a1, r0);  // bits [bit, bit + 96) of the payload
+            const uint32_t v1 = __funnelshift_r(a1, a2, r0);
+            const uint32_t v2 = __funnelshift_r(a2, a3, r0);
+            const bool hi2 = lc.s2 >= 32;
+            q0 = lc.off[0] + int32_t(v0 & lc.mask[0]);
+            q1 = lc.off[1] + int32_t(__funnelshift_r(v0, v1, lc.m0) & lc.mask[1]);
+            q2 = lc.off[2] + int32_t(__funnelshift_r(hi2 ? v1 : v0, hi2 ? v2 : v1, lc.s2) & lc.mask[2]);
+          }
+          qs[3 * k] = q0;
+          qs[3 * k + 1] = q1;
+          qs[3 * k + 2] = q2;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kDecPer; ++k) {
+        const int32_t sl = sl0 + k;
+        if (sl >= nloc) continue;
+        const uint64_t g = c0 + uint64_t(sl);
+        // many leaves, or a span beyond the staging area: search the leaf table
+        uint64_t lo = ci.first, hi = ci.last;
+        while (lo < hi) {
+          const uint64_t mid = (lo + hi + 1) >> 1;
+          if (load_rec(M.table, mid).po <= g) lo = mid;
+          else hi = mid - 1;
+        }
+        const Rec r = load_rec(M.table, lo);
+        const uint64_t po = r.po, wo = r.wo;
+        int32_t q0 = r.q[0], q1 = r.q[1], q2 = r.q[2];
+        const uint32_t mm = r.m[0] | (r.m[1] << 8) | (r.m[2] << 16);
+        const uint64_t i = g - po;
+        if (i > 0) {
+          const uint32_t w = (mm & 0xffu) + ((mm >> 8) & 0xffu) + ((mm >> 16) & 0xffu);
+          const uint64_t bit = 32ull * wo + (i - 1) * uint64_t(w);
+          const uint64_t wi = bit >> 5;
+          add_fields(word_at(M.words, M.payload_words, wi), word_at(M.words, M.payload_words, wi + 1),
+                     word_at(M.words, M.payload_words, wi + 2), word_at(M.words, M.payload_words, wi + 3),
+                     uint32_t(bit & 31), mm, q0, q1, q2);
+        }
+        qs[3 * k] = q0;
+        qs[3 * k + 1] = q1;
+        qs[3 * k + 2] = q2;
+      }
+    }
+    // dequantize the run: all lookups issued together
+    if (use_table) {
+#pragma unroll
+      for (int v = 0; v < 3 * kDecPer; ++v) vals[v] = __ldg((v % 3 == 0 ? tab0 : (v % 3 == 1 ? tab1 : tab2)) + qs[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 3 * kDecPer; ++v) vals[v] = dequant_particle<T, FAST>(A, v % 3, qs[v]);
+    }
+    // the run's 3 * kDecPer values are consecutive in the output
+    if (sl0 < nloc) {
+      T *out = static_cast<T *>(M.out) + 3 * (c0 + uint64_t(sl0));
+      if (VEC && sl0 + kDecPer <= nloc) {
+        constexpr int kVec = 3 * kDecPer * int(sizeof(T)) / 16;
+        uint4 *o4 = reinterpret_cast<uint4 *>(out);
+        const uint4 *v4 = reinterpret_cast<const uint4 *>(vals);
+#pragma unroll
+        for (int v = 0; v < kVec; ++v) __stcs(o4 + v, v4[v]);
+      } else {
+        const int m = 3 * min(kDecPer, nloc - sl0);
+#pragma unroll
+        for (int v = 0; v < 3 * kDecPer; ++v)
+          if (v < m) out[v] = vals[v];
+      }
+    }
+  }
+}
 }  // namespace
 
 uint64_t decode_chunks(uint64_t n) { return (n + kChunk - 1) / kChunk; }
@@ -598,6 +896,74 @@ uint64_t decode_chunk_bytes(uint64_t n) { return decode_chunks(n) * sizeof(Chunk
 cudaError_t launch_header(const HeaderLaunch &a, cudaStream_t st) {
   TraceScope ts("k_header", st);
   k_header<<<1, 1, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_headers(const uint8_t *const *streams, uint32_t count, uint8_t *dst, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const uint32_t words = count * (kHeaderBytes / 16);
+  k_gather_headers<<<(words + 255) / 256, 256, 0, st>>>(streams, count, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_batch(const DecItem *items, const uint64_t *leaf_start, uint32_t count, uint64_t leaves,
+                                  cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  TraceScope ts("k_validate", st);
+  for (uint32_t first = 0; first < count; first += 65535u) {  // one grid row per stream
+    const uint32_t rows = count - first < 65535u ? count - first : 65535u;
+    k_tag_chunks<<<dim3(8, rows), 256, 0, st>>>(items, first);
+  }
+  if (leaves) k_validate_batch<<<unsigned(8 * device_sm_count()), 64, 0, st>>>(items, leaf_start, count, leaves);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dtable_batch(const DecItem *items, uint32_t count, cudaStream_t st) {
+  TraceScope ts("k_dtable", st);
+  for (uint32_t first = 0; first < count; first += 65535u) {  // one grid row per stream
+    const uint32_t rows = count - first < 65535u ? count - first : 65535u;
+    k_dtable_batch<<<dim3((kTabEntries + 255) / 256, rows), 256, 0, st>>>(items + first);
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+template <typename T, bool FAST, bool VEC>
+cudaError_t decode_batch_as(const DecItem *items, const void *chunks, uint64_t num_chunks, cudaStream_t st) {
+  int per_sm = 0;
+  const cudaError_t e = resident_blocks<k_decode_batch<T, FAST, VEC>>(kDecThreads, 0, &per_sm);
+  if (e != cudaSuccess) return e;
+  uint64_t grid = uint64_t(per_sm < 1 ? 1 : per_sm) * uint64_t(device_sm_count());
+  if (grid > num_chunks) grid = num_chunks;
+  TraceScope ts("k_decode", st);
+  k_decode_batch<T, FAST, VEC><<<unsigned(grid), kDecThreads, 0, st>>>(items, static_cast<const ChunkInfo *>(chunks),
+                                                                       num_chunks);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_decode_batch(int kind, bool vec, const DecItem *items, const void *chunks, uint64_t num_chunks,
+                                cudaStream_t st) {
+  if (num_chunks == 0) return cudaSuccess;
+  switch (kind) {
+    case kDecKindF32Fast:
+      return vec ? decode_batch_as<float, true, true>(items, chunks, num_chunks, st)
+                 : decode_batch_as<float, true, false>(items, chunks, num_chunks, st);
+    case kDecKindF32:
+      return vec ? decode_batch_as<float, false, true>(items, chunks, num_chunks, st)
+                 : decode_batch_as<float, false, false>(items, chunks, num_chunks, st);
+    default:
+      return vec ? decode_batch_as<double, false, true>(items, chunks, num_chunks, st)
+                 : decode_batch_as<double, false, false>(items, chunks, num_chunks, st);
+  }
+}
+
+cudaError_t launch_decode_lossless(const DecodeLaunch &a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  TraceScope ts("k_decode", st);
+  const unsigned grid = unsigned((a.n + kDecThreads - 1) / kDecThreads);
+  if (a.dtype == 0) k_decode_lossless<float><<<grid, kDecThreads, 0, st>>>(a);
+  else k_decode_lossless<double><<<grid, kDecThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -144,6 +144,180 @@ class Arena {
   std::map<uint64_t, uint64_t> used_;  // offset -> length
 };
 
+// Workspace of a batched decompression: the stream pointers and headers, one
+// 64-byte error word and code bounds per item, the items' launch records, their
+// leaf starts, every item's chunk descriptors (planned from the item's particle
+// count) and one code table per item.
+struct DecBatchLayout {
+  uint64_t off_ptrs = 0, off_headers = 0, off_err = 0, off_items = 0, off_leaf_start = 0, off_chunks = 0,
+           off_tables = 0, table_stride = 0, total = 0;
+};
+
+int decode_batch_layout(const pc_decompress_item *items, uint32_t count, DecBatchLayout &L) {
+  uint64_t chunk_bytes = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (items[i].n > PC_MAX_PARTICLES) return PC_ERR_ARG;
+    chunk_bytes += pcx::decode_chunk_bytes(items[i].n);
+  }
+  uint64_t o = 0;
+  L.off_ptrs = o;
+  o = align_up(o + 8ull * count);
+  L.off_headers = o;
+  o = align_up(o + uint64_t(PC_HEADER_BYTES) * count);
+  L.off_err = o;
+  o = align_up(o + 64ull * count);
+  L.off_items = o;
+  o = align_up(o + sizeof(pcx::DecItem) * count);
+  L.off_leaf_start = o;
+  o = align_up(o + 8ull * (count + 1));
+  L.off_chunks = o;
+  o = align_up(o + chunk_bytes);
+  L.table_stride = align_up(pcx::decode_table_bytes());
+  L.off_tables = o;
+  o += L.table_stride * count;
+  L.total = o;
+  return PC_OK;
+}
+
+// The batched decompression proper: every item's status is set; returns
+// PC_ERR_CUDA when a CUDA call failed, else PC_OK.
+//  1. the headers of all streams: one gather kernel and one read-back;
+//  2. the plain call's checks per item, on the host, in its order;
+//  3. one validation launch over all streams' leaves, one table launch, one
+//     persistent decode launch per kind of stream (streams with lossless axes
+//     one launch each);
+//  4. every item's error word: one read-back.
+int decode_batch_run(pc_decompress_item *items, uint32_t count, const DecBatchLayout &L, uint8_t *ws,
+                     cudaStream_t st) {
+  std::vector<const uint8_t *> ptrs(count, nullptr);
+  std::vector<uint8_t> live(count, 0);
+  uint32_t first_live = count;
+  for (uint32_t i = 0; i < count; ++i) {
+    const pc_decompress_item &it = items[i];
+    items[i].status = PC_OK;
+    if (!it.stream_data || reinterpret_cast<uintptr_t>(it.stream_data) % 16) {
+      items[i].status = PC_ERR_ARG;
+    } else if (it.stream_bytes < PC_HEADER_BYTES) {
+      items[i].status = PC_ERR_CORRUPT;
+    } else {
+      live[i] = 1;
+      if (first_live == count) first_live = i;
+    }
+    ptrs[i] = static_cast<const uint8_t *>(it.stream_data);
+  }
+  if (first_live == count) return PC_OK;
+  for (uint32_t i = 0; i < count; ++i)
+    if (!live[i]) ptrs[i] = ptrs[first_live];  // a header that is not used: read from a valid stream
+  std::vector<uint8_t> headers(uint64_t(count) * PC_HEADER_BYTES);
+  if (cudaMemcpyAsync(ws + L.off_ptrs, ptrs.data(), 8ull * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      pcx::launch_gather_headers(reinterpret_cast<const uint8_t *const *>(ws + L.off_ptrs), count,
+                                 ws + L.off_headers, st) != cudaSuccess ||
+      cudaMemcpyAsync(headers.data(), ws + L.off_headers, headers.size(), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(ws + L.off_err, 0, 64ull * count, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return PC_ERR_CUDA;
+
+  std::vector<pcx::DecItem> dev;  // the streams that decode, in item order
+  std::vector<uint32_t> which;    // their item index
+  std::vector<int> kind;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (!live[i]) continue;
+    const pc_decompress_item &it = items[i];
+    pc_info I;
+    int s = pc_stream_info(headers.data() + uint64_t(i) * PC_HEADER_BYTES, PC_HEADER_BYTES, &I);
+    const uint64_t esz = I.dtype == PC_F32 ? 4 : 8;
+    if (!s && I.total_bytes > it.stream_bytes) s = PC_ERR_CORRUPT;
+    if (!s && it.out_capacity_bytes < 3 * esz * I.n) s = PC_ERR_CAPACITY;
+    if (!s && I.n == 0) continue;  // nothing to decode: PC_OK
+    if (!s && (!it.out_positions || reinterpret_cast<uintptr_t>(it.out_positions) % esz)) s = PC_ERR_ARG;
+    if (!s && I.n > it.n) s = PC_ERR_CAPACITY;  // the workspace was planned for it.n particles
+    if (s) {
+      items[i].status = s;
+      continue;
+    }
+    pcx::DecItem d = {};
+    pcx::DecodeLaunch &a = d.a;
+    a.stream = static_cast<const uint8_t *>(it.stream_data);
+    a.n = I.n;
+    a.dtype = int(I.dtype);
+    a.num_leaves = I.num_leaves;
+    a.payload_words = I.payload_words;
+    a.s = I.s;
+    bool exact_o = true;
+    for (int k = 0; k < 3; ++k) {
+      a.o[k] = I.o[k];
+      a.of[k] = float(I.o[k]);
+      exact_o = exact_o && double(a.of[k]) == I.o[k];
+    }
+    a.sh = float(I.s);
+    a.sl = float(I.s - double(a.sh));
+    a.fast = I.dtype == PC_F32 && exact_o && I.s > 0x1p-100 && I.s < 0x1p100;
+    a.out = it.out_positions;
+    a.vec = reinterpret_cast<uintptr_t>(it.out_positions) % 16 == 0;
+    a.err = reinterpret_cast<uint32_t *>(ws + L.off_err + 64ull * i);
+    a.qb = reinterpret_cast<int32_t *>(ws + L.off_err + 64ull * i + 32);
+    a.tab = ws + L.off_tables + L.table_stride * i;
+    a.raw = I.lossless_axes;
+    dev.push_back(d);
+    which.push_back(i);
+    kind.push_back(a.raw ? pcx::kDecKinds
+                         : (a.dtype == 0 ? (a.fast ? pcx::kDecKindF32Fast : pcx::kDecKindF32) : pcx::kDecKindF64));
+  }
+  const uint32_t nd = uint32_t(dev.size());
+  if (nd == 0) return PC_OK;
+  // chunk descriptors: each kind's streams one after another (lossless streams last)
+  uint64_t at = 0;
+  uint64_t kind_first[pcx::kDecKinds + 1] = {}, kind_chunks[pcx::kDecKinds + 1] = {};
+  bool kind_vec[pcx::kDecKinds] = {true, true, true};
+  for (int k = 0; k <= pcx::kDecKinds; ++k) {
+    kind_first[k] = at;
+    for (uint32_t j = 0; j < nd; ++j) {
+      if (kind[j] != k) continue;
+      dev[j].a.chunks = ws + L.off_chunks + 32ull * at;
+      dev[j].chunk0 = at - kind_first[k];
+      at += pcx::decode_chunks(dev[j].a.n);
+      if (k < pcx::kDecKinds) kind_vec[k] = kind_vec[k] && dev[j].a.vec;
+    }
+    kind_chunks[k] = at - kind_first[k];
+  }
+  // leaves: every stream from a multiple of 32
+  std::vector<uint64_t> leaf_start(nd + 1);
+  uint64_t leaves = 0;
+  for (uint32_t j = 0; j < nd; ++j) {
+    dev[j].leaf0 = leaves;
+    leaf_start[j] = leaves;
+    leaves += (dev[j].a.num_leaves + 31) / 32 * 32;
+  }
+  leaf_start[nd] = leaves;
+  pcx::DecItem *items_dev = reinterpret_cast<pcx::DecItem *>(ws + L.off_items);
+  uint64_t *leaf_dev = reinterpret_cast<uint64_t *>(ws + L.off_leaf_start);
+  if (cudaMemcpyAsync(items_dev, dev.data(), sizeof(pcx::DecItem) * nd, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(leaf_dev, leaf_start.data(), 8ull * (nd + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      pcx::launch_validate_batch(items_dev, leaf_dev, nd, leaves, st) != cudaSuccess ||
+      pcx::launch_dtable_batch(items_dev, nd, st) != cudaSuccess)
+    return PC_ERR_CUDA;
+  for (int k = 0; k < pcx::kDecKinds; ++k)
+    if (pcx::launch_decode_batch(k, kind_vec[k], items_dev, ws + L.off_chunks + 32ull * kind_first[k],
+                                 kind_chunks[k], st) != cudaSuccess)
+      return PC_ERR_CUDA;
+  for (uint32_t j = 0; j < nd; ++j)
+    if (kind[j] == pcx::kDecKinds && pcx::launch_decode_lossless(dev[j].a, st) != cudaSuccess) return PC_ERR_CUDA;
+  // every item's error word: one read-back
+  std::vector<uint32_t> errs(16ull * count);
+  if (cudaMemcpyAsync(errs.data(), ws + L.off_err, 64ull * count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PC_ERR_CUDA;
+  pcx::trace_flush();
+  for (uint32_t j = 0; j < nd; ++j) {
+    const uint32_t e = errs[16ull * which[j]];
+    items[which[j]].status = (e & pcx::kErrCorrupt)   ? PC_ERR_CORRUPT
+                             : (e & pcx::kErrTimeout) ? PC_ERR_TIMEOUT
+                             : e                      ? PC_ERR_CUDA
+                                                      : PC_OK;
+  }
+  return PC_OK;
+}
+
 }  // namespace
 
 struct pc_server {
@@ -321,38 +495,27 @@ int pc_compress_batch(pc_compress_item *items, uint32_t count, uint32_t lanes, v
 
 int pc_decompress_batch_workspace_size(const pc_decompress_item *items, uint32_t count, uint32_t lanes,
                                        uint64_t *out_bytes) {
+  (void)lanes;  // one set of launches serves every item
   if (!out_bytes || (count && !items)) return PC_ERR_ARG;
-  uint64_t slice = kArenaAlign;
-  for (uint32_t i = 0; i < count; ++i) {
-    uint64_t b = 0;
-    int rc = pc_decompress_workspace_size(items[i].n, &b);
-    if (rc) return rc;
-    slice = std::max(slice, align_up(b));
-  }
-  *out_bytes = slice * pick_lanes(lanes, count);
+  DecBatchLayout L;
+  const int rc = decode_batch_layout(items, count, L);
+  if (rc) return rc;
+  *out_bytes = L.total;
   return PC_OK;
 }
 
 int pc_decompress_batch(pc_decompress_item *items, uint32_t count, uint32_t lanes, void *workspace,
                         uint64_t workspace_bytes, void *stream) {
+  (void)lanes;  // one set of launches serves every item
   if (count == 0) return PC_OK;
   if (!items || !workspace || reinterpret_cast<uintptr_t>(workspace) % kArenaAlign) return PC_ERR_ARG;
-  lanes = pick_lanes(lanes, count);
-  uint64_t need = 0;
-  int rc = pc_decompress_batch_workspace_size(items, count, lanes, &need);
+  DecBatchLayout L;
+  const int rc = decode_batch_layout(items, count, L);
   if (rc) return rc;
-  if (workspace_bytes < need) return PC_ERR_CAPACITY;
-  const uint64_t slice = need / lanes;
-  std::vector<uint32_t> order(count);
-  std::iota(order.begin(), order.end(), 0u);
-  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return items[a].n > items[b].n; });
-  uint8_t *ws = static_cast<uint8_t *>(workspace);
-  rc = run_lanes(lanes, order, static_cast<cudaStream_t>(stream), [&](uint32_t lane, cudaStream_t s, uint32_t i) {
-    pc_decompress_item &it = items[i];
-    it.status = pc_decompress(it.stream_data, it.stream_bytes, it.out_positions, it.out_capacity_bytes,
-                              ws + lane * slice, slice, s);
-  });
-  if (rc) return rc;
+  if (workspace_bytes < L.total) return PC_ERR_CAPACITY;
+  const int cuda = decode_batch_run(items, count, L, static_cast<uint8_t *>(workspace),
+                                    static_cast<cudaStream_t>(stream));
+  if (cuda) return cuda;
   for (uint32_t i = 0; i < count; ++i)
     if (items[i].status != PC_OK) return items[i].status;
   return PC_OK;

@@ -276,6 +276,31 @@ struct DecodeLaunch {
   uint32_t raw;          // lossless-axis mask: those axes hold M-bit patterns, every particle in the payload
 };
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
+
+// Many streams decoded by one set of launches: each stream's plain launch
+// fields, and where its leaves start in the batch's leaf space (a multiple of
+// 32, so that no warp holds leaves of two streams) and its chunks in the chunk
+// space of its kind (the streams one decode launch serves: float with the
+// float-pair path, float, double).  A kind's chunk descriptors are one array,
+// the streams' parts of it in the kind's order.
+struct DecItem {
+  DecodeLaunch a;
+  uint64_t leaf0;
+  uint64_t chunk0;
+};
+enum : int { kDecKindF32Fast = 0, kDecKindF32 = 1, kDecKindF64 = 2, kDecKinds = 3 };
+// Copies the 96-byte header of `count` 16-byte aligned device streams into dst.
+cudaError_t launch_gather_headers(const uint8_t *const *streams, uint32_t count, uint8_t *dst, cudaStream_t st);
+// Validation and chunk descriptors of every stream (leaf_start: [count + 1], device).
+cudaError_t launch_validate_batch(const DecItem *items, const uint64_t *leaf_start, uint32_t count, uint64_t leaves,
+                                  cudaStream_t st);
+// Code tables of every stream that decodes through them.
+cudaError_t launch_dtable_batch(const DecItem *items, uint32_t count, cudaStream_t st);
+// Every chunk of one kind's streams, one persistent launch (chunks: that kind's descriptors).
+cudaError_t launch_decode_batch(int kind, bool vec, const DecItem *items, const void *chunks,
+                                uint64_t num_chunks, cudaStream_t st);
+// A stream with lossless axes, decoded on its own after the batch's validation.
+cudaError_t launch_decode_lossless(const DecodeLaunch &a, cudaStream_t st);
 uint64_t decode_chunks(uint64_t n);
 uint64_t decode_table_bytes();
 uint64_t decode_chunk_bytes(uint64_t n);

@@ -116,6 +116,59 @@ def test_batch_reports_failed_items(pc):
     assert torch.equal(outs[0][:sizes[0]], _alone(pc, good, pc.PC_EB_REL, 1e-3, 0))
 
 
+def test_decompress_batch_kinds_and_failures(pc, oracle_mod):
+    """One batched decompression over streams of every kind (float32, float64,
+    lossless axes, empty) and broken items (a corrupt leaf record, a truncated
+    stream, an output too small, an output 4 bytes off 16-byte alignment): each
+    item's status and output equal the plain call's, and the decoded floats the
+    oracle's."""
+    dev = torch.device("cuda:0")
+    specs = [("cosmology", 70_000, np.float32, pc.PC_EB_REL, 1e-3), ("fluid", 50_000, np.float64, pc.PC_EB_ABS, 1e-4),
+             ("cosmology", 30_000, np.float32, pc.PC_EB_REL, 1e-9), ("uniform", 0, np.float32, pc.PC_EB_REL, 1e-3),
+             ("uniform", 90_001, np.float32, pc.PC_EB_REL, 1e-2), ("fluid", 20_000, np.float64, pc.PC_EB_REL, 1e-12)]
+    pos, streams = [], []
+    for gen, n, dt, m, eb in specs:
+        p = synth.by_name(gen, n, seed=n % 13, dtype=dt) if n else np.zeros((0, 3), dt)
+        d = torch.from_numpy(p).to(dev)
+        c = pc.Compressor(max(n, 1), pc.PC_F32 if dt == np.float32 else pc.PC_F64, device=dev)
+        size = c.compress(d, m, eb)
+        om = oracle_mod.REL if m == pc.PC_EB_REL else oracle_mod.ABS
+        ref, _ = oracle_mod.compress(p, om, eb)
+        assert c.out[:size].cpu().numpy().tobytes() == ref
+        pos.append(p)
+        streams.append(c.out[:size].clone())
+    # broken items: a corrupt leaf record (its zero byte set), a truncated stream, too small an output
+    bad = streams[0].clone()
+    bad[96 + 32 * 2 + 31] = 1
+    items = [(s, s.numel(), torch.empty(p.shape, dtype=torch.from_numpy(p).dtype, device=dev))
+             for s, p in zip(streams, pos)]
+    items.append((bad, bad.numel(), torch.empty(pos[0].shape, dtype=torch.float32, device=dev)))
+    items.append((streams[1], streams[1].numel() - 4, torch.empty(pos[1].shape, dtype=torch.float64, device=dev)))
+    items.append((streams[4], streams[4].numel(), torch.empty((10, 3), dtype=torch.float32, device=dev)))
+    # an output 4 bytes off 16-byte alignment: the float32 streams then decode without 16-byte stores
+    off = torch.empty(pos[4].size + 1, dtype=torch.float32, device=dev)[1:].view(-1, 3)
+    items.append((streams[4], streams[4].numel(), off))
+    outs = [o for _, _, o in items]
+    got = pc.pc_decompress_batch([s for s, _, _ in items], [nb for _, nb, _ in items], outs)
+    for (s, nb, o), st in zip(items, got):
+        alone = torch.zeros_like(o)
+        c = pc.Compressor(max(o.shape[0], 1), pc.PC_F32 if o.dtype == torch.float32 else pc.PC_F64, device=dev)
+        try:
+            c.decompress(s[:nb] if nb <= s.numel() else s, alone, nb)
+            want = pc.PC_OK
+        except pc.PCError as e:
+            want = e.status
+        assert st == want
+        if st == pc.PC_OK and o.shape[0]:
+            assert torch.equal(o, alone)
+    expect = [pc.PC_OK] * 6 + [pc.PC_ERR_CORRUPT, pc.PC_ERR_CORRUPT, pc.PC_ERR_CAPACITY, pc.PC_OK]
+    assert got == expect
+    for p, s, o in zip(pos, streams, outs[:6]):
+        if p.shape[0]:
+            assert o.cpu().numpy().tobytes() == oracle_mod.decompress(s.cpu().numpy().tobytes()).tobytes()
+    assert torch.equal(outs[9], outs[4])
+
+
 @pytest.mark.parametrize("arena_mb,lanes", [(1024, 4), (96, 3)])
 def test_server_mix_equals_alone(pc, arena_mb, lanes):
     """Compress requests, then decompress requests of their streams, submitted
