@@ -286,16 +286,23 @@ int pc_leaf_size_sweep(const void *positions, uint64_t n, int dtype, int eb_mode
 
 /* ---- Many snapshots --------------------------------------------------------
  * The paper compresses one snapshot at a time; nothing below has a
- * counterpart in it.  These calls run many independent snapshots on one GPU
- * through `lanes` CUDA streams, each driven by its own host thread and owning
- * one slice of the workspace.  Items are taken largest first, so small
- * snapshots overlap on the device with each other and with large ones.  Each
- * item's stream (or positions) is byte-identical to a plain pc_compress (or
- * pc_decompress) of the same input: the same kernels run in the same order
- * within an item.  Work queued on `stream` before the call completes before
- * any item starts; every item is complete when the call returns.  The call
- * returns PC_OK when every item succeeded, else the status of the failed item
- * with the lowest index; every item carries its own status. */
+ * counterpart in it.
+ * Compression runs many independent snapshots on one GPU through `lanes` CUDA
+ * streams, each driven by its own host thread and owning one slice of the
+ * workspace; items are taken largest first, so small snapshots overlap on the
+ * device with each other and with large ones, and an item runs the plain
+ * call's kernels in the plain call's order.
+ * Decompression runs every item in one set of launches on `stream` (`lanes` is
+ * not used): the headers are gathered and read back once, the leaves of all
+ * streams are validated in one launch and their code tables built in one, and
+ * the chunks of all streams of one kind (float32, float64) are decoded by one
+ * persistent launch; streams with lossless axes decode one launch each.
+ * Either way each item's stream (or positions) is byte-identical to a plain
+ * pc_compress (or pc_decompress) of the same input.  Work queued on `stream`
+ * before the call completes before any item starts; every item is complete
+ * when the call returns.  The call returns PC_OK when every item succeeded,
+ * else the status of the failed item with the lowest index; every item
+ * carries its own status (a failed item's output holds nothing valid). */
 typedef struct {
     const void *positions;  /* device, T[n][3] */
     uint64_t n;
@@ -327,6 +334,10 @@ int pc_compress_batch_workspace_size(const pc_compress_item *items, uint32_t cou
                                      uint64_t *out_bytes);
 int pc_compress_batch(pc_compress_item *items, uint32_t count, uint32_t lanes, void *workspace,
                       uint64_t workspace_bytes, void *stream);
+/* Device scratch for a batched decompression (host only): per item a code
+ * table and the chunk descriptors of pc_decompress_item.n particles, plus the
+ * batch's headers and records; `lanes` is not used.  An item whose stream holds
+ * more particles than its n fails with PC_ERR_CAPACITY. */
 int pc_decompress_batch_workspace_size(const pc_decompress_item *items, uint32_t count, uint32_t lanes,
                                        uint64_t *out_bytes);
 int pc_decompress_batch(pc_decompress_item *items, uint32_t count, uint32_t lanes, void *workspace,
