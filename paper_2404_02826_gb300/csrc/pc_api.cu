@@ -825,6 +825,10 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   if (reinterpret_cast<uintptr_t>(stream_data) % 16 || reinterpret_cast<uintptr_t>(workspace) % kAlign)
     return PC_ERR_ARG;
   if (stream_bytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
+  if (workspace_bytes < 64) return PC_ERR_CAPACITY;
+  uint32_t *err = static_cast<uint32_t *>(workspace);
+  // the error word and code bounds are cleared while the header comes back
+  PC_TRY(cudaMemsetAsync(err, 0, 64, st));
   uint8_t h[PC_HEADER_BYTES];
   PC_TRY(cudaMemcpyAsync(h, stream_data, PC_HEADER_BYTES, cudaMemcpyDefault, st));
   PC_TRY(cudaStreamSynchronize(st));
@@ -837,8 +841,6 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   if (I.n == 0) return PC_OK;
   if (!out_positions || reinterpret_cast<uintptr_t>(out_positions) % esz) return PC_ERR_ARG;
   if (workspace_bytes < decompress_ws_bytes(I.n)) return PC_ERR_CAPACITY;
-  uint32_t *err = static_cast<uint32_t *>(workspace);
-  PC_TRY(cudaMemsetAsync(err, 0, 64, st));  // error word and code bounds
   DecodeLaunch da = {};
   da.stream = static_cast<const uint8_t *>(stream_data);
   da.n = I.n;
