@@ -13,7 +13,9 @@
 //   k_ro_counts, k_ro_scan, k_ro_records  new first particles (one block scans the
 //               counts in the new order) and the records;
 //   k_ro_sort   a block per sequence: keys R-index << 32 | position sorted in
-//               shared memory (bitonic), then the codes and indices moved;
+//               shared memory (kRadixMin to kRadixMax keys of at most 64 bits:
+//               stable radix passes over the R-index, 4 bits each; else
+//               bitonic), then the codes and indices moved;
 //               longer sequences with 8-byte keys are merge-sorted in global
 //               memory (k_ro_big_*: runs of kSmemSort keys sorted in shared
 //               memory, then merged pairwise, each key finding its place in the
@@ -32,6 +34,11 @@ constexpr int kRankThreads = 256;
 constexpr uint32_t kSmemSort = 16384;  // keys sorted in shared memory: 8-byte keys (128 KB)
 constexpr uint32_t kSmemWide = 8192;   // 16-byte keys (128 KB)
 constexpr int kSortThreads = 1024;
+constexpr uint32_t kRadixMin = 1000;   // narrow-key sequences of kRadixMin..kRadixMax particles after the centre
+constexpr uint32_t kRadixMax = 8192;   // are sorted by radix passes instead of the bitonic network (shorter ones
+                                       // sort faster in a warp's registers: 0.67 against 1.82 ms at 2^25, r = 128)
+constexpr int kRadixRounds = 8;        // their keys per thread, at most (kRadixMax over 1024 threads)
+constexpr uint32_t kRadixTable = 4096; // counters of one pass: 16 digits x rounds x warps <= kRadixMax / 2
 
 struct RoPlan {
   uint32_t hist_m[3][32];
@@ -350,6 +357,89 @@ __device__ void bitonic_regs(unsigned long long (&v)[E], uint32_t P, unsigned lo
     }
 }
 
+// Exclusive scan of n counters in shared memory by the whole block
+// (n <= 4 * blockDim.x, blockDim.x a multiple of 32); wsum: 32 words.
+__device__ __forceinline__ void block_scan_excl(uint32_t *c, uint32_t n, uint32_t *wsum) {
+  const uint32_t T = blockDim.x, per = (n + T - 1) / T, lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t b = threadIdx.x * per, W = T >> 5;
+  uint32_t v[4], sum = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < 4; ++i) {
+    v[i] = (i < per && b + i < n) ? c[b + i] : 0u;
+    sum += v[i];
+  }
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= uint32_t(o)) inc += y;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t t = lane < W ? wsum[lane] : 0u;
+    uint32_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= uint32_t(o)) ti += y;
+    }
+    if (lane < W) wsum[lane] = ti - t;
+  }
+  __syncthreads();
+  uint32_t run = wsum[warp] + inc - sum;
+#pragma unroll
+  for (uint32_t i = 0; i < 4; ++i)
+    if (i < per && b + i < n) {
+      c[b + i] = run;
+      run += v[i];
+    }
+  __syncthreads();
+}
+
+// Stable LSD radix sort of the L narrow keys in a (R-index << pbits | position,
+// in position order) by their R-index bits, 4 bits per pass; b is scratch of L
+// keys, tab kRadixTable counters, wsum 32 words.  Equal R-indices keep their
+// order, so the result is the keys' ascending order.  Round k of the block
+// takes keys k * T + t; a key's place is the count of keys before it in
+// (digit, round, warp, lane) order: its rank among its warp's equal digits
+// (match_any) plus the scanned counter of (digit, round, warp).  Returns the
+// array holding the sorted keys.
+__device__ unsigned long long *radix_narrow(unsigned long long *a, unsigned long long *b, uint32_t *tab,
+                                            uint32_t *wsum, uint32_t L, uint32_t pbits, uint32_t rbits) {
+  const uint32_t T = blockDim.x, W = T >> 5, K = (L + T - 1) / T;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
+  const uint32_t n = 16u * K * W;
+  for (uint32_t sh = pbits; sh < pbits + rbits; sh += 4) {
+    uint32_t dig[kRadixRounds], rank[kRadixRounds];
+    for (uint32_t i = threadIdx.x; i < n; i += T) tab[i] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRadixRounds; ++k) {
+      dig[k] = 16u;
+      rank[k] = 0;
+      if (uint32_t(k) < K) {  // block-uniform: every lane of a warp takes part in the match
+        const uint32_t e = uint32_t(k) * T + threadIdx.x;
+        const uint32_t d = e < L ? uint32_t(a[e] >> sh) & 15u : 16u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        dig[k] = d;
+        rank[k] = __popc(peers & lt);
+        if (d < 16u && (peers & lt) == 0) tab[(d * K + uint32_t(k)) * W + warp] = __popc(peers);
+      }
+    }
+    __syncthreads();
+    block_scan_excl(tab, n, wsum);
+#pragma unroll
+    for (int k = 0; k < kRadixRounds; ++k)
+      if (dig[k] < 16u) b[tab[(dig[k] * K + uint32_t(k)) * W + warp] + rank[k]] = a[uint32_t(k) * T + threadIdx.x];
+    __syncthreads();
+    unsigned long long *t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
 // Narrow keys of one sequence (P of them, a power of two, P <= E * blockDim)
 // sorted with bitonic_regs; the sorted keys end in sm[0 .. P).
 template <int E, typename C>
@@ -453,6 +543,10 @@ __global__ void __launch_bounds__(kSortThreads) k_ro_sort(const LeafRec *__restr
                                                           C *o0, C *o1, C *o2, uint32_t *oidx, uint32_t cap,
                                                           RoPlan *wplan, uint32_t *big_list) {
   extern __shared__ unsigned long long keys[];
+  // the radix passes: keys and scratch of rcap keys each, then their counters
+  const uint32_t rcap = cap < kRadixMax ? cap : kRadixMax;
+  uint32_t *const rtab = reinterpret_cast<uint32_t *>(keys + 2 * rcap);
+  uint32_t *const rwsum = rtab + kRadixTable;
   const int32_t order[3] = {plan->order[0], plan->order[1], plan->order[2]};
   for (uint64_t j = blockIdx.x; j < num_seq; j += gridDim.x) {
     const LeafRec r = recs[seq_at[j]];
@@ -470,16 +564,31 @@ __global__ void __launch_bounds__(kSortThreads) k_ro_sort(const LeafRec *__restr
     while (P < L) P <<= 1;
     const uint32_t pbits = pos_bits(r.cnt);
     if (narrow_keys(r)) {
-      // narrow keys: in registers (padded to a warp's worth at least), or all in shared memory
-      const uint32_t Pw = P < 32u * E ? 32u * E : P;
-      if (Pw <= E * blockDim.x)
-        sort_narrow<E, C>(r, Pw, pbits, order, q0, q1, q2, keys);
-      else
-        sort_narrow_smem<C>(r, P, pbits, order, q0, q1, q2, keys);
+      const unsigned long long *sorted = keys;
+      if (L >= kRadixMin && L <= rcap) {
+        // radix passes over the R-index bits
+        for (uint32_t e = threadIdx.x; e < L; e += blockDim.x) {
+          const uint32_t p = e < r.centre ? e : e + 1;
+          uint32_t q[3];
+          load_q(q0, q1, q2, uint64_t(r.off) + p, q);
+          unsigned long long h, l;
+          rkey(q, r, order, p, h, l);
+          keys[e] = (((h << 32) | (l >> 32)) << pbits) | p;
+        }
+        __syncthreads();
+        sorted = radix_narrow(keys, keys + rcap, rtab, rwsum, L, pbits, msum(r));
+      } else {
+        // narrow keys: in registers (padded to a warp's worth at least), or all in shared memory
+        const uint32_t Pw = P < 32u * E ? 32u * E : P;
+        if (Pw <= E * blockDim.x)
+          sort_narrow<E, C>(r, Pw, pbits, order, q0, q1, q2, keys);
+        else
+          sort_narrow_smem<C>(r, P, pbits, order, q0, q1, q2, keys);
+      }
       const unsigned long long pmask = (1ull << pbits) - 1;
       const uint32_t dst = off[j];
       for (uint32_t i = threadIdx.x; i <= L; i += blockDim.x) {
-        const uint32_t p = i == 0 ? r.centre : uint32_t(keys[i - 1] & pmask);
+        const uint32_t p = i == 0 ? r.centre : uint32_t(sorted[i - 1] & pmask);
         const uint64_t src = uint64_t(r.off) + p, d = uint64_t(dst) + i;
         o0[d] = q0[src];
         o1[d] = q1[src];
@@ -701,9 +810,12 @@ cudaError_t reorder_dispatch(const ReorderLaunch &a, cudaStream_t st) {
     // E keys per thread in registers: cap / E threads (a warp at least, 1024 at most), 4 keys below 2048,
     // 8 from there; shared memory for 8-byte keys up to cap and 16-byte keys up to kSmemWide
     const uint32_t c2 = cap < 256 ? 256 : cap;
-    const size_t smem = size_t(c2) * 8 > size_t(c2 < kSmemWide ? c2 : kSmemWide) * 16
-                            ? size_t(c2) * 8
-                            : size_t(c2 < kSmemWide ? c2 : kSmemWide) * 16;
+    size_t smem = size_t(c2) * 8 > size_t(c2 < kSmemWide ? c2 : kSmemWide) * 16
+                      ? size_t(c2) * 8
+                      : size_t(c2 < kSmemWide ? c2 : kSmemWide) * 16;
+    // the radix passes' keys, scratch and counters, when a sequence can take them
+    const size_t radix = size_t(c2 < kRadixMax ? c2 : kRadixMax) * 16 + 4 * (kRadixTable + 32);
+    if (c2 >= kRadixMin && radix > smem) smem = radix;
     const bool wide = cap >= 2048;
     const uint32_t tpc = cap / (wide ? 8 : 4);
     const int threads = int(tpc < 32 ? 32 : (tpc > uint32_t(kSortThreads) ? kSortThreads : tpc));
