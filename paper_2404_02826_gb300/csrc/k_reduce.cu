@@ -1002,6 +1002,29 @@ __global__ void k_rd_gather(State S, uint64_t n, const C *__restrict__ q0, const
   }
 }
 
+// A CUDA graph of launches captured from a private stream; destroyed with it.
+struct RoundGraph {
+  cudaGraphExec_t exec = nullptr;
+  template <typename Fn>
+  void capture(Fn issue) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      issue(cs);
+      if (cudaStreamEndCapture(cs, &g) == cudaSuccess && g) {
+        if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+        cudaGraphDestroy(g);
+      }
+    }
+    cudaStreamDestroy(cs);
+    (void)cudaGetLastError();  // a failed capture leaves the launches to be issued one by one
+  }
+  ~RoundGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 template <typename C>
 cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *num_seq, uint64_t *rounds) {
   const Layout L = layout_of(a.n, a.num_leaves);
@@ -1052,25 +1075,41 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
     TraceScope ts("k_rd_refit", st);
     k_rd_refit<<<refit_blocks, kThreads, 0, st>>>(S);
   }
-  uint64_t issued = 0;
-  for (;;) {
+  // kRoundsPerCheck rounds: the same launches with the same arguments every time
+  auto issue_rounds = [&](cudaStream_t s) {
     for (int k = 0; k < kRoundsPerCheck; ++k) {
       {
-        TraceScope ts("k_rd_select", st);
-        k_rd_select<<<select_blocks, kThreads, 0, st>>>(S);
+        TraceScope ts("k_rd_select", s);
+        k_rd_select<<<select_blocks, kThreads, 0, s>>>(S);
       }
       {
-        TraceScope ts("k_rd_take", st);
-        k_rd_take<C><<<take_blocks, kTakeThreads, 0, st>>>(S, q0, q1, q2);
+        TraceScope ts("k_rd_take", s);
+        k_rd_take<C><<<take_blocks, kTakeThreads, 0, s>>>(S, q0, q1, q2);
       }
       {
-        TraceScope ts("k_rd_scan", st);
-        k_rd_scan<<<1, 1024, 0, st>>>(S, a.seqs);
+        TraceScope ts("k_rd_scan", s);
+        k_rd_scan<<<1, 1024, 0, s>>>(S, a.seqs);
       }
       {
-        TraceScope ts("k_rd_rebuild", st);
-        k_rd_rebuild<C, false><<<box_blocks, kBoxThreads, 0, st>>>(S, q0, q1, q2, a.leafs);
+        TraceScope ts("k_rd_rebuild", s);
+        k_rd_rebuild<C, false><<<box_blocks, kBoxThreads, 0, s>>>(S, q0, q1, q2, a.leafs);
       }
+    }
+  };
+  // The rounds between two read-backs are captured once into a CUDA graph (on a
+  // private stream of this call, so that any stream, the legacy one included,
+  // can launch it) and launched once per read-back: one launch in place of
+  // 4 * kRoundsPerCheck.  Kernel tracing needs events around every launch, so
+  // with it on (or when the capture fails) the launches go one by one.
+  RoundGraph graph;
+  if (!trace_enabled()) graph.capture(issue_rounds);
+  uint64_t issued = 0;
+  for (;;) {
+    if (graph.exec) {
+      e = cudaGraphLaunch(graph.exec, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      issue_rounds(st);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -126,6 +126,7 @@ class TraceScope {
   void *a_, *b_;
 };
 void trace_flush();
+bool trace_enabled();  // whether kernel tracing is on (each launch then needs its own events)
 
 // ---- launchers (defined in the kernel translation units) -------------------
 

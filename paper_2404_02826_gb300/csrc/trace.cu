@@ -71,6 +71,11 @@ TraceScope::~TraceScope() {
   g_pending.push_back(Pending{name_, static_cast<cudaEvent_t>(a_), static_cast<cudaEvent_t>(b_)});
 }
 
+bool trace_enabled() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
+
 void trace_flush() {
   std::lock_guard<std::mutex> lk(g_mu);
   std::vector<Pending> keep;
