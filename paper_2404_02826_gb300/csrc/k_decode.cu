@@ -681,11 +681,13 @@ struct DecBatchSmem {
 
 // The batch's decoder for the streams of one kind: persistent blocks take the
 // kind's chunks k, k + G, ... as the single-stream decoder does; a chunk's
-// descriptor names its stream (written by the validation), and thread 0
-// refreshes what it keeps of a stream only when the stream changes.
+// descriptor names its stream (k_tag_chunks), and thread 0 refreshes what it
+// keeps of a stream only when the stream changes.  A staging area's record is
+// read only after its barrier completes (thread 0 writes it before arriving);
+// a wait that gives up sets the batch's own error word `berr`.
 template <typename T, bool FAST, bool VEC>
 __global__ void __launch_bounds__(kDecThreads, 5) k_decode_batch(const DecItem *items, const ChunkInfo *cinfo,
-                                                              uint64_t nchunks) {
+                                                              uint64_t nchunks, uint32_t *berr) {
   __shared__ __align__(16) DecBatchSmem S;
   uint64_t chunk = blockIdx.x;
   if (chunk >= nchunks) return;
@@ -733,7 +735,7 @@ __global__ void __launch_bounds__(kDecThreads, 5) k_decode_batch(const DecItem *
   __syncthreads();
   uint32_t ph0 = 0u, ph1 = 0u;
   for (int b = 0; chunk < nchunks; chunk += G, b ^= 1) {
-    const bool late = wait_buffer(&S.d.bar[b], b ? ph1 : ph0, S.meta[b].a->err);
+    const bool late = wait_buffer(&S.d.bar[b], b ? ph1 : ph0, berr);
     if (b) ph1 ^= 1u;
     else ph0 ^= 1u;
     const ChunkInfo ci = S.d.ci[b];
@@ -929,7 +931,8 @@ cudaError_t launch_dtable_batch(const DecItem *items, uint32_t count, cudaStream
 
 namespace {
 template <typename T, bool FAST, bool VEC>
-cudaError_t decode_batch_as(const DecItem *items, const void *chunks, uint64_t num_chunks, cudaStream_t st) {
+cudaError_t decode_batch_as(const DecItem *items, const void *chunks, uint64_t num_chunks, uint32_t *berr,
+                            cudaStream_t st) {
   int per_sm = 0;
   const cudaError_t e = resident_blocks<k_decode_batch<T, FAST, VEC>>(kDecThreads, 0, &per_sm);
   if (e != cudaSuccess) return e;
@@ -937,24 +940,24 @@ cudaError_t decode_batch_as(const DecItem *items, const void *chunks, uint64_t n
   if (grid > num_chunks) grid = num_chunks;
   TraceScope ts("k_decode", st);
   k_decode_batch<T, FAST, VEC><<<unsigned(grid), kDecThreads, 0, st>>>(items, static_cast<const ChunkInfo *>(chunks),
-                                                                       num_chunks);
+                                                                       num_chunks, berr);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_decode_batch(int kind, bool vec, const DecItem *items, const void *chunks, uint64_t num_chunks,
-                                cudaStream_t st) {
+                                uint32_t *berr, cudaStream_t st) {
   if (num_chunks == 0) return cudaSuccess;
   switch (kind) {
     case kDecKindF32Fast:
-      return vec ? decode_batch_as<float, true, true>(items, chunks, num_chunks, st)
-                 : decode_batch_as<float, true, false>(items, chunks, num_chunks, st);
+      return vec ? decode_batch_as<float, true, true>(items, chunks, num_chunks, berr, st)
+                 : decode_batch_as<float, true, false>(items, chunks, num_chunks, berr, st);
     case kDecKindF32:
-      return vec ? decode_batch_as<float, false, true>(items, chunks, num_chunks, st)
-                 : decode_batch_as<float, false, false>(items, chunks, num_chunks, st);
+      return vec ? decode_batch_as<float, false, true>(items, chunks, num_chunks, berr, st)
+                 : decode_batch_as<float, false, false>(items, chunks, num_chunks, berr, st);
     default:
-      return vec ? decode_batch_as<double, false, true>(items, chunks, num_chunks, st)
-                 : decode_batch_as<double, false, false>(items, chunks, num_chunks, st);
+      return vec ? decode_batch_as<double, false, true>(items, chunks, num_chunks, berr, st)
+                 : decode_batch_as<double, false, false>(items, chunks, num_chunks, berr, st);
   }
 }
 

@@ -197,7 +197,11 @@ __global__ void __launch_bounds__(kBoxThreads) k_leafbox(const C *__restrict__ q
   }
 }
 
-// The same bit box with one warp per leaf (small leaves).
+// The same bit box with one warp per leaf (small leaves).  The squared
+// distances of the centre search are formed in 32 bits when every side of the
+// box is below 2^15 codes (|2q - lo - hi| < 2^15, so the sum of three squares
+// stays below 2^32), else in 64; the next leaf's record is loaded while the
+// current one is worked.
 template <typename C>
 __global__ void __launch_bounds__(256) k_leafbox_warp(const C *__restrict__ q0, const C *__restrict__ q1,
                                                       const C *__restrict__ q2, LeafRec *recs, uint64_t num_leaves,
@@ -205,9 +209,12 @@ __global__ void __launch_bounds__(256) k_leafbox_warp(const C *__restrict__ q0, 
   if (call_failed(err)) return;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = uint64_t(gridDim.x) * 8;
-  for (uint64_t L = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5); L < num_leaves; L += warps) {
-    LeafRec rec = recs[L];
-    const uint32_t off = rec.off, cnt = rec.cnt;
+  uint64_t L = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+  uint4 nx = make_uint4(0u, 0u, 0u, 0u);  // offset and count of the next leaf (the record's first 16 bytes)
+  if (L < num_leaves) nx = *reinterpret_cast<const uint4 *>(recs + L);
+  for (; L < num_leaves; L += warps) {
+    const uint32_t off = nx.x, cnt = nx.y;
+    if (L + warps < num_leaves) nx = *reinterpret_cast<const uint4 *>(recs + L + warps);
     uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
     for (uint32_t i = lane; i < cnt; i += 32) {
       const uint32_t x[3] = {uint32_t(q0[off + i]), uint32_t(q1[off + i]), uint32_t(q2[off + i])};
@@ -223,27 +230,44 @@ __global__ void __launch_bounds__(256) k_leafbox_warp(const C *__restrict__ q0, 
       hi[d] = __reduce_max_sync(0xffffffffu, hi[d]);
     }
     // centre: least squared distance to the AABB centre, lowest position on ties
-    unsigned long long bd = ~0ull;
+    // (positions rise within a lane: the first minimum is the lowest)
     uint32_t bp = 0xffffffffu;
-    const long long s0 = (long long)lo[0] + hi[0], s1 = (long long)lo[1] + hi[1], s2 = (long long)lo[2] + hi[2];
-    for (uint32_t i = lane; i < cnt; i += 32) {
-      const long long a = 2ll * q0[off + i] - s0, b = 2ll * q1[off + i] - s1, c = 2ll * q2[off + i] - s2;
-      const unsigned long long d2 =
-          (unsigned long long)(a * a) + (unsigned long long)(b * b) + (unsigned long long)(c * c);
-      if (d2 < bd) {  // positions rise within a lane: the first minimum is the lowest
-        bd = d2;
-        bp = i;
+    if (max(hi[0] - lo[0], max(hi[1] - lo[1], hi[2] - lo[2])) < 32768u) {
+      const int s0 = int(lo[0] + hi[0]), s1 = int(lo[1] + hi[1]), s2 = int(lo[2] + hi[2]);
+      uint32_t md = 0xffffffffu, mp = 0xffffffffu;
+      for (uint32_t i = lane; i < cnt; i += 32) {
+        const int e0 = 2 * int(q0[off + i]) - s0, e1 = 2 * int(q1[off + i]) - s1, e2 = 2 * int(q2[off + i]) - s2;
+        const uint32_t d2 = uint32_t(e0 * e0) + uint32_t(e1 * e1) + uint32_t(e2 * e2);
+        if (d2 < md) {
+          md = d2;
+          mp = i;
+        }
       }
-    }
-    for (int o = 16; o; o >>= 1) {
-      const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
-      const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (od < bd || (od == bd && op < bp)) {
-        bd = od;
-        bp = op;
+      const uint32_t wmd = __reduce_min_sync(0xffffffffu, md);
+      bp = __reduce_min_sync(0xffffffffu, md == wmd ? mp : 0xffffffffu);
+    } else {
+      unsigned long long bd = ~0ull;
+      const long long s0 = (long long)lo[0] + hi[0], s1 = (long long)lo[1] + hi[1], s2 = (long long)lo[2] + hi[2];
+      for (uint32_t i = lane; i < cnt; i += 32) {
+        const long long a = 2ll * q0[off + i] - s0, b = 2ll * q1[off + i] - s1, c = 2ll * q2[off + i] - s2;
+        const unsigned long long d2 =
+            (unsigned long long)(a * a) + (unsigned long long)(b * b) + (unsigned long long)(c * c);
+        if (d2 < bd) {
+          bd = d2;
+          bp = i;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (od < bd || (od == bd && op < bp)) {
+          bd = od;
+          bp = op;
+        }
       }
     }
     if (lane == 0) {
+      LeafRec rec = recs[L];
       const uint32_t c = bp;
       const uint32_t qc[3] = {uint32_t(q0[off + c]), uint32_t(q1[off + c]), uint32_t(q2[off + c])};
       rec.centre = c;

@@ -164,8 +164,8 @@ int decode_batch_layout(const pc_decompress_item *items, uint32_t count, DecBatc
   o = align_up(o + 8ull * count);
   L.off_headers = o;
   o = align_up(o + uint64_t(PC_HEADER_BYTES) * count);
-  L.off_err = o;
-  o = align_up(o + 64ull * count);
+  L.off_err = o;  // 64 bytes per item, then the batch's own error word
+  o = align_up(o + 64ull * (count + 1));
   L.off_items = o;
   o = align_up(o + sizeof(pcx::DecItem) * count);
   L.off_leaf_start = o;
@@ -214,7 +214,8 @@ int decode_batch_run(pc_decompress_item *items, uint32_t count, const DecBatchLa
                                  ws + L.off_headers, st) != cudaSuccess ||
       cudaMemcpyAsync(headers.data(), ws + L.off_headers, headers.size(), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
-      cudaMemsetAsync(ws + L.off_err, 0, 64ull * count, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      cudaMemsetAsync(ws + L.off_err, 0, 64ull * (count + 1), st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return PC_ERR_CUDA;
 
   std::vector<pcx::DecItem> dev;  // the streams that decode, in item order
@@ -296,20 +297,22 @@ int decode_batch_run(pc_decompress_item *items, uint32_t count, const DecBatchLa
       pcx::launch_validate_batch(items_dev, leaf_dev, nd, leaves, st) != cudaSuccess ||
       pcx::launch_dtable_batch(items_dev, nd, st) != cudaSuccess)
     return PC_ERR_CUDA;
+  uint32_t *berr = reinterpret_cast<uint32_t *>(ws + L.off_err + 64ull * count);
   for (int k = 0; k < pcx::kDecKinds; ++k)
     if (pcx::launch_decode_batch(k, kind_vec[k], items_dev, ws + L.off_chunks + 32ull * kind_first[k],
-                                 kind_chunks[k], st) != cudaSuccess)
+                                 kind_chunks[k], berr, st) != cudaSuccess)
       return PC_ERR_CUDA;
   for (uint32_t j = 0; j < nd; ++j)
     if (kind[j] == pcx::kDecKinds && pcx::launch_decode_lossless(dev[j].a, st) != cudaSuccess) return PC_ERR_CUDA;
-  // every item's error word: one read-back
-  std::vector<uint32_t> errs(16ull * count);
-  if (cudaMemcpyAsync(errs.data(), ws + L.off_err, 64ull * count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  // every item's error word and the batch's: one read-back
+  std::vector<uint32_t> errs(16ull * (count + 1));
+  if (cudaMemcpyAsync(errs.data(), ws + L.off_err, 64ull * (count + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return PC_ERR_CUDA;
   pcx::trace_flush();
+  const uint32_t batch_err = errs[16ull * count];  // a wait gave up: no item's output can be trusted
   for (uint32_t j = 0; j < nd; ++j) {
-    const uint32_t e = errs[16ull * which[j]];
+    const uint32_t e = errs[16ull * which[j]] | batch_err;
     items[which[j]].status = (e & pcx::kErrCorrupt)   ? PC_ERR_CORRUPT
                              : (e & pcx::kErrTimeout) ? PC_ERR_TIMEOUT
                              : e                      ? PC_ERR_CUDA

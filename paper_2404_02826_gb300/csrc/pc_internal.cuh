@@ -297,9 +297,10 @@ cudaError_t launch_validate_batch(const DecItem *items, const uint64_t *leaf_sta
                                   cudaStream_t st);
 // Code tables of every stream that decodes through them.
 cudaError_t launch_dtable_batch(const DecItem *items, uint32_t count, cudaStream_t st);
-// Every chunk of one kind's streams, one persistent launch (chunks: that kind's descriptors).
+// Every chunk of one kind's streams, one persistent launch (chunks: that kind's descriptors);
+// berr: the batch's error word (a bounded wait that gave up).
 cudaError_t launch_decode_batch(int kind, bool vec, const DecItem *items, const void *chunks,
-                                uint64_t num_chunks, cudaStream_t st);
+                                uint64_t num_chunks, uint32_t *berr, cudaStream_t st);
 // A stream with lossless axes, decoded on its own after the batch's validation.
 cudaError_t launch_decode_lossless(const DecodeLaunch &a, cudaStream_t st);
 uint64_t decode_chunks(uint64_t n);
