@@ -397,16 +397,25 @@ __global__ void __launch_bounds__(256) k_scatter_node(LevelLaunch a) {
       *n2 = static_cast<C *>(a.dst[2]) + off;
     uint32_t *ni = IDX ? a.dst_idx + off : nullptr;
     uint32_t run_l = 0, run_t = 0;  // particles below v and equal to v before this round
+    // each round's codes are loaded one round ahead, so their latency overlaps the current round
+    C p0 = 0, p1 = 0, p2 = 0;
+    uint32_t pxi = 0;
+    if (lane < cnt) {
+      p0 = s0[off + lane];
+      p1 = s1[off + lane];
+      p2 = s2[off + lane];
+      if (IDX) pxi = a.src_idx[off + lane];
+    }
     for (uint32_t base = 0; base < cnt; base += 32) {
       const uint32_t i = base + lane;
       const bool valid = i < cnt;
-      C x0 = 0, x1 = 0, x2 = 0;
-      uint32_t xi = 0;
-      if (valid) {
-        x0 = s0[off + i];
-        x1 = s1[off + i];
-        x2 = s2[off + i];
-        if (IDX) xi = a.src_idx[off + i];
+      const C x0 = p0, x1 = p1, x2 = p2;
+      const uint32_t xi = pxi;
+      if (i + 32 < cnt) {
+        p0 = s0[off + i + 32];
+        p1 = s1[off + i + 32];
+        p2 = s2[off + i + 32];
+        if (IDX) pxi = a.src_idx[off + i + 32];
       }
       const uint32_t q = ax == 0 ? x0 : (ax == 1 ? x1 : x2);
       const bool isless = valid && q < v, istie = valid && q == v;
