@@ -65,6 +65,24 @@ struct SubMisc {
   uint32_t fb[kWarps], fbefore[kWarps];
 };
 
+// Warps per leaf in the leaf phase: kWarps >> lgwl slots of 2^lgwl warps;
+// more leaves than warps: a warp per leaf, in turns.
+struct LeafSlots {
+  uint32_t lgwl, WL, slots, lw, lt, lstep;
+};
+__device__ __forceinline__ LeafSlots leaf_slots(uint32_t nl, int warp, int lane) {
+  LeafSlots q;
+  uint32_t lgwl = kLgWarps;
+  while (lgwl > 0 && (uint32_t(kWarps) >> lgwl) < nl) --lgwl;
+  q.lgwl = lgwl;
+  q.WL = 1u << lgwl;
+  q.slots = uint32_t(kWarps) >> lgwl;
+  q.lw = uint32_t(warp) & (q.WL - 1u);  // warp within its leaf group
+  q.lt = q.lw * 32 + uint32_t(lane);
+  q.lstep = q.WL * 32;
+  return q;
+}
+
 __host__ __device__ constexpr uint32_t al128(uint32_t x) { return (x + 127u) & ~127u; }
 
 // Shared-memory layout of one CTA: the code arrays of a node of up to
@@ -239,7 +257,11 @@ __device__ __forceinline__ void load_rows(const E *A, uint32_t nv, uint32_t Tg, 
   }
 }
 
-template <typename C, bool IDX, bool WIDEST>
+// COST: the leaf-size search's pass.  Every subnode splits at every level;
+// before the first level and after each one the leaves at that depth get their
+// bit boxes, and their payload words are added to cost_words[level]; nothing
+// is written to the stream.
+template <typename C, bool IDX, bool WIDEST, bool COST>
 __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
   using L = SubL<C, IDX>;
   constexpr int R = L::R;
@@ -322,7 +344,7 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
   // it, and the CTA leaves.
   const bool late = wait_buffer(&M.bar, 0, a.err);
   if (__syncthreads_or(late || M.skip != 0u)) {
-    if (threadIdx.x == 0) st_release_u64(a.status + M.j, kStIncl);
+    if (!COST && threadIdx.x == 0) st_release_u64(a.status + M.j, kStIncl);
     tmem_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -348,6 +370,165 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
     if (IDX) load_rows<R>(XI, nv0, kT, threadIdx.x, tcol + 3 * NC);
     tmem_wait_st();
   }
+  const C *const Y0 = X0, *const Y1 = X0 + S, *const Y2 = X0 + 2 * S;
+  // Leaves below the subnodes cur[0..G): the two halves of a splitting subnode
+  // (with `halves`), else the subnode itself; their AABBs, centres (first
+  // position on ties), widths (Eq. 2) and payload words, in LF.  Returns
+  // their number.  Every thread calls it.
+  auto leaf_boxes = [&](uint32_t G, bool halves) -> uint32_t {
+    if (threadIdx.x == 0) {
+      uint32_t nl = 0;
+      for (uint32_t t = 0; t < G; ++t) {
+        const SubNode &u = cur[t];
+        if (halves && u.split) {
+          const uint32_t kk = u.cnt >> 1;
+          LF[nl].off = u.off;
+          LF[nl++].cnt = kk;
+          LF[nl].off = u.off + kk;
+          LF[nl++].cnt = u.cnt - kk;
+        } else {
+          LF[nl].off = u.off;
+          LF[nl++].cnt = u.cnt;
+        }
+      }
+      M.nl = nl;
+    }
+    __syncthreads();
+    const uint32_t nl = M.nl;
+    if (threadIdx.x < nl) {
+      for (int d = 0; d < 3; ++d) {
+        LF[threadIdx.x].lo[d] = 0xffffffffu;
+        LF[threadIdx.x].hi[d] = 0;
+      }
+    }
+    const LeafSlots q = leaf_slots(nl, warp, lane);
+    const uint32_t lgwl = q.lgwl, WL = q.WL, slots = q.slots, lt = q.lt, lstep = q.lstep;
+    __syncthreads();
+    // bit boxes: AABB
+    for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots) {
+      const uint32_t off = LF[f].off, cnt = LF[f].cnt;
+      uint32_t mn0 = 0xffffffffu, mn1 = 0xffffffffu, mn2 = 0xffffffffu, mx0 = 0, mx1 = 0, mx2 = 0;
+      for (uint32_t i = lt; i < cnt; i += lstep) {
+        const uint32_t c0 = Y0[off + i], c1 = Y1[off + i], c2 = Y2[off + i];
+        mn0 = min(mn0, c0);
+        mx0 = max(mx0, c0);
+        mn1 = min(mn1, c1);
+        mx1 = max(mx1, c1);
+        mn2 = min(mn2, c2);
+        mx2 = max(mx2, c2);
+      }
+      mn0 = __reduce_min_sync(0xffffffffu, mn0);
+      mn1 = __reduce_min_sync(0xffffffffu, mn1);
+      mn2 = __reduce_min_sync(0xffffffffu, mn2);
+      mx0 = __reduce_max_sync(0xffffffffu, mx0);
+      mx1 = __reduce_max_sync(0xffffffffu, mx1);
+      mx2 = __reduce_max_sync(0xffffffffu, mx2);
+      if (lane == 0) {
+        atomicMin(&LF[f].lo[0], mn0);
+        atomicMin(&LF[f].lo[1], mn1);
+        atomicMin(&LF[f].lo[2], mn2);
+        atomicMax(&LF[f].hi[0], mx0);
+        atomicMax(&LF[f].hi[1], mx1);
+        atomicMax(&LF[f].hi[2], mx2);
+      }
+    }
+    __syncthreads();
+    // centre: least squared distance to the AABB centre, first position on ties.
+    // When every side of the box is below 2^15 codes, |2q - lo - hi| < 2^15 and
+    // the squared distance is exact in 32 bits; otherwise it is formed in 64.
+    {
+      int it = 0;
+      for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots, ++it) {
+        const uint32_t off = LF[f].off, cnt = LF[f].cnt;
+        const uint32_t l0 = LF[f].lo[0], l1 = LF[f].lo[1], l2 = LF[f].lo[2];
+        const uint32_t u0 = LF[f].hi[0], u1 = LF[f].hi[1], u2 = LF[f].hi[2];
+        unsigned long long bd;
+        uint32_t bp;
+        if (max(u0 - l0, max(u1 - l1, u2 - l2)) < 32768u) {
+          const int s0 = int(l0 + u0), s1 = int(l1 + u1), s2 = int(l2 + u2);
+          uint32_t md = 0xffffffffu, mp = 0xffffffffu;
+          for (uint32_t i = lt; i < cnt; i += lstep) {
+            const int e0 = 2 * int(Y0[off + i]) - s0, e1 = 2 * int(Y1[off + i]) - s1, e2 = 2 * int(Y2[off + i]) - s2;
+            const uint32_t d2 = uint32_t(e0 * e0) + uint32_t(e1 * e1) + uint32_t(e2 * e2);
+            if (d2 < md) {  // positions rise within a thread: the first minimum is the lowest
+              md = d2;
+              mp = i;
+            }
+          }
+          const uint32_t wmd = __reduce_min_sync(0xffffffffu, md);
+          bp = __reduce_min_sync(0xffffffffu, md == wmd ? mp : 0xffffffffu);
+          bd = wmd;
+        } else {
+          const long long s0 = (long long)l0 + u0, s1 = (long long)l1 + u1, s2 = (long long)l2 + u2;
+          bd = ~0ull;
+          bp = 0xffffffffu;
+          for (uint32_t i = lt; i < cnt; i += lstep) {
+            const long long e0 = 2ll * Y0[off + i] - s0, e1 = 2ll * Y1[off + i] - s1, e2 = 2ll * Y2[off + i] - s2;
+            const unsigned long long d2 =
+                (unsigned long long)(e0 * e0) + (unsigned long long)(e1 * e1) + (unsigned long long)(e2 * e2);
+            if (d2 < bd) {
+              bd = d2;
+              bp = i;
+            }
+          }
+  #pragma unroll
+          for (int o = 16; o; o >>= 1) {
+            const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+            const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+            if (od < bd || (od == bd && op < bp)) {
+              bd = od;
+              bp = op;
+            }
+          }
+        }
+        if (lane == 0) {
+          M.wd[warp][it] = bd;
+          M.wp[warp][it] = bp;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nl) {
+      const uint32_t f = threadIdx.x;
+      unsigned long long bd = ~0ull;
+      uint32_t bp = 0xffffffffu;
+      const bool turns = nl > uint32_t(kWarps);
+      const uint32_t w0 = turns ? (f % kWarps) : (f << lgwl), wn = turns ? 1u : WL, it = turns ? (f / kWarps) : 0u;
+      for (uint32_t w = w0; w < w0 + wn; ++w) {
+        const unsigned long long od = M.wd[w][it];
+        const uint32_t op = M.wp[w][it];
+        if (od < bd || (od == bd && op < bp)) {
+          bd = od;
+          bp = op;
+        }
+      }
+      SubLeaf &lf = LF[f];
+      const uint32_t c = bp < lf.cnt ? bp : 0u;
+      const uint32_t q0 = Y0[lf.off + c], q1 = Y1[lf.off + c], q2 = Y2[lf.off + c];
+      const uint32_t m0 = bits_for_range(max(q0 - lf.lo[0], lf.hi[0] - q0));
+      const uint32_t m1 = bits_for_range(max(q1 - lf.lo[1], lf.hi[1] - q1));
+      const uint32_t m2 = bits_for_range(max(q2 - lf.lo[2], lf.hi[2] - q2));
+      lf.qref[0] = int32_t(q0);
+      lf.qref[1] = int32_t(q1);
+      lf.qref[2] = int32_t(q2);
+      lf.centre = c;
+      lf.m = m0 | (m1 << 8) | (m2 << 16);
+      lf.words = uint32_t((uint64_t(m0 + m1 + m2) * (lf.cnt ? lf.cnt - 1 : 0) + 31) >> 5);
+    }
+    __syncthreads();
+    return nl;
+  };
+  // the leaf-size search: payload words of the leaves at in-CTA depth k
+  auto add_cost = [&](uint32_t nl, int k) {
+    if (warp == 0) {
+      unsigned long long w = 0;
+      for (uint32_t f = lane; f < nl; f += 32) w += LF[f].words;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (lane == 0) atomicAdd(a.cost_words + k, w);
+    }
+  };
+  if (COST) add_cost(leaf_boxes(1, false), 0);  // the node itself as one leaf
   for (int k = 0; k < a.levels; ++k) {
     const int lgW = kLgWarps - k;  // log2 of the warps per group
     const uint32_t G = 1u << k;
@@ -580,6 +761,7 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
       cr.split = cr.cnt > a.leaf_size;
     }
     __syncthreads();  // the level's arrangement is complete in shared memory
+    if (COST) add_cost(leaf_boxes(G, true), k + 1);
     if (k + 1 < a.levels) {
       SubNode *t = cur;
       cur = nxt;
@@ -598,154 +780,31 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
     }
   }
 
+  if (COST) {
+    // the search pass: the deepest in-CTA arrangement back to HBM when asked
+    // (a deeper search continues there); no leaf records, look-back or packing
+    if (a.wb_codes[0]) {
+      const uint64_t o = M.off;
+      const uint32_t cnt = uint32_t(M.cnt);
+      for (uint32_t i = threadIdx.x; i < cnt; i += kT) {
+        static_cast<C *>(a.wb_codes[0])[o + i] = X0[i];
+        static_cast<C *>(a.wb_codes[1])[o + i] = X0[S + i];
+        static_cast<C *>(a.wb_codes[2])[o + i] = X0[2 * S + i];
+        if (IDX) a.wb_idx[o + i] = XI[i];
+      }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tmem_fence_after();
+      tmem_dealloc(M.tmem, kTmemCols);
+    }
+    return;
+  }
   // ---- leaves: the last level's subnodes, split or not, in order ----
-  if (threadIdx.x == 0) {
-    const uint32_t G = a.levels > 0 ? 1u << (a.levels - 1) : 1u;
-    uint32_t nl = 0;
-    for (uint32_t t = 0; t < G; ++t) {
-      const SubNode &u = cur[t];
-      if (u.split) {
-        const uint32_t kk = u.cnt >> 1;
-        LF[nl].off = u.off;
-        LF[nl++].cnt = kk;
-        LF[nl].off = u.off + kk;
-        LF[nl++].cnt = u.cnt - kk;
-      } else {
-        LF[nl].off = u.off;
-        LF[nl++].cnt = u.cnt;
-      }
-    }
-    M.nl = nl;
-  }
-  __syncthreads();
-  const uint32_t nl = M.nl;
-  if (threadIdx.x < nl) {
-    for (int d = 0; d < 3; ++d) {
-      LF[threadIdx.x].lo[d] = 0xffffffffu;
-      LF[threadIdx.x].hi[d] = 0;
-    }
-  }
-  // kWarps >> lgwl leaf slots of 2^lgwl warps; more leaves than warps: a warp per leaf, in turns
-  uint32_t lgwl = kLgWarps;
-  while (lgwl > 0 && (uint32_t(kWarps) >> lgwl) < nl) --lgwl;
-  const uint32_t WL = 1u << lgwl, slots = uint32_t(kWarps) >> lgwl;
-  const uint32_t lw = uint32_t(warp) & (WL - 1u);  // warp within its leaf group
-  const uint32_t lt = lw * 32 + lane, lstep = WL * 32;
-  const C *const Y0 = X0, *const Y1 = X0 + L::kCodeStride / sizeof(C), *const Y2 = X0 + 2 * (L::kCodeStride / sizeof(C));
-  __syncthreads();
-  // bit boxes: AABB
-  for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots) {
-    const uint32_t off = LF[f].off, cnt = LF[f].cnt;
-    uint32_t mn0 = 0xffffffffu, mn1 = 0xffffffffu, mn2 = 0xffffffffu, mx0 = 0, mx1 = 0, mx2 = 0;
-    for (uint32_t i = lt; i < cnt; i += lstep) {
-      const uint32_t c0 = Y0[off + i], c1 = Y1[off + i], c2 = Y2[off + i];
-      mn0 = min(mn0, c0);
-      mx0 = max(mx0, c0);
-      mn1 = min(mn1, c1);
-      mx1 = max(mx1, c1);
-      mn2 = min(mn2, c2);
-      mx2 = max(mx2, c2);
-    }
-    mn0 = __reduce_min_sync(0xffffffffu, mn0);
-    mn1 = __reduce_min_sync(0xffffffffu, mn1);
-    mn2 = __reduce_min_sync(0xffffffffu, mn2);
-    mx0 = __reduce_max_sync(0xffffffffu, mx0);
-    mx1 = __reduce_max_sync(0xffffffffu, mx1);
-    mx2 = __reduce_max_sync(0xffffffffu, mx2);
-    if (lane == 0) {
-      atomicMin(&LF[f].lo[0], mn0);
-      atomicMin(&LF[f].lo[1], mn1);
-      atomicMin(&LF[f].lo[2], mn2);
-      atomicMax(&LF[f].hi[0], mx0);
-      atomicMax(&LF[f].hi[1], mx1);
-      atomicMax(&LF[f].hi[2], mx2);
-    }
-  }
-  __syncthreads();
-  // centre: least squared distance to the AABB centre, first position on ties.
-  // When every side of the box is below 2^15 codes, |2q - lo - hi| < 2^15 and
-  // the squared distance is exact in 32 bits; otherwise it is formed in 64.
-  {
-    int it = 0;
-    for (uint32_t f = uint32_t(warp) >> lgwl; f < nl; f += slots, ++it) {
-      const uint32_t off = LF[f].off, cnt = LF[f].cnt;
-      const uint32_t l0 = LF[f].lo[0], l1 = LF[f].lo[1], l2 = LF[f].lo[2];
-      const uint32_t u0 = LF[f].hi[0], u1 = LF[f].hi[1], u2 = LF[f].hi[2];
-      unsigned long long bd;
-      uint32_t bp;
-      if (max(u0 - l0, max(u1 - l1, u2 - l2)) < 32768u) {
-        const int s0 = int(l0 + u0), s1 = int(l1 + u1), s2 = int(l2 + u2);
-        uint32_t md = 0xffffffffu, mp = 0xffffffffu;
-        for (uint32_t i = lt; i < cnt; i += lstep) {
-          const int e0 = 2 * int(Y0[off + i]) - s0, e1 = 2 * int(Y1[off + i]) - s1, e2 = 2 * int(Y2[off + i]) - s2;
-          const uint32_t d2 = uint32_t(e0 * e0) + uint32_t(e1 * e1) + uint32_t(e2 * e2);
-          if (d2 < md) {  // positions rise within a thread: the first minimum is the lowest
-            md = d2;
-            mp = i;
-          }
-        }
-        const uint32_t wmd = __reduce_min_sync(0xffffffffu, md);
-        bp = __reduce_min_sync(0xffffffffu, md == wmd ? mp : 0xffffffffu);
-        bd = wmd;
-      } else {
-        const long long s0 = (long long)l0 + u0, s1 = (long long)l1 + u1, s2 = (long long)l2 + u2;
-        bd = ~0ull;
-        bp = 0xffffffffu;
-        for (uint32_t i = lt; i < cnt; i += lstep) {
-          const long long e0 = 2ll * Y0[off + i] - s0, e1 = 2ll * Y1[off + i] - s1, e2 = 2ll * Y2[off + i] - s2;
-          const unsigned long long d2 =
-              (unsigned long long)(e0 * e0) + (unsigned long long)(e1 * e1) + (unsigned long long)(e2 * e2);
-          if (d2 < bd) {
-            bd = d2;
-            bp = i;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-          const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
-          const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
-          if (od < bd || (od == bd && op < bp)) {
-            bd = od;
-            bp = op;
-          }
-        }
-      }
-      if (lane == 0) {
-        M.wd[warp][it] = bd;
-        M.wp[warp][it] = bp;
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < nl) {
-    const uint32_t f = threadIdx.x;
-    unsigned long long bd = ~0ull;
-    uint32_t bp = 0xffffffffu;
-    const bool turns = nl > uint32_t(kWarps);
-    const uint32_t w0 = turns ? (f % kWarps) : (f << lgwl), wn = turns ? 1u : WL, it = turns ? (f / kWarps) : 0u;
-    for (uint32_t w = w0; w < w0 + wn; ++w) {
-      const unsigned long long od = M.wd[w][it];
-      const uint32_t op = M.wp[w][it];
-      if (od < bd || (od == bd && op < bp)) {
-        bd = od;
-        bp = op;
-      }
-    }
-    SubLeaf &lf = LF[f];
-    const uint32_t c = bp < lf.cnt ? bp : 0u;
-    const uint32_t q0 = Y0[lf.off + c], q1 = Y1[lf.off + c], q2 = Y2[lf.off + c];
-    const uint32_t m0 = bits_for_range(max(q0 - lf.lo[0], lf.hi[0] - q0));
-    const uint32_t m1 = bits_for_range(max(q1 - lf.lo[1], lf.hi[1] - q1));
-    const uint32_t m2 = bits_for_range(max(q2 - lf.lo[2], lf.hi[2] - q2));
-    lf.qref[0] = int32_t(q0);
-    lf.qref[1] = int32_t(q1);
-    lf.qref[2] = int32_t(q2);
-    lf.centre = c;
-    lf.m = m0 | (m1 << 8) | (m2 << 16);
-    lf.words = uint32_t((uint64_t(m0 + m1 + m2) * (lf.cnt ? lf.cnt - 1 : 0) + 31) >> 5);
-  }
-  __syncthreads();
-
+  const uint32_t nl = leaf_boxes(a.levels > 0 ? 1u << (a.levels - 1) : 1u, true);
+  const LeafSlots q = leaf_slots(nl, warp, lane);
+  const uint32_t lgwl = q.lgwl, WL = q.WL, slots = q.slots, lw = q.lw, lt = q.lt, lstep = q.lstep;
   // ---- payload words before this node: decoupled look-back ----
   const uint32_t j = M.j;
   if (warp == 0) {
@@ -895,16 +954,20 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
   }
 }
 
-template <typename C, bool IDX, bool WIDEST>
-cudaError_t subtree_launch(const SubtreeLaunch &a, cudaStream_t st) {
+template <typename C, bool IDX, bool WIDEST, bool COST>
+cudaError_t subtree_launch_as(const SubtreeLaunch &a, cudaStream_t st) {
   const uint32_t smem = SubL<C, IDX>::kTotal;
   int per_sm = 0;
-  cudaError_t e = resident_blocks<k_subtree<C, IDX, WIDEST>>(kT, smem, &per_sm);
+  cudaError_t e = resident_blocks<k_subtree<C, IDX, WIDEST, COST>>(kT, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  TraceScope ts("k_subtree", st);
-  k_subtree<C, IDX, WIDEST><<<unsigned(1ull << a.depth), kT, smem, st>>>(a);
+  TraceScope ts(COST ? "k_subtree_cost" : "k_subtree", st);
+  k_subtree<C, IDX, WIDEST, COST><<<unsigned(1ull << a.depth), kT, smem, st>>>(a);
   return cudaGetLastError();
+}
+template <typename C, bool IDX, bool WIDEST>
+cudaError_t subtree_launch(const SubtreeLaunch &a, cudaStream_t st) {
+  return a.cost_words ? subtree_launch_as<C, IDX, WIDEST, true>(a, st) : subtree_launch_as<C, IDX, WIDEST, false>(a, st);
 }
 
 }  // namespace

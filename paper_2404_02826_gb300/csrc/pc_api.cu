@@ -88,6 +88,7 @@ struct Plan {
   bool tune = false;  // leaf size chosen by descending from r_hi while the stream shrinks (sized for r)
   uint32_t r_hi = 0;
   int tune_first = 0, tune_last = 0;  // candidate depths
+  uint64_t off_tunecost = 0;          // leaf-size search: payload words per in-CTA depth (zeroed)
   uint64_t total = 0;
   int range_blocks = 0;
 };
@@ -118,6 +119,20 @@ int subtree_depth(uint64_t n, uint32_t r, int levels, int code_bytes, bool idx, 
   int d = lo;
   if (d < want) d = want < hi ? want : hi;
   if (d > kSubMaxDepth) d = kSubMaxDepth;
+  return d;
+}
+
+// Root depth of the leaf-size search's on-chip pass: the shallowest depth whose
+// nodes fit a CTA (the pass is efficient on large nodes), below the deepest
+// candidate, within the look-back room of the packing pass (2^(tune_last - 1)
+// words), and reaching a candidate within kSubMaxLevels levels.  -1: the
+// search stays on the levels over HBM.
+int tune_subtree_depth(uint64_t n, int tune_first, int tune_last, int code_bytes, bool idx) {
+  if (n == 0 || tune_last < 1) return -1;
+  const uint64_t cap = subtree_capacity(code_bytes, idx);
+  int d = 0;
+  while (d < tune_last && ((n + (1ull << d) - 1) >> d) > cap) ++d;
+  if (d >= tune_last || d > kSubMaxDepth || d + kSubMaxLevels < tune_first) return -1;
   return d;
 }
 
@@ -256,8 +271,10 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   o = align_up(o + 4 * (hist_bins ? hist_bins : 1));
   p.off_tiles = o;
   o = align_up(o + 8 * (tiles ? tiles : 1));
-  p.off_tickets = o;
-  o = align_up(o + 4 * (p.levels + 1));
+  p.off_tickets = o;  // one per level over HBM, the subtree's, the leaf-size search pass's
+  o = align_up(o + 4 * (p.levels + 2));
+  p.off_tunecost = o;
+  o = align_up(o + 8 * (kSubMaxLevels + 1));
   p.off_status = o;
   o = align_up(o + 8 * subtree_status_entries(p.levels));
   p.off_err = o;
@@ -480,7 +497,13 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     const int sub_depth = (p.tune || p.reduce || p.reorder || sweep || L.raw)
                               ? -1
                               : subtree_depth(n, p.r, p.levels, cb, use_idx, device_sm_count());
-    const int global_levels = sub_depth >= 0 ? sub_depth : levels;
+    // the leaf-size search over the plain stream: levels over HBM down to tune_depth, then
+    // the candidates below it costed on chip (the depth-mod-3 rule: a resumed level takes the
+    // root's cell, which the widest-cell rule could not)
+    const int tune_depth = (p.tune && !p.reduce && !p.reorder && !p.widest && !sweep && !L.raw)
+                               ? tune_subtree_depth(n, p.tune_first, p.tune_last, cb, use_idx)
+                               : -1;
+    const int global_levels = sub_depth >= 0 ? sub_depth : (tune_depth >= 0 ? tune_depth : levels);
     // a4-a5 on the arrangement at depth `depth` (leaves = its 2^depth nodes when split_level = depth - 1)
     auto leaf_launch = [&](void *const *codes, const uint32_t *idxs, int split_level, uint32_t r,
                            uint64_t num_leaves, bool cost_only, bool box_only = false) {
@@ -587,23 +610,12 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     uint64_t best_bytes = 0;    // stream bytes (without header) at the shallower candidate
     const int first_depth = p.tune_first;
     LevelNode *nodes = reinterpret_cast<LevelNode *>(ws + p.off_nodes);
-    uint64_t node_base = 0, tile_base = 0;
     void **src = codes_a, **dst = codes_b;
     uint32_t *isrc = idx_a, *idst = idx_b;
-    for (int l = 0; l < global_levels; ++l) {
-      if (p.tune && l >= first_depth) {
-        // src holds the arrangement at depth l, dst the one at depth l - 1
-        uint64_t bytes = 0;
-        rc = depth_cost(src, l, &bytes);
-        if (rc) return rc;
-        if (sweep) {
-          record(l, bytes);
-        } else if (l > first_depth && bytes >= best_bytes) {
-          chosen = l - 1;
-          break;
-        }
-        best_bytes = bytes;
-      }
+    int src_depth = 0;  // the depth of the arrangement in src; dst holds the one above
+    // level l over HBM: splits the arrangement in src into dst, then swaps them
+    // (no parents' records: every node takes the root's cell)
+    auto global_level = [&](int l, bool no_parents) -> int {
       LevelLaunch la = {};
       la.n = n;
       la.level = l;
@@ -626,8 +638,11 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       }
       la.src_idx = isrc;
       la.dst_idx = idst;
+      const uint64_t node_base = (1ull << l) - 1;  // the records of the levels above come first
       la.nodes = nodes + node_base;
-      la.parents = l > 0 ? nodes + node_base - (1ull << (l - 1)) : nullptr;
+      la.parents = (l > 0 && !no_parents) ? nodes + node_base - (1ull << (l - 1)) : nullptr;
+      uint64_t tile_base = 0;
+      for (int k = 0; k < l; ++k) tile_base += (1ull << k) * tiles_per_node(n, k, scatter_tile(cb, use_idx));
       la.hist = reinterpret_cast<uint32_t *>(ws + p.off_hist);
       la.tile_state = reinterpret_cast<unsigned long long *>(ws + p.off_tiles) + tile_base;
       la.groups = ws + p.off_groups;
@@ -637,14 +652,36 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.drop_copies = t_drop_tile_copies;
       la.wait_limit = t_drop_tile_copies ? kSelftestSpinLimit : kBarSpinLimit;
       PC_TRY(launch_level(la, st));
-      node_base += 1ull << l;
-      tile_base += (1ull << l) * la.tiles_per_node;
       void **t = src;
       src = dst;
       dst = t;
       uint32_t *ti = isrc;
       isrc = idst;
       idst = ti;
+      src_depth = l + 1;
+      return PC_OK;
+    };
+    // a candidate depth's stream size against the shallower one (the arrangement at
+    // depth l in src): the search stops at the first depth whose stream is not smaller
+    auto judge = [&](int l, uint64_t bytes) {
+      if (l > first_depth && bytes >= best_bytes) chosen = l - 1;
+      else best_bytes = bytes;
+    };
+    for (int l = 0; l < global_levels; ++l) {
+      if (p.tune && l >= first_depth) {
+        uint64_t bytes = 0;
+        rc = depth_cost(src, l, &bytes);
+        if (rc) return rc;
+        if (sweep) {
+          record(l, bytes);
+          best_bytes = bytes;
+        } else {
+          judge(l, bytes);
+          if (chosen >= 0) break;
+        }
+      }
+      rc = global_level(l, false);
+      if (rc) return rc;
     }
 
     if (sweep) {
@@ -694,32 +731,37 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       return pack_ready(reinterpret_cast<LeafRec *>(ws + p.off_leafrec), num_leaves, codes, idxs, spare, spare_idx,
                         r);
     };
-    // a4-a5: bit boxes, payload offsets, packing
-    if (sub_depth >= 0) {
+    // the on-chip subtree over the arrangement at `depth` (in src): `lv` levels
+    // inside a CTA, leaves of at most r particles
+    auto subtree_at = [&](int depth, int lv, uint32_t r, uint64_t num_leaves) {
       SubtreeLaunch sa = {};
       sa.n = n;
-      sa.depth = sub_depth;
-      sa.levels = p.levels - sub_depth;
+      sa.depth = depth;
+      sa.levels = lv;
       sa.code_bytes = cb;
-      sa.leaf_size = p.r;
+      sa.leaf_size = r;
       sa.widest = p.widest;
       for (int d = 0; d < 3; ++d) {
         sa.root_hi[d] = L.qmax[d];
         sa.codes[d] = src[d];
       }
-      sa.parents = sub_depth > 0 ? nodes + ((1ull << (sub_depth - 1)) - 1) : nullptr;
+      sa.parents = depth > 0 ? nodes + ((1ull << (depth - 1)) - 1) : nullptr;
       sa.idx = isrc;
       sa.out = static_cast<uint8_t *>(out);
       sa.perm = perm;
-      sa.num_leaves = p.num_leaves;
-      sa.leaves_small = leaves_for(n >> sub_depth, p.r);
-      sa.leaves_big = leaves_for((n >> sub_depth) + 1, p.r);
+      sa.num_leaves = num_leaves;
+      sa.leaves_small = leaves_for(n >> depth, r);
+      sa.leaves_big = leaves_for((n >> depth) + 1, r);
       sa.status = reinterpret_cast<unsigned long long *>(ws + p.off_status);
       sa.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + p.levels;
       sa.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);
-      sa.payload_cap = payload_words(out_capacity, p.num_leaves);
+      sa.payload_cap = payload_words(out_capacity, num_leaves);
       sa.err = err;
-      PC_TRY(launch_subtree(sa, st));
+      return sa;
+    };
+    // a4-a5: bit boxes, payload offsets, packing
+    if (sub_depth >= 0) {
+      PC_TRY(launch_subtree(subtree_at(sub_depth, p.levels - sub_depth, p.r, p.num_leaves), st));
     } else if (!p.tune) {
       if (p.reduce) {
         rc = reduce_launch(src, isrc, dst, idst, levels - 1, p.r, p.num_leaves);
@@ -731,34 +773,97 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
         PC_TRY(leaf_launch(src, isrc, levels - 1, p.r, p.num_leaves, false));
       }
     } else {
-      // the loop stopped at the first depth whose stream is not smaller, or built
-      // every level: then the smallest candidate (depth `levels`, in src) is compared too
-      if (chosen < 0) {
-        chosen = levels;
+      bool packed = false;  // the chosen leaves were packed on chip
+      if (chosen < 0 && tune_depth >= 0) {
+        const int D = tune_depth;
+        const int K = p.tune_last - D < kSubMaxLevels ? p.tune_last - D : kSubMaxLevels;
+        // depth D itself: the last candidate judged on the levels over HBM (in src)
+        if (D >= first_depth) {
+          uint64_t bytes = 0;
+          rc = depth_cost(src, D, &bytes);
+          if (rc) return rc;
+          judge(D, bytes);
+        }
+        if (chosen < 0) {
+          // depths D + 1 .. D + K costed in one pass over the depth-D nodes, read back once;
+          // when the search goes deeper the pass leaves depth D + K's arrangement in dst
+          const bool deeper = D + K < p.tune_last;
+          unsigned long long *cw = reinterpret_cast<unsigned long long *>(ws + p.off_tunecost);
+          SubtreeLaunch ca = subtree_at(D, K, uint32_t((n + (1ull << (D + K)) - 1) >> (D + K)), 1ull << (D + K));
+          ca.cost_words = cw;
+          ca.ticket = reinterpret_cast<uint32_t *>(ws + p.off_tickets) + p.levels + 1;
+          if (deeper) {
+            for (int d = 0; d < 3; ++d) ca.wb_codes[d] = dst[d];
+            ca.wb_idx = idst;
+          }
+          PC_TRY(launch_subtree(ca, st));
+          unsigned long long words[kSubMaxLevels + 1] = {};
+          PC_TRY(cudaMemcpyAsync(words, cw, 8ull * (K + 1), cudaMemcpyDeviceToHost, st));
+          const int failed = error_so_far();
+          if (failed) return failed;
+          for (int d = D + 1; d <= D + K && chosen < 0; ++d)
+            if (d >= first_depth) judge(d, uint64_t(PC_LEAF_BYTES) * (1ull << d) + 4ull * words[d - D]);
+          if (chosen < 0 && !deeper) chosen = p.tune_last;  // every candidate's stream shrank: the deepest
+          if (chosen >= D) {
+            const uint64_t r = (n + (1ull << chosen) - 1) >> chosen;
+            hl.leaf_size = uint32_t(r);
+            hl.num_leaves = 1ull << chosen;
+            PC_TRY(launch_subtree(subtree_at(D, chosen - D, uint32_t(r), 1ull << chosen), st));
+            packed = true;
+          } else if (chosen < 0) {
+            // still shrinking at D + K: the search goes on over HBM from the arrangement the pass
+            // wrote (src: depth D + K; dst: depth D, never the one chosen from here)
+            void **t = src;
+            src = dst;
+            dst = t;
+            uint32_t *ti = isrc;
+            isrc = idst;
+            idst = ti;
+            src_depth = D + K;
+            for (int l = D + K; l < levels; ++l) {
+              if (l > D + K && l >= first_depth) {
+                uint64_t bytes = 0;
+                rc = depth_cost(src, l, &bytes);
+                if (rc) return rc;
+                judge(l, bytes);
+                if (chosen >= 0) break;
+              }
+              rc = global_level(l, l == D + K);
+              if (rc) return rc;
+            }
+          }
+        }
+      }
+      // the search stopped at the first depth whose stream is not smaller, or reached the
+      // deepest candidate (in src), which is then judged too
+      if (!packed && chosen < 0) {
         if (levels > first_depth) {
           uint64_t bytes = 0;
           rc = depth_cost(src, levels, &bytes);
           if (rc) return rc;
-          if (bytes >= best_bytes) chosen = levels - 1;
+          judge(levels, bytes);
         }
+        if (chosen < 0) chosen = levels;
       }
-      const int depth = chosen;
-      const bool deepest = depth == levels;  // src holds depth `levels`, dst depth `levels - 1`
-      void **codes = deepest ? src : dst;
-      uint32_t *idxs = deepest ? isrc : idst;
-      const uint64_t r = depth ? (n + (1ull << depth) - 1) >> depth : n;
-      hl.leaf_size = uint32_t(r);
-      hl.num_leaves = 1ull << depth;
-      if (p.reduce) {
-        rc = reduce_launch(codes, idxs, deepest ? dst : src, deepest ? idst : isrc, depth - 1, uint32_t(r),
-                           1ull << depth);
-        if (rc) return rc;
-      } else if (p.reorder) {
-        rc = reorder_launch(codes, idxs, deepest ? dst : src, deepest ? idst : isrc, depth - 1, uint32_t(r),
-                            1ull << depth);
-        if (rc) return rc;
-      } else {
-        PC_TRY(leaf_launch(codes, idxs, depth - 1, uint32_t(r), 1ull << depth, false));
+      if (!packed) {
+        const int depth = chosen;
+        const bool deepest = depth == src_depth;  // else dst holds it, one level above
+        void **codes = deepest ? src : dst;
+        uint32_t *idxs = deepest ? isrc : idst;
+        const uint64_t r = depth ? (n + (1ull << depth) - 1) >> depth : n;
+        hl.leaf_size = uint32_t(r);
+        hl.num_leaves = 1ull << depth;
+        if (p.reduce) {
+          rc = reduce_launch(codes, idxs, deepest ? dst : src, deepest ? idst : isrc, depth - 1, uint32_t(r),
+                             1ull << depth);
+          if (rc) return rc;
+        } else if (p.reorder) {
+          rc = reorder_launch(codes, idxs, deepest ? dst : src, deepest ? idst : isrc, depth - 1, uint32_t(r),
+                              1ull << depth);
+          if (rc) return rc;
+        } else {
+          PC_TRY(leaf_launch(codes, idxs, depth - 1, uint32_t(r), 1ull << depth, false));
+        }
       }
     }
     hl.total_words = reinterpret_cast<uint64_t *>(ws + p.off_words);

@@ -175,7 +175,7 @@ struct LevelLaunch {
   const uint32_t *src_idx;
   uint32_t *dst_idx;
   LevelNode *nodes;       // this level [2^level]
-  const LevelNode *parents;  // previous level [2^(level-1)], null at level 0
+  const LevelNode *parents;  // previous level [2^(level-1)]; null: every node takes the root's cell
   uint32_t *hist;         // [2^level][2^digit_bits], zero on entry, zero on exit
   unsigned long long *tile_state;
   void *groups;           // [tiles][scatter_groups()] group records of this level
@@ -240,6 +240,11 @@ struct SubtreeLaunch {
   uint64_t *total_words;      // written by the last node
   uint64_t payload_cap;
   uint32_t *err;
+  // the leaf-size search's pass (cost_words non-null): [levels + 1] payload words per in-CTA
+  // depth (zero on entry), and where the deepest in-CTA arrangement goes (null: nowhere)
+  unsigned long long *cost_words;
+  void *wb_codes[3];
+  uint32_t *wb_idx;
 };
 cudaError_t launch_subtree(const SubtreeLaunch &a, cudaStream_t st);
 uint32_t subtree_capacity(int code_bytes, bool with_idx);  // largest node of one CTA
