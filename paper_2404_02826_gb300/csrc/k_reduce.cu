@@ -1115,9 +1115,7 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
     if (e != cudaSuccess) return e;
     issued += kRoundsPerCheck;
     RCounters h;
-    e = cudaMemcpyAsync(&h, S.ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(st);
+    e = read_back(&h, S.ctr, sizeof(h), st);
     if (e != cudaSuccess) return e;
     if (h.alive == 0) {
       *num_seq = h.nseq;

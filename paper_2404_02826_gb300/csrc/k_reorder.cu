@@ -782,9 +782,7 @@ cudaError_t reorder_dispatch(const ReorderLaunch &a, cudaStream_t st) {
     k_ro_plan<<<1, 32, 0, st>>>(plan, a.num_seq);
   }
   uint32_t max_cnt = 0;
-  e = cudaMemcpyAsync(&max_cnt, &plan->max_cnt, 4, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(st);
+  e = read_back(&max_cnt, &plan->max_cnt, 4, st);
   if (e != cudaSuccess) return e;
   {
     TraceScope ts("k_ro_rank", st);

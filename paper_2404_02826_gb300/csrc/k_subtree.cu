@@ -792,6 +792,22 @@ __global__ void __launch_bounds__(kT, 1) k_subtree(SubtreeLaunch a) {
         static_cast<C *>(a.wb_codes[2])[o + i] = X0[2 * S + i];
         if (IDX) a.wb_idx[o + i] = XI[i];
       }
+      // and the records of the last in-CTA level (depth + levels - 1), the parents of the
+      // level over HBM that continues from there: their cells and splits (k_prep's fields)
+      if (a.wb_nodes && a.levels > 0) {
+        const uint32_t G = 1u << (a.levels - 1);
+        if (threadIdx.x < G) {
+          const SubNode &u = cur[threadIdx.x];
+          LevelNode nd = {};
+          for (int d = 0; d < 3; ++d) {
+            nd.blo[d] = u.blo[d];
+            nd.bhi[d] = u.bhi[d];
+          }
+          nd.axis = u.axis;
+          nd.v = u.split ? u.v : 0xffffffffu;
+          a.wb_nodes[(uint64_t(M.j) << (a.levels - 1)) + threadIdx.x] = nd;
+        }
+      }
     }
     tmem_fence_before();
     __syncthreads();

@@ -41,9 +41,7 @@ __global__ void k_prep(LevelNode *nodes, const LevelNode *parents, uint64_t n, i
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= count) return;
   LevelNode nd = {};
-  // no parents' records (a level resumed after the on-chip search pass): the root's
-  // cell, looser than the node's own, which the radix digits allow
-  if (level == 0 || parents == nullptr) {
+  if (level == 0) {
     for (int d = 0; d < 3; ++d) {
       nd.blo[d] = 0;
       nd.bhi[d] = root_hi.v[d];

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "../../include/pc.h"
 #include "pc_internal.cuh"
@@ -17,6 +19,58 @@ thread_local bool t_drop_tile_copies = false;
 }  // namespace
 
 void set_drop_tile_copies(bool on) { t_drop_tile_copies = on; }
+
+namespace {
+constexpr size_t kPinnedBlock = 4096;
+std::mutex g_pinned_mu;
+std::vector<void *> g_pinned_free;  // staging blocks not in use, kept for the life of the process
+
+void *pinned_take() {
+  {
+    std::lock_guard<std::mutex> g(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+      void *p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return p;
+    }
+  }
+  void *p = nullptr;
+  if (cudaHostAlloc(&p, kPinnedBlock, cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();  // no staging block: the copies go to their destinations
+    return nullptr;
+  }
+  return p;
+}
+
+void pinned_give(void *p) {
+  std::lock_guard<std::mutex> g(g_pinned_mu);
+  g_pinned_free.push_back(p);
+}
+}  // namespace
+
+cudaError_t read_back(const ReadBack *items, int count, cudaStream_t st) {
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) total += (items[i].bytes + 15) & ~size_t(15);
+  void *blk = total <= kPinnedBlock ? pinned_take() : nullptr;
+  cudaError_t e = cudaSuccess;
+  size_t o = 0;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    void *to = blk ? static_cast<uint8_t *>(blk) + o : items[i].dst;
+    e = cudaMemcpyAsync(to, items[i].src, items[i].bytes, cudaMemcpyDefault, st);
+    o += (items[i].bytes + 15) & ~size_t(15);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (blk && e == cudaSuccess) {
+    o = 0;
+    for (int i = 0; i < count; ++i) {
+      std::memcpy(items[i].dst, static_cast<const uint8_t *>(blk) + o, items[i].bytes);
+      o += (items[i].bytes + 15) & ~size_t(15);
+    }
+    pinned_give(blk);
+  }
+  // after a failure a copy may still be in flight into the block: it is not reused
+  return e;
+}
 
 int device_sm_count() {
   int dev = 0;
@@ -442,8 +496,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     ra.blocks = p.range_blocks;
     PC_TRY(launch_range(ra, st));
     RangeResult rr;
-    PC_TRY(cudaMemcpyAsync(&rr, ra.result, sizeof(rr), cudaMemcpyDeviceToHost, st));
-    PC_TRY(cudaStreamSynchronize(st));
+    PC_TRY(read_back(&rr, ra.result, sizeof(rr), st));
     rc = lattice_from_range(rr, dtype, eb_mode, eb, L);
     if (rc) return rc;
     // lossless axes (Sec. 4.1, m_d > M): the plain stream only; the reduction,
@@ -573,23 +626,23 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       return PC_OK;
     };
     // The error word so far, read back: the paths that read back anyway (the
-    // leaf-size search, the reduction, the reordering) stop before working on
-    // the partition of a call that has failed.
+    // reduction, the reordering) stop before working on the partition of a
+    // call that has failed; the leaf-size search reads it with each cost.
     auto error_so_far = [&]() -> int {
       uint32_t e = 0;
-      PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
-      PC_TRY(cudaStreamSynchronize(st));
+      PC_TRY(read_back(&e, err, 4, st));
       return (e & kErrTimeout) ? PC_ERR_TIMEOUT : (e ? PC_ERR_CUDA : PC_OK);
     };
-    // autotuning: stream bytes of the leaves at `depth` (every node there is a leaf)
+    // autotuning: stream bytes of the leaves at `depth` (every node there is a leaf),
+    // read back with the error word (the leaf kernels of a failed call do nothing)
     auto depth_cost = [&](void *const *codes, int depth, uint64_t *bytes) -> int {
-      const int failed = error_so_far();
-      if (failed) return failed;
       const uint64_t r = (n + (1ull << depth) - 1) >> depth;
       PC_TRY(leaf_launch(codes, nullptr, depth - 1, uint32_t(r), 1ull << depth, true));
       uint64_t words = 0;
-      PC_TRY(cudaMemcpyAsync(&words, ws + p.off_words, 8, cudaMemcpyDeviceToHost, st));
-      PC_TRY(cudaStreamSynchronize(st));
+      uint32_t e = 0;
+      const ReadBack rb[2] = {{&words, ws + p.off_words, 8}, {&e, err, 4}};
+      PC_TRY(read_back(rb, 2, st));
+      if (e) return (e & kErrTimeout) ? PC_ERR_TIMEOUT : PC_ERR_CUDA;
       *bytes = uint64_t(PC_LEAF_BYTES) * (1ull << depth) + 4 * words;
       return PC_OK;
     };
@@ -614,8 +667,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     uint32_t *isrc = idx_a, *idst = idx_b;
     int src_depth = 0;  // the depth of the arrangement in src; dst holds the one above
     // level l over HBM: splits the arrangement in src into dst, then swaps them
-    // (no parents' records: every node takes the root's cell)
-    auto global_level = [&](int l, bool no_parents) -> int {
+    auto global_level = [&](int l) -> int {
       LevelLaunch la = {};
       la.n = n;
       la.level = l;
@@ -640,7 +692,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.dst_idx = idst;
       const uint64_t node_base = (1ull << l) - 1;  // the records of the levels above come first
       la.nodes = nodes + node_base;
-      la.parents = (l > 0 && !no_parents) ? nodes + node_base - (1ull << (l - 1)) : nullptr;
+      la.parents = l > 0 ? nodes + node_base - (1ull << (l - 1)) : nullptr;
       uint64_t tile_base = 0;
       for (int k = 0; k < l; ++k) tile_base += (1ull << k) * tiles_per_node(n, k, scatter_tile(cb, use_idx));
       la.hist = reinterpret_cast<uint32_t *>(ws + p.off_hist);
@@ -680,7 +732,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
           if (chosen >= 0) break;
         }
       }
-      rc = global_level(l, false);
+      rc = global_level(l);
       if (rc) return rc;
     }
 
@@ -795,12 +847,14 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
           if (deeper) {
             for (int d = 0; d < 3; ++d) ca.wb_codes[d] = dst[d];
             ca.wb_idx = idst;
+            ca.wb_nodes = nodes + ((1ull << (D + K - 1)) - 1);
           }
           PC_TRY(launch_subtree(ca, st));
           unsigned long long words[kSubMaxLevels + 1] = {};
-          PC_TRY(cudaMemcpyAsync(words, cw, 8ull * (K + 1), cudaMemcpyDeviceToHost, st));
-          const int failed = error_so_far();
-          if (failed) return failed;
+          uint32_t e = 0;
+          const ReadBack rb[2] = {{words, cw, 8ull * (K + 1)}, {&e, err, 4}};
+          PC_TRY(read_back(rb, 2, st));
+          if (e) return (e & kErrTimeout) ? PC_ERR_TIMEOUT : PC_ERR_CUDA;
           for (int d = D + 1; d <= D + K && chosen < 0; ++d)
             if (d >= first_depth) judge(d, uint64_t(PC_LEAF_BYTES) * (1ull << d) + 4ull * words[d - D]);
           if (chosen < 0 && !deeper) chosen = p.tune_last;  // every candidate's stream shrank: the deepest
@@ -811,8 +865,9 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
             PC_TRY(launch_subtree(subtree_at(D, chosen - D, uint32_t(r), 1ull << chosen), st));
             packed = true;
           } else if (chosen < 0) {
-            // still shrinking at D + K: the search goes on over HBM from the arrangement the pass
-            // wrote (src: depth D + K; dst: depth D, never the one chosen from here)
+            // still shrinking at D + K: the search goes on over HBM from the arrangement and the
+            // depth D + K - 1 records the pass wrote (src: depth D + K; dst: depth D, never the
+            // one chosen from here)
             void **t = src;
             src = dst;
             dst = t;
@@ -828,7 +883,7 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
                 judge(l, bytes);
                 if (chosen >= 0) break;
               }
-              rc = global_level(l, l == D + K);
+              rc = global_level(l);
               if (rc) return rc;
             }
           }
@@ -876,9 +931,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
     uint64_t total;
     uint32_t err;
   } back = {0, 0};
-  PC_TRY(cudaMemcpyAsync(&back.total, total_dev, 8, cudaMemcpyDeviceToHost, st));
-  PC_TRY(cudaMemcpyAsync(&back.err, err, 4, cudaMemcpyDeviceToHost, st));
-  PC_TRY(cudaStreamSynchronize(st));
+  const ReadBack rb[2] = {{&back.total, total_dev, 8}, {&back.err, err, 4}};
+  PC_TRY(read_back(rb, 2, st));
   trace_flush();
   if (back.err & kErrTimeout) return PC_ERR_TIMEOUT;
   if (back.err) return PC_ERR_CUDA;
@@ -935,8 +989,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   // the error word and code bounds are cleared while the header comes back
   PC_TRY(cudaMemsetAsync(err, 0, 64, st));
   uint8_t h[PC_HEADER_BYTES];
-  PC_TRY(cudaMemcpyAsync(h, stream_data, PC_HEADER_BYTES, cudaMemcpyDefault, st));
-  PC_TRY(cudaStreamSynchronize(st));
+  PC_TRY(read_back(h, stream_data, PC_HEADER_BYTES, st));
   pc_info I;
   int rc = parse_header(h, PC_HEADER_BYTES, &I);
   if (rc) return rc;
@@ -971,8 +1024,7 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   da.raw = I.lossless_axes;
   PC_TRY(launch_decode(da, st));
   uint32_t e = 0;
-  PC_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
-  PC_TRY(cudaStreamSynchronize(st));
+  PC_TRY(read_back(&e, err, 4, st));
   trace_flush();
   if (e & kErrCorrupt) return PC_ERR_CORRUPT;
   if (e) return PC_ERR_CUDA;

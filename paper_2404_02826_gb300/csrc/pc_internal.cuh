@@ -175,7 +175,7 @@ struct LevelLaunch {
   const uint32_t *src_idx;
   uint32_t *dst_idx;
   LevelNode *nodes;       // this level [2^level]
-  const LevelNode *parents;  // previous level [2^(level-1)]; null: every node takes the root's cell
+  const LevelNode *parents;  // previous level [2^(level-1)], null at level 0
   uint32_t *hist;         // [2^level][2^digit_bits], zero on entry, zero on exit
   unsigned long long *tile_state;
   void *groups;           // [tiles][scatter_groups()] group records of this level
@@ -241,10 +241,12 @@ struct SubtreeLaunch {
   uint64_t payload_cap;
   uint32_t *err;
   // the leaf-size search's pass (cost_words non-null): [levels + 1] payload words per in-CTA
-  // depth (zero on entry), and where the deepest in-CTA arrangement goes (null: nowhere)
+  // depth (zero on entry), and where the deepest in-CTA arrangement goes (null: nowhere),
+  // with the records of depth + levels - 1 (the nodes of that depth, in order)
   unsigned long long *cost_words;
   void *wb_codes[3];
   uint32_t *wb_idx;
+  LevelNode *wb_nodes;
 };
 cudaError_t launch_subtree(const SubtreeLaunch &a, cudaStream_t st);
 uint32_t subtree_capacity(int code_bytes, bool with_idx);  // largest node of one CTA
@@ -313,6 +315,22 @@ uint64_t decode_table_bytes();
 uint64_t decode_chunk_bytes(uint64_t n);
 
 int device_sm_count();
+
+// Small device-to-host read-backs (result words, a stream header), then one
+// synchronisation of the stream.  The copies land in a page-locked staging
+// block (one DMA each, no bounce through a driver buffer) and are copied out
+// after the synchronisation; regions of more than 4 KB together go straight
+// to their destinations.
+struct ReadBack {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+cudaError_t read_back(const ReadBack *items, int count, cudaStream_t st);
+inline cudaError_t read_back(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  const ReadBack r = {dst, src, bytes};
+  return read_back(&r, 1, st);
+}
 
 // Blocks of kernel F resident per SM with `smem` bytes of dynamic shared
 // memory, after raising the kernel's dynamic shared-memory limit to `smem`.
