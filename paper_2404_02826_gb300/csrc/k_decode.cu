@@ -144,6 +144,69 @@ __global__ void k_validate(const uint8_t *__restrict__ stream, uint64_t n, uint6
   validate_leaf(stream, n, num_leaves, words, info, err, qb, raw, M, uint64_t(blockIdx.x) * blockDim.x + threadIdx.x);
 }
 
+// ---- the decoding prologue on the device, launched before the header is back on the host ----
+
+// The header fields the prologue needs, with the host parser's checks
+// (format, version, kinds, sizes, the stream's own length, finite s > 0 and
+// o): a stream that fails them is not touched.
+struct DevHeader {
+  uint64_t n, num_leaves, payload_words;
+  double s, o[3];
+  uint32_t dtype, raw;
+  bool ok;
+};
+
+__device__ __forceinline__ DevHeader read_header(const uint8_t *stream, uint64_t stream_bytes) {
+  DevHeader H = {};
+  const uint4 *p = reinterpret_cast<const uint4 *>(stream);
+  uint32_t w[24];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const uint4 v = __ldg(p + i);
+    w[4 * i] = v.x;
+    w[4 * i + 1] = v.y;
+    w[4 * i + 2] = v.z;
+    w[4 * i + 3] = v.w;
+  }
+  auto u64 = [&](int byte) { return uint64_t(w[byte / 4]) | (uint64_t(w[byte / 4 + 1]) << 32); };
+  const uint32_t magic = 'P' | ('C' << 8) | ('B' << 16) | (uint32_t('1') << 24);
+  bool ok = w[0] == magic && (w[1] & 0xffffu) == 1u;
+  H.dtype = (w[1] >> 16) & 0xffu;
+  const uint32_t mode = w[1] >> 24;
+  ok = ok && H.dtype <= 1u && mode <= 1u;
+  H.n = u64(8);
+  H.s = __longlong_as_double((long long)u64(32));
+  for (int d = 0; d < 3; ++d) H.o[d] = __longlong_as_double((long long)u64(40 + 8 * d));
+  H.num_leaves = u64(64);
+  H.payload_words = u64(72);
+  H.raw = w[21] & 0xffu;
+  ok = ok && H.raw <= 7u && (w[21] >> 8) == 0u && w[22] == 0u && w[23] == 0u;
+  ok = ok && H.n <= PC_MAX_PARTICLES && H.num_leaves <= H.n && ((H.n > 0) == (H.num_leaves > 0));
+  ok = ok && H.payload_words <= (1ull << 40) && isfinite(H.s) && H.s > 0.0;
+  for (int d = 0; d < 3; ++d) ok = ok && isfinite(H.o[d]);
+  ok = ok && uint64_t(kHeaderBytes) + uint64_t(kLeafBytes) * H.num_leaves + 4 * H.payload_words <= stream_bytes;
+  H.ok = ok;
+  return H;
+}
+
+// k_validate with the header read on the device: a fixed grid strides over the
+// leaves (warp-uniform steps, as validate_leaf's reductions need); nothing is
+// done when the header fails its checks or the chunk facts would not fit the
+// `chunk_cap` entries the workspace holds (the host then returns the error).
+__global__ void __launch_bounds__(256) k_validate_dev(const uint8_t *stream, uint64_t stream_bytes, uint64_t chunk_cap,
+                                                      ChunkInfo *info, uint32_t *err, int32_t *qb) {
+  const DevHeader H = read_header(stream, stream_bytes);
+  if (!H.ok) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrCorrupt);
+    return;
+  }
+  if ((H.n + kChunk - 1) / kChunk > chunk_cap) return;
+  const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x; base < H.num_leaves; base += step)
+    validate_leaf(stream, H.n, H.num_leaves, H.payload_words, info, err, qb, H.raw, H.dtype == 0 ? 32u : 64u,
+                  base + threadIdx.x);
+}
+
 __device__ __forceinline__ uint32_t word_at(const uint32_t *__restrict__ w, uint64_t nwords, uint64_t i) {
   return i < nwords ? __ldg(w + i) : 0u;
 }
@@ -282,6 +345,30 @@ template <typename T, bool FAST>
 __global__ void k_dtable(DecodeLaunch a) {
   if (*a.err) return;
   fill_table<T, FAST>(a);
+}
+// k_dtable with the header read on the device: the same tables, the float-pair
+// path chosen by the host's rule (float output, o exact in float, s within
+// 2^-100 .. 2^100).  Nothing for a failed validation or lossless axes.
+__global__ void k_dtable_dev(const uint8_t *stream, uint64_t stream_bytes, const uint32_t *err, int32_t *qb,
+                             void *tab) {
+  if (*reinterpret_cast<const volatile uint32_t *>(err)) return;
+  const DevHeader H = read_header(stream, stream_bytes);
+  if (!H.ok || H.raw || H.n == 0) return;
+  DecodeLaunch a = {};
+  a.s = H.s;
+  bool exact_o = true;
+  for (int d = 0; d < 3; ++d) {
+    a.o[d] = H.o[d];
+    a.of[d] = __double2float_rn(H.o[d]);
+    exact_o = exact_o && double(a.of[d]) == H.o[d];
+  }
+  a.sh = __double2float_rn(H.s);
+  a.sl = __double2float_rn(H.s - double(a.sh));
+  a.qb = qb;
+  a.tab = tab;
+  if (H.dtype != 0) fill_table<double, false>(a);
+  else if (exact_o && H.s > 0x1p-100 && H.s < 0x1p100) fill_table<float, true>(a);
+  else fill_table<float, false>(a);
 }
 
 // Whether a chunk is decoded from shared memory: at most kChunkLeaves leaves
@@ -580,8 +667,8 @@ __global__ void k_header(HeaderLaunch a) {
 }
 
 template <typename T, bool FAST, bool VEC>
-cudaError_t decode_launch(const DecodeLaunch &a, cudaStream_t st) {
-  {
+cudaError_t decode_launch(const DecodeLaunch &a, cudaStream_t st, bool tables) {
+  if (tables) {
     TraceScope ts("k_dtable", st);
     k_dtable<T, FAST><<<unsigned((kTabEntries + 255) / 256), 256, 0, st>>>(a);
   }
@@ -597,8 +684,8 @@ cudaError_t decode_launch(const DecodeLaunch &a, cudaStream_t st) {
 }
 
 template <typename T, bool FAST>
-cudaError_t decode_dispatch(const DecodeLaunch &a, cudaStream_t st) {
-  return a.vec ? decode_launch<T, FAST, true>(a, st) : decode_launch<T, FAST, false>(a, st);
+cudaError_t decode_dispatch(const DecodeLaunch &a, cudaStream_t st, bool tables = true) {
+  return a.vec ? decode_launch<T, FAST, true>(a, st, tables) : decode_launch<T, FAST, false>(a, st, tables);
 }
 
 
@@ -970,8 +1057,25 @@ cudaError_t launch_decode_lossless(const DecodeLaunch &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_decode_prologue(const uint8_t *stream, uint64_t stream_bytes, uint64_t chunk_cap, uint32_t *err,
+                                   int32_t *qb, void *tab, void *chunks, cudaStream_t st) {
+  {
+    TraceScope ts("k_validate", st);
+    k_validate_dev<<<unsigned(4 * device_sm_count()), 256, 0, st>>>(stream, stream_bytes, chunk_cap,
+                                                                    static_cast<ChunkInfo *>(chunks), err, qb);
+  }
+  TraceScope ts("k_dtable", st);
+  k_dtable_dev<<<unsigned((kTabEntries + 255) / 256), 256, 0, st>>>(stream, stream_bytes, err, qb, tab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
+  if (a.prologue_done) {  // validation and tables already launched (launch_decode_prologue)
+    if (a.raw) return launch_decode_lossless(a, st);
+    if (a.dtype == 0) return a.fast ? decode_dispatch<float, true>(a, st, false) : decode_dispatch<float, false>(a, st, false);
+    return decode_dispatch<double, false>(a, st, false);
+  }
   {
     TraceScope ts("k_validate", st);
     // 64 threads a block: the leaves spread over every SM (each thread waits on its records)

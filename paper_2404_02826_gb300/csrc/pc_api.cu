@@ -46,7 +46,63 @@ void pinned_give(void *p) {
   std::lock_guard<std::mutex> g(g_pinned_mu);
   g_pinned_free.push_back(p);
 }
+
+// Events without timing, per device, kept for the life of the process.
+std::vector<cudaEvent_t> g_events[64];
+
+cudaEvent_t event_take(int dev) {
+  {
+    std::lock_guard<std::mutex> g(g_pinned_mu);
+    std::vector<cudaEvent_t> &v = g_events[dev & 63];
+    if (!v.empty()) {
+      cudaEvent_t e = v.back();
+      v.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void event_give(int dev, cudaEvent_t e) {
+  std::lock_guard<std::mutex> g(g_pinned_mu);
+  g_events[dev & 63].push_back(e);
+}
 }  // namespace
+
+HeaderCopy::~HeaderCopy() {
+  if (!done) return;  // a copy that may still be in flight keeps its block and event
+  if (blk) pinned_give(blk);
+  if (ev) event_give(dev, ev);
+}
+
+cudaError_t HeaderCopy::start(const void *src, cudaStream_t st) {
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  blk = pinned_take();
+  ev = blk ? event_take(dev) : nullptr;
+  if (!ev) {  // no staging: the copy is waited for here
+    done = true;
+    e = cudaMemcpyAsync(h, src, kHeaderBytes, cudaMemcpyDefault, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+  }
+  e = cudaMemcpyAsync(blk, src, kHeaderBytes, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+  return e;
+}
+
+cudaError_t HeaderCopy::finish() {
+  if (done) return cudaSuccess;
+  const cudaError_t e = cudaEventSynchronize(ev);
+  if (e != cudaSuccess) return e;
+  std::memcpy(h, blk, kHeaderBytes);
+  done = true;
+  return cudaSuccess;
+}
 
 cudaError_t read_back(const ReadBack *items, int count, cudaStream_t st) {
   size_t total = 0;
@@ -986,19 +1042,34 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   if (stream_bytes < PC_HEADER_BYTES) return PC_ERR_CORRUPT;
   if (workspace_bytes < 64) return PC_ERR_CAPACITY;
   uint32_t *err = static_cast<uint32_t *>(workspace);
-  // the error word and code bounds are cleared while the header comes back
+  uint8_t *const ws = static_cast<uint8_t *>(workspace);
+  int32_t *const qb = reinterpret_cast<int32_t *>(ws + 32);
+  void *const tab = ws + kAlign;
+  void *const chunks = ws + kAlign + align_up(decode_table_bytes());
+  // the error word and code bounds are cleared, then the header starts back to the
+  // host; meanwhile the validation and the tables run on the device, reading the
+  // header there (when the workspace holds the tables and a chunk's facts)
   PC_TRY(cudaMemsetAsync(err, 0, 64, st));
-  uint8_t h[PC_HEADER_BYTES];
-  PC_TRY(read_back(h, stream_data, PC_HEADER_BYTES, st));
-  pc_info I;
-  int rc = parse_header(h, PC_HEADER_BYTES, &I);
-  if (rc) return rc;
-  if (I.total_bytes > stream_bytes) return PC_ERR_CORRUPT;
+  HeaderCopy hc;
+  PC_TRY(hc.start(stream_data, st));
+  const uint64_t tab_end = kAlign + align_up(decode_table_bytes());
+  const bool early = workspace_bytes >= tab_end + decode_chunk_bytes(1);
+  if (early)
+    PC_TRY(launch_decode_prologue(static_cast<const uint8_t *>(stream_data), stream_bytes,
+                                  (workspace_bytes - tab_end) / decode_chunk_bytes(1), err, qb, tab, chunks, st));
+  PC_TRY(hc.finish());
+  pc_info I = {};
+  int rc = parse_header(hc.h, PC_HEADER_BYTES, &I);
+  if (!rc && I.total_bytes > stream_bytes) rc = PC_ERR_CORRUPT;
   const uint64_t esz = I.dtype == PC_F32 ? 4 : 8;
-  if (out_capacity_bytes < 3 * esz * I.n) return PC_ERR_CAPACITY;
-  if (I.n == 0) return PC_OK;
-  if (!out_positions || reinterpret_cast<uintptr_t>(out_positions) % esz) return PC_ERR_ARG;
-  if (workspace_bytes < decompress_ws_bytes(I.n)) return PC_ERR_CAPACITY;
+  if (!rc && out_capacity_bytes < 3 * esz * I.n) rc = PC_ERR_CAPACITY;
+  if (!rc && I.n > 0 && (!out_positions || reinterpret_cast<uintptr_t>(out_positions) % esz)) rc = PC_ERR_ARG;
+  if (!rc && I.n > 0 && workspace_bytes < decompress_ws_bytes(I.n)) rc = PC_ERR_CAPACITY;
+  if (rc || I.n == 0) {
+    // nothing of the early kernels outlives the call
+    if (early) PC_TRY(cudaStreamSynchronize(st));
+    return rc;
+  }
   DecodeLaunch da = {};
   da.stream = static_cast<const uint8_t *>(stream_data);
   da.n = I.n;
@@ -1018,10 +1089,11 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   da.out = out_positions;
   da.vec = reinterpret_cast<uintptr_t>(out_positions) % 16 == 0;
   da.err = err;
-  da.qb = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(workspace) + 32);
-  da.tab = static_cast<uint8_t *>(workspace) + kAlign;
-  da.chunks = static_cast<uint8_t *>(workspace) + kAlign + align_up(decode_table_bytes());
+  da.qb = qb;
+  da.tab = tab;
+  da.chunks = chunks;
   da.raw = I.lossless_axes;
+  da.prologue_done = early;
   PC_TRY(launch_decode(da, st));
   uint32_t e = 0;
   PC_TRY(read_back(&e, err, 4, st));

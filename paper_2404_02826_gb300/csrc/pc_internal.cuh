@@ -282,8 +282,15 @@ struct DecodeLaunch {
   void *tab;             // [decode_table_bytes()]: dequantized value of every code, when they fit
   void *chunks;          // [decode_chunk_bytes(n)]: per decode chunk, its leaves and payload words
   uint32_t raw;          // lossless-axis mask: those axes hold M-bit patterns, every particle in the payload
+  bool prologue_done;    // validation and tables already launched by launch_decode_prologue
 };
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
+// Validation and tables for a stream whose header is not yet on the host: both
+// kernels read it from the stream (stream_bytes long) and check it as the host
+// parser does; chunk_cap = the chunk facts the workspace holds.  err and qb
+// zero on entry; launch_decode with prologue_done then launches the decoder.
+cudaError_t launch_decode_prologue(const uint8_t *stream, uint64_t stream_bytes, uint64_t chunk_cap, uint32_t *err,
+                                   int32_t *qb, void *tab, void *chunks, cudaStream_t st);
 
 // Many streams decoded by one set of launches: each stream's plain launch
 // fields, and where its leaves start in the batch's leaf space (a multiple of
@@ -331,6 +338,21 @@ inline cudaError_t read_back(void *dst, const void *src, size_t bytes, cudaStrea
   const ReadBack r = {dst, src, bytes};
   return read_back(&r, 1, st);
 }
+
+// A stream header on its way to host memory: copied into a page-locked block
+// and waited for on an event (finish), so that what is queued on the stream
+// after start runs meanwhile.  Without a block or an event, start waits for
+// the copy itself.
+struct HeaderCopy {
+  uint8_t h[kHeaderBytes];
+  void *blk = nullptr;
+  cudaEvent_t ev = nullptr;
+  int dev = 0;
+  bool done = false;  // h holds the header (or the copy failed before it was queued)
+  cudaError_t start(const void *src, cudaStream_t st);
+  cudaError_t finish();
+  ~HeaderCopy();
+};
 
 // Blocks of kernel F resident per SM with `smem` bytes of dynamic shared
 // memory, after raising the kernel's dynamic shared-memory limit to `smem`.
