@@ -27,6 +27,10 @@ CASES = [
     ("cosmology", 200_000, np.float32, "rel", 1e-4, 0, True, True),
     ("uniform", 40_000, np.float32, "rel", 1e-3, 8000, False, False),
     ("cosmology", 70_001, np.float32, "rel", 5e-4, 300, False, True),
+    # 2^20 u16 codes, no permutation: the on-chip pass at depth 5 costs depths 6-11, the stream
+    # still shrinks there (r = 128 wins), so the search resumes over HBM from the pass's
+    # arrangement and its depth-10 node records
+    ("cosmology", 1 << 20, np.float32, "rel", 1e-4, 0, False, False),
 ]
 
 

@@ -5,6 +5,8 @@ table = partition + bit boxes, packed codes), the permutation, and the decoded
 floats (the oracle decodes with the same double-precision rule).  Every
 decoded coordinate must lie within eps of its input.
 """
+import struct
+
 import numpy as np
 import pytest
 
@@ -278,10 +280,23 @@ def test_corrupt_streams_are_rejected(pc, oracle_mod):
     b = bytearray(stream); b[96 + 32 * 7 + 0] ^= 64; cases.append((b, None))  # particle offset
     b = bytearray(stream); b[72] ^= 8; cases.append((b, None))                # payload words
     cases.append((bytearray(stream), len(stream) - 4))                        # truncated
+    # header fields the device-side validation also reads before the host has parsed them
+    b = bytearray(stream); b[6] = 2; cases.append((b, None))                  # element type
+    b = bytearray(stream); b[90] = 1; cases.append((b, None))                 # reserved byte
+    b = bytearray(stream); b[32:40] = struct.pack("<d", float("nan")); cases.append((b, None))  # s
+    b = bytearray(stream); b[64:72] = struct.pack("<Q", 60_000); cases.append((b, None))  # leaves > n
     for buf, nb in cases:
         with pytest.raises(pc.PCError) as e:
             attempt(buf, nb)
         assert e.value.status == pc.PC_ERR_CORRUPT
+    # a header claiming far more particles than the workspace's chunk facts can hold: the
+    # device-side validation leaves the workspace alone, the host reports the output too small
+    b = bytearray(stream); b[8:16] = struct.pack("<Q", 1_000_000_000)
+    with pytest.raises(pc.PCError) as e:
+        attempt(b)
+    assert e.value.status == pc.PC_ERR_CAPACITY
+    attempt(stream)  # and the workspace still decodes the intact stream
+    assert out.cpu().numpy().tobytes() == oracle_mod.decompress(stream).tobytes()
     small = torch.empty((10, 3), dtype=torch.float32, device=dev)
     with pytest.raises(pc.PCError) as e:
         pc.pc_decompress(torch.from_numpy(np.frombuffer(stream, np.uint8).copy()).to(dev), small, ws)
