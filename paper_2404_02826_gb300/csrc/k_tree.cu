@@ -152,12 +152,27 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const C *__restrict__ q0,
         const uint4 *v = reinterpret_cast<const uint4 *>(codes + a0);
         const uint64_t nv = (a1 - a0) / kVec;
         uint64_t i = threadIdx.x;
-        for (; i + 3 * blockDim.x < nv; i += 4 * blockDim.x) {
+        // four 16-byte loads per thread and step; the next step's loads are issued
+        // before this step's codes are counted, so their latency hides behind the atomics
+        if (i + 3 * blockDim.x < nv) {
           uint4 w[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) w[u] = __ldcg(v + i + u * blockDim.x);
+          for (;;) {
+            const uint64_t in = i + 4 * blockDim.x;
+            const bool more = in + 3 * blockDim.x < nv;
+            uint4 nx[4];
+            if (more) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) add4(w[u]);
+              for (int u = 0; u < 4; ++u) nx[u] = __ldcg(v + in + u * blockDim.x);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add4(w[u]);
+            i = in;
+            if (!more) break;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = nx[u];
+          }
         }
         for (; i < nv; i += blockDim.x) add4(__ldcg(v + i));
       }
