@@ -189,6 +189,16 @@ __device__ __forceinline__ DevHeader read_header(const uint8_t *stream, uint64_t
   return H;
 }
 
+// The first launch of a decompression: clears the workspace's first 64 bytes
+// (error word, the decoder's block count, code bounds) and copies the header
+// into page-locked host memory.
+__global__ void k_decode_start(const uint8_t *stream, uint32_t *ws64, uint8_t *host_header) {
+  const uint32_t t = threadIdx.x;
+  if (t < 16) ws64[t] = 0u;
+  if (t < kHeaderBytes / 16)
+    reinterpret_cast<uint4 *>(host_header)[t] = __ldg(reinterpret_cast<const uint4 *>(stream) + t);
+}
+
 // k_validate with the header read on the device: a fixed grid strides over the
 // leaves (warp-uniform steps, as validate_leaf's reductions need); nothing is
 // done when the header fails its checks or the chunk facts would not fit the
@@ -341,8 +351,12 @@ __device__ __forceinline__ void fill_table(const DecodeLaunch &a) {
     tab[e] = dequant<T, FAST>(a, d, q);
   }
 }
+// The decoder is launched as the tables' programmatic dependent: its blocks may
+// be placed as soon as every block of the tables has begun, and wait for the
+// tables' completion (griddepcontrol.wait) before they read anything.
 template <typename T, bool FAST>
 __global__ void k_dtable(DecodeLaunch a) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (*a.err) return;
   fill_table<T, FAST>(a);
 }
@@ -351,6 +365,7 @@ __global__ void k_dtable(DecodeLaunch a) {
 // 2^-100 .. 2^100).  Nothing for a failed validation or lossless axes.
 __global__ void k_dtable_dev(const uint8_t *stream, uint64_t stream_bytes, const uint32_t *err, int32_t *qb,
                              void *tab) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (*reinterpret_cast<const volatile uint32_t *>(err)) return;
   const DevHeader H = read_header(stream, stream_bytes);
   if (!H.ok || H.raw || H.n == 0) return;
@@ -419,6 +434,9 @@ __device__ __forceinline__ void dec_issue(uint64_t payload_words, DecSmem &S, in
 template <typename T, bool FAST, bool VEC>
 __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
   __shared__ __align__(16) DecSmem S;
+  // launched as the tables' programmatic dependent: they (and the validation before
+  // them) are complete and visible after this wait
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (call_failed(a.err)) return;  // validation failed: write nothing
   const uint64_t nchunks = (a.n + kChunk - 1) / kChunk;
   uint64_t chunk = blockIdx.x;
@@ -590,6 +608,19 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeLaunch a) {
       }
     }
   }
+  // with host_err: the last block to get here leaves the error word there (a block that
+  // returned early does not count, and the host then reads the word itself)
+  if (a.host_err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(a.err + 1, 1u) == gridDim.x - 1) {
+        __threadfence();
+        *reinterpret_cast<volatile uint32_t *>(a.host_err) = *reinterpret_cast<volatile uint32_t *>(a.err);
+        __threadfence_system();
+      }
+    }
+  }
 }
 
 // Decoding of a stream with lossless axes, one thread per particle: its leaf
@@ -679,8 +710,18 @@ cudaError_t decode_launch(const DecodeLaunch &a, cudaStream_t st, bool tables) {
   uint64_t grid = uint64_t(per_sm < 1 ? 1 : per_sm) * uint64_t(device_sm_count());
   if (grid > decode_chunks(a.n)) grid = decode_chunks(a.n);
   TraceScope ts("k_decode", st);
-  k_decode<T, FAST, VEC><<<unsigned(grid), kDecThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  // a programmatic dependent of the tables: its blocks are placed while they are filled
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kDecThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_decode<T, FAST, VEC>, a);
 }
 
 template <typename T, bool FAST>
@@ -1054,6 +1095,12 @@ cudaError_t launch_decode_lossless(const DecodeLaunch &a, cudaStream_t st) {
   const unsigned grid = unsigned((a.n + kDecThreads - 1) / kDecThreads);
   if (a.dtype == 0) k_decode_lossless<float><<<grid, kDecThreads, 0, st>>>(a);
   else k_decode_lossless<double><<<grid, kDecThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_start(const uint8_t *stream, uint32_t *ws64, uint8_t *host_header, cudaStream_t st) {
+  TraceScope ts("k_decode_start", st);
+  k_decode_start<<<1, 32, 0, st>>>(stream, ws64, host_header);
   return cudaGetLastError();
 }
 

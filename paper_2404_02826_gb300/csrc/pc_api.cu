@@ -35,7 +35,7 @@ void *pinned_take() {
     }
   }
   void *p = nullptr;
-  if (cudaHostAlloc(&p, kPinnedBlock, cudaHostAllocPortable) != cudaSuccess) {
+  if (cudaHostAlloc(&p, kPinnedBlock, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
     cudaGetLastError();  // no staging block: the copies go to their destinations
     return nullptr;
   }
@@ -80,17 +80,27 @@ HeaderCopy::~HeaderCopy() {
   if (ev) event_give(dev, ev);
 }
 
-cudaError_t HeaderCopy::start(const void *src, cudaStream_t st) {
+cudaError_t HeaderCopy::start(const void *src, uint32_t *ws64, cudaStream_t st) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   blk = pinned_take();
   ev = blk ? event_take(dev) : nullptr;
-  if (!ev) {  // no staging: the copy is waited for here
+  if (ev && cudaHostGetDevicePointer(&dblk, blk, 0) != cudaSuccess) {
+    cudaGetLastError();
+    dblk = nullptr;
+  }
+  if (!dblk) {  // no staging: plain calls, waited for here
+    if (ev) event_give(dev, ev);
+    if (blk) pinned_give(blk);
+    ev = nullptr;
+    blk = nullptr;
+    dblk = nullptr;
     done = true;
-    e = cudaMemcpyAsync(h, src, kHeaderBytes, cudaMemcpyDefault, st);
+    e = cudaMemsetAsync(ws64, 0, 64, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, src, kHeaderBytes, cudaMemcpyDefault, st);
     return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
   }
-  e = cudaMemcpyAsync(blk, src, kHeaderBytes, cudaMemcpyDefault, st);
+  e = launch_decode_start(static_cast<const uint8_t *>(src), ws64, static_cast<uint8_t *>(dblk), st);
   if (e == cudaSuccess) e = cudaEventRecord(ev, st);
   return e;
 }
@@ -1046,12 +1056,11 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   int32_t *const qb = reinterpret_cast<int32_t *>(ws + 32);
   void *const tab = ws + kAlign;
   void *const chunks = ws + kAlign + align_up(decode_table_bytes());
-  // the error word and code bounds are cleared, then the header starts back to the
-  // host; meanwhile the validation and the tables run on the device, reading the
-  // header there (when the workspace holds the tables and a chunk's facts)
-  PC_TRY(cudaMemsetAsync(err, 0, 64, st));
+  // the error word and code bounds are cleared and the header starts back to the host;
+  // meanwhile the validation and the tables run on the device, reading the header
+  // there (when the workspace holds the tables and a chunk's facts)
   HeaderCopy hc;
-  PC_TRY(hc.start(stream_data, st));
+  PC_TRY(hc.start(stream_data, err, st));
   const uint64_t tab_end = kAlign + align_up(decode_table_bytes());
   const bool early = workspace_bytes >= tab_end + decode_chunk_bytes(1);
   if (early)
@@ -1094,9 +1103,22 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   da.chunks = chunks;
   da.raw = I.lossless_axes;
   da.prologue_done = early;
+  // the decoder's last block leaves the error word in the header's staging block, over a
+  // mark that stays when a block returned early (then the word is read back here)
+  constexpr uint32_t kUnset = 0xffffffffu;
+  da.host_err = da.raw ? nullptr : hc.host_err_dev();
+  if (da.host_err) *hc.host_err() = kUnset;
   PC_TRY(launch_decode(da, st));
-  uint32_t e = 0;
-  PC_TRY(read_back(&e, err, 4, st));
+  uint32_t e = kUnset;
+  if (da.host_err) {
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (se != cudaSuccess) {
+      hc.done = false;  // the decoder may still write into the staging block: it is not reused
+      return PC_ERR_CUDA;
+    }
+    e = *hc.host_err();
+  }
+  if (e == kUnset) PC_TRY(read_back(&e, err, 4, st));
   trace_flush();
   if (e & kErrCorrupt) return PC_ERR_CORRUPT;
   if (e) return PC_ERR_CUDA;

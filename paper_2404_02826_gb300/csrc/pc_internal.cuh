@@ -283,6 +283,10 @@ struct DecodeLaunch {
   void *chunks;          // [decode_chunk_bytes(n)]: per decode chunk, its leaves and payload words
   uint32_t raw;          // lossless-axis mask: those axes hold M-bit patterns, every particle in the payload
   bool prologue_done;    // validation and tables already launched by launch_decode_prologue
+  // optional, page-locked host memory: the error word as the decoder's last block reads it
+  // once every block is done (the blocks count themselves in err[1], zero on entry); a
+  // block that returns early leaves it untouched
+  uint32_t *host_err;
 };
 cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
 // Validation and tables for a stream whose header is not yet on the host: both
@@ -291,6 +295,10 @@ cudaError_t launch_decode(const DecodeLaunch &a, cudaStream_t st);
 // zero on entry; launch_decode with prologue_done then launches the decoder.
 cudaError_t launch_decode_prologue(const uint8_t *stream, uint64_t stream_bytes, uint64_t chunk_cap, uint32_t *err,
                                    int32_t *qb, void *tab, void *chunks, cudaStream_t st);
+// The first launch of a decompression: clears the workspace's first 64 bytes (error
+// word, block count, code bounds) and copies the stream's header into page-locked
+// host memory (`host_header`, 16-byte aligned).
+cudaError_t launch_decode_start(const uint8_t *stream, uint32_t *ws64, uint8_t *host_header, cudaStream_t st);
 
 // Many streams decoded by one set of launches: each stream's plain launch
 // fields, and where its leaves start in the batch's leaf space (a multiple of
@@ -339,18 +347,28 @@ inline cudaError_t read_back(void *dst, const void *src, size_t bytes, cudaStrea
   return read_back(&r, 1, st);
 }
 
-// A stream header on its way to host memory: copied into a page-locked block
-// and waited for on an event (finish), so that what is queued on the stream
-// after start runs meanwhile.  Without a block or an event, start waits for
-// the copy itself.
+// A stream header on its way to host memory: written into a page-locked block
+// by launch_decode_start (which also clears the workspace's first 64 bytes) and
+// waited for on an event (finish), so that what is queued on the stream after
+// start runs meanwhile; the block's word after the header then receives the
+// decoder's error word.  Without a block or an event, start clears and copies
+// with plain calls and waits for them.
 struct HeaderCopy {
   uint8_t h[kHeaderBytes];
-  void *blk = nullptr;
+  void *blk = nullptr;   // the staging block, host address
+  void *dblk = nullptr;  // and device address
   cudaEvent_t ev = nullptr;
   int dev = 0;
   bool done = false;  // h holds the header (or the copy failed before it was queued)
-  cudaError_t start(const void *src, cudaStream_t st);
+  cudaError_t start(const void *src, uint32_t *ws64, cudaStream_t st);
   cudaError_t finish();
+  // the word after the header in the staging block (null without one): host, device address
+  volatile uint32_t *host_err() const {
+    return blk ? reinterpret_cast<volatile uint32_t *>(static_cast<uint8_t *>(blk) + kHeaderBytes) : nullptr;
+  }
+  uint32_t *host_err_dev() const {
+    return dblk ? reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(dblk) + kHeaderBytes) : nullptr;
+  }
   ~HeaderCopy();
 };
 
