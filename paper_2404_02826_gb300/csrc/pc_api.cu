@@ -25,20 +25,20 @@ constexpr size_t kPinnedBlock = 4096;
 std::mutex g_pinned_mu;
 std::vector<void *> g_pinned_free;  // staging blocks not in use, kept for the life of the process
 
+constexpr int kPinnedBatch = 16;  // blocks page-locked together: concurrent callers rarely wait for one
+
 void *pinned_take() {
-  {
-    std::lock_guard<std::mutex> g(g_pinned_mu);
-    if (!g_pinned_free.empty()) {
-      void *p = g_pinned_free.back();
-      g_pinned_free.pop_back();
-      return p;
+  std::lock_guard<std::mutex> g(g_pinned_mu);
+  if (g_pinned_free.empty()) {
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, kPinnedBlock * kPinnedBatch, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();  // no staging block: the copies go to their destinations
+      return nullptr;
     }
+    for (int i = kPinnedBatch - 1; i >= 0; --i) g_pinned_free.push_back(static_cast<uint8_t *>(p) + kPinnedBlock * i);
   }
-  void *p = nullptr;
-  if (cudaHostAlloc(&p, kPinnedBlock, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
-    cudaGetLastError();  // no staging block: the copies go to their destinations
-    return nullptr;
-  }
+  void *p = g_pinned_free.back();
+  g_pinned_free.pop_back();
   return p;
 }
 
