@@ -24,6 +24,10 @@
  *   - Calls are synchronous with respect to the host where stated: compress
  *     and decompress each read a few bytes back (the value range, then the
  *     final size or the error word) and so return with their work finished.
+ *     Those bytes pass through page-locked host blocks of 4 KB that the
+ *     library allocates on first use, sixteen at a time, and keeps for the
+ *     life of the process (one block per call in flight; decompression also
+ *     keeps one CUDA event per call in flight).
  *
  * Stream format (little-endian), version 1:
  *   header, 96 bytes:
