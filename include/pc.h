@@ -27,7 +27,8 @@
  *     Those bytes pass through page-locked host blocks of 4 KB that the
  *     library allocates on first use, sixteen at a time, and keeps for the
  *     life of the process (one block per call in flight; decompression also
- *     keeps one CUDA event per call in flight).
+ *     keeps one CUDA event per call in flight); pc_compress_noalloc allocates
+ *     none (it uses blocks that exist, else plain copies).
  *
  * Stream format (little-endian), version 1:
  *   header, 96 bytes:

@@ -36,6 +36,7 @@
 #include <climits>
 #include <cstdint>
 
+#include "pc_host.cuh"
 #include "pc_internal.cuh"
 #include "pc_reduce.cuh"
 
@@ -1100,9 +1101,10 @@ cudaError_t reduce_dispatch(const ReduceLaunch &a, cudaStream_t st, uint64_t *nu
   // private stream of this call, so that any stream, the legacy one included,
   // can launch it) and launched once per read-back: one launch in place of
   // 4 * kRoundsPerCheck.  Kernel tracing needs events around every launch, so
-  // with it on (or when the capture fails) the launches go one by one.
+  // with it on (or when the capture fails) the launches go one by one; so do
+  // they for a caller that may not allocate (no graph is instantiated).
   RoundGraph graph;
-  if (!trace_enabled()) graph.capture(issue_rounds);
+  if (!trace_enabled() && !no_host_alloc()) graph.capture(issue_rounds);
   uint64_t issued = 0;
   for (;;) {
     if (graph.exec) {

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/pc.h"
+#include "pc_host.cuh"
 #include "pc_internal.cuh"
 #include "pc_reduce.cuh"
 #include "pc_reorder.cuh"
@@ -16,9 +17,12 @@ namespace pcx {
 
 namespace {
 thread_local bool t_drop_tile_copies = false;
+thread_local bool t_no_host_alloc = false;
 }  // namespace
 
 void set_drop_tile_copies(bool on) { t_drop_tile_copies = on; }
+void set_no_host_alloc(bool on) { t_no_host_alloc = on; }
+bool no_host_alloc() { return t_no_host_alloc; }
 
 namespace {
 constexpr size_t kPinnedBlock = 4096;
@@ -30,6 +34,7 @@ constexpr int kPinnedBatch = 16;  // blocks page-locked together: concurrent cal
 void *pinned_take() {
   std::lock_guard<std::mutex> g(g_pinned_mu);
   if (g_pinned_free.empty()) {
+    if (t_no_host_alloc) return nullptr;  // the copies go to their destinations
     void *p = nullptr;
     if (cudaHostAlloc(&p, kPinnedBlock * kPinnedBatch, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
       cudaGetLastError();  // no staging block: the copies go to their destinations

@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "../../include/pc.h"
+#include "pc_host.cuh"
 #include "pc_internal.cuh"
 
 namespace {
@@ -69,6 +70,10 @@ extern "C" int pc_compress_noalloc(const void *positions, uint64_t n, int dtype,
   void *scratch = nullptr;
   const int ac = scratch_address(&scratch);
   if (ac != PC_OK) return ac;
-  return pcx::compress_device(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, scratch,
-                              kPcNoallocScratchBytes, static_cast<cudaStream_t>(stream));
+  // nor host memory: no page-locked staging block is allocated for the read-backs
+  pcx::set_no_host_alloc(true);
+  const int cc = pcx::compress_device(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, scratch,
+                                      kPcNoallocScratchBytes, static_cast<cudaStream_t>(stream));
+  pcx::set_no_host_alloc(false);
+  return cc;
 }

@@ -77,3 +77,17 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch(pc):
     rc = pc.load().pc_compress_noalloc(pos.data_ptr(), n, pc.PC_F32, pc.PC_EB_REL, 1e-3, None, out.data_ptr(),
                                        out.numel(), ctypes.byref(size), None)
     assert rc == pc.PC_ERR_CAPACITY
+
+
+def test_noalloc_with_the_box_reduction(pc):
+    """With PC_FLAG_BOX_REDUCTION the rounds go one launch at a time (no CUDA graph is
+    instantiated for a caller that may not allocate); the stream is pc_compress's."""
+    n = 300_000
+    dev = torch.device("cuda:0")
+    dpos = torch.from_numpy(synth.cosmology(n, seed=5)).to(dev)
+    cfg = pc.config(2048, reduce=True)
+    ref = reference_stream(pc, dpos, pc.PC_F32, pc.PC_EB_REL, 1e-3, cfg)
+    out = torch.empty(pc.pc_compress_bound(n, pc.PC_F32, cfg), dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        size = pc.pc_compress_noalloc(dpos, pc.PC_EB_REL, 1e-3, out, leaf_size=cfg)
+        assert out[:size].cpu().numpy().tobytes() == ref
