@@ -230,6 +230,9 @@ def algorithmic_bytes(kernel, n, esz, cb, stream_bytes, with_idx=False, launches
         "k_decode": stream_bytes + 3 * esz * n,
         # the deep levels, bit boxes and packing on chip: every particle's codes read once, the stream written
         "k_subtree": 3 * cb * n + idx * n + stream_bytes,
+        # the leaf-size search's on-chip pass: every particle's codes read once (the arrangement it
+        # writes back when the search goes deeper is not counted)
+        "k_subtree_cost": 3 * cb * n + idx * n,
     }.get(kernel)
 
 
