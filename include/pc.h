@@ -96,8 +96,22 @@ typedef struct {
     uint32_t leaf_size; /* r of Sec. 4.1: largest leaf; 0 = 4096; valid 1..PC_MAX_LEAF_SIZE.
                            With PC_FLAG_AUTOTUNE_LEAF: the largest candidate (0 = PC_MAX_LEAF_SIZE) */
     uint32_t flags;     /* 0, or any of PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION, PC_FLAG_REORDER,
-                           PC_FLAG_WIDEST_AXIS */
+                           PC_FLAG_WIDEST_AXIS, PC_FLAG_AUTOTUNE_KNOBS */
+    /* The two launch knobs below change how many threads work on one node or
+     * one leaf, never a byte of the stream (no counterpart in the paper). */
+    uint32_t warp_node_max; /* threads per node: in the k-d levels over HBM, nodes of at most this many
+                               particles are split by one warp each (32 threads, one pass, no tiles), larger
+                               ones by 512-thread blocks over tiles (count, tile scan, scatter passes);
+                               0 = PC_DEFAULT_WARP_NODE_MAX; valid 1..PC_MAX_WARP_NODE_MAX */
+    uint32_t warp_leaf_max; /* packing tile: when the leaves' bit boxes and packing run over HBM (the
+                               leaf-size search, the reduction, the reordering, lossless axes), leaves of
+                               at most this size (r) get one warp each, larger ones a 256-thread block each;
+                               0 = PC_DEFAULT_WARP_LEAF_MAX; valid 1..PC_MAX_LEAF_SIZE */
 } pc_config;
+
+#define PC_DEFAULT_WARP_NODE_MAX 2048u
+#define PC_MAX_WARP_NODE_MAX 65536u
+#define PC_DEFAULT_WARP_LEAF_MAX 1024u
 
 /* Leaf-size autotuning (no counterpart in the paper, which fixes r by hand,
  * Sec. 5): the leaves of the median tree for r = ceil(n / 2^d) are its nodes
@@ -149,6 +163,22 @@ typedef struct {
  * median rule, the leaves and the stream format are unchanged; the decoder
  * does not need to know the rule. */
 #define PC_FLAG_WIDEST_AXIS 8u
+
+/* Launch-knob autotuning (no counterpart in the paper): the autotuner's choice
+ * of threads per node (warp_node_max) and packing tile (warp_leaf_max).  Calls
+ * are grouped in classes by the bit length of n, dtype, the other flags and
+ * leaf_size.  The first call of a class writes its stream with the default
+ * knobs, then compresses the same input again under each candidate that
+ * changes the launches for that input (threads per node 512 .. 8192, then
+ * packing tile 256 .. 4096 with the best threads per node; each timed on the
+ * host clock, best of two) and keeps the fastest for the class; later calls of
+ * the class run with it.  While one call of a class is tuning, other calls of
+ * that class run with the defaults.  The stream is the same under every
+ * candidate (the tuner checks its size).  pc_tuned_config reports a class's
+ * choice as a config for a plain call, which then makes the same launches and
+ * writes the same stream.  The timing runs reuse the call's output, workspace
+ * and perm, so a tuning call costs up to about twenty compressions. */
+#define PC_FLAG_AUTOTUNE_KNOBS 16u
 #define PC_AUTOTUNE_MIN_LEAF 64u
 
 #define PC_DEFAULT_LEAF_SIZE 4096u
@@ -193,6 +223,18 @@ int pc_compress_workspace_size(uint64_t n, int dtype, const pc_config *cfg, int 
 int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                 void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
                 uint32_t *perm, void *stream);
+
+/* The launch knobs PC_FLAG_AUTOTUNE_KNOBS uses for calls of the class of
+ * (n, dtype, cfg) (host only, no device work): *out = *cfg without that flag,
+ * with warp_node_max and warp_leaf_max set to the class's tuned values, or to
+ * cfg's own (defaults for 0) while the class is untuned.  *tuned = 1 when the
+ * class has been tuned, else 0.  A pc_compress with *out makes the launches the
+ * tuned calls make and writes the same stream.  cfg must carry the flag. */
+int pc_tuned_config(uint64_t n, int dtype, const pc_config *cfg, pc_config *out, int *tuned);
+
+/* Forget every class's tuned knobs (host only); classes tune again on their
+ * next PC_FLAG_AUTOTUNE_KNOBS call. */
+int pc_autotune_reset(void);
 
 /* Compression for callers that may not allocate device memory (the paper has
  * no counterpart; this is a deployment convenience).  Examples are code running

@@ -42,6 +42,10 @@ PC_FLAG_AUTOTUNE_LEAF = 1
 PC_FLAG_BOX_REDUCTION = 2
 PC_FLAG_REORDER = 4
 PC_FLAG_WIDEST_AXIS = 8
+PC_FLAG_AUTOTUNE_KNOBS = 16
+PC_DEFAULT_WARP_NODE_MAX = 2048
+PC_MAX_WARP_NODE_MAX = 65536
+PC_DEFAULT_WARP_LEAF_MAX = 1024
 PC_AUTOTUNE_MIN_LEAF = 64
 LEAF_AUTO = -1  # leaf_size argument: autotune with candidates up to PC_MAX_LEAF_SIZE
 
@@ -54,7 +58,8 @@ EXPORTS = (
     "pc_compress_batch_workspace_size", "pc_compress_batch", "pc_decompress_batch_workspace_size",
     "pc_decompress_batch", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_release",
     "pc_server_stats", "pc_server_destroy", "pc_server_now", "pc_leaf_size_sweep_workspace_size",
-    "pc_leaf_size_sweep", "pc_selftest_wait_timeout", "pc_selftest_scatter_timeout",
+    "pc_leaf_size_sweep", "pc_selftest_wait_timeout", "pc_selftest_scatter_timeout", "pc_tuned_config",
+    "pc_autotune_reset",
 )
 PC_REQ_COMPRESS = 0
 PC_REQ_DECOMPRESS = 1
@@ -69,7 +74,8 @@ class PCError(RuntimeError):
 
 
 class pc_config(ctypes.Structure):
-    _fields_ = [("leaf_size", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+    _fields_ = [("leaf_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("warp_node_max", ctypes.c_uint32),
+                ("warp_leaf_max", ctypes.c_uint32)]
 
 
 class pc_info(ctypes.Structure):
@@ -158,6 +164,8 @@ def _lib():
                                          ctypes.POINTER(u32), vp, u64, vp]
         L.pc_server_now.argtypes = []
         L.pc_server_now.restype = dbl
+        L.pc_tuned_config.argtypes = [u64, i32, pcfg, pcfg, ctypes.POINTER(i32)]
+        L.pc_autotune_reset.argtypes = []
         _LIB = L
     return _LIB
 
@@ -173,13 +181,31 @@ def _check(rc: int, where: str):
 
 
 def config(leaf_size: int = 0, autotune: bool = False, reduce: bool = False, reorder: bool = False,
-           widest: bool = False) -> pc_config:
+           widest: bool = False, tune_knobs: bool = False, warp_node_max: int = 0,
+           warp_leaf_max: int = 0) -> pc_config:
     """A pc_config: leaf size r (0 = default; with autotune the largest candidate,
-    0 = PC_MAX_LEAF_SIZE), PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION, PC_FLAG_REORDER and
-    PC_FLAG_WIDEST_AXIS."""
+    0 = PC_MAX_LEAF_SIZE), PC_FLAG_AUTOTUNE_LEAF, PC_FLAG_BOX_REDUCTION, PC_FLAG_REORDER,
+    PC_FLAG_WIDEST_AXIS, PC_FLAG_AUTOTUNE_KNOBS, and the launch knobs (threads per node:
+    warp_node_max; packing tile: warp_leaf_max; 0 = default)."""
     return pc_config(int(leaf_size), (PC_FLAG_AUTOTUNE_LEAF if autotune else 0) |
                      (PC_FLAG_BOX_REDUCTION if reduce else 0) | (PC_FLAG_REORDER if reorder else 0) |
-                     (PC_FLAG_WIDEST_AXIS if widest else 0))
+                     (PC_FLAG_WIDEST_AXIS if widest else 0) | (PC_FLAG_AUTOTUNE_KNOBS if tune_knobs else 0),
+                     int(warp_node_max), int(warp_leaf_max))
+
+
+def tuned_config(n: int, dtype: int, cfg: pc_config):
+    """pc_tuned_config: (the config a plain call reproduces the class's launches with, tuned?)
+    for calls of (n, dtype, cfg), cfg carrying PC_FLAG_AUTOTUNE_KNOBS."""
+    out = pc_config()
+    tuned = ctypes.c_int(0)
+    _check(_lib().pc_tuned_config(n, dtype, ctypes.byref(cfg), ctypes.byref(out), ctypes.byref(tuned)),
+           "pc_tuned_config")
+    return out, bool(tuned.value)
+
+
+def autotune_reset() -> None:
+    """pc_autotune_reset: forget every class's tuned launch knobs."""
+    _check(_lib().pc_autotune_reset(), "pc_autotune_reset")
 
 
 def _cfg(leaf_size) -> pc_config:

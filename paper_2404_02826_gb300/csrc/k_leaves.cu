@@ -25,7 +25,6 @@ namespace {
 constexpr int kBoxThreads = 256;
 constexpr int kPackThreads = 256;
 constexpr int kPackWarps = kPackThreads / 32;
-constexpr uint32_t kSmallLeaf = 1024;  // leaves of at most this many particles: one warp each
 
 __global__ void k_leaftable(uint64_t n, int level, uint32_t r, LeafRec *recs, uint64_t num_leaves) {
   const uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -591,7 +590,7 @@ cudaError_t leaves_dispatch(const LeafLaunch &a, cudaStream_t st) {
                                                                a.num_leaves);
   }
   // threads per leaf: a CTA for large leaves, a warp for small ones
-  const bool small = a.leaf_size <= kSmallLeaf;
+  const bool small = a.leaf_size <= a.warp_leaf_max;
   const uint64_t warp_blocks = (a.num_leaves + 7) / 8;
   const unsigned wgrid = unsigned(warp_blocks < uint64_t(device_sm_count()) * 32 ? warp_blocks
                                                                                  : uint64_t(device_sm_count()) * 32);

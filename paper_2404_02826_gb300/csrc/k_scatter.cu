@@ -27,7 +27,6 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr uint64_t kSmallNode = 2048;  // levels whose nodes are at most this large: a warp per node
 
 template <typename C, bool IDX>
 struct Cfg {
@@ -374,7 +373,7 @@ __global__ void k_tilescan_small(LevelLaunch a) {
   }
 }
 
-// Levels of small nodes (at most kSmallNode particles): one warp partitions a
+// Levels of small nodes (at most a.warp_node_max particles): one warp partitions a
 // whole node in one pass, 32 consecutive particles per round, carrying the
 // counts of "code < v" and "code == v" from round to round - no tiles, no
 // count pass, no tile scan.  Same placement rule as k_scatter.  AXIS is the
@@ -467,7 +466,7 @@ cudaError_t scatter_node_launch(const LevelLaunch &a, cudaStream_t st) {
 
 template <typename C, bool IDX>
 cudaError_t scatter_dispatch(const LevelLaunch &a, cudaStream_t st) {
-  if (((a.n + (1ull << a.level) - 1) >> a.level) <= kSmallNode) {
+  if (((a.n + (1ull << a.level) - 1) >> a.level) <= a.warp_node_max) {
     if (a.widest) return scatter_node_launch<C, IDX, 3>(a, st);
     switch (a.level % 3) {
       case 0: return scatter_node_launch<C, IDX, 0>(a, st);

@@ -1,6 +1,7 @@
 // C ABI (include/pc.h): argument checks, the error-bound arithmetic of Sec. 3
 // on the host, workspace layout, and the launch sequence of the hot path.
 #include <cfloat>
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -210,6 +211,8 @@ struct Plan {
   uint64_t off_reduce = 0, off_seqrec = 0;  // bit-box reduction: its scratch and the sequence records
   uint64_t off_rorecs = 0, off_roscratch = 0;  // reordering: the records in the new order, its scratch
   bool reduce = false, reorder = false, widest = false;
+  uint32_t warp_node_max = PC_DEFAULT_WARP_NODE_MAX;  // threads per node: a warp per node up to this size
+  uint32_t warp_leaf_max = PC_DEFAULT_WARP_LEAF_MAX;  // packing tile: a warp per leaf up to this leaf size
   bool tune = false;  // leaf size chosen by descending from r_hi while the stream shrinks (sized for r)
   uint32_t r_hi = 0;
   int tune_first = 0, tune_last = 0;  // candidate depths
@@ -301,8 +304,12 @@ int make_plan(uint64_t n, int dtype, const pc_config *cfg, bool idx, int sm_coun
   uint32_t r = PC_DEFAULT_LEAF_SIZE;
   p.tune = false;
   if (cfg) {
-    if (cfg->flags & ~(PC_FLAG_AUTOTUNE_LEAF | PC_FLAG_BOX_REDUCTION | PC_FLAG_REORDER | PC_FLAG_WIDEST_AXIS))
+    if (cfg->flags & ~(PC_FLAG_AUTOTUNE_LEAF | PC_FLAG_BOX_REDUCTION | PC_FLAG_REORDER | PC_FLAG_WIDEST_AXIS |
+                       PC_FLAG_AUTOTUNE_KNOBS))
       return PC_ERR_ARG;
+    if (cfg->warp_node_max > PC_MAX_WARP_NODE_MAX || cfg->warp_leaf_max > PC_MAX_LEAF_SIZE) return PC_ERR_ARG;
+    if (cfg->warp_node_max) p.warp_node_max = cfg->warp_node_max;
+    if (cfg->warp_leaf_max) p.warp_leaf_max = cfg->warp_leaf_max;
     p.widest = (cfg->flags & PC_FLAG_WIDEST_AXIS) != 0;
     p.reduce = (cfg->flags & PC_FLAG_BOX_REDUCTION) != 0;
     p.reorder = (cfg->flags & PC_FLAG_REORDER) != 0;
@@ -515,9 +522,25 @@ static uint64_t payload_words(uint64_t capacity, uint64_t leaves) {
   return capacity > fixed ? (capacity - fixed) / 4 : 0;
 }
 
+// What one compression launched, for the launch-knob autotuner: which levels
+// ran over HBM (the warp-per-node choice is made per level) and the leaf sizes
+// the leaf kernels over HBM ran with (the warp-per-leaf choice is made per launch).
+struct RunFacts {
+  uint64_t hbm_levels = 0;  // bit l: level l ran over HBM
+  uint32_t leaf_sizes[32] = {};
+  int num_leaf_sizes = 0;
+  bool leaf_overflow = false;  // more distinct leaf sizes than recorded
+  void note_leaf_size(uint32_t r) {
+    for (int i = 0; i < num_leaf_sizes; ++i)
+      if (leaf_sizes[i] == r) return;
+    if (num_leaf_sizes < 32) leaf_sizes[num_leaf_sizes++] = r;
+    else leaf_overflow = true;
+  }
+};
+
 int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                   void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
-                  uint32_t *perm, cudaStream_t st, Sweep *sweep = nullptr) {
+                  uint32_t *perm, cudaStream_t st, Sweep *sweep = nullptr, RunFacts *facts = nullptr) {
   if (sweep) {
     if (!cfg || !(cfg->flags & PC_FLAG_AUTOTUNE_LEAF) || perm) return PC_ERR_ARG;
   } else if (!out || !out_size) {
@@ -636,6 +659,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       lf.split_level = split_level;
       lf.code_bytes = cb;
       lf.leaf_size = r;
+      lf.warp_leaf_max = p.warp_leaf_max;
+      if (facts) facts->note_leaf_size(r);
       lf.num_leaves = num_leaves;
       for (int d = 0; d < 3; ++d) lf.codes[d] = codes[d];
       lf.idx = idxs;
@@ -682,6 +707,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       lf.n = n;
       lf.code_bytes = cb;
       lf.leaf_size = r;
+      lf.warp_leaf_max = p.warp_leaf_max;
+      if (facts) facts->note_leaf_size(r);
       lf.num_leaves = num_seq;
       for (int d = 0; d < 3; ++d) lf.codes[d] = codes[d];
       lf.idx = idxs;
@@ -745,6 +772,8 @@ int compress_impl(const void *positions, uint64_t n, int dtype, int eb_mode, dou
       la.code_bytes = cb;
       la.with_idx = use_idx;
       la.leaf_size = p.r;
+      la.warp_node_max = p.warp_node_max;
+      if (facts && l < 64) facts->hbm_levels |= 1ull << l;
       // levels of at least 2048 nodes of at most kMedMaxNode particles: one warp per node
       la.warp_median = (1ull << l) >= 2048 && ((n + (1ull << l) - 1) >> l) <= kMedMaxNode;
       la.digit_bits = la.warp_median ? kMedD : digit_bits_for(l);
@@ -1130,6 +1159,201 @@ int decompress_impl(const void *stream_data, uint64_t stream_bytes, void *out_po
   return PC_OK;
 }
 
+// ---- Launch-knob autotuning (PC_FLAG_AUTOTUNE_KNOBS) --------------------------
+// The classes live in a fixed table (no heap allocation, so pc_compress_noalloc
+// may look them up).  The call that enters a class tunes it; a reset bumps the
+// generation, and a tuning that started before it stores nothing.
+constexpr int kKnobClasses = 256;
+constexpr uint32_t kNodeCandidates[] = {512, 1024, 2048, 4096, 8192};
+constexpr uint32_t kLeafCandidates[] = {256, 512, 1024, 2048, 4096};
+
+struct KnobClass {
+  int state;  // 0 free, 1 being tuned, 2 tuned
+  uint64_t key;
+  uint32_t leaf_size;
+  uint32_t node_max, leaf_max;
+};
+std::mutex g_knob_mu;
+KnobClass g_knob[kKnobClasses] = {};
+uint64_t g_knob_gen = 0;
+
+int bits_u64(uint64_t x) {
+  int b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+// Class of a call: bit length of n, dtype, device and the flags other than this one (leaf_size apart).
+uint64_t knob_key(uint64_t n, int dtype, const pc_config &c, int dev) {
+  return uint64_t(bits_u64(n)) | (uint64_t(dtype & 1) << 7) | (uint64_t(dev & 0xff) << 8) |
+         (uint64_t(c.flags & ~PC_FLAG_AUTOTUNE_KNOBS) << 16);
+}
+
+// Slot of the class (key, leaf_size), or -1.  With `claim`, a class not in the
+// table is entered as being tuned (when a slot is free) and *claimed is set.
+// Called with g_knob_mu held.
+int knob_find(uint64_t key, uint32_t leaf_size, bool claim, bool *claimed) {
+  *claimed = false;
+  int free_slot = -1;
+  for (int i = 0; i < kKnobClasses; ++i) {
+    if (g_knob[i].state == 0) {
+      if (free_slot < 0) free_slot = i;
+    } else if (g_knob[i].key == key && g_knob[i].leaf_size == leaf_size) {
+      return i;
+    }
+  }
+  if (!claim || free_slot < 0) return -1;
+  g_knob[free_slot] = KnobClass{1, key, leaf_size, 0, 0};
+  *claimed = true;
+  return free_slot;
+}
+
+// The tuning of one class: the call's own stream with cfg's knobs first, then
+// every candidate that changes a launch for this input, timed on the host clock
+// around the (synchronous) compression, best of two.  Threads per node first,
+// then the packing tile with the best threads per node.  Every run writes the
+// same stream into `out` (its size is checked).
+int tune_knobs(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config &base,
+               void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
+               uint32_t *perm, cudaStream_t st, uint32_t *node_max, uint32_t *leaf_max) {
+  RunFacts facts;
+  int rc = compress_impl(positions, n, dtype, eb_mode, eb, &base, out, out_capacity, out_size, workspace,
+                         workspace_bytes, perm, st, nullptr, &facts);
+  if (rc) return rc;
+  const uint64_t size0 = *out_size;
+  uint32_t best_node = base.warp_node_max ? base.warp_node_max : PC_DEFAULT_WARP_NODE_MAX;
+  uint32_t best_leaf = base.warp_leaf_max ? base.warp_leaf_max : PC_DEFAULT_WARP_LEAF_MAX;
+  auto timed = [&](uint32_t nm, uint32_t lm, double *sec) -> int {
+    pc_config c = base;
+    c.warp_node_max = nm;
+    c.warp_leaf_max = lm;
+    double best = 0.0;
+    for (int k = 0; k < 2; ++k) {
+      uint64_t size = 0;
+      const auto t0 = std::chrono::steady_clock::now();
+      const int r = compress_impl(positions, n, dtype, eb_mode, eb, &c, out, out_capacity, &size, workspace,
+                                  workspace_bytes, perm, st);
+      const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (r) return r;
+      if (size != size0) return PC_ERR_CUDA;  // a launch knob changed the stream: never expected
+      if (k == 0 || t < best) best = t;
+    }
+    *sec = best;
+    return PC_OK;
+  };
+  // what a candidate changes: the levels over HBM given a warp per node, or the
+  // leaf-kernel launches given a warp per leaf
+  auto signature = [&](bool node, uint32_t c) -> uint64_t {
+    uint64_t m = 0;
+    if (node) {
+      for (int l = 0; l < 40; ++l)
+        if (((facts.hbm_levels >> l) & 1ull) && ((n + (1ull << l) - 1) >> l) <= c) m |= 1ull << l;
+    } else {
+      for (int i = 0; i < facts.num_leaf_sizes; ++i)
+        if (facts.leaf_sizes[i] <= c) m |= 1ull << i;
+    }
+    return m;
+  };
+  auto dist = [](uint32_t a, uint32_t b) { return a > b ? a - b : b - a; };
+  // the current value and one candidate per other signature (the one nearest the current value)
+  auto pass = [&](bool node, const uint32_t *cands, int nc, uint32_t &cur) -> int {
+    uint64_t sig[8];
+    uint32_t rep[8];
+    int ns = 0;
+    sig[ns] = signature(node, cur);
+    rep[ns++] = cur;
+    for (int i = 0; i < nc; ++i) {
+      const uint64_t s = signature(node, cands[i]);
+      int j = 0;
+      while (j < ns && sig[j] != s) ++j;
+      if (j == ns) {
+        sig[ns] = s;
+        rep[ns++] = cands[i];
+      } else if (j > 0 && dist(cands[i], cur) < dist(rep[j], cur)) {
+        rep[j] = cands[i];
+      }
+    }
+    if (ns == 1) return PC_OK;  // no candidate changes a launch
+    double best_t = 0.0;
+    uint32_t best = cur;
+    for (int j = 0; j < ns; ++j) {
+      double t = 0.0;
+      const int r = node ? timed(rep[j], best_leaf, &t) : timed(best_node, rep[j], &t);
+      if (r) return r;
+      if (j == 0 || t < best_t) {
+        best_t = t;
+        best = rep[j];
+      }
+    }
+    cur = best;
+    return PC_OK;
+  };
+  rc = pass(true, kNodeCandidates, int(sizeof(kNodeCandidates) / sizeof(kNodeCandidates[0])), best_node);
+  if (rc) return rc;
+  if (!facts.leaf_overflow) {
+    rc = pass(false, kLeafCandidates, int(sizeof(kLeafCandidates) / sizeof(kLeafCandidates[0])), best_leaf);
+    if (rc) return rc;
+  }
+  *node_max = best_node;
+  *leaf_max = best_leaf;
+  return PC_OK;
+}
+
+// Every compression entry point comes here: the plain call, or the knobs of
+// the call's class (tuning the class when this call is its first).
+int compress_entry(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
+                   void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
+                   uint32_t *perm, cudaStream_t st) {
+  if (!cfg || !(cfg->flags & PC_FLAG_AUTOTUNE_KNOBS))
+    return compress_impl(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, workspace,
+                         workspace_bytes, perm, st);
+  pc_config base = *cfg;
+  base.flags &= ~PC_FLAG_AUTOTUNE_KNOBS;
+  {
+    Plan p;  // argument checks before the class table is touched
+    const int rc = make_plan(n, dtype, &base, perm != nullptr, device_sm_count(), p);
+    if (rc) return rc;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PC_ERR_CUDA;
+  const uint64_t key = knob_key(n, dtype, base, dev);
+  // tuning runs the compression many times and keeps a table entry: not for
+  // empty inputs nor for callers that allocate nothing
+  const bool may_tune = n > 0 && out && out_size && !no_host_alloc();
+  int slot = -1;
+  bool claimed = false;
+  uint64_t gen = 0;
+  {
+    std::lock_guard<std::mutex> g(g_knob_mu);
+    slot = knob_find(key, base.leaf_size, may_tune, &claimed);
+    gen = g_knob_gen;
+    if (slot >= 0 && g_knob[slot].state == 2) {
+      base.warp_node_max = g_knob[slot].node_max;
+      base.warp_leaf_max = g_knob[slot].leaf_max;
+    }
+  }
+  if (!claimed)
+    return compress_impl(positions, n, dtype, eb_mode, eb, &base, out, out_capacity, out_size, workspace,
+                         workspace_bytes, perm, st);
+  uint32_t node_max = 0, leaf_max = 0;
+  const int rc = tune_knobs(positions, n, dtype, eb_mode, eb, base, out, out_capacity, out_size, workspace,
+                            workspace_bytes, perm, st, &node_max, &leaf_max);
+  std::lock_guard<std::mutex> g(g_knob_mu);
+  if (g_knob_gen == gen) {
+    if (rc == PC_OK) {
+      g_knob[slot].node_max = node_max;
+      g_knob[slot].leaf_max = leaf_max;
+      g_knob[slot].state = 2;
+    } else {
+      g_knob[slot].state = 0;
+    }
+  }
+  return rc;
+}
+
 }  // namespace
 
 namespace pcx {
@@ -1137,8 +1361,8 @@ namespace pcx {
 int compress_device(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
                     void *out, uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes,
                     cudaStream_t st) {
-  return compress_impl(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, workspace,
-                       workspace_bytes, nullptr, st);
+  return compress_entry(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, workspace,
+                        workspace_bytes, nullptr, st);
 }
 
 }  // namespace pcx
@@ -1167,8 +1391,45 @@ int pc_compress_workspace_size(uint64_t n, int dtype, const pc_config *cfg, int 
 int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg, void *out,
                 uint64_t out_capacity, uint64_t *out_size, void *workspace, uint64_t workspace_bytes, uint32_t *perm,
                 void *stream) {
-  return compress_impl(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, workspace,
-                       workspace_bytes, perm, static_cast<cudaStream_t>(stream));
+  return compress_entry(positions, n, dtype, eb_mode, eb, cfg, out, out_capacity, out_size, workspace,
+                        workspace_bytes, perm, static_cast<cudaStream_t>(stream));
+}
+
+int pc_tuned_config(uint64_t n, int dtype, const pc_config *cfg, pc_config *out, int *tuned) {
+  if (!cfg || !out || !tuned || !(cfg->flags & PC_FLAG_AUTOTUNE_KNOBS)) return PC_ERR_ARG;
+  pc_config c = *cfg;
+  c.flags &= ~PC_FLAG_AUTOTUNE_KNOBS;
+  Plan p;
+  const int rc = make_plan(n, dtype, &c, false, 148, p);
+  if (rc) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  const uint64_t key = knob_key(n, dtype, c, dev);
+  c.warp_node_max = p.warp_node_max;
+  c.warp_leaf_max = p.warp_leaf_max;
+  *tuned = 0;
+  {
+    std::lock_guard<std::mutex> g(g_knob_mu);
+    bool claimed = false;
+    const int slot = knob_find(key, c.leaf_size, false, &claimed);
+    if (slot >= 0 && g_knob[slot].state == 2) {
+      c.warp_node_max = g_knob[slot].node_max;
+      c.warp_leaf_max = g_knob[slot].leaf_max;
+      *tuned = 1;
+    }
+  }
+  *out = c;
+  return PC_OK;
+}
+
+int pc_autotune_reset(void) {
+  std::lock_guard<std::mutex> g(g_knob_mu);
+  for (int i = 0; i < kKnobClasses; ++i) g_knob[i].state = 0;
+  ++g_knob_gen;
+  return PC_OK;
 }
 
 int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info) {
@@ -1241,8 +1502,8 @@ int pc_compress_host(const void *host_positions, uint64_t n, int dtype, int eb_m
   uint8_t *rest = dout + align_up(bound);
   if (n) PC_TRY(cudaMemcpyAsync(dpos, host_positions, 3 * esz * n, cudaMemcpyHostToDevice, st));
   uint64_t size = 0;
-  rc = compress_impl(dpos, n, dtype, eb_mode, eb, cfg, dout, bound, &size, rest, workspace_bytes - (rest - ws),
-                     nullptr, st);
+  rc = compress_entry(dpos, n, dtype, eb_mode, eb, cfg, dout, bound, &size, rest, workspace_bytes - (rest - ws),
+                      nullptr, st);
   if (rc) return rc;
   if (size > out_capacity) return PC_ERR_CAPACITY;
   PC_TRY(cudaMemcpyAsync(host_out, dout, size, cudaMemcpyDeviceToHost, st));

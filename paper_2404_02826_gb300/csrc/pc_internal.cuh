@@ -164,6 +164,7 @@ struct LevelLaunch {
   int code_bytes;
   bool with_idx;
   uint32_t leaf_size;     // nodes of at most this many particles are leaves (copied unchanged)
+  uint32_t warp_node_max; // levels whose nodes hold at most this many particles: one warp per node
   uint32_t digit_bits;
   bool warp_median;       // one warp per node runs the whole radix select (k_median, kMedD-bit digits)
   uint32_t passes;
@@ -195,6 +196,7 @@ struct LeafLaunch {
   int split_level;          // last level that split nodes (-1: the root is the only leaf)
   int code_bytes;
   uint32_t leaf_size;
+  uint32_t warp_leaf_max;   // leaf_size at most this: a warp per leaf for bit boxes and packing, else a block
   uint64_t num_leaves;
   const void *codes[3];     // leaf-ordered codes
   const uint32_t *idx;      // leaf-ordered input indices (optional)

@@ -101,7 +101,7 @@ def test_autotune_flag_sizes_and_rejections(pc):
     assert auto == pc.pc_compress_bound(n, pc.PC_F32, pc.PC_AUTOTUNE_MIN_LEAF)
     assert pc.pc_compress_workspace_size(n, pc.PC_F32, pc.LEAF_AUTO) >= pc.pc_compress_workspace_size(n, pc.PC_F32)
     assert pc.pc_compress_bound(n, pc.PC_F32, -512) == pc.pc_compress_bound(n, pc.PC_F32, pc.PC_AUTOTUNE_MIN_LEAF)
-    cfg = pc.pc_config(0, 16)  # no such flag
+    cfg = pc.pc_config(0, 32)  # no such flag
     out = pc.ctypes.c_uint64()
     assert pc.load().pc_compress_bound(n, pc.PC_F32, pc.ctypes.byref(cfg), pc.ctypes.byref(out)) == pc.PC_ERR_ARG
     # the bit-box reduction writes no more sequences than leaves, and needs more scratch
@@ -117,3 +117,41 @@ def test_autotune_flag_sizes_and_rejections(pc):
     with pytest.raises(pc.PCError) as e:
         pc.pc_compress_bound(n, pc.PC_F32, -8)
     assert e.value.status == pc.PC_ERR_ARG
+
+
+def test_launch_knobs_sizes_rejections_and_tuned_config(pc):
+    """The launch knobs (threads per node, packing tile) change neither the stream
+    bound nor the workspace; values above their maxima are rejected; the tuned
+    config of a class nobody has compressed is the call's own config, without
+    PC_FLAG_AUTOTUNE_KNOBS and with the defaults filled in (no device needed)."""
+    n = 300_000
+    L = pc.load()
+    out = pc.ctypes.c_uint64()
+    base_bound = pc.pc_compress_bound(n, pc.PC_F32, 512)
+    base_ws = pc.pc_compress_workspace_size(n, pc.PC_F32, 512)
+    for knobs in ((1, 1), (512, 256), (pc.PC_MAX_WARP_NODE_MAX, pc.PC_MAX_LEAF_SIZE)):
+        cfg = pc.config(512, warp_node_max=knobs[0], warp_leaf_max=knobs[1])
+        assert pc.pc_compress_bound(n, pc.PC_F32, cfg) == base_bound
+        assert pc.pc_compress_workspace_size(n, pc.PC_F32, cfg) == base_ws
+    tuned_cfg = pc.config(512, tune_knobs=True)
+    assert pc.pc_compress_bound(n, pc.PC_F32, tuned_cfg) == base_bound
+    assert pc.pc_compress_workspace_size(n, pc.PC_F32, tuned_cfg) == base_ws
+    for bad in (pc.config(512, warp_node_max=pc.PC_MAX_WARP_NODE_MAX + 1),
+                pc.config(512, warp_leaf_max=pc.PC_MAX_LEAF_SIZE + 1)):
+        assert L.pc_compress_bound(n, pc.PC_F32, pc.ctypes.byref(bad), pc.ctypes.byref(out)) == pc.PC_ERR_ARG
+    pc.autotune_reset()
+    got, tuned = pc.tuned_config(n, pc.PC_F32, pc.config(512, reduce=True, tune_knobs=True))
+    assert not tuned
+    assert (got.leaf_size, got.flags) == (512, pc.PC_FLAG_BOX_REDUCTION)
+    assert (got.warp_node_max, got.warp_leaf_max) == (pc.PC_DEFAULT_WARP_NODE_MAX, pc.PC_DEFAULT_WARP_LEAF_MAX)
+    got, _ = pc.tuned_config(n, pc.PC_F32, pc.config(512, tune_knobs=True, warp_node_max=700, warp_leaf_max=90))
+    assert (got.warp_node_max, got.warp_leaf_max) == (700, 90)
+    # the query wants the flag, and checks the config like the compression does
+    plain = pc.config(512)
+    tuned_out = pc.pc_config()
+    flag = pc.ctypes.c_int()
+    assert L.pc_tuned_config(n, pc.PC_F32, pc.ctypes.byref(plain), pc.ctypes.byref(tuned_out),
+                             pc.ctypes.byref(flag)) == pc.PC_ERR_ARG
+    bad = pc.config(512, tune_knobs=True, warp_leaf_max=pc.PC_MAX_LEAF_SIZE + 1)
+    assert L.pc_tuned_config(n, pc.PC_F32, pc.ctypes.byref(bad), pc.ctypes.byref(tuned_out),
+                             pc.ctypes.byref(flag)) == pc.PC_ERR_ARG
