@@ -253,6 +253,8 @@ int pc_autotune_reset(void);
  *   - all calls on a device share the array; what must start at zero is
  *     cleared by every call, but calls that overlap on the GPU race on it and
  *     must be serialised by the caller;
+ *   - with PC_FLAG_AUTOTUNE_KNOBS it runs with a class's tuned launch knobs
+ *     when that class has been tuned by another entry point, but never tunes;
  *   - no allocation happens while kernel tracing (pc_trace_enable) is off. */
 #define PC_NOALLOC_SCRATCH_BYTES (48u << 20)
 int pc_compress_noalloc(const void *positions, uint64_t n, int dtype, int eb_mode, double eb, const pc_config *cfg,
@@ -357,7 +359,8 @@ typedef struct {
     int32_t eb_mode;        /* pc_eb_mode */
     double eb;
     uint32_t leaf_size;     /* as pc_config.leaf_size */
-    uint32_t flags;         /* as pc_config.flags */
+    uint32_t flags;         /* as pc_config.flags; the launch knobs are the defaults, or with
+                               PC_FLAG_AUTOTUNE_KNOBS those of the item's class */
     void *out;              /* device, out_capacity bytes (pc_compress_bound suffices) */
     uint64_t out_capacity;
     uint64_t out_size;      /* written: stream bytes */
