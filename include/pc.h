@@ -225,15 +225,16 @@ int pc_compress(const void *positions, uint64_t n, int dtype, int eb_mode, doubl
                 uint32_t *perm, void *stream);
 
 /* The launch knobs PC_FLAG_AUTOTUNE_KNOBS uses for calls of the class of
- * (n, dtype, cfg) (host only, no device work): *out = *cfg without that flag,
+ * (n, dtype, cfg) (no counterpart in the paper; host only, no device work):
+ * *out = *cfg without that flag,
  * with warp_node_max and warp_leaf_max set to the class's tuned values, or to
  * cfg's own (defaults for 0) while the class is untuned.  *tuned = 1 when the
  * class has been tuned, else 0.  A pc_compress with *out makes the launches the
  * tuned calls make and writes the same stream.  cfg must carry the flag. */
 int pc_tuned_config(uint64_t n, int dtype, const pc_config *cfg, pc_config *out, int *tuned);
 
-/* Forget every class's tuned knobs (host only); classes tune again on their
- * next PC_FLAG_AUTOTUNE_KNOBS call. */
+/* Forget every class's tuned knobs (no counterpart in the paper; host only);
+ * classes tune again on their next PC_FLAG_AUTOTUNE_KNOBS call. */
 int pc_autotune_reset(void);
 
 /* Compression for callers that may not allocate device memory (the paper has
