@@ -51,3 +51,22 @@ def test_traffic_only_for_unchanged_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_traffic("k_scatter", "cosmology-2^27-f32-rel1e-4", n) is None
     assert bench.measured_traffic("k_nothing", "cosmology-2^27-f32-rel1e-4", n) is None
+
+
+def test_batch_workload_config_is_sized_like_the_leaf_autotuner_alone():
+    """The batch-256 line runs both autotuners (leaf size and launch knobs); the
+    knob flag changes no size the library reports for it (host-only queries)."""
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as pcbuild
+
+    pcbuild.build()
+    pc.load()
+    cfg = bench.BATCH_CFG(pc)
+    assert cfg.flags == pc.PC_FLAG_AUTOTUNE_LEAF | pc.PC_FLAG_AUTOTUNE_KNOBS
+    assert (cfg.leaf_size, cfg.warp_node_max, cfg.warp_leaf_max) == (0, 0, 0)
+    items = [(12_345, pc.PC_F32), (2_000_000, pc.PC_F64), (9_999_999, pc.PC_F32)]
+    for n, dt in items:
+        assert pc.pc_compress_bound(n, dt, cfg) == pc.pc_compress_bound(n, dt, pc.LEAF_AUTO)
+        assert pc.pc_compress_workspace_size(n, dt, cfg) == pc.pc_compress_workspace_size(n, dt, pc.LEAF_AUTO)
+    assert pc.pc_compress_batch_workspace_size([(n, dt, cfg) for n, dt in items], 16) == \
+        pc.pc_compress_batch_workspace_size([(n, dt, pc.LEAF_AUTO) for n, dt in items], 16)
