@@ -237,6 +237,34 @@ int pc_tuned_config(uint64_t n, int dtype, const pc_config *cfg, pc_config *out,
  * classes tune again on their next PC_FLAG_AUTOTUNE_KNOBS call. */
 int pc_autotune_reset(void);
 
+/* One tuned class of PC_FLAG_AUTOTUNE_KNOBS, as saved and restored (no
+ * counterpart in the paper).  A later process can load the tuned classes
+ * instead of timing them again. */
+typedef struct {
+    uint32_t n_bits;        /* bit length of n (0..31) */
+    int32_t dtype;          /* pc_dtype */
+    int32_t device;         /* CUDA device number (0..255) */
+    uint32_t flags;         /* the class's flags, without PC_FLAG_AUTOTUNE_KNOBS */
+    uint32_t leaf_size;     /* pc_config.leaf_size of the class */
+    uint32_t warp_node_max; /* the tuned knobs */
+    uint32_t warp_leaf_max;
+    uint32_t reserved;      /* zero */
+} pc_tuned_class;
+
+/* Copy the tuned classes out (host only): up to `capacity` entries into
+ * `out` (may be NULL when capacity is 0); *count receives the number of tuned
+ * classes, which may exceed capacity.  Classes being tuned are not listed. */
+int pc_autotune_export(pc_tuned_class *out, uint32_t capacity, uint32_t *count);
+
+/* Enter classes as tuned (host only), replacing any entry of the same class;
+ * later PC_FLAG_AUTOTUNE_KNOBS calls of those classes run with them.  Every
+ * entry is checked first (n_bits <= 31, dtype, device 0..255, known flags
+ * without PC_FLAG_AUTOTUNE_KNOBS, leaf_size and knobs within their ranges,
+ * knobs nonzero, reserved zero): PC_ERR_ARG enters none.  PC_ERR_CAPACITY
+ * when the table (256 classes) has no room for all new classes; none is
+ * entered then either. */
+int pc_autotune_import(const pc_tuned_class *classes, uint32_t count);
+
 /* Compression for callers that may not allocate device memory (the paper has
  * no counterpart; this is a deployment convenience).  Examples are code running
  * inside another framework's memory pool that is only handed its input and

@@ -59,7 +59,7 @@ EXPORTS = (
     "pc_decompress_batch", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_release",
     "pc_server_stats", "pc_server_destroy", "pc_server_now", "pc_leaf_size_sweep_workspace_size",
     "pc_leaf_size_sweep", "pc_selftest_wait_timeout", "pc_selftest_scatter_timeout", "pc_tuned_config",
-    "pc_autotune_reset",
+    "pc_autotune_reset", "pc_autotune_export", "pc_autotune_import",
 )
 PC_REQ_COMPRESS = 0
 PC_REQ_DECOMPRESS = 1
@@ -76,6 +76,12 @@ class PCError(RuntimeError):
 class pc_config(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("warp_node_max", ctypes.c_uint32),
                 ("warp_leaf_max", ctypes.c_uint32)]
+
+
+class pc_tuned_class(ctypes.Structure):
+    _fields_ = [("n_bits", ctypes.c_uint32), ("dtype", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("leaf_size", ctypes.c_uint32), ("warp_node_max", ctypes.c_uint32),
+                ("warp_leaf_max", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class pc_info(ctypes.Structure):
@@ -166,6 +172,8 @@ def _lib():
         L.pc_server_now.restype = dbl
         L.pc_tuned_config.argtypes = [u64, i32, pcfg, pcfg, ctypes.POINTER(i32)]
         L.pc_autotune_reset.argtypes = []
+        L.pc_autotune_export.argtypes = [ctypes.POINTER(pc_tuned_class), u32, ctypes.POINTER(u32)]
+        L.pc_autotune_import.argtypes = [ctypes.POINTER(pc_tuned_class), u32]
         _LIB = L
     return _LIB
 
@@ -206,6 +214,52 @@ def tuned_config(n: int, dtype: int, cfg: pc_config):
 def autotune_reset() -> None:
     """pc_autotune_reset: forget every class's tuned launch knobs."""
     _check(_lib().pc_autotune_reset(), "pc_autotune_reset")
+
+
+_TUNED_FIELDS = ("n_bits", "dtype", "device", "flags", "leaf_size", "warp_node_max", "warp_leaf_max")
+AUTOTUNE_FORMAT = "pc-autotune-knobs"
+
+
+def autotune_export() -> list:
+    """pc_autotune_export: the tuned classes, as dicts of pc_tuned_class's fields."""
+    L = _lib()
+    count = ctypes.c_uint32(0)
+    _check(L.pc_autotune_export(None, 0, ctypes.byref(count)), "pc_autotune_export")
+    while True:
+        arr = (pc_tuned_class * max(count.value, 1))()
+        cap = count.value
+        _check(L.pc_autotune_export(arr, cap, ctypes.byref(count)), "pc_autotune_export")
+        if count.value <= cap:
+            return [{f: int(getattr(arr[i], f)) for f in _TUNED_FIELDS} for i in range(count.value)]
+
+
+def autotune_import(classes) -> None:
+    """pc_autotune_import: enter classes (dicts as autotune_export gives) as tuned."""
+    arr = (pc_tuned_class * max(len(classes), 1))()
+    for i, c in enumerate(classes):
+        for f in _TUNED_FIELDS:
+            setattr(arr[i], f, int(c[f]))
+    _check(_lib().pc_autotune_import(arr, len(classes)), "pc_autotune_import")
+
+
+def autotune_save(path) -> int:
+    """Write the tuned classes to a JSON file; returns how many."""
+    import json
+    classes = autotune_export()
+    with open(path, "w") as f:
+        json.dump({"format": AUTOTUNE_FORMAT, "version": 1, "classes": classes}, f, indent=1)
+    return len(classes)
+
+
+def autotune_load(path) -> int:
+    """Enter the classes of a JSON file written by autotune_save as tuned; returns how many."""
+    import json
+    with open(path) as f:
+        doc = json.load(f)
+    if doc.get("format") != AUTOTUNE_FORMAT or doc.get("version") != 1:
+        raise ValueError(f"{path}: not a version-1 {AUTOTUNE_FORMAT} file")
+    autotune_import(doc["classes"])
+    return len(doc["classes"])
 
 
 def _cfg(leaf_size) -> pc_config:

@@ -1432,6 +1432,71 @@ int pc_autotune_reset(void) {
   return PC_OK;
 }
 
+int pc_autotune_export(pc_tuned_class *out, uint32_t capacity, uint32_t *count) {
+  if (!count || (capacity && !out)) return PC_ERR_ARG;
+  std::lock_guard<std::mutex> g(g_knob_mu);
+  uint32_t k = 0;
+  for (int i = 0; i < kKnobClasses; ++i) {
+    const KnobClass &c = g_knob[i];
+    if (c.state != 2) continue;
+    if (k < capacity) {
+      pc_tuned_class t = {};
+      t.n_bits = uint32_t(c.key & 0x7f);
+      t.dtype = int32_t((c.key >> 7) & 1);
+      t.device = int32_t((c.key >> 8) & 0xff);
+      t.flags = uint32_t(c.key >> 16);
+      t.leaf_size = c.leaf_size;
+      t.warp_node_max = c.node_max;
+      t.warp_leaf_max = c.leaf_max;
+      out[k] = t;
+    }
+    ++k;
+  }
+  *count = k;
+  return PC_OK;
+}
+
+int pc_autotune_import(const pc_tuned_class *classes, uint32_t count) {
+  if (count && !classes) return PC_ERR_ARG;
+  std::vector<uint64_t> keys(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    const pc_tuned_class &t = classes[i];
+    if (t.n_bits > 31 || (t.dtype != PC_F32 && t.dtype != PC_F64) || t.device < 0 || t.device > 255 ||
+        t.reserved || (t.flags & PC_FLAG_AUTOTUNE_KNOBS) || !t.warp_node_max || !t.warp_leaf_max)
+      return PC_ERR_ARG;
+    // the class's config must be one a compression accepts (flags, leaf size, knob ranges)
+    const pc_config c = {t.leaf_size, t.flags, t.warp_node_max, t.warp_leaf_max};
+    const uint64_t n_rep = t.n_bits ? (1ull << (t.n_bits - 1)) : 0;  // a size of that bit length
+    Plan p;
+    if (make_plan(n_rep, t.dtype, &c, false, 148, p)) return PC_ERR_ARG;
+    keys[i] = knob_key(n_rep, t.dtype, c, t.device);
+  }
+  std::lock_guard<std::mutex> g(g_knob_mu);
+  auto slot_of = [&](uint64_t key, uint32_t leaf_size) {
+    for (int s = 0; s < kKnobClasses; ++s)
+      if (g_knob[s].state != 0 && g_knob[s].key == key && g_knob[s].leaf_size == leaf_size) return s;
+    return -1;
+  };
+  // classes neither in the table nor earlier in the list need a free slot each
+  int free_slots = 0, need = 0;
+  for (int s = 0; s < kKnobClasses; ++s) free_slots += g_knob[s].state == 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    bool seen = slot_of(keys[i], classes[i].leaf_size) >= 0;
+    for (uint32_t j = 0; j < i && !seen; ++j) seen = keys[j] == keys[i] && classes[j].leaf_size == classes[i].leaf_size;
+    need += !seen;
+  }
+  if (need > free_slots) return PC_ERR_CAPACITY;
+  for (uint32_t i = 0; i < count; ++i) {
+    int s = slot_of(keys[i], classes[i].leaf_size);
+    if (s < 0) {
+      s = 0;
+      while (g_knob[s].state != 0) ++s;
+    }
+    g_knob[s] = KnobClass{2, keys[i], classes[i].leaf_size, classes[i].warp_node_max, classes[i].warp_leaf_max};
+  }
+  return PC_OK;
+}
+
 int pc_stream_info(const void *host_header, uint64_t header_bytes, pc_info *info) {
   if (!host_header || !info) return PC_ERR_ARG;
   return parse_header(static_cast<const uint8_t *>(host_header), header_bytes, info);

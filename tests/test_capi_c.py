@@ -93,7 +93,7 @@ def test_c_program_matches_the_binding(tmp_path, lib):
 
 
 LAYOUT_STRUCTS = ("pc_config", "pc_info", "pc_compress_item", "pc_decompress_item", "pc_sweep_point", "pc_request",
-                  "pc_completion")
+                  "pc_completion", "pc_tuned_class")
 
 
 def test_struct_layouts_match_the_binding(tmp_path, lib):

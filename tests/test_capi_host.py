@@ -155,3 +155,87 @@ def test_launch_knobs_sizes_rejections_and_tuned_config(pc):
     bad = pc.config(512, tune_knobs=True, warp_leaf_max=pc.PC_MAX_LEAF_SIZE + 1)
     assert L.pc_tuned_config(n, pc.PC_F32, pc.ctypes.byref(bad), pc.ctypes.byref(tuned_out),
                              pc.ctypes.byref(flag)) == pc.PC_ERR_ARG
+
+
+def _tuned(n_bits, dtype, flags, leaf, node, leaf_max, device=0):
+    return {"n_bits": n_bits, "dtype": dtype, "device": device, "flags": flags, "leaf_size": leaf,
+            "warp_node_max": node, "warp_leaf_max": leaf_max}
+
+
+def _key(c):
+    return tuple(sorted(c.items()))
+
+
+def test_tuned_classes_export_import_and_json(pc, tmp_path):
+    """Tuned launch-knob classes go out and come back (the autotuner's persisted
+    cache): imported classes are what pc_tuned_config reports for calls of those
+    classes, an import replaces a class's entry, a JSON file written by
+    autotune_save restores the same table, and bad entries are refused whole."""
+    pc.autotune_reset()
+    assert pc.autotune_export() == []
+    a = _tuned(17, pc.PC_F32, pc.PC_FLAG_AUTOTUNE_LEAF, 0, 4096, 512)
+    b = _tuned(20, pc.PC_F64, 0, 256, 1024, 2048)
+    c = _tuned(24, pc.PC_F32, pc.PC_FLAG_BOX_REDUCTION | pc.PC_FLAG_REORDER, 4096, 8192, 256)
+    pc.autotune_import([a, b, c])
+    assert sorted(map(_key, pc.autotune_export())) == sorted(map(_key, [a, b, c]))
+    got, tuned = pc.tuned_config(100_000, pc.PC_F32, pc.config(0, autotune=True, tune_knobs=True))  # 17 bits
+    assert tuned and (got.warp_node_max, got.warp_leaf_max) == (4096, 512)
+    assert got.flags == pc.PC_FLAG_AUTOTUNE_LEAF and got.leaf_size == 0
+    got, tuned = pc.tuned_config(600_000, pc.PC_F64, pc.config(256, tune_knobs=True))  # 20 bits
+    assert tuned and (got.warp_node_max, got.warp_leaf_max) == (1024, 2048)
+    # another leaf size, bit length or dtype is another class
+    assert not pc.tuned_config(600_000, pc.PC_F64, pc.config(512, tune_knobs=True))[1]
+    assert not pc.tuned_config(1_100_000, pc.PC_F64, pc.config(256, tune_knobs=True))[1]
+    assert not pc.tuned_config(600_000, pc.PC_F32, pc.config(256, tune_knobs=True))[1]
+    # re-importing a class replaces its knobs; duplicates within one import keep the last
+    b2 = dict(b, warp_node_max=512)
+    pc.autotune_import([b, b2])
+    table = {(_key(dict(x, warp_node_max=0, warp_leaf_max=0))): x for x in pc.autotune_export()}
+    assert len(table) == 3 and table[_key(dict(b, warp_node_max=0, warp_leaf_max=0))]["warp_node_max"] == 512
+    # JSON round trip
+    path = tmp_path / "knobs.json"
+    assert pc.autotune_save(path) == 3
+    before = sorted(map(_key, pc.autotune_export()))
+    pc.autotune_reset()
+    assert pc.autotune_load(path) == 3
+    assert sorted(map(_key, pc.autotune_export())) == before
+    # bad entries: nothing of the import is entered
+    L = pc.load()
+    for bad in (dict(a, n_bits=32), dict(a, dtype=2), dict(a, device=256), dict(a, device=-1),
+                dict(a, flags=pc.PC_FLAG_AUTOTUNE_KNOBS), dict(a, flags=64), dict(a, warp_node_max=0),
+                dict(a, warp_leaf_max=0), dict(a, warp_node_max=pc.PC_MAX_WARP_NODE_MAX + 1),
+                dict(a, warp_leaf_max=pc.PC_MAX_LEAF_SIZE + 1), dict(a, flags=0, leaf_size=pc.PC_MAX_LEAF_SIZE + 1),
+                dict(a, leaf_size=8)):  # the leaf-size search needs a largest candidate of at least 16
+        arr = (pc.pc_tuned_class * 2)()
+        for i, entry in enumerate((_tuned(5, pc.PC_F32, 0, 0, 2048, 1024), bad)):
+            for f, v in entry.items():
+                setattr(arr[i], f, v)
+        assert L.pc_autotune_import(arr, 2) == pc.PC_ERR_ARG, bad
+        assert sorted(map(_key, pc.autotune_export())) == before
+    arr = (pc.pc_tuned_class * 1)()
+    arr[0].n_bits, arr[0].warp_node_max, arr[0].warp_leaf_max, arr[0].reserved = 5, 2048, 1024, 1
+    assert L.pc_autotune_import(arr, 1) == pc.PC_ERR_ARG
+    with open(tmp_path / "other.json", "w") as f:
+        f.write('{"format": "something-else", "version": 1, "classes": []}')
+    with pytest.raises(ValueError):
+        pc.autotune_load(tmp_path / "other.json")
+    pc.autotune_reset()
+
+
+def test_tuned_class_table_capacity(pc):
+    """The table holds 256 classes; an import that needs more room than is free
+    enters nothing."""
+    pc.autotune_reset()
+    full = [_tuned(bits, dt, 0, leaf, 2048, 1024) for bits in range(32) for dt in (0, 1) for leaf in (0, 1, 2, 3)]
+    assert len(full) == 256
+    pc.autotune_import(full)
+    assert len(pc.autotune_export()) == 256
+    pc.autotune_import(full[:10])  # the same classes again: no room needed
+    with pytest.raises(pc.PCError) as e:
+        pc.autotune_import([_tuned(5, 0, 0, 7, 2048, 1024)])
+    assert e.value.status == pc.PC_ERR_CAPACITY
+    pc.autotune_reset()
+    with pytest.raises(pc.PCError) as e:
+        pc.autotune_import(full + [_tuned(5, 0, 0, 7, 2048, 1024)])
+    assert e.value.status == pc.PC_ERR_CAPACITY
+    assert pc.autotune_export() == []
