@@ -171,3 +171,28 @@ def test_widest_rule_follows_the_long_side(oracle_mod):
     assert len(xs) == 4 and all(xs[i].max() <= xs[i + 1].min() for i in range(3))
     o2, f2, c2 = oracle_mod.kdtree(q, 1024)
     assert [order[o:o + c].tolist() for o, c in zip(off, cnt)] != [o2[o:o + c].tolist() for o, c in zip(f2, c2)]
+
+
+def test_two_clusters_example_splits_the_larger_cluster(oracle_mod):
+    """The paper's example of the median rule's limitation (golden file
+    two_clusters_sec6.json): 100 particles in two clusters of 70 and 30 are split
+    50 / 50, so 20 particles of the larger cluster go to the side of the smaller."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "two_clusters_sec6.json")) as f:
+        g = json.load(f)
+    big, small = g["cluster_sizes"]
+    rng = np.random.default_rng(70)
+    a = np.column_stack([rng.normal(10.0, 1.0, big), rng.uniform(0, 1, big), rng.uniform(0, 1, big)])
+    b = np.column_stack([rng.normal(200.0, 1.0, small), rng.uniform(0, 1, small), rng.uniform(0, 1, small)])
+    pos = np.concatenate([a, b])
+    shuffle = rng.permutation(g["n"])
+    pos = pos[shuffle].astype(np.float32)
+    in_big = shuffle < big  # particle i of the input came from the larger cluster
+    q = oracle_mod.quantize(pos, oracle_mod.REL, 1e-4)
+    order, off, cnt = oracle_mod.kdtree(q, g["n"] // 2)
+    assert cnt.tolist() == g["first_split_sizes"]
+    left, right = order[off[0]:off[0] + cnt[0]], order[off[1]:off[1] + cnt[1]]
+    assert in_big[left].all()  # the smaller coordinates: only the larger cluster
+    assert int(in_big[right].sum()) == big - g["first_split_sizes"][0] and int((~in_big[right]).sum()) == small
