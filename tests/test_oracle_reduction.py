@@ -149,3 +149,40 @@ def test_rounds_stay_close_to_the_one_box_order(oracle_mod, gen, n, r, mode, eb)
     assert len(rounds) < len(plain) and len(one) < len(plain)
     assert nr < n1  # rounds take several boxes at once
     assert abs(len(rounds) / len(one) - 1.0) <= 0.006
+
+
+def test_paper_box_length_holds_the_integer_range(oracle_mod):
+    """Eq. 3 (bit box length): a bit box of m_d bits is l_d = 4 eps (2^(m_d - 1) - 0.5)
+    long, centred at its centre particle, i.e. 2^(m_d - 1) - 0.5 lattice steps
+    (2 eps) each side.  In doubled lattice units, to stay exact: the codes inside
+    it are exactly those within 2^(m_d - 1) - 1 of the centre code (the integer
+    range this library uses, reading 13); every particle of the leaf the oracle's
+    bit box comes from is inside; two boxes share a lattice code exactly when
+    their integer ranges overlap, and closed boxes one step further apart touch
+    only between lattice codes."""
+    rng = np.random.default_rng(13)
+
+    def inside(x, c, m):  # Eq. 3, closed box, doubled units
+        return 2 * abs(x - c) <= (1 << m) - 1 if m else x == c
+
+    for _ in range(300):
+        n = int(rng.integers(1, 40))
+        q = rng.integers(0, 1 << int(rng.integers(1, 12)), (n, 3)).astype(np.int64)
+        _, _, _, qref, m = oracle_mod.bitbox(q)
+        for d in range(3):
+            c, md = int(qref[d]), int(m[d])
+            h = (1 << (md - 1)) - 1 if md else 0
+            for x in range(c - h - 3, c + h + 4):
+                assert inside(x, c, md) == (abs(x - c) <= h)
+            assert all(inside(int(x), c, md) for x in q[:, d])
+    for _ in range(2000):
+        ma, mb = (int(v) for v in rng.integers(0, 8, 2))
+        ha = (1 << (ma - 1)) - 1 if ma else 0
+        hb = (1 << (mb - 1)) - 1 if mb else 0
+        delta = int(rng.integers(0, ha + hb + 4))
+        shared = any(inside(x, 0, ma) and inside(x, delta, mb) for x in range(-ha - 2, delta + hb + 3))
+        assert shared == (delta <= ha + hb)
+        # the closed real boxes: half-lengths ha + 1/2 and hb + 1/2 steps (a box of m_d = 0 is a point)
+        touch = 2 * delta <= ((1 << ma) - 1 if ma else 0) + ((1 << mb) - 1 if mb else 0)
+        if ma and mb:
+            assert touch == (delta <= ha + hb + 1)
