@@ -635,7 +635,8 @@ def run_extras(pc, dev, pos, args):
                     "lanes": b["lanes"], "batched_round_trip_gbs": b["batched"]["round_trip_gbs"],
                     "one_call_per_snapshot_round_trip_gbs": b["one_call_per_snapshot"]["round_trip_gbs"],
                     "speedup_round_trip": b["speedup_round_trip"], "identical_sizes": b["identical_sizes"],
-                    "compression_ratio": b["compression_ratio"], "tuning": BATCH_TUNING, "steps": 2}
+                    "compression_ratio": b["compression_ratio"], "tuning": BATCH_TUNING,
+                    "tuned_knobs": b["tuned_knobs"], "steps": 2}
     torch.cuda.empty_cache()
     v = serve_measure(pc, dev, 1, 0)
     out["serve"] = {"workload": SERVE_WORKLOAD, "requests": v["requests"], "lanes": v["lanes"],
@@ -689,6 +690,13 @@ def _pools(dev, size, gens, dtypes):
         for dt in dtypes:
             out[(g, dt)] = torch.from_numpy(generate(g, size, dt, seed=0)).to(dev)
     return out
+
+
+def knob_summary(pc):
+    """What the launch-knob autotuner chose: the tuned classes and how often each value was picked."""
+    classes = pc.autotune_export()
+    count = lambda key: {str(v): sum(1 for c in classes if c[key] == v) for v in sorted({c[key] for c in classes})}
+    return {"classes": len(classes), "warp_node_max": count("warp_node_max"), "warp_leaf_max": count("warp_leaf_max")}
 
 
 def batch_measure(pc, dev, world, rank, steps, warmup):
@@ -762,6 +770,7 @@ def batch_measure(pc, dev, world, rank, steps, warmup):
         results[name + "_sizes"] = sizes
     b, q = results["batched"], results["sequential"]
     out = {"snapshots": len(jobs), "particles": particles, "lanes": lanes, "batched": b, "one_call_per_snapshot": q,
+           "tuned_knobs": knob_summary(pc),
            "speedup_round_trip": round(b["round_trip_gbs"] / q["round_trip_gbs"], 3),
            # the batched streams are the plain calls' streams
            "identical_sizes": bool(results["batched_sizes"] == results["sequential_sizes"]),
@@ -797,7 +806,7 @@ def run_batch(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single"},
             "batched": b, "one_call_per_snapshot": r["one_call_per_snapshot"],
             "speedup_round_trip": r["speedup_round_trip"], "identical_sizes": r["identical_sizes"],
-            "compression_ratio": r["compression_ratio"],
+            "compression_ratio": r["compression_ratio"], "tuned_knobs": r["tuned_knobs"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -70,3 +70,21 @@ def test_batch_workload_config_is_sized_like_the_leaf_autotuner_alone():
         assert pc.pc_compress_workspace_size(n, dt, cfg) == pc.pc_compress_workspace_size(n, dt, pc.LEAF_AUTO)
     assert pc.pc_compress_batch_workspace_size([(n, dt, cfg) for n, dt in items], 16) == \
         pc.pc_compress_batch_workspace_size([(n, dt, pc.LEAF_AUTO) for n, dt in items], 16)
+
+
+def test_knob_summary_counts_the_tuned_classes():
+    """The batch line's `tuned_knobs`: how many classes the launch-knob autotuner
+    tuned and how often it picked each value (here from imported classes)."""
+    import paper_2404_02826_gb300 as pc
+    from paper_2404_02826_gb300 import build as pcbuild
+
+    pcbuild.build()
+    pc.load()
+    pc.autotune_reset()
+    assert bench.knob_summary(pc) == {"classes": 0, "warp_node_max": {}, "warp_leaf_max": {}}
+    mk = lambda bits, node, leaf: {"n_bits": bits, "dtype": 0, "device": 0, "flags": 1, "leaf_size": 0,
+                                   "warp_node_max": node, "warp_leaf_max": leaf}
+    pc.autotune_import([mk(15, 2048, 1024), mk(16, 4096, 1024), mk(17, 4096, 512)])
+    assert bench.knob_summary(pc) == {"classes": 3, "warp_node_max": {"2048": 1, "4096": 2},
+                                      "warp_leaf_max": {"512": 1, "1024": 2}}
+    pc.autotune_reset()
