@@ -166,14 +166,15 @@ typedef struct {
 
 /* Launch-knob autotuning (no counterpart in the paper): the autotuner's choice
  * of threads per node (warp_node_max) and packing tile (warp_leaf_max).  Calls
- * are grouped in classes by the bit length of n, dtype, the other flags and
- * leaf_size.  The first call of a class writes its stream with the default
- * knobs, then compresses the same input again under each candidate that
+ * are grouped in classes by the bit length of n, dtype, the current CUDA
+ * device, the other flags and leaf_size.  The first call of a class writes its
+ * stream with the config's own knobs (the defaults for 0), then compresses
+ * the same input again under each candidate that
  * changes the launches for that input (threads per node 512 .. 8192, then
  * packing tile 256 .. 4096 with the best threads per node; each timed on the
  * host clock, best of two) and keeps the fastest for the class; later calls of
  * the class run with it.  While one call of a class is tuning, other calls of
- * that class run with the defaults.  The stream is the same under every
+ * that class run with their config's own knobs.  The stream is the same under every
  * candidate (the tuner checks its size).  pc_tuned_config reports a class's
  * choice as a config for a plain call, which then makes the same launches and
  * writes the same stream.  The timing runs reuse the call's output, workspace
